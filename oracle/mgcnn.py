@@ -1,0 +1,234 @@
+"""MGCNN setup and solve phases in FP64 (Sec. 3.2, Algorithm 2; Sec. 3.3, Algorithm 3).
+
+Weights (a dict of float64 arrays; C channels, F = 5 setup features,
+nu_d / nu_u layers in ResNetDown / ResNetUp, S = 4 setup layers):
+
+  solve phase                                     setup phase
+  w_in   [C, 1, 3, 3]   reChannelCNN rhs -> C     sw_in [C, F, 3, 3], sb_in [C]
+  w_down [nu_d, C, C, 3, 3]                        sw    [S, C, C, 3, 3], sb [S, C]
+  w_up   [nu_u, C, C, 3, 3]                        sw_R  [C, C, 3, 3]   setup RCNN
+  w_R    [C, C, 3, 3]   RCNN   [c_out, c_in]
+  w_P    [C, C, 3, 3]   TCNN   [c_in, c_out]
+  w_out  [1, C, 3, 3]   reChannelCNN C -> sol
+
+One set serves every level (P3, Sec. 3.1).  The solve phase has no bias and
+no activation (P2), so B is linear in the right-hand side.
+
+Readings where the paper is silent (each is listed in the design notes):
+* setup input: the scale-free stencil [a_W, a_E, a_S, a_N]/a_C and
+  log10(h^2 a_C) (Remark "Matrix coefficients as input"), F = 5;
+* setup output scaling: setup_out_l is divided by a_C of the level-l
+  rediscretised operator (k restricted as in operator.restrict_k), a Jacobi-like D^{-1} that gives B the
+  units of A^{-1}; `scale_by_diag=False` gives the unscaled form;
+* the setup RCNN has its own weights, no bias; every setup layer is
+  tanh(K z + b) + z (Eq. resnet_nonlinear), the last one included.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import convnet as cn
+from .grid import spacing
+from .operator import Stencil, apply
+
+SETUP_LAYERS = 4
+FEATURES = 5
+
+
+def random_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, scale: float = 0.3) -> dict:
+    """Random weights of the right shapes (test inputs; not a trained solver)."""
+    def r(*shape, fan):
+        return rng.standard_normal(shape) * (scale / np.sqrt(fan))
+    return {
+        "w_in": r(C, 1, 3, 3, fan=9), "w_down": r(nu_d, C, C, 3, 3, fan=9 * C),
+        "w_up": r(nu_u, C, C, 3, 3, fan=9 * C), "w_R": r(C, C, 3, 3, fan=9 * C),
+        "w_P": r(C, C, 3, 3, fan=9 * C), "w_out": r(1, C, 3, 3, fan=9 * C),
+        "sw_in": r(C, FEATURES, 3, 3, fan=9 * FEATURES), "sb_in": r(C, fan=1),
+        "sw": r(SETUP_LAYERS, C, C, 3, 3, fan=9 * C), "sb": r(SETUP_LAYERS, C, fan=1),
+        "sw_R": r(C, C, 3, 3, fan=9 * C),
+    }
+
+
+def setup_features(st: Stencil) -> np.ndarray:
+    """[a_W/a_C, a_E/a_C, a_S/a_C, a_N/a_C, log10(h^2 a_C)] on the finest grid, shape [5, n, n]."""
+    h = spacing(st.n)
+    return np.stack([st.aW / st.aC, st.aE / st.aC, st.aS / st.aC, st.aN / st.aC,
+                     np.log10(h * h * st.aC)])
+
+
+def setup(weights: dict, stencils: list[Stencil], scale_by_diag: bool = True, keep: dict | None = None):
+    """Algorithm 2.  Returns setup_outs[l], each [C, n_l, n_l].
+
+    coef_1 = reChannelCNN(features); for each level: setup_out_l =
+    NonLinearResNet(coef_l) (4 x [z <- tanh(K_i z + b_i) + z]), then
+    coef_{l+1} = RCNN(coef_l).  If `keep` is a dict, the intermediates needed by
+    the adjoint are stored in it.
+    """
+    L = len(stencils)
+    feat = setup_features(stencils[0])
+    c = cn.conv_same(feat, weights["sw_in"], weights["sb_in"])
+    outs, cs, zs, ts = [], [], [], []
+    for l in range(L):
+        cs.append(c)
+        z = c
+        zl, tl = [], []
+        for i in range(SETUP_LAYERS):
+            zl.append(z)
+            t = np.tanh(cn.conv_same(z, weights["sw"][i], weights["sb"][i]))
+            tl.append(t)
+            z = t + z
+        zs.append(zl)
+        ts.append(tl)
+        outs.append(z / stencils[l].aC if scale_by_diag else z)
+        if l < L - 1:
+            c = cn.rcnn(c, weights["sw_R"])
+    if keep is not None:
+        keep.update(feat=feat, c=cs, z=zs, t=ts)
+    return outs
+
+
+def solve_phase(weights: dict, s: list[np.ndarray], r: np.ndarray, keep: dict | None = None) -> np.ndarray:
+    """Algorithm 3: one application e = B r of the solve network.
+
+    x_1 = reChannelCNN(r); down loop: x_l <- ResNetDown(s_l, x_l) then
+    x_{l+1} = RCNN(x_l); up loop: x_l <- ResNetUp(s_l, x_l) then
+    x_{l-1} <- x_{l-1} + TCNN(x_l); sol = reChannelCNN(x_1).
+    Each ResNet layer is y = K (s_l * x) + x (Eq. heteroresnet).
+    """
+    L = len(s)
+    sizes = [t.shape[1] for t in s]
+    nu_d = weights["w_down"].shape[0]
+    nu_u = weights["w_up"].shape[0]
+    x = [None] * L
+    x0, down_in, x_down, up_in, x_fin = [None] * L, [], [None] * L, [None] * L, [None] * L
+    x[0] = cn.conv_same(r[None], weights["w_in"])
+    for l in range(L):
+        x0[l] = x[l]
+        ins = []
+        for i in range(nu_d):
+            ins.append(x[l])
+            x[l] = x[l] + cn.conv_same(s[l] * x[l], weights["w_down"][i])
+        down_in.append(ins)
+        x_down[l] = x[l]
+        if l < L - 1:
+            x[l + 1] = cn.rcnn(x[l], weights["w_R"])
+    for l in reversed(range(L)):
+        ins = []
+        for i in range(nu_u):
+            ins.append(x[l])
+            x[l] = x[l] + cn.conv_same(s[l] * x[l], weights["w_up"][i])
+        up_in[l] = ins
+        x_fin[l] = x[l]
+        if l > 0:
+            x[l - 1] = x[l - 1] + cn.tcnn(x[l], weights["w_P"], sizes[l - 1])
+    e = cn.conv_same(x[0], weights["w_out"])[0]
+    if keep is not None:
+        keep.update(x0=x0, down_in=down_in, x_down=x_down, up_in=up_in, x_fin=x_fin)
+    return e
+
+
+def stationary_solve(weights: dict, s: list[np.ndarray], A: Stencil, f: np.ndarray,
+                     u0: np.ndarray | None, tol: float, maxit: int):
+    """Eq. 1 with B = solve_phase: u^{k+1} = u^k + B (f - A u^k).
+
+    Stops when ||r^k||_2 / ||f||_2 <= tol (checked before each cycle) or k = maxit.
+    Returns (u, iters, relres_history, iterates) with iterates[k] = u^k.
+    """
+    u = np.zeros_like(f) if u0 is None else u0.copy()
+    fn = np.linalg.norm(f)
+    if fn == 0.0:
+        return np.zeros_like(f), 0, [0.0], [np.zeros_like(f)]
+    hist, iterates = [], [u.copy()]
+    for k in range(maxit + 1):
+        r = f - apply(A, u)
+        rel = np.linalg.norm(r) / fn
+        hist.append(rel)
+        if rel <= tol or k == maxit:
+            return u, k, hist, iterates
+        u = u + solve_phase(weights, s, r)
+        iterates.append(u.copy())
+    raise AssertionError("unreachable")
+
+
+# --------------------------------------------------------------------------
+# Weights that turn the solve phase into classical GMG V(2,2) (weighted Jacobi,
+# full-weighting restriction, bilinear prolongation, rediscretised A_l).
+#
+# Any stencil acting on e rewrites in source-side form:
+#   sum_o a_o(p) e(p+o) = sum_o  ~a_o(q) e(q)  with q = p + o, ~a_o(q) = a_o(q - o),
+# so a setup tensor that multiplies a layer's input (Eq. heteroresnet) carries
+# the variable coefficient and the 3x3 kernel only selects the tap o.
+# Channels (13): E_C E_W E_E E_S E_N  (copies of e for the Jacobi update)
+#                G_C G_W G_E G_S G_N  (copies of e for the defect)
+#                F_J F_G              (copies of the level right-hand side)
+#                D                    (defect)
+# --------------------------------------------------------------------------
+GMG_CHANNELS = 13
+_E = [0, 1, 2, 3, 4]
+_G = [5, 6, 7, 8, 9]
+_FJ, _FG, _D = 10, 11, 12
+# offsets o = (dy, dx) for C, W, E, S, N and the 3x3 tap that reads p + o
+_OFFS = [(0, 0), (0, -1), (0, 1), (-1, 0), (1, 0)]
+_TAPS = [(dy + 1, dx + 1) for dy, dx in _OFFS]
+
+
+def gmg_equivalent_weights(nu1: int = 2, nu2: int = 2) -> dict:
+    """Solve-phase weights (C = 13) for GMG V(nu1, nu2): ResNetDown = nu1 Jacobi layers
+    and one defect layer, ResNetUp = nu2 Jacobi layers, RCNN = full weighting of the
+    defect into both rhs copies, TCNN = bilinear interpolation of E_C into every e copy."""
+    C = GMG_CHANNELS
+    KJ = np.zeros((C, C, 3, 3))
+    for t in _E + _G:
+        for ch, (a, b) in zip(_E, _TAPS):
+            KJ[t, ch, a, b] = 1.0
+        KJ[t, _FJ, 1, 1] = 1.0
+    KD = np.zeros((C, C, 3, 3))
+    for ch, (a, b) in zip(_G, _TAPS):
+        KD[_D, ch, a, b] = 1.0
+    KD[_D, _FG, 1, 1] = 1.0
+    fw = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 16.0
+    bil = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 4.0
+    R = np.zeros((C, C, 3, 3))
+    R[_FJ, _D] = fw
+    R[_FG, _D] = fw
+    P = np.zeros((C, C, 3, 3))
+    for t in _E + _G:
+        P[_E[0], t] = bil
+    w_in = np.zeros((C, 1, 3, 3))
+    w_in[_FJ, 0, 1, 1] = 1.0
+    w_in[_FG, 0, 1, 1] = 1.0
+    w_out = np.zeros((1, C, 3, 3))
+    w_out[0, _E[0], 1, 1] = 1.0
+    return {"w_in": w_in, "w_down": np.stack([KJ] * nu1 + [KD]), "w_up": np.stack([KJ] * nu2),
+            "w_R": R, "w_P": P, "w_out": w_out}
+
+
+def _shift_to_source(a: np.ndarray, dy: int, dx: int) -> np.ndarray:
+    """out[q] = a[q - o] for o = (dy, dx), zero where q - o is outside the grid."""
+    n = a.shape[0]
+    out = np.zeros_like(a)
+    qy = slice(max(dy, 0), n + min(dy, 0))
+    qx = slice(max(dx, 0), n + min(dx, 0))
+    py = slice(max(-dy, 0), n + min(-dy, 0))
+    px = slice(max(-dx, 0), n + min(-dx, 0))
+    out[qy, qx] = a[py, px]
+    return out
+
+
+def gmg_equivalent_setup(stencils: list[Stencil], omega: float = 0.8) -> list[np.ndarray]:
+    """Setup tensors for `gmg_equivalent_weights` on every level:
+    s[E_o](q) = -omega a_o(q-o)/a_C(q-o),  s[F_J] = omega/a_C,
+    s[G_o](q) = -a_o(q-o),                 s[F_G] = 1,  s[D] = 0."""
+    outs = []
+    for st in stencils:
+        n = st.n
+        s = np.zeros((GMG_CHANNELS, n, n))
+        coeffs = [st.aC, st.aW, st.aE, st.aS, st.aN]
+        for k, ((dy, dx), a) in enumerate(zip(_OFFS, coeffs)):
+            s[_E[k]] = _shift_to_source(-omega * a / st.aC, dy, dx)
+            s[_G[k]] = _shift_to_source(-a, dy, dx)
+        s[_FJ] = omega / st.aC
+        s[_FG] = 1.0
+        outs.append(s)
+    return outs
+

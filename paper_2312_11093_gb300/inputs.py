@@ -1,0 +1,111 @@
+"""Seeded synthetic inputs: coefficient fields and right-hand sides.
+
+This module is the only code shared by the CUDA path's tests/bench and the
+CPU oracle.  It draws random numbers and shapes them into coefficient fields
+of the kinds the workloads use; it holds none of the solver's arithmetic (no
+discretisation, no network, no iteration).  Importing it does not load the
+CUDA library.
+
+Grid convention: an n x n interior grid on the unit square with h = 1/(n+1);
+nodal fields that include the Dirichlet boundary ring have shape
+(n+2, n+2) and are indexed [j, i] with x = i*h, y = j*h.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "block_board_k",
+    "gaussian_random_field",
+    "lognormal_k",
+    "random_blocks_k",
+    "checkerboard_k",
+    "channelised_k",
+    "paper_white_noise_mu",
+    "normal_rhs",
+    "unit_rhs",
+]
+
+
+def block_board_k(n: int, rng: np.random.Generator, nblocks: int = 8, cell: int = 4,
+                  log10_lo: float = -1.0, log10_hi: float = 1.0) -> np.ndarray:
+    """Piecewise-constant nodal k on an nblocks x nblocks board of cell x cell blocks.
+
+    Draws nblocks^2 uniforms for log10 k (block-row major: block j then block i)
+    and assigns node (j, i), 0 <= i, j <= n+1, to block
+    (min(j // cell, nblocks-1), min(i // cell, nblocks-1)).
+    """
+    logk = rng.uniform(log10_lo, log10_hi, size=(nblocks, nblocks))
+    idx = np.minimum(np.arange(n + 2) // cell, nblocks - 1)
+    return 10.0 ** logk[idx[:, None], idx[None, :]]
+
+
+def gaussian_random_field(m: int, corr_len: float, h: float, rng: np.random.Generator) -> np.ndarray:
+    """Stationary Gaussian field on an m x m node lattice of spacing h.
+
+    Covariance sigma^2 exp(-r^2 / (2 l^2)) with sigma = 1, made by filtering
+    white noise with a Gaussian of standard deviation l/sqrt(2) (the
+    self-convolution of that Gaussian has the target correlation), through an
+    FFT on a grid padded by 4 l on each side so the periodic wrap does not
+    correlate opposite edges, and normalised so the field has unit variance.
+    """
+    s = corr_len / np.sqrt(2.0)
+    pad = int(np.ceil(4.0 * corr_len / h)) + 1
+    M = m + 2 * pad
+    noise = rng.standard_normal((M, M))
+    d = np.minimum(np.arange(M), M - np.arange(M)) * h
+    g1 = np.exp(-d * d / (2.0 * s * s))
+    kern = g1[:, None] * g1[None, :]
+    kern /= np.sqrt(np.sum(kern * kern))
+    field = np.fft.irfft2(np.fft.rfft2(noise) * np.fft.rfft2(kern), s=(M, M))
+    return np.ascontiguousarray(field[pad:pad + m, pad:pad + m])
+
+
+def lognormal_k(n: int, corr_len: float, rng: np.random.Generator, sigma: float = 1.0) -> np.ndarray:
+    """Nodal k = exp(sigma * g) on (n+2)^2 nodes, g a unit-variance GRF."""
+    h = 1.0 / (n + 1)
+    return np.exp(sigma * gaussian_random_field(n + 2, corr_len, h, rng))
+
+
+def random_blocks_k(n: int, rng: np.random.Generator, board: int = 16,
+                    log10_lo: float = -2.0, log10_hi: float = 2.0) -> np.ndarray:
+    """Piecewise-constant nodal k on a board x board partition of the unit square,
+    log10 k ~ U(log10_lo, log10_hi) per block (contrast up to 1e4)."""
+    logk = rng.uniform(log10_lo, log10_hi, size=(board, board))
+    idx = np.minimum((np.arange(n + 2) * board) // (n + 2), board - 1)
+    return 10.0 ** logk[idx[:, None], idx[None, :]]
+
+
+def checkerboard_k(n: int, board: int = 16, k_lo: float = 1.0, k_hi: float = 100.0) -> np.ndarray:
+    """Nodal k on a board x board checkerboard with values {k_lo, k_hi}."""
+    idx = np.minimum((np.arange(n + 2) * board) // (n + 2), board - 1)
+    par = (idx[:, None] + idx[None, :]) % 2
+    return np.where(par == 0, k_lo, k_hi).astype(np.float64)
+
+
+def channelised_k(n: int, rng: np.random.Generator, corr_len: float = 0.02,
+                  quantile: float = 0.70, k_lo: float = 1.0, k_hi: float = 1e3) -> np.ndarray:
+    """Binary channelised nodal k: k_hi where a GRF exceeds its `quantile`, else k_lo."""
+    h = 1.0 / (n + 1)
+    g = gaussian_random_field(n + 2, corr_len, h, rng)
+    thr = np.quantile(g, quantile)
+    return np.where(g > thr, k_hi, k_lo).astype(np.float64)
+
+
+def paper_white_noise_mu(n: int, rng: np.random.Generator, Re: float = 1000.0) -> np.ndarray:
+    """The paper's coefficient generator (Sec. 4.1): white noise mapped linearly to
+    a power in [0, log10 Re], then coef = 10^(-power) in [1/Re, 1]; returned on the
+    n x n interior nodes."""
+    w = rng.uniform(0.0, 1.0, size=(n, n))
+    power = w * np.log10(Re)
+    return 10.0 ** (-power)
+
+
+def normal_rhs(n: int, rng: np.random.Generator) -> np.ndarray:
+    """f iid N(0, 1) on the n x n interior nodes."""
+    return rng.standard_normal((n, n))
+
+
+def unit_rhs(n: int) -> np.ndarray:
+    """The paper's test right-hand side, constant 1 (Sec. 4.1)."""
+    return np.ones((n, n))

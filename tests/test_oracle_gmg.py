@@ -1,0 +1,76 @@
+"""Pins for the oracle's classical GMG (Sec. 2.3) and its outer stationary loop (Eq. 1)."""
+import numpy as np
+import pytest
+
+from oracle import gmg
+from oracle import operator as op
+from oracle.grid import num_levels
+from paper_2312_11093_gb300 import inputs
+
+
+def cfg0_problem():
+    """31x31, h = 1/32, 8x8 board of 4x4-cell blocks with log10 k ~ U(-1, 1),
+    b = (1, 0.5), f ~ N(0, 1), seed 0 (block draws first, then f)."""
+    n = 31
+    rng = np.random.default_rng(0)
+    k = inputs.block_board_k(n, rng)
+    f = inputs.normal_rhs(n, rng)
+    return n, k, (1.0, 0.5), f
+
+
+def test_transfer_transpose_relation():
+    """Full weighting is a quarter of the transpose of bilinear prolongation."""
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal((15, 15))
+    c = rng.standard_normal((7, 7))
+    lhs = np.sum(gmg.restrict_fw(d) * c)
+    rhs = 0.25 * np.sum(d * gmg.prolong_bilinear(c, 15))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_transfers_on_polynomials():
+    """FW keeps a linear field (away from the boundary); bilinear prolongation
+    reproduces a linear field at fine nodes whose coarse neighbours are interior."""
+    n, nc = 31, 15
+    h, hc = 1.0 / (n + 1), 1.0 / (nc + 1)
+    x = np.arange(1, n + 1) * h
+    X, Y = np.meshgrid(x, x)
+    lin = 0.3 + 2 * X - 1.5 * Y
+    xc = np.arange(1, nc + 1) * hc
+    Xc, Yc = np.meshgrid(xc, xc)
+    np.testing.assert_allclose(gmg.restrict_fw(lin), 0.3 + 2 * Xc - 1.5 * Yc, rtol=1e-13)
+    e = gmg.prolong_bilinear(0.3 + 2 * Xc - 1.5 * Yc, n)
+    np.testing.assert_allclose(e[1:-1, 1:-1], lin[1:-1, 1:-1], rtol=1e-13)
+
+
+def test_poisson_vcycle_convergence_factor():
+    """Constant k, b = 0, V(2,2), omega = 0.8.  The coarsest 3x3 grid is smoothed, not
+    solved, so the asymptotic factor is set by its smoothest mode: Jacobi damps it by
+    1 - omega * 2 sin^2(pi h_c / 2) per sweep with h_c = 1/4, over 4 sweeps
+    (the finer levels contract much faster).  Observed factor within 10% of that."""
+    n = 63
+    sts = op.level_stencils_div(np.ones((n + 2, n + 2)), (0.0, 0.0), num_levels(n))
+    f = np.random.default_rng(1).standard_normal((n, n))
+    _, it, hist, _ = gmg.stationary_solve(sts, f, None, 1e-10, 60)
+    rate = (hist[-1] / hist[-4]) ** (1 / 3)
+    coarse = (1 - 0.8 * 2 * np.sin(np.pi / 8) ** 2) ** 4
+    assert abs(rate - coarse) < 0.1 * coarse, (rate, coarse)
+    assert it < 30
+
+
+def test_cfg0_gmg_matches_direct_solve():
+    n, k, b, f = cfg0_problem()
+    sts = op.level_stencils_div(k, b, num_levels(n))
+    u, it, hist, _ = gmg.stationary_solve(sts, f, None, 1e-10, 200)
+    assert hist[-1] <= 1e-10 and it < 200
+    ustar = np.linalg.solve(op.dense_matrix(sts[0]), f.ravel()).reshape(n, n)
+    assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < 1e-7
+
+
+def test_zero_rhs_and_maxit():
+    n, k, b, f = cfg0_problem()
+    sts = op.level_stencils_div(k, b, num_levels(n))
+    u, it, hist, _ = gmg.stationary_solve(sts, np.zeros_like(f), None, 1e-10, 5)
+    assert it == 0 and not u.any()
+    _, it, hist, _ = gmg.stationary_solve(sts, f, None, 1e-30, 3)
+    assert it == 3 and len(hist) == 4
