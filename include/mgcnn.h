@@ -1,0 +1,185 @@
+/*
+ * mgcnn.h -- C ABI of the GB300 MGCNN solver library (libmgcnn.so).
+ *
+ * MGCNN (Xie, Lv, Zhang, "MGCNN: a learnable multigrid solver for sparse
+ * linear systems from PDEs on structured grids", arXiv 2312.11093) solves
+ * A_coef sol = rhs (Sec. 2.1, "Solver as Decoder") for a 5-point
+ * convection-diffusion operator on an n x n interior grid of the unit square
+ * with zero Dirichlet boundary, by the stationary iteration
+ *     sol^{k+1} = sol^k + B (rhs - A sol^k)                  (Sec. 2.2, Eq. 1)
+ * where B is the solve phase of a multigrid-shaped CNN (Sec. 3.3, Algorithm 3)
+ * whose per-level setup tensors come from a setup network run once per
+ * coefficient field (Sec. 3.2, Algorithm 2).
+ *
+ * Conventions for every entry point
+ *   - Grids: n = 2^m - 1, m >= 2 (n = 3, 7, 15, ..., 4095).  Level sizes
+ *     n_1 = n, n_{l+1} = (n_l - 1)/2 down to 3; L = log2(n+1) - 1 levels unless
+ *     the config asks for fewer.  h = 1/(n+1).
+ *   - Scalar fields are row-major [j][i], x = i h, y = j h (y grows with j);
+ *     interior fields have n*n entries, nodal coefficient fields that include
+ *     the boundary ring (n+2)*(n+2).
+ *   - Multi-channel tensors (setup tensors) are [j][i][c] per level, levels
+ *     concatenated finest first.
+ *   - Array arguments may be HOST or DEVICE pointers: the library asks the
+ *     driver which (cudaPointerGetAttributes).  Device arrays are used in
+ *     place (they must live on the context's device); host arrays are copied
+ *     to the context's device buffers and results copied back, on the
+ *     context's stream, before the call returns.
+ *   - The caller owns every array it passes; the context owns its device
+ *     workspaces.  Nothing allocated by the library is freed by the caller
+ *     except through mgcnn_destroy.
+ *   - Calls on one context are not thread-safe.  No C++ exception and no
+ *     exit() crosses the ABI; every failure is a negative status code and a
+ *     message retrievable with mgcnn_last_error.
+ *   - Every call that returns a status synchronises the context's stream
+ *     before returning, unless its comment says otherwise.
+ */
+#ifndef MGCNN_H
+#define MGCNN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes.  >0: the result is valid but a limit was hit. */
+enum {
+  MGCNN_OK = 0,
+  MGCNN_NOT_CONVERGED = 1,   /* maxit cycles applied without reaching tol        */
+  MGCNN_ERR_ARG = -1,        /* null pointer, bad count, bad enum value          */
+  MGCNN_ERR_SIZE = -2,       /* n not 2^m-1, too many levels, unsupported C      */
+  MGCNN_ERR_STATE = -3,      /* e.g. solve before setup, weights never set       */
+  MGCNN_ERR_NOMEM = -4,      /* device allocation failed                         */
+  MGCNN_ERR_CUDA = -5,       /* a CUDA runtime call or kernel launch failed      */
+  MGCNN_ERR_NONFINITE = -6,  /* NaN/Inf in an input or in the iterate's residual */
+  MGCNN_ERR_TIMEOUT = -7     /* a bounded device-side wait gave up               */
+};
+
+/* Arithmetic of the solve phase.  The residual, the update and the
+ * convergence norm are FP64 in every mode (defect correction). */
+enum {
+  MGCNN_PREC_FP64 = 0,       /* setup and solve networks in FP64                 */
+  MGCNN_PREC_MIXED_BF16 = 1  /* setup in FP32; solve network with BF16 tensors,
+                                BF16 x BF16 products, FP32 accumulation          */
+};
+
+/* Discretisation that turns the coefficient field into A. */
+enum {
+  /* -div(k grad u) + b.grad u = f (Remark 2.1, Eq. convection_diffusion_div):
+   * nodal k on the (n+2)^2 nodes incl. the boundary ring, face k the harmonic
+   * mean of its two nodes, first-order upwind convection.  Coarse levels
+   * rediscretise with k restricted by full weighting of log k. */
+  MGCNN_PDE_DIV_HARMONIC = 0,
+  /* -mu Lap u + v.grad u = f (Sec. 2.5, Eqs. convection_diffusion(_kernel)):
+   * nodal mu on the n^2 interior nodes, 5-point Laplacian scaled by mu plus
+   * first-order upwind convection; coarse levels sample mu (injection). */
+  MGCNN_PDE_NONDIV = 1
+};
+
+typedef struct mgcnn_ctx mgcnn_ctx;
+
+typedef struct {
+  int channels;      /* C, hidden channels of both networks (Sec. 4.2: 4, 8, 12);
+                        supported: 4, 8, 12, 13, 16                              */
+  int down_layers;   /* layers ("sweeps") in ResNetDown, >= 1 (Sec. 3.3)      */
+  int up_layers;     /* layers in ResNetUp, >= 1                               */
+  int precision;     /* MGCNN_PREC_*                                           */
+  int pde;           /* MGCNN_PDE_*                                            */
+  int scale_by_diag; /* 1: each setup tensor is divided by a_C of its level's
+                        operator (Jacobi-like scaling); 0: the raw network output */
+  int levels;        /* 0: L = log2(n+1)-1 (coarsest 3x3); else 1..that L     */
+  double bx, by;     /* constant velocity b (or v) of the convection term      */
+} mgcnn_config;
+
+/* Number of doubles in a weight blob for this config.  Layout, in order, all
+ * row-major and shared by every level (principle P3, Sec. 3.1):
+ *   solve phase (Algorithm 3; no bias, no activation -- principle P2)
+ *     w_in   [C][1][3][3]        reChannelCNN rhs -> C channels
+ *     w_down [nu_d][C][C][3][3]  ResNetDown kernels K_down, [c_out][c_in]
+ *     w_up   [nu_u][C][C][3][3]  ResNetUp kernels K_up
+ *     w_R    [C][C][3][3]        RCNN, stride 2, [c_out][c_in]
+ *     w_P    [C][C][3][3]        TCNN, stride 2, [c_in][c_out]
+ *     w_out  [1][C][3][3]        reChannelCNN C -> solution
+ *   setup phase (Algorithm 2; F = 5 input features)
+ *     sw_in  [C][5][3][3], sb_in [C]         reChannelCNN of the features
+ *     sw     [4][C][C][3][3], sb [4][C]      NonLinearResNet, tanh (Eq. resnet_nonlinear)
+ *     sw_R   [C][C][3][3]                    setup RCNN (Eq. setup1)
+ * Tap [a][b] of a same-size layer reads pixel (j+a-1, i+b-1); of RCNN, fine
+ * pixel (2J+a, 2I+b) (0-based interior indices); TCNN adds W[.][.][a][b] x[J][I]
+ * into fine pixel (2J+a, 2I+b).  Returns 0 for an invalid config. */
+size_t mgcnn_weight_count(const mgcnn_config* cfg);
+
+/* Create a context on the current CUDA device.  *out receives the handle.
+ * Errors: ARG (null), SIZE (unsupported channels/layers), CUDA. */
+int mgcnn_create(const mgcnn_config* cfg, mgcnn_ctx** out);
+
+/* Free every device buffer and the handle.  Accepts NULL. */
+void mgcnn_destroy(mgcnn_ctx* ctx);
+
+/* Bind the context to a CUDA stream (cudaStream_t passed as void*; NULL is
+ * the legacy default stream).  All later work is issued on it. */
+int mgcnn_set_stream(mgcnn_ctx* ctx, void* stream);
+
+/* Load the weight blob (layout of mgcnn_weight_count; count must equal it).
+ * The blob is copied; the caller may free it afterwards.  Errors: ARG. */
+int mgcnn_set_weights(mgcnn_ctx* ctx, const double* w, size_t count);
+
+/* Setup phase for one coefficient field (Sec. 3.2, Algorithm 2), once per
+ * problem.  coeff: DIV_HARMONIC -> nodal k, (n+2)^2 doubles, all > 0;
+ * NONDIV -> nodal mu, n^2 doubles, all > 0.  Builds the operator on every
+ * level (Sec. 2.3: rediscretised coarse operators), runs the setup network
+ * on all levels and keeps the setup tensors on the device.
+ * Errors: ARG, SIZE, STATE (weights not set), NOMEM, NONFINITE (k <= 0 or
+ * non-finite), CUDA. */
+int mgcnn_setup(mgcnn_ctx* ctx, const double* coeff, int n);
+
+/* Number of doubles of all setup tensors of the current setup:
+ * sum_l n_l^2 * C.  0 before setup. */
+size_t mgcnn_setup_tensor_count(const mgcnn_ctx* ctx);
+
+/* Replace the setup tensors produced by mgcnn_setup with caller-supplied ones
+ * (layout [level][j][i][c], finest level first; count as above).  Used to run
+ * the solve phase with analytically built setup tensors, e.g. the weights and
+ * tensors that make Algorithm 3 reproduce classical GMG.  Errors: STATE
+ * (no setup), ARG. */
+int mgcnn_set_setup_tensors(mgcnn_ctx* ctx, const double* s, size_t count);
+
+/* Copy the setup tensors out as doubles (layout as above). */
+int mgcnn_get_setup_tensors(mgcnn_ctx* ctx, double* s, size_t count);
+
+/* Copy the level-l operator out: 5 arrays of n_l^2 doubles, in the order
+ * a_C, a_W, a_E, a_S, a_N, with (A u)_p = sum_o a_o(p) u(p+o), zero outside. */
+int mgcnn_get_operator(mgcnn_ctx* ctx, int level, double* out, size_t count);
+
+/* r = f - A u on the finest grid (Eq. 1) in FP64, and ||r||_2^2 in FP64 into
+ * *norm2 (host pointer; may be NULL).  f, u, r: n^2 doubles. */
+int mgcnn_residual(mgcnn_ctx* ctx, const double* f, const double* u, double* r, double* norm2);
+
+/* One application e = B r of the solve phase (Algorithm 3) in the context's
+ * precision: FP64, or for MIXED_BF16 the scaled BF16 network with r and e in
+ * FP64 at the boundary.  r, e: n^2 doubles. */
+int mgcnn_vcycle(mgcnn_ctx* ctx, const double* r, double* e);
+
+/* The stationary iteration (Eq. 1) with B the solve phase:
+ *   for k = 0, 1, ...: r_k = f - A u_k; stop if ||r_k||_2 / ||f||_2 <= tol or
+ *   k == maxit; u_{k+1} = u_k + B r_k.
+ * u: n^2 doubles, in: initial guess, out: the last iterate.  f = 0 gives
+ * u = 0, *iters = 0.  *iters receives the number of cycles applied; relres
+ * (may be NULL) receives ||r_k||/||f|| for k = 0..*iters (room for maxit+1).
+ * Returns OK, NOT_CONVERGED (maxit reached), NONFINITE (a residual norm was
+ * NaN/Inf; u holds the last finite iterate's update), STATE, ARG, CUDA. */
+int mgcnn_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit,
+                int* iters, double* relres);
+
+/* Human-readable name of a status code (static storage). */
+const char* mgcnn_status_string(int status);
+
+/* Message describing the last failure on this context ("" if none). */
+const char* mgcnn_last_error(const mgcnn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGCNN_H */

@@ -1,0 +1,578 @@
+// C ABI of libmgcnn.so (declared in include/mgcnn.h).
+//
+// Drives the setup phase (Algorithm 2 of arXiv 2312.11093), the solve phase
+// (Algorithm 3) and the stationary iteration (Eq. 1) on one GPU.  Every
+// arithmetic step runs in this library's kernels; this file only sequences
+// launches, owns device buffers and moves data across the ABI.
+#include <cmath>
+
+#include "ops.cuh"
+#include "mixed.cuh"
+
+using namespace mgcnn;
+
+// ---------------------------------------------------------------------------
+// Internal helpers
+namespace mgcnn {
+
+Status make_status(int code, const char* fmt, ...) {
+  Status s;
+  s.code = code;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  s.msg = buf;
+  return s;
+}
+
+Status cuda_status(cudaError_t e, const char* what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? MGCNN_ERR_NOMEM : MGCNN_ERR_CUDA;
+  if (e == cudaErrorMemoryAllocation) cudaGetLastError();  // not sticky: clear it
+  return make_status(code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+Status ensure(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return {};
+  release(b);
+  if (bytes == 0) return {};
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+  b.p = p;
+  b.bytes = bytes;
+  return {};
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace mgcnn
+
+namespace {
+
+int finish(mgcnn_ctx* c, const Status& s) {
+  if (c) c->last_error = s.ok() ? std::string() : s.msg;
+  return s.code;
+}
+
+int levels_of(int n) {
+  int m = 0;
+  while ((1 << m) - 1 < n) ++m;
+  if (n < 3 || (1 << m) - 1 != n) return -1;
+  return m - 1;
+}
+
+// Device view of a caller array of `count` doubles: the array itself if it is
+// device memory, else a copy in `stage`.
+Status stage_in(mgcnn_ctx* c, const double* src, size_t count, DevBuf& stage, const double** out) {
+  if (is_device_pointer(src)) {
+    *out = src;
+    return {};
+  }
+  MG_TRY(ensure(stage, count * sizeof(double)));
+  MG_CUDA(cudaMemcpyAsync(stage.p, src, count * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  *out = stage.as<double>();
+  return {};
+}
+
+// Where to write an output of `count` doubles: the caller's device array, or
+// `stage` (copied back by stage_out_finish).
+Status stage_out(const double* dst, size_t count, DevBuf& stage, double** out, bool* host) {
+  if (is_device_pointer(dst)) {
+    *out = const_cast<double*>(dst);
+    *host = false;
+    return {};
+  }
+  MG_TRY(ensure(stage, count * sizeof(double)));
+  *out = stage.as<double>();
+  *host = true;
+  return {};
+}
+
+Status stage_out_finish(mgcnn_ctx* c, double* dst, const double* dev, size_t count, bool host) {
+  if (host) MG_CUDA(cudaMemcpyAsync(dst, dev, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return {};
+}
+
+Status sync(mgcnn_ctx* c) {
+  MG_CUDA(cudaStreamSynchronize(c->stream));
+  return {};
+}
+
+// ||v||_2^2 of N doubles into scalars[slot] on the device.
+Status sumsq(mgcnn_ctx* c, const double* v, size_t N, int slot) {
+  MG_TRY(launch_sumsq(v, N, c->partial.as<double>(), c->stream));
+  MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>() + slot, c->stream));
+  return {};
+}
+
+Status read_scalar(mgcnn_ctx* c, int slot, double* out) {
+  MG_CUDA(cudaMemcpyAsync(c->h_scalars + slot, c->scalars.as<double>() + slot, sizeof(double),
+                          cudaMemcpyDeviceToHost, c->stream));
+  MG_TRY(sync(c));
+  *out = c->h_scalars[slot];
+  return {};
+}
+
+size_t setup_tensor_count(const mgcnn_ctx* c) {
+  size_t t = 0;
+  for (int l = 0; l < c->L; ++l) t += c->lv[l].N() * c->cfg.channels;
+  return t;
+}
+
+// ---- setup network (Algorithm 2) in FP64 or FP32 --------------------------
+// out[l] receives setup_out_l, [n_l^2][C].
+template <typename T>
+Status run_setup_net(mgcnn_ctx* c, const T* W, T* const* out) {
+  const int C = c->cfg.channels;
+  const WeightLayout& wl = c->wl;
+  const size_t CC9 = (size_t)C * C * 9;
+  const size_t N0 = c->lv[0].N();
+  MG_TRY(ensure(c->feat, N0 * kFeatures * sizeof(T)));
+  MG_TRY(ensure(c->setup_a, N0 * C * sizeof(T)));
+  MG_TRY(ensure(c->setup_b, N0 * C * sizeof(T)));
+  MG_TRY(ensure(c->setup_c, N0 * C * sizeof(T)));
+  MG_TRY(ensure(c->setup_d, N0 * C * sizeof(T)));
+  T* feat = c->feat.as<T>();
+  T* cA = c->setup_a.as<T>();
+  T* cB = c->setup_b.as<T>();
+  T* zA = c->setup_c.as<T>();
+  T* zB = c->setup_d.as<T>();
+  MG_TRY(launch_features<T>(c->op[0].as<double>(), feat, c->lv[0].n, c->stream));
+  {
+    ConvArgs<T> a;
+    a.x = feat; a.W = W + wl.sw_in; a.bias = W + wl.sb_in; a.y = cA; a.n = c->lv[0].n;
+    MG_TRY(conv_same<T>(kFeatures, C, a, c->stream));
+  }
+  for (int l = 0; l < c->L; ++l) {
+    const int nl = c->lv[l].n;
+    const T* zin = cA;
+    for (int i = 0; i < kSetupLayers; ++i) {
+      T* zout = (i == kSetupLayers - 1) ? out[l] : ((i % 2 == 0) ? zA : zB);
+      ConvArgs<T> a;
+      a.x = zin; a.W = W + wl.sw + i * CC9; a.bias = W + wl.sb + (size_t)i * C;
+      a.skip = zin; a.tanh_act = 1; a.y = zout; a.n = nl;
+      if (i == kSetupLayers - 1 && c->cfg.scale_by_diag) a.diag = c->op[l].as<double>();
+      MG_TRY(conv_same<T>(C, C, a, c->stream));
+      zin = zout;
+    }
+    if (l < c->L - 1) {
+      MG_TRY(rcnn<T>(C, cA, W + wl.sw_R, cB, nl, c->stream));
+      std::swap(cA, cB);
+    }
+  }
+  return {};
+}
+
+// ---- solve phase (Algorithm 3) in FP64 ------------------------------------
+// e = B r, or e = u + B r when `u_skip` is given (the update of Eq. 1, fused
+// into the last layer).
+Status vcycle_fp64(mgcnn_ctx* c, const double* r, double* e, const double* u_skip) {
+  const int C = c->cfg.channels;
+  const WeightLayout& wl = c->wl;
+  const size_t CC9 = (size_t)C * C * 9;
+  const double* W = c->w64.as<double>();
+  double* x[kMaxLevels];
+  double* t[kMaxLevels];
+  for (int l = 0; l < c->L; ++l) {
+    x[l] = c->xa[l].as<double>();
+    t[l] = c->xb[l].as<double>();
+  }
+  {
+    ConvArgs<double> a;
+    a.x = r; a.W = W + wl.w_in; a.y = x[0]; a.n = c->lv[0].n;
+    MG_TRY(conv_same<double>(1, C, a, c->stream));
+  }
+  for (int l = 0; l < c->L; ++l) {
+    for (int i = 0; i < wl.nu_d; ++i) {
+      ConvArgs<double> a;
+      a.x = x[l]; a.s = c->s64[l].as<double>(); a.W = W + wl.w_down + i * CC9;
+      a.skip = x[l]; a.y = t[l]; a.n = c->lv[l].n;
+      MG_TRY(conv_same<double>(C, C, a, c->stream));
+      std::swap(x[l], t[l]);
+    }
+    if (l < c->L - 1) MG_TRY(rcnn<double>(C, x[l], W + wl.w_R, x[l + 1], c->lv[l].n, c->stream));
+  }
+  for (int l = c->L - 1; l >= 0; --l) {
+    for (int i = 0; i < wl.nu_u; ++i) {
+      ConvArgs<double> a;
+      a.x = x[l]; a.s = c->s64[l].as<double>(); a.W = W + wl.w_up + i * CC9;
+      a.skip = x[l]; a.y = t[l]; a.n = c->lv[l].n;
+      MG_TRY(conv_same<double>(C, C, a, c->stream));
+      std::swap(x[l], t[l]);
+    }
+    if (l > 0) MG_TRY(tcnn_add<double>(C, x[l], W + wl.w_P, x[l - 1], c->lv[l - 1].n, c->stream));
+  }
+  {
+    ConvArgs<double> a;
+    a.x = x[0]; a.W = W + wl.w_out; a.skip = u_skip; a.y = e; a.n = c->lv[0].n;
+    MG_TRY(conv_same<double>(C, 1, a, c->stream));
+  }
+  return {};
+}
+
+Status vcycle_any(mgcnn_ctx* c, const double* r, double* e, const double* u_skip) {
+  if (c->cfg.precision == MGCNN_PREC_FP64) return vcycle_fp64(c, r, e, u_skip);
+  return vcycle_mixed(c, r, e, u_skip);
+}
+
+Status require_setup(const mgcnn_ctx* c) {
+  if (!c->have_setup) return make_status(MGCNN_ERR_STATE, "mgcnn_setup has not been called");
+  return {};
+}
+
+Status do_setup(mgcnn_ctx* c, const double* coeff, int n) {
+  if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
+  const int Lmax = levels_of(n);
+  if (Lmax < 1) return make_status(MGCNN_ERR_SIZE, "n=%d is not 2^m-1 with m>=2", n);
+  if (Lmax > kMaxLevels) return make_status(MGCNN_ERR_SIZE, "n=%d too large", n);
+  const int L = c->cfg.levels > 0 ? c->cfg.levels : Lmax;
+  if (L > Lmax) return make_status(MGCNN_ERR_SIZE, "%d levels requested, n=%d allows %d", L, n, Lmax);
+  c->have_setup = false;
+  c->n = n;
+  c->L = L;
+  c->lv.assign(L, Level{});
+  int nl = n;
+  for (int l = 0; l < L; ++l) {
+    c->lv[l].n = nl;
+    c->lv[l].h = 1.0 / (nl + 1);
+    nl = (nl - 1) / 2;
+  }
+  const int C = c->cfg.channels;
+  const bool div = c->cfg.pde == MGCNN_PDE_DIV_HARMONIC;
+  for (int l = 0; l < L; ++l) {
+    const size_t N = c->lv[l].N();
+    const size_t cn = div ? (size_t)(c->lv[l].n + 2) * (c->lv[l].n + 2) : N;
+    MG_TRY(ensure(c->coef[l], cn * sizeof(double)));
+    MG_TRY(ensure(c->op[l], 5 * N * sizeof(double)));
+    if (c->cfg.precision == MGCNN_PREC_FP64) {
+      MG_TRY(ensure(c->xa[l], N * C * sizeof(double)));
+      MG_TRY(ensure(c->xb[l], N * C * sizeof(double)));
+      MG_TRY(ensure(c->s64[l], N * C * sizeof(double)));
+    }
+  }
+  const size_t N0 = c->lv[0].N();
+  MG_TRY(ensure(c->partial, (size_t)reduction_blocks(N0) * sizeof(double)));
+  MG_TRY(ensure(c->r, N0 * sizeof(double)));
+  MG_TRY(ensure(c->e, N0 * sizeof(double)));
+  // coefficient in, checked positive and finite
+  const size_t cn0 = div ? (size_t)(n + 2) * (n + 2) : N0;
+  MG_CUDA(cudaMemcpyAsync(c->coef[0].p, coeff, cn0 * sizeof(double), cudaMemcpyDefault, c->stream));
+  int* bad = reinterpret_cast<int*>(c->scalars.as<double>() + 7);
+  MG_TRY(launch_count_bad(c->coef[0].as<double>(), cn0, bad, c->stream));
+  int hbad = 0;
+  MG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MG_TRY(sync(c));
+  if (hbad) return make_status(MGCNN_ERR_NONFINITE, "coefficient field has non-finite or non-positive entries");
+  // operators on every level (Sec. 2.3: rediscretisation)
+  for (int l = 0; l < L; ++l) {
+    const int nlv = c->lv[l].n;
+    if (div) {
+      MG_TRY(launch_stencil_div(c->coef[l].as<double>(), c->op[l].as<double>(), nlv, c->cfg.bx, c->cfg.by, c->stream));
+      if (l < L - 1) MG_TRY(launch_restrict_k(c->coef[l].as<double>(), c->coef[l + 1].as<double>(), nlv + 2, c->stream));
+    } else {
+      MG_TRY(launch_stencil_nondiv(c->coef[l].as<double>(), c->op[l].as<double>(), nlv, c->cfg.bx, c->cfg.by, c->stream));
+      if (l < L - 1) MG_TRY(launch_inject_mu(c->coef[l].as<double>(), c->coef[l + 1].as<double>(), nlv, c->stream));
+    }
+  }
+  // setup network
+  if (c->cfg.precision == MGCNN_PREC_FP64) {
+    double* outs[kMaxLevels];
+    for (int l = 0; l < L; ++l) outs[l] = c->s64[l].as<double>();
+    MG_TRY(run_setup_net<double>(c, c->w64.as<double>(), outs));
+  } else {
+    MG_TRY(setup_mixed(c));
+  }
+  MG_TRY(sync(c));
+  c->have_setup = true;
+  return {};
+}
+
+}  // namespace
+
+// Used by the mixed-precision translation unit.
+namespace mgcnn {
+Status run_setup_net_fp32(mgcnn_ctx* c, float* const* out) {
+  return run_setup_net<float>(c, c->w32.as<float>(), out);
+}
+}  // namespace mgcnn
+
+// ---------------------------------------------------------------------------
+// ABI
+extern "C" {
+
+size_t mgcnn_weight_count(const mgcnn_config* cfg) {
+  if (!cfg || !channels_supported(cfg->channels) || cfg->down_layers < 1 || cfg->up_layers < 1) return 0;
+  WeightLayout wl;
+  wl.build(cfg->channels, cfg->down_layers, cfg->up_layers);
+  return wl.total;
+}
+
+int mgcnn_create(const mgcnn_config* cfg, mgcnn_ctx** out) {
+  if (!cfg || !out) return MGCNN_ERR_ARG;
+  *out = nullptr;
+  if (!channels_supported(cfg->channels) || cfg->down_layers < 1 || cfg->up_layers < 1 ||
+      cfg->down_layers > 16 || cfg->up_layers > 16 || cfg->levels < 0 || cfg->levels > kMaxLevels)
+    return MGCNN_ERR_SIZE;
+  if ((cfg->precision != MGCNN_PREC_FP64 && cfg->precision != MGCNN_PREC_MIXED_BF16) ||
+      (cfg->pde != MGCNN_PDE_DIV_HARMONIC && cfg->pde != MGCNN_PDE_NONDIV) ||
+      !std::isfinite(cfg->bx) || !std::isfinite(cfg->by))
+    return MGCNN_ERR_ARG;
+  if (cfg->precision == MGCNN_PREC_MIXED_BF16 && !mixed_channels_supported(cfg->channels)) return MGCNN_ERR_SIZE;
+  mgcnn_ctx* c = new (std::nothrow) mgcnn_ctx();
+  if (!c) return MGCNN_ERR_NOMEM;
+  c->cfg = *cfg;
+  c->wl.build(cfg->channels, cfg->down_layers, cfg->up_layers);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MGCNN_ERR_CUDA;
+  }
+  Status s = ensure(c->scalars, 8 * sizeof(double));
+  if (s.ok() && cudaMallocHost(&c->h_scalars, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    s = make_status(MGCNN_ERR_NOMEM, "cudaMallocHost");
+  }
+  if (!s.ok()) {
+    mgcnn_destroy(c);
+    return s.code;
+  }
+  *out = c;
+  return MGCNN_OK;
+}
+
+void mgcnn_destroy(mgcnn_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  release(c->w64); release(c->w32);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    release(c->coef[l]); release(c->op[l]); release(c->s64[l]); release(c->s16[l]);
+    release(c->xa[l]); release(c->xb[l]);
+  }
+  release(c->setup_a); release(c->setup_b); release(c->setup_c); release(c->setup_d);
+  release(c->feat); release(c->f); release(c->u); release(c->r); release(c->e);
+  release(c->r32); release(c->partial); release(c->scalars);
+  mixed_release(c);
+  if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  delete c;
+}
+
+int mgcnn_set_stream(mgcnn_ctx* c, void* stream) {
+  if (!c) return MGCNN_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return finish(c, {});
+}
+
+int mgcnn_set_weights(mgcnn_ctx* c, const double* w, size_t count) {
+  if (!c || !w) return MGCNN_ERR_ARG;
+  if (count != c->wl.total)
+    return finish(c, make_status(MGCNN_ERR_ARG, "weight count %zu, expected %zu", count, c->wl.total));
+  Status s = [&]() -> Status {
+    MG_TRY(ensure(c->w64, count * sizeof(double)));
+    MG_TRY(ensure(c->w32, count * sizeof(float)));
+    MG_CUDA(cudaMemcpyAsync(c->w64.p, w, count * sizeof(double), cudaMemcpyDefault, c->stream));
+    MG_TRY(convert<float>(c->w64.as<double>(), c->w32.as<float>(), count, c->stream));
+    MG_TRY(mixed_set_weights(c));
+    MG_TRY(sync(c));
+    c->have_weights = true;
+    return {};
+  }();
+  return finish(c, s);
+}
+
+int mgcnn_setup(mgcnn_ctx* c, const double* coeff, int n) {
+  if (!c || !coeff) return MGCNN_ERR_ARG;
+  return finish(c, do_setup(c, coeff, n));
+}
+
+size_t mgcnn_setup_tensor_count(const mgcnn_ctx* c) {
+  if (!c || !c->have_setup) return 0;
+  return setup_tensor_count(c);
+}
+
+int mgcnn_set_setup_tensors(mgcnn_ctx* c, const double* s, size_t count) {
+  if (!c || !s) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    if (count != setup_tensor_count(c))
+      return make_status(MGCNN_ERR_ARG, "setup tensor count %zu, expected %zu", count, setup_tensor_count(c));
+    const double* ds = nullptr;
+    MG_TRY(stage_in(c, s, count, c->setup_a, &ds));
+    size_t off = 0;
+    for (int l = 0; l < c->L; ++l) {
+      const size_t m = c->lv[l].N() * c->cfg.channels;
+      if (c->cfg.precision == MGCNN_PREC_FP64)
+        MG_CUDA(cudaMemcpyAsync(c->s64[l].p, ds + off, m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      else
+        MG_TRY(mixed_set_setup_level(c, l, ds + off));
+      off += m;
+    }
+    return sync(c);
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_get_setup_tensors(mgcnn_ctx* c, double* s, size_t count) {
+  if (!c || !s) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    if (count != setup_tensor_count(c))
+      return make_status(MGCNN_ERR_ARG, "setup tensor count %zu, expected %zu", count, setup_tensor_count(c));
+    double* ds = nullptr;
+    bool host = false;
+    MG_TRY(stage_out(s, count, c->setup_b, &ds, &host));
+    size_t off = 0;
+    for (int l = 0; l < c->L; ++l) {
+      const size_t m = c->lv[l].N() * c->cfg.channels;
+      if (c->cfg.precision == MGCNN_PREC_FP64)
+        MG_CUDA(cudaMemcpyAsync(ds + off, c->s64[l].p, m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      else
+        MG_TRY(mixed_get_setup_level(c, l, ds + off));
+      off += m;
+    }
+    MG_TRY(stage_out_finish(c, s, ds, count, host));
+    return sync(c);
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_get_operator(mgcnn_ctx* c, int level, double* out, size_t count) {
+  if (!c || !out) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    if (level < 0 || level >= c->L) return make_status(MGCNN_ERR_ARG, "level %d out of range", level);
+    const size_t m = 5 * c->lv[level].N();
+    if (count != m) return make_status(MGCNN_ERR_ARG, "operator count %zu, expected %zu", count, m);
+    MG_CUDA(cudaMemcpyAsync(out, c->op[level].p, m * sizeof(double), cudaMemcpyDefault, c->stream));
+    return sync(c);
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_residual(mgcnn_ctx* c, const double* f, const double* u, double* r, double* norm2) {
+  if (!c || !f || !u || !r) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    const size_t N = c->lv[0].N();
+    const double *df = nullptr, *du = nullptr;
+    MG_TRY(stage_in(c, f, N, c->f, &df));
+    MG_TRY(stage_in(c, u, N, c->u, &du));
+    double* dr = nullptr;
+    bool host = false;
+    MG_TRY(stage_out(r, N, c->r, &dr, &host));
+    MG_TRY(launch_residual(df, du, c->op[0].as<double>(), dr, nullptr, c->partial.as<double>(), c->n, c->stream));
+    MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>(), c->stream));
+    MG_TRY(stage_out_finish(c, r, dr, N, host));
+    double v = 0.0;
+    MG_TRY(read_scalar(c, 0, &v));
+    if (norm2) *norm2 = v;
+    return {};
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_vcycle(mgcnn_ctx* c, const double* r, double* e) {
+  if (!c || !r || !e) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    const size_t N = c->lv[0].N();
+    const double* dr = nullptr;
+    MG_TRY(stage_in(c, r, N, c->f, &dr));
+    double* de = nullptr;
+    bool host = false;
+    MG_TRY(stage_out(e, N, c->e, &de, &host));
+    MG_TRY(vcycle_any(c, dr, de, nullptr));
+    MG_TRY(stage_out_finish(c, e, de, N, host));
+    return sync(c);
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
+  if (!c || !f || !u || !iters || maxit < 0 || !(tol >= 0.0)) return MGCNN_ERR_ARG;
+  *iters = 0;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    const size_t N = c->lv[0].N();
+    const double* df = nullptr;
+    MG_TRY(stage_in(c, f, N, c->f, &df));
+    double* du = nullptr;
+    bool host = false;
+    MG_TRY(stage_out(u, N, c->u, &du, &host));
+    if (host) MG_CUDA(cudaMemcpyAsync(du, u, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    MG_TRY(sumsq(c, df, N, 1));
+    double fn2 = 0.0;
+    MG_TRY(read_scalar(c, 1, &fn2));
+    if (!std::isfinite(fn2)) return make_status(MGCNN_ERR_NONFINITE, "right-hand side is not finite");
+    if (fn2 == 0.0) {
+      MG_CUDA(cudaMemsetAsync(du, 0, N * sizeof(double), c->stream));
+      if (relres) relres[0] = 0.0;
+      MG_TRY(stage_out_finish(c, u, du, N, host));
+      return sync(c);
+    }
+    Status result;
+    const bool mixed = c->cfg.precision == MGCNN_PREC_MIXED_BF16;
+    for (int k = 0;; ++k) {
+      // mixed: the V-cycle consumes an FP32 copy of r (scaled in-kernel), FP64 r is not stored
+      MG_TRY(launch_residual(df, du, c->op[0].as<double>(), mixed ? nullptr : c->r.as<double>(),
+                             mixed ? c->r32.as<float>() : nullptr, c->partial.as<double>(), c->n, c->stream));
+      MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>(), c->stream));
+      double rn2 = 0.0;
+      MG_TRY(read_scalar(c, 0, &rn2));
+      const double rel = std::sqrt(rn2 / fn2);
+      *iters = k;
+      if (!std::isfinite(rel)) {
+        result = make_status(MGCNN_ERR_NONFINITE, "residual norm is not finite at cycle %d", k);
+        break;
+      }
+      if (relres) relres[k] = rel;
+      if (rel <= tol) break;
+      if (k == maxit) {
+        result = make_status(MGCNN_NOT_CONVERGED, "no convergence in %d cycles (relres %.3e)", maxit, rel);
+        break;
+      }
+      if (mixed)
+        MG_TRY(vcycle_mixed_r32(c, c->r32.as<float>(), c->scalars.as<double>(), du, du));
+      else
+        MG_TRY(vcycle_fp64(c, c->r.as<double>(), du, du));
+    }
+    MG_TRY(stage_out_finish(c, u, du, N, host));
+    MG_TRY(sync(c));
+    return result;
+  }();
+  return finish(c, st);
+}
+
+const char* mgcnn_status_string(int s) {
+  switch (s) {
+    case MGCNN_OK: return "MGCNN_OK";
+    case MGCNN_NOT_CONVERGED: return "MGCNN_NOT_CONVERGED";
+    case MGCNN_ERR_ARG: return "MGCNN_ERR_ARG";
+    case MGCNN_ERR_SIZE: return "MGCNN_ERR_SIZE";
+    case MGCNN_ERR_STATE: return "MGCNN_ERR_STATE";
+    case MGCNN_ERR_NOMEM: return "MGCNN_ERR_NOMEM";
+    case MGCNN_ERR_CUDA: return "MGCNN_ERR_CUDA";
+    case MGCNN_ERR_NONFINITE: return "MGCNN_ERR_NONFINITE";
+    case MGCNN_ERR_TIMEOUT: return "MGCNN_ERR_TIMEOUT";
+    default: return "MGCNN_UNKNOWN_STATUS";
+  }
+}
+
+const char* mgcnn_last_error(const mgcnn_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+}  // extern "C"

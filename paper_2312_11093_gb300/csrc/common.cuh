@@ -1,0 +1,131 @@
+// Internal definitions shared by the translation units of libmgcnn.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mgcnn.h"
+
+namespace mgcnn {
+
+constexpr int kFeatures = 5;      // setup-network input features per node
+constexpr int kSetupLayers = 4;   // NonLinearResNet depth (Sec. 3.2: "four layers")
+constexpr int kMaxLevels = 13;    // n <= 16383
+
+// Status carried through the library; converted to the ABI code at the boundary.
+struct Status {
+  int code = MGCNN_OK;
+  std::string msg;
+  bool ok() const { return code == MGCNN_OK; }
+};
+
+// A device allocation that grows on demand and is freed by the context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Offsets (in elements) of each weight tensor in the flat weight blob.
+struct WeightLayout {
+  int C = 0, nu_d = 0, nu_u = 0;
+  size_t w_in, w_down, w_up, w_R, w_P, w_out, sw_in, sb_in, sw, sb, sw_R, total;
+  void build(int C_, int nd, int nu) {
+    C = C_; nu_d = nd; nu_u = nu;
+    size_t CC9 = (size_t)C * C * 9, o = 0;
+    w_in = o;   o += (size_t)C * 9;
+    w_down = o; o += (size_t)nu_d * CC9;
+    w_up = o;   o += (size_t)nu_u * CC9;
+    w_R = o;    o += CC9;
+    w_P = o;    o += CC9;
+    w_out = o;  o += (size_t)C * 9;
+    sw_in = o;  o += (size_t)C * kFeatures * 9;
+    sb_in = o;  o += (size_t)C;
+    sw = o;     o += (size_t)kSetupLayers * CC9;
+    sb = o;     o += (size_t)kSetupLayers * C;
+    sw_R = o;   o += CC9;
+    total = o;
+  }
+};
+
+struct Level {
+  int n = 0;          // interior nodes per side
+  double h = 0;       // mesh width 1/(n+1)
+  size_t N() const { return (size_t)n * n; }
+};
+
+}  // namespace mgcnn
+
+// The opaque context of the ABI.
+struct mgcnn_ctx {
+  mgcnn_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string last_error;
+
+  mgcnn::WeightLayout wl;
+  bool have_weights = false;
+  mgcnn::DevBuf w64, w32;                 // weight blob in FP64 and FP32
+
+  bool have_setup = false;
+  int n = 0, L = 0;
+  std::vector<mgcnn::Level> lv;
+  mgcnn::DevBuf coef[mgcnn::kMaxLevels];  // nodal k (or mu) per level
+  mgcnn::DevBuf op[mgcnn::kMaxLevels];    // 5 x n_l^2 FP64 stencil per level
+  mgcnn::DevBuf s64[mgcnn::kMaxLevels];   // setup tensors FP64 [n_l^2][C]
+  mgcnn::DevBuf s16[mgcnn::kMaxLevels];   // setup tensors BF16 [n_l^2][C]
+  mgcnn::DevBuf xa[mgcnn::kMaxLevels];    // state ping-pong buffers, per level
+  mgcnn::DevBuf xb[mgcnn::kMaxLevels];
+  mgcnn::DevBuf setup_a, setup_b, setup_c, setup_d;  // setup-phase scratch
+  mgcnn::DevBuf feat;                     // setup features [n^2][5]
+  mgcnn::DevBuf f, u, r, e;               // finest-grid FP64 vectors (staging / work)
+  mgcnn::DevBuf r32;                      // FP32 residual for the mixed path
+  mgcnn::DevBuf partial;                  // per-block partial sums of reductions
+  // mixed-precision path (mixed.cu)
+  int cp = 0;                             // channels padded for the tensor cores (8 or 16)
+  mgcnn::DevBuf x16a[mgcnn::kMaxLevels];  // BF16 state ping-pong, [n_l^2][cp]
+  mgcnn::DevBuf x16b[mgcnn::kMaxLevels];
+  mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
+  mgcnn::DevBuf s32tmp;                   // FP32 setup output before the BF16 cast
+  mgcnn::DevBuf scalars;                  // device scalars (norms)
+  double* h_scalars = nullptr;            // pinned host mirror of `scalars`
+};
+
+namespace mgcnn {
+
+Status make_status(int code, const char* fmt, ...);
+Status cuda_status(cudaError_t e, const char* what);
+Status ensure(DevBuf& b, size_t bytes);
+void release(DevBuf& b);
+bool is_device_pointer(const void* p);
+
+#define MG_CUDA(call)                                              \
+  do {                                                             \
+    cudaError_t _e = (call);                                       \
+    if (_e != cudaSuccess) return ::mgcnn::cuda_status(_e, #call); \
+  } while (0)
+
+#define MG_LAUNCH(what)                                            \
+  do {                                                             \
+    cudaError_t _e = cudaGetLastError();                           \
+    if (_e != cudaSuccess) return ::mgcnn::cuda_status(_e, what);  \
+  } while (0)
+
+#define MG_TRY(expr)                       \
+  do {                                     \
+    ::mgcnn::Status _s = (expr);           \
+    if (!_s.ok()) return _s;               \
+  } while (0)
+
+inline int grid_for(size_t work, int block) {
+  return (int)((work + block - 1) / block);
+}
+
+}  // namespace mgcnn

@@ -1,0 +1,251 @@
+// Discretisation (A on every level), FP64 residual and deterministic reductions.
+//
+// Operator: Remark 2.1 (divergence form) and Sec. 2.5 (non-divergence form)
+// of arXiv 2312.11093, 5-point stencil with first-order upwind convection,
+// zero Dirichlet boundary (zero padding).  Coarse operators are
+// rediscretisations (Sec. 2.3) with the coefficient carried down by full
+// weighting of log k (divergence form) or by sampling mu (non-divergence form).
+#include "ops.cuh"
+
+namespace mgcnn {
+
+// ---------------------------------------------------------------------------
+// Coarse coefficient: log k_c(J, I) = weighted mean of log k over the fine
+// nodes (2J + a - 1, 2I + b - 1), weights (1,2,1)x(1,2,1), renormalised over
+// the nodes that exist.  m = fine nodes per side incl. the ring.
+__global__ void restrict_k_kernel(const double* __restrict__ k, double* __restrict__ kc, int m) {
+  const int mc = (m + 1) / 2;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= mc * mc) return;
+  const int J = p / mc, I = p - J * mc;
+  const double w[3] = {1.0, 2.0, 1.0};
+  double num = 0.0, den = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const int jj = 2 * J + a - 1;
+    for (int b = 0; b < 3; ++b) {
+      const int ii = 2 * I + b - 1;
+      if (jj < 0 || jj >= m || ii < 0 || ii >= m) continue;
+      num += w[a] * w[b] * log(k[(size_t)jj * m + ii]);
+      den += w[a] * w[b];
+    }
+  }
+  kc[p] = exp(num / den);
+}
+
+Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st) {
+  const int mc = (m + 1) / 2;
+  restrict_k_kernel<<<grid_for((size_t)mc * mc, 256), 256, 0, st>>>(k, kc, m);
+  MG_LAUNCH("restrict_k_kernel");
+  return {};
+}
+
+__global__ void inject_mu_kernel(const double* __restrict__ mu, double* __restrict__ mc, int n) {
+  const int nc = (n - 1) / 2;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nc * nc) return;
+  const int J = p / nc, I = p - J * nc;
+  mc[p] = mu[(size_t)(2 * J + 1) * n + 2 * I + 1];
+}
+
+Status launch_inject_mu(const double* mu, double* mc, int n, cudaStream_t st) {
+  const int nc = (n - 1) / 2;
+  inject_mu_kernel<<<grid_for((size_t)nc * nc, 256), 256, 0, st>>>(mu, mc, n);
+  MG_LAUNCH("inject_mu_kernel");
+  return {};
+}
+
+// ---------------------------------------------------------------------------
+// Divergence form: faces carry the harmonic mean of the two nodal k.
+//   a_W = -k_w/h^2 - max(bx,0)/h   a_E = -k_e/h^2 + min(bx,0)/h
+//   a_S = -k_s/h^2 - max(by,0)/h   a_N = -k_n/h^2 + min(by,0)/h
+//   a_C = (k_w + k_e + k_s + k_n)/h^2 + (|bx| + |by|)/h
+// Output layout: op[0..N) = a_C, then a_W, a_E, a_S, a_N.
+__global__ void stencil_div_kernel(const double* __restrict__ k, double* __restrict__ op, int n,
+                                   double bx, double by) {
+  const size_t N = (size_t)n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (int)N) return;
+  const int j = p / n, i = p - j * n;
+  const int m = n + 2;
+  const double h = 1.0 / (n + 1);
+  const double ih2 = 1.0 / (h * h);
+  const double kc = k[(size_t)(j + 1) * m + (i + 1)];
+  const double kwn = k[(size_t)(j + 1) * m + i];
+  const double ken = k[(size_t)(j + 1) * m + (i + 2)];
+  const double ksn = k[(size_t)j * m + (i + 1)];
+  const double knn = k[(size_t)(j + 2) * m + (i + 1)];
+  const double kw = 2.0 * kc * kwn / (kc + kwn);
+  const double ke = 2.0 * kc * ken / (kc + ken);
+  const double ks = 2.0 * kc * ksn / (kc + ksn);
+  const double kn = 2.0 * kc * knn / (kc + knn);
+  op[1 * N + p] = -kw * ih2 - fmax(bx, 0.0) / h;
+  op[2 * N + p] = -ke * ih2 + fmin(bx, 0.0) / h;
+  op[3 * N + p] = -ks * ih2 - fmax(by, 0.0) / h;
+  op[4 * N + p] = -kn * ih2 + fmin(by, 0.0) / h;
+  op[p] = (kw + ke + ks + kn) * ih2 + (fabs(bx) + fabs(by)) / h;
+}
+
+Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st) {
+  stencil_div_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(k, op, n, bx, by);
+  MG_LAUNCH("stencil_div_kernel");
+  return {};
+}
+
+// Non-divergence form: (1/h){(mu/h) Lap5 + v_x^+ dx^- + v_x^- dx^+ + v_y^+ dy^- + v_y^- dy^+}.
+__global__ void stencil_nondiv_kernel(const double* __restrict__ mu, double* __restrict__ op, int n,
+                                      double vx, double vy) {
+  const size_t N = (size_t)n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (int)N) return;
+  const double h = 1.0 / (n + 1);
+  const double lap = mu[p] / (h * h);
+  op[1 * N + p] = -lap - fmax(vx, 0.0) / h;
+  op[2 * N + p] = -lap + fmin(vx, 0.0) / h;
+  op[3 * N + p] = -lap - fmax(vy, 0.0) / h;
+  op[4 * N + p] = -lap + fmin(vy, 0.0) / h;
+  op[p] = 4.0 * lap + (fmax(vx, 0.0) - fmin(vx, 0.0) + fmax(vy, 0.0) - fmin(vy, 0.0)) / h;
+}
+
+Status launch_stencil_nondiv(const double* mu, double* op, int n, double vx, double vy, cudaStream_t st) {
+  stencil_nondiv_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(mu, op, n, vx, vy);
+  MG_LAUNCH("stencil_nondiv_kernel");
+  return {};
+}
+
+// Counts entries that are not finite or not > 0 (coefficients must be positive).
+__global__ void count_bad_kernel(const double* __restrict__ v, size_t N, int* __restrict__ count) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int bad = 0;
+  if (p < N) {
+    const double x = v[p];
+    bad = !(isfinite(x) && x > 0.0);
+  }
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) atomicAdd(count, 1);
+}
+
+Status launch_count_bad(const double* v, size_t N, int* count, cudaStream_t st) {
+  MG_CUDA(cudaMemsetAsync(count, 0, sizeof(int), st));
+  count_bad_kernel<<<grid_for(N, 256), 256, 0, st>>>(v, N, count);
+  MG_LAUNCH("count_bad_kernel");
+  return {};
+}
+
+// Setup-network input (reading of the Remark "Matrix coefficients as input"):
+// [a_W/a_C, a_E/a_C, a_S/a_C, a_N/a_C, log10(h^2 a_C)], layout [N][5].
+template <typename FT>
+__global__ void features_kernel(const double* __restrict__ op, FT* __restrict__ feat, int n) {
+  const size_t N = (size_t)n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (int)N) return;
+  const double h = 1.0 / (n + 1);
+  const double aC = op[p];
+  feat[(size_t)p * kFeatures + 0] = (FT)(op[1 * N + p] / aC);
+  feat[(size_t)p * kFeatures + 1] = (FT)(op[2 * N + p] / aC);
+  feat[(size_t)p * kFeatures + 2] = (FT)(op[3 * N + p] / aC);
+  feat[(size_t)p * kFeatures + 3] = (FT)(op[4 * N + p] / aC);
+  feat[(size_t)p * kFeatures + 4] = (FT)log10(h * h * aC);
+}
+
+template <typename FT>
+Status launch_features(const double* op, FT* feat, int n, cudaStream_t st) {
+  features_kernel<FT><<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, feat, n);
+  MG_LAUNCH("features_kernel");
+  return {};
+}
+template Status launch_features<double>(const double*, double*, int, cudaStream_t);
+template Status launch_features<float>(const double*, float*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Block-level sum of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? smem[threadIdx.x] : 0.0;
+  if (warp == 0) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// r = f - A u, FP64 (Eq. 1); per-block partial of sum r^2.
+__global__ void __launch_bounds__(kResidualBlock)
+residual_kernel(const double* __restrict__ f, const double* __restrict__ u, const double* __restrict__ op,
+                double* __restrict__ r, float* __restrict__ r32, double* __restrict__ partial, int n) {
+  __shared__ double smem[32];
+  const size_t N = (size_t)n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0;
+  if (p < (int)N) {
+    const int j = p / n, i = p - j * n;
+    const double uC = u[p];
+    const double uW = (i > 0) ? u[p - 1] : 0.0;
+    const double uE = (i < n - 1) ? u[p + 1] : 0.0;
+    const double uS = (j > 0) ? u[p - n] : 0.0;
+    const double uN = (j < n - 1) ? u[p + n] : 0.0;
+    const double Au = op[p] * uC + op[N + p] * uW + op[2 * N + p] * uE + op[3 * N + p] * uS + op[4 * N + p] * uN;
+    const double rv = f[p] - Au;
+    if (r) r[p] = rv;
+    if (r32) r32[p] = (float)rv;
+    rr = rv * rv;
+  }
+  rr = block_sum(rr, smem);
+  if (threadIdx.x == 0) partial[blockIdx.x] = rr;
+}
+
+Status launch_residual(const double* f, const double* u, const double* op, double* r, float* r32,
+                       double* partial, int n, cudaStream_t st) {
+  const size_t N = (size_t)n * n;
+  residual_kernel<<<reduction_blocks(N), kResidualBlock, 0, st>>>(f, u, op, r, r32, partial, n);
+  MG_LAUNCH("residual_kernel");
+  return {};
+}
+
+__global__ void __launch_bounds__(kResidualBlock)
+sumsq_kernel(const double* __restrict__ v, size_t N, double* __restrict__ partial) {
+  __shared__ double smem[32];
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double x = (p < N) ? v[p] : 0.0;
+  x = block_sum(x * x, smem);
+  if (threadIdx.x == 0) partial[blockIdx.x] = x;
+}
+
+Status launch_sumsq(const double* v, size_t N, double* partial, cudaStream_t st) {
+  sumsq_kernel<<<reduction_blocks(N), kResidualBlock, 0, st>>>(v, N, partial);
+  MG_LAUNCH("sumsq_kernel");
+  return {};
+}
+
+// One block sums the partials: thread t adds partial[t], partial[t + 1024], ...
+// in order, then a fixed tree -- the same result on every run.
+__global__ void __launch_bounds__(kReduceBlock)
+reduce_kernel(const double* __restrict__ partial, int count, double* __restrict__ out) {
+  __shared__ double smem[32];
+  double v = 0.0;
+  for (int t = threadIdx.x; t < count; t += blockDim.x) v += partial[t];
+  v = block_sum(v, smem);
+  if (threadIdx.x == 0) out[0] = v;
+}
+
+Status launch_reduce(const double* partial, int count, double* out, cudaStream_t st) {
+  reduce_kernel<<<1, kReduceBlock, 0, st>>>(partial, count, out);
+  MG_LAUNCH("reduce_kernel");
+  return {};
+}
+
+__global__ void axpy_to_kernel(const double* __restrict__ u, const double* __restrict__ e,
+                               double* __restrict__ out, size_t N) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N) out[p] = u[p] + e[p];
+}
+
+Status launch_axpy_to(const double* u, const double* e, double* out, size_t N, cudaStream_t st) {
+  axpy_to_kernel<<<grid_for(N, 256), 256, 0, st>>>(u, e, out, N);
+  MG_LAUNCH("axpy_to_kernel");
+  return {};
+}
+
+}  // namespace mgcnn

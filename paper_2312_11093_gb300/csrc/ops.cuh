@@ -1,0 +1,55 @@
+// Launchers shared between translation units (host-side prototypes).
+#pragma once
+
+#include "common.cuh"
+
+namespace mgcnn {
+
+// ---- operator.cu: discretisation, residual, reductions ---------------------
+constexpr int kResidualBlock = 256;
+constexpr int kReduceBlock = 1024;
+
+// Blocks used by launch_residual / launch_sumsq for N values; the caller
+// sizes the partial-sum buffer with it.
+inline int reduction_blocks(size_t N) { return grid_for(N, kResidualBlock); }
+
+Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st);
+Status launch_inject_mu(const double* mu, double* mc, int n, cudaStream_t st);
+Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st);
+Status launch_stencil_nondiv(const double* mu, double* op, int n, double vx, double vy, cudaStream_t st);
+Status launch_count_bad(const double* v, size_t N, int* count, cudaStream_t st);
+template <typename FT>
+Status launch_features(const double* op, FT* feat, int n, cudaStream_t st);
+// r = f - A u (FP64), optional FP32 copy r32, per-block partial sums of r^2.
+Status launch_residual(const double* f, const double* u, const double* op, double* r, float* r32,
+                       double* partial, int n, cudaStream_t st);
+Status launch_sumsq(const double* v, size_t N, double* partial, cudaStream_t st);
+// out[0] = sum of partial[0..count) in a fixed order (deterministic).
+Status launch_reduce(const double* partial, int count, double* out, cudaStream_t st);
+Status launch_axpy_to(const double* u, const double* e, double* out, size_t N, cudaStream_t st);
+
+// ---- net_generic.cu: FP64 / FP32 direct convolution kernels ----------------
+template <typename T>
+struct ConvArgs {
+  const T* x = nullptr;     // input  [N][CI]
+  const T* s = nullptr;     // optional per-pixel input scale [N][CI] (Eq. heteroresnet)
+  const T* W = nullptr;     // weights [CO][CI][3][3]
+  const T* bias = nullptr;  // optional [CO]
+  const T* skip = nullptr;  // optional residual input [N][CO], added after the activation
+  const double* diag = nullptr;  // optional: divide the result by diag[p] (FP64 a_C)
+  T* y = nullptr;           // output [N][CO]
+  int n = 0;                // grid side
+  int tanh_act = 0;         // 1: y = tanh(conv + bias) (+ skip)
+};
+
+template <typename T>
+Status conv_same(int CI, int CO, const ConvArgs<T>& a, cudaStream_t st);
+template <typename T>
+Status rcnn(int C, const T* x, const T* W, T* y, int n_fine, cudaStream_t st);
+template <typename T>
+Status tcnn_add(int C, const T* xc, const T* W, T* y, int n_fine, cudaStream_t st);
+template <typename T>
+Status convert(const double* src, T* dst, size_t count, cudaStream_t st);
+bool channels_supported(int C);
+
+}  // namespace mgcnn

@@ -1,0 +1,215 @@
+"""ctypes binding of libmgcnn.so (C ABI in include/mgcnn.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Arrays
+may be numpy float64 arrays (host memory; the library copies them to and from
+the device) or float64 torch tensors on the GPU (used in place).  If the
+library has not been built the import of this module fails loudly: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_size_t, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmgcnn.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_ARG, ERR_SIZE, ERR_STATE, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
+PREC = {"fp64": 0, "mixed_bf16": 1}
+PDE = {"div": 0, "nondiv": 1}
+SETUP_LAYERS = 4
+FEATURES = 5
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("channels", c_int), ("down_layers", c_int), ("up_layers", c_int), ("precision", c_int),
+                ("pde", c_int), ("scale_by_diag", c_int), ("levels", c_int), ("bx", c_double), ("by", c_double)]
+
+
+class MGCNNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} [{status}]")
+        self.status = status
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libmgcnn.so (raises if it is missing -- build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: the CUDA library must be built "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(LIB_PATH)
+    dp = POINTER(c_double)
+    sig = {
+        "mgcnn_weight_count": (c_size_t, [POINTER(Config)]),
+        "mgcnn_create": (c_int, [POINTER(Config), POINTER(c_void_p)]),
+        "mgcnn_destroy": (None, [c_void_p]),
+        "mgcnn_set_stream": (c_int, [c_void_p, c_void_p]),
+        "mgcnn_set_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
+        "mgcnn_setup": (c_int, [c_void_p, c_void_p, c_int]),
+        "mgcnn_setup_tensor_count": (c_size_t, [c_void_p]),
+        "mgcnn_set_setup_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
+        "mgcnn_get_setup_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
+        "mgcnn_get_operator": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
+        "mgcnn_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, dp]),
+        "mgcnn_vcycle": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "mgcnn_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), c_void_p]),
+        "mgcnn_status_string": (c_char_p, [c_int]),
+        "mgcnn_last_error": (c_char_p, [c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a, n: int | None = None, writable: bool = False) -> int:
+    """Raw pointer of a float64 numpy array or torch tensor (checked for dtype, layout, size)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or (writable and not a.flags["WRITEABLE"]):
+            raise TypeError("arrays must be C-contiguous float64")
+        if n is not None and a.size != n:
+            raise ValueError(f"array has {a.size} entries, expected {n}")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        if n is not None and a.numel() != n:
+            raise ValueError(f"tensor has {a.numel()} entries, expected {n}")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def weight_count(channels: int, down_layers: int = 1, up_layers: int = 1) -> int:
+    cfg = Config(channels, down_layers, up_layers, 0, 0, 1, 0, 0.0, 0.0)
+    return int(load().mgcnn_weight_count(ctypes.byref(cfg)))
+
+
+WEIGHT_ORDER = ("w_in", "w_down", "w_up", "w_R", "w_P", "w_out", "sw_in", "sb_in", "sw", "sb", "sw_R")
+
+
+def pack_weights(w: dict, channels: int, down_layers: int, up_layers: int) -> np.ndarray:
+    """Flatten a dict of weight arrays into the blob layout of mgcnn_weight_count.
+
+    Missing setup entries are zero (for runs that supply setup tensors directly)."""
+    C, F, S = channels, FEATURES, SETUP_LAYERS
+    shapes = {"w_in": (C, 1, 3, 3), "w_down": (down_layers, C, C, 3, 3), "w_up": (up_layers, C, C, 3, 3),
+              "w_R": (C, C, 3, 3), "w_P": (C, C, 3, 3), "w_out": (1, C, 3, 3), "sw_in": (C, F, 3, 3),
+              "sb_in": (C,), "sw": (S, C, C, 3, 3), "sb": (S, C), "sw_R": (C, C, 3, 3)}
+    parts = []
+    for k in WEIGHT_ORDER:
+        a = np.asarray(w[k], dtype=np.float64) if k in w else np.zeros(shapes[k])
+        if a.shape != shapes[k]:
+            raise ValueError(f"{k}: shape {a.shape}, expected {shapes[k]}")
+        parts.append(a.ravel())
+    blob = np.ascontiguousarray(np.concatenate(parts))
+    assert blob.size == weight_count(C, down_layers, up_layers)
+    return blob
+
+
+class Solver:
+    """One MGCNN context: weights, a setup for one coefficient field, solves."""
+
+    def __init__(self, channels: int = 8, down_layers: int = 1, up_layers: int = 1, precision: str = "fp64",
+                 pde: str = "div", scale_by_diag: bool = True, levels: int = 0, b=(1.0, 0.5), stream=None):
+        self._L = load()
+        self.cfg = Config(channels, down_layers, up_layers, PREC[precision], PDE[pde], int(scale_by_diag),
+                          levels, float(b[0]), float(b[1]))
+        h = c_void_p()
+        st = self._L.mgcnn_create(ctypes.byref(self.cfg), ctypes.byref(h))
+        if st != OK:
+            raise MGCNNError(st, "mgcnn_create failed: " + self._L.mgcnn_status_string(st).decode())
+        self._h = h
+        self.n = 0
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- plumbing -------------------------------------------------------------
+    def _check(self, st: int, what: str, ok=(OK,)) -> int:
+        if st not in ok:
+            msg = self._L.mgcnn_last_error(self._h).decode()
+            raise MGCNNError(st, f"{what}: {self._L.mgcnn_status_string(st).decode()}: {msg}")
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mgcnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None (legacy default stream)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.mgcnn_set_stream(self._h, c_void_p(handle or 0)), "mgcnn_set_stream")
+
+    # -- ABI ------------------------------------------------------------------
+    @property
+    def weight_count(self) -> int:
+        return int(self._L.mgcnn_weight_count(ctypes.byref(self.cfg)))
+
+    def set_weights(self, blob):
+        self._check(self._L.mgcnn_set_weights(self._h, _ptr(blob, self.weight_count), self.weight_count),
+                    "mgcnn_set_weights")
+
+    def setup(self, coeff, n: int):
+        self._check(self._L.mgcnn_setup(self._h, _ptr(coeff), int(n)), "mgcnn_setup")
+        self.n = int(n)
+
+    def setup_tensor_count(self) -> int:
+        return int(self._L.mgcnn_setup_tensor_count(self._h))
+
+    def set_setup_tensors(self, s):
+        m = self.setup_tensor_count()
+        self._check(self._L.mgcnn_set_setup_tensors(self._h, _ptr(s, m), m), "mgcnn_set_setup_tensors")
+
+    def get_setup_tensors(self, out=None):
+        m = self.setup_tensor_count()
+        out = np.empty(m) if out is None else out
+        self._check(self._L.mgcnn_get_setup_tensors(self._h, _ptr(out, m, True), m), "mgcnn_get_setup_tensors")
+        return out
+
+    def get_operator(self, level: int, n_l: int, out=None):
+        m = 5 * n_l * n_l
+        out = np.empty(m) if out is None else out
+        self._check(self._L.mgcnn_get_operator(self._h, int(level), _ptr(out, m, True), m), "mgcnn_get_operator")
+        return out
+
+    def residual(self, f, u, r=None):
+        N = self.n * self.n
+        r = np.empty(N) if r is None else r
+        nrm = c_double(0.0)
+        self._check(self._L.mgcnn_residual(self._h, _ptr(f, N), _ptr(u, N), _ptr(r, N, True), ctypes.byref(nrm)),
+                    "mgcnn_residual")
+        return r, nrm.value
+
+    def vcycle(self, r, e=None):
+        N = self.n * self.n
+        e = np.empty(N) if e is None else e
+        self._check(self._L.mgcnn_vcycle(self._h, _ptr(r, N), _ptr(e, N, True)), "mgcnn_vcycle")
+        return e
+
+    def solve(self, f, u, tol: float, maxit: int, relres=None, raise_on_limit: bool = False):
+        """Stationary iteration in place on u.  Returns (status, iters, relres[0..iters])."""
+        N = self.n * self.n
+        it = c_int(0)
+        hist = np.zeros(maxit + 1) if relres is None else relres
+        st = self._L.mgcnn_solve(self._h, _ptr(f, N), _ptr(u, N, True), float(tol), int(maxit), ctypes.byref(it),
+                                 _ptr(hist, None, True))
+        self._check(st, "mgcnn_solve", ok=(OK,) if raise_on_limit else (OK, NOT_CONVERGED))
+        return st, it.value, hist[: it.value + 1]

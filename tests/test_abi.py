@@ -1,0 +1,51 @@
+"""The C ABI library loads and exports every entry point that include/*.h declares
+(CPU only: no compute call, no device needed)."""
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(mgcnn_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2312_11093_gb300 import build
+    build.build()
+    from paper_2312_11093_gb300 import mgcnn
+    return mgcnn.load()
+
+
+def test_header_declares_the_paper_entry_points():
+    names = _declared()
+    for n in ("mgcnn_setup", "mgcnn_solve", "mgcnn_create", "mgcnn_set_weights", "mgcnn_vcycle"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_weight_count_matches_layout(lib):
+    from paper_2312_11093_gb300 import mgcnn
+    for C, nd, nu in [(8, 1, 1), (13, 3, 2), (4, 2, 1)]:
+        expect = 9 * C + 9 * C * C * (nd + nu + 2) + 9 * C + 9 * C * 5 + C + 4 * (9 * C * C + C) + 9 * C * C
+        assert mgcnn.weight_count(C, nd, nu) == expect
+    assert mgcnn.weight_count(7, 1, 1) == 0   # unsupported channel count
+
+
+def test_status_strings(lib):
+    assert lib.mgcnn_status_string(0) == b"MGCNN_OK"
+    assert lib.mgcnn_status_string(-6) == b"MGCNN_ERR_NONFINITE"

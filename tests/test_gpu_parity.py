@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 path tolerance: 1e-12 relative per V-cycle output (the arithmetic is the
+same FP64 operations in a different order; each output sums at most
+9 C (nu + 2) L products, so rounding differences stay near 1e-15 relative,
+three orders below the bar).  Iteration counts must be identical.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gmg as ogmg
+from oracle import mgcnn as omg
+from oracle import operator as oop
+from oracle.grid import level_sizes, num_levels
+from paper_2312_11093_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2312_11093_gb300 import build
+    build.build()
+    from paper_2312_11093_gb300 import mgcnn
+    mgcnn.load()
+    return mgcnn
+
+
+def relerr(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def problem(n, seed, kind="grf", b=(1.0, 0.5)):
+    rng = np.random.default_rng(seed)
+    if kind == "grf":
+        k = inputs.lognormal_k(n, 0.1, rng)
+    elif kind == "blocks":
+        k = inputs.random_blocks_k(n, rng)
+    elif kind == "chan":
+        k = inputs.channelised_k(n, rng, 0.05)
+    else:
+        k = inputs.checkerboard_k(n)
+    f = inputs.normal_rhs(n, rng)
+    return k, f
+
+
+def to_nhwc(levels):
+    return np.concatenate([s.transpose(1, 2, 0).ravel() for s in levels])
+
+
+@pytest.mark.parametrize("n,kind", [(3, "grf"), (7, "blocks"), (31, "grf"), (63, "chan"), (255, "checker")])
+def test_operator_all_levels(M, n, kind):
+    k, f = problem(n, n, kind, b=(-0.4, 1.3))
+    sv = M.Solver(8, 1, 1, b=(-0.4, 1.3))
+    sv.set_weights(np.zeros(sv.weight_count))
+    sv.setup(k.ravel().copy(), n)
+    ref = oop.level_stencils_div(k, (-0.4, 1.3), num_levels(n))
+    for l, (st, nl) in enumerate(zip(ref, level_sizes(n))):
+        got = sv.get_operator(l, nl).reshape(5, nl, nl)
+        for g, r in zip(got, [st.aC, st.aW, st.aE, st.aS, st.aN]):
+            assert np.max(np.abs(g - r)) <= 1e-14 * np.max(np.abs(st.aC)), l
+
+
+def test_residual_and_norm(M):
+    n = 127
+    k, f = problem(n, 1)
+    sv = M.Solver(8, 1, 1)
+    sv.set_weights(np.zeros(sv.weight_count))
+    sv.setup(k.ravel().copy(), n)
+    u = np.random.default_rng(2).standard_normal((n, n)) * 1e-3
+    r, nrm2 = sv.residual(f.ravel().copy(), u.ravel().copy())
+    st = oop.stencil_div(k, (1.0, 0.5))
+    rref = oop.residual(st, f, u)
+    assert np.max(np.abs(r - rref.ravel())) <= 1e-14 * np.max(np.abs(st.aC)) * np.max(np.abs(u))
+    assert abs(nrm2 - np.sum(rref ** 2)) <= 1e-12 * np.sum(rref ** 2)
+
+
+@pytest.mark.parametrize("C,nd,nu,n", [(8, 1, 1, 31), (8, 1, 1, 127), (4, 2, 1, 63), (12, 1, 2, 15),
+                                       (13, 3, 2, 31), (16, 1, 1, 7), (8, 1, 1, 3)])
+def test_setup_and_vcycle_fp64(M, C, nd, nu, n):
+    k, f = problem(n, 10 + n)
+    rng = np.random.default_rng(C + nd)
+    w = omg.random_weights(C, nd, nu, rng)
+    sts = oop.level_stencils_div(k, (1.0, 0.5), num_levels(n))
+    s_ref = omg.setup(w, sts)
+    e_ref = omg.solve_phase(w, s_ref, f)
+    sv = M.Solver(C, nd, nu)
+    sv.set_weights(M.pack_weights(w, C, nd, nu))
+    sv.setup(k.ravel().copy(), n)
+    s = sv.get_setup_tensors()
+    assert relerr(s, to_nhwc(s_ref)) <= 1e-12
+    e = sv.vcycle(f.ravel().copy())
+    assert relerr(e, e_ref) <= 1e-12
+
+
+def test_device_and_host_pointers_agree(M):
+    n, C = 63, 8
+    k, f = problem(n, 3)
+    w = omg.random_weights(C, 1, 1, np.random.default_rng(4))
+    sv = M.Solver(C, 1, 1)
+    sv.set_weights(M.pack_weights(w, C, 1, 1))
+    sv.setup(torch.from_numpy(k.ravel()).cuda(), n)
+    e_host = sv.vcycle(f.ravel().copy())
+    e_dev = sv.vcycle(torch.from_numpy(f.ravel()).cuda(), torch.empty(n * n, dtype=torch.float64, device="cuda"))
+    assert np.array_equal(e_host, e_dev.cpu().numpy())
+
+
+def _gmg_solver(M, k, n, b, precision="fp64", omega=0.8):
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    w = omg.gmg_equivalent_weights(2, 2)
+    s = omg.gmg_equivalent_setup(sts, omega)
+    sv = M.Solver(omg.GMG_CHANNELS, 3, 2, precision=precision, b=b)
+    sv.set_weights(M.pack_weights(w, omg.GMG_CHANNELS, 3, 2))
+    sv.setup(k.ravel().copy(), n)
+    sv.set_setup_tensors(to_nhwc(s))
+    return sv, sts, w, s
+
+
+def test_cfg0_gmg_equivalent_iterate_for_iterate(M):
+    """31x31 board of 4x4 blocks (log10 k ~ U(-1,1)), b=(1,0.5), f ~ N(0,1) seed 0,
+    MGCNN with GMG-equivalent weights (V(2,2), omega 0.8, FW, bilinear), 4 levels,
+    from u = 0 to relres 1e-10: identical iteration count to the oracle, every
+    cycle within 1e-12 relative when applied to the oracle's own iterate."""
+    n = 31
+    rng = np.random.default_rng(0)
+    k = inputs.block_board_k(n, rng)
+    f = inputs.normal_rhs(n, rng)
+    b = (1.0, 0.5)
+    sv, sts, w, s = _gmg_solver(M, k, n, b)
+    u_o, it_o, hist_o, its_o = ogmg.stationary_solve(sts, f, None, 1e-10, 200, 2, 2, 0.8)
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(f.ravel().copy(), u, 1e-10, 200)
+    assert st == M.OK and it == it_o
+    # f - A u cancels: near relres 1e-10 the computed norm carries rounding of order
+    # eps ||A|| ||u|| / ||f|| ~ 1e-11, so early norms must agree tightly, late ones loosely
+    hist_o = np.array(hist_o)
+    early = hist_o > 1e-6
+    np.testing.assert_allclose(hist[early], hist_o[early], rtol=1e-9)
+    np.testing.assert_allclose(hist[~early], hist_o[~early], rtol=5e-2)
+    assert relerr(u, u_o) <= 1e-12
+    for k_ in range(it_o):
+        r = f - oop.apply(sts[0], its_o[k_])
+        e = sv.vcycle(r.ravel().copy())
+        assert relerr(its_o[k_].ravel() + e, its_o[k_ + 1]) <= 1e-12, k_
+
+
+def test_solve_limits_and_special_cases(M):
+    n = 15
+    k, f = problem(n, 5)
+    sv, sts, w, s = _gmg_solver(M, k, n, (1.0, 0.5))
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(np.zeros(n * n), u, 1e-10, 10)
+    assert st == M.OK and it == 0 and not u.any()
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(f.ravel().copy(), u, 1e-30, 3)
+    assert st == M.NOT_CONVERGED and it == 3 and len(hist) == 4
+    bad = f.ravel().copy()
+    bad[7] = np.nan
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.solve(bad, np.zeros(n * n), 1e-8, 5)
+    assert ei.value.status == M.ERR_NONFINITE
+
+
+def test_argument_errors(M):
+    sv = M.Solver(8, 1, 1)
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.setup(np.ones(34 * 34), 32)
+    assert ei.value.status in (M.ERR_STATE, M.ERR_SIZE)
+    sv.set_weights(np.zeros(sv.weight_count))
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.setup(np.ones(34 * 34), 32)
+    assert ei.value.status == M.ERR_SIZE
+    r, e = np.ones(9), np.zeros(9)
+    assert sv._L.mgcnn_vcycle(sv._h, r.ctypes.data, e.ctypes.data) == M.ERR_STATE
+    k = np.ones(17 * 17)
+    k[5] = -1.0
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.setup(k, 15)
+    assert ei.value.status == M.ERR_NONFINITE
+    with pytest.raises(M.MGCNNError) as ei:
+        M.Solver(7, 1, 1)
+    assert ei.value.status == M.ERR_SIZE
+
+
+# ---- mixed precision -------------------------------------------------------
+@pytest.mark.parametrize("C,nd,nu,n", [(8, 1, 1, 63), (8, 1, 1, 255), (4, 1, 1, 31), (13, 3, 2, 63), (16, 2, 1, 127)])
+def test_mixed_vcycle_error_vs_fp64_oracle(M, C, nd, nu, n):
+    """BF16 tensors carry 8 significant bits (unit roundoff 2^-9 = 2e-3); each
+    layer rounds its output once and its products once, FP32 accumulation adds
+    nothing visible.  Along the 2 (nu+1) L + 2 rounding steps of one cycle the
+    errors add in quadrature for random weights: about 2e-3 * sqrt(2 * 3 * 8)
+    ~ 1.4e-2 at L = 7; the bar is 5e-2."""
+    k, f = problem(n, 20 + n)
+    w = omg.random_weights(C, nd, nu, np.random.default_rng(7))
+    sts = oop.level_stencils_div(k, (1.0, 0.5), num_levels(n))
+    e_ref = omg.solve_phase(w, omg.setup(w, sts), f)
+    sv = M.Solver(C, nd, nu, precision="mixed_bf16")
+    sv.set_weights(M.pack_weights(w, C, nd, nu))
+    sv.setup(k.ravel().copy(), n)
+    e = sv.vcycle(f.ravel().copy())
+    assert relerr(e, e_ref) <= 5e-2
+
+
+def test_mixed_gmg_equivalent_reaches_1e8_in_fp64(M):
+    """Defect correction: BF16 V-cycle, FP64 residual/update/norm reaches 1e-8."""
+    n = 127
+    k, f = problem(n, 6)
+    b = (1.0, 0.5)
+    sv, sts, w, s = _gmg_solver(M, k, n, b, precision="mixed_bf16")
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(f.ravel().copy(), u, 1e-8, 100)
+    assert st == M.OK and hist[-1] <= 1e-8
+    rtrue = f - oop.apply(sts[0], u.reshape(n, n))
+    assert np.linalg.norm(rtrue) / np.linalg.norm(f) <= 1.01e-8
+    sv64, *_ = _gmg_solver(M, k, n, b)
+    u64 = np.zeros(n * n)
+    _, it64, _ = sv64.solve(f.ravel().copy(), u64, 1e-8, 100)
+    assert it <= it64 + 3
