@@ -1,0 +1,384 @@
+"""Benchmark: MGCNN solves/s to relative residual 1e-6 at 4095^2 on GB300.
+
+One step = one whole solve through the C ABI: mgcnn_setup (operators on every
+level + setup network, or the analytic GMG-equivalent setup) followed by
+mgcnn_solve from u = 0 to ||f - A u||/||f|| <= tol (FP64 residual, BF16
+tensor-core V-cycle).  Inputs are resident in HBM when the timed region
+starts; the working set (> 2 GB per cycle) is far larger than L2.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead (bounded sample, see `cpu_reference`).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_11093_gb300 import inputs  # noqa: E402
+
+WEIGHTS_DIR = os.path.join(ROOT, "paper_2312_11093_gb300", "weights")
+TRAINED = os.path.join(WEIGHTS_DIR, "mgcnn_c8_trained.npy")
+METRIC = "solves/s to rel-res 1e-6 at 4095^2 (setup + solve), mixed BF16 MGCNN"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+# --------------------------------------------------------------------------- workload
+def make_workload(name: str, n: int, seed: int):
+    """Seeded synthetic problem.  Returns (k nodal (n+2)^2, f n^2, b)."""
+    rng = np.random.default_rng(seed)
+    if name == "channelised":
+        # binary k in {1, 1e3}: GRF (corr. length 0.02) above its 70th percentile is high-k
+        k = inputs.channelised_k(n, rng, 0.02, 0.70, 1.0, 1e3)
+        b = (1.0, 0.5)
+    elif name == "grf":
+        # lognormal GRF, corr. length 0.05, sigma 1; b = 10 (cos t, sin t), t ~ U(0, 2 pi)
+        t = rng.uniform(0.0, 2.0 * math.pi)
+        k = inputs.lognormal_k(n, 0.05, rng)
+        b = (10.0 * math.cos(t), 10.0 * math.sin(t))
+    else:
+        raise ValueError(name)
+    f = inputs.normal_rhs(n, rng)
+    return np.ascontiguousarray(k.ravel()), np.ascontiguousarray(f.ravel()), b
+
+
+def network(kind: str):
+    """(channels, nu_d, nu_u, blob, gmg) for the solve network."""
+    from paper_2312_11093_gb300 import mgcnn
+    if kind == "gmg":
+        return 13, 3, 2, mgcnn.gmg_weights(2, 2), True
+    blob = np.load(TRAINED)
+    return 8, 1, 1, np.ascontiguousarray(blob, dtype=np.float64), False
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=lambda: self.lines.extend(self.proc.stdout), daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.t.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- roofline helpers
+def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
+    """Bytes a launch of `kind` at the finest level must move (each operand once)."""
+    N = n * n
+    return {
+        "residual": 60.0 * N,                    # u, f (FP64) + 5 stencil arrays in, FP32 r out
+        "resnet": 6.0 * cp * N,                  # x, s in; y out (BF16, cp channels)
+        "restrict": 2.0 * cp * N + 0.5 * cp * N,  # fine x in, coarse y out
+        "prolong": 4.5 * cp * N,                 # fine y in/out, coarse x in
+        "in": (4.0 + 2.0 * cp) * N,              # FP32 r in, BF16 x out
+        "out": (2.0 * cp + 16.0) * N,            # BF16 x in, FP64 u in/out
+    }[kind]
+
+
+def traffic_record(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (source hash recorded beside the number)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2312_11093_gb300", "csrc", "mixed.cu"), "rb").read()
+    h = hashlib.sha1(src).hexdigest()[:12]
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[2] == h:
+            return float(parts[3])
+    return None
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_reference(workload: str, net: str, n_full: int = 4095, n_sample: int | None = None,
+                  n_iters: int | None = None, tol: float = 1e-6):
+    """FP64 oracle timed on this host: setup + one cycle at n_sample^2, scaled by unknowns to
+    n_full^2, times the oracle's own cycle count for the same workload at n_iters^2."""
+    import oracle.mgcnn as omg
+    import oracle.operator as oop
+    from oracle.grid import num_levels
+
+    # about 10-30 s of numpy work: the 13-channel GMG network costs ~3.4x the 8-channel one
+    n_sample = n_sample or min(n_full, 1023 if net == "gmg" else 2047)
+    n_iters = n_iters or min(n_full, 255 if net == "gmg" else 511)
+
+    def net_for(sts, n):
+        if net == "gmg":
+            return omg.gmg_equivalent_weights(2, 2), omg.gmg_equivalent_setup(sts, 0.8)
+        blob = np.load(TRAINED)
+        w = unpack_blob(blob, 8, 1, 1)
+        return w, omg.setup(w, sts)
+
+    k, f, b = make_workload(workload, n_iters, 123)
+    m = n_iters + 2
+    sts = oop.level_stencils_div(k.reshape(m, m), b, num_levels(n_iters))
+    w, s = net_for(sts, n_iters)
+    _, iters, _, _ = omg.stationary_solve(w, s, sts[0], f.reshape(n_iters, n_iters), None, tol, 300)
+    k, f, b = make_workload(workload, n_sample, 124)
+    m = n_sample + 2
+    t0 = time.perf_counter()
+    sts = oop.level_stencils_div(k.reshape(m, m), b, num_levels(n_sample))
+    w, s = net_for(sts, n_sample)
+    t1 = time.perf_counter()
+    fs = f.reshape(n_sample, n_sample)
+    r = fs - oop.apply(sts[0], np.zeros_like(fs))
+    _ = fs + omg.solve_phase(w, s, r)
+    t2 = time.perf_counter()
+    scale = (n_full / n_sample) ** 2
+    t_solve = scale * ((t1 - t0) + iters * (t2 - t1))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": (f"numpy FP64 oracle: setup {t1 - t0:.2f}s + 1 cycle {t2 - t1:.2f}s at {n_sample}^2, "
+                       f"x{scale:.2f} to {n_full}^2, x{iters} cycles (oracle's count at {n_iters}^2, tol {tol:g})"),
+            "seconds_per_solve": t_solve}
+
+
+def unpack_blob(blob, C, nd, nu):
+    from paper_2312_11093_gb300.mgcnn import FEATURES, SETUP_LAYERS, WEIGHT_ORDER
+    shapes = {"w_in": (C, 1, 3, 3), "w_down": (nd, C, C, 3, 3), "w_up": (nu, C, C, 3, 3), "w_R": (C, C, 3, 3),
+              "w_P": (C, C, 3, 3), "w_out": (1, C, 3, 3), "sw_in": (C, FEATURES, 3, 3), "sb_in": (C,),
+              "sw": (SETUP_LAYERS, C, C, 3, 3), "sb": (SETUP_LAYERS, C), "sw_R": (C, C, 3, 3)}
+    out, o = {}, 0
+    for key in WEIGHT_ORDER:
+        sz = int(np.prod(shapes[key]))
+        out[key] = np.asarray(blob[o:o + sz]).reshape(shapes[key])
+        o += sz
+    return out
+
+
+# --------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=4095)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--net", default=None, choices=["trained", "gmg"])
+    ap.add_argument("--workload", default=None, choices=["channelised", "grf"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg")
+    workload = args.workload or ("channelised" if net == "trained" else "grf")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        vals = []
+        for _ in range(args.steps):
+            vals.append(cpu_reference(workload, net, args.n, tol=args.tol))
+        v = statistics.median([x["value"] for x in vals])
+        base = vals[0]
+        base["value"] = v
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 / v, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": f"{workload}_{args.n}", "net": net, "tol": args.tol},
+                          "cpu_baseline": base,
+                          "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                          "wall_s": time.perf_counter() - t0}))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2312_11093_gb300 import mgcnn
+
+    n, tol = args.n, args.tol
+    C, nd, nu, blob, is_gmg = network(net)
+    k_h, f_h, b = make_workload(workload, n, 4 + 1000 * rank)
+    dev = torch.device("cuda", local)
+    k_d = torch.from_numpy(k_h).to(dev)
+    f_d = torch.from_numpy(f_h).to(dev)
+    u_d = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make_solver(prec):
+        sv = mgcnn.Solver(C, nd, nu, precision=prec, b=b, stream=stream)
+        sv.set_weights(blob)
+        return sv
+
+    def step(sv, k, f, u):
+        if is_gmg:
+            sv.setup_gmg(k, n, 0.8)
+        else:
+            sv.setup(k, n)
+        if isinstance(u, np.ndarray):
+            u[:] = 0.0
+        else:
+            u.zero_()
+        return sv.solve(f, u, tol, 300)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    sv = make_solver("mixed_bf16")
+    for _ in range(args.warmup):
+        st, iters, hist = step(sv, k_d, f_d, u_d)
+    sv.profile_read()
+    sv.profile(True)
+    launches0 = mgcnn.kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st, iters, hist = step(sv, k_d, f_d, u_d)
+        ev1.record(stream)
+        barrier()
+    launches = (mgcnn.kernel_launches() - launches0) // args.steps
+    prof = sv.profile_read()
+    sv.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * 1e3 / ms_per_step
+    relres_mixed = float(hist[-1])
+    u_mixed = u_d.clone()
+
+    # solve-only time (setup excluded), as the paper splits them
+    if is_gmg:
+        sv.setup_gmg(k_d, n, 0.8)
+    else:
+        sv.setup(k_d, n)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    u_d.zero_()
+    sv.solve(f_d, u_d, tol, 300)
+    torch.cuda.synchronize(dev)
+    solve_only_ms = (time.perf_counter() - t0) * 1e3
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    u_h = np.zeros(n * n)
+    step(sv, k_h, f_h, u_h)
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(sv, k_h, f_h, u_h)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    h2d = k_h.nbytes + f_h.nbytes + u_h.nbytes
+    d2h = u_h.nbytes
+
+    # roofline of the dominant kernel (largest share of timed kernel time)
+    cp = 8 if C <= 8 else 16
+    dom = max(prof, key=lambda kk: prof[kk][0])
+    dom_ms, dom_cnt = prof[dom]
+    with open(PEAKS) as fh:
+        peaks = json.load(fh)
+    peak = float(peaks["hbm_gbs"])
+    achieved = algorithmic_bytes(dom, n, cp) / (dom_ms / dom_cnt * 1e-3) / 1e9 if dom_cnt else None
+    kname = {"residual": "residual_kernel", "resnet": "resnet_mma_kernel", "restrict": "rcnn_mma_kernel",
+             "prolong": "tcnn_add_kernel16", "in": "in_kernel16", "out": "out_kernel16"}[dom]
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "traffic": traffic_record(kname, f"{workload}_{n}"),
+                "algorithmic_bytes_per_launch": algorithmic_bytes(dom, n, cp),
+                "avg_launch_ms": dom_ms / dom_cnt if dom_cnt else None,
+                "kernel_share_ms": {kk: round(v[0] / args.steps, 4) for kk, v in prof.items()}}
+
+    result = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+              "config": {"workload": f"{workload}_{n}", "n": n, "tol": tol, "net": net, "channels": C,
+                         "down_layers": nd, "up_layers": nu, "b": list(b), "l2": "inputs larger than L2",
+                         "parallelism": "replicas" if world > 1 else "single"},
+              "iters": iters, "relres": relres_mixed, "solve_only_ms": solve_only_ms,
+              "e2e": {"value": world * 1e3 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+              "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary()}
+
+    if not args.no_fp64 and rank == 0:
+        sv64 = make_solver("fp64")
+        u64 = torch.zeros_like(u_d)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st64, it64, h64 = step(sv64, k_d, f_d, u64)
+        torch.cuda.synchronize(dev)
+        t64 = time.perf_counter() - t0
+        err = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
+        result["fp64"] = {"value": 1.0 / t64, "unit": "solves/s", "iters": it64, "relres": float(h64[-1]),
+                          "mixed_vs_fp64_rel_err": err, "mixed_speedup": value / world * t64}
+        sv64.close()
+    if not args.no_cpu and rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_reference(workload, net, n, tol=tol)
+    sv.close()
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

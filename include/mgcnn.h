@@ -134,6 +134,21 @@ int mgcnn_set_weights(mgcnn_ctx* ctx, const double* w, size_t count);
  * non-finite), CUDA. */
 int mgcnn_setup(mgcnn_ctx* ctx, const double* coeff, int n);
 
+/* Setup for the 13-channel network whose solve phase is exactly classical
+ * geometric multigrid V(nu1, nu2) (Sec. 2.3: weighted Jacobi with weight
+ * omega, full-weighting restriction, bilinear prolongation, rediscretised
+ * coarse operators), used as a learning-free reference network and as the GMG
+ * comparator.  Builds the operators like mgcnn_setup, then sets the setup
+ * tensors analytically instead of running the setup network:
+ *   s[E_o](q) = -omega a_o(q-o)/a_C(q-o), s[G_o](q) = -a_o(q-o) for o in
+ *   {C, W, E, S, N} (channels 0-4 and 5-9), s[F_J] = omega/a_C, s[F_G] = 1,
+ *   s[D] = 0 (channels 10, 11, 12).
+ * The matching weights (ResNetDown = nu1 Jacobi layers + one defect layer,
+ * ResNetUp = nu2 Jacobi layers) must be loaded with mgcnn_set_weights; the
+ * Python binding's gmg_weights() builds that blob.  Requires channels == 13.
+ * Errors: SIZE (channels), ARG (omega not in (0,2)), as mgcnn_setup. */
+int mgcnn_setup_gmg(mgcnn_ctx* ctx, const double* coeff, int n, double omega);
+
 /* Number of doubles of all setup tensors of the current setup:
  * sum_l n_l^2 * C.  0 before setup. */
 size_t mgcnn_setup_tensor_count(const mgcnn_ctx* ctx);
@@ -171,6 +186,19 @@ int mgcnn_vcycle(mgcnn_ctx* ctx, const double* r, double* e);
  * NaN/Inf; u holds the last finite iterate's update), STATE, ARG, CUDA. */
 int mgcnn_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit,
                 int* iters, double* relres);
+
+/* Instrumentation (no counterpart in the paper; used by the benchmark).
+ * mgcnn_kernel_launches: kernels launched by this library in this process.
+ * mgcnn_profile(ctx, 1): from now on bracket the finest-level launch of each
+ * kernel class with CUDA events on the context's stream; mgcnn_profile_read
+ * returns, per class, the summed milliseconds and the number of launches
+ * since the last read (classes: 0 residual, 1 ResNet layer, 2 restriction,
+ * 3 prolongation-add into the finest level, 4 reChannel-in, 5 reChannel-out
+ * with update) and clears them.  Timing adds one event pair per bracketed
+ * launch. */
+long long mgcnn_kernel_launches(void);
+int mgcnn_profile(mgcnn_ctx* ctx, int enable);
+int mgcnn_profile_read(mgcnn_ctx* ctx, double* ms, long long* counts, int nkinds);
 
 /* Human-readable name of a status code (static storage). */
 const char* mgcnn_status_string(int status);

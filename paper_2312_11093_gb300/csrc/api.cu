@@ -4,6 +4,7 @@
 // (Algorithm 3) and the stationary iteration (Eq. 1) on one GPU.  Every
 // arithmetic step runs in this library's kernels; this file only sequences
 // launches, owns device buffers and moves data across the ABI.
+#include <atomic>
 #include <cmath>
 
 #include "ops.cuh"
@@ -49,6 +50,32 @@ Status ensure(DevBuf& b, size_t bytes) {
   b.p = p;
   b.bytes = bytes;
   return {};
+}
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int prof_begin(mgcnn_ctx* c, int kind) {
+  if (!c->prof) return -1;
+  if (c->ev_used == c->ev_start.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return -1;
+    }
+    c->ev_start.push_back(a);
+    c->ev_stop.push_back(b);
+    c->ev_kind.push_back(kind);
+  }
+  const size_t i = c->ev_used++;
+  c->ev_kind[i] = kind;
+  cudaEventRecord(c->ev_start[i], c->stream);
+  return (int)i;
+}
+
+void prof_end(mgcnn_ctx* c, int slot) {
+  if (slot >= 0) cudaEventRecord(c->ev_stop[slot], c->stream);
 }
 
 bool is_device_pointer(const void* p) {
@@ -236,8 +263,8 @@ Status require_setup(const mgcnn_ctx* c) {
   return {};
 }
 
-Status do_setup(mgcnn_ctx* c, const double* coeff, int n) {
-  if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
+// Levels, buffers, coefficient check and the operator on every level (A1).
+Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
   const int Lmax = levels_of(n);
   if (Lmax < 1) return make_status(MGCNN_ERR_SIZE, "n=%d is not 2^m-1 with m>=2", n);
   if (Lmax > kMaxLevels) return make_status(MGCNN_ERR_SIZE, "n=%d too large", n);
@@ -290,7 +317,14 @@ Status do_setup(mgcnn_ctx* c, const double* coeff, int n) {
       if (l < L - 1) MG_TRY(launch_inject_mu(c->coef[l].as<double>(), c->coef[l + 1].as<double>(), nlv, c->stream));
     }
   }
-  // setup network
+  return {};
+}
+
+Status do_setup(mgcnn_ctx* c, const double* coeff, int n) {
+  if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
+  MG_TRY(setup_operators(c, coeff, n));
+  const int L = c->L;
+  // setup network (Algorithm 2)
   if (c->cfg.precision == MGCNN_PREC_FP64) {
     double* outs[kMaxLevels];
     for (int l = 0; l < L; ++l) outs[l] = c->s64[l].as<double>();
@@ -368,6 +402,10 @@ void mgcnn_destroy(mgcnn_ctx* c) {
   release(c->feat); release(c->f); release(c->u); release(c->r); release(c->e);
   release(c->r32); release(c->partial); release(c->scalars);
   mixed_release(c);
+  for (size_t i = 0; i < c->ev_start.size(); ++i) {
+    cudaEventDestroy(c->ev_start[i]);
+    cudaEventDestroy(c->ev_stop[i]);
+  }
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   delete c;
 }
@@ -398,6 +436,26 @@ int mgcnn_set_weights(mgcnn_ctx* c, const double* w, size_t count) {
 int mgcnn_setup(mgcnn_ctx* c, const double* coeff, int n) {
   if (!c || !coeff) return MGCNN_ERR_ARG;
   return finish(c, do_setup(c, coeff, n));
+}
+
+int mgcnn_setup_gmg(mgcnn_ctx* c, const double* coeff, int n, double omega) {
+  if (!c || !coeff) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    if (c->cfg.channels != kGmgChannels)
+      return make_status(MGCNN_ERR_SIZE, "GMG-equivalent setup needs %d channels", kGmgChannels);
+    if (!(omega > 0.0 && omega < 2.0)) return make_status(MGCNN_ERR_ARG, "omega must be in (0, 2)");
+    MG_TRY(setup_operators(c, coeff, n));
+    for (int l = 0; l < c->L; ++l) {
+      if (c->cfg.precision == MGCNN_PREC_FP64)
+        MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->s64[l].as<double>(), c->lv[l].n, omega, c->stream));
+      else
+        MG_TRY(mixed_gmg_setup_level(c, l, omega));
+    }
+    MG_TRY(sync(c));
+    c->have_setup = true;
+    return {};
+  }();
+  return finish(c, st);
 }
 
 size_t mgcnn_setup_tensor_count(const mgcnn_ctx* c) {
@@ -529,8 +587,10 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
     const bool mixed = c->cfg.precision == MGCNN_PREC_MIXED_BF16;
     for (int k = 0;; ++k) {
       // mixed: the V-cycle consumes an FP32 copy of r (scaled in-kernel), FP64 r is not stored
+      const int ps = prof_begin(c, kProfResidual);
       MG_TRY(launch_residual(df, du, c->op[0].as<double>(), mixed ? nullptr : c->r.as<double>(),
                              mixed ? c->r32.as<float>() : nullptr, c->partial.as<double>(), c->n, c->stream));
+      prof_end(c, ps);
       MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>(), c->stream));
       double rn2 = 0.0;
       MG_TRY(read_scalar(c, 0, &rn2));
@@ -554,6 +614,37 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
     MG_TRY(stage_out_finish(c, u, du, N, host));
     MG_TRY(sync(c));
     return result;
+  }();
+  return finish(c, st);
+}
+
+long long mgcnn_kernel_launches(void) { return g_launches.load(); }
+
+int mgcnn_profile(mgcnn_ctx* c, int enable) {
+  if (!c) return MGCNN_ERR_ARG;
+  c->prof = enable ? 1 : 0;
+  c->ev_used = 0;
+  return finish(c, {});
+}
+
+int mgcnn_profile_read(mgcnn_ctx* c, double* ms, long long* counts, int nkinds) {
+  if (!c || !ms || !counts || nkinds < 1) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(sync(c));
+    for (int k = 0; k < nkinds; ++k) {
+      ms[k] = 0.0;
+      counts[k] = 0;
+    }
+    for (size_t i = 0; i < c->ev_used; ++i) {
+      const int k = c->ev_kind[i];
+      if (k >= nkinds) continue;
+      float t = 0.f;
+      MG_CUDA(cudaEventElapsedTime(&t, c->ev_start[i], c->ev_stop[i]));
+      ms[k] += t;
+      counts[k] += 1;
+    }
+    c->ev_used = 0;
+    return {};
   }();
   return finish(c, st);
 }

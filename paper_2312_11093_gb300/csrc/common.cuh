@@ -95,6 +95,11 @@ struct mgcnn_ctx {
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
   mgcnn::DevBuf s32tmp;                   // FP32 setup output before the BF16 cast
   mgcnn::DevBuf scalars;                  // device scalars (norms)
+  // optional per-kernel timing (mgcnn_profile)
+  int prof = 0;
+  std::vector<cudaEvent_t> ev_start, ev_stop;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
   double* h_scalars = nullptr;            // pinned host mirror of `scalars`
 };
 
@@ -112,11 +117,20 @@ bool is_device_pointer(const void* p);
     if (_e != cudaSuccess) return ::mgcnn::cuda_status(_e, #call); \
   } while (0)
 
+// Every kernel launch site is followed by MG_LAUNCH, which also counts it.
+void count_launch();
 #define MG_LAUNCH(what)                                            \
   do {                                                             \
+    ::mgcnn::count_launch();                                       \
     cudaError_t _e = cudaGetLastError();                           \
     if (_e != cudaSuccess) return ::mgcnn::cuda_status(_e, what);  \
   } while (0)
+
+// Profiling kinds: finest-level launches bracketed by events when enabled.
+enum ProfKind { kProfResidual = 0, kProfResnet = 1, kProfRestrict = 2, kProfProlong = 3, kProfIn = 4,
+                kProfOut = 5, kProfKinds = 6 };
+int prof_begin(mgcnn_ctx* c, int kind);   // -1 when profiling is off
+void prof_end(mgcnn_ctx* c, int slot);
 
 #define MG_TRY(expr)                       \
   do {                                     \

@@ -402,39 +402,51 @@ Status vcycle_cp(mgcnn_ctx* c, const float* r32, const double* norm2, double* e,
   }
   cudaStream_t st = c->stream;
   const int n0 = c->lv[0].n;
+  int ps = prof_begin(c, kProfIn);
   in_kernel16<CP><<<grid_for((size_t)n0 * n0, 128), 128, 0, st>>>(r32, norm2, w_in, x[0], n0);
   MG_LAUNCH("in_kernel16");
+  prof_end(c, ps);
   for (int l = 0; l < c->L; ++l) {
     const int nl = c->lv[l].n;
     const dim3 grid((nl + TW - 1) / TW, (nl + TH - 1) / TH);
     for (int i = 0; i < c->wl.nu_d; ++i) {
+      ps = (l == 0) ? prof_begin(c, kProfResnet) : -1;
       resnet_mma_kernel<CP><<<grid, kWarps * 32, 0, st>>>(x[l], c->s16[l].as<bf16>(), f_down + i * ml.frag_words, t[l], nl);
       MG_LAUNCH("resnet_mma_kernel(down)");
+      prof_end(c, ps);
       std::swap(x[l], t[l]);
     }
     if (l < c->L - 1) {
       const int nc = c->lv[l + 1].n;
       const dim3 g2((nc + TW - 1) / TW, (nc + TH - 1) / TH);
+      ps = (l == 0) ? prof_begin(c, kProfRestrict) : -1;
       rcnn_mma_kernel<CP><<<g2, kWarps * 32, 0, st>>>(x[l], f_R, x[l + 1], nl);
       MG_LAUNCH("rcnn_mma_kernel");
+      prof_end(c, ps);
     }
   }
   for (int l = c->L - 1; l >= 0; --l) {
     const int nl = c->lv[l].n;
     const dim3 grid((nl + TW - 1) / TW, (nl + TH - 1) / TH);
     for (int i = 0; i < c->wl.nu_u; ++i) {
+      ps = (l == 0) ? prof_begin(c, kProfResnet) : -1;
       resnet_mma_kernel<CP><<<grid, kWarps * 32, 0, st>>>(x[l], c->s16[l].as<bf16>(), f_up + i * ml.frag_words, t[l], nl);
       MG_LAUNCH("resnet_mma_kernel(up)");
+      prof_end(c, ps);
       std::swap(x[l], t[l]);
     }
     if (l > 0) {
       const int nf = c->lv[l - 1].n;
+      ps = (l == 1) ? prof_begin(c, kProfProlong) : -1;
       tcnn_add_kernel16<CP><<<grid_for((size_t)nf * nf, 128), 128, 0, st>>>(x[l], w_P, x[l - 1], nf);
       MG_LAUNCH("tcnn_add_kernel16");
+      prof_end(c, ps);
     }
   }
+  ps = prof_begin(c, kProfOut);
   out_kernel16<CP><<<grid_for((size_t)n0 * n0, 128), 128, 0, st>>>(x[0], w_out, norm2, u_skip, e, n0);
   MG_LAUNCH("out_kernel16");
+  prof_end(c, ps);
   return {};
 }
 
@@ -494,6 +506,21 @@ Status setup_mixed(mgcnn_ctx* c) {
     pad_to_bf16_kernel<float><<<grid_for(N * cp, 256), 256, 0, c->stream>>>(outs[l], c->s16[l].as<bf16>(), N, C, cp);
     MG_LAUNCH("pad_to_bf16_kernel");
   }
+  return {};
+}
+
+Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega) {
+  const size_t N = c->lv[l].N();
+  const int cp = c->cp;
+  MG_TRY(ensure(c->s16[l], N * cp * sizeof(bf16)));
+  MG_TRY(ensure(c->x16a[l], N * cp * sizeof(bf16)));
+  MG_TRY(ensure(c->x16b[l], N * cp * sizeof(bf16)));
+  MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
+  MG_TRY(ensure(c->setup_a, N * kGmgChannels * sizeof(double)));
+  MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->setup_a.as<double>(), c->lv[l].n, omega, c->stream));
+  pad_to_bf16_kernel<double><<<grid_for(N * cp, 256), 256, 0, c->stream>>>(c->setup_a.as<double>(),
+                                                                            c->s16[l].as<bf16>(), N, kGmgChannels, cp);
+  MG_LAUNCH("pad_to_bf16_kernel");
   return {};
 }
 

@@ -16,6 +16,8 @@ Status vcycle_mixed(mgcnn_ctx* c, const double* r, double* e, const double* u_sk
 Status vcycle_mixed_r32(mgcnn_ctx* c, const float* r32, const double* norm2_dev, double* e, const double* u_skip);
 Status mixed_set_setup_level(mgcnn_ctx* c, int l, const double* src);
 Status mixed_get_setup_level(mgcnn_ctx* c, int l, double* dst);
+// GMG-equivalent setup tensors of level l into the BF16 store.
+Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega);
 void mixed_release(mgcnn_ctx* c);
 // Defined in api.cu: Algorithm 2 in FP32 into out[l] ([n_l^2][C] floats).
 Status run_setup_net_fp32(mgcnn_ctx* c, float* const* out);

@@ -236,6 +236,42 @@ Status launch_reduce(const double* partial, int count, double* out, cudaStream_t
   return {};
 }
 
+// Setup tensors that turn Algorithm 3 into classical GMG (13 channels: E_C..E_N,
+// G_C..G_N, F_J, F_G, D).  A stencil acting on e is rewritten in source-side
+// form, sum_o a_o(p) e(p+o) = sum_o a_o(q-o) e(q) with q = p + o, so the setup
+// tensor multiplying a layer's input carries the coefficient of tap o:
+//   s[E_o](q) = -omega a_o(q-o) / a_C(q-o),  s[G_o](q) = -a_o(q-o)   (0 if q-o is outside)
+//   s[F_J] = omega / a_C,  s[F_G] = 1,  s[D] = 0.
+__global__ void gmg_setup_kernel(const double* __restrict__ op, double* __restrict__ out, int n, double omega) {
+  const size_t N = (size_t)n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (int)N) return;
+  const int j = p / n, i = p - j * n;
+  const int dy[5] = {0, 0, 0, -1, 1}, dx[5] = {0, -1, 1, 0, 0};  // C, W, E, S, N
+  double* o = out + (size_t)p * kGmgChannels;
+  for (int k = 0; k < 5; ++k) {
+    const int pj = j - dy[k], pi = i - dx[k];
+    double sE = 0.0, sG = 0.0;
+    if (pj >= 0 && pj < n && pi >= 0 && pi < n) {
+      const size_t q = (size_t)pj * n + pi;
+      const double a = op[k * N + q];
+      sE = -omega * a / op[q];
+      sG = -a;
+    }
+    o[k] = sE;
+    o[5 + k] = sG;
+  }
+  o[10] = omega / op[p];
+  o[11] = 1.0;
+  o[12] = 0.0;
+}
+
+Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st) {
+  gmg_setup_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, out, n, omega);
+  MG_LAUNCH("gmg_setup_kernel");
+  return {};
+}
+
 __global__ void axpy_to_kernel(const double* __restrict__ u, const double* __restrict__ e,
                                double* __restrict__ out, size_t N) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

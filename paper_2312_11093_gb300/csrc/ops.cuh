@@ -26,6 +26,10 @@ Status launch_residual(const double* f, const double* u, const double* op, doubl
 Status launch_sumsq(const double* v, size_t N, double* partial, cudaStream_t st);
 // out[0] = sum of partial[0..count) in a fixed order (deterministic).
 Status launch_reduce(const double* partial, int count, double* out, cudaStream_t st);
+// Setup tensors of the 13-channel network whose solve phase is classical GMG
+// (weighted Jacobi, full weighting, bilinear): out [N][13] FP64.
+constexpr int kGmgChannels = 13;
+Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st);
 Status launch_axpy_to(const double* u, const double* e, double* out, size_t N, cudaStream_t st);
 
 // ---- net_generic.cu: FP64 / FP32 direct convolution kernels ----------------

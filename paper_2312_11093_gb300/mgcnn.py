@@ -55,6 +55,7 @@ def load() -> ctypes.CDLL:
         "mgcnn_set_stream": (c_int, [c_void_p, c_void_p]),
         "mgcnn_set_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
         "mgcnn_setup": (c_int, [c_void_p, c_void_p, c_int]),
+        "mgcnn_setup_gmg": (c_int, [c_void_p, c_void_p, c_int, c_double]),
         "mgcnn_setup_tensor_count": (c_size_t, [c_void_p]),
         "mgcnn_set_setup_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
         "mgcnn_get_setup_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
@@ -62,6 +63,9 @@ def load() -> ctypes.CDLL:
         "mgcnn_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, dp]),
         "mgcnn_vcycle": (c_int, [c_void_p, c_void_p, c_void_p]),
         "mgcnn_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), c_void_p]),
+        "mgcnn_kernel_launches": (ctypes.c_longlong, []),
+        "mgcnn_profile": (c_int, [c_void_p, c_int]),
+        "mgcnn_profile_read": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
         "mgcnn_status_string": (c_char_p, [c_int]),
         "mgcnn_last_error": (c_char_p, [c_void_p]),
     }
@@ -91,6 +95,11 @@ def _ptr(a, n: int | None = None, writable: bool = False) -> int:
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def kernel_launches() -> int:
+    """Kernels launched by libmgcnn.so in this process so far."""
+    return int(load().mgcnn_kernel_launches())
+
+
 def weight_count(channels: int, down_layers: int = 1, up_layers: int = 1) -> int:
     cfg = Config(channels, down_layers, up_layers, 0, 0, 1, 0, 0.0, 0.0)
     return int(load().mgcnn_weight_count(ctypes.byref(cfg)))
@@ -116,6 +125,45 @@ def pack_weights(w: dict, channels: int, down_layers: int, up_layers: int) -> np
     blob = np.ascontiguousarray(np.concatenate(parts))
     assert blob.size == weight_count(C, down_layers, up_layers)
     return blob
+
+
+GMG_CHANNELS = 13
+
+
+def gmg_weights(nu1: int = 2, nu2: int = 2) -> np.ndarray:
+    """Weight blob (C = 13, nu_d = nu1 + 1, nu_u = nu2) whose solve phase, with the setup
+    tensors of mgcnn_setup_gmg, is classical GMG V(nu1, nu2) (Sec. 2.3).
+
+    Channels: 0-4 copies of the correction e used by the Jacobi update (taps C, W, E,
+    S, N), 5-9 copies used by the defect, 10 and 11 the level right-hand side (Jacobi
+    and defect copies), 12 the defect.  A Jacobi layer adds tap o of channel o and
+    the centre of channel 10 into every e copy; the defect layer adds tap o of
+    channel 5 + o and the centre of channel 11 into channel 12.  RCNN carries the
+    defect into both right-hand-side copies by full weighting; TCNN adds the
+    bilinear interpolation of channel 0 into every e copy."""
+    C = GMG_CHANNELS
+    taps = [(1, 1), (1, 0), (1, 2), (0, 1), (2, 1)]          # C, W, E, S, N
+    jac = np.zeros((C, C, 3, 3))
+    for t in range(10):
+        for o, (a, b) in enumerate(taps):
+            jac[t, o, a, b] = 1.0
+        jac[t, 10, 1, 1] = 1.0
+    dfc = np.zeros((C, C, 3, 3))
+    for o, (a, b) in enumerate(taps):
+        dfc[12, 5 + o, a, b] = 1.0
+    dfc[12, 11, 1, 1] = 1.0
+    stencil121 = np.outer([1.0, 2.0, 1.0], [1.0, 2.0, 1.0])
+    R = np.zeros((C, C, 3, 3))
+    R[10, 12] = R[11, 12] = stencil121 / 16.0
+    P = np.zeros((C, C, 3, 3))
+    P[0, :10] = stencil121 / 4.0
+    w_in = np.zeros((C, 1, 3, 3))
+    w_in[10, 0, 1, 1] = w_in[11, 0, 1, 1] = 1.0
+    w_out = np.zeros((1, C, 3, 3))
+    w_out[0, 0, 1, 1] = 1.0
+    w = {"w_in": w_in, "w_down": np.stack([jac] * nu1 + [dfc]), "w_up": np.stack([jac] * nu2),
+         "w_R": R, "w_P": P, "w_out": w_out}
+    return pack_weights(w, C, nu1 + 1, nu2)
 
 
 class Solver:
@@ -170,6 +218,24 @@ class Solver:
     def setup(self, coeff, n: int):
         self._check(self._L.mgcnn_setup(self._h, _ptr(coeff), int(n)), "mgcnn_setup")
         self.n = int(n)
+
+    def setup_gmg(self, coeff, n: int, omega: float = 0.8):
+        """Operators + analytic GMG-equivalent setup tensors (needs channels == 13)."""
+        self._check(self._L.mgcnn_setup_gmg(self._h, _ptr(coeff), int(n), float(omega)), "mgcnn_setup_gmg")
+        self.n = int(n)
+
+    PROFILE_KINDS = ("residual", "resnet", "restrict", "prolong", "in", "out")
+
+    def profile(self, enable: bool = True):
+        self._check(self._L.mgcnn_profile(self._h, int(enable)), "mgcnn_profile")
+
+    def profile_read(self) -> dict:
+        """{kind: (total_ms, launches)} since the last read."""
+        k = len(self.PROFILE_KINDS)
+        ms = np.zeros(k)
+        cnt = np.zeros(k, dtype=np.int64)
+        self._check(self._L.mgcnn_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, k), "mgcnn_profile_read")
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(self.PROFILE_KINDS)}
 
     def setup_tensor_count(self) -> int:
         return int(self._L.mgcnn_setup_tensor_count(self._h))

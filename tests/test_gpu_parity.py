@@ -220,3 +220,21 @@ def test_mixed_gmg_equivalent_reaches_1e8_in_fp64(M):
     u64 = np.zeros(n * n)
     _, it64, _ = sv64.solve(f.ravel().copy(), u64, 1e-8, 100)
     assert it <= it64 + 3
+
+
+def test_product_gmg_setup_matches_oracle_construction(M):
+    """The library's own GMG-equivalent setup tensors and the binding's weight blob
+    equal the oracle's independent construction; the solve then matches GMG."""
+    n = 63
+    k, f = problem(n, 8, "blocks")
+    b = (0.7, -1.2)
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    s_ref = omg.gmg_equivalent_setup(sts, 0.7)
+    w_ref = M.pack_weights(omg.gmg_equivalent_weights(2, 1), omg.GMG_CHANNELS, 3, 1)
+    assert np.array_equal(M.gmg_weights(2, 1), w_ref)
+    sv = M.Solver(omg.GMG_CHANNELS, 3, 1, b=b)
+    sv.set_weights(M.gmg_weights(2, 1))
+    sv.setup_gmg(k.ravel().copy(), n, 0.7)
+    assert relerr(sv.get_setup_tensors(), to_nhwc(s_ref)) <= 1e-15
+    r = f.copy()
+    assert relerr(sv.vcycle(r.ravel().copy()), ogmg.vcycle(sts, r, 2, 1, 0.7)) <= 1e-12
