@@ -187,6 +187,37 @@ int mgcnn_vcycle(mgcnn_ctx* ctx, const double* r, double* e);
 int mgcnn_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit,
                 int* iters, double* relres);
 
+/* ---- Training (Sec. 3.4, Eq. loss) ------------------------------------------
+ * Loss of a batch of problems after K stationary cycles from u = 0,
+ *     r_0 = f,  r_{k+1} = r_k - A B(r_k),   L = (1/N) sum_i ||r_K,i||^2 / ||f_i||^2
+ * (the paper's loss is the K = 1 case of this unrolled form), and its exact
+ * gradient with respect to every weight of the setup and solve networks,
+ * from a hand-written adjoint (reverse sweep over the cycles with per-cycle
+ * checkpointing: only r_k is kept, B's intermediates are recomputed).
+ * coeff[i]: nodal k of problem i, (n[i]+2)^2 doubles; rhs[i]: f, n[i]^2
+ * doubles; host or device.  Problems of equal n are batched together.
+ * Arithmetic: FP64 for an FP64 context, FP32 otherwise (gradients are
+ * accumulated in FP64).  grad (weight_count doubles, host or device) may be
+ * NULL to evaluate the loss only.  Divergence form only.
+ * Errors: STATE (no weights), ARG, SIZE, NONFINITE (zero f or non-finite loss). */
+int mgcnn_loss_grad(mgcnn_ctx* ctx, int nprob, const double* const* coeff, const double* const* rhs,
+                    const int* n, int K, double* loss, double* grad);
+
+/* One Adam update (Kingma & Ba; the paper trains with Adam, Appendix A) of the
+ * context's weights with gradient `grad` (weight_count doubles, host or
+ * device): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  Moments live in
+ * the context and start at zero.  Invalidates the current setup. */
+int mgcnn_adam_step(mgcnn_ctx* ctx, const double* grad, double lr, double beta1, double beta2, double eps);
+
+/* mgcnn_loss_grad followed by mgcnn_adam_step (beta 0.9, 0.999, eps 1e-8)
+ * with the gradient kept on the device; grad may be NULL. */
+int mgcnn_train_step(mgcnn_ctx* ctx, int nprob, const double* const* coeff, const double* const* rhs,
+                     const int* n, int K, double lr, double* loss, double* grad);
+
+/* Copy the context's current weights (layout of mgcnn_weight_count) out. */
+int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
+
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * mgcnn_kernel_launches: kernels launched by this library in this process.
  * mgcnn_profile(ctx, 1): from now on bracket the finest-level launch of each

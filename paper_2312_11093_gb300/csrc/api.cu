@@ -5,10 +5,12 @@
 // arithmetic step runs in this library's kernels; this file only sequences
 // launches, owns device buffers and moves data across the ABI.
 #include <atomic>
+#include <algorithm>
 #include <cmath>
 
 #include "ops.cuh"
 #include "mixed.cuh"
+#include "train.cuh"
 
 using namespace mgcnn;
 
@@ -402,6 +404,7 @@ void mgcnn_destroy(mgcnn_ctx* c) {
   release(c->feat); release(c->f); release(c->u); release(c->r); release(c->e);
   release(c->r32); release(c->partial); release(c->scalars);
   mixed_release(c);
+  train_release(c);
   for (size_t i = 0; i < c->ev_start.size(); ++i) {
     cudaEventDestroy(c->ev_start[i]);
     cudaEventDestroy(c->ev_stop[i]);
@@ -614,6 +617,75 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
     MG_TRY(stage_out_finish(c, u, du, N, host));
     MG_TRY(sync(c));
     return result;
+  }();
+  return finish(c, st);
+}
+
+static Status refresh_weights(mgcnn_ctx* c) {
+  MG_TRY(convert<float>(c->w64.as<double>(), c->w32.as<float>(), c->wl.total, c->stream));
+  MG_TRY(mixed_set_weights(c));
+  return {};
+}
+
+static Status loss_grad_any(mgcnn_ctx* c, int nprob, const double* const* coeff, const double* const* rhs,
+                            const int* n, int K, double* loss, bool want_grad) {
+  if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
+  if (nprob < 1 || K < 1 || K > 64) return make_status(MGCNN_ERR_ARG, "need nprob >= 1 and 1 <= K <= 64");
+  if (c->cfg.pde != MGCNN_PDE_DIV_HARMONIC) return make_status(MGCNN_ERR_ARG, "training supports the divergence form");
+  for (int i = 0; i < nprob; ++i) {
+    if (!coeff[i] || !rhs[i]) return make_status(MGCNN_ERR_ARG, "null problem array %d", i);
+    if (levels_of(n[i]) < 1 || levels_of(n[i]) > kMaxLevels) return make_status(MGCNN_ERR_SIZE, "bad n=%d", n[i]);
+  }
+  if (c->cfg.precision == MGCNN_PREC_FP64) return loss_grad_impl<double>(c, nprob, coeff, rhs, n, K, loss, want_grad);
+  return loss_grad_impl<float>(c, nprob, coeff, rhs, n, K, loss, want_grad);
+}
+
+int mgcnn_loss_grad(mgcnn_ctx* c, int nprob, const double* const* coeff, const double* const* rhs, const int* n,
+                    int K, double* loss, double* grad) {
+  if (!c || !coeff || !rhs || !n || !loss) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(loss_grad_any(c, nprob, coeff, rhs, n, K, loss, grad != nullptr));
+    if (grad) MG_CUDA(cudaMemcpyAsync(grad, c->grad.p, c->wl.total * sizeof(double), cudaMemcpyDefault, c->stream));
+    return sync(c);
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_adam_step(mgcnn_ctx* c, const double* grad, double lr, double beta1, double beta2, double eps) {
+  if (!c || !grad) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
+    const double* dg = nullptr;
+    MG_TRY(stage_in(c, grad, c->wl.total, c->e, &dg));
+    MG_TRY(adam_step(c, dg, lr, beta1, beta2, eps));
+    MG_TRY(refresh_weights(c));
+    c->have_setup = false;  // setup tensors belong to the old weights
+    return sync(c);
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_train_step(mgcnn_ctx* c, int nprob, const double* const* coeff, const double* const* rhs, const int* n,
+                     int K, double lr, double* loss, double* grad) {
+  if (!c || !coeff || !rhs || !n || !loss) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(loss_grad_any(c, nprob, coeff, rhs, n, K, loss, true));
+    if (grad) MG_CUDA(cudaMemcpyAsync(grad, c->grad.p, c->wl.total * sizeof(double), cudaMemcpyDefault, c->stream));
+    MG_TRY(adam_step(c, c->grad.as<double>(), lr, 0.9, 0.999, 1e-8));
+    MG_TRY(refresh_weights(c));
+    c->have_setup = false;
+    return sync(c);
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_get_weights(mgcnn_ctx* c, double* w, size_t count) {
+  if (!c || !w) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
+    if (count != c->wl.total) return make_status(MGCNN_ERR_ARG, "weight count %zu, expected %zu", count, c->wl.total);
+    MG_CUDA(cudaMemcpyAsync(w, c->w64.p, count * sizeof(double), cudaMemcpyDefault, c->stream));
+    return sync(c);
   }();
   return finish(c, st);
 }

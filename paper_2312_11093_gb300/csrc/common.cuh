@@ -18,6 +18,8 @@ namespace mgcnn {
 constexpr int kFeatures = 5;      // setup-network input features per node
 constexpr int kSetupLayers = 4;   // NonLinearResNet depth (Sec. 3.2: "four layers")
 constexpr int kMaxLevels = 13;    // n <= 16383
+constexpr int kMaxSweeps = 16;    // layers per ResNetDown / ResNetUp
+struct TrainGroup;
 
 // Status carried through the library; converted to the ABI code at the boundary.
 struct Status {
@@ -95,6 +97,10 @@ struct mgcnn_ctx {
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
   mgcnn::DevBuf s32tmp;                   // FP32 setup output before the BF16 cast
   mgcnn::DevBuf scalars;                  // device scalars (norms)
+  // training (train.cu)
+  std::vector<mgcnn::TrainGroup> groups;
+  mgcnn::DevBuf grad, wT, adam_m, adam_v;
+  long long adam_t = 0;
   // optional per-kernel timing (mgcnn_profile)
   int prof = 0;
   std::vector<cudaEvent_t> ev_start, ev_stop;

@@ -25,6 +25,12 @@ __global__ void __launch_bounds__(128) conv_same_kernel(ConvArgs<T> a) {
   const int n = a.n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n * n) return;
+  const size_t bi = blockIdx.y;
+  a.x += bi * a.x_bs;
+  if (a.s) a.s += bi * a.s_bs;
+  if (a.skip) a.skip += bi * a.skip_bs;
+  if (a.diag) a.diag += bi * a.diag_bs;
+  a.y += bi * a.y_bs;
   const int j = p / n, i = p - j * n;
   T acc[CO];
 #pragma unroll
@@ -62,6 +68,8 @@ __global__ void __launch_bounds__(128) rcnn_kernel(const T* __restrict__ x, cons
   const int nc = (n - 1) / 2;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nc * nc) return;
+  x += (size_t)blockIdx.y * n * n * C;
+  y += (size_t)blockIdx.y * nc * nc * C;
   const int J = p / nc, I = p - J * nc;
   T acc[C];
 #pragma unroll
@@ -90,6 +98,8 @@ __global__ void __launch_bounds__(128) tcnn_add_kernel(const T* __restrict__ xc,
   const int nc = (n - 1) / 2;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n * n) return;
+  xc += (size_t)blockIdx.y * nc * nc * C;
+  y += (size_t)blockIdx.y * n * n * C;
   const int j = p / n, i = p - j * n;
   T acc[C];
 #pragma unroll
@@ -130,7 +140,7 @@ namespace {
 
 template <typename T, int CI, int CO>
 Status conv_same_launch(const ConvArgs<T>& a, cudaStream_t st) {
-  conv_same_kernel<T, CI, CO><<<grid_for((size_t)a.n * a.n, 128), 128, 0, st>>>(a);
+  conv_same_kernel<T, CI, CO><<<dim3(grid_for((size_t)a.n * a.n, 128), a.batch), 128, 0, st>>>(a);
   MG_LAUNCH("conv_same_kernel");
   return {};
 }
@@ -163,19 +173,19 @@ Status conv_same(int CI, int CO, const ConvArgs<T>& a, cudaStream_t st) {
 }
 
 template <typename T>
-Status rcnn(int C, const T* x, const T* W, T* y, int n_fine, cudaStream_t st) {
+Status rcnn(int C, const T* x, const T* W, T* y, int n_fine, cudaStream_t st, int batch) {
   const int nc = (n_fine - 1) / 2;
   MG_DISPATCH_C(C, {
-    rcnn_kernel<T, CC><<<grid_for((size_t)nc * nc, 128), 128, 0, st>>>(x, W, y, n_fine);
+    rcnn_kernel<T, CC><<<dim3(grid_for((size_t)nc * nc, 128), batch), 128, 0, st>>>(x, W, y, n_fine);
     MG_LAUNCH("rcnn_kernel");
   });
   return {};
 }
 
 template <typename T>
-Status tcnn_add(int C, const T* xc, const T* W, T* y, int n_fine, cudaStream_t st) {
+Status tcnn_add(int C, const T* xc, const T* W, T* y, int n_fine, cudaStream_t st, int batch) {
   MG_DISPATCH_C(C, {
-    tcnn_add_kernel<T, CC><<<grid_for((size_t)n_fine * n_fine, 128), 128, 0, st>>>(xc, W, y, n_fine);
+    tcnn_add_kernel<T, CC><<<dim3(grid_for((size_t)n_fine * n_fine, 128), batch), 128, 0, st>>>(xc, W, y, n_fine);
     MG_LAUNCH("tcnn_add_kernel");
   });
   return {};
@@ -190,10 +200,10 @@ Status convert(const double* src, T* dst, size_t count, cudaStream_t st) {
 
 template Status conv_same<double>(int, int, const ConvArgs<double>&, cudaStream_t);
 template Status conv_same<float>(int, int, const ConvArgs<float>&, cudaStream_t);
-template Status rcnn<double>(int, const double*, const double*, double*, int, cudaStream_t);
-template Status rcnn<float>(int, const float*, const float*, float*, int, cudaStream_t);
-template Status tcnn_add<double>(int, const double*, const double*, double*, int, cudaStream_t);
-template Status tcnn_add<float>(int, const float*, const float*, float*, int, cudaStream_t);
+template Status rcnn<double>(int, const double*, const double*, double*, int, cudaStream_t, int);
+template Status rcnn<float>(int, const float*, const float*, float*, int, cudaStream_t, int);
+template Status tcnn_add<double>(int, const double*, const double*, double*, int, cudaStream_t, int);
+template Status tcnn_add<float>(int, const float*, const float*, float*, int, cudaStream_t, int);
 template Status convert<float>(const double*, float*, size_t, cudaStream_t);
 template Status convert<__nv_bfloat16>(const double*, __nv_bfloat16*, size_t, cudaStream_t);
 

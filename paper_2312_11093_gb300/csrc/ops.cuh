@@ -44,14 +44,19 @@ struct ConvArgs {
   T* y = nullptr;           // output [N][CO]
   int n = 0;                // grid side
   int tanh_act = 0;         // 1: y = tanh(conv + bias) (+ skip)
+  // batch of problems of the same size: blockIdx.y selects the problem and
+  // each pointer advances by its stride (elements; 0 = shared by the batch)
+  int batch = 1;
+  size_t x_bs = 0, s_bs = 0, skip_bs = 0, diag_bs = 0, y_bs = 0;
 };
 
 template <typename T>
 Status conv_same(int CI, int CO, const ConvArgs<T>& a, cudaStream_t st);
+// batch > 1: consecutive problems of the same size, tensors back to back.
 template <typename T>
-Status rcnn(int C, const T* x, const T* W, T* y, int n_fine, cudaStream_t st);
+Status rcnn(int C, const T* x, const T* W, T* y, int n_fine, cudaStream_t st, int batch = 1);
 template <typename T>
-Status tcnn_add(int C, const T* xc, const T* W, T* y, int n_fine, cudaStream_t st);
+Status tcnn_add(int C, const T* xc, const T* W, T* y, int n_fine, cudaStream_t st, int batch = 1);
 template <typename T>
 Status convert(const double* src, T* dst, size_t count, cudaStream_t st);
 bool channels_supported(int C);

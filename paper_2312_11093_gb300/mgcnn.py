@@ -63,6 +63,10 @@ def load() -> ctypes.CDLL:
         "mgcnn_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, dp]),
         "mgcnn_vcycle": (c_int, [c_void_p, c_void_p, c_void_p]),
         "mgcnn_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), c_void_p]),
+        "mgcnn_loss_grad": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, dp, c_void_p]),
+        "mgcnn_adam_step": (c_int, [c_void_p, c_void_p, c_double, c_double, c_double, c_double]),
+        "mgcnn_train_step": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_double, dp, c_void_p]),
+        "mgcnn_get_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
         "mgcnn_kernel_launches": (ctypes.c_longlong, []),
         "mgcnn_profile": (c_int, [c_void_p, c_int]),
         "mgcnn_profile_read": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
@@ -223,6 +227,41 @@ class Solver:
         """Operators + analytic GMG-equivalent setup tensors (needs channels == 13)."""
         self._check(self._L.mgcnn_setup_gmg(self._h, _ptr(coeff), int(n), float(omega)), "mgcnn_setup_gmg")
         self.n = int(n)
+
+    # -- training (Sec. 3.4) ---------------------------------------------------
+    @staticmethod
+    def _problems(problems):
+        """[(k, f, n), ...] -> ctypes arrays of pointers and sizes (arrays are kept alive by the caller)."""
+        m = len(problems)
+        kp = (c_void_p * m)(*[_ptr(k, (n + 2) * (n + 2)) for k, f, n in problems])
+        fp = (c_void_p * m)(*[_ptr(f, n * n) for k, f, n in problems])
+        ns = (c_int * m)(*[int(n) for k, f, n in problems])
+        return m, kp, fp, ns
+
+    def loss_grad(self, problems, K: int, want_grad: bool = True):
+        """Loss after K cycles from u = 0 (mean of ||r_K||^2/||f||^2) and its gradient."""
+        m, kp, fp, ns = self._problems(problems)
+        loss = c_double(0.0)
+        grad = np.zeros(self.weight_count) if want_grad else None
+        self._check(self._L.mgcnn_loss_grad(self._h, m, kp, fp, ns, int(K), ctypes.byref(loss),
+                                            grad.ctypes.data if want_grad else None), "mgcnn_loss_grad")
+        return loss.value, grad
+
+    def adam_step(self, grad, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        self._check(self._L.mgcnn_adam_step(self._h, _ptr(grad, self.weight_count), lr, beta1, beta2, eps),
+                    "mgcnn_adam_step")
+
+    def train_step(self, problems, K: int, lr: float) -> float:
+        m, kp, fp, ns = self._problems(problems)
+        loss = c_double(0.0)
+        self._check(self._L.mgcnn_train_step(self._h, m, kp, fp, ns, int(K), float(lr), ctypes.byref(loss), None),
+                    "mgcnn_train_step")
+        return loss.value
+
+    def get_weights(self) -> np.ndarray:
+        w = np.empty(self.weight_count)
+        self._check(self._L.mgcnn_get_weights(self._h, w.ctypes.data, w.size), "mgcnn_get_weights")
+        return w
 
     PROFILE_KINDS = ("residual", "resnet", "restrict", "prolong", "in", "out")
 

@@ -1,0 +1,124 @@
+"""GPU training path: the hand-written CUDA adjoint against the FP64 oracle adjoint,
+central finite differences, the FP32 variant, Adam and the autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint as oadj
+from oracle import mgcnn as omg
+from oracle import operator as oop
+from oracle.grid import num_levels
+from paper_2312_11093_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2312_11093_gb300 import build
+    build.build()
+    from paper_2312_11093_gb300 import mgcnn
+    mgcnn.load()
+    return mgcnn
+
+
+def _problems(sizes, seed, b=(1.0, 0.5)):
+    rng = np.random.default_rng(seed)
+    gpu, ora = [], []
+    for n in sizes:
+        k = inputs.lognormal_k(n, 0.1, rng)
+        f = inputs.normal_rhs(n, rng)
+        gpu.append((np.ascontiguousarray(k.ravel()), np.ascontiguousarray(f.ravel()), n))
+        ora.append((oop.level_stencils_div(k, b, num_levels(n)), f))
+    return gpu, ora
+
+
+def _solver(M, w, C, nd, nu, precision="fp64"):
+    sv = M.Solver(C, nd, nu, precision=precision)
+    sv.set_weights(M.pack_weights(w, C, nd, nu))
+    return sv
+
+
+@pytest.mark.parametrize("C,nd,nu,K", [(4, 1, 2, 2), (8, 1, 1, 3)])
+def test_loss_and_gradient_match_oracle_adjoint(M, C, nd, nu, K):
+    gpu, ora = _problems([7, 15, 15, 7, 31], 1)
+    w = omg.random_weights(C, nd, nu, np.random.default_rng(2), scale=0.5)
+    L_ref, g_ref = oadj.loss_and_grad(w, ora, K)
+    sv = _solver(M, w, C, nd, nu)
+    L, g = sv.loss_grad(gpu, K)
+    assert abs(L - L_ref) <= 1e-12 * abs(L_ref)
+    g_ref_blob = M.pack_weights(g_ref, C, nd, nu)
+    assert np.linalg.norm(g - g_ref_blob) <= 1e-10 * np.linalg.norm(g_ref_blob)
+
+
+def test_central_differences_on_gpu_loss(M):
+    """eps = 1e-6 max(1, |theta|); relative error <= 1e-6 (FP64)."""
+    C, nd, nu, K = 4, 1, 1, 2
+    gpu, _ = _problems([15, 31], 3)
+    w = omg.random_weights(C, nd, nu, np.random.default_rng(4), scale=0.5)
+    blob = M.pack_weights(w, C, nd, nu)
+    sv = M.Solver(C, nd, nu, precision="fp64")
+    sv.set_weights(blob)
+    L0, g = sv.loss_grad(gpu, K)
+    rng = np.random.default_rng(5)
+    idx = rng.choice(blob.size, size=24, replace=False)
+    for i in idx:
+        eps = 1e-6 * max(1.0, abs(blob[i]))
+        wp, wm = blob.copy(), blob.copy()
+        wp[i] += eps
+        wm[i] -= eps
+        sv.set_weights(wp)
+        lp, _ = sv.loss_grad(gpu, K, want_grad=False)
+        sv.set_weights(wm)
+        lm, _ = sv.loss_grad(gpu, K, want_grad=False)
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), 1e-3 * abs(L0)), (i, fd, g[i])
+
+
+def test_fp32_adjoint_close_to_fp64(M):
+    C, nd, nu, K = 8, 1, 1, 4
+    gpu, _ = _problems([31, 63, 31], 6)
+    w = omg.random_weights(C, nd, nu, np.random.default_rng(7), scale=0.5)
+    L64, g64 = _solver(M, w, C, nd, nu, "fp64").loss_grad(gpu, K)
+    L32, g32 = _solver(M, w, C, nd, nu, "mixed_bf16").loss_grad(gpu, K)
+    assert abs(L32 - L64) <= 1e-4 * abs(L64)
+    assert np.linalg.norm(g32 - g64) <= 1e-3 * np.linalg.norm(g64)
+
+
+def test_adam_first_step_closed_form(M):
+    """From zero moments, one Adam step moves each weight by -lr g / (|g| + eps)."""
+    C = 4
+    w = omg.random_weights(C, 1, 1, np.random.default_rng(8))
+    blob = M.pack_weights(w, C, 1, 1)
+    sv = M.Solver(C, 1, 1)
+    sv.set_weights(blob)
+    g = np.random.default_rng(9).standard_normal(blob.size)
+    g[:5] = 0.0
+    sv.adam_step(g, 1e-3, 0.9, 0.999, 1e-8)
+    np.testing.assert_allclose(sv.get_weights(), blob - 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+def test_autograd_function_uses_cuda_adjoint(M):
+    from paper_2312_11093_gb300.train import _autograd
+    C = 4
+    gpu, _ = _problems([15, 15], 10)
+    w = omg.random_weights(C, 1, 1, np.random.default_rng(11), scale=0.5)
+    blob = M.pack_weights(w, C, 1, 1)
+    sv = M.Solver(C, 1, 1)
+    wt = torch.tensor(blob, requires_grad=True)
+    loss = _autograd().apply(wt, sv, gpu, 2)
+    (3.0 * loss).backward()
+    sv.set_weights(blob)
+    L, g = sv.loss_grad(gpu, 2)
+    assert abs(loss.item() - L) <= 1e-14 * abs(L)
+    np.testing.assert_allclose(wt.grad.numpy(), 3.0 * g, rtol=1e-13, atol=0)
+
+
+def test_training_steps_reduce_loss(M):
+    from paper_2312_11093_gb300.train import init_weights, make_batch
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(init_weights(8, 1, 1, np.random.default_rng(0)))
+    losses = [sv.train_step(make_batch(s, sizes=(31,), per_size=8), 4, 3e-3) for s in range(40)]
+    assert np.mean(losses[-5:]) < 0.7 * np.mean(losses[:5])
