@@ -123,6 +123,9 @@ def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
         "prolong": 4.5 * cp * N,                 # fine y in/out, coarse x in
         "in": (4.0 + 2.0 * cp) * N,              # FP32 r in, BF16 x out
         "out": (2.0 * cp + 16.0) * N,            # BF16 x in, FP64 u in/out
+        # fused level kernels at the finest level (8 channels):
+        "down0": (4.0 + 2.0 * cp + 2.0 * cp + 0.5 * cp) * N,  # r (FP32), s in; x_down, coarse x out
+        "up0": (2.0 * cp + 2.0 * cp + 0.5 * cp + 16.0) * N,   # x_down, s, coarse x, u in; u out
     }[kind]
 
 
@@ -340,7 +343,8 @@ def main():
     peak = float(peaks["hbm_gbs"])
     achieved = algorithmic_bytes(dom, n, cp) / (dom_ms / dom_cnt * 1e-3) / 1e9 if dom_cnt else None
     kname = {"residual": "residual_kernel", "resnet": "resnet_mma_kernel", "restrict": "rcnn_mma_kernel",
-             "prolong": "tcnn_add_kernel16", "in": "in_kernel16", "out": "out_kernel16"}[dom]
+             "prolong": "tcnn_add_kernel16", "in": "in_kernel16", "out": "out_kernel16",
+             "down0": "down_kernel", "up0": "up_kernel"}[dom]
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "traffic": traffic_record(kname, f"{workload}_{n}"),

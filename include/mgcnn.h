@@ -218,6 +218,15 @@ int mgcnn_train_step(mgcnn_ctx* ctx, int nprob, const double* const* coeff, cons
 /* Copy the context's current weights (layout of mgcnn_weight_count) out. */
 int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
 
+/* Implementation options (no counterpart in the paper).
+ * MGCNN_OPT_FUSED (default 1): in MIXED_BF16 mode with 8 channels and one
+ * layer per ResNet, run each level of the V-cycle as two fused kernels (down:
+ * [reChannel-in] + ResNetDown + RCNN; up: TCNN-add + ResNetUp [+ reChannel-out
+ * and the FP64 update]); 0 runs one kernel per layer.  Both compute the same
+ * function; roundings to BF16 happen at different points. */
+enum { MGCNN_OPT_FUSED = 1 };
+int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
+
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * mgcnn_kernel_launches: kernels launched by this library in this process.
  * mgcnn_profile(ctx, 1): from now on bracket the finest-level launch of each
@@ -225,7 +234,7 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * returns, per class, the summed milliseconds and the number of launches
  * since the last read (classes: 0 residual, 1 ResNet layer, 2 restriction,
  * 3 prolongation-add into the finest level, 4 reChannel-in, 5 reChannel-out
- * with update) and clears them.  Timing adds one event pair per bracketed
+ * with update, 6 fused down kernel, 7 fused up kernel) and clears them.  Timing adds one event pair per bracketed
  * launch. */
 long long mgcnn_kernel_launches(void);
 int mgcnn_profile(mgcnn_ctx* ctx, int enable);

@@ -690,6 +690,17 @@ int mgcnn_get_weights(mgcnn_ctx* c, double* w, size_t count) {
   return finish(c, st);
 }
 
+int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
+  if (!c) return MGCNN_ERR_ARG;
+  switch (option) {
+    case MGCNN_OPT_FUSED:
+      c->fused = value ? 1 : 0;
+      return finish(c, {});
+    default:
+      return finish(c, make_status(MGCNN_ERR_ARG, "unknown option %d", option));
+  }
+}
+
 long long mgcnn_kernel_launches(void) { return g_launches.load(); }
 
 int mgcnn_profile(mgcnn_ctx* c, int enable) {

@@ -92,6 +92,7 @@ struct mgcnn_ctx {
   mgcnn::DevBuf partial;                  // per-block partial sums of reductions
   // mixed-precision path (mixed.cu)
   int cp = 0;                             // channels padded for the tensor cores (8 or 16)
+  int fused = 1;                          // use the fused level kernels when they apply
   mgcnn::DevBuf x16a[mgcnn::kMaxLevels];  // BF16 state ping-pong, [n_l^2][cp]
   mgcnn::DevBuf x16b[mgcnn::kMaxLevels];
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
@@ -134,7 +135,7 @@ void count_launch();
 
 // Profiling kinds: finest-level launches bracketed by events when enabled.
 enum ProfKind { kProfResidual = 0, kProfResnet = 1, kProfRestrict = 2, kProfProlong = 3, kProfIn = 4,
-                kProfOut = 5, kProfKinds = 6 };
+                kProfOut = 5, kProfDown0 = 6, kProfUp0 = 7, kProfKinds = 8 };
 int prof_begin(mgcnn_ctx* c, int kind);   // -1 when profiling is off
 void prof_end(mgcnn_ctx* c, int slot);
 

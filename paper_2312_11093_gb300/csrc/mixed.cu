@@ -394,6 +394,8 @@ Status vcycle_cp(mgcnn_ctx* c, const float* r32, const double* norm2, double* e,
   const float* w_in = reinterpret_cast<const float*>(wb + ml.w_in);
   const float* w_out = reinterpret_cast<const float*>(wb + ml.w_out);
   const float* w_P = reinterpret_cast<const float*>(wb + ml.w_P);
+  if (CP == 8 && c->fused && fused_supported(c))
+    return vcycle_fused_cp8(c, r32, norm2, e, u_skip, f_down, f_up, f_R, w_in, w_out, w_P);
   bf16* x[kMaxLevels];
   bf16* t[kMaxLevels];
   for (int l = 0; l < c->L; ++l) {

@@ -1,0 +1,409 @@
+// Fused level kernels of the mixed-precision solve phase for 8 channels
+// (one 16-byte BF16 vector per pixel) and one layer per ResNetDown/Up, the
+// configuration of the paper's experiments (Sec. 4.1: sweeps = 1, C = 8).
+//
+// Down kernel, level l (Algorithm 3, down loop):
+//   [finest level: x_1 = alpha W_in * r, FP32 CUDA cores]
+//   x_l <- x_l + K_down (s_l * x_l)            tensor cores (implicit GEMM)
+//   x_{l+1} = RCNN(x_l)                        tensor cores, stride 2
+// One block owns a 16 x 32 fine tile and the 8 x 16 coarse tile under it.
+// The restriction needs one extra fine row and column, which the block
+// recomputes (17 x 33 layer outputs) instead of reading a neighbour's.
+//
+// Up kernel, level l (Algorithm 3, up loop):
+//   x_l <- x_l + TCNN(x_{l+1})                 FP32 CUDA cores (2.25 taps per pixel)
+//   x_l <- x_l + K_up (s_l * x_l)              tensor cores
+//   [finest level: e = W_out * x_1 / alpha, u <- u + e in FP64]
+// One block owns a 16 x 32 fine tile, with a 1-pixel halo of the layer input
+// (2 at the finest level, where W_out needs the layer output's halo).
+//
+// Tensor-core tiling: a warp computes 16 output pixels x 8 channels with
+// mma.m16n8k16 (+ one m16n8k8 for the ninth tap), A rows fetched by ldmatrix
+// from per-lane shared-memory addresses, so a strip can be any 16 pixels of
+// an odd-sized region.
+#include <cmath>
+
+#include "mixed.cuh"
+#include "ops.cuh"
+
+namespace mgcnn {
+
+using bf16 = __nv_bfloat16;
+using bf162 = __nv_bfloat162;
+
+namespace {
+
+constexpr int FH = 16, FW = 32;      // fine tile owned by a block
+constexpr int NT = 256;              // threads per block (8 warps)
+constexpr int NW = NT / 32;
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t* r, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma1688(float* d, uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a0), "r"(a1), "r"(b0));
+}
+
+__device__ __forceinline__ float2 bf2f(uint32_t v) { return __bfloat1622float2(*reinterpret_cast<bf162*>(&v)); }
+__device__ __forceinline__ uint32_t f2bf(float a, float b) {
+  bf162 r = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&r);
+}
+__device__ __forceinline__ uint4 mul8(uint4 a, uint4 b) {
+  float2 x, y;
+  uint4 o;
+  x = bf2f(a.x); y = bf2f(b.x); o.x = f2bf(x.x * y.x, x.y * y.y);
+  x = bf2f(a.y); y = bf2f(b.y); o.y = f2bf(x.x * y.x, x.y * y.y);
+  x = bf2f(a.z); y = bf2f(b.z); o.z = f2bf(x.x * y.x, x.y * y.y);
+  x = bf2f(a.w); y = bf2f(b.w); o.w = f2bf(x.x * y.x, x.y * y.y);
+  return o;
+}
+
+// 16 pixels x 8 channels of a 3x3 conv; pix(m, tap) = shared pixel index of
+// A row m for tap (each pixel is one uint4 of 8 BF16 channels).
+template <typename Pix>
+__device__ __forceinline__ void strip_conv(const uint4* tile, const uint32_t* wf, Pix pix, float* acc) {
+  const int lane = threadIdx.x & 31;
+  const int m = (lane & 7) + ((lane >> 3) & 1) * 8;
+  const int kh = lane >> 4;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    uint32_t a[4];
+    ldsm_x4(a, tile + pix(m, 2 * s + kh));
+    mma16816(acc, a, wf[2 * s], wf[2 * s + 1]);
+  }
+  uint32_t a[2];
+  ldsm_x2(a, tile + pix(lane & 15, 8));
+  mma1688(acc, a[0], a[1], wf[8]);
+}
+
+__device__ __forceinline__ double alpha_of(const double* norm2, size_t N) {
+  const double v = *norm2;
+  return (v > 0.0) ? sqrt((double)N / v) : 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Down kernel.  Regions, in fine coordinates relative to (j0, i0) = (2 J0, 2 I0):
+//   X (layer output kept):   rows 0..XH-1, cols 0..XW-1 (XH = 16 + R, XW = 32 + R)
+//   Z (layer input, halo 1): rows -1..XH,  cols -1..XW
+//   Rg (residual, halo 2):   rows -2..XH+1, cols -2..XW+1   (finest level only)
+template <bool FIRST, bool HAS_R>
+__global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, const double* __restrict__ norm2,
+                                                  const float* __restrict__ w_in, const bf16* __restrict__ x0,
+                                                  const bf16* __restrict__ s, const uint32_t* __restrict__ fK,
+                                                  const uint32_t* __restrict__ fR, bf16* __restrict__ xdown,
+                                                  bf16* __restrict__ xc, int n) {
+  constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
+  constexpr int ZH = XH + 2, ZW = XW + 2;
+  constexpr int RH = ZH + 2, RW = ZW + 2;
+  __shared__ __align__(16) uint4 zs[ZH * ZW];   // s * x_in (BF16)
+  __shared__ __align__(16) uint4 xs[ZH * ZW];   // x_in (BF16), for the skip
+  __shared__ __align__(16) uint4 xd[XH * XW];   // layer output
+  __shared__ float rs[FIRST ? RH * RW : 1];
+  __shared__ float wi[FIRST ? 72 : 1];
+  const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t N = (size_t)n * n;
+
+  uint32_t wk[9], wr[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    wk[k] = fK[k * 32 + lane];
+    if (HAS_R) wr[k] = fR[k * 32 + lane];
+  }
+
+  if constexpr (FIRST) {
+    const float alpha = (float)alpha_of(norm2, N);
+    for (int e = threadIdx.x; e < 72; e += NT) wi[e] = w_in[e];
+    for (int e = threadIdx.x; e < RH * RW; e += NT) {
+      const int rr = e / RW, cc = e - rr * RW;
+      const int gj = j0 + rr - 2, gi = i0 + cc - 2;
+      rs[e] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? alpha * r[(size_t)gj * n + gi] : 0.f;
+    }
+    __syncthreads();
+    // x_in = W_in * (alpha r) on Z, rounded to BF16 (zero outside the grid)
+    for (int e = threadIdx.x; e < ZH * ZW; e += NT) {
+      const int zr = e / ZW, zc = e - zr * ZW;
+      const int gj = j0 + zr - 1, gi = i0 + zc - 1;
+      uint4 xv = make_uint4(0, 0, 0, 0), zv = xv;
+      if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
+        float rv[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) rv[t] = rs[(zr + t / 3) * RW + zc + t % 3];
+        float o[8];
+#pragma unroll
+        for (int co = 0; co < 8; ++co) {
+          float a = 0.f;
+#pragma unroll
+          for (int t = 0; t < 9; ++t) a += wi[co * 9 + t] * rv[t];
+          o[co] = a;
+        }
+        xv = make_uint4(f2bf(o[0], o[1]), f2bf(o[2], o[3]), f2bf(o[4], o[5]), f2bf(o[6], o[7]));
+        zv = mul8(xv, reinterpret_cast<const uint4*>(s)[(size_t)gj * n + gi]);
+      }
+      xs[e] = xv;
+      zs[e] = zv;
+    }
+  } else {
+    for (int e = threadIdx.x; e < ZH * ZW; e += NT) {
+      const int zr = e / ZW, zc = e - zr * ZW;
+      const int gj = j0 + zr - 1, gi = i0 + zc - 1;
+      uint4 xv = make_uint4(0, 0, 0, 0), zv = xv;
+      if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
+        const size_t q = (size_t)gj * n + gi;
+        xv = reinterpret_cast<const uint4*>(x0)[q];
+        zv = mul8(xv, reinterpret_cast<const uint4*>(s)[q]);
+      }
+      xs[e] = xv;
+      zs[e] = zv;
+    }
+  }
+  __syncthreads();
+
+  // layer: X = x_in + K (s * x_in), strips of 16 pixels over X in row-major order
+  const int g = lane >> 2, q = lane & 3;
+  constexpr int NSTRIP = (XH * XW + 15) / 16;
+  for (int st = warp; st < NSTRIP; st += NW) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    strip_conv(zs, wk, [&](int m, int tap) {
+      int p = st * 16 + m;
+      p = p < XH * XW ? p : XH * XW - 1;
+      const int xr = p / XW, xc_ = p - xr * XW;
+      return (xr + tap / 3) * ZW + xc_ + tap % 3;
+    }, acc);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = st * 16 + g + 8 * h;
+      if (p >= XH * XW) continue;
+      const int xr = p / XW, xcol = p - xr * XW;
+      const int zi = (xr + 1) * ZW + xcol + 1;
+      const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&xs[zi])[q]);
+      const uint32_t o = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
+      reinterpret_cast<uint32_t*>(&xd[p])[q] = o;
+      const int gj = j0 + xr, gi = i0 + xcol;
+      if (xr < FH && xcol < FW && gj < n && gi < n)
+        reinterpret_cast<uint32_t*>(xdown + ((size_t)gj * n + gi) * 8)[q] = o;
+    }
+  }
+  if constexpr (HAS_R) {
+    __syncthreads();
+    // restriction: coarse (J0 + r, I0 + c), r < 8, c < 16, taps (2r + a, 2c + b) of X
+    const int nc = (n - 1) / 2;
+    const int J0 = blockIdx.y * (FH / 2), I0 = blockIdx.x * (FW / 2);
+    for (int st = warp; st < 8; st += NW) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      strip_conv(xd, wr, [&](int m, int tap) { return (2 * st + tap / 3) * XW + 2 * m + tap % 3; }, acc);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int J = J0 + st, I = I0 + g + 8 * h;
+        if (J < nc && I < nc)
+          reinterpret_cast<uint32_t*>(xc + ((size_t)J * nc + I) * 8)[q] = f2bf(acc[2 * h], acc[2 * h + 1]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Up kernel.  Output tile 16 x 32 at (j0, i0).  H = halo of the layer output
+// that is needed (1 at the finest level for W_out, else 0).
+//   O (layer output):  rows -H..15+H, cols -H..31+H        (OH x OW)
+//   P (layer input x_pre = x_down + TCNN(x_c)): O plus halo 1  (PH x PW)
+//   coarse rows/cols J: floor((j0 - H - 1) / 2) - 1 .. , enough for P
+template <bool LAST, bool HAS_P>
+__global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, const bf16* __restrict__ xcf,
+                                                const float* __restrict__ wP, const bf16* __restrict__ s,
+                                                const uint32_t* __restrict__ fK, const float* __restrict__ w_out,
+                                                const double* __restrict__ norm2, const double* __restrict__ u_in,
+                                                bf16* __restrict__ xfin, double* __restrict__ u_out, int n) {
+  constexpr int H = LAST ? 1 : 0;
+  constexpr int OH = FH + 2 * H, OW = FW + 2 * H;
+  constexpr int PH = OH + 2, PW = OW + 2;
+  constexpr int CH = PH / 2 + 2, CW = PW / 2 + 2;   // coarse rows / cols staged
+  __shared__ __align__(16) uint4 ps[PH * PW];       // x_pre
+  __shared__ __align__(16) uint4 zs[PH * PW];       // s * x_pre
+  __shared__ __align__(16) uint4 os[LAST ? OH * OW : 1];
+  __shared__ __align__(16) uint4 cs[HAS_P ? CH * CW : 1];
+  __shared__ float wp[HAS_P ? 8 * 8 * 9 : 1];
+  __shared__ float wo[LAST ? 72 : 1];
+  const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
+  const int pj0 = j0 - H - 1, pi0 = i0 - H - 1;      // global coords of P's corner
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nc = (n - 1) / 2;
+  // coarse corner: the smallest J with 2J + 2 >= pj0
+  const int cj0 = (pj0 - 2 >= 0) ? (pj0 - 2) / 2 : -((2 - pj0 + 1) / 2);
+  const int ci0 = (pi0 - 2 >= 0) ? (pi0 - 2) / 2 : -((2 - pi0 + 1) / 2);
+
+  uint32_t wk[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) wk[k] = fK[k * 32 + lane];
+  if constexpr (HAS_P) {
+    for (int e = threadIdx.x; e < 8 * 8 * 9; e += NT) wp[e] = wP[e];
+    for (int e = threadIdx.x; e < CH * CW; e += NT) {
+      const int cr = e / CW, cc = e - cr * CW;
+      const int J = cj0 + cr, I = ci0 + cc;
+      cs[e] = (J >= 0 && J < nc && I >= 0 && I < nc) ? reinterpret_cast<const uint4*>(xcf)[(size_t)J * nc + I]
+                                                     : make_uint4(0, 0, 0, 0);
+    }
+  }
+  if constexpr (LAST)
+    for (int e = threadIdx.x; e < 72; e += NT) wo[e] = w_out[e];
+  __syncthreads();
+
+  // x_pre on P
+  for (int e = threadIdx.x; e < PH * PW; e += NT) {
+    const int pr = e / PW, pc = e - pr * PW;
+    const int gj = pj0 + pr, gi = pi0 + pc;
+    uint4 xv = make_uint4(0, 0, 0, 0), zv = xv;
+    if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
+      const size_t qg = (size_t)gj * n + gi;
+      xv = reinterpret_cast<const uint4*>(xdown)[qg];
+      if constexpr (HAS_P) {
+        float acc[8];
+        const float2 a0 = bf2f(xv.x), a1 = bf2f(xv.y), a2 = bf2f(xv.z), a3 = bf2f(xv.w);
+        acc[0] = a0.x; acc[1] = a0.y; acc[2] = a1.x; acc[3] = a1.y;
+        acc[4] = a2.x; acc[5] = a2.y; acc[6] = a3.x; acc[7] = a3.y;
+        for (int ta = 0; ta < 3; ++ta) {
+          const int dj = gj - ta;
+          if (dj < 0 || (dj & 1) || (dj >> 1) >= nc) continue;
+          for (int tb = 0; tb < 3; ++tb) {
+            const int di = gi - tb;
+            if (di < 0 || (di & 1) || (di >> 1) >= nc) continue;
+            const uint4 cv = cs[((dj >> 1) - cj0) * CW + (di >> 1) - ci0];
+            const int tap = ta * 3 + tb;
+            float xin[8];
+            const float2 b0 = bf2f(cv.x), b1 = bf2f(cv.y), b2 = bf2f(cv.z), b3 = bf2f(cv.w);
+            xin[0] = b0.x; xin[1] = b0.y; xin[2] = b1.x; xin[3] = b1.y;
+            xin[4] = b2.x; xin[5] = b2.y; xin[6] = b3.x; xin[7] = b3.y;
+#pragma unroll
+            for (int ci = 0; ci < 8; ++ci)
+#pragma unroll
+              for (int co = 0; co < 8; ++co) acc[co] += wp[(ci * 8 + co) * 9 + tap] * xin[ci];
+          }
+        }
+        xv = make_uint4(f2bf(acc[0], acc[1]), f2bf(acc[2], acc[3]), f2bf(acc[4], acc[5]), f2bf(acc[6], acc[7]));
+      }
+      zv = mul8(xv, reinterpret_cast<const uint4*>(s)[qg]);
+    }
+    ps[e] = xv;
+    zs[e] = zv;
+  }
+  __syncthreads();
+
+  // layer on O
+  const int g = lane >> 2, q = lane & 3;
+  constexpr int NSTRIP = (OH * OW + 15) / 16;
+  for (int st = warp; st < NSTRIP; st += NW) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    strip_conv(zs, wk, [&](int m, int tap) {
+      int p = st * 16 + m;
+      p = p < OH * OW ? p : OH * OW - 1;
+      const int orow = p / OW, ocol = p - orow * OW;
+      return (orow + tap / 3) * PW + ocol + tap % 3;
+    }, acc);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = st * 16 + g + 8 * h;
+      if (p >= OH * OW) continue;
+      const int orow = p / OW, ocol = p - orow * OW;
+      const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&ps[(orow + 1) * PW + ocol + 1])[q]);
+      const uint32_t o = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
+      const int gj = j0 - H + orow, gi = i0 - H + ocol;
+      if constexpr (LAST) {
+        // zero outside the grid: W_out's zero padding
+        reinterpret_cast<uint32_t*>(&os[p])[q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? o : 0u;
+      } else {
+        if (gj < n && gi < n) reinterpret_cast<uint32_t*>(xfin + ((size_t)gj * n + gi) * 8)[q] = o;
+      }
+    }
+  }
+  if constexpr (LAST) {
+    __syncthreads();
+    const double inv_alpha = 1.0 / alpha_of(norm2, (size_t)n * n);
+    for (int e = threadIdx.x; e < FH * FW; e += NT) {
+      const int rr = e / FW, cc = e - rr * FW;
+      const int gj = j0 + rr, gi = i0 + cc;
+      if (gj >= n || gi >= n) continue;
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const uint4 v = os[(rr + t / 3) * OW + cc + t % 3];
+        const float2 a0 = bf2f(v.x), a1 = bf2f(v.y), a2 = bf2f(v.z), a3 = bf2f(v.w);
+        acc += wo[0 * 9 + t] * a0.x + wo[1 * 9 + t] * a0.y + wo[2 * 9 + t] * a1.x + wo[3 * 9 + t] * a1.y +
+               wo[4 * 9 + t] * a2.x + wo[5 * 9 + t] * a2.y + wo[6 * 9 + t] * a3.x + wo[7 * 9 + t] * a3.y;
+      }
+      const size_t qg = (size_t)gj * n + gi;
+      const double ev = (double)acc * inv_alpha;
+      u_out[qg] = (u_in ? u_in[qg] : 0.0) + ev;
+    }
+  }
+}
+
+}  // namespace
+
+bool fused_supported(const mgcnn_ctx* c) {
+  return c->cp == 8 && c->wl.nu_d == 1 && c->wl.nu_u == 1;
+}
+
+// e = B r (u_skip == nullptr) or e = u_skip + B r, fused level kernels, CP = 8.
+Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
+                        const uint32_t* f_down, const uint32_t* f_up, const uint32_t* f_R, const float* w_in,
+                        const float* w_out, const float* w_P) {
+  cudaStream_t st = c->stream;
+  const int L = c->L;
+  // x_down[l] in x16a[l]; x_in[l] (l >= 1) and then x_fin[l] in x16b[l]
+  auto xa = [&](int l) { return c->x16a[l].as<bf16>(); };
+  auto xb = [&](int l) { return c->x16b[l].as<bf16>(); };
+  auto grid_f = [&](int l) { return dim3((c->lv[l].n + FW - 1) / FW, (c->lv[l].n + FH - 1) / FH); };
+  for (int l = 0; l < L; ++l) {
+    const int nl = c->lv[l].n;
+    const bool first = l == 0, has_r = l + 1 < L;
+    const bf16* s = c->s16[l].as<bf16>();
+    bf16* xc = has_r ? xb(l + 1) : nullptr;
+    const int ps = first ? prof_begin(c, kProfDown0) : -1;
+    if (first && has_r)
+      down_kernel<true, true><<<grid_f(l), NT, 0, st>>>(r32, norm2, w_in, nullptr, s, f_down, f_R, xa(l), xc, nl);
+    else if (first)
+      down_kernel<true, false><<<grid_f(l), NT, 0, st>>>(r32, norm2, w_in, nullptr, s, f_down, f_R, xa(l), xc, nl);
+    else if (has_r)
+      down_kernel<false, true><<<grid_f(l), NT, 0, st>>>(r32, norm2, w_in, xb(l), s, f_down, f_R, xa(l), xc, nl);
+    else
+      down_kernel<false, false><<<grid_f(l), NT, 0, st>>>(r32, norm2, w_in, xb(l), s, f_down, f_R, xa(l), xc, nl);
+    MG_LAUNCH("down_kernel");
+    prof_end(c, ps);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const int nl = c->lv[l].n;
+    const bool last = l == 0, has_p = l + 1 < L;
+    const bf16* s = c->s16[l].as<bf16>();
+    const bf16* xcf = has_p ? xb(l + 1) : nullptr;
+    const int ps = last ? prof_begin(c, kProfUp0) : -1;
+    if (last && has_p)
+      up_kernel<true, true><<<grid_f(l), NT, 0, st>>>(xa(l), xcf, w_P, s, f_up, w_out, norm2, u_skip, nullptr, e, nl);
+    else if (last)
+      up_kernel<true, false><<<grid_f(l), NT, 0, st>>>(xa(l), xcf, w_P, s, f_up, w_out, norm2, u_skip, nullptr, e, nl);
+    else if (has_p)
+      up_kernel<false, true><<<grid_f(l), NT, 0, st>>>(xa(l), xcf, w_P, s, f_up, w_out, norm2, u_skip, xb(l), e, nl);
+    else
+      up_kernel<false, false><<<grid_f(l), NT, 0, st>>>(xa(l), xcf, w_P, s, f_up, w_out, norm2, u_skip, xb(l), e, nl);
+    MG_LAUNCH("up_kernel");
+    prof_end(c, ps);
+  }
+  return {};
+}
+
+}  // namespace mgcnn

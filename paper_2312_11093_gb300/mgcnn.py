@@ -67,6 +67,7 @@ def load() -> ctypes.CDLL:
         "mgcnn_adam_step": (c_int, [c_void_p, c_void_p, c_double, c_double, c_double, c_double]),
         "mgcnn_train_step": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_double, dp, c_void_p]),
         "mgcnn_get_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
+        "mgcnn_set_option": (c_int, [c_void_p, c_int, c_int]),
         "mgcnn_kernel_launches": (ctypes.c_longlong, []),
         "mgcnn_profile": (c_int, [c_void_p, c_int]),
         "mgcnn_profile_read": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
@@ -263,7 +264,11 @@ class Solver:
         self._check(self._L.mgcnn_get_weights(self._h, w.ctypes.data, w.size), "mgcnn_get_weights")
         return w
 
-    PROFILE_KINDS = ("residual", "resnet", "restrict", "prolong", "in", "out")
+    PROFILE_KINDS = ("residual", "resnet", "restrict", "prolong", "in", "out", "down0", "up0")
+    OPT_FUSED = 1
+
+    def set_option(self, option: int, value: int):
+        self._check(self._L.mgcnn_set_option(self._h, int(option), int(value)), "mgcnn_set_option")
 
     def profile(self, enable: bool = True):
         self._check(self._L.mgcnn_profile(self._h, int(enable)), "mgcnn_profile")

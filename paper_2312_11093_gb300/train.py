@@ -50,20 +50,33 @@ def _autograd():
     return MGCNNLoss
 
 
-def init_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, scale: float = 0.1) -> np.ndarray:
-    """Random initial weights (uniform, fan-in scaled like PyTorch's default), with
-    the output layer shrunk so that the initial B is small and the unrolled
-    cycles start from a loss near 1."""
+def init_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, out_scale: float = 0.3) -> np.ndarray:
+    """Random initial weights (uniform, fan-in scaled like PyTorch's default) arranged
+    so that the initial B is small: every path from rhs to solution must pass through
+    at least one s-scaled convolution (s ~ 1/a_C carries the units of A^{-1}).
+
+    The skip connections of Eq. heteroresnet and the transfers are unscaled, so with
+    unstructured weights B contains an O(1) multiple of the identity and A B ~ a_C
+    blows the unrolled cycles up.  reChannel-in writes the first half of the
+    channels, reChannel-out reads the second half, and RCNN / TCNN start
+    block-diagonal on the two halves: only the ResNet layers move a signal from
+    the first half to the second."""
     F, S = mgcnn.FEATURES, mgcnn.SETUP_LAYERS
+    h = C // 2
 
     def u(*shape, fan):
         b = 1.0 / np.sqrt(fan)
         return rng.uniform(-b, b, size=shape)
     w = {"w_in": u(C, 1, 3, 3, fan=9), "w_down": u(nu_d, C, C, 3, 3, fan=9 * C),
          "w_up": u(nu_u, C, C, 3, 3, fan=9 * C), "w_R": u(C, C, 3, 3, fan=9 * C),
-         "w_P": u(C, C, 3, 3, fan=9 * C), "w_out": scale * u(1, C, 3, 3, fan=9 * C),
+         "w_P": u(C, C, 3, 3, fan=9 * C), "w_out": out_scale * u(1, C, 3, 3, fan=9 * C),
          "sw_in": u(C, F, 3, 3, fan=9 * F), "sb_in": u(C, fan=9 * F),
          "sw": u(S, C, C, 3, 3, fan=9 * C), "sb": u(S, C, fan=9 * C), "sw_R": u(C, C, 3, 3, fan=9 * C)}
+    w["w_in"][h:] = 0.0
+    w["w_out"][:, :h] = 0.0
+    for key in ("w_R", "w_P"):
+        w[key][:h, h:] = 0.0
+        w[key][h:, :h] = 0.0
     return mgcnn.pack_weights(w, C, nu_d, nu_u)
 
 

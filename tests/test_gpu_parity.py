@@ -238,3 +238,25 @@ def test_product_gmg_setup_matches_oracle_construction(M):
     assert relerr(sv.get_setup_tensors(), to_nhwc(s_ref)) <= 1e-15
     r = f.copy()
     assert relerr(sv.vcycle(r.ravel().copy()), ogmg.vcycle(sts, r, 2, 1, 0.7)) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [3, 7, 63, 255])
+def test_fused_and_per_layer_kernels_agree(M, n):
+    """8 channels, one layer per ResNet: the fused level kernels and the one-kernel-
+    per-layer path compute the same V-cycle; they round to BF16 at different points
+    (the fused path keeps the pre-layer TCNN sum in FP32), so they agree to BF16
+    accuracy, and both stay within the BF16 bound of the FP64 oracle."""
+    C = 8
+    k, f = problem(n, 30 + n)
+    w = omg.random_weights(C, 1, 1, np.random.default_rng(12))
+    sts = oop.level_stencils_div(k, (1.0, 0.5), num_levels(n))
+    e_ref = omg.solve_phase(w, omg.setup(w, sts), f)
+    out = {}
+    for fused in (1, 0):
+        sv = M.Solver(C, 1, 1, precision="mixed_bf16")
+        sv.set_option(sv.OPT_FUSED, fused)
+        sv.set_weights(M.pack_weights(w, C, 1, 1))
+        sv.setup(k.ravel().copy(), n)
+        out[fused] = sv.vcycle(f.ravel().copy())
+        assert relerr(out[fused], e_ref) <= 5e-2
+    assert relerr(out[1], out[0]) <= 3e-2
