@@ -29,21 +29,22 @@ SETUP_KEYS = ("sw_in", "sb_in", "sw", "sb", "sw_R")
 
 
 def unrolled_residuals(weights: dict, stencils: list[Stencil], f: np.ndarray, K: int,
-                       scale_by_diag: bool = True):
+                       scale_by_diag: bool = True, input_diag: bool = False):
     """r_0 = f, r_{k+1} = r_k - A B r_k for k < K.  Returns (r list, setup tensors)."""
     s = mg.setup(weights, stencils, scale_by_diag)
     A = stencils[0]
+    d_inv = (1.0 / A.aC) if input_diag else None
     rs = [f.copy()]
     for _ in range(K):
-        rs.append(rs[-1] - apply(A, mg.solve_phase(weights, s, rs[-1])))
+        rs.append(rs[-1] - apply(A, mg.solve_phase(weights, s, rs[-1], d_inv=d_inv)))
     return rs, s
 
 
-def loss(weights: dict, problems: list, K: int, scale_by_diag: bool = True) -> float:
+def loss(weights: dict, problems: list, K: int, scale_by_diag: bool = True, input_diag: bool = False) -> float:
     """L = (1/N) sum_i ||r_K,i||^2 / ||f_i||^2 over problems [(stencils, f), ...]."""
     total = 0.0
     for stencils, f in problems:
-        rs, _ = unrolled_residuals(weights, stencils, f, K, scale_by_diag)
+        rs, _ = unrolled_residuals(weights, stencils, f, K, scale_by_diag, input_diag)
         total += float(np.sum(rs[-1] ** 2) / np.sum(f ** 2))
     return total / len(problems)
 
@@ -58,14 +59,15 @@ def _resnet_layer_backward(xbar, x_in, s_l, W, gW, sbar_l):
 
 
 def solve_phase_backward(weights: dict, s: list[np.ndarray], r: np.ndarray, ebar: np.ndarray,
-                         grads: dict, sbar: list[np.ndarray]) -> np.ndarray:
-    """Adjoint of e = B r (Algorithm 3) at input r for output adjoint e_bar.
+                         grads: dict, sbar: list[np.ndarray], d_inv: np.ndarray | None = None) -> np.ndarray:
+    """Adjoint of e = B r (Algorithm 3, on D^{-1} r when d_inv is given) at input r
+    for output adjoint e_bar.
 
     Returns r_bar = B^T e_bar; adds the weight gradients into `grads` and the
     setup-tensor gradients into `sbar`.
     """
     keep = {}
-    mg.solve_phase(weights, s, r, keep)
+    mg.solve_phase(weights, s, r, keep, d_inv=d_inv)
     L = len(s)
     sizes = [t.shape[1] for t in s]
     nu_d = weights["w_down"].shape[0]
@@ -98,8 +100,10 @@ def solve_phase_backward(weights: dict, s: list[np.ndarray], r: np.ndarray, ebar
             xbar_down[l - 1] += cn.tcnn(xb, weights["w_R"], sizes[l - 1])  # RCNN^T = TCNN
             grads["w_R"] += cn.rcnn_wgrad(xb, keep["x_down"][l - 1])
         else:
-            grads["w_in"] += cn.conv_same_wgrad(xb, r[None])
+            grads["w_in"] += cn.conv_same_wgrad(xb, keep["rin"][None])
             rbar = cn.conv_same_adjoint(xb, weights["w_in"])[0]
+            if d_inv is not None:
+                rbar = rbar * d_inv
     return rbar
 
 
@@ -128,20 +132,21 @@ def setup_backward(weights: dict, stencils: list[Stencil], sbar: list[np.ndarray
     grads["sb_in"] += cbar[0].sum(axis=(1, 2))
 
 
-def loss_and_grad(weights: dict, problems: list, K: int, scale_by_diag: bool = True):
+def loss_and_grad(weights: dict, problems: list, K: int, scale_by_diag: bool = True, input_diag: bool = False):
     """Loss and its gradient with respect to every weight (dict of arrays like `weights`)."""
     grads = {k: np.zeros_like(v) for k, v in weights.items()}
     N = len(problems)
     total = 0.0
     for stencils, f in problems:
         A = stencils[0]
-        rs, s = unrolled_residuals(weights, stencils, f, K, scale_by_diag)
+        d_inv = (1.0 / A.aC) if input_diag else None
+        rs, s = unrolled_residuals(weights, stencils, f, K, scale_by_diag, input_diag)
         fn2 = float(np.sum(f * f))
         total += float(np.sum(rs[-1] ** 2)) / fn2
         g = 2.0 * rs[-1] / (N * fn2)
         sbar = [np.zeros_like(t) for t in s]
         for k in reversed(range(K)):
             ebar = -apply_transpose(A, g)
-            g = g + solve_phase_backward(weights, s, rs[k], ebar, grads, sbar)
+            g = g + solve_phase_backward(weights, s, rs[k], ebar, grads, sbar, d_inv)
         setup_backward(weights, stencils, sbar, grads, scale_by_diag)
     return total / N, grads

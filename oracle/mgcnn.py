@@ -21,7 +21,13 @@ Readings where the paper is silent (each is listed in the design notes):
   rediscretised operator (k restricted as in operator.restrict_k), a Jacobi-like D^{-1} that gives B the
   units of A^{-1}; `scale_by_diag=False` gives the unscaled form;
 * the setup RCNN has its own weights, no bias; every setup layer is
-  tanh(K z + b) + z (Eq. resnet_nonlinear), the last one included.
+  tanh(K z + b) + z (Eq. resnet_nonlinear), the last one included;
+* input normalisation: Sec. 2.5 removes the 1/h factor of the stencil so that
+  the network works on an O(1) operator at every grid size.  For a
+  heterogeneous divergence-form operator the pointwise analogue is the
+  diagonal: with `d_inv` = 1/a_C (finest level) the solve phase is applied to
+  D^{-1} r, i.e. B r = Net(D^{-1} r).  Without it the ResNet skip paths give B
+  an O(1) multiple of the identity while A ~ k/h^2, and A B grows like n^2.
 """
 from __future__ import annotations
 
@@ -87,13 +93,15 @@ def setup(weights: dict, stencils: list[Stencil], scale_by_diag: bool = True, ke
     return outs
 
 
-def solve_phase(weights: dict, s: list[np.ndarray], r: np.ndarray, keep: dict | None = None) -> np.ndarray:
+def solve_phase(weights: dict, s: list[np.ndarray], r: np.ndarray, keep: dict | None = None,
+                d_inv: np.ndarray | None = None) -> np.ndarray:
     """Algorithm 3: one application e = B r of the solve network.
 
-    x_1 = reChannelCNN(r); down loop: x_l <- ResNetDown(s_l, x_l) then
-    x_{l+1} = RCNN(x_l); up loop: x_l <- ResNetUp(s_l, x_l) then
-    x_{l-1} <- x_{l-1} + TCNN(x_l); sol = reChannelCNN(x_1).
-    Each ResNet layer is y = K (s_l * x) + x (Eq. heteroresnet).
+    x_1 = reChannelCNN(r) (of D^{-1} r when d_inv is given); down loop:
+    x_l <- ResNetDown(s_l, x_l) then x_{l+1} = RCNN(x_l); up loop:
+    x_l <- ResNetUp(s_l, x_l) then x_{l-1} <- x_{l-1} + TCNN(x_l);
+    sol = reChannelCNN(x_1).  Each ResNet layer is y = K (s_l * x) + x
+    (Eq. heteroresnet).
     """
     L = len(s)
     sizes = [t.shape[1] for t in s]
@@ -101,7 +109,8 @@ def solve_phase(weights: dict, s: list[np.ndarray], r: np.ndarray, keep: dict | 
     nu_u = weights["w_up"].shape[0]
     x = [None] * L
     x0, down_in, x_down, up_in, x_fin = [None] * L, [], [None] * L, [None] * L, [None] * L
-    x[0] = cn.conv_same(r[None], weights["w_in"])
+    rin = r if d_inv is None else r * d_inv
+    x[0] = cn.conv_same(rin[None], weights["w_in"])
     for l in range(L):
         x0[l] = x[l]
         ins = []
@@ -123,13 +132,14 @@ def solve_phase(weights: dict, s: list[np.ndarray], r: np.ndarray, keep: dict | 
             x[l - 1] = x[l - 1] + cn.tcnn(x[l], weights["w_P"], sizes[l - 1])
     e = cn.conv_same(x[0], weights["w_out"])[0]
     if keep is not None:
-        keep.update(x0=x0, down_in=down_in, x_down=x_down, up_in=up_in, x_fin=x_fin)
+        keep.update(x0=x0, down_in=down_in, x_down=x_down, up_in=up_in, x_fin=x_fin, rin=rin)
     return e
 
 
 def stationary_solve(weights: dict, s: list[np.ndarray], A: Stencil, f: np.ndarray,
-                     u0: np.ndarray | None, tol: float, maxit: int):
-    """Eq. 1 with B = solve_phase: u^{k+1} = u^k + B (f - A u^k).
+                     u0: np.ndarray | None, tol: float, maxit: int, input_diag: bool = False):
+    """Eq. 1 with B = solve_phase: u^{k+1} = u^k + B (f - A u^k)
+    (B r = Net(D^{-1} r) when input_diag).
 
     Stops when ||r^k||_2 / ||f||_2 <= tol (checked before each cycle) or k = maxit.
     Returns (u, iters, relres_history, iterates) with iterates[k] = u^k.
@@ -145,7 +155,7 @@ def stationary_solve(weights: dict, s: list[np.ndarray], A: Stencil, f: np.ndarr
         hist.append(rel)
         if rel <= tol or k == maxit:
             return u, k, hist, iterates
-        u = u + solve_phase(weights, s, r)
+        u = u + solve_phase(weights, s, r, d_inv=(1.0 / A.aC) if input_diag else None)
         iterates.append(u.copy())
     raise AssertionError("unreachable")
 
@@ -215,20 +225,26 @@ def _shift_to_source(a: np.ndarray, dy: int, dx: int) -> np.ndarray:
     return out
 
 
-def gmg_equivalent_setup(stencils: list[Stencil], omega: float = 0.8) -> list[np.ndarray]:
+def gmg_equivalent_setup(stencils: list[Stencil], omega: float = 0.8, input_diag: bool = False) -> list[np.ndarray]:
     """Setup tensors for `gmg_equivalent_weights` on every level:
     s[E_o](q) = -omega a_o(q-o)/a_C(q-o),  s[F_J] = omega/a_C,
-    s[G_o](q) = -a_o(q-o),                 s[F_G] = 1,  s[D] = 0."""
+    s[G_o](q) = -a_o(q-o),                 s[F_G] = 1,  s[D] = 0.
+    With input_diag the finest level's rhs copies hold D^{-1} r, so there
+    s[F_J] = omega and s[F_G] = a_C (the same Jacobi update and defect)."""
     outs = []
-    for st in stencils:
+    for lev, st in enumerate(stencils):
         n = st.n
         s = np.zeros((GMG_CHANNELS, n, n))
         coeffs = [st.aC, st.aW, st.aE, st.aS, st.aN]
         for k, ((dy, dx), a) in enumerate(zip(_OFFS, coeffs)):
             s[_E[k]] = _shift_to_source(-omega * a / st.aC, dy, dx)
             s[_G[k]] = _shift_to_source(-a, dy, dx)
-        s[_FJ] = omega / st.aC
-        s[_FG] = 1.0
+        if input_diag and lev == 0:
+            s[_FJ] = omega
+            s[_FG] = st.aC
+        else:
+            s[_FJ] = omega / st.aC
+            s[_FG] = 1.0
         outs.append(s)
     return outs
 

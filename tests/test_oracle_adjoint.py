@@ -39,13 +39,15 @@ def test_dot_product_transpose():
     assert abs(lhs - np.sum(v * btw)) <= 1e-12 * abs(lhs)
 
 
-def test_central_differences():
+@pytest.mark.parametrize("scale_by_diag,input_diag", [(True, False), (False, True)])
+def test_central_differences(scale_by_diag, input_diag):
     probs = _problems([7, 15], 3)
     rng = np.random.default_rng(4)
     w = mg.random_weights(3, 1, 2, rng, scale=0.5)
     K = 2
-    L0, g = adj.loss_and_grad(w, probs, K)
-    assert np.isclose(L0, adj.loss(w, probs, K), rtol=1e-13)
+    kw = dict(scale_by_diag=scale_by_diag, input_diag=input_diag)
+    L0, g = adj.loss_and_grad(w, probs, K, **kw)
+    assert np.isclose(L0, adj.loss(w, probs, K, **kw), rtol=1e-13)
     checked = 0
     for key in w:
         flat = w[key].reshape(-1)
@@ -53,9 +55,9 @@ def test_central_differences():
             eps = 1e-6 * max(1.0, abs(flat[idx]))
             old = flat[idx]
             flat[idx] = old + eps
-            lp = adj.loss(w, probs, K)
+            lp = adj.loss(w, probs, K, **kw)
             flat[idx] = old - eps
-            lm = adj.loss(w, probs, K)
+            lm = adj.loss(w, probs, K, **kw)
             flat[idx] = old
             fd = (lp - lm) / (2 * eps)
             an = g[key].reshape(-1)[idx]
@@ -64,7 +66,7 @@ def test_central_differences():
     assert checked >= 25
 
 
-def _torch_loss(wt, probs, K):
+def _torch_loss(wt, probs, K, input_diag=False):
     total = 0.0
     for sts, f in probs:
         aC = [torch.from_numpy(st.aC) for st in sts]
@@ -75,7 +77,7 @@ def _torch_loss(wt, probs, K):
             z = c
             for i in range(4):
                 z = torch.tanh(F.conv2d(z, wt["sw"][i], wt["sb"][i], padding=1)) + z
-            s.append(z / aC[l])
+            s.append(z if input_diag else z / aC[l])
             c = F.conv2d(c, wt["sw_R"], stride=2)
         A = sts[0]
         coef = [torch.from_numpy(a) for a in (A.aC, A.aW, A.aE, A.aS, A.aN)]
@@ -88,7 +90,8 @@ def _torch_loss(wt, probs, K):
         def B(r):
             L = len(s)
             x = [None] * L
-            x[0] = F.conv2d(r[None, None], wt["w_in"], padding=1)
+            rin = r / aC[0] if input_diag else r
+            x[0] = F.conv2d(rin[None, None], wt["w_in"], padding=1)
             for l in range(L):
                 for i in range(wt["w_down"].shape[0]):
                     x[l] = x[l] + F.conv2d(s[l] * x[l], wt["w_down"][i], padding=1)
@@ -109,13 +112,14 @@ def _torch_loss(wt, probs, K):
     return total / len(probs)
 
 
-def test_against_torch_autograd():
+@pytest.mark.parametrize("input_diag", [False, True])
+def test_against_torch_autograd(input_diag):
     probs = _problems([15, 31], 5)
     w = mg.random_weights(4, 2, 1, np.random.default_rng(6), scale=0.5)
     K = 3
-    L0, g = adj.loss_and_grad(w, probs, K)
+    L0, g = adj.loss_and_grad(w, probs, K, scale_by_diag=not input_diag, input_diag=input_diag)
     wt = {k: torch.tensor(v, requires_grad=True) for k, v in w.items()}
-    Lt = _torch_loss(wt, probs, K)
+    Lt = _torch_loss(wt, probs, K, input_diag)
     Lt.backward()
     assert np.isclose(L0, Lt.item(), rtol=1e-12)
     for k in w:

@@ -115,3 +115,29 @@ def test_setup_features_are_scale_free():
     f2 = mg.setup_features(op.stencil_div(100 * k, (0, 0)))
     np.testing.assert_allclose(f1[:4], f2[:4], rtol=1e-13)
     np.testing.assert_allclose(f2[4] - f1[4], 2.0, rtol=1e-12)
+
+
+def test_gmg_equivalence_with_input_normalisation():
+    """With B r = Net(D^{-1} r) the finest-level setup tensors absorb the diagonal
+    (s[F_J] = omega, s[F_G] = a_C) and the network is still GMG iterate for iterate."""
+    n, k, b, f = cfg0_problem()
+    sts = op.level_stencils_div(k, b, num_levels(n))
+    w = mg.gmg_equivalent_weights(2, 2)
+    s = mg.gmg_equivalent_setup(sts, 0.8, input_diag=True)
+    u_m, it_m, _, its_m = mg.stationary_solve(w, s, sts[0], f, None, 1e-10, 200, input_diag=True)
+    u_g, it_g, _, its_g = gmg.stationary_solve(sts, f, None, 1e-10, 200, 2, 2, 0.8)
+    assert it_m == it_g
+    for a, c in zip(its_m[1:], its_g[1:]):
+        assert np.linalg.norm(a - c) <= 1e-13 * np.linalg.norm(c)
+
+
+def test_linearity_with_input_normalisation():
+    sts, f = _problem(31, 22)
+    rng = np.random.default_rng(23)
+    w = mg.random_weights(8, 1, 1, rng)
+    s = mg.setup(w, sts, scale_by_diag=False)
+    d = 1.0 / sts[0].aC
+    g = rng.standard_normal(f.shape)
+    lhs = mg.solve_phase(w, s, 3.0 * f + g, d_inv=d)
+    rhs = 3.0 * mg.solve_phase(w, s, f, d_inv=d) + mg.solve_phase(w, s, g, d_inv=d)
+    assert np.linalg.norm(lhs - rhs) <= 1e-13 * np.linalg.norm(lhs)
