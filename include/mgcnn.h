@@ -88,6 +88,10 @@ typedef struct {
   int pde;           /* MGCNN_PDE_*                                            */
   int scale_by_diag; /* 1: each setup tensor is divided by a_C of its level's
                         operator (Jacobi-like scaling); 0: the raw network output */
+  int input_diag;    /* 1: the solve network is applied to D^{-1} r, D = diag(A)
+                        of the finest level (B r = Net(D^{-1} r)): the pointwise
+                        analogue of the paper's normalisation of the stencil to
+                        O(1) entries (Sec. 2.5); 0: Net(r)                       */
   int levels;        /* 0: L = log2(n+1)-1 (coarsest 3x3); else 1..that L     */
   double bx, by;     /* constant velocity b (or v) of the convection term      */
 } mgcnn_config;
@@ -142,7 +146,8 @@ int mgcnn_setup(mgcnn_ctx* ctx, const double* coeff, int n);
  * tensors analytically instead of running the setup network:
  *   s[E_o](q) = -omega a_o(q-o)/a_C(q-o), s[G_o](q) = -a_o(q-o) for o in
  *   {C, W, E, S, N} (channels 0-4 and 5-9), s[F_J] = omega/a_C, s[F_G] = 1,
- *   s[D] = 0 (channels 10, 11, 12).
+ *   s[D] = 0 (channels 10, 11, 12); with input_diag the finest level's
+ *   right-hand-side copies hold D^{-1} r, so there s[F_J] = omega, s[F_G] = a_C.
  * The matching weights (ResNetDown = nu1 Jacobi layers + one defect layer,
  * ResNetUp = nu2 Jacobi layers) must be loaded with mgcnn_set_weights; the
  * Python binding's gmg_weights() builds that blob.  Requires channels == 13.

@@ -225,6 +225,7 @@ Status vcycle_fp64(mgcnn_ctx* c, const double* r, double* e, const double* u_ski
   {
     ConvArgs<double> a;
     a.x = r; a.W = W + wl.w_in; a.y = x[0]; a.n = c->lv[0].n;
+    if (c->cfg.input_diag) a.s = c->dinv.as<double>();   // Net(D^{-1} r)
     MG_TRY(conv_same<double>(1, C, a, c->stream));
   }
   for (int l = 0; l < c->L; ++l) {
@@ -308,6 +309,8 @@ Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
   MG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   MG_TRY(sync(c));
   if (hbad) return make_status(MGCNN_ERR_NONFINITE, "coefficient field has non-finite or non-positive entries");
+  MG_TRY(ensure(c->dinv, N0 * sizeof(double)));
+  MG_TRY(ensure(c->dinv32, N0 * sizeof(float)));
   // operators on every level (Sec. 2.3: rediscretisation)
   for (int l = 0; l < L; ++l) {
     const int nlv = c->lv[l].n;
@@ -319,6 +322,7 @@ Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
       if (l < L - 1) MG_TRY(launch_inject_mu(c->coef[l].as<double>(), c->coef[l + 1].as<double>(), nlv, c->stream));
     }
   }
+  MG_TRY(launch_diag_inverse(c->op[0].as<double>(), c->dinv.as<double>(), c->dinv32.as<float>(), N0, c->stream));
   return {};
 }
 
@@ -450,7 +454,8 @@ int mgcnn_setup_gmg(mgcnn_ctx* c, const double* coeff, int n, double omega) {
     MG_TRY(setup_operators(c, coeff, n));
     for (int l = 0; l < c->L; ++l) {
       if (c->cfg.precision == MGCNN_PREC_FP64)
-        MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->s64[l].as<double>(), c->lv[l].n, omega, c->stream));
+        MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->s64[l].as<double>(), c->lv[l].n, omega, c->stream,
+                                l == 0 && c->cfg.input_diag));
       else
         MG_TRY(mixed_gmg_setup_level(c, l, omega));
     }
@@ -592,7 +597,8 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
       // mixed: the V-cycle consumes an FP32 copy of r (scaled in-kernel), FP64 r is not stored
       const int ps = prof_begin(c, kProfResidual);
       MG_TRY(launch_residual(df, du, c->op[0].as<double>(), mixed ? nullptr : c->r.as<double>(),
-                             mixed ? c->r32.as<float>() : nullptr, c->partial.as<double>(), c->n, c->stream));
+                             mixed ? c->r32.as<float>() : nullptr, c->partial.as<double>(), c->n, c->stream,
+                             c->cfg.input_diag ? c->dinv32.as<float>() : nullptr));
       prof_end(c, ps);
       MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>(), c->stream));
       double rn2 = 0.0;

@@ -88,7 +88,8 @@ struct mgcnn_ctx {
   mgcnn::DevBuf setup_a, setup_b, setup_c, setup_d;  // setup-phase scratch
   mgcnn::DevBuf feat;                     // setup features [n^2][5]
   mgcnn::DevBuf f, u, r, e;               // finest-grid FP64 vectors (staging / work)
-  mgcnn::DevBuf r32;                      // FP32 residual for the mixed path
+  mgcnn::DevBuf r32;                      // FP32 network input (r or D^{-1} r) for the mixed path
+  mgcnn::DevBuf dinv, dinv32;             // 1/a_C of the finest level, FP64 and FP32
   mgcnn::DevBuf partial;                  // per-block partial sums of reductions
   // mixed-precision path (mixed.cu)
   int cp = 0;                             // channels padded for the tensor cores (8 or 16)

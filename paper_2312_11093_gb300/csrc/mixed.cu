@@ -379,9 +379,10 @@ __global__ void unpad_bf16_kernel(const bf16* __restrict__ src, double* __restri
   dst[p] = (double)__bfloat162float(src[pix * cp + ch]);
 }
 
-__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, size_t N) {
+__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, size_t N,
+                              const float* __restrict__ scale) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < N) dst[p] = (float)src[p];
+  if (p < N) dst[p] = scale ? (float)src[p] * scale[p] : (float)src[p];
 }
 
 template <int CP>
@@ -519,7 +520,8 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega) {
   MG_TRY(ensure(c->x16b[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
   MG_TRY(ensure(c->setup_a, N * kGmgChannels * sizeof(double)));
-  MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->setup_a.as<double>(), c->lv[l].n, omega, c->stream));
+  MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->setup_a.as<double>(), c->lv[l].n, omega, c->stream,
+                          l == 0 && c->cfg.input_diag));
   pad_to_bf16_kernel<double><<<grid_for(N * cp, 256), 256, 0, c->stream>>>(c->setup_a.as<double>(),
                                                                             c->s16[l].as<bf16>(), N, kGmgChannels, cp);
   MG_LAUNCH("pad_to_bf16_kernel");
@@ -549,7 +551,8 @@ Status vcycle_mixed_r32(mgcnn_ctx* c, const float* r32, const double* norm2_dev,
 
 Status vcycle_mixed(mgcnn_ctx* c, const double* r, double* e, const double* u_skip) {
   const size_t N = c->lv[0].N();
-  to_f32_kernel<<<grid_for(N, 256), 256, 0, c->stream>>>(r, c->r32.as<float>(), N);
+  to_f32_kernel<<<grid_for(N, 256), 256, 0, c->stream>>>(r, c->r32.as<float>(), N,
+                                                         c->cfg.input_diag ? c->dinv32.as<float>() : nullptr);
   MG_LAUNCH("to_f32_kernel");
   double* norm2 = c->scalars.as<double>() + 2;
   MG_TRY(launch_sumsq(r, N, c->partial.as<double>(), c->stream));

@@ -174,7 +174,8 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
 // r = f - A u, FP64 (Eq. 1); per-block partial of sum r^2.
 __global__ void __launch_bounds__(kResidualBlock)
 residual_kernel(const double* __restrict__ f, const double* __restrict__ u, const double* __restrict__ op,
-                double* __restrict__ r, float* __restrict__ r32, double* __restrict__ partial, int n) {
+                double* __restrict__ r, float* __restrict__ r32, double* __restrict__ partial, int n,
+                const float* __restrict__ dinv32) {
   __shared__ double smem[32];
   const size_t N = (size_t)n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,7 +190,7 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
     const double Au = op[p] * uC + op[N + p] * uW + op[2 * N + p] * uE + op[3 * N + p] * uS + op[4 * N + p] * uN;
     const double rv = f[p] - Au;
     if (r) r[p] = rv;
-    if (r32) r32[p] = (float)rv;
+    if (r32) r32[p] = dinv32 ? (float)rv * dinv32[p] : (float)rv;
     rr = rv * rv;
   }
   rr = block_sum(rr, smem);
@@ -197,10 +198,25 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
 }
 
 Status launch_residual(const double* f, const double* u, const double* op, double* r, float* r32,
-                       double* partial, int n, cudaStream_t st) {
+                       double* partial, int n, cudaStream_t st, const float* dinv32) {
   const size_t N = (size_t)n * n;
-  residual_kernel<<<reduction_blocks(N), kResidualBlock, 0, st>>>(f, u, op, r, r32, partial, n);
+  residual_kernel<<<reduction_blocks(N), kResidualBlock, 0, st>>>(f, u, op, r, r32, partial, n, dinv32);
   MG_LAUNCH("residual_kernel");
+  return {};
+}
+
+__global__ void diag_inverse_kernel(const double* __restrict__ op, double* __restrict__ dinv,
+                                    float* __restrict__ dinv32, size_t N) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const double d = 1.0 / op[p];
+  dinv[p] = d;
+  dinv32[p] = (float)d;
+}
+
+Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t N, cudaStream_t st) {
+  diag_inverse_kernel<<<grid_for(N, 256), 256, 0, st>>>(op, dinv, dinv32, N);
+  MG_LAUNCH("diag_inverse_kernel");
   return {};
 }
 
@@ -242,7 +258,8 @@ Status launch_reduce(const double* partial, int count, double* out, cudaStream_t
 // tensor multiplying a layer's input carries the coefficient of tap o:
 //   s[E_o](q) = -omega a_o(q-o) / a_C(q-o),  s[G_o](q) = -a_o(q-o)   (0 if q-o is outside)
 //   s[F_J] = omega / a_C,  s[F_G] = 1,  s[D] = 0.
-__global__ void gmg_setup_kernel(const double* __restrict__ op, double* __restrict__ out, int n, double omega) {
+__global__ void gmg_setup_kernel(const double* __restrict__ op, double* __restrict__ out, int n, double omega,
+                                 int input_diag_level) {
   const size_t N = (size_t)n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (int)N) return;
@@ -261,13 +278,15 @@ __global__ void gmg_setup_kernel(const double* __restrict__ op, double* __restri
     o[k] = sE;
     o[5 + k] = sG;
   }
-  o[10] = omega / op[p];
-  o[11] = 1.0;
+  // rhs copies: r at coarse levels; D^{-1} r at the finest level when the input is normalised
+  o[10] = input_diag_level ? omega : omega / op[p];
+  o[11] = input_diag_level ? op[p] : 1.0;
   o[12] = 0.0;
 }
 
-Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st) {
-  gmg_setup_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, out, n, omega);
+Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st,
+                        bool input_diag_level) {
+  gmg_setup_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, out, n, omega, input_diag_level ? 1 : 0);
   MG_LAUNCH("gmg_setup_kernel");
   return {};
 }

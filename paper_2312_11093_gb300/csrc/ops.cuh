@@ -20,16 +20,20 @@ Status launch_stencil_nondiv(const double* mu, double* op, int n, double vx, dou
 Status launch_count_bad(const double* v, size_t N, int* count, cudaStream_t st);
 template <typename FT>
 Status launch_features(const double* op, FT* feat, int n, cudaStream_t st);
-// r = f - A u (FP64), optional FP32 copy r32, per-block partial sums of r^2.
+// r = f - A u (FP64), optional FP32 copy r32 (times dinv32 when given), per-block
+// partial sums of r^2.
 Status launch_residual(const double* f, const double* u, const double* op, double* r, float* r32,
-                       double* partial, int n, cudaStream_t st);
+                       double* partial, int n, cudaStream_t st, const float* dinv32 = nullptr);
+// dinv = 1/a_C (FP64 and FP32) from the first plane of op.
+Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t N, cudaStream_t st);
 Status launch_sumsq(const double* v, size_t N, double* partial, cudaStream_t st);
 // out[0] = sum of partial[0..count) in a fixed order (deterministic).
 Status launch_reduce(const double* partial, int count, double* out, cudaStream_t st);
 // Setup tensors of the 13-channel network whose solve phase is classical GMG
 // (weighted Jacobi, full weighting, bilinear): out [N][13] FP64.
 constexpr int kGmgChannels = 13;
-Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st);
+Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st,
+                        bool input_diag_level = false);
 Status launch_axpy_to(const double* u, const double* e, double* out, size_t N, cudaStream_t st);
 
 // ---- net_generic.cu: FP64 / FP32 direct convolution kernels ----------------

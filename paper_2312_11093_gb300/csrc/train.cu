@@ -73,6 +73,15 @@ __global__ void div_diag_kernel(const T* __restrict__ in, const double* __restri
   out[q] = (T)((double)in[q] / op[b * 5 * N + p]);
 }
 
+// d[b][p] = 1 / a_C[b][p] (first plane of op [b][5][N])
+template <typename T>
+__global__ void dinv_kernel(const double* __restrict__ op, T* __restrict__ d, size_t N, int B) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)B * N) return;
+  const size_t b = q / N, p = q - b * N;
+  d[q] = (T)(1.0 / op[b * 5 * N + p]);
+}
+
 template <typename T>
 __global__ void copy_cast_kernel(const double* __restrict__ src, T* __restrict__ dst, size_t count) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -488,13 +497,14 @@ struct Trainer {
   }
 };
 
+// add / mul are also used in place (out == a), so their pointers are not __restrict__
 template <typename T>
-__global__ void add_kernel(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, size_t count) {
+__global__ void add_kernel(const T* a, const T* b, T* out, size_t count) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < count) out[p] = a[p] + b[p];
 }
 template <typename T>
-__global__ void mul_kernel(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, size_t count) {
+__global__ void mul_kernel(const T* a, const T* b, T* out, size_t count) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < count) out[p] = a[p] * b[p];
 }
@@ -553,6 +563,8 @@ Status alloc_group(mgcnn_ctx* c, TrainGroup& g, int n, int B, int K, size_t tsiz
   MG_TRY(T_(g.ev, (size_t)B * N0));
   MG_TRY(T_(g.eb, (size_t)B * N0));
   MG_TRY(T_(g.rb, (size_t)B * N0));
+  MG_TRY(T_(g.dinvT, (size_t)B * N0));
+  MG_TRY(T_(g.rin, (size_t)B * N0));
   MG_TRY(ensure(g.fn2, (size_t)B * sizeof(double)));
   MG_TRY(ensure(g.rn2, (size_t)B * sizeof(double)));
   MG_TRY(ensure(g.npart, (size_t)B * grid_for(N0, 256) * sizeof(double)));
@@ -576,7 +588,8 @@ void train_release(mgcnn_ctx* c) {
         release(g.xu[l][i]);
       }
     }
-    for (DevBuf* b : {&g.coef, &g.feat, &g.rs, &g.gv, &g.ev, &g.eb, &g.rb, &g.fn2, &g.rn2, &g.npart, &g.wpart})
+    for (DevBuf* b : {&g.coef, &g.feat, &g.rs, &g.gv, &g.ev, &g.eb, &g.rb, &g.fn2, &g.rn2, &g.npart, &g.wpart,
+                      &g.dinvT, &g.rin})
       release(*b);
   }
   c->groups.clear();
@@ -649,12 +662,23 @@ Status loss_grad_impl(mgcnn_ctx* c, int nprob, const double* const* coeff, const
       MG_LAUNCH("copy_cast_kernel");
     }
     Trainer<T> tr(c, g, W, WT, c->grad.as<double>());
+    const bool idiag = c->cfg.input_diag != 0;
+    if (idiag) {
+      dinv_kernel<T><<<grid_for((size_t)B * N0, 256), 256, 0, st>>>(g.op[0].as<double>(), g.dinvT.as<T>(), N0, B);
+      MG_LAUNCH("dinv_kernel");
+    }
+    // network input for cycle k: r_k, or D^{-1} r_k
+    auto net_input = [&](const T* rk) -> const T* {
+      if (!idiag) return rk;
+      tr.mul(rk, g.dinvT.as<T>(), g.rin.as<T>(), (size_t)B * N0);
+      return g.rin.as<T>();
+    };
     MG_TRY(tr.setup_forward());
     // K cycles, storing r_k
     for (int k = 0; k < K; ++k) {
       T* rk = g.rs.as<T>() + (size_t)k * B * N0;
       T* rk1 = rk + (size_t)B * N0;
-      MG_TRY(tr.solve_forward_full(rk, g.ev.as<T>()));
+      MG_TRY(tr.solve_forward_full(net_input(rk), g.ev.as<T>()));
       stencil_kernel<T><<<dim3(grid_for(N0, 256), B), 256, 0, st>>>(g.op[0].as<double>(), g.ev.as<T>(), rk, rk1, n, 0);
       MG_LAUNCH("stencil_kernel");
     }
@@ -692,9 +716,12 @@ Status loss_grad_impl(mgcnn_ctx* c, int nprob, const double* const* coeff, const
       stencil_kernel<T><<<dim3(grid_for(N0, 256), B), 256, 0, st>>>(g.op[0].as<double>(), g.gv.as<T>(), nullptr,
                                                                      g.eb.as<T>(), n, 1);
       MG_LAUNCH("stencil_kernel");
-      MG_TRY(tr.solve_forward_full(rk, g.ev.as<T>()));
-      MG_TRY(tr.solve_backward(rk, g.eb.as<T>(), g.rb.as<T>(), WT + wl.w_in, WT + wl.w_out, WT + wl.w_down,
+      const T* rin = net_input(rk);
+      MG_TRY(tr.solve_forward_full(rin, g.ev.as<T>()));
+      MG_TRY(tr.solve_backward(rin, g.eb.as<T>(), g.rb.as<T>(), WT + wl.w_in, WT + wl.w_out, WT + wl.w_down,
                                WT + wl.w_up));
+      // d(D^{-1} r)/dr = D^{-1}
+      if (idiag) tr.mul(g.rb.as<T>(), g.dinvT.as<T>(), g.rb.as<T>(), (size_t)B * N0);
       tr.add(g.gv.as<T>(), g.rb.as<T>(), g.gv.as<T>(), (size_t)B * N0);
     }
     MG_TRY(tr.setup_backward(WT + wl.sw));

@@ -22,6 +22,7 @@ struct TrainGroup {
   DevBuf rs;                                   // r_0 .. r_K, [K+1][B][N]
   DevBuf gv, ev, eb, rb;                       // g_k, B r_k, e_bar, B^T e_bar
   DevBuf fn2, rn2, npart, wpart;
+  DevBuf dinvT, rin;                           // 1/a_C (finest) in T; network input D^{-1} r_k
 };
 
 void train_release(mgcnn_ctx* c);

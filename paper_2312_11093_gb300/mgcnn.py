@@ -26,7 +26,8 @@ FEATURES = 5
 
 class Config(ctypes.Structure):
     _fields_ = [("channels", c_int), ("down_layers", c_int), ("up_layers", c_int), ("precision", c_int),
-                ("pde", c_int), ("scale_by_diag", c_int), ("levels", c_int), ("bx", c_double), ("by", c_double)]
+                ("pde", c_int), ("scale_by_diag", c_int), ("input_diag", c_int), ("levels", c_int),
+                ("bx", c_double), ("by", c_double)]
 
 
 class MGCNNError(RuntimeError):
@@ -106,7 +107,7 @@ def kernel_launches() -> int:
 
 
 def weight_count(channels: int, down_layers: int = 1, up_layers: int = 1) -> int:
-    cfg = Config(channels, down_layers, up_layers, 0, 0, 1, 0, 0.0, 0.0)
+    cfg = Config(channels, down_layers, up_layers, 0, 0, 0, 1, 0, 0.0, 0.0)
     return int(load().mgcnn_weight_count(ctypes.byref(cfg)))
 
 
@@ -175,10 +176,13 @@ class Solver:
     """One MGCNN context: weights, a setup for one coefficient field, solves."""
 
     def __init__(self, channels: int = 8, down_layers: int = 1, up_layers: int = 1, precision: str = "fp64",
-                 pde: str = "div", scale_by_diag: bool = True, levels: int = 0, b=(1.0, 0.5), stream=None):
+                 pde: str = "div", scale_by_diag: bool = False, input_diag: bool = True, levels: int = 0,
+                 b=(1.0, 0.5), stream=None):
+        """Defaults are the learned network's configuration: unscaled setup tensors and
+        the network applied to D^{-1} r (see include/mgcnn.h, mgcnn_config)."""
         self._L = load()
         self.cfg = Config(channels, down_layers, up_layers, PREC[precision], PDE[pde], int(scale_by_diag),
-                          levels, float(b[0]), float(b[1]))
+                          int(input_diag), levels, float(b[0]), float(b[1]))
         h = c_void_p()
         st = self._L.mgcnn_create(ctypes.byref(self.cfg), ctypes.byref(h))
         if st != OK:

@@ -50,19 +50,12 @@ def _autograd():
     return MGCNNLoss
 
 
-def init_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, out_scale: float = 0.3) -> np.ndarray:
-    """Random initial weights (uniform, fan-in scaled like PyTorch's default) arranged
-    so that the initial B is small: every path from rhs to solution must pass through
-    at least one s-scaled convolution (s ~ 1/a_C carries the units of A^{-1}).
-
-    The skip connections of Eq. heteroresnet and the transfers are unscaled, so with
-    unstructured weights B contains an O(1) multiple of the identity and A B ~ a_C
-    blows the unrolled cycles up.  reChannel-in writes the first half of the
-    channels, reChannel-out reads the second half, and RCNN / TCNN start
-    block-diagonal on the two halves: only the ResNet layers move a signal from
-    the first half to the second."""
+def init_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, out_scale: float = 0.1) -> np.ndarray:
+    """Random initial weights, uniform with PyTorch's default fan-in bound, the output
+    layer shrunk so that the unrolled cycles start from a loss near 1.  With the
+    network applied to D^{-1} r, A B has O(1) entries at every grid size, so no
+    further structure is needed."""
     F, S = mgcnn.FEATURES, mgcnn.SETUP_LAYERS
-    h = C // 2
 
     def u(*shape, fan):
         b = 1.0 / np.sqrt(fan)
@@ -72,11 +65,6 @@ def init_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, out_sca
          "w_P": u(C, C, 3, 3, fan=9 * C), "w_out": out_scale * u(1, C, 3, 3, fan=9 * C),
          "sw_in": u(C, F, 3, 3, fan=9 * F), "sb_in": u(C, fan=9 * F),
          "sw": u(S, C, C, 3, 3, fan=9 * C), "sb": u(S, C, fan=9 * C), "sw_R": u(C, C, 3, 3, fan=9 * C)}
-    w["w_in"][h:] = 0.0
-    w["w_out"][:, :h] = 0.0
-    for key in ("w_R", "w_P"):
-        w[key][:h, h:] = 0.0
-        w[key][h:, :h] = 0.0
     return mgcnn.pack_weights(w, C, nu_d, nu_u)
 
 
@@ -93,7 +81,7 @@ def make_batch(step: int, sizes=(63, 127), per_size: int = 32, corr_len: float =
 
 def train(steps: int = 2000, K: int = 8, lr: float = 1e-3, C: int = 8, seed: int = 0, log_every: int = 50,
           out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size: int = 32):
-    sv = mgcnn.Solver(C, 1, 1, precision=precision, b=(1.0, 0.5))
+    sv = mgcnn.Solver(C, 1, 1, precision=precision, b=(1.0, 0.5), scale_by_diag=False, input_diag=True)
     sv.set_weights(init_weights(C, 1, 1, np.random.default_rng(seed)))
     hist = []
     t0 = time.time()

@@ -79,16 +79,31 @@ def test_residual_and_norm(M):
     assert abs(nrm2 - np.sum(rref ** 2)) <= 1e-12 * np.sum(rref ** 2)
 
 
+# network configurations: (scale_by_diag, input_diag)
+CFGS = {"scaled_setup": (True, False), "normalised_input": (False, True)}
+
+
+def oracle_B(w, sts, r, cfg):
+    sbd, idiag = CFGS[cfg]
+    s = omg.setup(w, sts, scale_by_diag=sbd)
+    return s, omg.solve_phase(w, s, r, d_inv=(1.0 / sts[0].aC) if idiag else None)
+
+
+def make_solver(M, C, nd, nu, cfg, **kw):
+    sbd, idiag = CFGS[cfg]
+    return M.Solver(C, nd, nu, scale_by_diag=sbd, input_diag=idiag, **kw)
+
+
+@pytest.mark.parametrize("cfg", list(CFGS))
 @pytest.mark.parametrize("C,nd,nu,n", [(8, 1, 1, 31), (8, 1, 1, 127), (4, 2, 1, 63), (12, 1, 2, 15),
                                        (13, 3, 2, 31), (16, 1, 1, 7), (8, 1, 1, 3)])
-def test_setup_and_vcycle_fp64(M, C, nd, nu, n):
+def test_setup_and_vcycle_fp64(M, C, nd, nu, n, cfg):
     k, f = problem(n, 10 + n)
     rng = np.random.default_rng(C + nd)
     w = omg.random_weights(C, nd, nu, rng)
     sts = oop.level_stencils_div(k, (1.0, 0.5), num_levels(n))
-    s_ref = omg.setup(w, sts)
-    e_ref = omg.solve_phase(w, s_ref, f)
-    sv = M.Solver(C, nd, nu)
+    s_ref, e_ref = oracle_B(w, sts, f, cfg)
+    sv = make_solver(M, C, nd, nu, cfg)
     sv.set_weights(M.pack_weights(w, C, nd, nu))
     sv.setup(k.ravel().copy(), n)
     s = sv.get_setup_tensors()
@@ -109,18 +124,19 @@ def test_device_and_host_pointers_agree(M):
     assert np.array_equal(e_host, e_dev.cpu().numpy())
 
 
-def _gmg_solver(M, k, n, b, precision="fp64", omega=0.8):
+def _gmg_solver(M, k, n, b, precision="fp64", omega=0.8, input_diag=True):
     sts = oop.level_stencils_div(k, b, num_levels(n))
     w = omg.gmg_equivalent_weights(2, 2)
-    s = omg.gmg_equivalent_setup(sts, omega)
-    sv = M.Solver(omg.GMG_CHANNELS, 3, 2, precision=precision, b=b)
+    s = omg.gmg_equivalent_setup(sts, omega, input_diag=input_diag)
+    sv = M.Solver(omg.GMG_CHANNELS, 3, 2, precision=precision, b=b, input_diag=input_diag)
     sv.set_weights(M.pack_weights(w, omg.GMG_CHANNELS, 3, 2))
     sv.setup(k.ravel().copy(), n)
     sv.set_setup_tensors(to_nhwc(s))
     return sv, sts, w, s
 
 
-def test_cfg0_gmg_equivalent_iterate_for_iterate(M):
+@pytest.mark.parametrize("input_diag", [True, False])
+def test_cfg0_gmg_equivalent_iterate_for_iterate(M, input_diag):
     """31x31 board of 4x4 blocks (log10 k ~ U(-1,1)), b=(1,0.5), f ~ N(0,1) seed 0,
     MGCNN with GMG-equivalent weights (V(2,2), omega 0.8, FW, bilinear), 4 levels,
     from u = 0 to relres 1e-10: identical iteration count to the oracle, every
@@ -130,7 +146,7 @@ def test_cfg0_gmg_equivalent_iterate_for_iterate(M):
     k = inputs.block_board_k(n, rng)
     f = inputs.normal_rhs(n, rng)
     b = (1.0, 0.5)
-    sv, sts, w, s = _gmg_solver(M, k, n, b)
+    sv, sts, w, s = _gmg_solver(M, k, n, b, input_diag=input_diag)
     u_o, it_o, hist_o, its_o = ogmg.stationary_solve(sts, f, None, 1e-10, 200, 2, 2, 0.8)
     u = np.zeros(n * n)
     st, it, hist = sv.solve(f.ravel().copy(), u, 1e-10, 200)
@@ -187,8 +203,9 @@ def test_argument_errors(M):
 
 
 # ---- mixed precision -------------------------------------------------------
+@pytest.mark.parametrize("cfg", list(CFGS))
 @pytest.mark.parametrize("C,nd,nu,n", [(8, 1, 1, 63), (8, 1, 1, 255), (4, 1, 1, 31), (13, 3, 2, 63), (16, 2, 1, 127)])
-def test_mixed_vcycle_error_vs_fp64_oracle(M, C, nd, nu, n):
+def test_mixed_vcycle_error_vs_fp64_oracle(M, C, nd, nu, n, cfg):
     """BF16 tensors carry 8 significant bits (unit roundoff 2^-9 = 2e-3); each
     layer rounds its output once and its products once, FP32 accumulation adds
     nothing visible.  Along the 2 (nu+1) L + 2 rounding steps of one cycle the
@@ -197,8 +214,8 @@ def test_mixed_vcycle_error_vs_fp64_oracle(M, C, nd, nu, n):
     k, f = problem(n, 20 + n)
     w = omg.random_weights(C, nd, nu, np.random.default_rng(7))
     sts = oop.level_stencils_div(k, (1.0, 0.5), num_levels(n))
-    e_ref = omg.solve_phase(w, omg.setup(w, sts), f)
-    sv = M.Solver(C, nd, nu, precision="mixed_bf16")
+    _, e_ref = oracle_B(w, sts, f, cfg)
+    sv = make_solver(M, C, nd, nu, cfg, precision="mixed_bf16")
     sv.set_weights(M.pack_weights(w, C, nd, nu))
     sv.setup(k.ravel().copy(), n)
     e = sv.vcycle(f.ravel().copy())
@@ -222,17 +239,18 @@ def test_mixed_gmg_equivalent_reaches_1e8_in_fp64(M):
     assert it <= it64 + 3
 
 
-def test_product_gmg_setup_matches_oracle_construction(M):
+@pytest.mark.parametrize("input_diag", [True, False])
+def test_product_gmg_setup_matches_oracle_construction(M, input_diag):
     """The library's own GMG-equivalent setup tensors and the binding's weight blob
     equal the oracle's independent construction; the solve then matches GMG."""
     n = 63
     k, f = problem(n, 8, "blocks")
     b = (0.7, -1.2)
     sts = oop.level_stencils_div(k, b, num_levels(n))
-    s_ref = omg.gmg_equivalent_setup(sts, 0.7)
+    s_ref = omg.gmg_equivalent_setup(sts, 0.7, input_diag=input_diag)
     w_ref = M.pack_weights(omg.gmg_equivalent_weights(2, 1), omg.GMG_CHANNELS, 3, 1)
     assert np.array_equal(M.gmg_weights(2, 1), w_ref)
-    sv = M.Solver(omg.GMG_CHANNELS, 3, 1, b=b)
+    sv = M.Solver(omg.GMG_CHANNELS, 3, 1, b=b, input_diag=input_diag)
     sv.set_weights(M.gmg_weights(2, 1))
     sv.setup_gmg(k.ravel().copy(), n, 0.7)
     assert relerr(sv.get_setup_tensors(), to_nhwc(s_ref)) <= 1e-15
@@ -250,10 +268,10 @@ def test_fused_and_per_layer_kernels_agree(M, n):
     k, f = problem(n, 30 + n)
     w = omg.random_weights(C, 1, 1, np.random.default_rng(12))
     sts = oop.level_stencils_div(k, (1.0, 0.5), num_levels(n))
-    e_ref = omg.solve_phase(w, omg.setup(w, sts), f)
+    _, e_ref = oracle_B(w, sts, f, "normalised_input")
     out = {}
     for fused in (1, 0):
-        sv = M.Solver(C, 1, 1, precision="mixed_bf16")
+        sv = make_solver(M, C, 1, 1, "normalised_input", precision="mixed_bf16")
         sv.set_option(sv.OPT_FUSED, fused)
         sv.set_weights(M.pack_weights(w, C, 1, 1))
         sv.setup(k.ravel().copy(), n)
