@@ -86,8 +86,10 @@ typedef struct {
   int up_layers;     /* layers in ResNetUp, >= 1                               */
   int precision;     /* MGCNN_PREC_*                                           */
   int pde;           /* MGCNN_PDE_*                                            */
-  int scale_by_diag; /* 1: each setup tensor is divided by a_C of its level's
-                        operator (Jacobi-like scaling); 0: the raw network output */
+  int scale_by_diag; /* scaling of each level's setup tensor (Algorithm 2 output):
+                        0: none; 1: divided by a_C of its level's operator
+                        (Jacobi-like D^{-1}); 2: multiplied by (h_l/h_1)^2 =
+                        4^(l-1), the coefficient-free level ratio of D^{-1}     */
   int input_diag;    /* 1: the solve network is applied to D^{-1} r, D = diag(A)
                         of the finest level (B r = Net(D^{-1} r)): the pointwise
                         analogue of the paper's normalisation of the stencil to

@@ -116,7 +116,13 @@ def setup_backward(weights: dict, stencils: list[Stencil], sbar: list[np.ndarray
     sizes = [st.n for st in stencils]
     cbar = [np.zeros_like(c) for c in keep["c"]]
     for l in reversed(range(L)):
-        zb = sbar[l] / stencils[l].aC if scale_by_diag else sbar[l].copy()
+        mode = int(scale_by_diag)
+        if mode == 1:
+            zb = sbar[l] / stencils[l].aC
+        elif mode == 2:
+            zb = sbar[l] * (stencils[0].n + 1.0) ** 2 / (stencils[l].n + 1.0) ** 2
+        else:
+            zb = sbar[l].copy()
         for i in reversed(range(mg.SETUP_LAYERS)):
             t = keep["t"][l][i]
             dpre = zb * (1.0 - t * t)

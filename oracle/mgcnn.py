@@ -17,9 +17,12 @@ no activation (P2), so B is linear in the right-hand side.
 Readings where the paper is silent (each is listed in the design notes):
 * setup input: the scale-free stencil [a_W, a_E, a_S, a_N]/a_C and
   log10(h^2 a_C) (Remark "Matrix coefficients as input"), F = 5;
-* setup output scaling: setup_out_l is divided by a_C of the level-l
-  rediscretised operator (k restricted as in operator.restrict_k), a Jacobi-like D^{-1} that gives B the
-  units of A^{-1}; `scale_by_diag=False` gives the unscaled form;
+* setup output scaling (`scale_by_diag`): 1 (True) divides setup_out_l by a_C
+  of the level-l rediscretised operator (k restricted as in
+  operator.restrict_k), a Jacobi-like D^{-1} that gives B the units of A^{-1};
+  2 multiplies it by (h_l / h_1)^2 = 4^(l-1), the coefficient-free part of that
+  ratio between levels (a coarse diagonal is 4x smaller per level), for use
+  with the normalised input below; 0 (False) leaves it unscaled;
 * the setup RCNN has its own weights, no bias; every setup layer is
   tanh(K z + b) + z (Eq. resnet_nonlinear), the last one included;
 * input normalisation: Sec. 2.5 removes the 1/h factor of the stencil so that
@@ -85,7 +88,13 @@ def setup(weights: dict, stencils: list[Stencil], scale_by_diag: bool = True, ke
             z = t + z
         zs.append(zl)
         ts.append(tl)
-        outs.append(z / stencils[l].aC if scale_by_diag else z)
+        mode = int(scale_by_diag)
+        if mode == 1:
+            outs.append(z / stencils[l].aC)
+        elif mode == 2:
+            outs.append(z * (spacing(stencils[l].n) / spacing(stencils[0].n)) ** 2)
+        else:
+            outs.append(z)
         if l < L - 1:
             c = cn.rcnn(c, weights["sw_R"])
     if keep is not None:

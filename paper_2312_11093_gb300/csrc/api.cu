@@ -196,7 +196,8 @@ Status run_setup_net(mgcnn_ctx* c, const T* W, T* const* out) {
       ConvArgs<T> a;
       a.x = zin; a.W = W + wl.sw + i * CC9; a.bias = W + wl.sb + (size_t)i * C;
       a.skip = zin; a.tanh_act = 1; a.y = zout; a.n = nl;
-      if (i == kSetupLayers - 1 && c->cfg.scale_by_diag) a.diag = c->op[l].as<double>();
+      if (i == kSetupLayers - 1 && c->cfg.scale_by_diag == 1) a.diag = c->op[l].as<double>();
+      if (i == kSetupLayers - 1 && c->cfg.scale_by_diag == 2) a.out_scale = (double)(1u << (2 * l));  // (h_l/h_1)^2
       MG_TRY(conv_same<T>(C, C, a, c->stream));
       zin = zout;
     }
@@ -374,6 +375,7 @@ int mgcnn_create(const mgcnn_config* cfg, mgcnn_ctx** out) {
       !std::isfinite(cfg->bx) || !std::isfinite(cfg->by))
     return MGCNN_ERR_ARG;
   if (cfg->precision == MGCNN_PREC_MIXED_BF16 && !mixed_channels_supported(cfg->channels)) return MGCNN_ERR_SIZE;
+  if (cfg->scale_by_diag < 0 || cfg->scale_by_diag > 2) return MGCNN_ERR_ARG;
   mgcnn_ctx* c = new (std::nothrow) mgcnn_ctx();
   if (!c) return MGCNN_ERR_NOMEM;
   c->cfg = *cfg;

@@ -455,6 +455,14 @@ Status vcycle_cp(mgcnn_ctx* c, const float* r32, const double* norm2, double* e,
 
 }  // namespace
 
+FusedWeights fused_weights(const mgcnn_ctx* c) {
+  const MixLayout ml = mix_layout(c);
+  const char* wb = c->wmix.as<char>();
+  return FusedWeights{reinterpret_cast<const uint32_t*>(wb + ml.down), reinterpret_cast<const uint32_t*>(wb + ml.up),
+                      reinterpret_cast<const uint32_t*>(wb + ml.R), reinterpret_cast<const float*>(wb + ml.w_in),
+                      reinterpret_cast<const float*>(wb + ml.w_out), reinterpret_cast<const float*>(wb + ml.w_P)};
+}
+
 Status mixed_set_weights(mgcnn_ctx* c) {
   if (c->cfg.precision != MGCNN_PREC_MIXED_BF16) return {};
   const int C = c->cfg.channels;

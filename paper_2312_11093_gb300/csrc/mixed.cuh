@@ -20,6 +20,22 @@ Status mixed_get_setup_level(mgcnn_ctx* c, int l, double* dst);
 Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega);
 void mixed_release(mgcnn_ctx* c);
 // mixed_fused.cu: fused level kernels (8 channels, one layer per ResNet)
+struct FusedLevels {
+  int L = 0, batch = 1;
+  int n[kMaxLevels] = {};
+  const __nv_bfloat16* s[kMaxLevels] = {};
+  __nv_bfloat16* xa[kMaxLevels] = {};
+  __nv_bfloat16* xb[kMaxLevels] = {};
+};
+struct FusedWeights {
+  const uint32_t *f_down, *f_up, *f_R;
+  const float *w_in, *w_out, *w_P;
+};
+Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
+                           const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
+                           mgcnn_ctx* prof_ctx);
+// Pointers into ctx->wmix for the fused kernels (valid after mixed_set_weights).
+FusedWeights fused_weights(const mgcnn_ctx* c);
 bool fused_supported(const mgcnn_ctx* c);
 Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
                         const uint32_t* f_down, const uint32_t* f_up, const uint32_t* f_R, const float* w_in,

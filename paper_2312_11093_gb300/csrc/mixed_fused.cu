@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
                                                   const float* __restrict__ w_in, const bf16* __restrict__ x0,
                                                   const bf16* __restrict__ s, const uint32_t* __restrict__ fK,
                                                   const uint32_t* __restrict__ fR, bf16* __restrict__ xdown,
-                                                  bf16* __restrict__ xc, int n) {
+                                                  bf16* __restrict__ xc, int n, const int* __restrict__ active) {
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
   constexpr int ZH = XH + 2, ZW = XW + 2;
   constexpr int RH = ZH + 2, RW = ZW + 2;
@@ -119,6 +119,21 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t N = (size_t)n * n;
+  // problem blockIdx.z of a batch of equal-size problems stored back to back
+  const size_t bz = blockIdx.z;
+  if (active && !active[bz]) return;
+  {
+    const size_t Nc = (size_t)((n - 1) / 2) * ((n - 1) / 2);
+    if (FIRST) {
+      r += bz * N;
+      norm2 += bz;
+    } else {
+      x0 += bz * N * 8;
+    }
+    s += bz * N * 8;
+    xdown += bz * N * 8;
+    if (HAS_R) xc += bz * Nc * 8;
+  }
 
   uint32_t wk[9], wr[9];
 #pragma unroll
@@ -229,7 +244,8 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
                                                 const float* __restrict__ wP, const bf16* __restrict__ s,
                                                 const uint32_t* __restrict__ fK, const float* __restrict__ w_out,
                                                 const double* __restrict__ norm2, const double* __restrict__ u_in,
-                                                bf16* __restrict__ xfin, double* __restrict__ u_out, int n) {
+                                                bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
+                                                const int* __restrict__ active) {
   constexpr int H = LAST ? 1 : 0;
   constexpr int OH = FH + 2 * H, OW = FW + 2 * H;
   constexpr int PH = OH + 2, PW = OW + 2;
@@ -244,6 +260,21 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
   const int pj0 = j0 - H - 1, pi0 = i0 - H - 1;      // global coords of P's corner
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nc = (n - 1) / 2;
+  const size_t bz = blockIdx.z;
+  if (active && !active[bz]) return;
+  {
+    const size_t N = (size_t)n * n, Nc = (size_t)nc * nc;
+    xdown += bz * N * 8;
+    s += bz * N * 8;
+    if (HAS_P) xcf += bz * Nc * 8;
+    if (LAST) {
+      norm2 += bz;
+      if (u_in) u_in += bz * N;
+      u_out += bz * N;
+    } else {
+      xfin += bz * N * 8;
+    }
+  }
   // coarse corner: the smallest J with 2J + 2 >= pj0
   const int cj0 = (pj0 - 2 >= 0) ? (pj0 - 2) / 2 : -((2 - pj0 + 1) / 2);
   const int ci0 = (pi0 - 2 >= 0) ? (pi0 - 2) / 2 : -((2 - pi0 + 1) / 2);
@@ -355,55 +386,73 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
 
 }  // namespace
 
+// One V-cycle with the fused level kernels (CP = 8) for a batch of `batch`
+// equal-size problems stored back to back: level l state in xa[l] (down state)
+// and xb[l] (restricted input, then final up state), setup tensors s[l];
+// r32/norm2/u/e per problem.  `active` (nullable, [batch]) skips converged problems.
+Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
+                           const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
+                           mgcnn_ctx* prof_ctx) {
+  const int L = fl.L;
+  auto grid_f = [&](int l) {
+    return dim3((fl.n[l] + FW - 1) / FW, (fl.n[l] + FH - 1) / FH, fl.batch);
+  };
+  for (int l = 0; l < L; ++l) {
+    const int nl = fl.n[l];
+    const bool first = l == 0, has_r = l + 1 < L;
+    const bf16* s = fl.s[l];
+    bf16* xc = has_r ? fl.xb[l + 1] : nullptr;
+    const int ps = (first && prof_ctx) ? prof_begin(prof_ctx, kProfDown0) : -1;
+    if (first && has_r)
+      down_kernel<true, true><<<grid_f(l), NT, 0, st>>>(r32, norm2, w.w_in, nullptr, s, w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    else if (first)
+      down_kernel<true, false><<<grid_f(l), NT, 0, st>>>(r32, norm2, w.w_in, nullptr, s, w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    else if (has_r)
+      down_kernel<false, true><<<grid_f(l), NT, 0, st>>>(r32, norm2, w.w_in, fl.xb[l], s, w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    else
+      down_kernel<false, false><<<grid_f(l), NT, 0, st>>>(r32, norm2, w.w_in, fl.xb[l], s, w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    MG_LAUNCH("down_kernel");
+    if (prof_ctx) prof_end(prof_ctx, ps);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const int nl = fl.n[l];
+    const bool last = l == 0, has_p = l + 1 < L;
+    const bf16* s = fl.s[l];
+    const bf16* xcf = has_p ? fl.xb[l + 1] : nullptr;
+    const int ps = (last && prof_ctx) ? prof_begin(prof_ctx, kProfUp0) : -1;
+    if (last && has_p)
+      up_kernel<true, true><<<grid_f(l), NT, 0, st>>>(fl.xa[l], xcf, w.w_P, s, w.f_up, w.w_out, norm2, u_skip, nullptr, e, nl, active);
+    else if (last)
+      up_kernel<true, false><<<grid_f(l), NT, 0, st>>>(fl.xa[l], xcf, w.w_P, s, w.f_up, w.w_out, norm2, u_skip, nullptr, e, nl, active);
+    else if (has_p)
+      up_kernel<false, true><<<grid_f(l), NT, 0, st>>>(fl.xa[l], xcf, w.w_P, s, w.f_up, w.w_out, norm2, u_skip, fl.xb[l], e, nl, active);
+    else
+      up_kernel<false, false><<<grid_f(l), NT, 0, st>>>(fl.xa[l], xcf, w.w_P, s, w.f_up, w.w_out, norm2, u_skip, fl.xb[l], e, nl, active);
+    MG_LAUNCH("up_kernel");
+    if (prof_ctx) prof_end(prof_ctx, ps);
+  }
+  return {};
+}
+
 bool fused_supported(const mgcnn_ctx* c) {
   return c->cp == 8 && c->wl.nu_d == 1 && c->wl.nu_u == 1;
 }
 
-// e = B r (u_skip == nullptr) or e = u_skip + B r, fused level kernels, CP = 8.
+// e = B r (u_skip == nullptr) or e = u_skip + B r for the context's single problem.
 Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
                         const uint32_t* f_down, const uint32_t* f_up, const uint32_t* f_R, const float* w_in,
                         const float* w_out, const float* w_P) {
-  cudaStream_t st = c->stream;
-  const int L = c->L;
-  // x_down[l] in x16a[l]; x_in[l] (l >= 1) and then x_fin[l] in x16b[l]
-  auto xa = [&](int l) { return c->x16a[l].as<bf16>(); };
-  auto xb = [&](int l) { return c->x16b[l].as<bf16>(); };
-  auto grid_f = [&](int l) { return dim3((c->lv[l].n + FW - 1) / FW, (c->lv[l].n + FH - 1) / FH); };
-  for (int l = 0; l < L; ++l) {
-    const int nl = c->lv[l].n;
-    const bool first = l == 0, has_r = l + 1 < L;
-    const bf16* s = c->s16[l].as<bf16>();
-    bf16* xc = has_r ? xb(l + 1) : nullptr;
-    const int ps = first ? prof_begin(c, kProfDown0) : -1;
-    if (first && has_r)
-      down_kernel<true, true><<<grid_f(l), NT, 0, st>>>(r32, norm2, w_in, nullptr, s, f_down, f_R, xa(l), xc, nl);
-    else if (first)
-      down_kernel<true, false><<<grid_f(l), NT, 0, st>>>(r32, norm2, w_in, nullptr, s, f_down, f_R, xa(l), xc, nl);
-    else if (has_r)
-      down_kernel<false, true><<<grid_f(l), NT, 0, st>>>(r32, norm2, w_in, xb(l), s, f_down, f_R, xa(l), xc, nl);
-    else
-      down_kernel<false, false><<<grid_f(l), NT, 0, st>>>(r32, norm2, w_in, xb(l), s, f_down, f_R, xa(l), xc, nl);
-    MG_LAUNCH("down_kernel");
-    prof_end(c, ps);
+  FusedLevels fl;
+  fl.L = c->L;
+  fl.batch = 1;
+  for (int l = 0; l < c->L; ++l) {
+    fl.n[l] = c->lv[l].n;
+    fl.s[l] = c->s16[l].as<bf16>();
+    fl.xa[l] = c->x16a[l].as<bf16>();
+    fl.xb[l] = c->x16b[l].as<bf16>();
   }
-  for (int l = L - 1; l >= 0; --l) {
-    const int nl = c->lv[l].n;
-    const bool last = l == 0, has_p = l + 1 < L;
-    const bf16* s = c->s16[l].as<bf16>();
-    const bf16* xcf = has_p ? xb(l + 1) : nullptr;
-    const int ps = last ? prof_begin(c, kProfUp0) : -1;
-    if (last && has_p)
-      up_kernel<true, true><<<grid_f(l), NT, 0, st>>>(xa(l), xcf, w_P, s, f_up, w_out, norm2, u_skip, nullptr, e, nl);
-    else if (last)
-      up_kernel<true, false><<<grid_f(l), NT, 0, st>>>(xa(l), xcf, w_P, s, f_up, w_out, norm2, u_skip, nullptr, e, nl);
-    else if (has_p)
-      up_kernel<false, true><<<grid_f(l), NT, 0, st>>>(xa(l), xcf, w_P, s, f_up, w_out, norm2, u_skip, xb(l), e, nl);
-    else
-      up_kernel<false, false><<<grid_f(l), NT, 0, st>>>(xa(l), xcf, w_P, s, f_up, w_out, norm2, u_skip, xb(l), e, nl);
-    MG_LAUNCH("up_kernel");
-    prof_end(c, ps);
-  }
-  return {};
+  FusedWeights w{f_down, f_up, f_R, w_in, w_out, w_P};
+  return fused_vcycle_levels(fl, r32, norm2, e, u_skip, w, nullptr, c->stream, c);
 }
 
 }  // namespace mgcnn

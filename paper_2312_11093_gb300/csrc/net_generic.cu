@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(128) conv_same_kernel(ConvArgs<T> a) {
     if (a.tanh_act) v = dev_tanh<T>(v);
     if (a.skip) v += a.skip[(size_t)p * CO + co];
     if (a.diag) v = (T)((double)v / a.diag[p]);
+    if (a.out_scale != 1.0) v = (T)((double)v * a.out_scale);
     a.y[(size_t)p * CO + co] = v;
   }
 }

@@ -45,6 +45,7 @@ struct ConvArgs {
   const T* bias = nullptr;  // optional [CO]
   const T* skip = nullptr;  // optional residual input [N][CO], added after the activation
   const double* diag = nullptr;  // optional: divide the result by diag[p] (FP64 a_C)
+  double out_scale = 1.0;        // multiply the result (after skip) by this constant
   T* y = nullptr;           // output [N][CO]
   int n = 0;                // grid side
   int tanh_act = 0;         // 1: y = tanh(conv + bias) (+ skip)

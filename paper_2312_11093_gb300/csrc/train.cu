@@ -314,13 +314,13 @@ struct Trainer {
         add(buf(g.t[l][i]), z, znext, g.B * N(l) * C);
         if (i + 1 < kSetupLayers) z = znext;
       }
-      // s_l = z_4 / a_C (or z_4)
-      if (c->cfg.scale_by_diag) {
+      // s_l = z_4 / a_C, z_4 (h_l/h_1)^2, or z_4
+      if (c->cfg.scale_by_diag == 1) {
         div_diag_kernel<T><<<grid_for(g.B * N(l) * C, 256), 256, 0, st>>>(buf(g.tmp[l]), g.op[l].as<double>(),
                                                                            buf(g.s[l]), N(l), C, g.B);
         MG_LAUNCH("div_diag_kernel");
       } else {
-        MG_CUDA(cudaMemcpyAsync(g.s[l].p, g.tmp[l].p, g.B * N(l) * C * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        scale_copy(buf(g.tmp[l]), buf(g.s[l]), g.B * N(l) * C, level_factor(l));
       }
       if (l + 1 < g.L) MG_TRY(rcnn<T>(C, buf(g.c[l]), W + wl.sw_R, buf(g.c[l + 1]), nl(l), st, g.B));
     }
@@ -417,6 +417,9 @@ struct Trainer {
   }
 
   void mul(const T* a, const T* b, T* out, size_t count);
+  void scale_copy(const T* a, T* out, size_t count, double factor);
+  // (h_l / h_1)^2 for the grid setup scaling, else 1
+  double level_factor(int l) const { return c->cfg.scale_by_diag == 2 ? (double)(1u << (2 * l)) : 1.0; }
 
   // B^T e_bar at input r (intermediates from solve_forward_full); accumulates weight
   // grads and s_bar; writes r_bar.
@@ -466,11 +469,11 @@ struct Trainer {
     for (int l = g.L - 1; l >= 0; --l) {
       const size_t cnt = g.B * N(l) * C;
       T* zb = buf(g.zb[l]);
-      if (c->cfg.scale_by_diag) {
+      if (c->cfg.scale_by_diag == 1) {
         div_diag_kernel<T><<<grid_for(cnt, 256), 256, 0, st>>>(buf(g.sbar[l]), g.op[l].as<double>(), zb, N(l), C, g.B);
         MG_LAUNCH("div_diag_kernel");
       } else {
-        MG_CUDA(cudaMemcpyAsync(zb, g.sbar[l].p, cnt * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        scale_copy(buf(g.sbar[l]), zb, cnt, level_factor(l));
       }
       for (int i = kSetupLayers - 1; i >= 0; --i) {
         T* d = buf(g.tmp[l]);
@@ -507,6 +510,18 @@ template <typename T>
 __global__ void mul_kernel(const T* a, const T* b, T* out, size_t count) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < count) out[p] = a[p] * b[p];
+}
+
+template <typename T>
+__global__ void scale_copy_kernel(const T* __restrict__ a, T* __restrict__ out, size_t count, T factor) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < count) out[p] = a[p] * factor;
+}
+
+template <typename T>
+void Trainer<T>::scale_copy(const T* a, T* out, size_t count, double factor) {
+  scale_copy_kernel<T><<<grid_for(count, 256), 256, 0, st>>>(a, out, count, (T)factor);
+  count_launch();
 }
 
 template <typename T>

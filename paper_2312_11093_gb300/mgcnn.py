@@ -176,7 +176,7 @@ class Solver:
     """One MGCNN context: weights, a setup for one coefficient field, solves."""
 
     def __init__(self, channels: int = 8, down_layers: int = 1, up_layers: int = 1, precision: str = "fp64",
-                 pde: str = "div", scale_by_diag: bool = False, input_diag: bool = True, levels: int = 0,
+                 pde: str = "div", scale_by_diag: int = 0, input_diag: bool = True, levels: int = 0,
                  b=(1.0, 0.5), stream=None):
         """Defaults are the learned network's configuration: unscaled setup tensors and
         the network applied to D^{-1} r (see include/mgcnn.h, mgcnn_config)."""

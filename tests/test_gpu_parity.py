@@ -80,7 +80,7 @@ def test_residual_and_norm(M):
 
 
 # network configurations: (scale_by_diag, input_diag)
-CFGS = {"scaled_setup": (True, False), "normalised_input": (False, True)}
+CFGS = {"scaled_setup": (1, False), "normalised_input": (0, True), "grid_setup": (2, True)}
 
 
 def oracle_B(w, sts, r, cfg):

@@ -35,7 +35,7 @@ def _problems(sizes, seed, b=(1.0, 0.5)):
     return gpu, ora
 
 
-CFGS = {"scaled_setup": (True, False), "normalised_input": (False, True)}
+CFGS = {"scaled_setup": (1, False), "normalised_input": (0, True), "grid_setup": (2, True)}
 
 
 def _solver(M, w, C, nd, nu, precision="fp64", cfg="normalised_input"):

@@ -39,7 +39,7 @@ def test_dot_product_transpose():
     assert abs(lhs - np.sum(v * btw)) <= 1e-12 * abs(lhs)
 
 
-@pytest.mark.parametrize("scale_by_diag,input_diag", [(True, False), (False, True)])
+@pytest.mark.parametrize("scale_by_diag,input_diag", [(1, False), (0, True), (2, True)])
 def test_central_differences(scale_by_diag, input_diag):
     probs = _problems([7, 15], 3)
     rng = np.random.default_rng(4)
@@ -66,7 +66,7 @@ def test_central_differences(scale_by_diag, input_diag):
     assert checked >= 25
 
 
-def _torch_loss(wt, probs, K, input_diag=False):
+def _torch_loss(wt, probs, K, input_diag=False, setup_scale=1):
     total = 0.0
     for sts, f in probs:
         aC = [torch.from_numpy(st.aC) for st in sts]
@@ -77,7 +77,12 @@ def _torch_loss(wt, probs, K, input_diag=False):
             z = c
             for i in range(4):
                 z = torch.tanh(F.conv2d(z, wt["sw"][i], wt["sb"][i], padding=1)) + z
-            s.append(z if input_diag else z / aC[l])
+            if setup_scale == 1:
+                s.append(z / aC[l])
+            elif setup_scale == 2:
+                s.append(z * 4.0 ** l)
+            else:
+                s.append(z)
             c = F.conv2d(c, wt["sw_R"], stride=2)
         A = sts[0]
         coef = [torch.from_numpy(a) for a in (A.aC, A.aW, A.aE, A.aS, A.aN)]
@@ -112,14 +117,14 @@ def _torch_loss(wt, probs, K, input_diag=False):
     return total / len(probs)
 
 
-@pytest.mark.parametrize("input_diag", [False, True])
-def test_against_torch_autograd(input_diag):
+@pytest.mark.parametrize("setup_scale,input_diag", [(1, False), (0, True), (2, True)])
+def test_against_torch_autograd(setup_scale, input_diag):
     probs = _problems([15, 31], 5)
     w = mg.random_weights(4, 2, 1, np.random.default_rng(6), scale=0.5)
     K = 3
-    L0, g = adj.loss_and_grad(w, probs, K, scale_by_diag=not input_diag, input_diag=input_diag)
+    L0, g = adj.loss_and_grad(w, probs, K, scale_by_diag=setup_scale, input_diag=input_diag)
     wt = {k: torch.tensor(v, requires_grad=True) for k, v in w.items()}
-    Lt = _torch_loss(wt, probs, K, input_diag)
+    Lt = _torch_loss(wt, probs, K, input_diag, setup_scale)
     Lt.backward()
     assert np.isclose(L0, Lt.item(), rtol=1e-12)
     for k in w:
