@@ -194,6 +194,27 @@ int mgcnn_vcycle(mgcnn_ctx* ctx, const double* r, double* e);
 int mgcnn_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit,
                 int* iters, double* relres);
 
+/* ---- Batched solves ------------------------------------------------------------
+ * Many coefficient fields and right-hand sides of uneven grid sizes at once:
+ * the setup phase (Sec. 3.2) for every field, then the stationary iteration
+ * (Eq. 1) for every problem, each stopping on its own tolerance test.
+ * Problems of equal n are grouped; one cycle of the whole batch (residual,
+ * convergence test and V-cycle of every still-active problem) is one CUDA
+ * graph, replayed until no problem is active, with one 4-byte readback per
+ * cycle.  The level kernels' tile shapes are chosen per grid size by timing
+ * (autotuned in mgcnn_setup_batched).  Requires MIXED_BF16, 8 channels, one
+ * layer per ResNet and the divergence form; otherwise ERR_SIZE.
+ * coeff[i]: nodal k of problem i, (n[i]+2)^2 doubles; host or device; copied. */
+int mgcnn_setup_batched(mgcnn_ctx* ctx, int nprob, const double* const* coeff, const int* n);
+
+/* rhs[i], u[i]: n[i]^2 doubles (host or device); u[i] is the initial guess on
+ * entry and the last iterate on return.  iters[i] (may be NULL) receives the
+ * cycles applied, relres[i] (may be NULL) the last ||r||/||f||, status[i]
+ * (may be NULL) OK / NOT_CONVERGED / ERR_NONFINITE per problem.  Returns OK if
+ * every problem converged, else the first error, else NOT_CONVERGED. */
+int mgcnn_solve_batched(mgcnn_ctx* ctx, int nprob, const double* const* rhs, double* const* u, double tol,
+                        int maxit, int* iters, double* relres, int* status);
+
 /* ---- Training (Sec. 3.4, Eq. loss) ------------------------------------------
  * Loss of a batch of problems after K stationary cycles from u = 0,
  *     r_0 = f,  r_{k+1} = r_k - A B(r_k),   L = (1/N) sum_i ||r_K,i||^2 / ||f_i||^2

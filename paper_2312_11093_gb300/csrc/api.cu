@@ -11,6 +11,7 @@
 #include "ops.cuh"
 #include "mixed.cuh"
 #include "train.cuh"
+#include "batch.cuh"
 
 using namespace mgcnn;
 
@@ -56,6 +57,7 @@ Status ensure(DevBuf& b, size_t bytes) {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 int prof_begin(mgcnn_ctx* c, int kind) {
   if (!c->prof) return -1;
@@ -275,6 +277,7 @@ Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
   const int L = c->cfg.levels > 0 ? c->cfg.levels : Lmax;
   if (L > Lmax) return make_status(MGCNN_ERR_SIZE, "%d levels requested, n=%d allows %d", L, n, Lmax);
   c->have_setup = false;
+  if (c->n != n) c->tuned = false;   // tile shapes are tuned per grid size
   c->n = n;
   c->L = L;
   c->lv.assign(L, Level{});
@@ -411,6 +414,7 @@ void mgcnn_destroy(mgcnn_ctx* c) {
   release(c->r32); release(c->partial); release(c->scalars);
   mixed_release(c);
   train_release(c);
+  batch_release(c);
   for (size_t i = 0; i < c->ev_start.size(); ++i) {
     cudaEventDestroy(c->ev_start[i]);
     cudaEventDestroy(c->ev_stop[i]);
@@ -696,6 +700,17 @@ int mgcnn_get_weights(mgcnn_ctx* c, double* w, size_t count) {
     return sync(c);
   }();
   return finish(c, st);
+}
+
+int mgcnn_setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* n) {
+  if (!c || !coeff || !n) return MGCNN_ERR_ARG;
+  return finish(c, setup_batched(c, nprob, coeff, n));
+}
+
+int mgcnn_solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol, int maxit,
+                        int* iters, double* relres, int* status) {
+  if (!c || !rhs || !u || maxit < 0 || !(tol >= 0.0)) return MGCNN_ERR_ARG;
+  return finish(c, solve_batched(c, nprob, rhs, u, tol, maxit, iters, relres, status));
 }
 
 int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {

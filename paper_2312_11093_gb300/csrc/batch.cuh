@@ -1,0 +1,35 @@
+// Batched setup / solve of many problems of uneven grid sizes (batch.cu).
+#pragma once
+
+#include "common.cuh"
+#include "mixed.cuh"
+
+namespace mgcnn {
+
+// Problems of one grid size, stored back to back in every buffer.
+struct BatchClass {
+  int n = 0, B = 0, L = 0;
+  std::vector<int> members;                    // caller's problem indices
+  int nl[kMaxLevels] = {};
+  DevBuf coef;                                 // [2][B][(n+2)^2] nodal k, level ping-pong
+  DevBuf op[kMaxLevels];                       // [B][5][N_l] FP64 operators
+  DevBuf s16[kMaxLevels], xa[kMaxLevels], xb[kMaxLevels];  // [B][N_l][8] BF16
+  DevBuf dinv32, r32;                          // [B][N] FP32
+  DevBuf f, u;                                 // [B][N] FP64
+  DevBuf partial;                              // [B][blocks]
+  DevBuf rn2, fn2;                             // [B]
+  DevBuf state;                                // int [3][B]: active, iters, status
+  DevBuf hist;                                 // [B][maxit + 1]
+  DevBuf feat, ca, cb, za, zb, s32;            // FP32 setup scratch
+  DevBuf scratch;                              // [B][N] FP64 (autotuning output)
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  FusedLevels fl;
+};
+
+void batch_release(mgcnn_ctx* c);
+Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* ns);
+Status solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol, int maxit,
+                     int* iters, double* relres, int* status);
+
+}  // namespace mgcnn

@@ -20,6 +20,7 @@ constexpr int kSetupLayers = 4;   // NonLinearResNet depth (Sec. 3.2: "four laye
 constexpr int kMaxLevels = 13;    // n <= 16383
 constexpr int kMaxSweeps = 16;    // layers per ResNetDown / ResNetUp
 struct TrainGroup;
+struct BatchClass;
 
 // Status carried through the library; converted to the ABI code at the boundary.
 struct Status {
@@ -94,6 +95,8 @@ struct mgcnn_ctx {
   // mixed-precision path (mixed.cu)
   int cp = 0;                             // channels padded for the tensor cores (8 or 16)
   int fused = 1;                          // use the fused level kernels when they apply
+  int tile_var[2][mgcnn::kMaxLevels] = {};  // autotuned tile variants (down, up) per level
+  bool tuned = false;                       // set by the first solve after a setup
   mgcnn::DevBuf x16a[mgcnn::kMaxLevels];  // BF16 state ping-pong, [n_l^2][cp]
   mgcnn::DevBuf x16b[mgcnn::kMaxLevels];
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
@@ -103,6 +106,17 @@ struct mgcnn_ctx {
   std::vector<mgcnn::TrainGroup> groups;
   mgcnn::DevBuf grad, wT, adam_m, adam_v;
   long long adam_t = 0;
+  // batched solves (batch.cu)
+  std::vector<mgcnn::BatchClass> bcls;
+  int bn = 0, bmaxit = -1;
+  bool bready = false;
+  std::vector<int> bcls_of, bidx_of;
+  cudaStream_t bstream = nullptr;
+  cudaEvent_t bfork = nullptr;
+  cudaGraphExec_t bgraph = nullptr;
+  long long bgraph_kernels = 0;
+  mgcnn::DevBuf bparams, bcount;
+  int* h_bcount = nullptr;
   // optional per-kernel timing (mgcnn_profile)
   int prof = 0;
   std::vector<cudaEvent_t> ev_start, ev_stop;
@@ -127,6 +141,7 @@ bool is_device_pointer(const void* p);
 
 // Every kernel launch site is followed by MG_LAUNCH, which also counts it.
 void count_launch();
+void add_launches(long long k);   // kernels launched through a CUDA graph
 #define MG_LAUNCH(what)                                            \
   do {                                                             \
     ::mgcnn::count_launch();                                       \

@@ -520,6 +520,12 @@ Status setup_mixed(mgcnn_ctx* c) {
   return {};
 }
 
+Status pad_setup_bf16(const float* src, bf16* dst, size_t N, int C, int cp, cudaStream_t st) {
+  pad_to_bf16_kernel<float><<<grid_for(N * cp, 256), 256, 0, st>>>(src, dst, N, C, cp);
+  MG_LAUNCH("pad_to_bf16_kernel");
+  return {};
+}
+
 Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega) {
   const size_t N = c->lv[l].N();
   const int cp = c->cp;

@@ -20,9 +20,12 @@ Status mixed_get_setup_level(mgcnn_ctx* c, int l, double* dst);
 Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega);
 void mixed_release(mgcnn_ctx* c);
 // mixed_fused.cu: fused level kernels (8 channels, one layer per ResNet)
+constexpr int kFusedVariants = 3;        // tile shapes 16x32, 8x32, 16x16
 struct FusedLevels {
   int L = 0, batch = 1;
   int n[kMaxLevels] = {};
+  int var_down[kMaxLevels] = {};         // tile variant per level (autotuned)
+  int var_up[kMaxLevels] = {};
   const __nv_bfloat16* s[kMaxLevels] = {};
   __nv_bfloat16* xa[kMaxLevels] = {};
   __nv_bfloat16* xb[kMaxLevels] = {};
@@ -34,9 +37,13 @@ struct FusedWeights {
 Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
                            const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
                            mgcnn_ctx* prof_ctx);
+Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, double* scratch,
+                      const FusedWeights& w, cudaStream_t st, int reps);
 // Pointers into ctx->wmix for the fused kernels (valid after mixed_set_weights).
 FusedWeights fused_weights(const mgcnn_ctx* c);
 bool fused_supported(const mgcnn_ctx* c);
+// [N][C] FP32 -> [N][cp] BF16, zero padded
+Status pad_setup_bf16(const float* src, __nv_bfloat16* dst, size_t N, int C, int cp, cudaStream_t st);
 Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
                         const uint32_t* f_down, const uint32_t* f_up, const uint32_t* f_R, const float* w_in,
                         const float* w_out, const float* w_P);

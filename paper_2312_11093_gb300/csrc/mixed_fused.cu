@@ -33,7 +33,8 @@ using bf162 = __nv_bfloat162;
 
 namespace {
 
-constexpr int FH = 16, FW = 32;      // fine tile owned by a block
+// Fine tile owned by a block: FH x FW, a template parameter chosen per level
+// size by the autotuner (variants below).
 constexpr int NT = 256;              // threads per block (8 warps)
 constexpr int NW = NT / 32;
 
@@ -102,7 +103,7 @@ __device__ __forceinline__ double alpha_of(const double* norm2, size_t N) {
 //   X (layer output kept):   rows 0..XH-1, cols 0..XW-1 (XH = 16 + R, XW = 32 + R)
 //   Z (layer input, halo 1): rows -1..XH,  cols -1..XW
 //   Rg (residual, halo 2):   rows -2..XH+1, cols -2..XW+1   (finest level only)
-template <bool FIRST, bool HAS_R>
+template <int FH, int FW, bool FIRST, bool HAS_R>
 __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, const double* __restrict__ norm2,
                                                   const float* __restrict__ w_in, const bf16* __restrict__ x0,
                                                   const bf16* __restrict__ s, const uint32_t* __restrict__ fK,
@@ -217,15 +218,21 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   }
   if constexpr (HAS_R) {
     __syncthreads();
-    // restriction: coarse (J0 + r, I0 + c), r < 8, c < 16, taps (2r + a, 2c + b) of X
+    // restriction: coarse (J0 + cr, I0 + cc) over the CH x CW coarse tile, taps
+    // (2 cr + a, 2 cc + b) of X; strips of 16 coarse pixels in row-major order
+    constexpr int CH = FH / 2, CW = FW / 2;
     const int nc = (n - 1) / 2;
-    const int J0 = blockIdx.y * (FH / 2), I0 = blockIdx.x * (FW / 2);
-    for (int st = warp; st < 8; st += NW) {
+    const int J0 = blockIdx.y * CH, I0 = blockIdx.x * CW;
+    for (int st = warp; st < CH * CW / 16; st += NW) {
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      strip_conv(xd, wr, [&](int m, int tap) { return (2 * st + tap / 3) * XW + 2 * m + tap % 3; }, acc);
+      strip_conv(xd, wr, [&](int m, int tap) {
+        const int p = st * 16 + m, cr = p / CW, cc = p - cr * CW;
+        return (2 * cr + tap / 3) * XW + 2 * cc + tap % 3;
+      }, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int J = J0 + st, I = I0 + g + 8 * h;
+        const int p = st * 16 + g + 8 * h, cr = p / CW, cc = p - cr * CW;
+        const int J = J0 + cr, I = I0 + cc;
         if (J < nc && I < nc)
           reinterpret_cast<uint32_t*>(xc + ((size_t)J * nc + I) * 8)[q] = f2bf(acc[2 * h], acc[2 * h + 1]);
       }
@@ -239,7 +246,7 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
 //   O (layer output):  rows -H..15+H, cols -H..31+H        (OH x OW)
 //   P (layer input x_pre = x_down + TCNN(x_c)): O plus halo 1  (PH x PW)
 //   coarse rows/cols J: floor((j0 - H - 1) / 2) - 1 .. , enough for P
-template <bool LAST, bool HAS_P>
+template <int FH, int FW, bool LAST, bool HAS_P>
 __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, const bf16* __restrict__ xcf,
                                                 const float* __restrict__ wP, const bf16* __restrict__ s,
                                                 const uint32_t* __restrict__ fK, const float* __restrict__ w_out,
@@ -384,54 +391,122 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
   }
 }
 
+// Tile variants (FH x FW): 0 = 16 x 32, 1 = 8 x 32, 2 = 16 x 16.
+template <int FH, int FW>
+Status launch_down(int l, const FusedLevels& fl, const float* r32, const double* norm2, const FusedWeights& w,
+                   const int* active, cudaStream_t st) {
+  const int nl = fl.n[l];
+  const bool first = l == 0, has_r = l + 1 < fl.L;
+  const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
+  __nv_bfloat16* xc = has_r ? fl.xb[l + 1] : nullptr;
+  if (first && has_r)
+    down_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(r32, norm2, w.w_in, nullptr, fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+  else if (first)
+    down_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(r32, norm2, w.w_in, nullptr, fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+  else if (has_r)
+    down_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(r32, norm2, w.w_in, fl.xb[l], fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+  else
+    down_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(r32, norm2, w.w_in, fl.xb[l], fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+  MG_LAUNCH("down_kernel");
+  return {};
+}
+
+template <int FH, int FW>
+Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, const double* u_skip,
+                 const FusedWeights& w, const int* active, cudaStream_t st) {
+  const int nl = fl.n[l];
+  const bool last = l == 0, has_p = l + 1 < fl.L;
+  const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
+  const __nv_bfloat16* xcf = has_p ? fl.xb[l + 1] : nullptr;
+  if (last && has_p)
+    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.w_P, fl.s[l], w.f_up, w.w_out, norm2, u_skip, nullptr, e, nl, active);
+  else if (last)
+    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.w_P, fl.s[l], w.f_up, w.w_out, norm2, u_skip, nullptr, e, nl, active);
+  else if (has_p)
+    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.w_P, fl.s[l], w.f_up, w.w_out, norm2, u_skip, fl.xb[l], e, nl, active);
+  else
+    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.w_P, fl.s[l], w.f_up, w.w_out, norm2, u_skip, fl.xb[l], e, nl, active);
+  MG_LAUNCH("up_kernel");
+  return {};
+}
+
+Status launch_down_variant(int v, int l, const FusedLevels& fl, const float* r32, const double* norm2,
+                           const FusedWeights& w, const int* active, cudaStream_t st) {
+  switch (v) {
+    case 1: return launch_down<8, 32>(l, fl, r32, norm2, w, active, st);
+    case 2: return launch_down<16, 16>(l, fl, r32, norm2, w, active, st);
+    default: return launch_down<16, 32>(l, fl, r32, norm2, w, active, st);
+  }
+}
+
+Status launch_up_variant(int v, int l, const FusedLevels& fl, const double* norm2, double* e, const double* u_skip,
+                         const FusedWeights& w, const int* active, cudaStream_t st) {
+  switch (v) {
+    case 1: return launch_up<8, 32>(l, fl, norm2, e, u_skip, w, active, st);
+    case 2: return launch_up<16, 16>(l, fl, norm2, e, u_skip, w, active, st);
+    default: return launch_up<16, 32>(l, fl, norm2, e, u_skip, w, active, st);
+  }
+}
+
 }  // namespace
 
 // One V-cycle with the fused level kernels (CP = 8) for a batch of `batch`
 // equal-size problems stored back to back: level l state in xa[l] (down state)
 // and xb[l] (restricted input, then final up state), setup tensors s[l];
-// r32/norm2/u/e per problem.  `active` (nullable, [batch]) skips converged problems.
+// r32/norm2/u/e per problem.  `active` (nullable, [batch]) skips converged
+// problems.  fl.var_down / fl.var_up pick each level's tile variant.
 Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
                            const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
                            mgcnn_ctx* prof_ctx) {
   const int L = fl.L;
-  auto grid_f = [&](int l) {
-    return dim3((fl.n[l] + FW - 1) / FW, (fl.n[l] + FH - 1) / FH, fl.batch);
-  };
   for (int l = 0; l < L; ++l) {
-    const int nl = fl.n[l];
-    const bool first = l == 0, has_r = l + 1 < L;
-    const bf16* s = fl.s[l];
-    bf16* xc = has_r ? fl.xb[l + 1] : nullptr;
-    const int ps = (first && prof_ctx) ? prof_begin(prof_ctx, kProfDown0) : -1;
-    if (first && has_r)
-      down_kernel<true, true><<<grid_f(l), NT, 0, st>>>(r32, norm2, w.w_in, nullptr, s, w.f_down, w.f_R, fl.xa[l], xc, nl, active);
-    else if (first)
-      down_kernel<true, false><<<grid_f(l), NT, 0, st>>>(r32, norm2, w.w_in, nullptr, s, w.f_down, w.f_R, fl.xa[l], xc, nl, active);
-    else if (has_r)
-      down_kernel<false, true><<<grid_f(l), NT, 0, st>>>(r32, norm2, w.w_in, fl.xb[l], s, w.f_down, w.f_R, fl.xa[l], xc, nl, active);
-    else
-      down_kernel<false, false><<<grid_f(l), NT, 0, st>>>(r32, norm2, w.w_in, fl.xb[l], s, w.f_down, w.f_R, fl.xa[l], xc, nl, active);
-    MG_LAUNCH("down_kernel");
+    const int ps = (l == 0 && prof_ctx) ? prof_begin(prof_ctx, kProfDown0) : -1;
+    MG_TRY(launch_down_variant(fl.var_down[l], l, fl, r32, norm2, w, active, st));
     if (prof_ctx) prof_end(prof_ctx, ps);
   }
   for (int l = L - 1; l >= 0; --l) {
-    const int nl = fl.n[l];
-    const bool last = l == 0, has_p = l + 1 < L;
-    const bf16* s = fl.s[l];
-    const bf16* xcf = has_p ? fl.xb[l + 1] : nullptr;
-    const int ps = (last && prof_ctx) ? prof_begin(prof_ctx, kProfUp0) : -1;
-    if (last && has_p)
-      up_kernel<true, true><<<grid_f(l), NT, 0, st>>>(fl.xa[l], xcf, w.w_P, s, w.f_up, w.w_out, norm2, u_skip, nullptr, e, nl, active);
-    else if (last)
-      up_kernel<true, false><<<grid_f(l), NT, 0, st>>>(fl.xa[l], xcf, w.w_P, s, w.f_up, w.w_out, norm2, u_skip, nullptr, e, nl, active);
-    else if (has_p)
-      up_kernel<false, true><<<grid_f(l), NT, 0, st>>>(fl.xa[l], xcf, w.w_P, s, w.f_up, w.w_out, norm2, u_skip, fl.xb[l], e, nl, active);
-    else
-      up_kernel<false, false><<<grid_f(l), NT, 0, st>>>(fl.xa[l], xcf, w.w_P, s, w.f_up, w.w_out, norm2, u_skip, fl.xb[l], e, nl, active);
-    MG_LAUNCH("up_kernel");
+    const int ps = (l == 0 && prof_ctx) ? prof_begin(prof_ctx, kProfUp0) : -1;
+    MG_TRY(launch_up_variant(fl.var_up[l], l, fl, norm2, e, u_skip, w, active, st));
     if (prof_ctx) prof_end(prof_ctx, ps);
   }
   return {};
+}
+
+// Autotuner: for every level, time each tile variant of the down and up kernels
+// (CUDA events, `reps` launches after one warm-up launch) on the real buffers
+// and keep the fastest.  The up kernel of the finest level writes its FP64
+// output to `scratch` (n_0^2 x batch doubles) so that no caller data changes.
+Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, double* scratch,
+                      const FusedWeights& w, cudaStream_t st, int reps) {
+  cudaEvent_t e0, e1;
+  MG_CUDA(cudaEventCreate(&e0));
+  MG_CUDA(cudaEventCreate(&e1));
+  Status result;
+  for (int l = 0; l < fl.L && result.ok(); ++l) {
+    float best_d = 1e30f, best_u = 1e30f;
+    for (int v = 0; v < kFusedVariants && result.ok(); ++v) {
+      float t = 0.f;
+      result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st);
+      if (!result.ok()) break;
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < reps && result.ok(); ++k) result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t, e0, e1);
+      if (t < best_d) { best_d = t; fl.var_down[l] = v; }
+      result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st);
+      if (!result.ok()) break;
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < reps && result.ok(); ++k) result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t, e0, e1);
+      if (t < best_u) { best_u = t; fl.var_up[l] = v; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return result;
 }
 
 bool fused_supported(const mgcnn_ctx* c) {
@@ -452,6 +527,20 @@ Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, dou
     fl.xb[l] = c->x16b[l].as<bf16>();
   }
   FusedWeights w{f_down, f_up, f_R, w_in, w_out, w_P};
+  if (!c->tuned) {
+    // first V-cycle after a setup: time the tile variants per level (output to
+    // the context's scratch vector, so no caller data changes), keep the fastest
+    MG_TRY(fused_autotune(fl, r32, norm2, c->e.as<double>(), w, c->stream, 3));
+    for (int l = 0; l < c->L; ++l) {
+      c->tile_var[0][l] = fl.var_down[l];
+      c->tile_var[1][l] = fl.var_up[l];
+    }
+    c->tuned = true;
+  }
+  for (int l = 0; l < c->L; ++l) {
+    fl.var_down[l] = c->tile_var[0][l];
+    fl.var_up[l] = c->tile_var[1][l];
+  }
   return fused_vcycle_levels(fl, r32, norm2, e, u_skip, w, nullptr, c->stream, c);
 }
 

@@ -17,6 +17,8 @@ __global__ void restrict_k_kernel(const double* __restrict__ k, double* __restri
   const int mc = (m + 1) / 2;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= mc * mc) return;
+  k += (size_t)blockIdx.y * m * m;      // problem blockIdx.y of a batch stored back to back
+  kc += (size_t)blockIdx.y * mc * mc;
   const int J = p / mc, I = p - J * mc;
   const double w[3] = {1.0, 2.0, 1.0};
   double num = 0.0, den = 0.0;
@@ -32,9 +34,9 @@ __global__ void restrict_k_kernel(const double* __restrict__ k, double* __restri
   kc[p] = exp(num / den);
 }
 
-Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st) {
+Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch) {
   const int mc = (m + 1) / 2;
-  restrict_k_kernel<<<grid_for((size_t)mc * mc, 256), 256, 0, st>>>(k, kc, m);
+  restrict_k_kernel<<<dim3(grid_for((size_t)mc * mc, 256), batch), 256, 0, st>>>(k, kc, m);
   MG_LAUNCH("restrict_k_kernel");
   return {};
 }
@@ -67,6 +69,8 @@ __global__ void stencil_div_kernel(const double* __restrict__ k, double* __restr
   if (p >= (int)N) return;
   const int j = p / n, i = p - j * n;
   const int m = n + 2;
+  k += (size_t)blockIdx.y * m * m;
+  op += (size_t)blockIdx.y * 5 * N;
   const double h = 1.0 / (n + 1);
   const double ih2 = 1.0 / (h * h);
   const double kc = k[(size_t)(j + 1) * m + (i + 1)];
@@ -85,8 +89,8 @@ __global__ void stencil_div_kernel(const double* __restrict__ k, double* __restr
   op[p] = (kw + ke + ks + kn) * ih2 + (fabs(bx) + fabs(by)) / h;
 }
 
-Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st) {
-  stencil_div_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(k, op, n, bx, by);
+Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st, int batch) {
+  stencil_div_kernel<<<dim3(grid_for((size_t)n * n, 256), batch), 256, 0, st>>>(k, op, n, bx, by);
   MG_LAUNCH("stencil_div_kernel");
   return {};
 }
@@ -138,6 +142,8 @@ __global__ void features_kernel(const double* __restrict__ op, FT* __restrict__ 
   const size_t N = (size_t)n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (int)N) return;
+  op += (size_t)blockIdx.y * 5 * N;
+  feat += (size_t)blockIdx.y * N * kFeatures;
   const double h = 1.0 / (n + 1);
   const double aC = op[p];
   feat[(size_t)p * kFeatures + 0] = (FT)(op[1 * N + p] / aC);
@@ -148,13 +154,13 @@ __global__ void features_kernel(const double* __restrict__ op, FT* __restrict__ 
 }
 
 template <typename FT>
-Status launch_features(const double* op, FT* feat, int n, cudaStream_t st) {
-  features_kernel<FT><<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, feat, n);
+Status launch_features(const double* op, FT* feat, int n, cudaStream_t st, int batch) {
+  features_kernel<FT><<<dim3(grid_for((size_t)n * n, 256), batch), 256, 0, st>>>(op, feat, n);
   MG_LAUNCH("features_kernel");
   return {};
 }
-template Status launch_features<double>(const double*, double*, int, cudaStream_t);
-template Status launch_features<float>(const double*, float*, int, cudaStream_t);
+template Status launch_features<double>(const double*, double*, int, cudaStream_t, int);
+template Status launch_features<float>(const double*, float*, int, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // Block-level sum of one double per thread; result valid in thread 0.
@@ -179,6 +185,16 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
   __shared__ double smem[32];
   const size_t N = (size_t)n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  {
+    const size_t b = blockIdx.y;   // problem of a batch stored back to back
+    f += b * N;
+    u += b * N;
+    op += b * 5 * N;
+    if (r) r += b * N;
+    if (r32) r32 += b * N;
+    if (dinv32) dinv32 += b * N;
+    partial += b * gridDim.x;
+  }
   double rr = 0.0;
   if (p < (int)N) {
     const int j = p / n, i = p - j * n;
@@ -198,9 +214,9 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
 }
 
 Status launch_residual(const double* f, const double* u, const double* op, double* r, float* r32,
-                       double* partial, int n, cudaStream_t st, const float* dinv32) {
+                       double* partial, int n, cudaStream_t st, const float* dinv32, int batch) {
   const size_t N = (size_t)n * n;
-  residual_kernel<<<reduction_blocks(N), kResidualBlock, 0, st>>>(f, u, op, r, r32, partial, n, dinv32);
+  residual_kernel<<<dim3(reduction_blocks(N), batch), kResidualBlock, 0, st>>>(f, u, op, r, r32, partial, n, dinv32);
   MG_LAUNCH("residual_kernel");
   return {};
 }
@@ -209,13 +225,16 @@ __global__ void diag_inverse_kernel(const double* __restrict__ op, double* __res
                                     float* __restrict__ dinv32, size_t N) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
+  op += (size_t)blockIdx.y * 5 * N;
+  if (dinv) dinv += (size_t)blockIdx.y * N;
+  dinv32 += (size_t)blockIdx.y * N;
   const double d = 1.0 / op[p];
-  dinv[p] = d;
+  if (dinv) dinv[p] = d;
   dinv32[p] = (float)d;
 }
 
-Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t N, cudaStream_t st) {
-  diag_inverse_kernel<<<grid_for(N, 256), 256, 0, st>>>(op, dinv, dinv32, N);
+Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t N, cudaStream_t st, int batch) {
+  diag_inverse_kernel<<<dim3(grid_for(N, 256), batch), 256, 0, st>>>(op, dinv, dinv32, N);
   MG_LAUNCH("diag_inverse_kernel");
   return {};
 }

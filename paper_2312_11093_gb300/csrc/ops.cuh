@@ -13,19 +13,21 @@ constexpr int kReduceBlock = 1024;
 // sizes the partial-sum buffer with it.
 inline int reduction_blocks(size_t N) { return grid_for(N, kResidualBlock); }
 
-Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st);
+// batch > 1: problems of the same size stored back to back (blockIdx.y selects one).
+Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch = 1);
 Status launch_inject_mu(const double* mu, double* mc, int n, cudaStream_t st);
-Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st);
+Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st, int batch = 1);
 Status launch_stencil_nondiv(const double* mu, double* op, int n, double vx, double vy, cudaStream_t st);
 Status launch_count_bad(const double* v, size_t N, int* count, cudaStream_t st);
 template <typename FT>
-Status launch_features(const double* op, FT* feat, int n, cudaStream_t st);
+Status launch_features(const double* op, FT* feat, int n, cudaStream_t st, int batch = 1);
 // r = f - A u (FP64), optional FP32 copy r32 (times dinv32 when given), per-block
 // partial sums of r^2.
+// With batch > 1 every array is per problem, back to back; partial is [batch][blocks].
 Status launch_residual(const double* f, const double* u, const double* op, double* r, float* r32,
-                       double* partial, int n, cudaStream_t st, const float* dinv32 = nullptr);
-// dinv = 1/a_C (FP64 and FP32) from the first plane of op.
-Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t N, cudaStream_t st);
+                       double* partial, int n, cudaStream_t st, const float* dinv32 = nullptr, int batch = 1);
+// dinv = 1/a_C (FP64, may be null, and FP32) from the first plane of op.
+Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t N, cudaStream_t st, int batch = 1);
 Status launch_sumsq(const double* v, size_t N, double* partial, cudaStream_t st);
 // out[0] = sum of partial[0..count) in a fixed order (deterministic).
 Status launch_reduce(const double* partial, int count, double* out, cudaStream_t st);

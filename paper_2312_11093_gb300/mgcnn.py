@@ -69,6 +69,9 @@ def load() -> ctypes.CDLL:
         "mgcnn_train_step": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_double, dp, c_void_p]),
         "mgcnn_get_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
         "mgcnn_set_option": (c_int, [c_void_p, c_int, c_int]),
+        "mgcnn_setup_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+        "mgcnn_solve_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
+                                        c_void_p]),
         "mgcnn_kernel_launches": (ctypes.c_longlong, []),
         "mgcnn_profile": (c_int, [c_void_p, c_int]),
         "mgcnn_profile_read": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
@@ -267,6 +270,28 @@ class Solver:
         w = np.empty(self.weight_count)
         self._check(self._L.mgcnn_get_weights(self._h, w.ctypes.data, w.size), "mgcnn_get_weights")
         return w
+
+    # -- batched solves -----------------------------------------------------------
+    def setup_batched(self, coeffs, ns):
+        """coeffs[i]: nodal k of problem i ((n_i+2)^2 doubles), ns[i] = n_i."""
+        m = len(coeffs)
+        kp = (c_void_p * m)(*[_ptr(k, (n + 2) * (n + 2)) for k, n in zip(coeffs, ns)])
+        nn = (c_int * m)(*[int(n) for n in ns])
+        self._check(self._L.mgcnn_setup_batched(self._h, m, kp, nn), "mgcnn_setup_batched")
+        self.batch_sizes = [int(n) for n in ns]
+
+    def solve_batched(self, rhs, us, tol: float, maxit: int):
+        """Solves every problem in place on us[i].  Returns (status, iters, relres, statuses)."""
+        m = len(rhs)
+        fp = (c_void_p * m)(*[_ptr(f, n * n) for f, n in zip(rhs, self.batch_sizes)])
+        up = (c_void_p * m)(*[_ptr(u, n * n, True) for u, n in zip(us, self.batch_sizes)])
+        iters = np.zeros(m, dtype=np.int32)
+        relres = np.zeros(m)
+        stat = np.zeros(m, dtype=np.int32)
+        st = self._L.mgcnn_solve_batched(self._h, m, fp, up, float(tol), int(maxit), iters.ctypes.data,
+                                         relres.ctypes.data, stat.ctypes.data)
+        self._check(st, "mgcnn_solve_batched", ok=(OK, NOT_CONVERGED))
+        return st, iters, relres, stat
 
     PROFILE_KINDS = ("residual", "resnet", "restrict", "prolong", "in", "out", "down0", "up0")
     OPT_FUSED = 1

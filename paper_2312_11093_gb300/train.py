@@ -80,7 +80,7 @@ def make_batch(step: int, sizes=(63, 127), per_size: int = 32, corr_len: float =
 
 
 def train(steps: int = 2000, K: int = 8, lr: float = 1e-3, C: int = 8, seed: int = 0, log_every: int = 50,
-          out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size: int = 32, setup_scale: int = 2):
+          out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size: int = 32, setup_scale: int = 0):
     sv = mgcnn.Solver(C, 1, 1, precision=precision, b=(1.0, 0.5), scale_by_diag=setup_scale, input_diag=True)
     sv.set_weights(init_weights(C, 1, 1, np.random.default_rng(seed)))
     hist = []

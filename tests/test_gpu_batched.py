@@ -1,0 +1,93 @@
+"""Batched solves of uneven sizes (one CUDA graph per cycle) against independent
+single-problem solves of the same fields with the same network."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mgcnn as omg
+from paper_2312_11093_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2312_11093_gb300 import build
+    build.build()
+    from paper_2312_11093_gb300 import mgcnn
+    mgcnn.load()
+    return mgcnn
+
+
+def _weights(M):
+    """A convergent 8-channel network: trained weights when present, else random
+    weights with a small output layer (the iteration then contracts slowly)."""
+    import os
+    path = os.path.join(os.path.dirname(M.__file__), "weights", "mgcnn_c8_trained.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    from paper_2312_11093_gb300.train import init_weights
+    return init_weights(8, 1, 1, np.random.default_rng(3), out_scale=0.05)
+
+
+def _fields(sizes, seed):
+    rng = np.random.default_rng(seed)
+    ks, fs = [], []
+    for i, n in enumerate(sizes):
+        kind = i % 3
+        k = (inputs.lognormal_k(n, 0.1, rng) if kind == 0 else
+             inputs.random_blocks_k(n, rng) if kind == 1 else inputs.checkerboard_k(n))
+        ks.append(np.ascontiguousarray(k.ravel()))
+        fs.append(np.ascontiguousarray(inputs.normal_rhs(n, rng).ravel()))
+    return ks, fs
+
+
+def test_batched_equals_single_problem_solves(M):
+    """Same kernels, same arithmetic per pixel (the tile shape does not change the
+    summation order) and the same norm reduction: bit-identical iterates."""
+    sizes = [63, 15, 127, 63, 7, 31, 127, 3, 63]
+    ks, fs = _fields(sizes, 1)
+    w = _weights(M)
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(w)
+    sv.setup_batched(ks, sizes)
+    us = [np.zeros(n * n) for n in sizes]
+    st, iters, relres, stat = sv.solve_batched(fs, us, 1e-6, 40)
+    for i, n in enumerate(sizes):
+        one = M.Solver(8, 1, 1, precision="mixed_bf16")
+        one.set_weights(w)
+        one.setup(ks[i].copy(), n)
+        u = np.zeros(n * n)
+        st1, it1, h1 = one.solve(fs[i].copy(), u, 1e-6, 40)
+        assert it1 == iters[i], (i, n, it1, iters[i])
+        assert np.array_equal(u, us[i]), (i, n)
+        assert relres[i] == h1[-1]
+        assert stat[i] == st1
+
+
+def test_batched_statuses_and_special_cases(M):
+    sizes = [31, 31, 15]
+    ks, fs = _fields(sizes, 2)
+    fs[1] = np.zeros(31 * 31)                   # f = 0: u = 0, no cycles
+    fs[2][5] = np.nan                           # non-finite right-hand side
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(_weights(M))
+    sv.setup_batched(ks, sizes)
+    us = [np.ones(n * n) for n in sizes]
+    with pytest.raises(M.MGCNNError):
+        sv.solve_batched(fs, us, 1e-30, 3)
+    fs[2][5] = 0.0
+    us = [np.ones(n * n) for n in sizes]
+    st, iters, relres, stat = sv.solve_batched(fs, us, 1e-30, 3)
+    assert st == M.NOT_CONVERGED
+    assert list(iters) == [3, 0, 3] and stat[1] == M.OK and not us[1].any()
+
+
+def test_batched_rejects_unsupported_config(M):
+    sv = M.Solver(13, 3, 2, precision="mixed_bf16")
+    sv.set_weights(M.gmg_weights(2, 2))
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.setup_batched([np.ones(9 * 9)], [7])
+    assert ei.value.status == M.ERR_SIZE
