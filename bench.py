@@ -54,6 +54,26 @@ def make_workload(name: str, n: int, seed: int):
     return np.ascontiguousarray(k.ravel()), np.ascontiguousarray(f.ravel()), b
 
 
+def make_batch_workload(count: int, seed: int, sizes=(63, 127, 255, 511, 1023)):
+    """Uneven batch: n ~ U{sizes}; k family ~ U{lognormal GRF (corr. 0.1, sigma 1),
+    random blocks on a 16x16 board with log10 k ~ U(-2, 2), 16x16 checkerboard {1, 100}};
+    b = (1, 0.5); f ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    ns = [int(x) for x in rng.choice(sizes, size=count)]
+    fam = rng.integers(0, 3, size=count)
+    ks, fs = [], []
+    for n, fm in zip(ns, fam):
+        if fm == 0:
+            k = inputs.lognormal_k(n, 0.1, rng)
+        elif fm == 1:
+            k = inputs.random_blocks_k(n, rng)
+        else:
+            k = inputs.checkerboard_k(n)
+        ks.append(np.ascontiguousarray(k.ravel()))
+        fs.append(np.ascontiguousarray(inputs.normal_rhs(n, rng).ravel()))
+    return ns, ks, fs
+
+
 def network(kind: str):
     """(channels, nu_d, nu_u, blob, gmg) for the solve network."""
     from paper_2312_11093_gb300 import mgcnn
@@ -211,13 +231,15 @@ def main():
     ap.add_argument("--n", type=int, default=4095)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--net", default=None, choices=["trained", "gmg"])
-    ap.add_argument("--workload", default=None, choices=["channelised", "grf"])
+    ap.add_argument("--workload", default=None, choices=["channelised", "grf", "batched256"])
+    ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg")
     workload = args.workload or ("channelised" if net == "trained" else "grf")
+    args.net_resolved = net
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -241,6 +263,9 @@ def main():
                           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                           "wall_s": time.perf_counter() - t0}))
         return
+
+    if workload == "batched256":
+        return bench_batched(args, rank, world, local)
 
     import torch
     if world > 1:
@@ -380,6 +405,80 @@ def main():
     sv.close()
     if rank == 0:
         print(json.dumps(result))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def bench_batched(args, rank, world, local):
+    """256 uneven problems per step (setup + solve of the whole batch), one CUDA graph
+    per cycle, tile shapes autotuned at setup; solves/s = problems / step time."""
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2312_11093_gb300 import mgcnn
+    C, nd, nu, blob, is_gmg = network("trained")
+    ns, ks, fs = make_batch_workload(args.batch, 3 + 1000 * rank)
+    dev = torch.device("cuda", local)
+    kd = [torch.from_numpy(k).to(dev) for k in ks]
+    fd = [torch.from_numpy(f).to(dev) for f in fs]
+    ud = [torch.zeros(n * n, dtype=torch.float64, device=dev) for n in ns]
+    sv = mgcnn.Solver(C, nd, nu, precision="mixed_bf16")
+    sv.set_weights(blob)
+
+    def step(kk, ff, uu):
+        sv.setup_batched(kk, ns)
+        for u in uu:
+            u.zero_() if hasattr(u, "zero_") else u.fill(0.0)
+        return sv.solve_batched(ff, uu, args.tol, 300)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        st, iters, relres, stat = step(kd, fd, ud)
+    launches0 = mgcnn.kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st, iters, relres, stat = step(kd, fd, ud)
+        barrier()
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    launches = (mgcnn.kernel_launches() - launches0) // args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    uh = [np.zeros(n * n) for n in ns]
+    step(ks, fs, uh)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = 2
+    for _ in range(e2e_steps):
+        step(ks, fs, uh)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    unknowns = int(sum(n * n for n in ns))
+    res = {"metric": "solves/s to rel-res 1e-6, batch of uneven sizes (setup + solve)",
+           "value": world * args.batch * 1e3 / ms, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": f"batched{args.batch}_63-1023", "problems": args.batch, "unknowns": unknowns,
+                      "tol": args.tol, "net": "trained", "l2": "inputs larger than L2",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
+           "converged": int((stat == 0).sum()), "relres_max": float(relres.max()),
+           "e2e": {"value": world * args.batch * 1e3 / e2e_ms, "unit": "solves/s",
+                   "h2d_bytes_per_step": int(sum(k.nbytes for k in ks) + 2 * sum(f.nbytes for f in fs)),
+                   "d2h_bytes_per_step": int(sum(f.nbytes for f in fs)), "ms_per_step": e2e_ms},
+           "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None}
+    if rank == 0:
+        print(json.dumps(res))
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -50,11 +50,17 @@ def _autograd():
     return MGCNNLoss
 
 
-def init_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, out_scale: float = 0.1) -> np.ndarray:
-    """Random initial weights, uniform with PyTorch's default fan-in bound, the output
-    layer shrunk so that the unrolled cycles start from a loss near 1.  With the
-    network applied to D^{-1} r, A B has O(1) entries at every grid size, so no
-    further structure is needed."""
+def init_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, out_scale: float = 0.1,
+                 setup_out: float = 0.01) -> np.ndarray:
+    """Random initial weights, uniform with PyTorch's default fan-in bound.
+
+    The output layer is shrunk (out_scale) and the setup network starts near zero
+    (its input layer and biases times setup_out), so the setup tensors, and with
+    them every s-scaled path of the solve phase, start small: the initial solve
+    network is its unscaled skip/transfer paths, A B has O(1) entries with the
+    normalised input, and the unrolled cycles start from a loss near 1 at every
+    training size, also when the setup tensors carry the per-level factor
+    (h_l/h_1)^2."""
     F, S = mgcnn.FEATURES, mgcnn.SETUP_LAYERS
 
     def u(*shape, fan):
@@ -63,8 +69,8 @@ def init_weights(C: int, nu_d: int, nu_u: int, rng: np.random.Generator, out_sca
     w = {"w_in": u(C, 1, 3, 3, fan=9), "w_down": u(nu_d, C, C, 3, 3, fan=9 * C),
          "w_up": u(nu_u, C, C, 3, 3, fan=9 * C), "w_R": u(C, C, 3, 3, fan=9 * C),
          "w_P": u(C, C, 3, 3, fan=9 * C), "w_out": out_scale * u(1, C, 3, 3, fan=9 * C),
-         "sw_in": u(C, F, 3, 3, fan=9 * F), "sb_in": u(C, fan=9 * F),
-         "sw": u(S, C, C, 3, 3, fan=9 * C), "sb": u(S, C, fan=9 * C), "sw_R": u(C, C, 3, 3, fan=9 * C)}
+         "sw_in": setup_out * u(C, F, 3, 3, fan=9 * F), "sb_in": setup_out * u(C, fan=9 * F),
+         "sw": u(S, C, C, 3, 3, fan=9 * C), "sb": setup_out * u(S, C, fan=9 * C), "sw_R": u(C, C, 3, 3, fan=9 * C)}
     return mgcnn.pack_weights(w, C, nu_d, nu_u)
 
 
@@ -80,7 +86,7 @@ def make_batch(step: int, sizes=(63, 127), per_size: int = 32, corr_len: float =
 
 
 def train(steps: int = 2000, K: int = 8, lr: float = 1e-3, C: int = 8, seed: int = 0, log_every: int = 50,
-          out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size: int = 32, setup_scale: int = 0):
+          out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size: int = 32, setup_scale: int = 2):
     sv = mgcnn.Solver(C, 1, 1, precision=precision, b=(1.0, 0.5), scale_by_diag=setup_scale, input_diag=True)
     sv.set_weights(init_weights(C, 1, 1, np.random.default_rng(seed)))
     hist = []
