@@ -400,6 +400,21 @@ def main():
         result["fp64"] = {"value": 1.0 / t64, "unit": "solves/s", "iters": it64, "relres": float(h64[-1]),
                           "mixed_vs_fp64_rel_err": err, "mixed_speedup": value / world * t64}
         sv64.close()
+    if not args.no_fp64 and rank == 0:
+        # classical GMG comparator (Sec. 2.3): FP64 V(2,2), omega 0.8, same operators and tolerance
+        svg = make_solver("fp64")
+        svg.setup_gmg(k_d, n, 0.8) if is_gmg else svg.setup(k_d, n)
+        ug = torch.zeros_like(u_d)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        try:
+            stg, itg, hg = svg.gmg_solve(f_d, ug, tol, 300, 2, 2, 0.8)
+            tg = time.perf_counter() - t0
+            result["gmg"] = {"value": 1.0 / tg, "unit": "solves/s", "iters": itg, "relres": float(hg[-1]),
+                             "converged": bool(stg == mgcnn.OK), "cycle": "V(2,2) weighted Jacobi 0.8, FP64"}
+        except mgcnn.MGCNNError as err:
+            result["gmg"] = {"converged": False, "error": str(err)[:120], "cycle": "V(2,2) weighted Jacobi 0.8, FP64"}
+        svg.close()
     if not args.no_cpu and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_reference(workload, net, n, tol=tol)
     sv.close()

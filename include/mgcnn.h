@@ -194,6 +194,16 @@ int mgcnn_vcycle(mgcnn_ctx* ctx, const double* r, double* e);
 int mgcnn_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit,
                 int* iters, double* relres);
 
+/* Classical geometric multigrid (Sec. 2.3), the comparator of the learned
+ * solver, on the context's operators (mgcnn_setup or mgcnn_setup_gmg must have
+ * run): the stationary iteration of Eq. 1 with B one V(nu1, nu2) cycle of
+ * weighted Jacobi (weight omega in (0,2)), full-weighting restriction of the
+ * defect, bilinear prolongation and the rediscretised coarse operators; the
+ * coarsest grid gets nu1 + nu2 sweeps.  FP64.  f, u, iters, relres as
+ * mgcnn_solve.  Errors: ARG (nu1 + nu2 < 1, omega), STATE, NONFINITE, CUDA. */
+int mgcnn_gmg_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit, int nu1, int nu2,
+                    double omega, int* iters, double* relres);
+
 /* ---- Batched solves ------------------------------------------------------------
  * Many coefficient fields and right-hand sides of uneven grid sizes at once:
  * the setup phase (Sec. 3.2) for every field, then the stationary iteration
@@ -251,8 +261,14 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * layer per ResNet, run each level of the V-cycle as two fused kernels (down:
  * [reChannel-in] + ResNetDown + RCNN; up: TCNN-add + ResNetUp [+ reChannel-out
  * and the FP64 update]); 0 runs one kernel per layer.  Both compute the same
- * function; roundings to BF16 happen at different points. */
-enum { MGCNN_OPT_FUSED = 1 };
+ * function; roundings to BF16 happen at different points.
+ * MGCNN_OPT_DEVICE_LOOP (default 1): where the fused kernels apply, mgcnn_solve
+ * runs the whole stationary iteration as one launch of a CUDA graph with a
+ * conditional WHILE node (residual, norm, convergence test and V-cycle on the
+ * device, no host round trip per cycle; the graph is captured once per setup,
+ * f and u are copied through the context's buffers); 0 runs the host loop
+ * (one 8-byte readback per cycle).  Both give identical iterates. */
+enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2 };
 int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).

@@ -12,6 +12,8 @@
 #include "mixed.cuh"
 #include "train.cuh"
 #include "batch.cuh"
+#include "gmg.cuh"
+#include "solve_graph.cuh"
 
 using namespace mgcnn;
 
@@ -277,6 +279,7 @@ Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
   const int L = c->cfg.levels > 0 ? c->cfg.levels : Lmax;
   if (L > Lmax) return make_status(MGCNN_ERR_SIZE, "%d levels requested, n=%d allows %d", L, n, Lmax);
   c->have_setup = false;
+  c->sgraph_valid = false;           // buffers may move: recapture the device loop
   if (c->n != n) c->tuned = false;   // tile shapes are tuned per grid size
   c->n = n;
   c->L = L;
@@ -415,6 +418,12 @@ void mgcnn_destroy(mgcnn_ctx* c) {
   mixed_release(c);
   train_release(c);
   batch_release(c);
+  graph_release(c);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    release(c->gmg_r[l]);
+    release(c->gmg_e[l]);
+    release(c->gmg_t[l]);
+  }
   for (size_t i = 0; i < c->ev_start.size(); ++i) {
     cudaEventDestroy(c->ev_start[i]);
     cudaEventDestroy(c->ev_stop[i]);
@@ -597,6 +606,15 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
       MG_TRY(stage_out_finish(c, u, du, N, host));
       return sync(c);
     }
+    if (c->device_loop) {
+      bool used = false;
+      Status d = solve_on_device(c, df, du, tol, maxit, iters, relres, &used);
+      if (used || !d.ok()) {
+        MG_TRY(stage_out_finish(c, u, du, N, host));
+        MG_TRY(sync(c));
+        return d;
+      }
+    }
     Status result;
     const bool mixed = c->cfg.precision == MGCNN_PREC_MIXED_BF16;
     for (int k = 0;; ++k) {
@@ -713,11 +731,81 @@ int mgcnn_solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, doubl
   return finish(c, solve_batched(c, nprob, rhs, u, tol, maxit, iters, relres, status));
 }
 
+int mgcnn_gmg_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int nu1, int nu2, double omega,
+                    int* iters, double* relres) {
+  if (!c || !f || !u || !iters || maxit < 0 || !(tol >= 0.0) || nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 ||
+      !(omega > 0.0 && omega < 2.0))
+    return MGCNN_ERR_ARG;
+  *iters = 0;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    const size_t N = c->lv[0].N();
+    GmgLevels g;
+    g.L = c->L;
+    for (int l = 0; l < c->L; ++l) {
+      const size_t Nl = c->lv[l].N();
+      MG_TRY(ensure(c->gmg_r[l], Nl * sizeof(double)));
+      MG_TRY(ensure(c->gmg_e[l], Nl * sizeof(double)));
+      MG_TRY(ensure(c->gmg_t[l], Nl * sizeof(double)));
+      g.n[l] = c->lv[l].n;
+      g.op[l] = c->op[l].as<double>();
+      g.r[l] = c->gmg_r[l].as<double>();
+      g.e[l] = c->gmg_e[l].as<double>();
+      g.t[l] = c->gmg_t[l].as<double>();
+    }
+    const double* df = nullptr;
+    MG_TRY(stage_in(c, f, N, c->f, &df));
+    double* du = nullptr;
+    bool host = false;
+    MG_TRY(stage_out(u, N, c->u, &du, &host));
+    if (host) MG_CUDA(cudaMemcpyAsync(du, u, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    MG_TRY(sumsq(c, df, N, 1));
+    double fn2 = 0.0;
+    MG_TRY(read_scalar(c, 1, &fn2));
+    if (!std::isfinite(fn2)) return make_status(MGCNN_ERR_NONFINITE, "right-hand side is not finite");
+    Status result;
+    if (fn2 == 0.0) {
+      MG_CUDA(cudaMemsetAsync(du, 0, N * sizeof(double), c->stream));
+      if (relres) relres[0] = 0.0;
+    } else {
+      for (int k = 0;; ++k) {
+        MG_TRY(launch_residual(df, du, c->op[0].as<double>(), g.r[0], nullptr, c->partial.as<double>(), c->n,
+                               c->stream));
+        MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>(), c->stream));
+        double rn2 = 0.0;
+        MG_TRY(read_scalar(c, 0, &rn2));
+        const double rel = std::sqrt(rn2 / fn2);
+        *iters = k;
+        if (!std::isfinite(rel)) {
+          result = make_status(MGCNN_ERR_NONFINITE, "residual norm is not finite at cycle %d", k);
+          break;
+        }
+        if (relres) relres[k] = rel;
+        if (rel <= tol) break;
+        if (k == maxit) {
+          result = make_status(MGCNN_NOT_CONVERGED, "no convergence in %d cycles (relres %.3e)", maxit, rel);
+          break;
+        }
+        MG_TRY(gmg_vcycle(g, 0, nu1, nu2, omega, c->stream));
+        MG_TRY(launch_axpy_to(du, g.e[0], du, N, c->stream));
+      }
+    }
+    MG_TRY(stage_out_finish(c, u, du, N, host));
+    MG_TRY(sync(c));
+    return result;
+  }();
+  return finish(c, st);
+}
+
 int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
   if (!c) return MGCNN_ERR_ARG;
   switch (option) {
     case MGCNN_OPT_FUSED:
       c->fused = value ? 1 : 0;
+      c->sgraph_valid = false;
+      return finish(c, {});
+    case MGCNN_OPT_DEVICE_LOOP:
+      c->device_loop = value ? 1 : 0;
       return finish(c, {});
     default:
       return finish(c, make_status(MGCNN_ERR_ARG, "unknown option %d", option));

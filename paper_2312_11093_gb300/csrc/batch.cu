@@ -194,8 +194,10 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff) {
   MG_TRY(ensure(k.rn2, B * sizeof(double)));
   MG_TRY(ensure(k.fn2, B * sizeof(double)));
   MG_TRY(ensure(k.state, 3 * B * sizeof(int)));
-  MG_TRY(ensure(k.feat, B * N0 * kFeatures * sizeof(float)));
-  for (DevBuf* b : {&k.ca, &k.cb, &k.za, &k.zb, &k.s32}) MG_TRY(ensure(*b, B * N0 * C * sizeof(float)));
+  if (!c->fused) {   // FP32 scratch of the unfused setup network only
+    MG_TRY(ensure(k.feat, B * N0 * kFeatures * sizeof(float)));
+    for (DevBuf* b : {&k.ca, &k.cb, &k.za, &k.zb, &k.s32}) MG_TRY(ensure(*b, B * N0 * C * sizeof(float)));
+  }
   cudaStream_t st = k.stream;
   // coefficients in, checked positive and finite
   double* k0 = k.coef.as<double>();
@@ -214,7 +216,20 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff) {
     if (l + 1 < k.L) MG_TRY(launch_restrict_k(kh[l & 1], kh[(l + 1) & 1], k.nl[l] + 2, st, k.B));
   }
   MG_TRY(launch_diag_inverse(k.op[0].as<double>(), nullptr, k.dinv32.as<float>(), N0, st, k.B));
-  MG_TRY(batched_setup_net(c, k));
+  if (c->fused) {
+    const double* ops[kMaxLevels];
+    bf16* ss[kMaxLevels];
+    bf16* cs[kMaxLevels];
+    for (int l = 0; l < k.L; ++l) {
+      ops[l] = k.op[l].as<double>();
+      ss[l] = k.s16[l].as<bf16>();
+      cs[l] = k.xb[l].as<bf16>();
+    }
+    const SetupWeights sw = setup_weights(c);
+    MG_TRY(setup_fused_levels(k.L, k.nl, k.B, ops, ss, cs, sw.frags, sw.fp, c->cfg.scale_by_diag, st));
+  } else {
+    MG_TRY(batched_setup_net(c, k));
+  }
   // level geometry for the fused kernels, then autotune the tile shapes
   k.fl = FusedLevels{};
   k.fl.L = k.L;

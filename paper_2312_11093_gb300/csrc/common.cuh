@@ -106,6 +106,15 @@ struct mgcnn_ctx {
   std::vector<mgcnn::TrainGroup> groups;
   mgcnn::DevBuf grad, wT, adam_m, adam_v;
   long long adam_t = 0;
+  // device-side solve loop (solve_graph.cu)
+  int device_loop = 1;                    // option: run mgcnn_solve as one conditional CUDA graph
+  bool graph_failed = false, sgraph_valid = false;
+  cudaGraphExec_t sgraph = nullptr;
+  long long sgraph_kernels = 0;
+  cudaStream_t gstream = nullptr;
+  mgcnn::DevBuf gstate, ghist, gparams;
+  // classical GMG comparator (gmg.cu): per-level rhs, correction, ping-pong
+  mgcnn::DevBuf gmg_r[mgcnn::kMaxLevels], gmg_e[mgcnn::kMaxLevels], gmg_t[mgcnn::kMaxLevels];
   // batched solves (batch.cu)
   std::vector<mgcnn::BatchClass> bcls;
   int bn = 0, bmaxit = -1;

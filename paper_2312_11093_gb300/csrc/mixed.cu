@@ -38,6 +38,7 @@ struct MixLayout {
   size_t frag_words = 0;                 // uint32 words per packed C x C conv
   size_t down = 0, up = 0, R = 0;        // byte offsets of the fragment blocks
   size_t w_in = 0, w_out = 0, w_P = 0;   // byte offsets of FP32 arrays
+  size_t s_frag = 0, s_fp = 0;           // setup network: 5 fragment blocks, FP32 biases + W_cin (CP = 8)
   size_t bytes = 0;
 };
 
@@ -53,6 +54,8 @@ MixLayout mix_layout(const mgcnn_ctx* c) {
   m.w_in = o;  o += (size_t)m.cp * 9 * 4;
   m.w_out = o; o += (size_t)m.cp * 9 * 4;
   m.w_P = o;   o += (size_t)m.cp * m.cp * 9 * 4;
+  m.s_frag = o; o += 5 * m.frag_words * 4;
+  m.s_fp = o;   o += (4 * 8 + 8 * kFeatures * 9 + 8) * 4;
   m.bytes = o;
   return m;
 }
@@ -489,15 +492,51 @@ Status mixed_set_weights(mgcnn_ctx* c) {
   for (int ci = 0; ci < C; ++ci)
     for (int co = 0; co < C; ++co)
       for (int t = 0; t < 9; ++t) wP[(ci * ml.cp + co) * 9 + t] = (float)w[c->wl.w_P + ((size_t)ci * C + co) * 9 + t];
+  if (C == 8) {
+    // fused setup network: 4 tanh layers and the setup RCNN as fragments; b_i, W_cin, b_cin in FP32
+    uint32_t* sf = reinterpret_cast<uint32_t*>(blob.data() + ml.s_frag);
+    for (int i = 0; i < kSetupLayers; ++i) pack_frags(w.data() + c->wl.sw + i * CC9, C, ml.cp, sf + i * ml.frag_words);
+    pack_frags(w.data() + c->wl.sw_R, C, ml.cp, sf + 4 * ml.frag_words);
+    float* sp = reinterpret_cast<float*>(blob.data() + ml.s_fp);
+    for (int i = 0; i < 4 * 8; ++i) sp[i] = (float)w[c->wl.sb + i];
+    for (int i = 0; i < 8 * kFeatures * 9; ++i) sp[32 + i] = (float)w[c->wl.sw_in + i];
+    for (int i = 0; i < 8; ++i) sp[32 + 8 * kFeatures * 9 + i] = (float)w[c->wl.sb_in + i];
+  }
   MG_TRY(ensure(c->wmix, ml.bytes));
   MG_CUDA(cudaMemcpyAsync(c->wmix.p, blob.data(), ml.bytes, cudaMemcpyHostToDevice, c->stream));
   MG_CUDA(cudaStreamSynchronize(c->stream));
   return {};
 }
 
+SetupWeights setup_weights(const mgcnn_ctx* c) {
+  const MixLayout ml = mix_layout(c);
+  const char* wb = c->wmix.as<char>();
+  return SetupWeights{reinterpret_cast<const uint32_t*>(wb + ml.s_frag), reinterpret_cast<const float*>(wb + ml.s_fp)};
+}
+
 Status setup_mixed(mgcnn_ctx* c) {
   const int C = c->cfg.channels;
   const int cp = c->cp;
+  if (C == 8 && c->fused) {
+    // one fused kernel per level; coef_l (l >= 1) is kept in the level's second state buffer
+    const double* ops[kMaxLevels];
+    bf16* ss[kMaxLevels];
+    bf16* cs[kMaxLevels];
+    int ns[kMaxLevels];
+    for (int l = 0; l < c->L; ++l) {
+      const size_t N = c->lv[l].N();
+      MG_TRY(ensure(c->s16[l], N * cp * sizeof(bf16)));
+      MG_TRY(ensure(c->x16a[l], N * cp * sizeof(bf16)));
+      MG_TRY(ensure(c->x16b[l], N * cp * sizeof(bf16)));
+      ops[l] = c->op[l].as<double>();
+      ss[l] = c->s16[l].as<bf16>();
+      cs[l] = c->x16b[l].as<bf16>();
+      ns[l] = c->lv[l].n;
+    }
+    MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
+    const SetupWeights sw = setup_weights(c);
+    return setup_fused_levels(c->L, ns, 1, ops, ss, cs, sw.frags, sw.fp, c->cfg.scale_by_diag, c->stream);
+  }
   size_t total = 0;
   for (int l = 0; l < c->L; ++l) total += c->lv[l].N() * C;
   MG_TRY(ensure(c->s32tmp, total * sizeof(float)));

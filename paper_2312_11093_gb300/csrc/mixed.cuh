@@ -42,6 +42,15 @@ Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, do
 // Pointers into ctx->wmix for the fused kernels (valid after mixed_set_weights).
 FusedWeights fused_weights(const mgcnn_ctx* c);
 bool fused_supported(const mgcnn_ctx* c);
+// setup_fused.cu: Algorithm 2 for 8 channels, one fused kernel per level
+struct SetupWeights {
+  const uint32_t* frags;
+  const float* fp;
+};
+SetupWeights setup_weights(const mgcnn_ctx* c);
+Status setup_fused_levels(int L, const int* n, int batch, const double* const* op, __nv_bfloat16* const* s,
+                          __nv_bfloat16* const* coef, const uint32_t* frags, const float* fp, int mode,
+                          cudaStream_t st);
 // [N][C] FP32 -> [N][cp] BF16, zero padded
 Status pad_setup_bf16(const float* src, __nv_bfloat16* dst, size_t N, int C, int cp, cudaStream_t st);
 Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,

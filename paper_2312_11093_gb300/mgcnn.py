@@ -69,6 +69,8 @@ def load() -> ctypes.CDLL:
         "mgcnn_train_step": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_double, dp, c_void_p]),
         "mgcnn_get_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
         "mgcnn_set_option": (c_int, [c_void_p, c_int, c_int]),
+        "mgcnn_gmg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_int, c_double,
+                                    POINTER(c_int), c_void_p]),
         "mgcnn_setup_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
         "mgcnn_solve_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
                                         c_void_p]),
@@ -271,6 +273,17 @@ class Solver:
         self._check(self._L.mgcnn_get_weights(self._h, w.ctypes.data, w.size), "mgcnn_get_weights")
         return w
 
+    def gmg_solve(self, f, u, tol: float, maxit: int, nu1: int = 2, nu2: int = 2, omega: float = 0.8):
+        """Classical GMG V(nu1, nu2) on this context's operators, in place on u.
+        Returns (status, iters, relres[0..iters])."""
+        N = self.n * self.n
+        it = c_int(0)
+        hist = np.zeros(maxit + 1)
+        st = self._L.mgcnn_gmg_solve(self._h, _ptr(f, N), _ptr(u, N, True), float(tol), int(maxit), int(nu1),
+                                     int(nu2), float(omega), ctypes.byref(it), hist.ctypes.data)
+        self._check(st, "mgcnn_gmg_solve", ok=(OK, NOT_CONVERGED))
+        return st, it.value, hist[: it.value + 1]
+
     # -- batched solves -----------------------------------------------------------
     def setup_batched(self, coeffs, ns):
         """coeffs[i]: nodal k of problem i ((n_i+2)^2 doubles), ns[i] = n_i."""
@@ -295,6 +308,7 @@ class Solver:
 
     PROFILE_KINDS = ("residual", "resnet", "restrict", "prolong", "in", "out", "down0", "up0")
     OPT_FUSED = 1
+    OPT_DEVICE_LOOP = 2
 
     def set_option(self, option: int, value: int):
         self._check(self._L.mgcnn_set_option(self._h, int(option), int(value)), "mgcnn_set_option")

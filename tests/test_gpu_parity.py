@@ -278,3 +278,75 @@ def test_fused_and_per_layer_kernels_agree(M, n):
         out[fused] = sv.vcycle(f.ravel().copy())
         assert relerr(out[fused], e_ref) <= 5e-2
     assert relerr(out[1], out[0]) <= 3e-2
+
+
+@pytest.mark.parametrize("n,mode", [(7, 0), (63, 0), (255, 1), (127, 2)])
+def test_fused_setup_network(M, n, mode):
+    """The fused BF16 setup kernel (tensor-core layers, FP32 z) against the FP64
+    oracle and the FP32 direct-convolution setup.  Setup tensors are stored in BF16
+    either way; the fused path also rounds the layer operands to BF16 (unit
+    roundoff 2^-9, four layers), hence 3e-2."""
+    C = 8
+    k, f = problem(n, 40 + n)
+    w = omg.random_weights(C, 1, 1, np.random.default_rng(13), scale=0.3)
+    sts = oop.level_stencils_div(k, (1.0, 0.5), num_levels(n))
+    s_ref = to_nhwc(omg.setup(w, sts, scale_by_diag=mode))
+    got = {}
+    for fused in (1, 0):
+        sv = M.Solver(C, 1, 1, precision="mixed_bf16", scale_by_diag=mode)
+        sv.set_option(sv.OPT_FUSED, fused)
+        sv.set_weights(M.pack_weights(w, C, 1, 1))
+        sv.setup(k.ravel().copy(), n)
+        got[fused] = sv.get_setup_tensors()
+        assert relerr(got[fused], s_ref) <= 3e-2, (fused, relerr(got[fused], s_ref))
+    assert relerr(got[1], got[0]) <= 3e-2
+
+
+@pytest.mark.parametrize("n,nu1,nu2,omega,kind", [(31, 2, 2, 0.8, "cfg0"), (63, 1, 2, 0.7, "grf"), (7, 3, 0, 0.8, "grf")])
+def test_gpu_gmg_iterate_for_iterate(M, n, nu1, nu2, omega, kind):
+    """The GPU classical GMG against the oracle's GMG (Sec. 2.3): identical cycle
+    counts, every cycle within 1e-12 when applied to the oracle's own iterate."""
+    if kind == "cfg0":
+        rng = np.random.default_rng(0)
+        k = inputs.block_board_k(n, rng)
+        f = inputs.normal_rhs(n, rng)
+    else:
+        k, f = problem(n, 50 + n)
+    b = (1.0, 0.5)
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    u_o, it_o, hist_o, its_o = ogmg.stationary_solve(sts, f, None, 1e-10, 300, nu1, nu2, omega)
+    sv = M.Solver(8, 1, 1, b=b)
+    sv.set_weights(np.zeros(sv.weight_count))
+    sv.setup(k.ravel().copy(), n)
+    u = np.zeros(n * n)
+    st, it, hist = sv.gmg_solve(f.ravel().copy(), u, 1e-10, 300, nu1, nu2, omega)
+    assert st == M.OK and it == it_o
+    assert relerr(u, u_o) <= 1e-12
+    for k_ in range(0, it_o, max(1, it_o // 5)):
+        uk = its_o[k_].ravel().copy()
+        _, it1, _ = sv.gmg_solve(f.ravel().copy(), uk, 0.0, 1, nu1, nu2, omega)
+        assert relerr(uk, its_o[k_ + 1]) <= 1e-12, k_
+
+
+@pytest.mark.parametrize("n,tol,maxit", [(63, 1e-6, 60), (255, 1e-30, 7), (7, 1e-8, 50)])
+def test_device_loop_equals_host_loop(M, n, tol, maxit):
+    """The solve as one conditional CUDA graph and the host-driven loop run the same
+    kernels: identical iterates, cycle counts, residual histories and statuses."""
+    from paper_2312_11093_gb300.train import init_weights
+    k, f = problem(n, 60 + n)
+    w = init_weights(8, 1, 1, np.random.default_rng(5), out_scale=0.05)
+    out = {}
+    for loop in (1, 0):
+        sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+        sv.set_option(sv.OPT_DEVICE_LOOP, loop)
+        sv.set_weights(w)
+        sv.setup(k.ravel().copy(), n)
+        u = np.zeros(n * n)
+        st, it, hist = sv.solve(f.ravel().copy(), u, tol, maxit)
+        out[loop] = (st, it, hist.copy(), u)
+        u2 = np.zeros(n * n)                       # a second solve reuses the captured graph
+        st2, it2, hist2 = sv.solve(f.ravel().copy(), u2, tol, maxit)
+        assert st2 == st and it2 == it and np.array_equal(u2, u)
+    assert out[1][0] == out[0][0] and out[1][1] == out[0][1]
+    assert np.array_equal(out[1][2], out[0][2])
+    assert np.array_equal(out[1][3], out[0][3])

@@ -126,5 +126,5 @@ def test_training_steps_reduce_loss(M):
     from paper_2312_11093_gb300.train import init_weights, make_batch
     sv = M.Solver(8, 1, 1, precision="mixed_bf16")
     sv.set_weights(init_weights(8, 1, 1, np.random.default_rng(0)))
-    losses = [sv.train_step(make_batch(s, sizes=(31,), per_size=8), 4, 1e-3) for s in range(40)]
+    losses = [sv.train_step(make_batch(s, sizes=(31,), per_size=(8,)), 4, 1e-3) for s in range(40)]
     assert np.mean(losses[-5:]) < 0.7 * np.mean(losses[:5])
