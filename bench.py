@@ -75,10 +75,17 @@ def make_batch_workload(count: int, seed: int, sizes=(63, 127, 255, 511, 1023)):
 
 
 def network(kind: str):
-    """(channels, nu_d, nu_u, blob, gmg) for the solve network."""
+    """(channels, nu_d, nu_u, blob, gmg) for the solve network: the trained 8-channel
+    network, the 8-channel network that is GMG V(1,0) (same shape, same fused
+    kernels, analytic setup tensors), or the 13-channel network that is GMG V(2,2)."""
     from paper_2312_11093_gb300 import mgcnn
     if kind == "gmg":
         return 13, 3, 2, mgcnn.gmg_weights(2, 2), True
+    if kind == "gmg_v10":
+        return 8, 1, 1, mgcnn.gmg_v10_weights(), True
+    if not os.path.exists(TRAINED):
+        raise SystemExit(f"no trained weights at {TRAINED}: train them (python -m paper_2312_11093_gb300.train) "
+                         "or pick --net gmg_v10")
     blob = np.load(TRAINED)
     return 8, 1, 1, np.ascontiguousarray(blob, dtype=np.float64), False
 
@@ -180,6 +187,8 @@ def cpu_reference(workload: str, net: str, n_full: int = 4095, n_sample: int | N
     def net_for(sts, n):
         if net == "gmg":
             return omg.gmg_equivalent_weights(2, 2), omg.gmg_equivalent_setup(sts, 0.8)
+        if net == "gmg_v10":
+            return omg.gmg_v10_weights(), omg.gmg_v10_setup(sts, 0.8)
         blob = np.load(TRAINED)
         w = unpack_blob(blob, 8, 1, 1)
         return w, omg.setup(w, sts)
@@ -230,15 +239,15 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--n", type=int, default=4095)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--net", default=None, choices=["trained", "gmg"])
+    ap.add_argument("--net", default=None, choices=["trained", "gmg_v10", "gmg"])
     ap.add_argument("--workload", default=None, choices=["channelised", "grf", "batched256"])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg")
-    workload = args.workload or ("channelised" if net == "trained" else "grf")
+    net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg_v10")
+    workload = args.workload or "grf"
     args.net_resolved = net
 
     rank = int(os.environ.get("RANK", "0"))

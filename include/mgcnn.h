@@ -152,8 +152,19 @@ int mgcnn_setup(mgcnn_ctx* ctx, const double* coeff, int n);
  *   right-hand-side copies hold D^{-1} r, so there s[F_J] = omega, s[F_G] = a_C.
  * The matching weights (ResNetDown = nu1 Jacobi layers + one defect layer,
  * ResNetUp = nu2 Jacobi layers) must be loaded with mgcnn_set_weights; the
- * Python binding's gmg_weights() builds that blob.  Requires channels == 13.
- * Errors: SIZE (channels), ARG (omega not in (0,2)), as mgcnn_setup. */
+ * Python binding's gmg_weights() builds that blob.
+ * A context with channels == 8, down_layers == 1 and up_layers == 1 (the
+ * learned network's shape) gets instead the setup tensors of the 8-channel
+ * network that is GMG V(1, 0): one down layer does the Jacobi sweep from
+ * e = 0 and the defect of its result, d = (1-omega) r - sum_{o != C} omega
+ * a_o(p) r(p+o)/a_C(p+o); the up layer is the identity.  Channels T_W, T_E,
+ * T_S, T_N, F_G, F_J, D, E (0-7):
+ *   s[T_o](q) = -omega a_o(q-o)/a_C(q), s[F_G] = 1 - omega, s[F_J] = omega/a_C,
+ *   s[D] = s[E] = 0; with input_diag at the finest level
+ *   s[T_o](q) = -omega a_o(q-o), s[F_G] = (1 - omega) a_C, s[F_J] = omega.
+ * Its weights come from the binding's gmg_v10_weights().
+ * Errors: SIZE (any other channels / layer counts), ARG (omega not in (0,2)),
+ * as mgcnn_setup. */
 int mgcnn_setup_gmg(mgcnn_ctx* ctx, const double* coeff, int n, double omega);
 
 /* Number of doubles of all setup tensors of the current setup:

@@ -257,3 +257,65 @@ def gmg_equivalent_setup(stencils: list[Stencil], omega: float = 0.8, input_diag
         outs.append(s)
     return outs
 
+
+
+# --------------------------------------------------------------------------
+# An 8-channel network (one ResNetDown and one ResNetUp layer, the learned
+# network's shape) that is classical GMG V(1, 0) (Sec. 2.3).  The one down
+# layer does the single pre-smoothing sweep from e = 0 and forms the defect in
+# the same pass: with e = omega D^{-1} r,
+#   d(p) = r(p) - sum_o a_o(p) e(p + o) = (1 - omega) r(p) - sum_{o != C} omega a_o(p) r(p+o) / a_C(p+o),
+# whose off-centre coefficients are again source-side setup tensors
+# (~a_o(q) = -omega a_o(q - o) / a_C(q)).  The up layer is the identity
+# (no post-smoothing), the TCNN adds the bilinear interpolation of the coarse
+# correction into the correction channel.
+# Channels (8): T_W T_E T_S T_N (rhs copies read by the defect's off-centre
+#               taps), F_G (rhs copy, defect centre), F_J (rhs copy, Jacobi),
+#               D (defect), E (correction)
+# --------------------------------------------------------------------------
+V10_CHANNELS = 8
+_T10 = [0, 1, 2, 3]
+_FG10, _FJ10, _D10, _E10 = 4, 5, 6, 7
+
+
+def gmg_v10_weights() -> dict:
+    """Solve-phase weights (C = 8, one down and one up layer) for GMG V(1, 0)."""
+    C = V10_CHANNELS
+    KD = np.zeros((C, C, 3, 3))
+    for ch, (a, b) in zip(_T10, _TAPS[1:]):
+        KD[_D10, ch, a, b] = 1.0
+    KD[_D10, _FG10, 1, 1] = 1.0
+    KD[_E10, _FJ10, 1, 1] = 1.0
+    fw = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 16.0
+    bil = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 4.0
+    R = np.zeros((C, C, 3, 3))
+    for ch in _T10 + [_FG10, _FJ10]:
+        R[ch, _D10] = fw
+    P = np.zeros((C, C, 3, 3))
+    P[_E10, _E10] = bil
+    w_in = np.zeros((C, 1, 3, 3))
+    for ch in _T10 + [_FG10, _FJ10]:
+        w_in[ch, 0, 1, 1] = 1.0
+    w_out = np.zeros((1, C, 3, 3))
+    w_out[0, _E10, 1, 1] = 1.0
+    return {"w_in": w_in, "w_down": KD[None], "w_up": np.zeros((1, C, C, 3, 3)),
+            "w_R": R, "w_P": P, "w_out": w_out}
+
+
+def gmg_v10_setup(stencils: list[Stencil], omega: float = 0.8, input_diag: bool = False) -> list[np.ndarray]:
+    """Setup tensors for `gmg_v10_weights` on every level:
+    s[T_o](q) = -omega a_o(q-o)/a_C(q),  s[F_G] = 1 - omega,  s[F_J] = omega/a_C,  s[D] = s[E] = 0.
+    With input_diag the finest level's rhs copies hold D^{-1} r, so there
+    s[T_o](q) = -omega a_o(q-o), s[F_G] = (1 - omega) a_C, s[F_J] = omega."""
+    outs = []
+    for lev, st in enumerate(stencils):
+        n = st.n
+        s = np.zeros((V10_CHANNELS, n, n))
+        normalised = input_diag and lev == 0
+        for ch, (dy, dx), a in zip(_T10, _OFFS[1:], [st.aW, st.aE, st.aS, st.aN]):
+            shifted = _shift_to_source(-omega * a, dy, dx)
+            s[ch] = shifted if normalised else shifted / st.aC
+        s[_FG10] = (1.0 - omega) * st.aC if normalised else 1.0 - omega
+        s[_FJ10] = omega if normalised else omega / st.aC
+        outs.append(s)
+    return outs

@@ -463,14 +463,16 @@ int mgcnn_setup(mgcnn_ctx* c, const double* coeff, int n) {
 int mgcnn_setup_gmg(mgcnn_ctx* c, const double* coeff, int n, double omega) {
   if (!c || !coeff) return MGCNN_ERR_ARG;
   Status st = [&]() -> Status {
-    if (c->cfg.channels != kGmgChannels)
-      return make_status(MGCNN_ERR_SIZE, "GMG-equivalent setup needs %d channels", kGmgChannels);
+    const bool v10 = c->cfg.channels == kGmgV10Channels && c->cfg.down_layers == 1 && c->cfg.up_layers == 1;
+    if (c->cfg.channels != kGmgChannels && !v10)
+      return make_status(MGCNN_ERR_SIZE, "GMG-equivalent setup needs %d channels, or %d channels with one down "
+                         "and one up layer", kGmgChannels, kGmgV10Channels);
     if (!(omega > 0.0 && omega < 2.0)) return make_status(MGCNN_ERR_ARG, "omega must be in (0, 2)");
     MG_TRY(setup_operators(c, coeff, n));
     for (int l = 0; l < c->L; ++l) {
       if (c->cfg.precision == MGCNN_PREC_FP64)
         MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->s64[l].as<double>(), c->lv[l].n, omega, c->stream,
-                                l == 0 && c->cfg.input_diag));
+                                l == 0 && c->cfg.input_diag, c->cfg.channels));
       else
         MG_TRY(mixed_gmg_setup_level(c, l, omega));
     }

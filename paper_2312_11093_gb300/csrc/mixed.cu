@@ -572,11 +572,12 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega) {
   MG_TRY(ensure(c->x16a[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->x16b[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
-  MG_TRY(ensure(c->setup_a, N * kGmgChannels * sizeof(double)));
+  const int C = c->cfg.channels;
+  MG_TRY(ensure(c->setup_a, N * C * sizeof(double)));
   MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->setup_a.as<double>(), c->lv[l].n, omega, c->stream,
-                          l == 0 && c->cfg.input_diag));
+                          l == 0 && c->cfg.input_diag, C));
   pad_to_bf16_kernel<double><<<grid_for(N * cp, 256), 256, 0, c->stream>>>(c->setup_a.as<double>(),
-                                                                            c->s16[l].as<bf16>(), N, kGmgChannels, cp);
+                                                                            c->s16[l].as<bf16>(), N, C, cp);
   MG_LAUNCH("pad_to_bf16_kernel");
   return {};
 }

@@ -303,8 +303,45 @@ __global__ void gmg_setup_kernel(const double* __restrict__ op, double* __restri
   o[12] = 0.0;
 }
 
+// Setup tensors of the 8-channel network (one down, one up layer) that is GMG
+// V(1, 0): the down layer does the Jacobi sweep from e = 0 and the defect of its
+// result in one pass, d(p) = (1 - omega) r(p) - sum_{o != C} omega a_o(p) r(p+o) / a_C(p+o),
+// so the off-centre setup tensors divide by the SOURCE node's diagonal:
+//   s[T_o](q) = -omega a_o(q-o) / a_C(q) (o = W, E, S, N; 0 if q-o is outside),
+//   s[F_G] = 1 - omega,  s[F_J] = omega / a_C,  s[D] = s[E] = 0.
+// With the normalised input at the finest level (rhs copies hold D^{-1} r):
+//   s[T_o](q) = -omega a_o(q-o),  s[F_G] = (1 - omega) a_C,  s[F_J] = omega.
+__global__ void gmg_v10_setup_kernel(const double* __restrict__ op, double* __restrict__ out, int n, double omega,
+                                     int input_diag_level) {
+  const size_t N = (size_t)n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (int)N) return;
+  const int j = p / n, i = p - j * n;
+  const int dy[4] = {0, 0, -1, 1}, dx[4] = {-1, 1, 0, 0};  // W, E, S, N
+  const double aCq = op[p];
+  double* o = out + (size_t)p * kGmgV10Channels;
+  for (int k = 0; k < 4; ++k) {
+    const int pj = j - dy[k], pi = i - dx[k];
+    double v = 0.0;
+    if (pj >= 0 && pj < n && pi >= 0 && pi < n) {
+      const double a = op[(k + 1) * N + (size_t)pj * n + pi];
+      v = input_diag_level ? -omega * a : -omega * a / aCq;
+    }
+    o[k] = v;
+  }
+  o[4] = input_diag_level ? (1.0 - omega) * aCq : 1.0 - omega;
+  o[5] = input_diag_level ? omega : omega / aCq;
+  o[6] = 0.0;
+  o[7] = 0.0;
+}
+
 Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st,
-                        bool input_diag_level) {
+                        bool input_diag_level, int channels) {
+  if (channels == kGmgV10Channels) {
+    gmg_v10_setup_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, out, n, omega, input_diag_level ? 1 : 0);
+    MG_LAUNCH("gmg_v10_setup_kernel");
+    return {};
+  }
   gmg_setup_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, out, n, omega, input_diag_level ? 1 : 0);
   MG_LAUNCH("gmg_setup_kernel");
   return {};

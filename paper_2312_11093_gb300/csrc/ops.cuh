@@ -31,11 +31,13 @@ Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t
 Status launch_sumsq(const double* v, size_t N, double* partial, cudaStream_t st);
 // out[0] = sum of partial[0..count) in a fixed order (deterministic).
 Status launch_reduce(const double* partial, int count, double* out, cudaStream_t st);
-// Setup tensors of the 13-channel network whose solve phase is classical GMG
-// (weighted Jacobi, full weighting, bilinear): out [N][13] FP64.
+// Setup tensors of the networks whose solve phase is classical GMG (weighted
+// Jacobi, full weighting, bilinear): the 13-channel V(nu1, nu2) network or the
+// 8-channel V(1, 0) network; out [N][channels] FP64.
 constexpr int kGmgChannels = 13;
+constexpr int kGmgV10Channels = 8;
 Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st,
-                        bool input_diag_level = false);
+                        bool input_diag_level = false, int channels = kGmgChannels);
 Status launch_axpy_to(const double* u, const double* e, double* out, size_t N, cudaStream_t st);
 
 // ---- net_generic.cu: FP64 / FP32 direct convolution kernels ----------------

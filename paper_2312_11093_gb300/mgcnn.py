@@ -177,6 +177,36 @@ def gmg_weights(nu1: int = 2, nu2: int = 2) -> np.ndarray:
     return pack_weights(w, C, nu1 + 1, nu2)
 
 
+def gmg_v10_weights() -> np.ndarray:
+    """Weight blob (C = 8, nu_d = nu_u = 1) whose solve phase, with the setup tensors of
+    mgcnn_setup_gmg on such a context, is classical GMG V(1, 0) (Sec. 2.3).
+
+    Channels T_W, T_E, T_S, T_N, F_G, F_J (copies of the level right-hand side), D
+    (defect), E (correction).  The down layer sums the off-centre taps of T_o and the
+    centre of F_G into D and the centre of F_J into E; the up layer is zero (the
+    identity); RCNN carries D by full weighting into every rhs copy; TCNN adds the
+    bilinear interpolation of E into E; the output reads E."""
+    C = 8
+    taps = [(1, 0), (1, 2), (0, 1), (2, 1)]                  # W, E, S, N
+    down = np.zeros((C, C, 3, 3))
+    for ch, (a, b) in enumerate(taps):
+        down[6, ch, a, b] = 1.0
+    down[6, 4, 1, 1] = 1.0
+    down[7, 5, 1, 1] = 1.0
+    stencil121 = np.outer([1.0, 2.0, 1.0], [1.0, 2.0, 1.0])
+    R = np.zeros((C, C, 3, 3))
+    R[:6, 6] = stencil121 / 16.0
+    P = np.zeros((C, C, 3, 3))
+    P[7, 7] = stencil121 / 4.0
+    w_in = np.zeros((C, 1, 3, 3))
+    w_in[:6, 0, 1, 1] = 1.0
+    w_out = np.zeros((1, C, 3, 3))
+    w_out[0, 7, 1, 1] = 1.0
+    w = {"w_in": w_in, "w_down": down[None], "w_up": np.zeros((1, C, C, 3, 3)), "w_R": R, "w_P": P,
+         "w_out": w_out}
+    return pack_weights(w, C, 1, 1)
+
+
 class Solver:
     """One MGCNN context: weights, a setup for one coefficient field, solves."""
 

@@ -113,27 +113,59 @@ RECIPE_63_127 = [((63, 127), (32, 32), 2000, 1e-3)]
 
 def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int = 8, seed: int = 0,
           log_every: int = 50, out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size=None,
-          setup_scale: int = 0, mg_transfers: bool = True, schedule=None):
+          setup_scale: int = 0, mg_transfers: bool = True, schedule=None, snapshot_every: int = 25,
+          spike: float = 5.0, max_restarts: int = 8):
     """Run the schedule (or a single phase when steps/lr/per_size are given) and
-    return (weights, loss history)."""
+    return (weights, loss history).
+
+    Safeguard against blow-ups: the K-cycle loss of a network whose cycle stops
+    contracting on one problem grows like rho^K, and Adam does not come back from
+    there.  Every snapshot_every steps the weights are copied to the host when the
+    step's loss is finite and within `spike` x the median of the last 20 losses;
+    a loss outside that band restores the last snapshot in a fresh context (fresh
+    Adam moments) and halves the phase's learning rate."""
     if schedule is None:
         schedule = SCHEDULE if steps is None else [((63, 127), per_size or (32, 32), steps, lr or 1e-3)]
-    sv = mgcnn.Solver(C, 1, 1, precision=precision, b=(1.0, 0.5), scale_by_diag=setup_scale, input_diag=True)
-    sv.set_weights(init_weights(C, 1, 1, np.random.default_rng(seed), mg_transfers=mg_transfers))
+
+    def fresh(weights):
+        sv = mgcnn.Solver(C, 1, 1, precision=precision, b=(1.0, 0.5), scale_by_diag=setup_scale, input_diag=True)
+        sv.set_weights(weights)
+        return sv
+
+    sv = fresh(init_weights(C, 1, 1, np.random.default_rng(seed), mg_transfers=mg_transfers))
+    snap, snap_step = sv.get_weights(), 0
     hist = []
     t0 = time.time()
-    step = 0
+    step, restarts = 0, 0
     for sizes, counts, nsteps, plr in schedule:
         for _ in range(nsteps):
-            loss = sv.train_step(make_batch(step, sizes, counts), K, plr)
-            if not np.isfinite(loss):
-                raise RuntimeError(f"loss became non-finite at step {step}")
+            try:
+                loss = sv.train_step(make_batch(step, sizes, counts), K, plr)
+            except mgcnn.MGCNNError as err:
+                if err.status != mgcnn.ERR_NONFINITE:
+                    raise
+                loss = float("inf")
+            recent = hist[-20:]
+            bad = not np.isfinite(loss) or (len(recent) >= 5 and loss > spike * float(np.median(recent)))
+            if bad:
+                restarts += 1
+                if restarts > max_restarts:
+                    raise RuntimeError(f"loss blew up {restarts} times (last at step {step})")
+                sv.close()
+                sv = fresh(snap)
+                plr *= 0.5
+                print(json.dumps({"step": step, "restart_from": snap_step, "loss": loss, "lr": plr}), flush=True)
+                step += 1
+                continue
             hist.append(loss)
+            if step % snapshot_every == 0:
+                snap, snap_step = sv.get_weights(), step
             if step % log_every == 0:
-                print(json.dumps({"step": step, "sizes": list(sizes), "loss": loss,
+                print(json.dumps({"step": step, "sizes": list(sizes), "loss": loss, "lr": plr,
                                   "elapsed_s": round(time.time() - t0, 1)}), flush=True)
             step += 1
     w = sv.get_weights()
+    sv.close()
     if out:
         os.makedirs(os.path.dirname(out), exist_ok=True)
         np.save(out, w)

@@ -49,3 +49,14 @@ def test_weight_count_matches_layout(lib):
 def test_status_strings(lib):
     assert lib.mgcnn_status_string(0) == b"MGCNN_OK"
     assert lib.mgcnn_status_string(-6) == b"MGCNN_ERR_NONFINITE"
+
+
+def test_v10_blob_matches_oracle_construction():
+    """The binding's V(1,0) weight blob equals the oracle's construction packed in
+    the library's layout (host logic only)."""
+    import numpy as np
+
+    from oracle import mgcnn as omg
+    from paper_2312_11093_gb300 import mgcnn
+    ref = mgcnn.pack_weights(omg.gmg_v10_weights(), omg.V10_CHANNELS, 1, 1)
+    assert np.array_equal(mgcnn.gmg_v10_weights(), ref)

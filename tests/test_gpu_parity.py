@@ -350,3 +350,70 @@ def test_device_loop_equals_host_loop(M, n, tol, maxit):
     assert out[1][0] == out[0][0] and out[1][1] == out[0][1]
     assert np.array_equal(out[1][2], out[0][2])
     assert np.array_equal(out[1][3], out[0][3])
+
+
+# ---- the 8-channel GMG V(1,0) network (the learned network's shape) ----------
+@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
+@pytest.mark.parametrize("input_diag", [True, False])
+def test_v10_setup_matches_oracle(M, precision, input_diag):
+    """mgcnn_setup_gmg on an 8-channel, one-down-one-up context builds the V(1,0)
+    setup tensors of the oracle's construction (BF16: one rounding, 2^-9)."""
+    n = 127
+    k, f = problem(n, 41, "blocks")
+    b = (-0.6, 1.1)
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    s_ref = to_nhwc(omg.gmg_v10_setup(sts, 0.8, input_diag=input_diag))
+    sv = M.Solver(8, 1, 1, precision=precision, b=b, input_diag=input_diag)
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_gmg(k.ravel().copy(), n, 0.8)
+    got = sv.get_setup_tensors()
+    if precision == "fp64":
+        assert relerr(got, s_ref) <= 1e-15
+    else:
+        assert np.all(np.abs(got - s_ref) <= 2.0 ** -8 * np.abs(s_ref))
+
+
+@pytest.mark.parametrize("input_diag", [True, False])
+def test_v10_fp64_iterate_for_iterate(M, input_diag):
+    """FP64 path with the V(1,0) network: the oracle's GMG V(1,0) iteration count,
+    every cycle within 1e-12 of the oracle's on the oracle's own iterate."""
+    n = 63
+    k, f = problem(n, 42)
+    b = (1.0, 0.5)
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    u_o, it_o, hist_o, its_o = ogmg.stationary_solve(sts, f, None, 1e-8, 200, 1, 0, 0.8)
+    sv = M.Solver(8, 1, 1, precision="fp64", b=b, input_diag=input_diag)
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_gmg(k.ravel().copy(), n, 0.8)
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(f.ravel().copy(), u, 1e-8, 200)
+    assert st == M.OK and it == it_o
+    assert relerr(u, u_o) <= 1e-12
+    for k_ in range(0, it_o, 5):
+        r = f - oop.apply(sts[0], its_o[k_])
+        e = sv.vcycle(r.ravel().copy())
+        assert relerr(its_o[k_].ravel() + e, its_o[k_ + 1]) <= 1e-12, k_
+
+
+@pytest.mark.parametrize("n", [255, 1023])
+def test_v10_fused_mixed_reaches_1e8_in_fp64(M, n):
+    """The fused BF16 level kernels with the V(1,0) network inside the FP64 defect
+    correction reach relres 1e-8, checked by the oracle's own residual, within a
+    few cycles of the FP64 path."""
+    rng = np.random.default_rng(43 + n)
+    t = rng.uniform(0.0, 2.0 * np.pi)
+    k = inputs.lognormal_k(n, 0.05, rng)
+    f = inputs.normal_rhs(n, rng)
+    b = (10.0 * np.cos(t), 10.0 * np.sin(t))
+    its = {}
+    for prec in ("fp64", "mixed_bf16"):
+        sv = M.Solver(8, 1, 1, precision=prec, b=b)
+        sv.set_weights(M.gmg_v10_weights())
+        sv.setup_gmg(k.ravel().copy(), n, 0.8)
+        u = np.zeros(n * n)
+        st, its[prec], hist = sv.solve(f.ravel().copy(), u, 1e-8, 200)
+        assert st == M.OK
+        sts = oop.level_stencils_div(k, b, num_levels(n))
+        rtrue = f - oop.apply(sts[0], u.reshape(n, n))
+        assert np.linalg.norm(rtrue) / np.linalg.norm(f) <= 1.05e-8
+    assert its["mixed_bf16"] <= its["fp64"] + 3

@@ -141,3 +141,19 @@ def test_linearity_with_input_normalisation():
     lhs = mg.solve_phase(w, s, 3.0 * f + g, d_inv=d)
     rhs = 3.0 * mg.solve_phase(w, s, f, d_inv=d) + mg.solve_phase(w, s, g, d_inv=d)
     assert np.linalg.norm(lhs - rhs) <= 1e-13 * np.linalg.norm(lhs)
+
+
+@pytest.mark.parametrize("input_diag", [False, True])
+def test_v10_network_is_gmg_v10(input_diag):
+    """The 8-channel, one-down-one-up network with the V(1,0) weights and setup
+    tensors reproduces GMG V(1, 0) iterate for iterate (Sec. 2.3), including the
+    normalised input B r = Net(D^{-1} r)."""
+    for n, b in [(31, (1.0, 0.5)), (63, (-0.3, 2.0))]:
+        sts, f = _problem(n, n + 7, b=b)
+        w = mg.gmg_v10_weights()
+        s = mg.gmg_v10_setup(sts, 0.8, input_diag=input_diag)
+        u_m, it_m, _, its_m = mg.stationary_solve(w, s, sts[0], f, None, 1e-9, 200, input_diag=input_diag)
+        u_g, it_g, _, its_g = gmg.stationary_solve(sts, f, None, 1e-9, 200, 1, 0, 0.8)
+        assert it_m == it_g < 200
+        for a, c in zip(its_m[1:], its_g[1:]):
+            assert np.linalg.norm(a - c) <= 1e-12 * np.linalg.norm(c)
