@@ -290,7 +290,9 @@ int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
  * since the last read (classes: 0 residual, 1 ResNet layer, 2 restriction,
  * 3 prolongation-add into the finest level, 4 reChannel-in, 5 reChannel-out
  * with update, 6 fused down kernel, 7 fused up kernel) and clears them.  Timing adds one event pair per bracketed
- * launch. */
+ * launch.  While profiling is on, mgcnn_solve runs its host-driven loop (not
+ * the device-side loop of MGCNN_OPT_DEVICE_LOOP), so that every bracketed
+ * kernel is a plain launch on the context's stream. */
 long long mgcnn_kernel_launches(void);
 int mgcnn_profile(mgcnn_ctx* ctx, int enable);
 int mgcnn_profile_read(mgcnn_ctx* ctx, double* ms, long long* counts, int nkinds);

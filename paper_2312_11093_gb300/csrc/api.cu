@@ -559,7 +559,7 @@ int mgcnn_residual(mgcnn_ctx* c, const double* f, const double* u, double* r, do
     bool host = false;
     MG_TRY(stage_out(r, N, c->r, &dr, &host));
     MG_TRY(launch_residual(df, du, c->op[0].as<double>(), dr, nullptr, c->partial.as<double>(), c->n, c->stream));
-    MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>(), c->stream));
+    MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), c->scalars.as<double>(), c->stream));
     MG_TRY(stage_out_finish(c, r, dr, N, host));
     double v = 0.0;
     MG_TRY(read_scalar(c, 0, &v));
@@ -608,7 +608,7 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
       MG_TRY(stage_out_finish(c, u, du, N, host));
       return sync(c);
     }
-    if (c->device_loop) {
+    if (c->device_loop && !c->prof) {   // profiling brackets need plain stream launches
       bool used = false;
       Status d = solve_on_device(c, df, du, tol, maxit, iters, relres, &used);
       if (used || !d.ok()) {
@@ -626,7 +626,7 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
                              mixed ? c->r32.as<float>() : nullptr, c->partial.as<double>(), c->n, c->stream,
                              c->cfg.input_diag ? c->dinv32.as<float>() : nullptr));
       prof_end(c, ps);
-      MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>(), c->stream));
+      MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), c->scalars.as<double>(), c->stream));
       double rn2 = 0.0;
       MG_TRY(read_scalar(c, 0, &rn2));
       const double rel = std::sqrt(rn2 / fn2);
@@ -773,7 +773,7 @@ int mgcnn_gmg_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int ma
       for (int k = 0;; ++k) {
         MG_TRY(launch_residual(df, du, c->op[0].as<double>(), g.r[0], nullptr, c->partial.as<double>(), c->n,
                                c->stream));
-        MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>(), c->stream));
+        MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), c->scalars.as<double>(), c->stream));
         double rn2 = 0.0;
         MG_TRY(read_scalar(c, 0, &rn2));
         const double rel = std::sqrt(rn2 / fn2);

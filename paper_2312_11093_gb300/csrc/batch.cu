@@ -226,7 +226,7 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff) {
       cs[l] = k.xb[l].as<bf16>();
     }
     const SetupWeights sw = setup_weights(c);
-    MG_TRY(setup_fused_levels(k.L, k.nl, k.B, ops, ss, cs, sw.frags, sw.fp, c->cfg.scale_by_diag, st));
+    MG_TRY(setup_fused_levels(k.L, k.nl, k.B, ops, ss, cs, sw, c->cfg.scale_by_diag, st));
   } else {
     MG_TRY(batched_setup_net(c, k));
   }
@@ -264,7 +264,7 @@ Status capture_cycle(mgcnn_ctx* c) {
     MG_CUDA(cudaEventRecord(c->bfork, main));
     for (BatchClass& k : c->bcls) {
       const size_t N0 = (size_t)k.n * k.n;
-      const int nblk = reduction_blocks(N0);
+      const int nblk = residual_blocks(N0);
       int* state = k.state.as<int>();
       MG_CUDA(cudaStreamWaitEvent(k.stream, c->bfork, 0));
       MG_TRY(launch_residual(k.f.as<double>(), k.u.as<double>(), k.op[0].as<double>(), nullptr, k.r32.as<float>(),

@@ -64,6 +64,23 @@ struct Level {
   size_t N() const { return (size_t)n * n; }
 };
 
+// FP32 weights of the fused kernels' small layers (8 channels), passed to the
+// kernels by value: they sit in the kernel-parameter constant bank and the
+// unrolled loops read them as constant operands, with no shared-memory loads.
+// Layouts: w_in[t][co], w_out[t][ci], w_P[tap][ci][co] (t, tap = 3 a + b).
+struct SmallWeights {
+  float w_in[72];
+  float w_out[72];
+  float w_P[576];
+};
+
+// FP32 weights of the fused setup kernel's small layers, by value like
+// SmallWeights: v[0..32) = b_i [4][8], v[32..392) = W_cin [8][5][9],
+// v[392..400) = b_cin [8].
+struct SetupSmallWeights {
+  float v[400];
+};
+
 }  // namespace mgcnn
 
 // The opaque context of the ABI.
@@ -100,6 +117,8 @@ struct mgcnn_ctx {
   mgcnn::DevBuf x16a[mgcnn::kMaxLevels];  // BF16 state ping-pong, [n_l^2][cp]
   mgcnn::DevBuf x16b[mgcnn::kMaxLevels];
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
+  mgcnn::SmallWeights small_w{};          // host copy of the fused kernels' small layers
+  mgcnn::SetupSmallWeights setup_small_w{};  // host copy of the fused setup kernel's small layers
   mgcnn::DevBuf s32tmp;                   // FP32 setup output before the BF16 cast
   mgcnn::DevBuf scalars;                  // device scalars (norms)
   // training (train.cu)

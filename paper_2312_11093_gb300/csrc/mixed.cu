@@ -16,6 +16,7 @@
 // Defect correction: the residual r (FP64, computed elsewhere) enters scaled
 // by alpha = sqrt(N)/||r||_2 -- exact by linearity (P2, Sec. 3.1) -- and the
 // correction leaves as e/alpha, added to u in FP64.
+#include <algorithm>
 #include <cmath>
 
 #include "mixed.cuh"
@@ -399,7 +400,7 @@ Status vcycle_cp(mgcnn_ctx* c, const float* r32, const double* norm2, double* e,
   const float* w_out = reinterpret_cast<const float*>(wb + ml.w_out);
   const float* w_P = reinterpret_cast<const float*>(wb + ml.w_P);
   if (CP == 8 && c->fused && fused_supported(c))
-    return vcycle_fused_cp8(c, r32, norm2, e, u_skip, f_down, f_up, f_R, w_in, w_out, w_P);
+    return vcycle_fused_cp8(c, r32, norm2, e, u_skip, fused_weights(c));
   bf16* x[kMaxLevels];
   bf16* t[kMaxLevels];
   for (int l = 0; l < c->L; ++l) {
@@ -462,8 +463,7 @@ FusedWeights fused_weights(const mgcnn_ctx* c) {
   const MixLayout ml = mix_layout(c);
   const char* wb = c->wmix.as<char>();
   return FusedWeights{reinterpret_cast<const uint32_t*>(wb + ml.down), reinterpret_cast<const uint32_t*>(wb + ml.up),
-                      reinterpret_cast<const uint32_t*>(wb + ml.R), reinterpret_cast<const float*>(wb + ml.w_in),
-                      reinterpret_cast<const float*>(wb + ml.w_out), reinterpret_cast<const float*>(wb + ml.w_P)};
+                      reinterpret_cast<const uint32_t*>(wb + ml.R), c->small_w};
 }
 
 Status mixed_set_weights(mgcnn_ctx* c) {
@@ -492,6 +492,18 @@ Status mixed_set_weights(mgcnn_ctx* c) {
   for (int ci = 0; ci < C; ++ci)
     for (int co = 0; co < C; ++co)
       for (int t = 0; t < 9; ++t) wP[(ci * ml.cp + co) * 9 + t] = (float)w[c->wl.w_P + ((size_t)ci * C + co) * 9 + t];
+  if (ml.cp == 8) {
+    // small layers of the fused kernels, zero beyond C channels
+    SmallWeights& sw = c->small_w;
+    sw = SmallWeights{};
+    for (int t = 0; t < 9; ++t)
+      for (int ch = 0; ch < C; ++ch) {
+        sw.w_in[t * 8 + ch] = (float)w[c->wl.w_in + ch * 9 + t];
+        sw.w_out[t * 8 + ch] = (float)w[c->wl.w_out + ch * 9 + t];
+        for (int co = 0; co < C; ++co)
+          sw.w_P[(t * 8 + ch) * 8 + co] = (float)w[c->wl.w_P + ((size_t)ch * C + co) * 9 + t];
+      }
+  }
   if (C == 8) {
     // fused setup network: 4 tanh layers and the setup RCNN as fragments; b_i, W_cin, b_cin in FP32
     uint32_t* sf = reinterpret_cast<uint32_t*>(blob.data() + ml.s_frag);
@@ -501,6 +513,8 @@ Status mixed_set_weights(mgcnn_ctx* c) {
     for (int i = 0; i < 4 * 8; ++i) sp[i] = (float)w[c->wl.sb + i];
     for (int i = 0; i < 8 * kFeatures * 9; ++i) sp[32 + i] = (float)w[c->wl.sw_in + i];
     for (int i = 0; i < 8; ++i) sp[32 + 8 * kFeatures * 9 + i] = (float)w[c->wl.sb_in + i];
+    static_assert(32 + 8 * kFeatures * 9 + 8 == sizeof(SetupSmallWeights) / sizeof(float), "setup small weights");
+    std::copy(sp, sp + 400, c->setup_small_w.v);
   }
   MG_TRY(ensure(c->wmix, ml.bytes));
   MG_CUDA(cudaMemcpyAsync(c->wmix.p, blob.data(), ml.bytes, cudaMemcpyHostToDevice, c->stream));
@@ -511,7 +525,7 @@ Status mixed_set_weights(mgcnn_ctx* c) {
 SetupWeights setup_weights(const mgcnn_ctx* c) {
   const MixLayout ml = mix_layout(c);
   const char* wb = c->wmix.as<char>();
-  return SetupWeights{reinterpret_cast<const uint32_t*>(wb + ml.s_frag), reinterpret_cast<const float*>(wb + ml.s_fp)};
+  return SetupWeights{reinterpret_cast<const uint32_t*>(wb + ml.s_frag), c->setup_small_w};
 }
 
 Status setup_mixed(mgcnn_ctx* c) {
@@ -535,7 +549,7 @@ Status setup_mixed(mgcnn_ctx* c) {
     }
     MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
     const SetupWeights sw = setup_weights(c);
-    return setup_fused_levels(c->L, ns, 1, ops, ss, cs, sw.frags, sw.fp, c->cfg.scale_by_diag, c->stream);
+    return setup_fused_levels(c->L, ns, 1, ops, ss, cs, sw, c->cfg.scale_by_diag, c->stream);
   }
   size_t total = 0;
   for (int l = 0; l < c->L; ++l) total += c->lv[l].N() * C;

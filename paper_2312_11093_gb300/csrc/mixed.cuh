@@ -31,8 +31,8 @@ struct FusedLevels {
   __nv_bfloat16* xb[kMaxLevels] = {};
 };
 struct FusedWeights {
-  const uint32_t *f_down, *f_up, *f_R;
-  const float *w_in, *w_out, *w_P;
+  const uint32_t *f_down, *f_up, *f_R;   // mma B fragments (device)
+  SmallWeights small;                    // by value, see SmallWeights
 };
 Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
                            const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
@@ -44,18 +44,16 @@ FusedWeights fused_weights(const mgcnn_ctx* c);
 bool fused_supported(const mgcnn_ctx* c);
 // setup_fused.cu: Algorithm 2 for 8 channels, one fused kernel per level
 struct SetupWeights {
-  const uint32_t* frags;
-  const float* fp;
+  const uint32_t* frags;      // mma B fragments (device)
+  SetupSmallWeights small;    // by value
 };
 SetupWeights setup_weights(const mgcnn_ctx* c);
 Status setup_fused_levels(int L, const int* n, int batch, const double* const* op, __nv_bfloat16* const* s,
-                          __nv_bfloat16* const* coef, const uint32_t* frags, const float* fp, int mode,
-                          cudaStream_t st);
+                          __nv_bfloat16* const* coef, const SetupWeights& w, int mode, cudaStream_t st);
 // [N][C] FP32 -> [N][cp] BF16, zero padded
 Status pad_setup_bf16(const float* src, __nv_bfloat16* dst, size_t N, int C, int cp, cudaStream_t st);
 Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
-                        const uint32_t* f_down, const uint32_t* f_up, const uint32_t* f_R, const float* w_in,
-                        const float* w_out, const float* w_P);
+                        const FusedWeights& w);
 // Defined in api.cu: Algorithm 2 in FP32 into out[l] ([n_l^2][C] floats).
 Status run_setup_net_fp32(mgcnn_ctx* c, float* const* out);
 

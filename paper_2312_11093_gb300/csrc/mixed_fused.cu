@@ -105,7 +105,7 @@ __device__ __forceinline__ double alpha_of(const double* norm2, size_t N) {
 //   Rg (residual, halo 2):   rows -2..XH+1, cols -2..XW+1   (finest level only)
 template <int FH, int FW, bool FIRST, bool HAS_R>
 __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, const double* __restrict__ norm2,
-                                                  const float* __restrict__ w_in, const bf16* __restrict__ x0,
+                                                  const __grid_constant__ SmallWeights sw, const bf16* __restrict__ x0,
                                                   const bf16* __restrict__ s, const uint32_t* __restrict__ fK,
                                                   const uint32_t* __restrict__ fR, bf16* __restrict__ xdown,
                                                   bf16* __restrict__ xc, int n, const int* __restrict__ active) {
@@ -116,7 +116,6 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   __shared__ __align__(16) uint4 xs[ZH * ZW];   // x_in (BF16), for the skip
   __shared__ __align__(16) uint4 xd[XH * XW];   // layer output
   __shared__ float rs[FIRST ? RH * RW : 1];
-  __shared__ float wi[FIRST ? 72 : 1];
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t N = (size_t)n * n;
@@ -144,8 +143,12 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   }
 
   if constexpr (FIRST) {
-    const float alpha = (float)alpha_of(norm2, N);
-    for (int e = threadIdx.x; e < 72; e += NT) wi[e] = w_in[e];
+    // the input scale alpha = sqrt(N / ||r||^2): FP64 divide and square root are
+    // dozens of FP64-pipe instructions, so one thread computes it per block
+    __shared__ float s_alpha;
+    if (threadIdx.x == 0) s_alpha = (float)alpha_of(norm2, N);
+    __syncthreads();
+    const float alpha = s_alpha;
     for (int e = threadIdx.x; e < RH * RW; e += NT) {
       const int rr = e / RW, cc = e - rr * RW;
       const int gj = j0 + rr - 2, gi = i0 + cc - 2;
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
         for (int co = 0; co < 8; ++co) {
           float a = 0.f;
 #pragma unroll
-          for (int t = 0; t < 9; ++t) a += wi[co * 9 + t] * rv[t];
+          for (int t = 0; t < 9; ++t) a += sw.w_in[t * 8 + co] * rv[t];
           o[co] = a;
         }
         xv = make_uint4(f2bf(o[0], o[1]), f2bf(o[2], o[3]), f2bf(o[4], o[5]), f2bf(o[6], o[7]));
@@ -240,6 +243,64 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   }
 }
 
+// Shared-memory view of an up-kernel block for the TCNN pass.
+struct TcnnTile {
+  uint4* ps;          // P region: x_down in, x_pre out
+  uint4* zs;          // P region: s in, s * x_pre out
+  const uint4* cs;    // staged coarse pixels
+  int pj0, pi0;       // global coordinates of P's corner
+  int cj0, ci0;       // global coordinates of cs's corner
+  int n, nc;
+};
+
+// Fine pixels of P with gj & 1 == A and gi & 1 == B.  A fine row 2J + a gets
+// coarse row J through TCNN tap row a: a in {0, 2} for even rows, a = 1 for
+// odd rows (likewise columns), so each class has a fixed tap list.
+template <int A, int B, int PH, int PW, int CW>
+__device__ __forceinline__ void tcnn_class(const TcnnTile& t, const SmallWeights& sw) {
+  const int r0 = (A ^ t.pj0) & 1, c0 = (B ^ t.pi0) & 1;   // first P row / column of the class
+  const int nr = (PH - r0 + 1) >> 1, ncl = (PW - c0 + 1) >> 1;
+  for (int e = threadIdx.x; e < nr * ncl; e += NT) {
+    const int rr = e / ncl, cc = e - rr * ncl;
+    const int pr = r0 + 2 * rr, pc = c0 + 2 * cc;
+    const int gj = t.pj0 + pr, gi = t.pi0 + pc;
+    if (gj < 0 || gj >= t.n || gi < 0 || gi >= t.n) continue;
+    const int pe = pr * PW + pc;
+    const uint4 xv = t.ps[pe];
+    float acc[8];
+    {
+      const float2 a0 = bf2f(xv.x), a1 = bf2f(xv.y), a2 = bf2f(xv.z), a3 = bf2f(xv.w);
+      acc[0] = a0.x; acc[1] = a0.y; acc[2] = a1.x; acc[3] = a1.y;
+      acc[4] = a2.x; acc[5] = a2.y; acc[6] = a3.x; acc[7] = a3.y;
+    }
+#pragma unroll
+    for (int x = 0; x < (A ? 1 : 2); ++x) {
+      const int ta = A ? 1 : 2 * x;
+      const int J = (gj - ta) >> 1;   // gj - ta is even and >= -2
+      if (J < 0 || J >= t.nc) continue;
+#pragma unroll
+      for (int y = 0; y < (B ? 1 : 2); ++y) {
+        const int tb = B ? 1 : 2 * y;
+        const int I = (gi - tb) >> 1;
+        if (I < 0 || I >= t.nc) continue;
+        const uint4 cv = t.cs[(J - t.cj0) * CW + I - t.ci0];
+        const int tap = ta * 3 + tb;
+        float xin[8];
+        const float2 b0 = bf2f(cv.x), b1 = bf2f(cv.y), b2 = bf2f(cv.z), b3 = bf2f(cv.w);
+        xin[0] = b0.x; xin[1] = b0.y; xin[2] = b1.x; xin[3] = b1.y;
+        xin[4] = b2.x; xin[5] = b2.y; xin[6] = b3.x; xin[7] = b3.y;
+#pragma unroll
+        for (int ci = 0; ci < 8; ++ci)
+#pragma unroll
+          for (int co = 0; co < 8; ++co) acc[co] += sw.w_P[(tap * 8 + ci) * 8 + co] * xin[ci];
+      }
+    }
+    const uint4 xo = make_uint4(f2bf(acc[0], acc[1]), f2bf(acc[2], acc[3]), f2bf(acc[4], acc[5]), f2bf(acc[6], acc[7]));
+    t.ps[pe] = xo;
+    t.zs[pe] = mul8(xo, t.zs[pe]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Up kernel.  Output tile 16 x 32 at (j0, i0).  H = halo of the layer output
 // that is needed (1 at the finest level for W_out, else 0).
@@ -248,8 +309,8 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
 //   coarse rows/cols J: floor((j0 - H - 1) / 2) - 1 .. , enough for P
 template <int FH, int FW, bool LAST, bool HAS_P>
 __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, const bf16* __restrict__ xcf,
-                                                const float* __restrict__ wP, const bf16* __restrict__ s,
-                                                const uint32_t* __restrict__ fK, const float* __restrict__ w_out,
+                                                const __grid_constant__ SmallWeights sw, const bf16* __restrict__ s,
+                                                const uint32_t* __restrict__ fK,
                                                 const double* __restrict__ norm2, const double* __restrict__ u_in,
                                                 bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
                                                 const int* __restrict__ active) {
@@ -261,8 +322,6 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
   __shared__ __align__(16) uint4 zs[PH * PW];       // s * x_pre
   __shared__ __align__(16) uint4 os[LAST ? OH * OW : 1];
   __shared__ __align__(16) uint4 cs[HAS_P ? CH * CW : 1];
-  __shared__ float wp[HAS_P ? 8 * 8 * 9 : 1];
-  __shared__ float wo[LAST ? 72 : 1];
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int pj0 = j0 - H - 1, pi0 = i0 - H - 1;      // global coords of P's corner
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -282,6 +341,9 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
       xfin += bz * N * 8;
     }
   }
+  // 1 / alpha for the output layer, once per block (see the down kernel)
+  __shared__ float s_inv_alpha;
+  if (LAST && threadIdx.x == 0) s_inv_alpha = (float)(1.0 / alpha_of(norm2, (size_t)n * n));
   // coarse corner: the smallest J with 2J + 2 >= pj0
   const int cj0 = (pj0 - 2 >= 0) ? (pj0 - 2) / 2 : -((2 - pj0 + 1) / 2);
   const int ci0 = (pi0 - 2 >= 0) ? (pi0 - 2) / 2 : -((2 - pi0 + 1) / 2);
@@ -290,7 +352,6 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
 #pragma unroll
   for (int k = 0; k < 9; ++k) wk[k] = fK[k * 32 + lane];
   if constexpr (HAS_P) {
-    for (int e = threadIdx.x; e < 8 * 8 * 9; e += NT) wp[e] = wP[e];
     for (int e = threadIdx.x; e < CH * CW; e += NT) {
       const int cr = e / CW, cc = e - cr * CW;
       const int J = cj0 + cr, I = ci0 + cc;
@@ -298,47 +359,31 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
                                                      : make_uint4(0, 0, 0, 0);
     }
   }
-  if constexpr (LAST)
-    for (int e = threadIdx.x; e < 72; e += NT) wo[e] = w_out[e];
-  __syncthreads();
+  // (the barrier below, after x_down and s are staged, also covers cs)
 
-  // x_pre on P
+  // x_pre on P in two passes.  (1) x_down and s, coalesced.  (2) per parity
+  // class (gj & 1, gi & 1) of the fine pixel, the TCNN taps that reach it --
+  // 4, 2, 2 or 1, known at compile time, so the weights are constant operands
+  // -- x_pre = x_down + TCNN(x_c) rounded once, then z = s * x_pre.
   for (int e = threadIdx.x; e < PH * PW; e += NT) {
     const int pr = e / PW, pc = e - pr * PW;
     const int gj = pj0 + pr, gi = pi0 + pc;
-    uint4 xv = make_uint4(0, 0, 0, 0), zv = xv;
+    uint4 xv = make_uint4(0, 0, 0, 0), sv = xv;
     if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
       const size_t qg = (size_t)gj * n + gi;
       xv = reinterpret_cast<const uint4*>(xdown)[qg];
-      if constexpr (HAS_P) {
-        float acc[8];
-        const float2 a0 = bf2f(xv.x), a1 = bf2f(xv.y), a2 = bf2f(xv.z), a3 = bf2f(xv.w);
-        acc[0] = a0.x; acc[1] = a0.y; acc[2] = a1.x; acc[3] = a1.y;
-        acc[4] = a2.x; acc[5] = a2.y; acc[6] = a3.x; acc[7] = a3.y;
-        for (int ta = 0; ta < 3; ++ta) {
-          const int dj = gj - ta;
-          if (dj < 0 || (dj & 1) || (dj >> 1) >= nc) continue;
-          for (int tb = 0; tb < 3; ++tb) {
-            const int di = gi - tb;
-            if (di < 0 || (di & 1) || (di >> 1) >= nc) continue;
-            const uint4 cv = cs[((dj >> 1) - cj0) * CW + (di >> 1) - ci0];
-            const int tap = ta * 3 + tb;
-            float xin[8];
-            const float2 b0 = bf2f(cv.x), b1 = bf2f(cv.y), b2 = bf2f(cv.z), b3 = bf2f(cv.w);
-            xin[0] = b0.x; xin[1] = b0.y; xin[2] = b1.x; xin[3] = b1.y;
-            xin[4] = b2.x; xin[5] = b2.y; xin[6] = b3.x; xin[7] = b3.y;
-#pragma unroll
-            for (int ci = 0; ci < 8; ++ci)
-#pragma unroll
-              for (int co = 0; co < 8; ++co) acc[co] += wp[(ci * 8 + co) * 9 + tap] * xin[ci];
-          }
-        }
-        xv = make_uint4(f2bf(acc[0], acc[1]), f2bf(acc[2], acc[3]), f2bf(acc[4], acc[5]), f2bf(acc[6], acc[7]));
-      }
-      zv = mul8(xv, reinterpret_cast<const uint4*>(s)[qg]);
+      sv = reinterpret_cast<const uint4*>(s)[qg];
     }
     ps[e] = xv;
-    zs[e] = zv;
+    zs[e] = HAS_P ? sv : mul8(xv, sv);
+  }
+  if constexpr (HAS_P) {
+    __syncthreads();
+    TcnnTile t{ps, zs, cs, pj0, pi0, cj0, ci0, n, nc};
+    tcnn_class<0, 0, PH, PW, CW>(t, sw);
+    tcnn_class<0, 1, PH, PW, CW>(t, sw);
+    tcnn_class<1, 0, PH, PW, CW>(t, sw);
+    tcnn_class<1, 1, PH, PW, CW>(t, sw);
   }
   __syncthreads();
 
@@ -371,7 +416,7 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
   }
   if constexpr (LAST) {
     __syncthreads();
-    const double inv_alpha = 1.0 / alpha_of(norm2, (size_t)n * n);
+    const float inv_alpha = s_inv_alpha;
     for (int e = threadIdx.x; e < FH * FW; e += NT) {
       const int rr = e / FW, cc = e - rr * FW;
       const int gj = j0 + rr, gi = i0 + cc;
@@ -381,11 +426,12 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
       for (int t = 0; t < 9; ++t) {
         const uint4 v = os[(rr + t / 3) * OW + cc + t % 3];
         const float2 a0 = bf2f(v.x), a1 = bf2f(v.y), a2 = bf2f(v.z), a3 = bf2f(v.w);
-        acc += wo[0 * 9 + t] * a0.x + wo[1 * 9 + t] * a0.y + wo[2 * 9 + t] * a1.x + wo[3 * 9 + t] * a1.y +
-               wo[4 * 9 + t] * a2.x + wo[5 * 9 + t] * a2.y + wo[6 * 9 + t] * a3.x + wo[7 * 9 + t] * a3.y;
+        acc += sw.w_out[t * 8 + 0] * a0.x + sw.w_out[t * 8 + 1] * a0.y + sw.w_out[t * 8 + 2] * a1.x +
+               sw.w_out[t * 8 + 3] * a1.y + sw.w_out[t * 8 + 4] * a2.x + sw.w_out[t * 8 + 5] * a2.y +
+               sw.w_out[t * 8 + 6] * a3.x + sw.w_out[t * 8 + 7] * a3.y;
       }
       const size_t qg = (size_t)gj * n + gi;
-      const double ev = (double)acc * inv_alpha;
+      const double ev = (double)(acc * inv_alpha);
       u_out[qg] = (u_in ? u_in[qg] : 0.0) + ev;
     }
   }
@@ -400,13 +446,13 @@ Status launch_down(int l, const FusedLevels& fl, const float* r32, const double*
   const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
   __nv_bfloat16* xc = has_r ? fl.xb[l + 1] : nullptr;
   if (first && has_r)
-    down_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(r32, norm2, w.w_in, nullptr, fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    down_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(r32, norm2, w.small, nullptr, fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
   else if (first)
-    down_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(r32, norm2, w.w_in, nullptr, fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    down_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(r32, norm2, w.small, nullptr, fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
   else if (has_r)
-    down_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(r32, norm2, w.w_in, fl.xb[l], fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    down_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(r32, norm2, w.small, fl.xb[l], fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
   else
-    down_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(r32, norm2, w.w_in, fl.xb[l], fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    down_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(r32, norm2, w.small, fl.xb[l], fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
   MG_LAUNCH("down_kernel");
   return {};
 }
@@ -419,13 +465,13 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
   const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
   const __nv_bfloat16* xcf = has_p ? fl.xb[l + 1] : nullptr;
   if (last && has_p)
-    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.w_P, fl.s[l], w.f_up, w.w_out, norm2, u_skip, nullptr, e, nl, active);
+    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.small, fl.s[l], w.f_up, norm2, u_skip, nullptr, e, nl, active);
   else if (last)
-    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.w_P, fl.s[l], w.f_up, w.w_out, norm2, u_skip, nullptr, e, nl, active);
+    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.small, fl.s[l], w.f_up, norm2, u_skip, nullptr, e, nl, active);
   else if (has_p)
-    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.w_P, fl.s[l], w.f_up, w.w_out, norm2, u_skip, fl.xb[l], e, nl, active);
+    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.small, fl.s[l], w.f_up, norm2, u_skip, fl.xb[l], e, nl, active);
   else
-    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.w_P, fl.s[l], w.f_up, w.w_out, norm2, u_skip, fl.xb[l], e, nl, active);
+    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.small, fl.s[l], w.f_up, norm2, u_skip, fl.xb[l], e, nl, active);
   MG_LAUNCH("up_kernel");
   return {};
 }
@@ -515,8 +561,7 @@ bool fused_supported(const mgcnn_ctx* c) {
 
 // e = B r (u_skip == nullptr) or e = u_skip + B r for the context's single problem.
 Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
-                        const uint32_t* f_down, const uint32_t* f_up, const uint32_t* f_R, const float* w_in,
-                        const float* w_out, const float* w_P) {
+                        const FusedWeights& w) {
   FusedLevels fl;
   fl.L = c->L;
   fl.batch = 1;
@@ -526,7 +571,6 @@ Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, dou
     fl.xa[l] = c->x16a[l].as<bf16>();
     fl.xb[l] = c->x16b[l].as<bf16>();
   }
-  FusedWeights w{f_down, f_up, f_R, w_in, w_out, w_P};
   if (!c->tuned) {
     // first V-cycle after a setup: time the tile variants per level (output to
     // the context's scratch vector, so no caller data changes), keep the fastest

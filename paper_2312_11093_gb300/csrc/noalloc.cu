@@ -58,7 +58,7 @@ extern "C" int mgcnn_residual_noalloc(const double* op, const double* f, const d
     // every block overwrites its partial sum and the reduction overwrites the
     // last slot, so nothing left by an earlier call needs clearing
     MG_TRY(launch_residual(f, u, op, r, nullptr, scratch, n, st));
-    MG_TRY(launch_reduce(scratch, reduction_blocks(N), scratch + kNoAllocMaxBlocks, st));
+    MG_TRY(launch_reduce(scratch, residual_blocks(N), scratch + kNoAllocMaxBlocks, st));
     if (norm2) MG_CUDA(cudaMemcpyAsync(norm2, scratch + kNoAllocMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, st));
     MG_CUDA(cudaStreamSynchronize(st));
     return {};

@@ -5,6 +5,8 @@
 // zero Dirichlet boundary (zero padding).  Coarse operators are
 // rediscretisations (Sec. 2.3) with the coefficient carried down by full
 // weighting of log k (divergence form) or by sampling mu (non-divergence form).
+#include <cmath>
+
 #include "ops.cuh"
 
 namespace mgcnn {
@@ -13,13 +15,56 @@ namespace mgcnn {
 // Coarse coefficient: log k_c(J, I) = weighted mean of log k over the fine
 // nodes (2J + a - 1, 2I + b - 1), weights (1,2,1)x(1,2,1), renormalised over
 // the nodes that exist.  m = fine nodes per side incl. the ring.
-__global__ void restrict_k_kernel(const double* __restrict__ k, double* __restrict__ kc, int m) {
+//
+// FP64 log and exp cost dozens of FP64-pipe instructions each, and FP64 runs
+// at 1/58 of the FP32 rate here, so interior coarse nodes (all nine fine nodes
+// present, weights summing to 16) use the equivalent weighted geometric mean
+//   k_c = (prod k^w)^(1/16),
+// formed from the binary mantissas m in [1, 2) and exponents e of the nine k
+// (k = m 2^e): P = prod m^w lies in [1, 2^16), E = sum w e, and
+//   k_c = P^(1/16) * 2^(r/16) * 2^q  with E = 16 q + r, 0 <= r < 16,
+// P^(1/16) by four square roots, 2^(r/16) from a table made on the host.
+// Ring nodes (renormalised weights) and subnormal k take the log / exp form.
+struct Pow2Sixteenths {
+  double t[16];   // t[r] = 2^(r/16)
+};
+
+__device__ __forceinline__ double split_pow2(double x, int& e) {
+  const long long b = __double_as_longlong(x);
+  e = (int)((b >> 52) & 0x7ff) - 1023;
+  return __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+}
+
+__global__ void restrict_k_kernel(const double* __restrict__ k, double* __restrict__ kc, int m,
+                                  const Pow2Sixteenths p2) {
   const int mc = (m + 1) / 2;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= mc * mc) return;
   k += (size_t)blockIdx.y * m * m;      // problem blockIdx.y of a batch stored back to back
   kc += (size_t)blockIdx.y * mc * mc;
   const int J = p / mc, I = p - J * mc;
+  if (J >= 1 && I >= 1 && 2 * J + 1 < m && 2 * I + 1 < m) {
+    const double* k0 = k + (size_t)(2 * J - 1) * m + (2 * I - 1);
+    int e[9];
+    double v[9];
+    bool normal = true;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      v[t] = split_pow2(k0[(size_t)(t / 3) * m + t % 3], e[t]);
+      normal = normal && e[t] > -1023;
+    }
+    if (normal) {
+      const double corners = (v[0] * v[2]) * (v[6] * v[8]);
+      const double edges = (v[1] * v[3]) * (v[5] * v[7]);
+      const double c2 = v[4] * v[4];
+      const double P = corners * (edges * edges) * (c2 * c2);
+      const int E = (e[0] + e[2] + e[6] + e[8]) + 2 * (e[1] + e[3] + e[5] + e[7]) + 4 * e[4];
+      const double root = sqrt(sqrt(sqrt(sqrt(P))));
+      const int q = E >> 4, r = E & 15;
+      kc[p] = (root * p2.t[r]) * __longlong_as_double((long long)(q + 1023) << 52);
+      return;
+    }
+  }
   const double w[3] = {1.0, 2.0, 1.0};
   double num = 0.0, den = 0.0;
   for (int a = 0; a < 3; ++a) {
@@ -35,8 +80,13 @@ __global__ void restrict_k_kernel(const double* __restrict__ k, double* __restri
 }
 
 Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch) {
+  static const Pow2Sixteenths p2 = [] {
+    Pow2Sixteenths t{};
+    for (int r = 0; r < 16; ++r) t.t[r] = std::exp2(r / 16.0);
+    return t;
+  }();
   const int mc = (m + 1) / 2;
-  restrict_k_kernel<<<dim3(grid_for((size_t)mc * mc, 256), batch), 256, 0, st>>>(k, kc, m);
+  restrict_k_kernel<<<dim3(grid_for((size_t)mc * mc, 256), batch), 256, 0, st>>>(k, kc, m, p2);
   MG_LAUNCH("restrict_k_kernel");
   return {};
 }
@@ -62,8 +112,17 @@ Status launch_inject_mu(const double* mu, double* mc, int n, cudaStream_t st) {
 //   a_S = -k_s/h^2 - max(by,0)/h   a_N = -k_n/h^2 + min(by,0)/h
 //   a_C = (k_w + k_e + k_s + k_n)/h^2 + (|bx| + |by|)/h
 // Output layout: op[0..N) = a_C, then a_W, a_E, a_S, a_N.
+// The constant terms come from the host (StencilConsts); the four harmonic
+// means 2 k_c k_o / (k_c + k_o) share one FP64 reciprocal of the product of
+// the four sums (an FP64 divide is a long FP64-pipe sequence), with the plain
+// divisions as the fallback when that product leaves the normal range.
+struct StencilConsts {
+  double ih2;          // 1 / h^2
+  double cW, cE, cS, cN, cC;   // max(bx,0)/h, min(bx,0)/h, max(by,0)/h, min(by,0)/h, (|bx|+|by|)/h
+};
+
 __global__ void stencil_div_kernel(const double* __restrict__ k, double* __restrict__ op, int n,
-                                   double bx, double by) {
+                                   const StencilConsts sc) {
   const size_t N = (size_t)n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (int)N) return;
@@ -71,26 +130,41 @@ __global__ void stencil_div_kernel(const double* __restrict__ k, double* __restr
   const int m = n + 2;
   k += (size_t)blockIdx.y * m * m;
   op += (size_t)blockIdx.y * 5 * N;
-  const double h = 1.0 / (n + 1);
-  const double ih2 = 1.0 / (h * h);
   const double kc = k[(size_t)(j + 1) * m + (i + 1)];
   const double kwn = k[(size_t)(j + 1) * m + i];
   const double ken = k[(size_t)(j + 1) * m + (i + 2)];
   const double ksn = k[(size_t)j * m + (i + 1)];
   const double knn = k[(size_t)(j + 2) * m + (i + 1)];
-  const double kw = 2.0 * kc * kwn / (kc + kwn);
-  const double ke = 2.0 * kc * ken / (kc + ken);
-  const double ks = 2.0 * kc * ksn / (kc + ksn);
-  const double kn = 2.0 * kc * knn / (kc + knn);
-  op[1 * N + p] = -kw * ih2 - fmax(bx, 0.0) / h;
-  op[2 * N + p] = -ke * ih2 + fmin(bx, 0.0) / h;
-  op[3 * N + p] = -ks * ih2 - fmax(by, 0.0) / h;
-  op[4 * N + p] = -kn * ih2 + fmin(by, 0.0) / h;
-  op[p] = (kw + ke + ks + kn) * ih2 + (fabs(bx) + fabs(by)) / h;
+  const double sW = kc + kwn, sE = kc + ken, sS = kc + ksn, sN = kc + knn;
+  const double pWE = sW * sE, pSN = sS * sN;
+  const double D = pWE * pSN;
+  const double t2 = 2.0 * kc;
+  double kw, ke, ks, kn;
+  if (D >= 1e-300 && D <= 1e300) {
+    const double R = 1.0 / D;
+    const double rWE = R * pSN, rSN = R * pWE;   // 1 / (sW sE), 1 / (sS sN)
+    kw = t2 * kwn * (sE * rWE);
+    ke = t2 * ken * (sW * rWE);
+    ks = t2 * ksn * (sN * rSN);
+    kn = t2 * knn * (sS * rSN);
+  } else {
+    kw = t2 * kwn / sW;
+    ke = t2 * ken / sE;
+    ks = t2 * ksn / sS;
+    kn = t2 * knn / sN;
+  }
+  op[1 * N + p] = -kw * sc.ih2 - sc.cW;
+  op[2 * N + p] = -ke * sc.ih2 + sc.cE;
+  op[3 * N + p] = -ks * sc.ih2 - sc.cS;
+  op[4 * N + p] = -kn * sc.ih2 + sc.cN;
+  op[p] = (kw + ke + ks + kn) * sc.ih2 + sc.cC;
 }
 
 Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st, int batch) {
-  stencil_div_kernel<<<dim3(grid_for((size_t)n * n, 256), batch), 256, 0, st>>>(k, op, n, bx, by);
+  const double h = 1.0 / (n + 1);
+  const StencilConsts sc{1.0 / (h * h), std::fmax(bx, 0.0) / h, std::fmin(bx, 0.0) / h, std::fmax(by, 0.0) / h,
+                         std::fmin(by, 0.0) / h, (std::fabs(bx) + std::fabs(by)) / h};
+  stencil_div_kernel<<<dim3(grid_for((size_t)n * n, 256), batch), 256, 0, st>>>(k, op, n, sc);
   MG_LAUNCH("stencil_div_kernel");
   return {};
 }
@@ -144,13 +218,26 @@ __global__ void features_kernel(const double* __restrict__ op, FT* __restrict__ 
   if (p >= (int)N) return;
   op += (size_t)blockIdx.y * 5 * N;
   feat += (size_t)blockIdx.y * N * kFeatures;
-  const double h = 1.0 / (n + 1);
-  const double aC = op[p];
-  feat[(size_t)p * kFeatures + 0] = (FT)(op[1 * N + p] / aC);
-  feat[(size_t)p * kFeatures + 1] = (FT)(op[2 * N + p] / aC);
-  feat[(size_t)p * kFeatures + 2] = (FT)(op[3 * N + p] / aC);
-  feat[(size_t)p * kFeatures + 3] = (FT)(op[4 * N + p] / aC);
-  feat[(size_t)p * kFeatures + 4] = (FT)log10(h * h * aC);
+  if constexpr (sizeof(FT) == sizeof(float)) {
+    // FP32 features feed the BF16 network: FP32 arithmetic (FP64 divides and
+    // log10 would cost dozens of slow FP64-pipe instructions per node)
+    const float np1 = (float)(n + 1);
+    const float aC = (float)op[p];
+    const float inv = 1.0f / aC;
+    feat[(size_t)p * kFeatures + 0] = (float)op[1 * N + p] * inv;
+    feat[(size_t)p * kFeatures + 1] = (float)op[2 * N + p] * inv;
+    feat[(size_t)p * kFeatures + 2] = (float)op[3 * N + p] * inv;
+    feat[(size_t)p * kFeatures + 3] = (float)op[4 * N + p] * inv;
+    feat[(size_t)p * kFeatures + 4] = log10f(aC / (np1 * np1));
+  } else {
+    const double h = 1.0 / (n + 1);
+    const double aC = op[p];
+    feat[(size_t)p * kFeatures + 0] = (FT)(op[1 * N + p] / aC);
+    feat[(size_t)p * kFeatures + 1] = (FT)(op[2 * N + p] / aC);
+    feat[(size_t)p * kFeatures + 2] = (FT)(op[3 * N + p] / aC);
+    feat[(size_t)p * kFeatures + 3] = (FT)(op[4 * N + p] / aC);
+    feat[(size_t)p * kFeatures + 4] = (FT)log10(h * h * aC);
+  }
 }
 
 template <typename FT>
@@ -178,13 +265,16 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
 }
 
 // r = f - A u, FP64 (Eq. 1); per-block partial of sum r^2.
+// FP64 runs at 1/58 of the FP32 rate here, so the kernel keeps FP64 work to the
+// minimum: five FMAs for f - A u, one for r^2, and the block reduction once per
+// kResidualPix pixels per thread (thread t of block b takes pixels
+// b * kResidualPix * blockDim + k * blockDim + t, k = 0.., summed in that order).
 __global__ void __launch_bounds__(kResidualBlock)
 residual_kernel(const double* __restrict__ f, const double* __restrict__ u, const double* __restrict__ op,
                 double* __restrict__ r, float* __restrict__ r32, double* __restrict__ partial, int n,
                 const float* __restrict__ dinv32) {
   __shared__ double smem[32];
   const size_t N = (size_t)n * n;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
   {
     const size_t b = blockIdx.y;   // problem of a batch stored back to back
     f += b * N;
@@ -196,18 +286,25 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
     partial += b * gridDim.x;
   }
   double rr = 0.0;
-  if (p < (int)N) {
-    const int j = p / n, i = p - j * n;
-    const double uC = u[p];
-    const double uW = (i > 0) ? u[p - 1] : 0.0;
-    const double uE = (i < n - 1) ? u[p + 1] : 0.0;
-    const double uS = (j > 0) ? u[p - n] : 0.0;
-    const double uN = (j < n - 1) ? u[p + n] : 0.0;
-    const double Au = op[p] * uC + op[N + p] * uW + op[2 * N + p] * uE + op[3 * N + p] * uS + op[4 * N + p] * uN;
-    const double rv = f[p] - Au;
-    if (r) r[p] = rv;
-    if (r32) r32[p] = dinv32 ? (float)rv * dinv32[p] : (float)rv;
-    rr = rv * rv;
+  const int base = blockIdx.x * (kResidualPix * kResidualBlock) + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < kResidualPix; ++k) {
+    const int p = base + k * kResidualBlock;
+    if (p < (int)N) {
+      const int j = p / n, i = p - j * n;
+      const double uW = (i > 0) ? u[p - 1] : 0.0;
+      const double uE = (i < n - 1) ? u[p + 1] : 0.0;
+      const double uS = (j > 0) ? u[p - n] : 0.0;
+      const double uN = (j < n - 1) ? u[p + n] : 0.0;
+      double rv = fma(-op[p], u[p], f[p]);
+      rv = fma(-op[N + p], uW, rv);
+      rv = fma(-op[2 * N + p], uE, rv);
+      rv = fma(-op[3 * N + p], uS, rv);
+      rv = fma(-op[4 * N + p], uN, rv);
+      if (r) r[p] = rv;
+      if (r32) r32[p] = dinv32 ? (float)rv * dinv32[p] : (float)rv;
+      rr = fma(rv, rv, rr);
+    }
   }
   rr = block_sum(rr, smem);
   if (threadIdx.x == 0) partial[blockIdx.x] = rr;
@@ -216,7 +313,7 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
 Status launch_residual(const double* f, const double* u, const double* op, double* r, float* r32,
                        double* partial, int n, cudaStream_t st, const float* dinv32, int batch) {
   const size_t N = (size_t)n * n;
-  residual_kernel<<<dim3(reduction_blocks(N), batch), kResidualBlock, 0, st>>>(f, u, op, r, r32, partial, n, dinv32);
+  residual_kernel<<<dim3(residual_blocks(N), batch), kResidualBlock, 0, st>>>(f, u, op, r, r32, partial, n, dinv32);
   MG_LAUNCH("residual_kernel");
   return {};
 }
@@ -319,18 +416,16 @@ __global__ void gmg_v10_setup_kernel(const double* __restrict__ op, double* __re
   const int j = p / n, i = p - j * n;
   const int dy[4] = {0, 0, -1, 1}, dx[4] = {-1, 1, 0, 0};  // W, E, S, N
   const double aCq = op[p];
+  const double inv = input_diag_level ? 1.0 : 1.0 / aCq;   // one FP64 divide per node
   double* o = out + (size_t)p * kGmgV10Channels;
   for (int k = 0; k < 4; ++k) {
     const int pj = j - dy[k], pi = i - dx[k];
     double v = 0.0;
-    if (pj >= 0 && pj < n && pi >= 0 && pi < n) {
-      const double a = op[(k + 1) * N + (size_t)pj * n + pi];
-      v = input_diag_level ? -omega * a : -omega * a / aCq;
-    }
+    if (pj >= 0 && pj < n && pi >= 0 && pi < n) v = -omega * op[(k + 1) * N + (size_t)pj * n + pi] * inv;
     o[k] = v;
   }
   o[4] = input_diag_level ? (1.0 - omega) * aCq : 1.0 - omega;
-  o[5] = input_diag_level ? omega : omega / aCq;
+  o[5] = omega * inv;
   o[6] = 0.0;
   o[7] = 0.0;
 }

@@ -12,6 +12,9 @@ constexpr int kReduceBlock = 1024;
 // Blocks used by launch_residual / launch_sumsq for N values; the caller
 // sizes the partial-sum buffer with it.
 inline int reduction_blocks(size_t N) { return grid_for(N, kResidualBlock); }
+// The residual kernel's blocks (and partial sums): kResidualPix pixels per thread.
+constexpr int kResidualPix = 4;
+inline int residual_blocks(size_t N) { return grid_for(N, (size_t)kResidualBlock * kResidualPix); }
 
 // batch > 1: problems of the same size stored back to back (blockIdx.y selects one).
 Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch = 1);

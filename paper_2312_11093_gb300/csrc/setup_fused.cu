@@ -77,12 +77,14 @@ struct SetupSmem {
 };
 
 // frags: 5 packed B-fragment blocks (4 setup layers, setup RCNN), 9 x 32 words each.
-// fp: FP32 small weights: b_i [4][8], W_cin [8][5][9], b_cin [8].
+// sw: FP32 small weights by value (b_i [4][8], W_cin [8][5][9], b_cin [8]).
 template <bool FIRST, bool HAS_R>
 __global__ void __launch_bounds__(NT) setup_level_kernel(const double* __restrict__ op, const bf16* __restrict__ cin,
                                                          const uint32_t* __restrict__ frags,
-                                                         const float* __restrict__ fp, int mode, float lscale,
-                                                         bf16* __restrict__ sout, bf16* __restrict__ cout, int n) {
+                                                         const __grid_constant__ SetupSmallWeights sw, int mode,
+                                                         float lscale, bf16* __restrict__ sout,
+                                                         bf16* __restrict__ cout, int n) {
+  const float* fp = sw.v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SetupSmem& sm = *reinterpret_cast<SetupSmem*>(smem_raw);
   const int j0 = blockIdx.y * SH, i0 = blockIdx.x * SW;
@@ -94,8 +96,36 @@ __global__ void __launch_bounds__(NT) setup_level_kernel(const double* __restric
   sout += bz * N * 8;
   if (HAS_R) cout += bz * (size_t)((n - 1) / 2) * ((n - 1) / 2) * 8;
 
+  // finest level: the five features once per pixel of the 26 x 42 region under
+  // the staged tile, in FP32 (they feed a BF16 network), into the second z
+  // buffer, which the first layer overwrites only later; zero outside the grid,
+  // where W_cin's zero padding leaves them out of the sum
+  constexpr int FH = CH0 + 2, FW = CW0 + 2;
+  static_assert(FH * FW * kFeatures <= CH0 * CW0 * 8, "feature staging");
+  float* fts = &sm.zf[1][0][0];
+  if constexpr (FIRST) {
+    const float np1 = (float)(n + 1);
+    const float h2 = 1.0f / (np1 * np1);
+    for (int e = threadIdx.x; e < FH * FW; e += NT) {
+      const int r = e / FW, c = e - r * FW;
+      const int gj = j0 + r - HALO - 1, gi = i0 + c - HALO - 1;
+      float ft[kFeatures] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
+        const size_t q = (size_t)gj * n + gi;
+        const float aC = (float)op[q];
+        const float inv = 1.0f / aC;
+        ft[0] = (float)op[N + q] * inv;
+        ft[1] = (float)op[2 * N + q] * inv;
+        ft[2] = (float)op[3 * N + q] * inv;
+        ft[3] = (float)op[4 * N + q] * inv;
+        ft[4] = log10f(h2 * aC);
+      }
+#pragma unroll
+      for (int fi = 0; fi < kFeatures; ++fi) fts[e * kFeatures + fi] = ft[fi];
+    }
+    __syncthreads();
+  }
   // stage coef_l on the 24 x 40 tile (zero outside the grid: zero padding)
-  const double h = 1.0 / (n + 1);
   for (int e = threadIdx.x; e < CH0 * CW0; e += NT) {
     const int r = e / CW0, c = e - r * CW0;
     const int gj = j0 + r - HALO, gi = i0 + c - HALO;
@@ -107,17 +137,9 @@ __global__ void __launch_bounds__(NT) setup_level_kernel(const double* __restric
         const float* bcin = fp + 32 + 8 * 5 * 9;
 #pragma unroll
         for (int co = 0; co < 8; ++co) v[co] = bcin[co];
+#pragma unroll
         for (int t = 0; t < 9; ++t) {
-          const int qj = gj + t / 3 - 1, qi = gi + t % 3 - 1;
-          if (qj < 0 || qj >= n || qi < 0 || qi >= n) continue;
-          const size_t q = (size_t)qj * n + qi;
-          const double aC = op[q];
-          float ft[5];
-          ft[0] = (float)(op[N + q] / aC);
-          ft[1] = (float)(op[2 * N + q] / aC);
-          ft[2] = (float)(op[3 * N + q] / aC);
-          ft[3] = (float)(op[4 * N + q] / aC);
-          ft[4] = (float)log10(h * h * aC);
+          const float* ft = fts + ((r + t / 3) * FW + c + t % 3) * kFeatures;
 #pragma unroll
           for (int co = 0; co < 8; ++co)
 #pragma unroll
@@ -211,7 +233,7 @@ __global__ void __launch_bounds__(NT) setup_level_kernel(const double* __restric
     if (gj >= n || gi >= n) continue;
     const int t = (r + HALO) * CW0 + c + HALO;
     float sc = lscale;
-    if (mode == 1) sc = (float)(1.0 / op[(size_t)gj * n + gi]);
+    if (mode == 1) sc = 1.0f / (float)op[(size_t)gj * n + gi];
     const float* z = sm.zf[0][t];
     reinterpret_cast<uint4*>(sout)[(size_t)gj * n + gi] =
         make_uint4(f2bf(z[0] * sc, z[1] * sc), f2bf(z[2] * sc, z[3] * sc), f2bf(z[4] * sc, z[5] * sc),
@@ -227,8 +249,8 @@ size_t setup_fused_smem() { return sizeof(SetupSmem); }
 // s[l] setup tensors out ([B][N_l][8] BF16), coef[l] (l >= 1) BF16 coefficient
 // storage ([B][N_l][8]).  mode / level scale as mgcnn_config.scale_by_diag.
 Status setup_fused_levels(int L, const int* n, int batch, const double* const* op, __nv_bfloat16* const* s,
-                          __nv_bfloat16* const* coef, const uint32_t* frags, const float* fp, int mode,
-                          cudaStream_t st) {
+                          __nv_bfloat16* const* coef, const SetupWeights& w, int mode, cudaStream_t st) {
+  const uint32_t* frags = w.frags;
   static bool attr_set = false;
   const size_t smem = sizeof(SetupSmem);
   if (!attr_set) {
@@ -245,13 +267,13 @@ Status setup_fused_levels(int L, const int* n, int batch, const double* const* o
     const bf16* cin = first ? nullptr : coef[l];
     bf16* cout = has_r ? coef[l + 1] : nullptr;
     if (first && has_r)
-      setup_level_kernel<true, true><<<grid, NT, smem, st>>>(op[l], cin, frags, fp, mode, lscale, s[l], cout, n[l]);
+      setup_level_kernel<true, true><<<grid, NT, smem, st>>>(op[l], cin, frags, w.small, mode, lscale, s[l], cout, n[l]);
     else if (first)
-      setup_level_kernel<true, false><<<grid, NT, smem, st>>>(op[l], cin, frags, fp, mode, lscale, s[l], cout, n[l]);
+      setup_level_kernel<true, false><<<grid, NT, smem, st>>>(op[l], cin, frags, w.small, mode, lscale, s[l], cout, n[l]);
     else if (has_r)
-      setup_level_kernel<false, true><<<grid, NT, smem, st>>>(op[l], cin, frags, fp, mode, lscale, s[l], cout, n[l]);
+      setup_level_kernel<false, true><<<grid, NT, smem, st>>>(op[l], cin, frags, w.small, mode, lscale, s[l], cout, n[l]);
     else
-      setup_level_kernel<false, false><<<grid, NT, smem, st>>>(op[l], cin, frags, fp, mode, lscale, s[l], cout, n[l]);
+      setup_level_kernel<false, false><<<grid, NT, smem, st>>>(op[l], cin, frags, w.small, mode, lscale, s[l], cout, n[l]);
     MG_LAUNCH("setup_level_kernel");
   }
   return {};

@@ -73,7 +73,7 @@ Status build_graph(mgcnn_ctx* c) {
       MG_TRY(launch_residual(c->f.as<double>(), c->u.as<double>(), c->op[0].as<double>(), nullptr,
                              c->r32.as<float>(), c->partial.as<double>(), c->n, st,
                              c->cfg.input_diag ? c->dinv32.as<float>() : nullptr));
-      MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N0), sc, st));
+      MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N0), sc, st));
       solve_check_kernel<<<1, 32, 0, st>>>(sc, sc + 1, c->gstate.as<int>(), c->ghist.as<double>(),
                                            c->gparams.as<double>(), loop);
       MG_LAUNCH("solve_check_kernel");

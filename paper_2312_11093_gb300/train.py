@@ -105,8 +105,9 @@ def make_batch(step: int, sizes=(63, 127), per_size=32, corr_len: float = 0.1):
 # from exploding losses.  Every batch therefore mixes the sizes of the paper's
 # progressive schedule (Appendix A, Table training_settings: 31^2 ... 511^2, the
 # batch halving as the size doubles): 16 x 63^2 + 8 x 127^2 + 4 x 255^2 + 2 x 511^2,
-# K = 8, Adam at lr 1e-3, then 3e-4 (the paper decays its rate stepwise).
-SCHEDULE = [((63, 127, 255, 511), (16, 8, 4, 2), 1500, 1e-3), ((63, 127, 255, 511), (16, 8, 4, 2), 500, 3e-4)]
+# K = 8, Adam at lr 1e-4, then 3e-5 (the paper decays its rate stepwise; at 1e-3
+# the K-cycle loss of this mix blows up within the first hundred steps).
+SCHEDULE = [((63, 127, 255, 511), (16, 8, 4, 2), 1500, 1e-4), ((63, 127, 255, 511), (16, 8, 4, 2), 500, 3e-5)]
 # The recipe on 63^2 / 127^2 only (batch 64, 2000 steps, lr 1e-3).
 RECIPE_63_127 = [((63, 127), (32, 32), 2000, 1e-3)]
 
@@ -114,7 +115,7 @@ RECIPE_63_127 = [((63, 127), (32, 32), 2000, 1e-3)]
 def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int = 8, seed: int = 0,
           log_every: int = 50, out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size=None,
           setup_scale: int = 0, mg_transfers: bool = True, schedule=None, snapshot_every: int = 25,
-          spike: float = 5.0, max_restarts: int = 8):
+          spike: float = 50.0, max_restarts: int = 8):
     """Run the schedule (or a single phase when steps/lr/per_size are given) and
     return (weights, loss history).
 
