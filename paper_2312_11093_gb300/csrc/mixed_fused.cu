@@ -75,21 +75,37 @@ __device__ __forceinline__ uint4 mul8(uint4 a, uint4 b) {
   return o;
 }
 
-// 16 pixels x 8 channels of a 3x3 conv; pix(m, tap) = shared pixel index of
-// A row m for tap (each pixel is one uint4 of 8 BF16 channels).
-template <typename Pix>
-__device__ __forceinline__ void strip_conv(const uint4* tile, const uint32_t* wf, Pix pix, float* acc) {
-  const int lane = threadIdx.x & 31;
-  const int m = (lane & 7) + ((lane >> 3) & 1) * 8;
-  const int kh = lane >> 4;
+// Per-lane tap offsets of a shared-memory tile with row pitch PITCH (in
+// pixels): this lane's four taps 2s + kh (kh = lane / 16) of the x4 loads and
+// the ninth tap, relative to the tap-(0,0) pixel of the lane's A row.
+template <int PITCH>
+struct TapOffsets {
+  int off[4];
+  __device__ __forceinline__ TapOffsets() {
+    const int kh = (threadIdx.x & 31) >> 4;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int t = 2 * s + kh;
+      off[s] = (t / 3) * PITCH + t % 3;
+    }
+  }
+  static constexpr int off8 = 2 * PITCH + 2;
+};
+
+// strip_conv with precomputed addressing: base_m is the tap-(0,0) pixel of
+// A row m = (lane & 7) + 8 ((lane >> 3) & 1) (the x4 loads), base_l the one of
+// row lane & 15 (the ninth tap's x2 load).
+template <int PITCH>
+__device__ __forceinline__ void strip_conv_at(const uint4* tile, const uint32_t* wf, int base_m, int base_l,
+                                              const TapOffsets<PITCH>& to, float* acc) {
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     uint32_t a[4];
-    ldsm_x4(a, tile + pix(m, 2 * s + kh));
+    ldsm_x4(a, tile + base_m + to.off[s]);
     mma16816(acc, a, wf[2 * s], wf[2 * s + 1]);
   }
   uint32_t a[2];
-  ldsm_x2(a, tile + pix(lane & 15, 8));
+  ldsm_x2(a, tile + base_l + TapOffsets<PITCH>::off8);
   mma1688(acc, a[0], a[1], wf[8]);
 }
 
@@ -149,6 +165,7 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
     if (threadIdx.x == 0) s_alpha = (float)alpha_of(norm2, N);
     __syncthreads();
     const float alpha = s_alpha;
+    #pragma unroll 4
     for (int e = threadIdx.x; e < RH * RW; e += NT) {
       const int rr = e / RW, cc = e - rr * RW;
       const int gj = j0 + rr - 2, gi = i0 + cc - 2;
@@ -179,6 +196,7 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
       zs[e] = zv;
     }
   } else {
+    #pragma unroll 4
     for (int e = threadIdx.x; e < ZH * ZW; e += NT) {
       const int zr = e / ZW, zc = e - zr * ZW;
       const int gj = j0 + zr - 1, gi = i0 + zc - 1;
@@ -194,29 +212,29 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   }
   __syncthreads();
 
-  // layer: X = x_in + K (s * x_in), strips of 16 pixels over X in row-major order
+  // layer: X = x_in + K (s * x_in).  Strips are 16 consecutive pixels of one X
+  // row (SPR strips per row, the last one clamped and partly idle), so every
+  // lane's A-row address is a row base plus a column and fixed tap offsets.
   const int g = lane >> 2, q = lane & 3;
-  constexpr int NSTRIP = (XH * XW + 15) / 16;
-  for (int st = warp; st < NSTRIP; st += NW) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    strip_conv(zs, wk, [&](int m, int tap) {
-      int p = st * 16 + m;
-      p = p < XH * XW ? p : XH * XW - 1;
-      const int xr = p / XW, xc_ = p - xr * XW;
-      return (xr + tap / 3) * ZW + xc_ + tap % 3;
-    }, acc);
+  const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
+  {
+    constexpr int SPR = (XW + 15) / 16;
+    const TapOffsets<ZW> to;
+    for (int st = warp; st < XH * SPR; st += NW) {
+      const int xr = st / SPR, c0 = (st - xr * SPR) * 16;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      strip_conv_at<ZW>(zs, wk, xr * ZW + min(c0 + mrow, XW - 1), xr * ZW + min(c0 + lrow, XW - 1), to, acc);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int p = st * 16 + g + 8 * h;
-      if (p >= XH * XW) continue;
-      const int xr = p / XW, xcol = p - xr * XW;
-      const int zi = (xr + 1) * ZW + xcol + 1;
-      const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&xs[zi])[q]);
-      const uint32_t o = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
-      reinterpret_cast<uint32_t*>(&xd[p])[q] = o;
-      const int gj = j0 + xr, gi = i0 + xcol;
-      if (xr < FH && xcol < FW && gj < n && gi < n)
-        reinterpret_cast<uint32_t*>(xdown + ((size_t)gj * n + gi) * 8)[q] = o;
+      for (int h = 0; h < 2; ++h) {
+        const int xcol = c0 + g + 8 * h;
+        if (xcol >= XW) continue;
+        const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&xs[(xr + 1) * ZW + xcol + 1])[q]);
+        const uint32_t o = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
+        reinterpret_cast<uint32_t*>(&xd[xr * XW + xcol])[q] = o;
+        const int gj = j0 + xr, gi = i0 + xcol;
+        if (xr < FH && xcol < FW && gj < n && gi < n)
+          reinterpret_cast<uint32_t*>(xdown + ((size_t)gj * n + gi) * 8)[q] = o;
+      }
     }
   }
   if constexpr (HAS_R) {
@@ -226,12 +244,11 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
     constexpr int CH = FH / 2, CW = FW / 2;
     const int nc = (n - 1) / 2;
     const int J0 = blockIdx.y * CH, I0 = blockIdx.x * CW;
+    const TapOffsets<XW> tr;
     for (int st = warp; st < CH * CW / 16; st += NW) {
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      strip_conv(xd, wr, [&](int m, int tap) {
-        const int p = st * 16 + m, cr = p / CW, cc = p - cr * CW;
-        return (2 * cr + tap / 3) * XW + 2 * cc + tap % 3;
-      }, acc);
+      const int pm = st * 16 + mrow, pl = st * 16 + lrow;
+      strip_conv_at<XW>(xd, wr, 2 * (pm / CW) * XW + 2 * (pm % CW), 2 * (pl / CW) * XW + 2 * (pl % CW), tr, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int p = st * 16 + g + 8 * h, cr = p / CW, cc = p - cr * CW;
@@ -259,12 +276,12 @@ struct TcnnTile {
 template <int A, int B, int PH, int PW, int CW>
 __device__ __forceinline__ void tcnn_class(const TcnnTile& t, const SmallWeights& sw) {
   const int r0 = (A ^ t.pj0) & 1, c0 = (B ^ t.pi0) & 1;   // first P row / column of the class
-  const int nr = (PH - r0 + 1) >> 1, ncl = (PW - c0 + 1) >> 1;
-  for (int e = threadIdx.x; e < nr * ncl; e += NT) {
-    const int rr = e / ncl, cc = e - rr * ncl;
+  constexpr int NR = (PH + 1) / 2, NC = (PW + 1) / 2;       // class rows / columns, at most
+  for (int e = threadIdx.x; e < NR * NC; e += NT) {
+    const int rr = e / NC, cc = e - rr * NC;
     const int pr = r0 + 2 * rr, pc = c0 + 2 * cc;
     const int gj = t.pj0 + pr, gi = t.pi0 + pc;
-    if (gj < 0 || gj >= t.n || gi < 0 || gi >= t.n) continue;
+    if (pr >= PH || pc >= PW || gj < 0 || gj >= t.n || gi < 0 || gi >= t.n) continue;
     const int pe = pr * PW + pc;
     const uint4 xv = t.ps[pe];
     float acc[8];
@@ -352,6 +369,7 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
 #pragma unroll
   for (int k = 0; k < 9; ++k) wk[k] = fK[k * 32 + lane];
   if constexpr (HAS_P) {
+    #pragma unroll 4
     for (int e = threadIdx.x; e < CH * CW; e += NT) {
       const int cr = e / CW, cc = e - cr * CW;
       const int J = cj0 + cr, I = ci0 + cc;
@@ -365,6 +383,7 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
   // class (gj & 1, gi & 1) of the fine pixel, the TCNN taps that reach it --
   // 4, 2, 2 or 1, known at compile time, so the weights are constant operands
   // -- x_pre = x_down + TCNN(x_c) rounded once, then z = s * x_pre.
+  #pragma unroll 4
   for (int e = threadIdx.x; e < PH * PW; e += NT) {
     const int pr = e / PW, pc = e - pr * PW;
     const int gj = pj0 + pr, gi = pi0 + pc;
@@ -387,30 +406,29 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
   }
   __syncthreads();
 
-  // layer on O
+  // layer on O, row-aligned strips as in the down kernel
   const int g = lane >> 2, q = lane & 3;
-  constexpr int NSTRIP = (OH * OW + 15) / 16;
-  for (int st = warp; st < NSTRIP; st += NW) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    strip_conv(zs, wk, [&](int m, int tap) {
-      int p = st * 16 + m;
-      p = p < OH * OW ? p : OH * OW - 1;
-      const int orow = p / OW, ocol = p - orow * OW;
-      return (orow + tap / 3) * PW + ocol + tap % 3;
-    }, acc);
+  {
+    constexpr int SPR = (OW + 15) / 16;
+    const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
+    const TapOffsets<PW> to;
+    for (int st = warp; st < OH * SPR; st += NW) {
+      const int orow = st / SPR, c0 = (st - orow * SPR) * 16;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      strip_conv_at<PW>(zs, wk, orow * PW + min(c0 + mrow, OW - 1), orow * PW + min(c0 + lrow, OW - 1), to, acc);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int p = st * 16 + g + 8 * h;
-      if (p >= OH * OW) continue;
-      const int orow = p / OW, ocol = p - orow * OW;
-      const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&ps[(orow + 1) * PW + ocol + 1])[q]);
-      const uint32_t o = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
-      const int gj = j0 - H + orow, gi = i0 - H + ocol;
-      if constexpr (LAST) {
-        // zero outside the grid: W_out's zero padding
-        reinterpret_cast<uint32_t*>(&os[p])[q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? o : 0u;
-      } else {
-        if (gj < n && gi < n) reinterpret_cast<uint32_t*>(xfin + ((size_t)gj * n + gi) * 8)[q] = o;
+      for (int h = 0; h < 2; ++h) {
+        const int ocol = c0 + g + 8 * h;
+        if (ocol >= OW) continue;
+        const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&ps[(orow + 1) * PW + ocol + 1])[q]);
+        const uint32_t o = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
+        const int gj = j0 - H + orow, gi = i0 - H + ocol;
+        if constexpr (LAST) {
+          // zero outside the grid: W_out's zero padding
+          reinterpret_cast<uint32_t*>(&os[orow * OW + ocol])[q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? o : 0u;
+        } else {
+          if (gj < n && gi < n) reinterpret_cast<uint32_t*>(xfin + ((size_t)gj * n + gi) * 8)[q] = o;
+        }
       }
     }
   }
