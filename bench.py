@@ -156,13 +156,16 @@ def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
     }[kind]
 
 
+KERNEL_SOURCE = {"residual_kernel": "operator.cu", "down_kernel": "mixed_fused.cu", "up_kernel": "mixed_fused.cu"}
+
+
 def traffic_record(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (source hash recorded beside the number)."""
+    current source of that kernel (source hash recorded beside the number)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCE:
         return None
-    src = open(os.path.join(ROOT, "paper_2312_11093_gb300", "csrc", "mixed.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2312_11093_gb300", "csrc", KERNEL_SOURCE[kernel]), "rb").read()
     h = hashlib.sha1(src).hexdigest()[:12]
     for ln in open(path):
         parts = ln.split()

@@ -112,10 +112,38 @@ SCHEDULE = [((63, 127, 255, 511), (16, 8, 4, 2), 1500, 1e-4), ((63, 127, 255, 51
 RECIPE_63_127 = [((63, 127), (32, 32), 2000, 1e-3)]
 
 
+def slow_modes(weights: np.ndarray, problems, iters: int = 30, C: int = 8, precision: str = "mixed_bf16",
+               seed: int = 0):
+    """For each problem (k, f, n): the dominant mode of the residual iteration
+    r <- (I - A B) r of the current network (power iteration from a random start,
+    normalised every step).  Unrolled-loss training with white-noise right-hand
+    sides weighs each eigenmode of I - A B by about 1/N, so a single slow mode
+    barely shows in the loss yet decides the asymptotic rate of Eq. 1."""
+    rng = np.random.default_rng(seed)
+    sv = mgcnn.Solver(C, 1, 1, precision=precision, b=(1.0, 0.5), input_diag=True)
+    sv.set_weights(weights)
+    modes = []
+    for k, _, n in problems:
+        sv.setup(k, n)
+        r = rng.standard_normal(n * n)
+        r /= np.linalg.norm(r)
+        for _ in range(iters):
+            e = sv.vcycle(r)
+            r, _ = sv.residual(r, e)
+            nr = np.linalg.norm(r)
+            if not np.isfinite(nr) or nr == 0.0:
+                break
+            r /= nr
+        modes.append(np.ascontiguousarray(r))
+    sv.close()
+    return modes
+
+
 def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int = 8, seed: int = 0,
           log_every: int = 50, out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size=None,
           setup_scale: int = 0, mg_transfers: bool = True, schedule=None, snapshot_every: int = 25,
-          spike: float = 50.0, max_restarts: int = 8):
+          spike: float = 50.0, max_restarts: int = 8, init: np.ndarray | None = None, hard_every: int = 0,
+          hard_sizes=(63, 127, 255, 511)):
     """Run the schedule (or a single phase when steps/lr/per_size are given) and
     return (weights, loss history).
 
@@ -124,7 +152,13 @@ def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int 
     there.  Every snapshot_every steps the weights are copied to the host when the
     step's loss is finite and within `spike` x the median of the last 20 losses;
     a loss outside that band restores the last snapshot in a fresh context (fresh
-    Adam moments) and halves the phase's learning rate."""
+    Adam moments) and halves the phase's learning rate.
+
+    hard_every > 0: every hard_every steps draw one fresh training problem per
+    size in hard_sizes and replace its right-hand side by the slowest residual
+    mode of the current network (`slow_modes`); these problems join every batch
+    until the next refresh, so the loss sees the mode that limits Eq. 1.
+    init: start from these weights instead of the random initialisation."""
     if schedule is None:
         schedule = SCHEDULE if steps is None else [((63, 127), per_size or (32, 32), steps, lr or 1e-3)]
 
@@ -133,15 +167,21 @@ def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int 
         sv.set_weights(weights)
         return sv
 
-    sv = fresh(init_weights(C, 1, 1, np.random.default_rng(seed), mg_transfers=mg_transfers))
+    w0 = init if init is not None else init_weights(C, 1, 1, np.random.default_rng(seed), mg_transfers=mg_transfers)
+    sv = fresh(w0)
     snap, snap_step = sv.get_weights(), 0
+    hard = []
     hist = []
     t0 = time.time()
     step, restarts = 0, 0
     for sizes, counts, nsteps, plr in schedule:
         for _ in range(nsteps):
+            if hard_every and step % hard_every == 0:
+                base = make_batch(500000 + step, hard_sizes, 1)
+                modes = slow_modes(sv.get_weights(), base, C=C, precision=precision, seed=step)
+                hard = [(k, v, n) for (k, _, n), v in zip(base, modes)]
             try:
-                loss = sv.train_step(make_batch(step, sizes, counts), K, plr)
+                loss = sv.train_step(make_batch(step, sizes, counts) + hard, K, plr)
             except mgcnn.MGCNNError as err:
                 if err.status != mgcnn.ERR_NONFINITE:
                     raise
