@@ -9,6 +9,7 @@
 #include <cmath>
 
 #include "ops.cuh"
+#include "tma.cuh"
 #include "mixed.cuh"
 #include "train.cuh"
 #include "batch.cuh"
@@ -144,6 +145,16 @@ Status stage_out_finish(mgcnn_ctx* c, double* dst, const double* dev, size_t cou
 
 Status sync(mgcnn_ctx* c) {
   MG_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->kerr.p) {
+    int flag = 0;
+    MG_CUDA(cudaMemcpyAsync(&flag, c->kerr.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+    if (flag) {
+      MG_CUDA(cudaMemsetAsync(c->kerr.p, 0, sizeof(int), c->stream));
+      MG_CUDA(cudaStreamSynchronize(c->stream));
+      return make_status(MGCNN_ERR_TIMEOUT, "a fused kernel gave up waiting for its tile copies (TMA)");
+    }
+  }
   return {};
 }
 
@@ -392,6 +403,12 @@ int mgcnn_create(const mgcnn_config* cfg, mgcnn_ctx** out) {
     return MGCNN_ERR_CUDA;
   }
   Status s = ensure(c->scalars, 8 * sizeof(double));
+  if (s.ok()) s = ensure(c->kerr, sizeof(int));
+  if (s.ok() && cudaMemset(c->kerr.p, 0, sizeof(int)) != cudaSuccess) s = make_status(MGCNN_ERR_CUDA, "cudaMemset");
+  if (s.ok()) {
+    c->tma = new (std::nothrow) TmaMaps();
+    if (!c->tma) s = make_status(MGCNN_ERR_NOMEM, "tensor map cache");
+  }
   if (s.ok() && cudaMallocHost(&c->h_scalars, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     s = make_status(MGCNN_ERR_NOMEM, "cudaMallocHost");
@@ -429,6 +446,8 @@ void mgcnn_destroy(mgcnn_ctx* c) {
     cudaEventDestroy(c->ev_stop[i]);
   }
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  release(c->kerr);
+  delete c->tma;
   delete c;
 }
 

@@ -234,6 +234,8 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff) {
   k.fl = FusedLevels{};
   k.fl.L = k.L;
   k.fl.batch = k.B;
+  k.fl.maps = c->tma;
+  k.fl.err = c->kerr.as<int>();
   for (int l = 0; l < k.L; ++l) {
     k.fl.n[l] = k.nl[l];
     k.fl.s[l] = k.s16[l].as<bf16>();

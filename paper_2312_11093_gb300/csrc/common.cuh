@@ -64,6 +64,8 @@ struct Level {
   size_t N() const { return (size_t)n * n; }
 };
 
+class TmaMaps;   // tma.cuh
+
 // FP32 weights of the fused kernels' small layers (8 channels), passed to the
 // kernels by value: they sit in the kernel-parameter constant bank and the
 // unrolled loops read them as constant operands, with no shared-memory loads.
@@ -117,6 +119,8 @@ struct mgcnn_ctx {
   mgcnn::DevBuf x16a[mgcnn::kMaxLevels];  // BF16 state ping-pong, [n_l^2][cp]
   mgcnn::DevBuf x16b[mgcnn::kMaxLevels];
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
+  mgcnn::TmaMaps* tma = nullptr;          // tensor maps of the fused kernels' TMA tile loads
+  mgcnn::DevBuf kerr;                     // device flag: a kernel gave up waiting for its tile copies
   mgcnn::SmallWeights small_w{};          // host copy of the fused kernels' small layers
   mgcnn::SetupSmallWeights setup_small_w{};  // host copy of the fused setup kernel's small layers
   mgcnn::DevBuf s32tmp;                   // FP32 setup output before the BF16 cast

@@ -21,8 +21,11 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega);
 void mixed_release(mgcnn_ctx* c);
 // mixed_fused.cu: fused level kernels (8 channels, one layer per ResNet)
 constexpr int kFusedVariants = 3;        // tile shapes 16x32, 8x32, 16x16
+class TmaMaps;
 struct FusedLevels {
   int L = 0, batch = 1;
+  TmaMaps* maps = nullptr;               // tensor-map cache of the owner (context or batch class)
+  int* err = nullptr;                    // device flag: a block's tile copies timed out
   int n[kMaxLevels] = {};
   int var_down[kMaxLevels] = {};         // tile variant per level (autotuned)
   int var_up[kMaxLevels] = {};

@@ -25,6 +25,7 @@
 
 #include "mixed.cuh"
 #include "ops.cuh"
+#include "tma.cuh"
 
 namespace mgcnn {
 
@@ -121,34 +122,48 @@ __device__ __forceinline__ double alpha_of(const double* norm2, size_t N) {
 //   Rg (residual, halo 2):   rows -2..XH+1, cols -2..XW+1   (finest level only)
 template <int FH, int FW, bool FIRST, bool HAS_R>
 __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, const double* __restrict__ norm2,
-                                                  const __grid_constant__ SmallWeights sw, const bf16* __restrict__ x0,
-                                                  const bf16* __restrict__ s, const uint32_t* __restrict__ fK,
-                                                  const uint32_t* __restrict__ fR, bf16* __restrict__ xdown,
-                                                  bf16* __restrict__ xc, int n, const int* __restrict__ active) {
+                                                  const __grid_constant__ SmallWeights sw,
+                                                  const __grid_constant__ CUtensorMap map_x,
+                                                  const __grid_constant__ CUtensorMap map_s,
+                                                  const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fR,
+                                                  bf16* __restrict__ xdown, bf16* __restrict__ xc, int n,
+                                                  const int* __restrict__ active, int* __restrict__ err) {
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
   constexpr int ZH = XH + 2, ZW = XW + 2;
   constexpr int RH = ZH + 2, RW = ZW + 2;
-  __shared__ __align__(16) uint4 zs[ZH * ZW];   // s * x_in (BF16)
-  __shared__ __align__(16) uint4 xs[ZH * ZW];   // x_in (BF16), for the skip
+  // zs: s, then z = s * x_in in place (BF16); xs: x_in, for the skip.  Both are
+  // TMA destinations: the box of rows j0-1.. and columns i0-1.. of the tensor,
+  // zero outside the grid.
+  __shared__ __align__(128) uint4 zs[ZH * ZW];
+  __shared__ __align__(128) uint4 xs[ZH * ZW];
   __shared__ __align__(16) uint4 xd[XH * XW];   // layer output
   __shared__ float rs[FIRST ? RH * RW : 1];
+  __shared__ __align__(8) uint64_t bar;
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t N = (size_t)n * n;
   // problem blockIdx.z of a batch of equal-size problems stored back to back
-  const size_t bz = blockIdx.z;
+  const int bz = blockIdx.z;
   if (active && !active[bz]) return;
   {
     const size_t Nc = (size_t)((n - 1) / 2) * ((n - 1) / 2);
     if (FIRST) {
       r += bz * N;
       norm2 += bz;
-    } else {
-      x0 += bz * N * 8;
     }
-    s += bz * N * 8;
     xdown += bz * N * 8;
     if (HAS_R) xc += bz * Nc * 8;
+  }
+  // the input scale alpha = sqrt(N / ||r||^2) of the finest level: FP64 divide
+  // and square root are dozens of FP64-pipe instructions, so one thread
+  // computes it per block
+  __shared__ float s_alpha;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, (FIRST ? 1u : 2u) * ZH * ZW * 16u);
+    tma_load_pix(zs, &map_s, i0 - 1, j0 - 1, bz, &bar);
+    if (!FIRST) tma_load_pix(xs, &map_x, i0 - 1, j0 - 1, bz, &bar);
+    if (FIRST) s_alpha = (float)alpha_of(norm2, N);
   }
 
   uint32_t wk[9], wr[9];
@@ -157,13 +172,9 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
     wk[k] = fK[k * 32 + lane];
     if (HAS_R) wr[k] = fR[k * 32 + lane];
   }
+  __syncthreads();   // barrier initialised, alpha published
 
   if constexpr (FIRST) {
-    // the input scale alpha = sqrt(N / ||r||^2): FP64 divide and square root are
-    // dozens of FP64-pipe instructions, so one thread computes it per block
-    __shared__ float s_alpha;
-    if (threadIdx.x == 0) s_alpha = (float)alpha_of(norm2, N);
-    __syncthreads();
     const float alpha = s_alpha;
     #pragma unroll 4
     for (int e = threadIdx.x; e < RH * RW; e += NT) {
@@ -171,12 +182,20 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
       const int gj = j0 + rr - 2, gi = i0 + cc - 2;
       rs[e] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? alpha * r[(size_t)gj * n + gi] : 0.f;
     }
-    __syncthreads();
-    // x_in = W_in * (alpha r) on Z, rounded to BF16 (zero outside the grid)
+  }
+  // the copies of the block's tiles (a uniform decision: every thread agrees
+  // before any of them returns)
+  const bool landed = mbar_wait_bounded(&bar, 0);
+  if (!__syncthreads_and(landed)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
+  if constexpr (FIRST) {
+    // x_in = W_in * (alpha r) on Z, rounded to BF16 (zero outside the grid); z = s * x_in
     for (int e = threadIdx.x; e < ZH * ZW; e += NT) {
       const int zr = e / ZW, zc = e - zr * ZW;
       const int gj = j0 + zr - 1, gi = i0 + zc - 1;
-      uint4 xv = make_uint4(0, 0, 0, 0), zv = xv;
+      uint4 xv = make_uint4(0, 0, 0, 0);
       if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
         float rv[9];
 #pragma unroll
@@ -190,25 +209,12 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
           o[co] = a;
         }
         xv = make_uint4(f2bf(o[0], o[1]), f2bf(o[2], o[3]), f2bf(o[4], o[5]), f2bf(o[6], o[7]));
-        zv = mul8(xv, reinterpret_cast<const uint4*>(s)[(size_t)gj * n + gi]);
       }
       xs[e] = xv;
-      zs[e] = zv;
+      zs[e] = mul8(xv, zs[e]);
     }
   } else {
-    #pragma unroll 4
-    for (int e = threadIdx.x; e < ZH * ZW; e += NT) {
-      const int zr = e / ZW, zc = e - zr * ZW;
-      const int gj = j0 + zr - 1, gi = i0 + zc - 1;
-      uint4 xv = make_uint4(0, 0, 0, 0), zv = xv;
-      if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
-        const size_t q = (size_t)gj * n + gi;
-        xv = reinterpret_cast<const uint4*>(x0)[q];
-        zv = mul8(xv, reinterpret_cast<const uint4*>(s)[q]);
-      }
-      xs[e] = xv;
-      zs[e] = zv;
-    }
+    for (int e = threadIdx.x; e < ZH * ZW; e += NT) zs[e] = mul8(xs[e], zs[e]);
   }
   __syncthreads();
 
@@ -325,31 +331,33 @@ __device__ __forceinline__ void tcnn_class(const TcnnTile& t, const SmallWeights
 //   P (layer input x_pre = x_down + TCNN(x_c)): O plus halo 1  (PH x PW)
 //   coarse rows/cols J: floor((j0 - H - 1) / 2) - 1 .. , enough for P
 template <int FH, int FW, bool LAST, bool HAS_P>
-__global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, const bf16* __restrict__ xcf,
-                                                const __grid_constant__ SmallWeights sw, const bf16* __restrict__ s,
+__global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensorMap map_xd,
+                                                const __grid_constant__ CUtensorMap map_s,
+                                                const __grid_constant__ CUtensorMap map_c,
+                                                const __grid_constant__ SmallWeights sw,
                                                 const uint32_t* __restrict__ fK,
                                                 const double* __restrict__ norm2, const double* __restrict__ u_in,
                                                 bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
-                                                const int* __restrict__ active) {
+                                                const int* __restrict__ active, int* __restrict__ err) {
   constexpr int H = LAST ? 1 : 0;
   constexpr int OH = FH + 2 * H, OW = FW + 2 * H;
   constexpr int PH = OH + 2, PW = OW + 2;
   constexpr int CH = PH / 2 + 2, CW = PW / 2 + 2;   // coarse rows / cols staged
-  __shared__ __align__(16) uint4 ps[PH * PW];       // x_pre
-  __shared__ __align__(16) uint4 zs[PH * PW];       // s * x_pre
+  // TMA destinations (zero outside the grid): ps = x_down on P, then x_pre;
+  // zs = s on P, then s * x_pre; cs = the coarse pixels under P
+  __shared__ __align__(128) uint4 ps[PH * PW];
+  __shared__ __align__(128) uint4 zs[PH * PW];
+  __shared__ __align__(128) uint4 cs[HAS_P ? CH * CW : 1];
   __shared__ __align__(16) uint4 os[LAST ? OH * OW : 1];
-  __shared__ __align__(16) uint4 cs[HAS_P ? CH * CW : 1];
+  __shared__ __align__(8) uint64_t bar;
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int pj0 = j0 - H - 1, pi0 = i0 - H - 1;      // global coords of P's corner
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nc = (n - 1) / 2;
-  const size_t bz = blockIdx.z;
+  const int bz = blockIdx.z;
   if (active && !active[bz]) return;
   {
-    const size_t N = (size_t)n * n, Nc = (size_t)nc * nc;
-    xdown += bz * N * 8;
-    s += bz * N * 8;
-    if (HAS_P) xcf += bz * Nc * 8;
+    const size_t N = (size_t)n * n;
     if (LAST) {
       norm2 += bz;
       if (u_in) u_in += bz * N;
@@ -358,51 +366,41 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
       xfin += bz * N * 8;
     }
   }
-  // 1 / alpha for the output layer, once per block (see the down kernel)
-  __shared__ float s_inv_alpha;
-  if (LAST && threadIdx.x == 0) s_inv_alpha = (float)(1.0 / alpha_of(norm2, (size_t)n * n));
   // coarse corner: the smallest J with 2J + 2 >= pj0
   const int cj0 = (pj0 - 2 >= 0) ? (pj0 - 2) / 2 : -((2 - pj0 + 1) / 2);
   const int ci0 = (pi0 - 2 >= 0) ? (pi0 - 2) / 2 : -((2 - pi0 + 1) / 2);
+  // 1 / alpha for the output layer, once per block (see the down kernel)
+  __shared__ float s_inv_alpha;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, (2u * PH * PW + (HAS_P ? CH * CW : 0u)) * 16u);
+    tma_load_pix(ps, &map_xd, pi0, pj0, bz, &bar);
+    tma_load_pix(zs, &map_s, pi0, pj0, bz, &bar);
+    if (HAS_P) tma_load_pix(cs, &map_c, ci0, cj0, bz, &bar);
+    if (LAST) s_inv_alpha = (float)(1.0 / alpha_of(norm2, (size_t)n * n));
+  }
 
   uint32_t wk[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) wk[k] = fK[k * 32 + lane];
-  if constexpr (HAS_P) {
-    #pragma unroll 4
-    for (int e = threadIdx.x; e < CH * CW; e += NT) {
-      const int cr = e / CW, cc = e - cr * CW;
-      const int J = cj0 + cr, I = ci0 + cc;
-      cs[e] = (J >= 0 && J < nc && I >= 0 && I < nc) ? reinterpret_cast<const uint4*>(xcf)[(size_t)J * nc + I]
-                                                     : make_uint4(0, 0, 0, 0);
-    }
+  __syncthreads();   // barrier initialised
+  const bool landed = mbar_wait_bounded(&bar, 0);
+  if (!__syncthreads_and(landed)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
   }
-  // (the barrier below, after x_down and s are staged, also covers cs)
 
-  // x_pre on P in two passes.  (1) x_down and s, coalesced.  (2) per parity
-  // class (gj & 1, gi & 1) of the fine pixel, the TCNN taps that reach it --
-  // 4, 2, 2 or 1, known at compile time, so the weights are constant operands
-  // -- x_pre = x_down + TCNN(x_c) rounded once, then z = s * x_pre.
-  #pragma unroll 4
-  for (int e = threadIdx.x; e < PH * PW; e += NT) {
-    const int pr = e / PW, pc = e - pr * PW;
-    const int gj = pj0 + pr, gi = pi0 + pc;
-    uint4 xv = make_uint4(0, 0, 0, 0), sv = xv;
-    if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
-      const size_t qg = (size_t)gj * n + gi;
-      xv = reinterpret_cast<const uint4*>(xdown)[qg];
-      sv = reinterpret_cast<const uint4*>(s)[qg];
-    }
-    ps[e] = xv;
-    zs[e] = HAS_P ? sv : mul8(xv, sv);
-  }
+  // x_pre on P: per parity class (gj & 1, gi & 1) of the fine pixel, the TCNN
+  // taps that reach it -- 4, 2, 2 or 1, known at compile time, so the weights are
+  // constant operands -- x_pre = x_down + TCNN(x_c) rounded once, z = s * x_pre.
   if constexpr (HAS_P) {
-    __syncthreads();
     TcnnTile t{ps, zs, cs, pj0, pi0, cj0, ci0, n, nc};
     tcnn_class<0, 0, PH, PW, CW>(t, sw);
     tcnn_class<0, 1, PH, PW, CW>(t, sw);
     tcnn_class<1, 0, PH, PW, CW>(t, sw);
     tcnn_class<1, 1, PH, PW, CW>(t, sw);
+  } else {
+    for (int e = threadIdx.x; e < PH * PW; e += NT) zs[e] = mul8(ps[e], zs[e]);
   }
   __syncthreads();
 
@@ -455,6 +453,15 @@ __global__ void __launch_bounds__(NT) up_kernel(const bf16* __restrict__ xdown, 
   }
 }
 
+// Tensor map of a level tensor for a box of bw x bh pixels (copied out of the
+// cache at once: a later lookup may move the cache's storage).
+Status pix8_map(const FusedLevels& fl, const void* base, int n, int bw, int bh, CUtensorMap* out) {
+  const CUtensorMap* m = fl.maps ? fl.maps->pix8(base, n, fl.batch, bw, bh) : nullptr;
+  if (!m) return make_status(MGCNN_ERR_CUDA, "cannot encode a TMA tensor map (n %d, box %d x %d)", n, bw, bh);
+  *out = *m;
+  return {};
+}
+
 // Tile variants (FH x FW): 0 = 16 x 32, 1 = 8 x 32, 2 = 16 x 16.
 template <int FH, int FW>
 Status launch_down(int l, const FusedLevels& fl, const float* r32, const double* norm2, const FusedWeights& w,
@@ -463,14 +470,21 @@ Status launch_down(int l, const FusedLevels& fl, const float* r32, const double*
   const bool first = l == 0, has_r = l + 1 < fl.L;
   const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
   __nv_bfloat16* xc = has_r ? fl.xb[l + 1] : nullptr;
-  if (first && has_r)
-    down_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(r32, norm2, w.small, nullptr, fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
-  else if (first)
-    down_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(r32, norm2, w.small, nullptr, fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
-  else if (has_r)
-    down_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(r32, norm2, w.small, fl.xb[l], fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+  const int R = has_r ? 1 : 0, ZH = FH + R + 2, ZW = FW + R + 2;
+  CUtensorMap ms, mx;
+  MG_TRY(pix8_map(fl, fl.s[l], nl, ZW, ZH, &ms));
+  if (first)
+    mx = ms;   // not read on the finest level
   else
-    down_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(r32, norm2, w.small, fl.xb[l], fl.s[l], w.f_down, w.f_R, fl.xa[l], xc, nl, active);
+    MG_TRY(pix8_map(fl, fl.xb[l], nl, ZW, ZH, &mx));
+  if (first && has_r)
+    down_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(r32, norm2, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+  else if (first)
+    down_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(r32, norm2, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+  else if (has_r)
+    down_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(r32, norm2, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+  else
+    down_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(r32, norm2, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
   MG_LAUNCH("down_kernel");
   return {};
 }
@@ -481,15 +495,22 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
   const int nl = fl.n[l];
   const bool last = l == 0, has_p = l + 1 < fl.L;
   const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
-  const __nv_bfloat16* xcf = has_p ? fl.xb[l + 1] : nullptr;
-  if (last && has_p)
-    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.small, fl.s[l], w.f_up, norm2, u_skip, nullptr, e, nl, active);
-  else if (last)
-    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.small, fl.s[l], w.f_up, norm2, u_skip, nullptr, e, nl, active);
-  else if (has_p)
-    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.small, fl.s[l], w.f_up, norm2, u_skip, fl.xb[l], e, nl, active);
+  const int H = last ? 1 : 0, PH = FH + 2 * H + 2, PW = FW + 2 * H + 2;
+  CUtensorMap mxd, ms, mc;
+  MG_TRY(pix8_map(fl, fl.xa[l], nl, PW, PH, &mxd));
+  MG_TRY(pix8_map(fl, fl.s[l], nl, PW, PH, &ms));
+  if (has_p)
+    MG_TRY(pix8_map(fl, fl.xb[l + 1], fl.n[l + 1], PW / 2 + 2, PH / 2 + 2, &mc));
   else
-    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(fl.xa[l], xcf, w.small, fl.s[l], w.f_up, norm2, u_skip, fl.xb[l], e, nl, active);
+    mc = ms;   // not read on the coarsest level
+  if (last && has_p)
+    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, norm2, u_skip, nullptr, e, nl, active, fl.err);
+  else if (last)
+    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, norm2, u_skip, nullptr, e, nl, active, fl.err);
+  else if (has_p)
+    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, norm2, u_skip, fl.xb[l], e, nl, active, fl.err);
+  else
+    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, norm2, u_skip, fl.xb[l], e, nl, active, fl.err);
   MG_LAUNCH("up_kernel");
   return {};
 }
@@ -583,6 +604,8 @@ Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, dou
   FusedLevels fl;
   fl.L = c->L;
   fl.batch = 1;
+  fl.maps = c->tma;
+  fl.err = c->kerr.as<int>();
   for (int l = 0; l < c->L; ++l) {
     fl.n[l] = c->lv[l].n;
     fl.s[l] = c->s16[l].as<bf16>();

@@ -80,6 +80,8 @@ Status build_graph(mgcnn_ctx* c) {
       FusedLevels fl;
       fl.L = c->L;
       fl.batch = 1;
+      fl.maps = c->tma;
+      fl.err = c->kerr.as<int>();
       for (int l = 0; l < c->L; ++l) {
         fl.n[l] = c->lv[l].n;
         fl.s[l] = c->s16[l].as<__nv_bfloat16>();
@@ -156,6 +158,8 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
     FusedLevels fl;
     fl.L = c->L;
     fl.batch = 1;
+    fl.maps = c->tma;
+    fl.err = c->kerr.as<int>();
     for (int l = 0; l < c->L; ++l) {
       fl.n[l] = c->lv[l].n;
       fl.s[l] = c->s16[l].as<__nv_bfloat16>();

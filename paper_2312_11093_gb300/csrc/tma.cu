@@ -1,0 +1,46 @@
+// Host side of the TMA tile loads: tensor-map encoding through the driver entry
+// point (no link-time dependency on libcuda) and a per-context cache.
+#include "tma.cuh"
+
+namespace mgcnn {
+
+namespace {
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+  static EncodeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeFn>(p);
+  }();
+  return fn;
+}
+
+}  // namespace
+
+const CUtensorMap* TmaMaps::pix8(const void* base, int n, int batch, int bw, int bh) {
+  for (const Entry& e : entries_)
+    if (e.base == base && e.n == n && e.batch == batch && e.bw == bw && e.bh == bh) return &e.map;
+  EncodeFn enc = encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || bw < 1 || bw > 256 || bh < 1 || bh > 256) return nullptr;
+  Entry e{base, n, batch, bw, bh, {}};
+  const cuuint64_t dims[4] = {8, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {16, 16ull * n, 16ull * n * n};
+  const cuuint32_t box[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  if (enc(&e.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, elem,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return nullptr;
+  if (entries_.size() >= 256) entries_.clear();   // bounded: maps are re-made on demand
+  entries_.push_back(e);
+  return &entries_.back().map;
+}
+
+}  // namespace mgcnn
