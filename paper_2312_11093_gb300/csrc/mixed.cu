@@ -40,6 +40,8 @@ struct MixLayout {
   size_t down = 0, up = 0, R = 0;        // byte offsets of the fragment blocks
   size_t w_in = 0, w_out = 0, w_P = 0;   // byte offsets of FP32 arrays
   size_t s_frag = 0, s_fp = 0;           // setup network: 5 fragment blocks, FP32 biases + W_cin (CP = 8)
+  size_t out_hi = 0, out_lo = 0;         // W_out fragments for the fused up kernel (CP = 8)
+  size_t tcnn = 0;                       // TCNN fragments by parity class (CP = 8)
   size_t bytes = 0;
 };
 
@@ -57,6 +59,9 @@ MixLayout mix_layout(const mgcnn_ctx* c) {
   m.w_P = o;   o += (size_t)m.cp * m.cp * 9 * 4;
   m.s_frag = o; o += 5 * m.frag_words * 4;
   m.s_fp = o;   o += (4 * 8 + 8 * kFeatures * 9 + 8) * 4;
+  m.out_hi = o; o += m.frag_words * 4;
+  m.out_lo = o; o += m.frag_words * 4;
+  m.tcnn = o;   o += m.frag_words * 4;
   m.bytes = o;
   return m;
 }
@@ -73,6 +78,27 @@ uint16_t f2bf_host(float f) {
 // B[k][n] with k = tap * CP + ci (zero for ci >= C), n = co (zero for co >= C).
 // Per lane (g = lane/4, q = lane%4) a 32-bit register holds B[k0][n], B[k0+1][n]
 // (low half = lower k) with k0 = 16 s + 2 q (first) or + 8 (second register).
+// B fragments of the TCNN W[ci][co][a][b] for the fused up kernel's parity-class
+// GEMMs: steps (taps 0, 2), (6, 8), (1, 7), (3, 5) as m16n8k16 (k 0-7 = first
+// tap's input channels, k 8-15 = second's) and tap 4 as m16n8k8; n = co.
+void pack_tcnn_frags(const double* W, int C, uint32_t* out) {
+  auto B = [&](int tap, int ci, int co) -> float {
+    return (ci < C && co < C) ? (float)W[((size_t)ci * C + co) * 9 + tap] : 0.0f;
+  };
+  auto pair = [&](int tap, int ci, int co) -> uint32_t {
+    return (uint32_t)f2bf_host(B(tap, ci, co)) | ((uint32_t)f2bf_host(B(tap, ci + 1, co)) << 16);
+  };
+  const int steps[4][2] = {{0, 2}, {6, 8}, {1, 7}, {3, 5}};
+  for (int lane = 0; lane < 32; ++lane) {
+    const int g = lane >> 2, q = lane & 3;
+    for (int s = 0; s < 4; ++s) {
+      out[(2 * s + 0) * 32 + lane] = pair(steps[s][0], 2 * q, g);
+      out[(2 * s + 1) * 32 + lane] = pair(steps[s][1], 2 * q, g);
+    }
+    out[8 * 32 + lane] = pair(4, 2 * q, g);
+  }
+}
+
 void pack_frags(const double* W, int C, int cp, uint32_t* out) {
   auto B = [&](int k, int nn) -> float {
     const int tap = k / cp, ci = k % cp;
@@ -463,7 +489,9 @@ FusedWeights fused_weights(const mgcnn_ctx* c) {
   const MixLayout ml = mix_layout(c);
   const char* wb = c->wmix.as<char>();
   return FusedWeights{reinterpret_cast<const uint32_t*>(wb + ml.down), reinterpret_cast<const uint32_t*>(wb + ml.up),
-                      reinterpret_cast<const uint32_t*>(wb + ml.R), c->small_w};
+                      reinterpret_cast<const uint32_t*>(wb + ml.R), reinterpret_cast<const uint32_t*>(wb + ml.out_hi),
+                      reinterpret_cast<const uint32_t*>(wb + ml.out_lo), reinterpret_cast<const uint32_t*>(wb + ml.tcnn),
+                      c->small_w};
 }
 
 Status mixed_set_weights(mgcnn_ctx* c) {
@@ -493,6 +521,20 @@ Status mixed_set_weights(mgcnn_ctx* c) {
     for (int co = 0; co < C; ++co)
       for (int t = 0; t < 9; ++t) wP[(ci * ml.cp + co) * 9 + t] = (float)w[c->wl.w_P + ((size_t)ci * C + co) * 9 + t];
   if (ml.cp == 8) {
+    // W_out as an 8 -> 8 layer with output channel 0 only, split into BF16 hi + lo
+    std::vector<double> whi(8 * 8 * 9, 0.0), wlo(8 * 8 * 9, 0.0);
+    for (int ci = 0; ci < C; ++ci)
+      for (int t = 0; t < 9; ++t) {
+        const float v = (float)w[c->wl.w_out + ci * 9 + t];
+        const uint32_t hb = (uint32_t)f2bf_host(v) << 16;
+        float hi;
+        std::memcpy(&hi, &hb, 4);
+        whi[ci * 9 + t] = hi;
+        wlo[ci * 9 + t] = (double)(v - hi);
+      }
+    pack_frags(whi.data(), 8, 8, reinterpret_cast<uint32_t*>(blob.data() + ml.out_hi));
+    pack_frags(wlo.data(), 8, 8, reinterpret_cast<uint32_t*>(blob.data() + ml.out_lo));
+    pack_tcnn_frags(w.data() + c->wl.w_P, C, reinterpret_cast<uint32_t*>(blob.data() + ml.tcnn));
     // small layers of the fused kernels, zero beyond C channels
     SmallWeights& sw = c->small_w;
     sw = SmallWeights{};

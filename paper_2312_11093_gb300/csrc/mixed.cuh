@@ -35,6 +35,8 @@ struct FusedLevels {
 };
 struct FusedWeights {
   const uint32_t *f_down, *f_up, *f_R;   // mma B fragments (device)
+  const uint32_t *f_out_hi, *f_out_lo;   // W_out as an 8 -> 8 layer (output channel 0), BF16 hi + lo parts
+  const uint32_t* f_tcnn;                // TCNN by pixel-parity class (taps 0,2 | 6,8 | 1,7 | 3,5 | 4)
   SmallWeights small;                    // by value, see SmallWeights
 };
 Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,

@@ -110,6 +110,36 @@ __device__ __forceinline__ void strip_conv_at(const uint4* tile, const uint32_t*
   mma1688(acc, a[0], a[1], wf[8]);
 }
 
+// One ResNet layer strip y = x + K z (Eq. heteroresnet) with the skip folded
+// into the last MMA step: K = 80, the ninth tap's 8 channels of z followed by
+// the 8 channels of x at the centre pixel, whose B block is the identity.  zt
+// (tile of z) and xt (tile of x) share the pitch; base_m as in strip_conv_at,
+// fI the identity half of the last step's B fragment.
+template <int PITCH>
+__device__ __forceinline__ void layer_strip(const uint4* zt, const uint4* xt, const uint32_t* wf, uint32_t fI,
+                                            int base_m, const TapOffsets<PITCH>& to, float* acc) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    uint32_t a[4];
+    ldsm_x4(a, zt + base_m + to.off[s]);
+    mma16816(acc, a, wf[2 * s], wf[2 * s + 1]);
+  }
+  // lanes 0-15 address rows 0-15 of tap 8 of z (k 0-7), lanes 16-31 the same
+  // rows of x at the centre pixel (k 8-15)
+  uint32_t a[4];
+  ldsm_x4(a, (lane < 16) ? zt + base_m + TapOffsets<PITCH>::off8 : xt + base_m + PITCH + 1);
+  mma16816(acc, a, wf[8], fI);
+}
+
+// The identity block of the last step's B fragment: k = 8 + ci, n = co, one
+// where ci == co (this lane holds ci = 2q, 2q + 1 for co = g).
+__device__ __forceinline__ uint32_t identity_frag() {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const uint32_t one = 0x3F80u;   // BF16 1.0
+  return (2 * q == g ? one : 0u) | ((2 * q + 1 == g ? one : 0u) << 16);
+}
+
 __device__ __forceinline__ double alpha_of(const double* norm2, size_t N) {
   const double v = *norm2;
   return (v > 0.0) ? sqrt((double)N / v) : 1.0;
@@ -226,16 +256,16 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   {
     constexpr int SPR = (XW + 15) / 16;
     const TapOffsets<ZW> to;
+    const uint32_t fI = identity_frag();
     for (int st = warp; st < XH * SPR; st += NW) {
       const int xr = st / SPR, c0 = (st - xr * SPR) * 16;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      strip_conv_at<ZW>(zs, wk, xr * ZW + min(c0 + mrow, XW - 1), xr * ZW + min(c0 + lrow, XW - 1), to, acc);
+      layer_strip<ZW>(zs, xs, wk, fI, xr * ZW + min(c0 + mrow, XW - 1), to, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int xcol = c0 + g + 8 * h;
         if (xcol >= XW) continue;
-        const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&xs[(xr + 1) * ZW + xcol + 1])[q]);
-        const uint32_t o = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
+        const uint32_t o = f2bf(acc[2 * h], acc[2 * h + 1]);
         reinterpret_cast<uint32_t*>(&xd[xr * XW + xcol])[q] = o;
         const int gj = j0 + xr, gi = i0 + xcol;
         if (xr < FH && xcol < FW && gj < n && gi < n)
@@ -270,57 +300,85 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
 struct TcnnTile {
   uint4* ps;          // P region: x_down in, x_pre out
   uint4* zs;          // P region: s in, s * x_pre out
-  const uint4* cs;    // staged coarse pixels
+  const uint4* cs;    // staged coarse pixels (zero outside the coarse grid)
   int pj0, pi0;       // global coordinates of P's corner
   int cj0, ci0;       // global coordinates of cs's corner
-  int n, nc;
+  int n;
 };
 
-// Fine pixels of P with gj & 1 == A and gi & 1 == B.  A fine row 2J + a gets
-// coarse row J through TCNN tap row a: a in {0, 2} for even rows, a = 1 for
-// odd rows (likewise columns), so each class has a fixed tap list.
+// TCNN-add on the tensor cores, one parity class (gj & 1 == A, gi & 1 == B) of
+// the fine pixels of P at a time.  A fine row 2J + a gets coarse row J through
+// tap row a: a in {0, 2} for even rows, a = 1 for odd rows (likewise columns),
+// so a class has a fixed tap list -- 4, 2, 2 or 1 taps, i.e. K = 32, 16, 16 or
+// 8 -- and each 16 class pixels of one class row are a GEMM [16 x K] x [K x 8]
+// whose A rows are coarse pixels gathered by ldmatrix (per-lane addresses; the
+// zero-filled staging covers coarse pixels outside the grid).  fT holds the B
+// fragments in the step order (taps 0, 2 | 6, 8 | 1, 7 | 3, 5 | 4).
+// Epilogue: x_pre = x_down + TCNN rounded once to BF16, z = s * x_pre.
 template <int A, int B, int PH, int PW, int CW>
-__device__ __forceinline__ void tcnn_class(const TcnnTile& t, const SmallWeights& sw) {
+__device__ __forceinline__ void tcnn_class_mma(const TcnnTile& t, const uint32_t* fT, int st, int lane) {
+  constexpr int NCM = (PW + 1) / 2, SPC = (NCM + 15) / 16;
   const int r0 = (A ^ t.pj0) & 1, c0 = (B ^ t.pi0) & 1;   // first P row / column of the class
-  constexpr int NR = (PH + 1) / 2, NC = (PW + 1) / 2;       // class rows / columns, at most
-  for (int e = threadIdx.x; e < NR * NC; e += NT) {
-    const int rr = e / NC, cc = e - rr * NC;
-    const int pr = r0 + 2 * rr, pc = c0 + 2 * cc;
-    const int gj = t.pj0 + pr, gi = t.pi0 + pc;
-    if (pr >= PH || pc >= PW || gj < 0 || gj >= t.n || gi < 0 || gi >= t.n) continue;
+  const int nc_cls = (PW - c0 + 1) >> 1;                    // class columns
+  const int rr = st / SPC, cc0 = (st - rr * SPC) * 16;
+  const int pr = r0 + 2 * rr;
+  if (pr >= PH) return;
+  const int gj = t.pj0 + pr;
+  const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, kh = lane >> 4;
+  const int gi_m = t.pi0 + c0 + 2 * min(cc0 + mrow, nc_cls - 1);
+  const int gi_l = t.pi0 + c0 + 2 * min(cc0 + (lane & 15), nc_cls - 1);
+  // shared-memory pixel of coarse (J, I) for fine (gj, gi) through tap (ta, tb)
+  auto at = [&](int gi_, int ta, int tb) {
+    return t.cs + (((gj - ta) >> 1) - t.cj0) * CW + (((gi_ - tb) >> 1) - t.ci0);
+  };
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  uint32_t a[4];
+  if constexpr (A == 0 && B == 0) {
+    // step 0: taps (0,0) | (0,2); step 1: taps (2,0) | (2,2)
+    ldsm_x4(a, at(gi_m, 0, kh ? 2 : 0));
+    mma16816(acc, a, fT[0], fT[1]);
+    ldsm_x4(a, at(gi_m, 2, kh ? 2 : 0));
+    mma16816(acc, a, fT[2], fT[3]);
+  } else if constexpr (A == 0 && B == 1) {
+    ldsm_x4(a, at(gi_m, kh ? 2 : 0, 1));     // taps (0,1) | (2,1)
+    mma16816(acc, a, fT[4], fT[5]);
+  } else if constexpr (A == 1 && B == 0) {
+    ldsm_x4(a, at(gi_m, 1, kh ? 2 : 0));     // taps (1,0) | (1,2)
+    mma16816(acc, a, fT[6], fT[7]);
+  } else {
+    ldsm_x2(a, at(gi_l, 1, 1));              // tap (1,1)
+    mma1688(acc, a[0], a[1], fT[8]);
+  }
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int cc = cc0 + g + 8 * h;
+    const int pc = c0 + 2 * cc, gi = t.pi0 + pc;
+    if (cc >= nc_cls || gj < 0 || gj >= t.n || gi < 0 || gi >= t.n) continue;
     const int pe = pr * PW + pc;
-    const uint4 xv = t.ps[pe];
-    float acc[8];
-    {
-      const float2 a0 = bf2f(xv.x), a1 = bf2f(xv.y), a2 = bf2f(xv.z), a3 = bf2f(xv.w);
-      acc[0] = a0.x; acc[1] = a0.y; acc[2] = a1.x; acc[3] = a1.y;
-      acc[4] = a2.x; acc[5] = a2.y; acc[6] = a3.x; acc[7] = a3.y;
-    }
-#pragma unroll
-    for (int x = 0; x < (A ? 1 : 2); ++x) {
-      const int ta = A ? 1 : 2 * x;
-      const int J = (gj - ta) >> 1;   // gj - ta is even and >= -2
-      if (J < 0 || J >= t.nc) continue;
-#pragma unroll
-      for (int y = 0; y < (B ? 1 : 2); ++y) {
-        const int tb = B ? 1 : 2 * y;
-        const int I = (gi - tb) >> 1;
-        if (I < 0 || I >= t.nc) continue;
-        const uint4 cv = t.cs[(J - t.cj0) * CW + I - t.ci0];
-        const int tap = ta * 3 + tb;
-        float xin[8];
-        const float2 b0 = bf2f(cv.x), b1 = bf2f(cv.y), b2 = bf2f(cv.z), b3 = bf2f(cv.w);
-        xin[0] = b0.x; xin[1] = b0.y; xin[2] = b1.x; xin[3] = b1.y;
-        xin[4] = b2.x; xin[5] = b2.y; xin[6] = b3.x; xin[7] = b3.y;
-#pragma unroll
-        for (int ci = 0; ci < 8; ++ci)
-#pragma unroll
-          for (int co = 0; co < 8; ++co) acc[co] += sw.w_P[(tap * 8 + ci) * 8 + co] * xin[ci];
-      }
-    }
-    const uint4 xo = make_uint4(f2bf(acc[0], acc[1]), f2bf(acc[2], acc[3]), f2bf(acc[4], acc[5]), f2bf(acc[6], acc[7]));
-    t.ps[pe] = xo;
-    t.zs[pe] = mul8(xo, t.zs[pe]);
+    const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&t.ps[pe])[q]);
+    const uint32_t xo = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
+    reinterpret_cast<uint32_t*>(&t.ps[pe])[q] = xo;
+    const float2 xf = bf2f(xo), sf = bf2f(reinterpret_cast<const uint32_t*>(&t.zs[pe])[q]);
+    reinterpret_cast<uint32_t*>(&t.zs[pe])[q] = f2bf(xf.x * sf.x, xf.y * sf.y);
+  }
+}
+
+// All four classes, strips spread over the warps.
+template <int PH, int PW, int CW>
+__device__ __forceinline__ void tcnn_mma(const TcnnTile& t, const uint32_t* fT) {
+  constexpr int NRM = (PH + 1) / 2, NCM = (PW + 1) / 2, SPC = (NCM + 15) / 16, PER = NRM * SPC;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int st = warp; st < 4 * PER; st += NW) {
+    const int cls = st / PER, sl = st - cls * PER;
+    if (cls == 0)
+      tcnn_class_mma<0, 0, PH, PW, CW>(t, fT, sl, lane);
+    else if (cls == 1)
+      tcnn_class_mma<0, 1, PH, PW, CW>(t, fT, sl, lane);
+    else if (cls == 2)
+      tcnn_class_mma<1, 0, PH, PW, CW>(t, fT, sl, lane);
+    else
+      tcnn_class_mma<1, 1, PH, PW, CW>(t, fT, sl, lane);
   }
 }
 
@@ -335,7 +393,9 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
                                                 const __grid_constant__ CUtensorMap map_s,
                                                 const __grid_constant__ CUtensorMap map_c,
                                                 const __grid_constant__ SmallWeights sw,
-                                                const uint32_t* __restrict__ fK,
+                                                const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
+                                                const uint32_t* __restrict__ fOutHi,
+                                                const uint32_t* __restrict__ fOutLo,
                                                 const double* __restrict__ norm2, const double* __restrict__ u_in,
                                                 bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
                                                 const int* __restrict__ active, int* __restrict__ err) {
@@ -353,7 +413,6 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int pj0 = j0 - H - 1, pi0 = i0 - H - 1;      // global coords of P's corner
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nc = (n - 1) / 2;
   const int bz = blockIdx.z;
   if (active && !active[bz]) return;
   {
@@ -394,11 +453,11 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
   // taps that reach it -- 4, 2, 2 or 1, known at compile time, so the weights are
   // constant operands -- x_pre = x_down + TCNN(x_c) rounded once, z = s * x_pre.
   if constexpr (HAS_P) {
-    TcnnTile t{ps, zs, cs, pj0, pi0, cj0, ci0, n, nc};
-    tcnn_class<0, 0, PH, PW, CW>(t, sw);
-    tcnn_class<0, 1, PH, PW, CW>(t, sw);
-    tcnn_class<1, 0, PH, PW, CW>(t, sw);
-    tcnn_class<1, 1, PH, PW, CW>(t, sw);
+    uint32_t fT[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fT[k] = fTc[k * 32 + lane];
+    const TcnnTile t{ps, zs, cs, pj0, pi0, cj0, ci0, n};
+    tcnn_mma<PH, PW, CW>(t, fT);
   } else {
     for (int e = threadIdx.x; e < PH * PW; e += NT) zs[e] = mul8(ps[e], zs[e]);
   }
@@ -408,18 +467,18 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
   const int g = lane >> 2, q = lane & 3;
   {
     constexpr int SPR = (OW + 15) / 16;
-    const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
+    const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
     const TapOffsets<PW> to;
+    const uint32_t fI = identity_frag();
     for (int st = warp; st < OH * SPR; st += NW) {
       const int orow = st / SPR, c0 = (st - orow * SPR) * 16;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      strip_conv_at<PW>(zs, wk, orow * PW + min(c0 + mrow, OW - 1), orow * PW + min(c0 + lrow, OW - 1), to, acc);
+      layer_strip<PW>(zs, ps, wk, fI, orow * PW + min(c0 + mrow, OW - 1), to, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int ocol = c0 + g + 8 * h;
         if (ocol >= OW) continue;
-        const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&ps[(orow + 1) * PW + ocol + 1])[q]);
-        const uint32_t o = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
+        const uint32_t o = f2bf(acc[2 * h], acc[2 * h + 1]);
         const int gj = j0 - H + orow, gi = i0 - H + ocol;
         if constexpr (LAST) {
           // zero outside the grid: W_out's zero padding
@@ -431,24 +490,38 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
     }
   }
   if constexpr (LAST) {
+    // W_out on the tensor cores: an 8 -> 8 channel layer whose only nonzero
+    // output channel is 0, with the FP32 weights split as hi + lo BF16 (the two
+    // products are accumulated in FP32, so the weights keep ~16 bits); strips of
+    // 16 owned pixels of one row, as in the layer above
+    uint32_t wh[9], wl[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      wh[k] = fOutHi[k * 32 + lane];
+      wl[k] = fOutLo[k * 32 + lane];
+    }
     __syncthreads();
     const float inv_alpha = s_inv_alpha;
-    for (int e = threadIdx.x; e < FH * FW; e += NT) {
-      const int rr = e / FW, cc = e - rr * FW;
-      const int gj = j0 + rr, gi = i0 + cc;
-      if (gj >= n || gi >= n) continue;
-      float acc = 0.f;
+    constexpr int SPRO = (FW + 15) / 16;
+    const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
+    const TapOffsets<OW> to;
+    for (int st = warp; st < FH * SPRO; st += NW) {
+      const int rr = st / SPRO, c0 = (st - rr * SPRO) * 16;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const int bm = rr * OW + min(c0 + mrow, FW - 1), bl = rr * OW + min(c0 + lrow, FW - 1);
+      strip_conv_at<OW>(os, wh, bm, bl, to, acc);
+      strip_conv_at<OW>(os, wl, bm, bl, to, acc);
+      if (q == 0) {
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const uint4 v = os[(rr + t / 3) * OW + cc + t % 3];
-        const float2 a0 = bf2f(v.x), a1 = bf2f(v.y), a2 = bf2f(v.z), a3 = bf2f(v.w);
-        acc += sw.w_out[t * 8 + 0] * a0.x + sw.w_out[t * 8 + 1] * a0.y + sw.w_out[t * 8 + 2] * a1.x +
-               sw.w_out[t * 8 + 3] * a1.y + sw.w_out[t * 8 + 4] * a2.x + sw.w_out[t * 8 + 5] * a2.y +
-               sw.w_out[t * 8 + 6] * a3.x + sw.w_out[t * 8 + 7] * a3.y;
+        for (int h = 0; h < 2; ++h) {
+          const int cc = c0 + g + 8 * h;
+          const int gj = j0 + rr, gi = i0 + cc;
+          if (cc >= FW || gj >= n || gi >= n) continue;
+          const size_t qg = (size_t)gj * n + gi;
+          const double ev = (double)(acc[2 * h] * inv_alpha);
+          u_out[qg] = (u_in ? u_in[qg] : 0.0) + ev;
+        }
       }
-      const size_t qg = (size_t)gj * n + gi;
-      const double ev = (double)(acc * inv_alpha);
-      u_out[qg] = (u_in ? u_in[qg] : 0.0) + ev;
     }
   }
 }
@@ -504,13 +577,13 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
   else
     mc = ms;   // not read on the coarsest level
   if (last && has_p)
-    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, norm2, u_skip, nullptr, e, nl, active, fl.err);
+    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, norm2, u_skip, nullptr, e, nl, active, fl.err);
   else if (last)
-    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, norm2, u_skip, nullptr, e, nl, active, fl.err);
+    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, norm2, u_skip, nullptr, e, nl, active, fl.err);
   else if (has_p)
-    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, norm2, u_skip, fl.xb[l], e, nl, active, fl.err);
+    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, norm2, u_skip, fl.xb[l], e, nl, active, fl.err);
   else
-    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, norm2, u_skip, fl.xb[l], e, nl, active, fl.err);
+    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, norm2, u_skip, fl.xb[l], e, nl, active, fl.err);
   MG_LAUNCH("up_kernel");
   return {};
 }
