@@ -447,6 +447,7 @@ void mgcnn_destroy(mgcnn_ctx* c) {
   }
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   release(c->kerr);
+  release(c->alpha32);
   delete c->tma;
   delete c;
 }

@@ -192,6 +192,7 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff) {
   MG_TRY(ensure(k.scratch, B * N0 * sizeof(double)));
   MG_TRY(ensure(k.partial, B * reduction_blocks(N0) * sizeof(double)));
   MG_TRY(ensure(k.rn2, B * sizeof(double)));
+  MG_TRY(ensure(k.alpha, 2 * B * sizeof(float)));
   MG_TRY(ensure(k.fn2, B * sizeof(double)));
   MG_TRY(ensure(k.state, 3 * B * sizeof(int)));
   if (!c->fused) {   // FP32 scratch of the unfused setup network only
@@ -236,6 +237,7 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff) {
   k.fl.batch = k.B;
   k.fl.maps = c->tma;
   k.fl.err = c->kerr.as<int>();
+  k.fl.alpha = k.alpha.as<float>();
   for (int l = 0; l < k.L; ++l) {
     k.fl.n[l] = k.nl[l];
     k.fl.s[l] = k.s16[l].as<bf16>();
@@ -309,7 +311,7 @@ void batch_release(mgcnn_ctx* c) {
     for (int l = 0; l < kMaxLevels; ++l) {
       release(k.op[l]); release(k.s16[l]); release(k.xa[l]); release(k.xb[l]);
     }
-    for (DevBuf* b : {&k.dinv32, &k.r32, &k.f, &k.u, &k.partial, &k.rn2, &k.fn2, &k.state, &k.hist, &k.feat,
+    for (DevBuf* b : {&k.dinv32, &k.r32, &k.f, &k.u, &k.partial, &k.rn2, &k.alpha, &k.fn2, &k.state, &k.hist, &k.feat,
                       &k.ca, &k.cb, &k.za, &k.zb, &k.s32, &k.scratch})
       release(*b);
     if (k.stream) cudaStreamDestroy(k.stream);

@@ -18,6 +18,7 @@ struct BatchClass {
   DevBuf f, u;                                 // [B][N] FP64
   DevBuf partial;                              // [B][blocks]
   DevBuf rn2, fn2;                             // [B]
+  DevBuf alpha;                                // [B][2] input scale of the fused V-cycle
   DevBuf state;                                // int [3][B]: active, iters, status
   DevBuf hist;                                 // [B][maxit + 1]
   DevBuf feat, ca, cb, za, zb, s32;            // FP32 setup scratch

@@ -121,6 +121,7 @@ struct mgcnn_ctx {
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
   mgcnn::TmaMaps* tma = nullptr;          // tensor maps of the fused kernels' TMA tile loads
   mgcnn::DevBuf kerr;                     // device flag: a kernel gave up waiting for its tile copies
+  mgcnn::DevBuf alpha32;                  // input scale of the fused V-cycle (alpha, 1 / alpha)
   mgcnn::SmallWeights small_w{};          // host copy of the fused kernels' small layers
   mgcnn::SetupSmallWeights setup_small_w{};  // host copy of the fused setup kernel's small layers
   mgcnn::DevBuf s32tmp;                   // FP32 setup output before the BF16 cast

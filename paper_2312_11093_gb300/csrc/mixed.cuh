@@ -26,6 +26,7 @@ struct FusedLevels {
   int L = 0, batch = 1;
   TmaMaps* maps = nullptr;               // tensor-map cache of the owner (context or batch class)
   int* err = nullptr;                    // device flag: a block's tile copies timed out
+  float* alpha = nullptr;                // device [batch][2]: input scale alpha and 1 / alpha per problem
   int n[kMaxLevels] = {};
   int var_down[kMaxLevels] = {};         // tile variant per level (autotuned)
   int var_up[kMaxLevels] = {};

@@ -23,6 +23,7 @@
 // an odd-sized region.
 #include <cmath>
 
+#include "fpconv.cuh"
 #include "mixed.cuh"
 #include "ops.cuh"
 #include "tma.cuh"
@@ -145,13 +146,31 @@ __device__ __forceinline__ double alpha_of(const double* norm2, size_t N) {
   return (v > 0.0) ? sqrt((double)N / v) : 1.0;
 }
 
+// alpha2[2b] = alpha = sqrt(N / ||r_b||^2), alpha2[2b + 1] = 1 / alpha, once per
+// cycle and problem: an FP64 divide and square root are dozens of FP64-pipe
+// instructions, too many to repeat in every block of the level kernels.
+__global__ void alpha_kernel(const double* __restrict__ norm2, float* __restrict__ alpha2, size_t N, int batch) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const double a = alpha_of(norm2 + b, N);
+  alpha2[2 * b] = (float)a;
+  alpha2[2 * b + 1] = (float)(1.0 / a);
+}
+
+Status launch_alpha(const FusedLevels& fl, const double* norm2, cudaStream_t st) {
+  if (!fl.alpha) return make_status(MGCNN_ERR_STATE, "fused levels without an alpha buffer");
+  alpha_kernel<<<(fl.batch + 127) / 128, 128, 0, st>>>(norm2, fl.alpha, (size_t)fl.n[0] * fl.n[0], fl.batch);
+  MG_LAUNCH("alpha_kernel");
+  return {};
+}
+
 // ---------------------------------------------------------------------------
 // Down kernel.  Regions, in fine coordinates relative to (j0, i0) = (2 J0, 2 I0):
 //   X (layer output kept):   rows 0..XH-1, cols 0..XW-1 (XH = 16 + R, XW = 32 + R)
 //   Z (layer input, halo 1): rows -1..XH,  cols -1..XW
 //   Rg (residual, halo 2):   rows -2..XH+1, cols -2..XW+1   (finest level only)
 template <int FH, int FW, bool FIRST, bool HAS_R>
-__global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, const double* __restrict__ norm2,
+__global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, const float* __restrict__ alpha2,
                                                   const __grid_constant__ SmallWeights sw,
                                                   const __grid_constant__ CUtensorMap map_x,
                                                   const __grid_constant__ CUtensorMap map_s,
@@ -177,23 +196,15 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   if (active && !active[bz]) return;
   {
     const size_t Nc = (size_t)((n - 1) / 2) * ((n - 1) / 2);
-    if (FIRST) {
-      r += bz * N;
-      norm2 += bz;
-    }
+    if (FIRST) r += bz * N;
     xdown += bz * N * 8;
     if (HAS_R) xc += bz * Nc * 8;
   }
-  // the input scale alpha = sqrt(N / ||r||^2) of the finest level: FP64 divide
-  // and square root are dozens of FP64-pipe instructions, so one thread
-  // computes it per block
-  __shared__ float s_alpha;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     mbar_expect_tx(&bar, (FIRST ? 1u : 2u) * ZH * ZW * 16u);
     tma_load_pix(zs, &map_s, i0 - 1, j0 - 1, bz, &bar);
     if (!FIRST) tma_load_pix(xs, &map_x, i0 - 1, j0 - 1, bz, &bar);
-    if (FIRST) s_alpha = (float)alpha_of(norm2, N);
   }
 
   uint32_t wk[9], wr[9];
@@ -202,10 +213,10 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
     wk[k] = fK[k * 32 + lane];
     if (HAS_R) wr[k] = fR[k * 32 + lane];
   }
-  __syncthreads();   // barrier initialised, alpha published
+  __syncthreads();   // barrier initialised
 
   if constexpr (FIRST) {
-    const float alpha = s_alpha;
+    const float alpha = alpha2[2 * bz];   // the finest level's input scale
     #pragma unroll 4
     for (int e = threadIdx.x; e < RH * RW; e += NT) {
       const int rr = e / RW, cc = e - rr * RW;
@@ -396,7 +407,7 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
                                                 const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
                                                 const uint32_t* __restrict__ fOutHi,
                                                 const uint32_t* __restrict__ fOutLo,
-                                                const double* __restrict__ norm2, const double* __restrict__ u_in,
+                                                const float* __restrict__ alpha2, const double* __restrict__ u_in,
                                                 bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
                                                 const int* __restrict__ active, int* __restrict__ err) {
   constexpr int H = LAST ? 1 : 0;
@@ -418,7 +429,6 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
   {
     const size_t N = (size_t)n * n;
     if (LAST) {
-      norm2 += bz;
       if (u_in) u_in += bz * N;
       u_out += bz * N;
     } else {
@@ -428,15 +438,12 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
   // coarse corner: the smallest J with 2J + 2 >= pj0
   const int cj0 = (pj0 - 2 >= 0) ? (pj0 - 2) / 2 : -((2 - pj0 + 1) / 2);
   const int ci0 = (pi0 - 2 >= 0) ? (pi0 - 2) / 2 : -((2 - pi0 + 1) / 2);
-  // 1 / alpha for the output layer, once per block (see the down kernel)
-  __shared__ float s_inv_alpha;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     mbar_expect_tx(&bar, (2u * PH * PW + (HAS_P ? CH * CW : 0u)) * 16u);
     tma_load_pix(ps, &map_xd, pi0, pj0, bz, &bar);
     tma_load_pix(zs, &map_s, pi0, pj0, bz, &bar);
     if (HAS_P) tma_load_pix(cs, &map_c, ci0, cj0, bz, &bar);
-    if (LAST) s_inv_alpha = (float)(1.0 / alpha_of(norm2, (size_t)n * n));
   }
 
   uint32_t wk[9];
@@ -501,7 +508,9 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
       wl[k] = fOutLo[k * 32 + lane];
     }
     __syncthreads();
-    const float inv_alpha = s_inv_alpha;
+    const float inv_alpha = alpha2[2 * bz + 1];
+    float* ev = reinterpret_cast<float*>(ps);   // FH x FW corrections
+    static_assert(FH * FW * sizeof(float) <= sizeof(ps), "correction staging");
     constexpr int SPRO = (FW + 15) / 16;
     const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
     const TapOffsets<OW> to;
@@ -511,17 +520,24 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
       const int bm = rr * OW + min(c0 + mrow, FW - 1), bl = rr * OW + min(c0 + lrow, FW - 1);
       strip_conv_at<OW>(os, wh, bm, bl, to, acc);
       strip_conv_at<OW>(os, wl, bm, bl, to, acc);
+      // output channel 0 sits in the q == 0 lanes: stage it in shared memory
+      // (the P tiles are free now) so that the FP64 update below runs on
+      // full warps -- an FP64 instruction costs the same with 8 lanes or 32
       if (q == 0) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int cc = c0 + g + 8 * h;
-          const int gj = j0 + rr, gi = i0 + cc;
-          if (cc >= FW || gj >= n || gi >= n) continue;
-          const size_t qg = (size_t)gj * n + gi;
-          const double ev = (double)(acc[2 * h] * inv_alpha);
-          u_out[qg] = (u_in ? u_in[qg] : 0.0) + ev;
+          if (cc < FW) ev[rr * FW + cc] = acc[2 * h] * inv_alpha;
         }
       }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < FH * FW; e += NT) {
+      const int rr = e / FW, cc = e - rr * FW;
+      const int gj = j0 + rr, gi = i0 + cc;
+      if (gj >= n || gi >= n) continue;
+      const size_t qg = (size_t)gj * n + gi;
+      u_out[qg] = (u_in ? u_in[qg] : 0.0) + f32_to_f64_exact(ev[e]);
     }
   }
 }
@@ -551,13 +567,13 @@ Status launch_down(int l, const FusedLevels& fl, const float* r32, const double*
   else
     MG_TRY(pix8_map(fl, fl.xb[l], nl, ZW, ZH, &mx));
   if (first && has_r)
-    down_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(r32, norm2, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+    down_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
   else if (first)
-    down_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(r32, norm2, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+    down_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
   else if (has_r)
-    down_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(r32, norm2, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+    down_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
   else
-    down_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(r32, norm2, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+    down_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
   MG_LAUNCH("down_kernel");
   return {};
 }
@@ -577,13 +593,13 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
   else
     mc = ms;   // not read on the coarsest level
   if (last && has_p)
-    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, norm2, u_skip, nullptr, e, nl, active, fl.err);
+    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, nullptr, e, nl, active, fl.err);
   else if (last)
-    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, norm2, u_skip, nullptr, e, nl, active, fl.err);
+    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, nullptr, e, nl, active, fl.err);
   else if (has_p)
-    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, norm2, u_skip, fl.xb[l], e, nl, active, fl.err);
+    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, fl.xb[l], e, nl, active, fl.err);
   else
-    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, norm2, u_skip, fl.xb[l], e, nl, active, fl.err);
+    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, fl.xb[l], e, nl, active, fl.err);
   MG_LAUNCH("up_kernel");
   return {};
 }
@@ -617,6 +633,7 @@ Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double
                            const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
                            mgcnn_ctx* prof_ctx) {
   const int L = fl.L;
+  MG_TRY(launch_alpha(fl, norm2, st));
   for (int l = 0; l < L; ++l) {
     const int ps = (l == 0 && prof_ctx) ? prof_begin(prof_ctx, kProfDown0) : -1;
     MG_TRY(launch_down_variant(fl.var_down[l], l, fl, r32, norm2, w, active, st));
@@ -639,7 +656,7 @@ Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, do
   cudaEvent_t e0, e1;
   MG_CUDA(cudaEventCreate(&e0));
   MG_CUDA(cudaEventCreate(&e1));
-  Status result;
+  Status result = launch_alpha(fl, norm2, st);
   for (int l = 0; l < fl.L && result.ok(); ++l) {
     float best_d = 1e30f, best_u = 1e30f;
     for (int v = 0; v < kFusedVariants && result.ok(); ++v) {
@@ -679,6 +696,8 @@ Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, dou
   fl.batch = 1;
   fl.maps = c->tma;
   fl.err = c->kerr.as<int>();
+  MG_TRY(ensure(c->alpha32, 2 * sizeof(float)));
+  fl.alpha = c->alpha32.as<float>();
   for (int l = 0; l < c->L; ++l) {
     fl.n[l] = c->lv[l].n;
     fl.s[l] = c->s16[l].as<bf16>();

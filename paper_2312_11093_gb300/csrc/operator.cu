@@ -7,6 +7,7 @@
 // weighting of log k (divergence form) or by sampling mu (non-divergence form).
 #include <cmath>
 
+#include "fpconv.cuh"
 #include "ops.cuh"
 
 namespace mgcnn {
@@ -266,7 +267,8 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
 
 // r = f - A u, FP64 (Eq. 1); per-block partial of sum r^2.
 // FP64 runs at 1/58 of the FP32 rate here, so the kernel keeps FP64 work to the
-// minimum: five FMAs for f - A u, one for r^2, and the block reduction once per
+// minimum: five FMAs for f - A u, one for r^2, the FP32 copy converted with
+// integer operations (fpconv.cuh), and the block reduction once per
 // kResidualPix pixels per thread (thread t of block b takes pixels
 // b * kResidualPix * blockDim + k * blockDim + t, k = 0.., summed in that order).
 __global__ void __launch_bounds__(kResidualBlock)
@@ -302,7 +304,10 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
       rv = fma(-op[3 * N + p], uS, rv);
       rv = fma(-op[4 * N + p], uN, rv);
       if (r) r[p] = rv;
-      if (r32) r32[p] = dinv32 ? (float)rv * dinv32[p] : (float)rv;
+      if (r32) {
+        const float rf = f64_to_f32_rn(rv);
+        r32[p] = dinv32 ? rf * dinv32[p] : rf;
+      }
       rr = fma(rv, rv, rr);
     }
   }

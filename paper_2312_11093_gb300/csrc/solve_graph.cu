@@ -82,6 +82,7 @@ Status build_graph(mgcnn_ctx* c) {
       fl.batch = 1;
       fl.maps = c->tma;
       fl.err = c->kerr.as<int>();
+      fl.alpha = c->alpha32.as<float>();
       for (int l = 0; l < c->L; ++l) {
         fl.n[l] = c->lv[l].n;
         fl.s[l] = c->s16[l].as<__nv_bfloat16>();
@@ -129,6 +130,7 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
   const size_t N0 = c->lv[0].N();
   cudaStream_t st = c->stream;
   MG_TRY(ensure(c->gstate, 4 * sizeof(int)));
+  MG_TRY(ensure(c->alpha32, 2 * sizeof(float)));
   MG_TRY(ensure(c->gparams, 2 * sizeof(double)));
   if (c->ghist.bytes < (size_t)(maxit + 1) * sizeof(double)) {
     MG_TRY(ensure(c->ghist, (size_t)(maxit + 1) * sizeof(double)));
@@ -160,6 +162,7 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
     fl.batch = 1;
     fl.maps = c->tma;
     fl.err = c->kerr.as<int>();
+    fl.alpha = c->alpha32.as<float>();
     for (int l = 0; l < c->L; ++l) {
       fl.n[l] = c->lv[l].n;
       fl.s[l] = c->s16[l].as<__nv_bfloat16>();
