@@ -228,6 +228,13 @@ int mgcnn_gmg_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int 
  * coeff[i]: nodal k of problem i, (n[i]+2)^2 doubles; host or device; copied. */
 int mgcnn_setup_batched(mgcnn_ctx* ctx, int nprob, const double* const* coeff, const int* n);
 
+/* As mgcnn_setup_batched, but every problem gets the analytic setup tensors of
+ * the 8-channel GMG V(1, 0) network (the ones mgcnn_setup_gmg builds on such a
+ * context, Jacobi weight omega) instead of running the setup network; load
+ * that network's weights first.  Errors as mgcnn_setup_batched, ARG for omega
+ * outside (0, 2). */
+int mgcnn_setup_batched_gmg(mgcnn_ctx* ctx, int nprob, const double* const* coeff, const int* n, double omega);
+
 /* rhs[i], u[i]: n[i]^2 doubles (host or device); u[i] is the initial guess on
  * entry and the last iterate on return.  iters[i] (may be NULL) receives the
  * cycles applied, relres[i] (may be NULL) the last ||r||/||f||, status[i]

@@ -747,6 +747,12 @@ int mgcnn_setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, con
   return finish(c, setup_batched(c, nprob, coeff, n));
 }
 
+int mgcnn_setup_batched_gmg(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* n, double omega) {
+  if (!c || !coeff || !n) return MGCNN_ERR_ARG;
+  if (!(omega > 0.0 && omega < 2.0)) return finish(c, make_status(MGCNN_ERR_ARG, "omega must be in (0, 2)"));
+  return finish(c, setup_batched(c, nprob, coeff, n, omega));
+}
+
 int mgcnn_solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol, int maxit,
                         int* iters, double* relres, int* status) {
   if (!c || !rhs || !u || maxit < 0 || !(tol >= 0.0)) return MGCNN_ERR_ARG;

@@ -29,7 +29,8 @@ struct BatchClass {
 };
 
 void batch_release(mgcnn_ctx* c);
-Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* ns);
+// omega > 0: analytic setup tensors of the 8-channel GMG V(1, 0) network (Jacobi weight omega)
+Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* ns, double omega = 0.0);
 Status solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol, int maxit,
                      int* iters, double* relres, int* status);
 

@@ -629,6 +629,9 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega) {
   MG_TRY(ensure(c->x16b[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
   const int C = c->cfg.channels;
+  if (C == kGmgV10Channels)   // straight into the BF16 layout
+    return launch_gmg_v10_setup_bf16(c->op[l].as<double>(), c->s16[l].as<bf16>(), c->lv[l].n, omega, c->stream,
+                                     l == 0 && c->cfg.input_diag);
   MG_TRY(ensure(c->setup_a, N * C * sizeof(double)));
   MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->setup_a.as<double>(), c->lv[l].n, omega, c->stream,
                           l == 0 && c->cfg.input_diag, C));

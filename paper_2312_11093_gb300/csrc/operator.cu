@@ -413,16 +413,14 @@ __global__ void gmg_setup_kernel(const double* __restrict__ op, double* __restri
 //   s[F_G] = 1 - omega,  s[F_J] = omega / a_C,  s[D] = s[E] = 0.
 // With the normalised input at the finest level (rhs copies hold D^{-1} r):
 //   s[T_o](q) = -omega a_o(q-o),  s[F_G] = (1 - omega) a_C,  s[F_J] = omega.
-__global__ void gmg_v10_setup_kernel(const double* __restrict__ op, double* __restrict__ out, int n, double omega,
-                                     int input_diag_level) {
+// The eight values of node p (problem blockIdx.y of a batch stored back to back).
+__device__ __forceinline__ void gmg_v10_values(const double* __restrict__ op, int n, double omega,
+                                               int input_diag_level, int p, double* o) {
   const size_t N = (size_t)n * n;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (int)N) return;
   const int j = p / n, i = p - j * n;
   const int dy[4] = {0, 0, -1, 1}, dx[4] = {-1, 1, 0, 0};  // W, E, S, N
   const double aCq = op[p];
   const double inv = input_diag_level ? 1.0 : 1.0 / aCq;   // one FP64 divide per node
-  double* o = out + (size_t)p * kGmgV10Channels;
   for (int k = 0; k < 4; ++k) {
     const int pj = j - dy[k], pi = i - dx[k];
     double v = 0.0;
@@ -433,6 +431,39 @@ __global__ void gmg_v10_setup_kernel(const double* __restrict__ op, double* __re
   o[5] = omega * inv;
   o[6] = 0.0;
   o[7] = 0.0;
+}
+
+__global__ void gmg_v10_setup_kernel(const double* __restrict__ op, double* __restrict__ out, int n, double omega,
+                                     int input_diag_level) {
+  const size_t N = (size_t)n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (int)N) return;
+  gmg_v10_values(op, n, omega, input_diag_level, p, out + (size_t)p * kGmgV10Channels);
+}
+
+// BF16 variant for the mixed-precision path: one 16-byte pixel per node, the
+// values rounded as FP64 -> FP32 -> BF16 (the rounding of the FP64 -> BF16
+// padding copy), for a batch of problems stored back to back.
+__global__ void gmg_v10_setup_bf16_kernel(const double* __restrict__ op, __nv_bfloat16* __restrict__ out, int n,
+                                          double omega, int input_diag_level) {
+  const size_t N = (size_t)n * n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (int)N) return;
+  op += (size_t)blockIdx.y * 5 * N;
+  out += (size_t)blockIdx.y * N * kGmgV10Channels;
+  double o[8];
+  gmg_v10_values(op, n, omega, input_diag_level, p, o);
+  __nv_bfloat162 h[4];
+  for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn((float)o[2 * k], (float)o[2 * k + 1]);
+  reinterpret_cast<uint4*>(out)[p] = *reinterpret_cast<const uint4*>(h);
+}
+
+Status launch_gmg_v10_setup_bf16(const double* op, __nv_bfloat16* out, int n, double omega, cudaStream_t st,
+                                 bool input_diag_level, int batch) {
+  gmg_v10_setup_bf16_kernel<<<dim3(grid_for((size_t)n * n, 256), batch), 256, 0, st>>>(op, out, n, omega,
+                                                                                        input_diag_level ? 1 : 0);
+  MG_LAUNCH("gmg_v10_setup_bf16_kernel");
+  return {};
 }
 
 Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st,

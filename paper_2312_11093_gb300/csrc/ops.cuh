@@ -41,6 +41,9 @@ constexpr int kGmgChannels = 13;
 constexpr int kGmgV10Channels = 8;
 Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st,
                         bool input_diag_level = false, int channels = kGmgChannels);
+// The 8-channel V(1, 0) setup tensors straight into the BF16 [batch][N][8] layout.
+Status launch_gmg_v10_setup_bf16(const double* op, __nv_bfloat16* out, int n, double omega, cudaStream_t st,
+                                 bool input_diag_level, int batch = 1);
 Status launch_axpy_to(const double* u, const double* e, double* out, size_t N, cudaStream_t st);
 
 // ---- net_generic.cu: FP64 / FP32 direct convolution kernels ----------------

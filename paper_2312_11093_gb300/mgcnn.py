@@ -72,6 +72,7 @@ def load() -> ctypes.CDLL:
         "mgcnn_gmg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_int, c_double,
                                     POINTER(c_int), c_void_p]),
         "mgcnn_setup_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+        "mgcnn_setup_batched_gmg": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double]),
         "mgcnn_solve_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
                                         c_void_p]),
         "mgcnn_kernel_launches": (ctypes.c_longlong, []),
@@ -315,12 +316,17 @@ class Solver:
         return st, it.value, hist[: it.value + 1]
 
     # -- batched solves -----------------------------------------------------------
-    def setup_batched(self, coeffs, ns):
-        """coeffs[i]: nodal k of problem i ((n_i+2)^2 doubles), ns[i] = n_i."""
+    def setup_batched(self, coeffs, ns, gmg_omega: float | None = None):
+        """coeffs[i]: nodal k of problem i ((n_i+2)^2 doubles), ns[i] = n_i.  With
+        gmg_omega, the analytic setup of the 8-channel GMG V(1,0) network."""
         m = len(coeffs)
         kp = (c_void_p * m)(*[_ptr(k, (n + 2) * (n + 2)) for k, n in zip(coeffs, ns)])
         nn = (c_int * m)(*[int(n) for n in ns])
-        self._check(self._L.mgcnn_setup_batched(self._h, m, kp, nn), "mgcnn_setup_batched")
+        if gmg_omega is None:
+            self._check(self._L.mgcnn_setup_batched(self._h, m, kp, nn), "mgcnn_setup_batched")
+        else:
+            self._check(self._L.mgcnn_setup_batched_gmg(self._h, m, kp, nn, float(gmg_omega)),
+                        "mgcnn_setup_batched_gmg")
         self.batch_sizes = [int(n) for n in ns]
 
     def solve_batched(self, rhs, us, tol: float, maxit: int):
