@@ -245,6 +245,7 @@ def main():
     ap.add_argument("--net", default=None, choices=["trained", "gmg_v10", "gmg"])
     ap.add_argument("--workload", default=None, choices=["channelised", "grf", "batched256"])
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--maxit", type=int, default=100, help="cycle limit of the batched solves")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -486,7 +487,7 @@ def bench_batched(args, rank, world, local):
         sv.setup_batched(kk, ns, gmg_omega=0.8 if is_gmg else None)
         for u in uu:
             u.zero_() if hasattr(u, "zero_") else u.fill(0.0)
-        return sv.solve_batched(ff, uu, args.tol, 300)
+        return sv.solve_batched(ff, uu, args.tol, args.maxit)
 
     def barrier():
         if world > 1:
@@ -523,8 +524,9 @@ def bench_batched(args, rank, world, local):
         step(ks, fs, uh)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     unknowns = int(sum(n * n for n in ns))
+    done = int((stat == 0).sum())   # problems that reached the tolerance count as solves
     res = {"metric": "solves/s to rel-res 1e-6, batch of uneven sizes (setup + solve)",
-           "value": world * args.batch * 1e3 / ms, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "value": world * done * 1e3 / ms, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
            "config": {"workload": f"batched{args.batch}_63-1023" + ("_grf" if is_gmg else ""), "problems": args.batch,
@@ -532,7 +534,7 @@ def bench_batched(args, rank, world, local):
                       "parallelism": "replicas" if world > 1 else "single"},
            "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
            "converged": int((stat == 0).sum()), "relres_max": float(relres.max()),
-           "e2e": {"value": world * args.batch * 1e3 / e2e_ms, "unit": "solves/s",
+           "e2e": {"value": world * done * 1e3 / e2e_ms, "unit": "solves/s",
                    "h2d_bytes_per_step": int(sum(k.nbytes for k in ks) + 2 * sum(f.nbytes for f in fs)),
                    "d2h_bytes_per_step": int(sum(f.nbytes for f in fs)), "ms_per_step": e2e_ms},
            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None}

@@ -170,7 +170,7 @@ Status launch_alpha(const FusedLevels& fl, const double* norm2, cudaStream_t st)
 //   Z (layer input, halo 1): rows -1..XH,  cols -1..XW
 //   Rg (residual, halo 2):   rows -2..XH+1, cols -2..XW+1   (finest level only)
 template <int FH, int FW, bool FIRST, bool HAS_R>
-__global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, const float* __restrict__ alpha2,
+__global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r, const float* __restrict__ alpha2,
                                                   const __grid_constant__ SmallWeights sw,
                                                   const __grid_constant__ CUtensorMap map_x,
                                                   const __grid_constant__ CUtensorMap map_s,
@@ -259,23 +259,25 @@ __global__ void __launch_bounds__(NT) down_kernel(const float* __restrict__ r, c
   }
   __syncthreads();
 
-  // layer: X = x_in + K (s * x_in).  Strips are 16 consecutive pixels of one X
-  // row (SPR strips per row, the last one clamped and partly idle), so every
-  // lane's A-row address is a row base plus a column and fixed tap offsets.
+  // layer: X = x_in + K (s * x_in); every lane's A-row address is its pixel's
+  // tile position plus fixed tap offsets.
   const int g = lane >> 2, q = lane & 3;
   const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
   {
-    constexpr int SPR = (XW + 15) / 16;
+    // strips of 16 consecutive pixels of X in row-major order (a strip may wrap
+    // to the next row); the division by the compile-time width is a multiply
+    constexpr int NX = XH * XW, NSTRIP = (NX + 15) / 16;
     const TapOffsets<ZW> to;
     const uint32_t fI = identity_frag();
-    for (int st = warp; st < XH * SPR; st += NW) {
-      const int xr = st / SPR, c0 = (st - xr * SPR) * 16;
+    for (int st = warp; st < NSTRIP; st += NW) {
+      const int pm = min(st * 16 + mrow, NX - 1), rm = pm / XW;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      layer_strip<ZW>(zs, xs, wk, fI, xr * ZW + min(c0 + mrow, XW - 1), to, acc);
+      layer_strip<ZW>(zs, xs, wk, fI, rm * ZW + (pm - rm * XW), to, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int xcol = c0 + g + 8 * h;
-        if (xcol >= XW) continue;
+        const int p = st * 16 + g + 8 * h;
+        if (p >= NX) continue;
+        const int xr = p / XW, xcol = p - xr * XW;
         const uint32_t o = f2bf(acc[2 * h], acc[2 * h + 1]);
         reinterpret_cast<uint32_t*>(&xd[xr * XW + xcol])[q] = o;
         const int gj = j0 + xr, gi = i0 + xcol;
@@ -321,51 +323,61 @@ struct TcnnTile {
 // the fine pixels of P at a time.  A fine row 2J + a gets coarse row J through
 // tap row a: a in {0, 2} for even rows, a = 1 for odd rows (likewise columns),
 // so a class has a fixed tap list -- 4, 2, 2 or 1 taps, i.e. K = 32, 16, 16 or
-// 8 -- and each 16 class pixels of one class row are a GEMM [16 x K] x [K x 8]
+// 8 -- and each 16 class pixels are a GEMM [16 x K] x [K x 8]
 // whose A rows are coarse pixels gathered by ldmatrix (per-lane addresses; the
 // zero-filled staging covers coarse pixels outside the grid).  fT holds the B
 // fragments in the step order (taps 0, 2 | 6, 8 | 1, 7 | 3, 5 | 4).
 // Epilogue: x_pre = x_down + TCNN rounded once to BF16, z = s * x_pre.
 template <int A, int B, int PH, int PW, int CW>
 __device__ __forceinline__ void tcnn_class_mma(const TcnnTile& t, const uint32_t* fT, int st, int lane) {
-  constexpr int NCM = (PW + 1) / 2, SPC = (NCM + 15) / 16;
+  // the class's pixels in row-major order over an NRM x NCM grid (class rows
+  // and columns, at most); strips of 16 of them, wrapping across class rows
+  constexpr int NRM = (PH + 1) / 2, NCM = (PW + 1) / 2, NP = NRM * NCM;
   const int r0 = (A ^ t.pj0) & 1, c0 = (B ^ t.pi0) & 1;   // first P row / column of the class
-  const int nc_cls = (PW - c0 + 1) >> 1;                    // class columns
-  const int rr = st / SPC, cc0 = (st - rr * SPC) * 16;
-  const int pr = r0 + 2 * rr;
-  if (pr >= PH) return;
-  const int gj = t.pj0 + pr;
+  const int nr_cls = (PH - r0 + 1) >> 1, nc_cls = (PW - c0 + 1) >> 1;
   const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, kh = lane >> 4;
-  const int gi_m = t.pi0 + c0 + 2 * min(cc0 + mrow, nc_cls - 1);
-  const int gi_l = t.pi0 + c0 + 2 * min(cc0 + (lane & 15), nc_cls - 1);
+  // fine pixel of A row m (clamped into the class so that every address is valid)
+  auto fine = [&](int m, int& gj, int& gi) {
+    const int p = min(st * 16 + m, NP - 1);
+    const int rr = p / NCM, cc = p - rr * NCM;
+    gj = t.pj0 + r0 + 2 * min(rr, nr_cls - 1);
+    gi = t.pi0 + c0 + 2 * min(cc, nc_cls - 1);
+  };
   // shared-memory pixel of coarse (J, I) for fine (gj, gi) through tap (ta, tb)
-  auto at = [&](int gi_, int ta, int tb) {
-    return t.cs + (((gj - ta) >> 1) - t.cj0) * CW + (((gi_ - tb) >> 1) - t.ci0);
+  auto at = [&](int gj, int gi, int ta, int tb) {
+    return t.cs + (((gj - ta) >> 1) - t.cj0) * CW + (((gi - tb) >> 1) - t.ci0);
   };
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   uint32_t a[4];
-  if constexpr (A == 0 && B == 0) {
-    // step 0: taps (0,0) | (0,2); step 1: taps (2,0) | (2,2)
-    ldsm_x4(a, at(gi_m, 0, kh ? 2 : 0));
-    mma16816(acc, a, fT[0], fT[1]);
-    ldsm_x4(a, at(gi_m, 2, kh ? 2 : 0));
-    mma16816(acc, a, fT[2], fT[3]);
-  } else if constexpr (A == 0 && B == 1) {
-    ldsm_x4(a, at(gi_m, kh ? 2 : 0, 1));     // taps (0,1) | (2,1)
-    mma16816(acc, a, fT[4], fT[5]);
-  } else if constexpr (A == 1 && B == 0) {
-    ldsm_x4(a, at(gi_m, 1, kh ? 2 : 0));     // taps (1,0) | (1,2)
-    mma16816(acc, a, fT[6], fT[7]);
-  } else {
-    ldsm_x2(a, at(gi_l, 1, 1));              // tap (1,1)
+  int gj, gi;
+  if constexpr (A == 1 && B == 1) {
+    fine(lane & 15, gj, gi);
+    ldsm_x2(a, at(gj, gi, 1, 1));              // tap (1,1)
     mma1688(acc, a[0], a[1], fT[8]);
+  } else {
+    fine(mrow, gj, gi);
+    if constexpr (A == 0 && B == 0) {
+      // step 0: taps (0,0) | (0,2); step 1: taps (2,0) | (2,2)
+      ldsm_x4(a, at(gj, gi, 0, kh ? 2 : 0));
+      mma16816(acc, a, fT[0], fT[1]);
+      ldsm_x4(a, at(gj, gi, 2, kh ? 2 : 0));
+      mma16816(acc, a, fT[2], fT[3]);
+    } else if constexpr (A == 0 && B == 1) {
+      ldsm_x4(a, at(gj, gi, kh ? 2 : 0, 1));   // taps (0,1) | (2,1)
+      mma16816(acc, a, fT[4], fT[5]);
+    } else {
+      ldsm_x4(a, at(gj, gi, 1, kh ? 2 : 0));   // taps (1,0) | (1,2)
+      mma16816(acc, a, fT[6], fT[7]);
+    }
   }
   const int g = lane >> 2, q = lane & 3;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int cc = cc0 + g + 8 * h;
-    const int pc = c0 + 2 * cc, gi = t.pi0 + pc;
-    if (cc >= nc_cls || gj < 0 || gj >= t.n || gi < 0 || gi >= t.n) continue;
+    const int p = st * 16 + g + 8 * h;
+    const int rr = p / NCM, cc = p - rr * NCM;
+    const int pr = r0 + 2 * rr, pc = c0 + 2 * cc;
+    const int ogj = t.pj0 + pr, ogi = t.pi0 + pc;
+    if (p >= NP || rr >= nr_cls || cc >= nc_cls || ogj < 0 || ogj >= t.n || ogi < 0 || ogi >= t.n) continue;
     const int pe = pr * PW + pc;
     const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&t.ps[pe])[q]);
     const uint32_t xo = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
@@ -378,7 +390,7 @@ __device__ __forceinline__ void tcnn_class_mma(const TcnnTile& t, const uint32_t
 // All four classes, strips spread over the warps.
 template <int PH, int PW, int CW>
 __device__ __forceinline__ void tcnn_mma(const TcnnTile& t, const uint32_t* fT) {
-  constexpr int NRM = (PH + 1) / 2, NCM = (PW + 1) / 2, SPC = (NCM + 15) / 16, PER = NRM * SPC;
+  constexpr int NRM = (PH + 1) / 2, NCM = (PW + 1) / 2, PER = (NRM * NCM + 15) / 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int st = warp; st < 4 * PER; st += NW) {
     const int cls = st / PER, sl = st - cls * PER;
@@ -400,7 +412,7 @@ __device__ __forceinline__ void tcnn_mma(const TcnnTile& t, const uint32_t* fT) 
 //   P (layer input x_pre = x_down + TCNN(x_c)): O plus halo 1  (PH x PW)
 //   coarse rows/cols J: floor((j0 - H - 1) / 2) - 1 .. , enough for P
 template <int FH, int FW, bool LAST, bool HAS_P>
-__global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensorMap map_xd,
+__global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUtensorMap map_xd,
                                                 const __grid_constant__ CUtensorMap map_s,
                                                 const __grid_constant__ CUtensorMap map_c,
                                                 const __grid_constant__ SmallWeights sw,
@@ -473,18 +485,19 @@ __global__ void __launch_bounds__(NT) up_kernel(const __grid_constant__ CUtensor
   // layer on O, row-aligned strips as in the down kernel
   const int g = lane >> 2, q = lane & 3;
   {
-    constexpr int SPR = (OW + 15) / 16;
+    constexpr int NO = OH * OW, NSTRIP = (NO + 15) / 16;   // row-major strips, as in the down kernel
     const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
     const TapOffsets<PW> to;
     const uint32_t fI = identity_frag();
-    for (int st = warp; st < OH * SPR; st += NW) {
-      const int orow = st / SPR, c0 = (st - orow * SPR) * 16;
+    for (int st = warp; st < NSTRIP; st += NW) {
+      const int pm = min(st * 16 + mrow, NO - 1), rm = pm / OW;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      layer_strip<PW>(zs, ps, wk, fI, orow * PW + min(c0 + mrow, OW - 1), to, acc);
+      layer_strip<PW>(zs, ps, wk, fI, rm * PW + (pm - rm * OW), to, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int ocol = c0 + g + 8 * h;
-        if (ocol >= OW) continue;
+        const int p = st * 16 + g + 8 * h;
+        if (p >= NO) continue;
+        const int orow = p / OW, ocol = p - orow * OW;
         const uint32_t o = f2bf(acc[2 * h], acc[2 * h + 1]);
         const int gj = j0 - H + orow, gi = i0 - H + ocol;
         if constexpr (LAST) {
