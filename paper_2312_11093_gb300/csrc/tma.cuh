@@ -41,7 +41,11 @@ class TmaMaps {
 };
 
 #ifdef __CUDACC__
-constexpr int kMbarWaitLimit = 1 << 20;   // try_wait rounds before a block gives up
+// A waiting thread is suspended until the phase completes or kMbarSuspendNs
+// pass (it issues nothing meanwhile); a block gives up after kMbarWaitLimit
+// such rounds, about two seconds.
+constexpr int kMbarWaitLimit = 2048;
+constexpr uint32_t kMbarSuspendNs = 1000000;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -60,11 +64,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   asm volatile(
       "{\n"
       " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n"
       "}\n"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(kMbarSuspendNs)
       : "memory");
   return ok != 0;
 }
