@@ -253,7 +253,7 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, doub
   fill_kernel<<<grid_for(B, 128), 128, 0, st>>>(k.rn2.as<double>(), B, 1.0);
   MG_LAUNCH("fill_kernel");
   MG_CUDA(cudaMemsetAsync(k.r32.p, 0, B * N0 * sizeof(float), st));
-  MG_TRY(fused_autotune(k.fl, k.r32.as<float>(), k.rn2.as<double>(), k.scratch.as<double>(), fused_weights(c), st, 3));
+  MG_TRY(fused_autotune(k.fl, k.r32.as<float>(), k.rn2.as<double>(), k.scratch.as<double>(), fused_weights(c), st, 5));
   MG_CUDA(cudaStreamSynchronize(st));
   return {};
 }

@@ -672,25 +672,28 @@ Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, do
   Status result = launch_alpha(fl, norm2, st);
   for (int l = 0; l < fl.L && result.ok(); ++l) {
     float best_d = 1e30f, best_u = 1e30f;
-    for (int v = 0; v < kFusedVariants && result.ok(); ++v) {
-      float t = 0.f;
-      result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st);
-      if (!result.ok()) break;
-      cudaEventRecord(e0, st);
-      for (int k = 0; k < reps && result.ok(); ++k) result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      cudaEventElapsedTime(&t, e0, e1);
-      if (t < best_d) { best_d = t; fl.var_down[l] = v; }
-      result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st);
-      if (!result.ok()) break;
-      cudaEventRecord(e0, st);
-      for (int k = 0; k < reps && result.ok(); ++k) result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      cudaEventElapsedTime(&t, e0, e1);
-      if (t < best_u) { best_u = t; fl.var_up[l] = v; }
-    }
+    // two timed rounds per variant, keeping the faster one: a single short
+    // round is easily disturbed (clock ramp, other work on the GPU)
+    for (int round = 0; round < 2 && result.ok(); ++round)
+      for (int v = 0; v < kFusedVariants && result.ok(); ++v) {
+        float t = 0.f;
+        result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st);
+        if (!result.ok()) break;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps && result.ok(); ++k) result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < best_d) { best_d = t; fl.var_down[l] = v; }
+        result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st);
+        if (!result.ok()) break;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps && result.ok(); ++k) result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < best_u) { best_u = t; fl.var_up[l] = v; }
+      }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -720,7 +723,7 @@ Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, dou
   if (!c->tuned) {
     // first V-cycle after a setup: time the tile variants per level (output to
     // the context's scratch vector, so no caller data changes), keep the fastest
-    MG_TRY(fused_autotune(fl, r32, norm2, c->e.as<double>(), w, c->stream, 3));
+    MG_TRY(fused_autotune(fl, r32, norm2, c->e.as<double>(), w, c->stream, 5));
     for (int l = 0; l < c->L; ++l) {
       c->tile_var[0][l] = fl.var_down[l];
       c->tile_var[1][l] = fl.var_up[l];

@@ -170,7 +170,7 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
       fl.xb[l] = c->x16b[l].as<__nv_bfloat16>();
     }
     MG_TRY(fused_autotune(fl, c->r32.as<float>(), c->scalars.as<double>() + 1, c->e.as<double>(), fused_weights(c),
-                          st, 3));
+                          st, 5));
     for (int l = 0; l < c->L; ++l) {
       c->tile_var[0][l] = fl.var_down[l];
       c->tile_var[1][l] = fl.var_up[l];
