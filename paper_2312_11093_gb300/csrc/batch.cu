@@ -250,10 +250,27 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, doub
     k.fl.xa[l] = k.xa[l].as<bf16>();
     k.fl.xb[l] = k.xb[l].as<bf16>();
   }
+  // tile shapes: reuse the choice made for an earlier class of the same size and
+  // batch (the timing depends only on the shapes), else time the variants
+  for (const auto& tc : c->tuned_classes)
+    if (tc.n == k.n && tc.batch == k.B) {
+      for (int l = 0; l < k.L; ++l) {
+        k.fl.var_down[l] = tc.var[0][l];
+        k.fl.var_up[l] = tc.var[1][l];
+      }
+      MG_CUDA(cudaStreamSynchronize(st));
+      return {};
+    }
   fill_kernel<<<grid_for(B, 128), 128, 0, st>>>(k.rn2.as<double>(), B, 1.0);
   MG_LAUNCH("fill_kernel");
   MG_CUDA(cudaMemsetAsync(k.r32.p, 0, B * N0 * sizeof(float), st));
   MG_TRY(fused_autotune(k.fl, k.r32.as<float>(), k.rn2.as<double>(), k.scratch.as<double>(), fused_weights(c), st, 5));
+  mgcnn_ctx::TunedClass tc{k.n, k.B, {}};
+  for (int l = 0; l < k.L; ++l) {
+    tc.var[0][l] = k.fl.var_down[l];
+    tc.var[1][l] = k.fl.var_up[l];
+  }
+  c->tuned_classes.push_back(tc);
   MG_CUDA(cudaStreamSynchronize(st));
   return {};
 }

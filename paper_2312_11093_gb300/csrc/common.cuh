@@ -116,6 +116,11 @@ struct mgcnn_ctx {
   int fused = 1;                          // use the fused level kernels when they apply
   int tile_var[2][mgcnn::kMaxLevels] = {};  // autotuned tile variants (down, up) per level
   bool tuned = false;                       // set by the first solve after a setup
+  struct TunedClass {                       // tile variants chosen for batched classes, per (n, batch)
+    int n, batch;
+    int var[2][mgcnn::kMaxLevels];
+  };
+  std::vector<TunedClass> tuned_classes;
   mgcnn::DevBuf x16a[mgcnn::kMaxLevels];  // BF16 state ping-pong, [n_l^2][cp]
   mgcnn::DevBuf x16b[mgcnn::kMaxLevels];
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
