@@ -233,6 +233,29 @@ def unpack_blob(blob, C, nd, nu):
     return out
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time: each rank (one GPU) runs its own replica of the
+    workload, and the job is done when the last one is."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, solves_per_rank: int, ms: float) -> float:
+    """Solves per second of the whole job: every rank finished solves_per_rank
+    solves in (at most) ms milliseconds."""
+    return world * solves_per_rank * 1e3 / ms
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank draws its own problems (weak scaling, independent replicas)."""
+    return base + 1000 * rank
+
+
 # --------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -291,7 +314,7 @@ def main():
 
     n, tol = args.n, args.tol
     C, nd, nu, blob, is_gmg = network(net)
-    k_h, f_h, b = make_workload(workload, n, 4 + 1000 * rank)
+    k_h, f_h, b = make_workload(workload, n, rank_seed(4, rank))
     dev = torch.device("cuda", local)
     k_d = torch.from_numpy(k_h).to(dev)
     f_d = torch.from_numpy(f_h).to(dev)
@@ -353,12 +376,9 @@ def main():
     prof = sv.profile_read()
     sv.profile(False)
     profiled_ms_per_step = pv0.elapsed_time(pv1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_per_step = ms / args.steps
-    value = world * 1e3 / ms_per_step
+    value = whole_job_rate(world, 1, ms_per_step)
     relres_mixed = float(hist[-1])
     u_mixed = u_d.clone()
 
@@ -475,7 +495,7 @@ def bench_batched(args, rank, world, local):
     net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg_v10")
     C, nd, nu, blob, is_gmg = network(net)
     families = 1 if is_gmg else 3
-    ns, ks, fs = make_batch_workload(args.batch, 3 + 1000 * rank, families=families)
+    ns, ks, fs = make_batch_workload(args.batch, rank_seed(3, rank), families=families)
     dev = torch.device("cuda", local)
     kd = [torch.from_numpy(k).to(dev) for k in ks]
     fd = [torch.from_numpy(f).to(dev) for f in fs]
@@ -511,10 +531,7 @@ def bench_batched(args, rank, world, local):
         barrier()
         ms = ev0.elapsed_time(ev1) / args.steps
     launches = (mgcnn.kernel_launches() - launches0) // args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     uh = [np.zeros(n * n) for n in ns]
     step(ks, fs, uh)
     barrier()
@@ -526,7 +543,7 @@ def bench_batched(args, rank, world, local):
     unknowns = int(sum(n * n for n in ns))
     done = int((stat == 0).sum())   # problems that reached the tolerance count as solves
     res = {"metric": "solves/s to rel-res 1e-6, batch of uneven sizes (setup + solve)",
-           "value": world * done * 1e3 / ms, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "value": whole_job_rate(world, done, ms), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
            "config": {"workload": f"batched{args.batch}_63-1023" + ("_grf" if is_gmg else ""), "problems": args.batch,

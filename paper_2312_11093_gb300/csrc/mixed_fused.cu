@@ -63,20 +63,6 @@ __device__ __forceinline__ void mma1688(float* d, uint32_t a0, uint32_t a1, uint
                : "r"(a0), "r"(a1), "r"(b0));
 }
 
-__device__ __forceinline__ uint32_t f2tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-  return r;
-}
-// D += A B, m16n8k8, TF32 inputs, FP32 accumulation: a0 = A[g][q], a1 = A[g+8][q],
-// a2 = A[g][q+4], a3 = A[g+8][q+4]; b0 = B[q][g], b1 = B[q+4][g]
-__device__ __forceinline__ void mma1688_tf32(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                             uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 __device__ __forceinline__ float2 bf2f(uint32_t v) { return __bfloat1622float2(*reinterpret_cast<bf162*>(&v)); }
 __device__ __forceinline__ uint32_t f2bf(float a, float b) {
   bf162 r = __floats2bfloat162_rn(a, b);
@@ -249,36 +235,27 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
     return;
   }
   if constexpr (FIRST) {
-    // x_in = W_in * (alpha r) on Z on the tensor cores (TF32, FP32 accumulation):
-    // per strip of 16 Z pixels a GEMM [16 x 9 taps] x [9 x 8 channels] as two
-    // m16n8k8 steps (taps 0-7, then tap 8 and zeros), A read straight from the
-    // FP32 staging; then rounded to BF16 (zero outside the grid), z = s * x_in.
-    constexpr int NZ = ZH * ZW;
-    const int g = lane >> 2, q = lane & 3;
-    auto roff = [](int t) { return (t / 3) * RW + t % 3; };
-    const int o_q = roff(q), o_q4 = roff(q + 4), o_8 = roff(8);
-    const uint32_t b0 = f2tf32(sw.w_in[q * 8 + g]), b1 = f2tf32(sw.w_in[(q + 4) * 8 + g]);
-    const uint32_t b8 = (q == 0) ? f2tf32(sw.w_in[8 * 8 + g]) : 0u;
-    for (int st = warp; st < (NZ + 15) / 16; st += NW) {
-      const int pa = min(st * 16 + g, NZ - 1), pb = min(st * 16 + g + 8, NZ - 1);
-      const int ra = pa / ZW, rb = pb / ZW;
-      const int ba = ra * RW + (pa - ra * ZW), bb = rb * RW + (pb - rb * ZW);   // tap (0,0) in rs
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      mma1688_tf32(acc, f2tf32(rs[ba + o_q]), f2tf32(rs[bb + o_q]), f2tf32(rs[ba + o_q4]), f2tf32(rs[bb + o_q4]),
-                   b0, b1);
-      mma1688_tf32(acc, q == 0 ? f2tf32(rs[ba + o_8]) : 0u, q == 0 ? f2tf32(rs[bb + o_8]) : 0u, 0u, 0u, b8, 0u);
+    // x_in = W_in * (alpha r) on Z, rounded to BF16 (zero outside the grid); z = s * x_in
+    for (int e = threadIdx.x; e < ZH * ZW; e += NT) {
+      const int zr = e / ZW, zc = e - zr * ZW;
+      const int gj = j0 + zr - 1, gi = i0 + zc - 1;
+      uint4 xv = make_uint4(0, 0, 0, 0);
+      if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
+        float rv[9];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int p = st * 16 + g + 8 * h;
-        if (p >= NZ) continue;
-        const int zr = p / ZW, zc = p - zr * ZW;
-        const int gj = j0 + zr - 1, gi = i0 + zc - 1;
-        const bool in = gj >= 0 && gj < n && gi >= 0 && gi < n;
-        const uint32_t xo = in ? f2bf(acc[2 * h], acc[2 * h + 1]) : 0u;
-        reinterpret_cast<uint32_t*>(&xs[p])[q] = xo;
-        const float2 xf = bf2f(xo), sf = bf2f(reinterpret_cast<const uint32_t*>(&zs[p])[q]);
-        reinterpret_cast<uint32_t*>(&zs[p])[q] = f2bf(xf.x * sf.x, xf.y * sf.y);
+        for (int t = 0; t < 9; ++t) rv[t] = rs[(zr + t / 3) * RW + zc + t % 3];
+        float o[8];
+#pragma unroll
+        for (int co = 0; co < 8; ++co) {
+          float a = 0.f;
+#pragma unroll
+          for (int t = 0; t < 9; ++t) a += sw.w_in[t * 8 + co] * rv[t];
+          o[co] = a;
+        }
+        xv = make_uint4(f2bf(o[0], o[1]), f2bf(o[2], o[3]), f2bf(o[4], o[5]), f2bf(o[6], o[7]));
       }
+      xs[e] = xv;
+      zs[e] = mul8(xv, zs[e]);
     }
   } else {
     for (int e = threadIdx.x; e < ZH * ZW; e += NT) zs[e] = mul8(xs[e], zs[e]);
