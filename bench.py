@@ -469,6 +469,31 @@ def main():
         except mgcnn.MGCNNError as err:
             result["gmg"] = {"converged": False, "error": str(err)[:120], "cycle": "V(2,2) weighted Jacobi 0.8, FP64"}
         svg.close()
+    if rank == 0:
+        # the same network as the preconditioner of flexible GMRES(30), same tolerance
+        uk = torch.zeros_like(u_d)
+
+        def kstep():
+            if is_gmg:
+                sv.setup_gmg(k_d, n, 0.8)
+            else:
+                sv.setup(k_d, n)
+            uk.zero_()
+            return sv.solve_krylov(f_d, uk, tol, 300, 30)
+        kstep()
+        ksteps = max(2, min(args.steps, 5))
+        kv0 = torch.cuda.Event(enable_timing=True)
+        kv1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        kv0.record(stream)
+        for _ in range(ksteps):
+            kst, kit, kh = kstep()
+        kv1.record(stream)
+        barrier()
+        kms = kv0.elapsed_time(kv1) / ksteps
+        result["krylov"] = {"value": 1e3 / kms, "unit": "solves/s", "ms_per_step": kms, "iters": kit,
+                            "relres": float(kh[-1]), "converged": bool(kst == mgcnn.OK),
+                            "method": "flexible GMRES(30), the network as right preconditioner, setup + solve"}
     if not args.no_cpu and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_reference(workload, net, n, tol=tol)
     sv.close()

@@ -205,6 +205,26 @@ int mgcnn_vcycle(mgcnn_ctx* ctx, const double* r, double* e);
 int mgcnn_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit,
                 int* iters, double* relres);
 
+/* The solve network as the right preconditioner of flexible GMRES (Sec. 2.2:
+ * the network approximates A^{-1}; besides the stationary iteration of Eq. 1
+ * it can precondition a Krylov method).  Each inner iteration applies one
+ * V-cycle z_j = B v_j in the context's precision (the mixed network differs
+ * slightly from one input to the next, hence the flexible variant, which keeps
+ * the z_j) and one FP64 product A z_j; Arnoldi orthogonalises by classical
+ * Gram-Schmidt applied twice, the least-squares problem uses Givens rotations,
+ * and every `restart` iterations (1..MGCNN_KRYLOV_MAX_RESTART) the iterate is
+ * updated, u += Z y, and the cycle restarts from the true FP64 residual.
+ * Stops when ||r|| / ||f|| <= tol (the recursive estimate inside a cycle, the
+ * true residual at its end) or after maxit inner iterations.  f, u as in
+ * mgcnn_solve; *iters = inner iterations; relres (may be NULL, room for
+ * maxit + 1) receives ||r|| / ||f|| before the first and after every inner
+ * iteration (the true residual at each cycle's end).  Workspace: 2 restart + 3
+ * vectors of n^2 doubles.  Returns OK, NOT_CONVERGED, NONFINITE, STATE, ARG,
+ * NOMEM, CUDA. */
+#define MGCNN_KRYLOV_MAX_RESTART 64
+int mgcnn_solve_krylov(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit, int restart,
+                       int* iters, double* relres);
+
 /* Classical geometric multigrid (Sec. 2.3), the comparator of the learned
  * solver, on the context's operators (mgcnn_setup or mgcnn_setup_gmg must have
  * run): the stationary iteration of Eq. 1 with B one V(nu1, nu2) cycle of

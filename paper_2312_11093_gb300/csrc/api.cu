@@ -277,6 +277,114 @@ Status vcycle_any(mgcnn_ctx* c, const double* r, double* e, const double* u_skip
   return vcycle_mixed(c, r, e, u_skip);
 }
 
+// Flexible GMRES(restart) with the network as right preconditioner: z_j = B v_j
+// (one V-cycle of the context's precision), Arnoldi with classical Gram-Schmidt
+// applied twice, Givens rotations on the host, u += Z y at the end of a cycle and
+// a restart from the true FP64 residual.  df, du: device arrays.  hist gets
+// ||r|| / ||f|| before the first and after every inner iteration (the recursive
+// estimate inside a cycle, the true residual at its end).
+Status krylov_solve(mgcnn_ctx* c, const double* df, double* du, double tol, int maxit, int restart, int* iters,
+                    std::vector<double>& hist) {
+  const size_t N = c->lv[0].N();
+  const int n = c->n, m = restart;
+  cudaStream_t st = c->stream;
+  *iters = 0;
+  hist.clear();
+  MG_TRY(sumsq(c, df, N, 1));
+  double fn2 = 0.0;
+  MG_TRY(read_scalar(c, 1, &fn2));
+  if (!std::isfinite(fn2)) return make_status(MGCNN_ERR_NONFINITE, "right-hand side is not finite");
+  if (fn2 == 0.0) {
+    MG_CUDA(cudaMemsetAsync(du, 0, N * sizeof(double), st));
+    hist.push_back(0.0);
+    return {};
+  }
+  const double fn = std::sqrt(fn2);
+  MG_TRY(ensure(c->kV, (size_t)(m + 1) * N * sizeof(double)));
+  MG_TRY(ensure(c->kZ, (size_t)m * N * sizeof(double)));
+  MG_TRY(ensure(c->kw, N * sizeof(double)));
+  MG_TRY(ensure(c->kr, N * sizeof(double)));
+  MG_TRY(ensure(c->kcoef, (size_t)3 * (m + 1) * sizeof(double)));
+  MG_TRY(ensure(c->kpart, krylov_partial_count(N, m + 1) * sizeof(double)));
+  double* V = c->kV.as<double>();
+  double* Z = c->kZ.as<double>();
+  double* w = c->kw.as<double>();
+  double* r = c->kr.as<double>();
+  double* coef = c->kcoef.as<double>();
+  auto true_residual = [&](double* beta) -> Status {
+    MG_TRY(launch_residual(df, du, c->op[0].as<double>(), r, nullptr, c->partial.as<double>(), n, st));
+    MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), c->scalars.as<double>() + 3, st));
+    double b2 = 0.0;
+    MG_TRY(read_scalar(c, 3, &b2));
+    *beta = std::sqrt(b2);
+    return {};
+  };
+  double beta = 0.0;
+  MG_TRY(true_residual(&beta));
+  hist.push_back(beta / fn);
+  int it = 0;
+  std::vector<double> H, cs, sn, g, y, hc(2 * (size_t)(m + 1));
+  while (hist.back() > tol && it < maxit && std::isfinite(hist.back())) {
+    const int mm = std::min(m, maxit - it);
+    H.assign((size_t)(mm + 1) * mm, 0.0);   // H[i * mm + j]
+    cs.assign(mm, 0.0);
+    sn.assign(mm, 0.0);
+    g.assign(mm + 1, 0.0);
+    g[0] = beta;
+    MG_TRY(launch_scale(r, V, 1.0 / beta, N, st));
+    int k = 0;
+    for (int j = 0; j < mm; ++j) {
+      MG_TRY(vcycle_any(c, V + (size_t)j * N, Z + (size_t)j * N, nullptr));
+      MG_TRY(launch_apply_A(c->op[0].as<double>(), Z + (size_t)j * N, w, n, st));
+      for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+        double* cp = coef + (size_t)pass * (m + 1);
+        MG_TRY(launch_block_dots(V, j + 1, w, N, c->kpart.as<double>(), cp, st));
+        MG_TRY(launch_combine(w, V, j + 1, cp, -1.0, N, st));
+      }
+      MG_TRY(sumsq(c, w, N, 4));
+      MG_CUDA(cudaMemcpyAsync(hc.data(), coef, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      double hn2 = 0.0;
+      MG_TRY(read_scalar(c, 4, &hn2));
+      const double hn = std::sqrt(hn2);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * mm + j] = (0.0 + hc[i]) + hc[(size_t)(m + 1) + i];
+      H[(size_t)(j + 1) * mm + j] = hn;
+      for (int i = 0; i < j; ++i) {   // earlier rotations on column j, then a new one
+        const double a = H[(size_t)i * mm + j], b = H[(size_t)(i + 1) * mm + j];
+        H[(size_t)i * mm + j] = cs[i] * a + sn[i] * b;
+        H[(size_t)(i + 1) * mm + j] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = H[(size_t)j * mm + j], b = H[(size_t)(j + 1) * mm + j];
+      const double d = std::hypot(a, b);
+      cs[j] = a / d;
+      sn[j] = b / d;
+      H[(size_t)j * mm + j] = d;
+      H[(size_t)(j + 1) * mm + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      ++it;
+      const double est = std::fabs(g[j + 1]) / fn;
+      if (est <= tol || it >= maxit || !std::isfinite(est)) break;
+      hist.push_back(est);
+      MG_TRY(launch_scale(w, V + (size_t)(j + 1) * N, 1.0 / hn, N, st));
+    }
+    y.assign(k, 0.0);
+    for (int i = k - 1; i >= 0; --i) {   // back substitution on the rotated H
+      double t = g[i];
+      for (int q = i + 1; q < k; ++q) t -= H[(size_t)i * mm + q] * y[q];
+      y[i] = t / H[(size_t)i * mm + i];
+    }
+    double* cy = coef + 2 * (size_t)(m + 1);
+    MG_CUDA(cudaMemcpyAsync(cy, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
+    MG_TRY(launch_combine(du, Z, k, cy, 1.0, N, st));
+    MG_TRY(true_residual(&beta));
+    hist.push_back(beta / fn);
+  }
+  *iters = it;
+  if (!std::isfinite(hist.back())) return make_status(MGCNN_ERR_NONFINITE, "residual norm is not finite");
+  return {};
+}
+
 Status require_setup(const mgcnn_ctx* c) {
   if (!c->have_setup) return make_status(MGCNN_ERR_STATE, "mgcnn_setup has not been called");
   return {};
@@ -447,6 +555,7 @@ void mgcnn_destroy(mgcnn_ctx* c) {
   }
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   release(c->kerr);
+  for (DevBuf* b : {&c->kV, &c->kZ, &c->kw, &c->kr, &c->kcoef, &c->kpart}) release(*b);
   release(c->alpha32);
   delete c->tma;
   delete c;
@@ -602,6 +711,33 @@ int mgcnn_vcycle(mgcnn_ctx* c, const double* r, double* e) {
     MG_TRY(vcycle_any(c, dr, de, nullptr));
     MG_TRY(stage_out_finish(c, e, de, N, host));
     return sync(c);
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_solve_krylov(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int restart, int* iters,
+                       double* relres) {
+  if (!c || !f || !u || !iters || maxit < 0 || !(tol >= 0.0) || restart < 1 || restart > MGCNN_KRYLOV_MAX_RESTART)
+    return MGCNN_ERR_ARG;
+  *iters = 0;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    const size_t N = c->lv[0].N();
+    const double* df = nullptr;
+    MG_TRY(stage_in(c, f, N, c->f, &df));
+    double* du = nullptr;
+    bool host = false;
+    MG_TRY(stage_out(u, N, c->u, &du, &host));
+    if (host) MG_CUDA(cudaMemcpyAsync(du, u, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    std::vector<double> hist;
+    const Status s = krylov_solve(c, df, du, tol, maxit, restart, iters, hist);
+    if (relres) std::copy(hist.begin(), hist.end(), relres);
+    MG_TRY(stage_out_finish(c, u, du, N, host));
+    MG_TRY(sync(c));
+    if (!s.ok()) return s;
+    if (hist.back() > tol)
+      return make_status(MGCNN_NOT_CONVERGED, "no convergence in %d iterations (relres %.3e)", maxit, hist.back());
+    return {};
   }();
   return finish(c, st);
 }

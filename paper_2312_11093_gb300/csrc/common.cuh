@@ -144,6 +144,9 @@ struct mgcnn_ctx {
   mgcnn::DevBuf gstate, ghist, gparams;
   // classical GMG comparator (gmg.cu): per-level rhs, correction, ping-pong
   mgcnn::DevBuf gmg_r[mgcnn::kMaxLevels], gmg_e[mgcnn::kMaxLevels], gmg_t[mgcnn::kMaxLevels];
+  // flexible GMRES (mgcnn_solve_krylov): basis V, preconditioned directions Z, work vectors,
+  // Gram-Schmidt coefficients and the dots' per-block partial sums
+  mgcnn::DevBuf kV, kZ, kw, kr, kcoef, kpart;
   // batched solves (batch.cu)
   std::vector<mgcnn::BatchClass> bcls;
   int bn = 0, bmaxit = -1;

@@ -1,0 +1,131 @@
+// Vector kernels of the flexible GMRES driver (MGCNN as a Krylov preconditioner):
+// y = A x on the finest grid, the Gram-Schmidt dot products of one vector with
+// a block of basis vectors, and linear combinations with device coefficients.
+// FP64 throughout; every reduction sums in a fixed order (one partial per block,
+// then one block per coefficient), so results repeat bit for bit.
+#include "ops.cuh"
+
+namespace mgcnn {
+
+namespace {
+
+constexpr int KB = 256;            // threads per block
+constexpr int KPIX = 4;            // pixels per thread
+constexpr int KCHUNK = KB * KPIX;  // pixels per block
+
+__device__ __forceinline__ double block_sum_d(double v, double* smem) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();   // smem may still be read by the previous call
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? smem[threadIdx.x] : 0.0;
+  if (warp == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// y = A x, the 5-point operator (planes a_C, a_W, a_E, a_S, a_N of n^2 each).
+__global__ void __launch_bounds__(KB) apply_kernel(const double* __restrict__ op, const double* __restrict__ x,
+                                                   double* __restrict__ y, int n) {
+  const size_t N = (size_t)n * n;
+  const int base = blockIdx.x * KCHUNK + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < KPIX; ++k) {
+    const int p = base + k * KB;
+    if (p >= (int)N) continue;
+    const int j = p / n, i = p - j * n;
+    double v = op[p] * x[p];
+    if (i > 0) v = fma(op[N + p], x[p - 1], v);
+    if (i < n - 1) v = fma(op[2 * N + p], x[p + 1], v);
+    if (j > 0) v = fma(op[3 * N + p], x[p - n], v);
+    if (j < n - 1) v = fma(op[4 * N + p], x[p + n], v);
+    y[p] = v;
+  }
+}
+
+// partial[i * gridDim.x + b] = sum over block b's pixels of V_i[p] w[p], i < nvec.
+__global__ void __launch_bounds__(KB) dots_partial_kernel(const double* __restrict__ V, int nvec,
+                                                          const double* __restrict__ w, size_t N,
+                                                          double* __restrict__ partial) {
+  __shared__ double smem[32];
+  const size_t base = (size_t)blockIdx.x * KCHUNK + threadIdx.x;
+  for (int i = 0; i < nvec; ++i) {
+    const double* v = V + (size_t)i * N;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < KPIX; ++k) {
+      const size_t p = base + (size_t)k * KB;
+      if (p < N) acc = fma(v[p], w[p], acc);
+    }
+    acc = block_sum_d(acc, smem);
+    if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
+  }
+}
+
+// out[i] = sum_b partial[i * nblk + b], one block per i, fixed order.
+__global__ void __launch_bounds__(KB) dots_final_kernel(const double* __restrict__ partial, int nblk,
+                                                        double* __restrict__ out) {
+  __shared__ double smem[32];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += KB) acc += partial[(size_t)blockIdx.x * nblk + b];
+  acc = block_sum_d(acc, smem);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
+// y[p] <- y[p] + sign * sum_i coef[i] V_i[p], the terms added in the order i = 0, 1, ...
+__global__ void __launch_bounds__(KB) combine_kernel(double* __restrict__ y, const double* __restrict__ V, int nvec,
+                                                     const double* __restrict__ coef, double sign, size_t N) {
+  const size_t base = (size_t)blockIdx.x * KCHUNK + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < KPIX; ++k) {
+    const size_t p = base + (size_t)k * KB;
+    if (p >= N) continue;
+    double acc = y[p];
+    for (int i = 0; i < nvec; ++i) acc = fma(sign * coef[i], V[(size_t)i * N + p], acc);
+    y[p] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(KB) scale_kernel(const double* __restrict__ x, double* __restrict__ y, double a,
+                                                   size_t N) {
+  const size_t p = (size_t)blockIdx.x * KB + threadIdx.x;
+  if (p < N) y[p] = a * x[p];
+}
+
+int chunks(size_t N) { return (int)((N + KCHUNK - 1) / KCHUNK); }
+
+}  // namespace
+
+size_t krylov_partial_count(size_t N, int nvec) { return (size_t)chunks(N) * nvec; }
+
+Status launch_apply_A(const double* op, const double* x, double* y, int n, cudaStream_t st) {
+  apply_kernel<<<chunks((size_t)n * n), KB, 0, st>>>(op, x, y, n);
+  MG_LAUNCH("apply_kernel");
+  return {};
+}
+
+Status launch_block_dots(const double* V, int nvec, const double* w, size_t N, double* partial, double* out,
+                         cudaStream_t st) {
+  const int nb = chunks(N);
+  dots_partial_kernel<<<nb, KB, 0, st>>>(V, nvec, w, N, partial);
+  MG_LAUNCH("dots_partial_kernel");
+  dots_final_kernel<<<nvec, KB, 0, st>>>(partial, nb, out);
+  MG_LAUNCH("dots_final_kernel");
+  return {};
+}
+
+Status launch_combine(double* y, const double* V, int nvec, const double* coef, double sign, size_t N,
+                      cudaStream_t st) {
+  combine_kernel<<<chunks(N), KB, 0, st>>>(y, V, nvec, coef, sign, N);
+  MG_LAUNCH("combine_kernel");
+  return {};
+}
+
+Status launch_scale(const double* x, double* y, double a, size_t N, cudaStream_t st) {
+  scale_kernel<<<grid_for(N, KB), KB, 0, st>>>(x, y, a, N);
+  MG_LAUNCH("scale_kernel");
+  return {};
+}
+
+}  // namespace mgcnn

@@ -45,6 +45,16 @@ Status launch_gmg_setup(const double* op, double* out, int n, double omega, cuda
 Status launch_gmg_v10_setup_bf16(const double* op, __nv_bfloat16* out, int n, double omega, cudaStream_t st,
                                  bool input_diag_level, int batch = 1);
 Status launch_axpy_to(const double* u, const double* e, double* out, size_t N, cudaStream_t st);
+// krylov.cu: vector kernels of the flexible GMRES driver (FP64, fixed-order sums)
+size_t krylov_partial_count(size_t N, int nvec);   // doubles of the dots scratch
+Status launch_apply_A(const double* op, const double* x, double* y, int n, cudaStream_t st);
+// out[i] = <V_i, w>, i < nvec (V: nvec vectors of N back to back)
+Status launch_block_dots(const double* V, int nvec, const double* w, size_t N, double* partial, double* out,
+                         cudaStream_t st);
+// y += sign * sum_i coef[i] V_i (coef on the device)
+Status launch_combine(double* y, const double* V, int nvec, const double* coef, double sign, size_t N,
+                      cudaStream_t st);
+Status launch_scale(const double* x, double* y, double a, size_t N, cudaStream_t st);
 
 // ---- net_generic.cu: FP64 / FP32 direct convolution kernels ----------------
 template <typename T>

@@ -73,6 +73,7 @@ def load() -> ctypes.CDLL:
                                     POINTER(c_int), c_void_p]),
         "mgcnn_setup_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
         "mgcnn_setup_batched_gmg": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double]),
+        "mgcnn_solve_krylov": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_void_p]),
         "mgcnn_solve_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
                                         c_void_p]),
         "mgcnn_kernel_launches": (ctypes.c_longlong, []),
@@ -392,6 +393,17 @@ class Solver:
         e = np.empty(N) if e is None else e
         self._check(self._L.mgcnn_vcycle(self._h, _ptr(r, N), _ptr(e, N, True)), "mgcnn_vcycle")
         return e
+
+    def solve_krylov(self, f, u, tol: float, maxit: int, restart: int = 30):
+        """Flexible GMRES with the network as preconditioner, in place on u.
+        Returns (status, iters, relres[0..iters])."""
+        N = self.n * self.n
+        it = c_int(0)
+        hist = np.zeros(maxit + 1)
+        st = self._L.mgcnn_solve_krylov(self._h, _ptr(f, N), _ptr(u, N, True), float(tol), int(maxit), int(restart),
+                                        ctypes.byref(it), hist.ctypes.data)
+        self._check(st, "mgcnn_solve_krylov", ok=(OK, NOT_CONVERGED))
+        return st, it.value, hist[: it.value + 1]
 
     def solve(self, f, u, tol: float, maxit: int, relres=None, raise_on_limit: bool = False):
         """Stationary iteration in place on u.  Returns (status, iters, relres[0..iters])."""

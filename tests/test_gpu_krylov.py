@@ -1,0 +1,90 @@
+"""Flexible GMRES with the solve network as preconditioner (mgcnn_solve_krylov)
+against the oracle's FGMRES with the oracle's network."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import krylov as okr
+from oracle import mgcnn as omg
+from oracle import operator as oop
+from oracle.grid import num_levels
+from paper_2312_11093_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2312_11093_gb300 import build
+    build.build()
+    from paper_2312_11093_gb300 import mgcnn
+    mgcnn.load()
+    return mgcnn
+
+
+def _grf(n, seed, corr=0.1):
+    rng = np.random.default_rng(seed)
+    return inputs.lognormal_k(n, corr, rng), inputs.normal_rhs(n, rng)
+
+
+def test_fp64_fgmres_matches_oracle(M):
+    """FP64 network, restarts every 8 iterations: the oracle's iteration count and
+    residual history (rounding-order differences only), and the same iterate."""
+    n, b = 63, (1.0, 0.5)
+    k, f = _grf(n, 51)
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    w = omg.gmg_v10_weights()
+    s = omg.gmg_v10_setup(sts, 0.8, input_diag=True)
+    dinv = 1.0 / sts[0].aC
+    u_o, it_o, h_o = okr.fgmres(lambda x: oop.apply(sts[0], x), lambda v: omg.solve_phase(w, s, v, d_inv=dinv),
+                                f, None, 1e-10, 200, 8)
+    sv = M.Solver(8, 1, 1, precision="fp64", b=b)
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_gmg(k.ravel().copy(), n, 0.8)
+    u = np.zeros(n * n)
+    st, it, h = sv.solve_krylov(f.ravel().copy(), u, 1e-10, 200, restart=8)
+    assert st == M.OK and it == it_o
+    h_o = np.array(h_o)
+    early = h_o > 1e-7
+    np.testing.assert_allclose(h[early], h_o[early], rtol=1e-7)
+    assert np.linalg.norm(u - u_o.ravel()) / np.linalg.norm(u_o) <= 1e-9
+
+
+@pytest.mark.parametrize("n", [255, 1023])
+def test_mixed_fgmres_reaches_1e8_and_beats_stationary(M, n):
+    rng = np.random.default_rng(60 + n)
+    t = rng.uniform(0.0, 2.0 * np.pi)
+    k = inputs.lognormal_k(n, 0.05, rng)
+    f = inputs.normal_rhs(n, rng)
+    b = (10.0 * np.cos(t), 10.0 * np.sin(t))
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16", b=b)
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_gmg(k.ravel().copy(), n, 0.8)
+    u = np.zeros(n * n)
+    st, it, h = sv.solve_krylov(f.ravel().copy(), u, 1e-8, 300, restart=30)
+    assert st == M.OK
+    st_ = oop.stencil_div(k, b)
+    rtrue = f - oop.apply(st_, u.reshape(n, n))
+    assert np.linalg.norm(rtrue) / np.linalg.norm(f) <= 1.05e-8
+    u2 = np.zeros(n * n)
+    st2, it2, _ = sv.solve(f.ravel().copy(), u2, 1e-8, 300)
+    assert st2 == M.OK and it < it2
+
+
+def test_krylov_arguments_and_limits(M):
+    n = 15
+    k, f = _grf(n, 52)
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_gmg(k.ravel().copy(), n, 0.8)
+    u = np.zeros(n * n)
+    for restart in (0, 65):
+        with pytest.raises(M.MGCNNError) as ei:
+            sv.solve_krylov(f.ravel().copy(), u, 1e-8, 10, restart=restart)
+        assert ei.value.status == M.ERR_ARG
+    st, it, h = sv.solve_krylov(f.ravel().copy(), u, 1e-30, 3, restart=2)
+    assert st == M.NOT_CONVERGED and it == 3 and len(h) == 4
+    st, it, h = sv.solve_krylov(np.zeros(n * n), u, 1e-8, 10)
+    assert st == M.OK and it == 0 and not u.any()
