@@ -27,8 +27,8 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray], precond: Callable[[np.nd
 
     maxit counts preconditioner applications (inner iterations) over all restarts.
     Returns (u, iters, history) with history[k] = the residual-norm ratio after k
-    inner iterations (history[0] = ||f - A u0|| / ||f||); at every restart the
-    history entry is the TRUE residual of the restarted iterate."""
+    inner iterations (history[0] = ||f - A u0|| / ||f||): the recursive estimate
+    inside a cycle, the TRUE residual after a cycle's last iteration."""
     u = np.zeros_like(f) if u0 is None else u0.astype(np.float64).copy()
     fn = np.linalg.norm(f)
     if fn == 0.0:
@@ -70,8 +70,8 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray], precond: Callable[[np.nd
             k = j + 1
             it += 1
             est = abs(g[j + 1]) / fn
-            if est <= tol or it >= maxit or not np.isfinite(est):
-                break
+            if est <= tol or it >= maxit or not np.isfinite(est) or j == m - 1:
+                break                                # the cycle's last entry is the true residual
             hist.append(est)
             V.append(w / hn)
         y = np.zeros(k)

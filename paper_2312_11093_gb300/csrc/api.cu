@@ -364,7 +364,7 @@ Status krylov_solve(mgcnn_ctx* c, const double* df, double* du, double tol, int 
       k = j + 1;
       ++it;
       const double est = std::fabs(g[j + 1]) / fn;
-      if (est <= tol || it >= maxit || !std::isfinite(est)) break;
+      if (est <= tol || it >= maxit || !std::isfinite(est) || j == mm - 1) break;   // then the true residual
       hist.push_back(est);
       MG_TRY(launch_scale(w, V + (size_t)(j + 1) * N, 1.0 / hn, N, st));
     }

@@ -58,7 +58,7 @@ def test_v10_network_preconditioner_reaches_direct_solve_with_restarts():
     ustar = np.linalg.solve(op.dense_matrix(sts[0]), f.ravel()).reshape(n, n)
     for restart in (30, 4):
         u, it, hist = krylov.fgmres(apply_A, B, f, None, 1e-11, 200, restart)
-        assert hist[-1] <= 1e-11
+        assert hist[-1] <= 1e-11 and len(hist) == it + 1   # one entry per inner iteration
         assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) <= 1e-8
         true = np.linalg.norm(f - apply_A(u)) / np.linalg.norm(f)
         assert abs(true - hist[-1]) <= 1e-3 * hist[-1] + 1e-15
