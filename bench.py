@@ -271,6 +271,7 @@ def main():
     ap.add_argument("--maxit", type=int, default=100, help="cycle limit of the batched solves")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--krylov", action="store_true", help="also time flexible GMRES with the network as preconditioner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg_v10")
@@ -469,7 +470,7 @@ def main():
         except mgcnn.MGCNNError as err:
             result["gmg"] = {"converged": False, "error": str(err)[:120], "cycle": "V(2,2) weighted Jacobi 0.8, FP64"}
         svg.close()
-    if rank == 0:
+    if args.krylov and rank == 0:
         # the same network as the preconditioner of flexible GMRES(30), same tolerance
         uk = torch.zeros_like(u_d)
 
