@@ -66,14 +66,12 @@ struct Level {
 
 class TmaMaps;   // tma.cuh
 
-// FP32 weights of the fused kernels' small layers (8 channels), passed to the
-// kernels by value: they sit in the kernel-parameter constant bank and the
-// unrolled loops read them as constant operands, with no shared-memory loads.
-// Layouts: w_in[t][co], w_out[t][ci], w_P[tap][ci][co] (t, tap = 3 a + b).
+// FP32 weights of the fused down kernel's input layer W_in (8 channels), passed
+// by value: they sit in the kernel-parameter constant bank and the unrolled
+// loop reads them as constant operands, with no shared-memory loads.
+// Layout w_in[t][co] (t = 3 a + b).
 struct SmallWeights {
   float w_in[72];
-  float w_out[72];
-  float w_P[576];
 };
 
 // FP32 weights of the fused setup kernel's small layers, by value like
@@ -127,7 +125,7 @@ struct mgcnn_ctx {
   mgcnn::TmaMaps* tma = nullptr;          // tensor maps of the fused kernels' TMA tile loads
   mgcnn::DevBuf kerr;                     // device flag: a kernel gave up waiting for its tile copies
   mgcnn::DevBuf alpha32;                  // input scale of the fused V-cycle (alpha, 1 / alpha)
-  mgcnn::SmallWeights small_w{};          // host copy of the fused kernels' small layers
+  mgcnn::SmallWeights small_w{};          // host copy of the fused down kernel's W_in
   mgcnn::SetupSmallWeights setup_small_w{};  // host copy of the fused setup kernel's small layers
   mgcnn::DevBuf s32tmp;                   // FP32 setup output before the BF16 cast
   mgcnn::DevBuf scalars;                  // device scalars (norms)

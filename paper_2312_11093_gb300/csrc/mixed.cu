@@ -535,16 +535,11 @@ Status mixed_set_weights(mgcnn_ctx* c) {
     pack_frags(whi.data(), 8, 8, reinterpret_cast<uint32_t*>(blob.data() + ml.out_hi));
     pack_frags(wlo.data(), 8, 8, reinterpret_cast<uint32_t*>(blob.data() + ml.out_lo));
     pack_tcnn_frags(w.data() + c->wl.w_P, C, reinterpret_cast<uint32_t*>(blob.data() + ml.tcnn));
-    // small layers of the fused kernels, zero beyond C channels
+    // W_in of the fused down kernel, zero beyond C channels
     SmallWeights& sw = c->small_w;
     sw = SmallWeights{};
     for (int t = 0; t < 9; ++t)
-      for (int ch = 0; ch < C; ++ch) {
-        sw.w_in[t * 8 + ch] = (float)w[c->wl.w_in + ch * 9 + t];
-        sw.w_out[t * 8 + ch] = (float)w[c->wl.w_out + ch * 9 + t];
-        for (int co = 0; co < C; ++co)
-          sw.w_P[(t * 8 + ch) * 8 + co] = (float)w[c->wl.w_P + ((size_t)ch * C + co) * 9 + t];
-      }
+      for (int ch = 0; ch < C; ++ch) sw.w_in[t * 8 + ch] = (float)w[c->wl.w_in + ch * 9 + t];
   }
   if (C == 8) {
     // fused setup network: 4 tanh layers and the setup RCNN as fragments; b_i, W_cin, b_cin in FP32

@@ -3,24 +3,25 @@
 // configuration of the paper's experiments (Sec. 4.1: sweeps = 1, C = 8).
 //
 // Down kernel, level l (Algorithm 3, down loop):
-//   [finest level: x_1 = alpha W_in * r, FP32 CUDA cores]
-//   x_l <- x_l + K_down (s_l * x_l)            tensor cores (implicit GEMM)
+//   [finest level: x_1 = alpha W_in * r, FP32 FMAs, weights as constants]
+//   x_l <- x_l + K_down (s_l * x_l)            tensor cores (implicit GEMM, skip folded in)
 //   x_{l+1} = RCNN(x_l)                        tensor cores, stride 2
-// One block owns a 16 x 32 fine tile and the 8 x 16 coarse tile under it.
-// The restriction needs one extra fine row and column, which the block
-// recomputes (17 x 33 layer outputs) instead of reading a neighbour's.
+// One block owns an FH x FW fine tile (16 x 32, 8 x 32 or 16 x 16, autotuned)
+// and the coarse tile under it.  The restriction needs one extra fine row and
+// column, which the block recomputes instead of reading a neighbour's.
 //
 // Up kernel, level l (Algorithm 3, up loop):
-//   x_l <- x_l + TCNN(x_{l+1})                 FP32 CUDA cores (2.25 taps per pixel)
-//   x_l <- x_l + K_up (s_l * x_l)              tensor cores
-//   [finest level: e = W_out * x_1 / alpha, u <- u + e in FP64]
-// One block owns a 16 x 32 fine tile, with a 1-pixel halo of the layer input
+//   x_l <- x_l + TCNN(x_{l+1})                 tensor cores, per pixel-parity class
+//   x_l <- x_l + K_up (s_l * x_l)              tensor cores (skip folded in)
+//   [finest level: e = W_out * x_1 / alpha     tensor cores, BF16 hi + lo weights
+//    u <- u + e                                FP64, full warps]
+// One block owns an FH x FW fine tile, with a 1-pixel halo of the layer input
 // (2 at the finest level, where W_out needs the layer output's halo).
 //
-// Tensor-core tiling: a warp computes 16 output pixels x 8 channels with
-// mma.m16n8k16 (+ one m16n8k8 for the ninth tap), A rows fetched by ldmatrix
-// from per-lane shared-memory addresses, so a strip can be any 16 pixels of
-// an odd-sized region.
+// Tiles arrive by TMA (tma.cuh; zero fill outside the grid).  Tensor-core
+// tiling: a warp computes 16 output pixels x 8 channels with mma.m16n8k16 (+
+// m16n8k8), A rows fetched by ldmatrix from per-lane shared-memory addresses,
+// so a strip can be any 16 pixels of an odd-sized region.
 #include <cmath>
 
 #include "fpconv.cuh"
@@ -419,7 +420,6 @@ template <int FH, int FW, bool LAST, bool HAS_P>
 __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUtensorMap map_xd,
                                                 const __grid_constant__ CUtensorMap map_s,
                                                 const __grid_constant__ CUtensorMap map_c,
-                                                const __grid_constant__ SmallWeights sw,
                                                 const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
                                                 const uint32_t* __restrict__ fOutHi,
                                                 const uint32_t* __restrict__ fOutLo,
@@ -610,13 +610,13 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
   else
     mc = ms;   // not read on the coarsest level
   if (last && has_p)
-    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, nullptr, e, nl, active, fl.err);
+    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, nullptr, e, nl, active, fl.err);
   else if (last)
-    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, nullptr, e, nl, active, fl.err);
+    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, nullptr, e, nl, active, fl.err);
   else if (has_p)
-    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, fl.xb[l], e, nl, active, fl.err);
+    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, fl.xb[l], e, nl, active, fl.err);
   else
-    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.small, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, fl.xb[l], e, nl, active, fl.err);
+    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, fl.xb[l], e, nl, active, fl.err);
   MG_LAUNCH("up_kernel");
   return {};
 }
