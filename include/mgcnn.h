@@ -321,6 +321,13 @@ int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
  * the device-side loop of MGCNN_OPT_DEVICE_LOOP), so that every bracketed
  * kernel is a plain launch on the context's stream. */
 long long mgcnn_kernel_launches(void);
+/* Check of the failure path of the fused kernels' tile waits (no counterpart in
+ * the paper): one block waits on a tile copy that is never issued, gives up
+ * after eight suspended waits of at most 1 ms, and sets the context's device
+ * error flag; the call then returns MGCNN_ERR_TIMEOUT, as a solve whose copies
+ * never arrived would, and the context stays usable (the flag is cleared).
+ * Nothing faults or hangs. */
+int mgcnn_check_wait_timeout(mgcnn_ctx* ctx);
 int mgcnn_profile(mgcnn_ctx* ctx, int enable);
 int mgcnn_profile_read(mgcnn_ctx* ctx, double* ms, long long* counts, int nkinds);
 

@@ -883,6 +883,15 @@ int mgcnn_setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, con
   return finish(c, setup_batched(c, nprob, coeff, n));
 }
 
+int mgcnn_check_wait_timeout(mgcnn_ctx* c) {
+  if (!c) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    MG_TRY(launch_wait_check(c->kerr.as<int>(), 8, c->stream));
+    return sync(c);   // turns the device flag into ERR_TIMEOUT and clears it
+  }();
+  return finish(c, st);
+}
+
 int mgcnn_setup_batched_gmg(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* n, double omega) {
   if (!c || !coeff || !n) return MGCNN_ERR_ARG;
   if (!(omega > 0.0 && omega < 2.0)) return finish(c, make_status(MGCNN_ERR_ARG, "omega must be in (0, 2)"));

@@ -44,3 +44,35 @@ const CUtensorMap* TmaMaps::pix8(const void* base, int n, int batch, int bw, int
 }
 
 }  // namespace mgcnn
+
+namespace mgcnn {
+
+namespace {
+
+// Check of the bounded-wait path of the TMA tile loads: thread 0 arms an
+// mbarrier for 16 bytes that no copy will ever deliver, every thread waits
+// with at most `rounds` suspended tries (kMbarSuspendNs each), and a block that
+// gives up records the error flag, exactly as the level kernels do.
+__global__ void wait_check_kernel(int* err, int rounds) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16u);
+  }
+  __syncthreads();
+  bool landed = false;
+  for (int i = 0; i < rounds && !landed; ++i) landed = mbar_try_wait(&bar, 0);
+  if (!__syncthreads_and(landed) && threadIdx.x == 0) atomicExch(err, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(&bar)) : "memory");
+}
+
+}  // namespace
+
+Status launch_wait_check(int* err, int rounds, cudaStream_t st) {
+  wait_check_kernel<<<1, 64, 0, st>>>(err, rounds);
+  MG_LAUNCH("wait_check_kernel");
+  return {};
+}
+
+}  // namespace mgcnn

@@ -24,6 +24,10 @@
 
 namespace mgcnn {
 
+// Launches one block whose tile wait can never complete (no copy is issued):
+// its bounded wait gives up after `rounds` suspended tries and sets *err.
+Status launch_wait_check(int* err, int rounds, cudaStream_t st);
+
 // Host: encoder and a small cache of tensor maps (base pointer, grid, batch, box).
 class TmaMaps {
  public:

@@ -73,6 +73,7 @@ def load() -> ctypes.CDLL:
                                     POINTER(c_int), c_void_p]),
         "mgcnn_setup_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
         "mgcnn_setup_batched_gmg": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double]),
+        "mgcnn_check_wait_timeout": (c_int, [c_void_p]),
         "mgcnn_solve_krylov": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_void_p]),
         "mgcnn_solve_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
                                         c_void_p]),

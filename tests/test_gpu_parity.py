@@ -417,3 +417,18 @@ def test_v10_fused_mixed_reaches_1e8_in_fp64(M, n):
         rtrue = f - oop.apply(sts[0], u.reshape(n, n))
         assert np.linalg.norm(rtrue) / np.linalg.norm(f) <= 1.05e-8
     assert its["mixed_bf16"] <= its["fp64"] + 3
+
+
+def test_tile_wait_timeout_is_reported_and_context_survives(M):
+    """The fused kernels wait for their TMA tiles with a bounded wait.  A block
+    waiting on a copy that is never issued gives up, flags the error, and the call
+    returns ERR_TIMEOUT; the context then solves normally (the flag was cleared)."""
+    n = 31
+    k, f = problem(n, 70)
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_gmg(k.ravel().copy(), n, 0.8)
+    assert sv._L.mgcnn_check_wait_timeout(sv._h) == M.ERR_TIMEOUT
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(f.ravel().copy(), u, 1e-8, 200)
+    assert st == M.OK and hist[-1] <= 1e-8
