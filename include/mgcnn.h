@@ -305,8 +305,16 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * conditional WHILE node (residual, norm, convergence test and V-cycle on the
  * device, no host round trip per cycle; the graph is captured once per setup,
  * f and u are copied through the context's buffers); 0 runs the host loop
- * (one 8-byte readback per cycle).  Both give identical iterates. */
-enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2 };
+ * (one 8-byte readback per cycle).  Both give identical iterates.
+ * MGCNN_OPT_TILE (default -1): tile shape of the fused kernels.  -1: the first
+ * solve after a setup on a new grid size times every shape on every level and
+ * keeps the fastest; 0..4: that shape on every level, no timing (0 = 16 x 32,
+ * 1 = 8 x 32, 2 = 16 x 16, 3 = 32 x 32, 4 = 24 x 32 fine pixels per block,
+ * rows x columns); other values:
+ * ERR_ARG.  Every shape gives bit-identical results: a pixel's arithmetic does
+ * not depend on the tile that holds it.  Applies to mgcnn_solve and
+ * mgcnn_solve_krylov; the batched solves keep their own timing. */
+enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3 };
 int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).

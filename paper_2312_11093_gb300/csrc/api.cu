@@ -399,7 +399,7 @@ Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
   if (L > Lmax) return make_status(MGCNN_ERR_SIZE, "%d levels requested, n=%d allows %d", L, n, Lmax);
   c->have_setup = false;
   c->sgraph_valid = false;           // buffers may move: recapture the device loop
-  if (c->n != n) c->tuned = false;   // tile shapes are tuned per grid size
+  if (c->n != n) c->tuned = c->tile_fixed >= 0;   // tile shapes are tuned per grid size
   c->n = n;
   c->L = L;
   c->lv.assign(L, Level{});
@@ -979,6 +979,18 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
       return finish(c, {});
     case MGCNN_OPT_DEVICE_LOOP:
       c->device_loop = value ? 1 : 0;
+      return finish(c, {});
+    case MGCNN_OPT_TILE:
+      if (value < -1 || value >= kFusedVariants)
+        return finish(c, make_status(MGCNN_ERR_ARG, "tile shape %d not in -1..%d", value, kFusedVariants - 1));
+      c->tile_fixed = value;
+      c->sgraph_valid = false;   // the captured loop holds the old shapes
+      if (value >= 0) {
+        for (int l = 0; l < kMaxLevels; ++l) c->tile_var[0][l] = c->tile_var[1][l] = value;
+        c->tuned = true;
+      } else {
+        c->tuned = false;
+      }
       return finish(c, {});
     default:
       return finish(c, make_status(MGCNN_ERR_ARG, "unknown option %d", option));

@@ -114,6 +114,7 @@ struct mgcnn_ctx {
   int fused = 1;                          // use the fused level kernels when they apply
   int tile_var[2][mgcnn::kMaxLevels] = {};  // autotuned tile variants (down, up) per level
   bool tuned = false;                       // set by the first solve after a setup
+  int tile_fixed = -1;                      // MGCNN_OPT_TILE: a fixed tile variant, or -1 (autotune)
   struct TunedClass {                       // tile variants chosen for batched classes, per (n, batch)
     int n, batch;
     int var[2][mgcnn::kMaxLevels];

@@ -20,7 +20,7 @@ Status mixed_get_setup_level(mgcnn_ctx* c, int l, double* dst);
 Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega);
 void mixed_release(mgcnn_ctx* c);
 // mixed_fused.cu: fused level kernels (8 channels, one layer per ResNet)
-constexpr int kFusedVariants = 3;        // tile shapes 16x32, 8x32, 16x16
+constexpr int kFusedVariants = 5;        // tile shapes 16x32, 8x32, 16x16, 32x32, 24x32
 class TmaMaps;
 struct FusedLevels {
   int L = 0, batch = 1;

@@ -6,7 +6,7 @@
 //   [finest level: x_1 = alpha W_in * r, FP32 FMAs, weights as constants]
 //   x_l <- x_l + K_down (s_l * x_l)            tensor cores (implicit GEMM, skip folded in)
 //   x_{l+1} = RCNN(x_l)                        tensor cores, stride 2
-// One block owns an FH x FW fine tile (16 x 32, 8 x 32 or 16 x 16, autotuned)
+// One block owns an FH x FW fine tile (16 x 32, 8 x 32, 16 x 16, 32 x 32 or 24 x 32, autotuned)
 // and the coarse tile under it.  The restriction needs one extra fine row and
 // column, which the block recomputes instead of reading a neighbour's.
 //
@@ -22,6 +22,7 @@
 // tiling: a warp computes 16 output pixels x 8 channels with mma.m16n8k16 (+
 // m16n8k8), A rows fetched by ldmatrix from per-lane shared-memory addresses,
 // so a strip can be any 16 pixels of an odd-sized region.
+#include <algorithm>
 #include <cmath>
 
 #include "fpconv.cuh"
@@ -78,6 +79,24 @@ __device__ __forceinline__ uint4 mul8(uint4 a, uint4 b) {
   x = bf2f(a.w); y = bf2f(b.w); o.w = f2bf(x.x * y.x, x.y * y.y);
   return o;
 }
+
+// The tiles of a block live in dynamic shared memory (the 32 x 32 variant needs
+// more than the 48 KB of static shared memory); every array starts on a 128-byte
+// boundary (TMA destinations).
+constexpr int pad8(int pixels) { return (pixels + 7) / 8 * 8; }   // uint4 count -> multiple of 128 bytes
+template <int FH, int FW, bool FIRST, bool HAS_R>
+constexpr size_t down_smem_bytes() {
+  constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0), ZH = XH + 2, ZW = XW + 2;
+  constexpr int RH = ZH + 2, RW = ZW + 2;
+  return 16u * (2 * pad8(ZH * ZW) + pad8(XH * XW)) + (FIRST ? 4u * RH * RW : 0u);
+}
+template <int FH, int FW, bool LAST, bool HAS_P>
+constexpr size_t up_smem_bytes() {
+  constexpr int H = LAST ? 1 : 0, OH = FH + 2 * H, OW = FW + 2 * H, PH = OH + 2, PW = OW + 2;
+  constexpr int CH = PH / 2 + 2, CW = PW / 2 + 2;
+  return 16u * (2 * pad8(PH * PW) + (HAS_P ? pad8(CH * CW) : 0) + (LAST ? OH * OW : 0));
+}
+extern __shared__ __align__(128) unsigned char fused_dsm[];
 
 // Per-lane tap offsets of a shared-memory tile with row pitch PITCH (in
 // pixels): this lane's four taps 2s + kh (kh = lane / 16) of the x4 loads and
@@ -181,16 +200,17 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
                                                   const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fR,
                                                   bf16* __restrict__ xdown, bf16* __restrict__ xc, int n,
                                                   const int* __restrict__ active, int* __restrict__ err) {
+  static_assert(FH % 2 == 0 && FW % 2 == 0 && (FH / 2) * (FW / 2) % 16 == 0, "tile shape");
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
   constexpr int ZH = XH + 2, ZW = XW + 2;
   constexpr int RH = ZH + 2, RW = ZW + 2;
   // zs: s, then z = s * x_in in place (BF16); xs: x_in, for the skip.  Both are
   // TMA destinations: the box of rows j0-1.. and columns i0-1.. of the tensor,
   // zero outside the grid.
-  __shared__ __align__(128) uint4 zs[ZH * ZW];
-  __shared__ __align__(128) uint4 xs[ZH * ZW];
-  __shared__ __align__(16) uint4 xd[XH * XW];   // layer output
-  __shared__ float rs[FIRST ? RH * RW : 1];
+  uint4* zs = reinterpret_cast<uint4*>(fused_dsm);
+  uint4* xs = zs + pad8(ZH * ZW);
+  uint4* xd = xs + pad8(ZH * ZW);                                   // layer output
+  float* rs = reinterpret_cast<float*>(xd + pad8(XH * XW));         // finest level only
   __shared__ __align__(8) uint64_t bar;
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -432,10 +452,10 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   constexpr int CH = PH / 2 + 2, CW = PW / 2 + 2;   // coarse rows / cols staged
   // TMA destinations (zero outside the grid): ps = x_down on P, then x_pre;
   // zs = s on P, then s * x_pre; cs = the coarse pixels under P
-  __shared__ __align__(128) uint4 ps[PH * PW];
-  __shared__ __align__(128) uint4 zs[PH * PW];
-  __shared__ __align__(128) uint4 cs[HAS_P ? CH * CW : 1];
-  __shared__ __align__(16) uint4 os[LAST ? OH * OW : 1];
+  uint4* ps = reinterpret_cast<uint4*>(fused_dsm);
+  uint4* zs = ps + pad8(PH * PW);
+  uint4* cs = zs + pad8(PH * PW);                                    // coarser level only
+  uint4* os = cs + (HAS_P ? pad8(CH * CW) : 0);                      // finest level only
   __shared__ __align__(8) uint64_t bar;
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int pj0 = j0 - H - 1, pi0 = i0 - H - 1;      // global coords of P's corner
@@ -527,7 +547,7 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
     __syncthreads();
     const float inv_alpha = alpha2[2 * bz + 1];
     float* ev = reinterpret_cast<float*>(ps);   // FH x FW corrections
-    static_assert(FH * FW * sizeof(float) <= sizeof(ps), "correction staging");
+    static_assert(FH * FW * sizeof(float) <= PH * PW * sizeof(uint4), "correction staging");
     constexpr int SPRO = (FW + 15) / 16;
     const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
     const TapOffsets<OW> to;
@@ -559,6 +579,20 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   }
 }
 
+// Dynamic shared memory of a kernel instantiation: above 48 KB the kernel must be
+// allowed it once (cudaFuncSetAttribute); the instantiations already allowed are
+// remembered.  Returns the byte count for the launch.
+template <typename K>
+size_t dyn_smem(K* kernel, size_t bytes) {
+  static std::vector<const void*> allowed;
+  const void* key = reinterpret_cast<const void*>(kernel);
+  if (bytes > 48 * 1024 && std::find(allowed.begin(), allowed.end(), key) == allowed.end()) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+      allowed.push_back(key);
+  }
+  return bytes;
+}
+
 // Tensor map of a level tensor for a box of bw x bh pixels (copied out of the
 // cache at once: a later lookup may move the cache's storage).
 Status pix8_map(const FusedLevels& fl, const void* base, int n, int bw, int bh, CUtensorMap* out) {
@@ -568,7 +602,9 @@ Status pix8_map(const FusedLevels& fl, const void* base, int n, int bw, int bh, 
   return {};
 }
 
-// Tile variants (FH x FW): 0 = 16 x 32, 1 = 8 x 32, 2 = 16 x 16.
+// Tile variants (FH x FW): 0 = 16 x 32, 1 = 8 x 32, 2 = 16 x 16, 3 = 32 x 32,
+// 4 = 24 x 32.  FH must be even and (FH / 2) x (FW / 2) a multiple of 16 (the
+// restriction's strips of 16 coarse pixels).
 template <int FH, int FW>
 Status launch_down(int l, const FusedLevels& fl, const float* r32, const double* norm2, const FusedWeights& w,
                    const int* active, cudaStream_t st) {
@@ -583,14 +619,18 @@ Status launch_down(int l, const FusedLevels& fl, const float* r32, const double*
     mx = ms;   // not read on the finest level
   else
     MG_TRY(pix8_map(fl, fl.xb[l], nl, ZW, ZH, &mx));
+  auto run = [&](auto* kernel, size_t smem) {
+    kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc,
+                                                      nl, active, fl.err);
+  };
   if (first && has_r)
-    down_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+    run(down_kernel<FH, FW, true, true>, down_smem_bytes<FH, FW, true, true>());
   else if (first)
-    down_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+    run(down_kernel<FH, FW, true, false>, down_smem_bytes<FH, FW, true, false>());
   else if (has_r)
-    down_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+    run(down_kernel<FH, FW, false, true>, down_smem_bytes<FH, FW, false, true>());
   else
-    down_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
+    run(down_kernel<FH, FW, false, false>, down_smem_bytes<FH, FW, false, false>());
   MG_LAUNCH("down_kernel");
   return {};
 }
@@ -609,14 +649,18 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
     MG_TRY(pix8_map(fl, fl.xb[l + 1], fl.n[l + 1], PW / 2 + 2, PH / 2 + 2, &mc));
   else
     mc = ms;   // not read on the coarsest level
+  auto run = [&](auto* kernel, size_t smem, bf16* xfin) {
+    kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha,
+                                                      u_skip, xfin, e, nl, active, fl.err);
+  };
   if (last && has_p)
-    up_kernel<FH, FW, true, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, nullptr, e, nl, active, fl.err);
+    run(up_kernel<FH, FW, true, true>, up_smem_bytes<FH, FW, true, true>(), nullptr);
   else if (last)
-    up_kernel<FH, FW, true, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, nullptr, e, nl, active, fl.err);
+    run(up_kernel<FH, FW, true, false>, up_smem_bytes<FH, FW, true, false>(), nullptr);
   else if (has_p)
-    up_kernel<FH, FW, false, true><<<grid, NT, 0, st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, fl.xb[l], e, nl, active, fl.err);
+    run(up_kernel<FH, FW, false, true>, up_smem_bytes<FH, FW, false, true>(), fl.xb[l]);
   else
-    up_kernel<FH, FW, false, false><<<grid, NT, 0, st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha, u_skip, fl.xb[l], e, nl, active, fl.err);
+    run(up_kernel<FH, FW, false, false>, up_smem_bytes<FH, FW, false, false>(), fl.xb[l]);
   MG_LAUNCH("up_kernel");
   return {};
 }
@@ -626,6 +670,8 @@ Status launch_down_variant(int v, int l, const FusedLevels& fl, const float* r32
   switch (v) {
     case 1: return launch_down<8, 32>(l, fl, r32, norm2, w, active, st);
     case 2: return launch_down<16, 16>(l, fl, r32, norm2, w, active, st);
+    case 3: return launch_down<32, 32>(l, fl, r32, norm2, w, active, st);
+    case 4: return launch_down<24, 32>(l, fl, r32, norm2, w, active, st);
     default: return launch_down<16, 32>(l, fl, r32, norm2, w, active, st);
   }
 }
@@ -635,6 +681,8 @@ Status launch_up_variant(int v, int l, const FusedLevels& fl, const double* norm
   switch (v) {
     case 1: return launch_up<8, 32>(l, fl, norm2, e, u_skip, w, active, st);
     case 2: return launch_up<16, 16>(l, fl, norm2, e, u_skip, w, active, st);
+    case 3: return launch_up<32, 32>(l, fl, norm2, e, u_skip, w, active, st);
+    case 4: return launch_up<24, 32>(l, fl, norm2, e, u_skip, w, active, st);
     default: return launch_up<16, 32>(l, fl, norm2, e, u_skip, w, active, st);
   }
 }

@@ -347,6 +347,7 @@ class Solver:
     PROFILE_KINDS = ("residual", "resnet", "restrict", "prolong", "in", "out", "down0", "up0")
     OPT_FUSED = 1
     OPT_DEVICE_LOOP = 2
+    OPT_TILE = 3
 
     def set_option(self, option: int, value: int):
         self._check(self._L.mgcnn_set_option(self._h, int(option), int(value)), "mgcnn_set_option")

@@ -432,3 +432,39 @@ def test_tile_wait_timeout_is_reported_and_context_survives(M):
     u = np.zeros(n * n)
     st, it, hist = sv.solve(f.ravel().copy(), u, 1e-8, 200)
     assert st == M.OK and hist[-1] <= 1e-8
+
+
+@pytest.mark.parametrize("n", [63, 255, 1023])
+@pytest.mark.parametrize("net", ["gmg_v10", "random"])
+def test_every_tile_shape_gives_identical_iterates(M, n, net):
+    """Each tile shape of the fused kernels (16 x 32, 8 x 32, 16 x 16, 32 x 32,
+    24 x 32, forced by MGCNN_OPT_TILE) and the autotuned choice give bit-identical
+    iterates and histories: a pixel's arithmetic does not depend on the tile that
+    holds it.  n = 2^m - 1 leaves a ragged last tile on every level."""
+    from paper_2312_11093_gb300.train import init_weights
+    k, f = problem(n, 80 + n, "blocks")
+    w = M.gmg_v10_weights() if net == "gmg_v10" else init_weights(8, 1, 1, np.random.default_rng(9), out_scale=0.05)
+    out = {}
+    for tile in (-1, 0, 1, 2, 3, 4):
+        sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+        sv.set_option(sv.OPT_TILE, tile)
+        sv.set_weights(w)
+        if net == "gmg_v10":
+            sv.setup_gmg(k.ravel().copy(), n, 0.8)
+        else:
+            sv.setup(k.ravel().copy(), n)
+        u = np.zeros(n * n)
+        st, it, hist = sv.solve(f.ravel().copy(), u, 1e-30, 4)
+        assert it == 4
+        out[tile] = (hist.copy(), u)
+    for tile in (0, 1, 2, 3, 4):
+        assert np.array_equal(out[tile][0], out[-1][0]), tile
+        assert np.array_equal(out[tile][1], out[-1][1]), tile
+
+
+def test_tile_option_range(M):
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    for bad in (-2, 5):
+        with pytest.raises(M.MGCNNError) as ei:
+            sv.set_option(sv.OPT_TILE, bad)
+        assert ei.value.status == M.ERR_ARG
