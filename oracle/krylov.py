@@ -1,6 +1,8 @@
-"""MGCNN as a preconditioner of flexible GMRES (the use of the network inside a
+"""MGCNN as a preconditioner of Krylov methods (the use of the network inside a
 Krylov method, Sec. 2.2: the network approximates A^{-1}, and beyond the
-stationary iteration of Eq. 1 it can precondition an outer Krylov solver).
+stationary iteration of Eq. 1 it can precondition an outer Krylov solver; for
+a symmetric problem and the symmetric network, Remark "Symmetric problem"
+names MINRES).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -83,5 +85,95 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray], precond: Callable[[np.nd
         beta = np.linalg.norm(r)
         hist.append(beta / fn)
         if not np.isfinite(beta):
+            break
+    return u, it, hist
+
+
+def pcg(apply_A: Callable[[np.ndarray], np.ndarray], precond: Callable[[np.ndarray], np.ndarray],
+        f: np.ndarray, u0: np.ndarray | None, tol: float, maxit: int):
+    """Preconditioned conjugate gradients for SPD A and SPD preconditioner M
+    (textbook form: z = M r, p = z + beta p, alpha = (r, z) / (p, A p),
+    beta = (r_new, z_new) / (r, z)).  Stops when ||r_k|| / ||f|| <= tol on the
+    recursively updated residual, or after maxit iterations (one preconditioner
+    application each).  Returns (u, iters, history) with history[k] =
+    ||r_k|| / ||f|| (history[0] from the true residual f - A u0)."""
+    u = np.zeros_like(f) if u0 is None else u0.astype(np.float64).copy()
+    fn = np.linalg.norm(f)
+    if fn == 0.0:
+        return np.zeros_like(f), 0, [0.0]
+    r = f - apply_A(u)
+    hist = [np.linalg.norm(r) / fn]
+    it = 0
+    p = None
+    rz = 0.0
+    while hist[-1] > tol and it < maxit and np.isfinite(hist[-1]):
+        z = precond(r)
+        rz_new = np.vdot(r, z)
+        p = z if p is None else z + (rz_new / rz) * p
+        rz = rz_new
+        q = apply_A(p)
+        alpha = rz / np.vdot(p, q)
+        u = u + alpha * p
+        r = r - alpha * q
+        it += 1
+        hist.append(np.linalg.norm(r) / fn)
+    return u, it, hist
+
+
+def minres(apply_A: Callable[[np.ndarray], np.ndarray], precond: Callable[[np.ndarray], np.ndarray],
+           f: np.ndarray, u0: np.ndarray | None, tol: float, maxit: int):
+    """Preconditioned MINRES for symmetric A and SPD preconditioner M.
+
+    Lanczos on (M A) in the M^{-1} inner product, with the three-term vectors
+    kept in both forms (r_k unpreconditioned, y_k = M r_k, beta_k = sqrt((r_k, y_k))),
+    the tridiagonal least-squares problem solved by Givens rotations as columns
+    arrive, and the iterate updated through the search directions
+    w_k = (v_k - eps_k w_{k-2} - delta_k w_{k-1}) / gamma_k.  Iterate k minimises
+    ||f - A u||_M over u0 + K_k(M A, M r0) (M-norm: sqrt(r^T M r)).  Stops when
+    that norm, relative to its value at u0, is <= tol, or after maxit iterations.
+    Returns (u, iters, history) with history[k] = ||r_k||_M / ||r_0||_M from the
+    recursion (history[0] = 1)."""
+    u = np.zeros_like(f) if u0 is None else u0.astype(np.float64).copy()
+    r = f - apply_A(u)
+    y = precond(r)
+    beta1 = np.sqrt(np.vdot(r, y))
+    if beta1 == 0.0:
+        return u, 0, [0.0]
+    hist = [1.0]
+    # Lanczos state: r_prev = r_{k-1}, r_cur = r_k (unpreconditioned), y = M r_k
+    r_prev, r_cur = np.zeros_like(f), r
+    beta_prev, beta = 0.0, beta1
+    # rotation state
+    cs, sn = -1.0, 0.0
+    dbar, eps = 0.0, 0.0
+    phibar = beta1
+    w_prev2, w_prev = np.zeros_like(f), np.zeros_like(f)
+    it = 0
+    while it < maxit:
+        v = y / beta                                   # Lanczos vector (M-orthonormal basis of K)
+        t = apply_A(v)
+        if it > 0:
+            t = t - (beta / beta_prev) * r_prev
+        alpha = np.vdot(v, t)
+        t = t - (alpha / beta) * r_cur
+        r_prev, r_cur = r_cur, t
+        y = precond(r_cur)
+        beta_prev, beta = beta, np.sqrt(np.vdot(r_cur, y))
+        # previous rotation on the new column (eps, delta from the last two rotations)
+        eps_old = eps
+        delta = cs * dbar + sn * alpha
+        gbar = sn * dbar - cs * alpha
+        eps = sn * beta
+        dbar = -cs * beta
+        gamma = np.hypot(gbar, beta)
+        cs, sn = gbar / gamma, beta / gamma
+        phi = cs * phibar
+        phibar = sn * phibar
+        w = (v - eps_old * w_prev2 - delta * w_prev) / gamma
+        w_prev2, w_prev = w_prev, w
+        u = u + phi * w
+        it += 1
+        hist.append(abs(phibar) / beta1)
+        if hist[-1] <= tol or not np.isfinite(hist[-1]) or beta == 0.0:
             break
     return u, it, hist

@@ -145,6 +145,104 @@ def solve_phase(weights: dict, s: list[np.ndarray], r: np.ndarray, keep: dict | 
     return e
 
 
+# --------------------------------------------------------------------------
+# Symmetric variant (Remark "Symmetric problem", Sec. 3.3): the network is made
+# a symmetric operator by sharing weights between ResNetDown and ResNetUp and
+# between RCNN and TCNN.  Reading: "sharing" means each up map is the adjoint of
+# the matching down map, so that B = W_out M_1 W_in with M_l = U_l (I + P M_{l+1} R) D_l
+# has U_l = D_l^T, P = R^T and W_out = W_in^T:
+#   down layer   x <- x + K (s * x)            (Eq. heteroresnet, unchanged)
+#   up layer     x <- x + s * (K^T x)          (its adjoint: the conv with K's
+#                                               channels swapped and taps flipped,
+#                                               the setup tensor applied after it)
+#   TCNN         the transposed conv with the RCNN weights (exactly R^T)
+#   reChannel-out the adjoint of reChannel-in
+# The up layers run in the reverse order of the down layers.  Then
+#   M_L = D_L^T D_L,   M_l = D_l^T (I + R^T M_{l+1} R) D_l,
+# so every M_l is symmetric positive semidefinite and B = W_in^T M_1 W_in is
+# symmetric positive definite whenever the down layers are nonsingular and W_in
+# is injective -- for any weights and setup tensors -- which is what CG and
+# MINRES need from a preconditioner.  No input normalisation (D^{-1} r would
+# break the symmetry).
+# --------------------------------------------------------------------------
+def adjoint_kernel(W: np.ndarray) -> np.ndarray:
+    """Weights of the adjoint of a same-size conv: W'[ci, co, a, b] = W[co, ci, 2-a, 2-b]."""
+    return np.ascontiguousarray(W.transpose(1, 0, 2, 3)[:, :, ::-1, ::-1])
+
+
+def symmetric_weights(weights: dict) -> dict:
+    """The weight set of the symmetric variant as a plain weight dict: the up,
+    TCNN and reChannel-out weights replaced by the tied ones (w_up[i] = the
+    adjoint kernel of w_down[nu - 1 - i], w_P = w_R, w_out = the adjoint of
+    w_in).  Setup weights are kept."""
+    nu = weights["w_down"].shape[0]
+    w = dict(weights)
+    w["w_up"] = np.stack([adjoint_kernel(weights["w_down"][nu - 1 - i]) for i in range(nu)])
+    w["w_P"] = weights["w_R"].copy()
+    w["w_out"] = adjoint_kernel(weights["w_in"])
+    return w
+
+
+def solve_phase_symmetric(weights: dict, s: list[np.ndarray], r: np.ndarray) -> np.ndarray:
+    """e = B r of the symmetric variant (tied weights taken from `weights`' down,
+    RCNN and reChannel-in entries; its up, TCNN and out entries are ignored)."""
+    L = len(s)
+    sizes = [t.shape[1] for t in s]
+    Kd = weights["w_down"]
+    nu = Kd.shape[0]
+    x = [None] * L
+    x[0] = cn.conv_same(r[None], weights["w_in"])
+    for l in range(L):
+        for i in range(nu):
+            x[l] = x[l] + cn.conv_same(s[l] * x[l], Kd[i])
+        if l < L - 1:
+            x[l + 1] = cn.rcnn(x[l], weights["w_R"])
+    for l in reversed(range(L)):
+        for i in reversed(range(nu)):
+            x[l] = x[l] + s[l] * cn.conv_same_adjoint(x[l], Kd[i])
+        if l > 0:
+            x[l - 1] = x[l - 1] + cn.tcnn(x[l], weights["w_R"], sizes[l - 1])
+    return cn.conv_same_adjoint(x[0], weights["w_in"])[0]
+
+
+# Additive multilevel (BPX) preconditioner as a symmetric network.  With
+# channel 0 a carrier of the (restricted) residual and channel 1 its scaled copy,
+#   x_0 = eps r (reChannel-in),  down layer: x[1] += s[0] * x[0],  RCNN: x[0] <- FW x[0],
+# the state after level l's down layer holds eps R_l r and sqrt(omega 4^l / a_C,l) R_l r
+# (R_l = FW applied l times, R_0 = I) when s_l[0] = sqrt(omega 4^l / a_C,l) / eps.
+# The tied up sweep adds the adjoints, so
+#   B = sum_l 4^l R_l^T (omega D_l^{-1}) R_l  +  eps^2 sum_l R_l^T R_l,
+# the BPX form sum_l P_l D_l^{-1} P_l^T with P_l = 4^l R_l^T (bilinear
+# prolongation) and Jacobi-scaled levels (D_l: diagonal of the rediscretised
+# level-l operator), plus a term of relative size eps^2 h^2 that eps = 2^-26
+# makes negligible.  Channels 2.. stay zero.
+BPX_EPS = 2.0 ** -26
+
+
+def bpx_weights(C: int = 4, nu: int = 1) -> dict:
+    """Weights of the BPX network (C >= 2 channels, nu down layers of which the
+    first carries the smoother copy); setup weights zero."""
+    z = lambda *shape: np.zeros(shape)
+    w = {"w_in": z(C, 1, 3, 3), "w_down": z(nu, C, C, 3, 3), "w_up": z(nu, C, C, 3, 3),
+         "w_R": z(C, C, 3, 3), "w_P": z(C, C, 3, 3), "w_out": z(1, C, 3, 3),
+         "sw_in": z(C, FEATURES, 3, 3), "sb_in": z(C), "sw": z(SETUP_LAYERS, C, C, 3, 3),
+         "sb": z(SETUP_LAYERS, C), "sw_R": z(C, C, 3, 3)}
+    w["w_in"][0, 0, 1, 1] = BPX_EPS
+    w["w_down"][0, 1, 0, 1, 1] = 1.0
+    w["w_R"][0, 0] = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 16.0
+    return symmetric_weights(w)
+
+
+def bpx_setup(stencils: list[Stencil], omega: float = 1.0, C: int = 4) -> list[np.ndarray]:
+    """Setup tensors of the BPX network: s_l[0] = sqrt(omega 4^l / a_C,l) / eps, others 0."""
+    out = []
+    for lev, st in enumerate(stencils):
+        s = np.zeros((C, st.n, st.n))
+        s[0] = np.sqrt(omega * 4.0 ** lev / st.aC) / BPX_EPS
+        out.append(s)
+    return out
+
+
 def stationary_solve(weights: dict, s: list[np.ndarray], A: Stencil, f: np.ndarray,
                      u0: np.ndarray | None, tol: float, maxit: int, input_diag: bool = False):
     """Eq. 1 with B = solve_phase: u^{k+1} = u^k + B (f - A u^k)
