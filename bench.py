@@ -274,6 +274,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--krylov", action="store_true", help="also time flexible GMRES with the network as preconditioner")
+    ap.add_argument("--bpx", action="store_true",
+                    help="also time CG with the symmetric network in its BPX form (same k field, b = 0, FP64, tol 1e-8)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg_v10")
@@ -500,6 +502,34 @@ def main():
         result["krylov"] = {"value": 1e3 / kms, "unit": "solves/s", "ms_per_step": kms, "iters": kit,
                             "relres": float(kh[-1]), "converged": bool(kst == mgcnn.OK),
                             "method": "flexible GMRES(30), the network as right preconditioner, setup + solve"}
+    if args.bpx and rank == 0:
+        # the symmetric variant: CG preconditioned by the BPX network on the symmetric
+        # problem of the same coefficient field (b = 0), the paper's FP64 tolerance
+        svb = mgcnn.Solver(4, 1, 1, precision="fp64", input_diag=False, b=(0.0, 0.0), stream=stream)
+        svb.set_option(svb.OPT_SYMMETRIC, 1)
+        svb.set_weights(mgcnn.bpx_weights(4))
+        ub = torch.zeros_like(u_d)
+
+        def bstep():
+            svb.setup_bpx(k_d, n, 1.0)
+            ub.zero_()
+            return svb.solve_pcg(f_d, ub, 1e-8, 300)
+        bstep()
+        bsteps = max(2, min(args.steps, 3))
+        bv0 = torch.cuda.Event(enable_timing=True)
+        bv1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        bv0.record(stream)
+        for _ in range(bsteps):
+            bst, bit, bh = bstep()
+        bv1.record(stream)
+        barrier()
+        bms = bv0.elapsed_time(bv1) / bsteps
+        result["bpx_pcg"] = {"value": 1e3 / bms, "unit": "solves/s", "ms_per_step": bms, "iters": bit,
+                             "relres": float(bh[-1]), "tol": 1e-8, "converged": bool(bst == mgcnn.OK),
+                             "method": "CG, symmetric network as BPX preconditioner (C = 4, FP64), b = 0, "
+                                       "setup + solve"}
+        svb.close()
     if not args.no_cpu and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_reference(workload, net, n, tol=tol)
     sv.close()

@@ -225,6 +225,57 @@ int mgcnn_solve(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxi
 int mgcnn_solve_krylov(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit, int restart,
                        int* iters, double* relres);
 
+/* Symmetric variant (Remark "Symmetric problem", Sec. 3.3: a symmetric solver
+ * for a symmetric problem, with MINRES as the outer method).  Turned on by
+ * mgcnn_set_option(ctx, MGCNN_OPT_SYMMETRIC, 1), which needs precision FP64,
+ * input_diag 0 and down_layers == up_layers (else ERR_ARG).  The network then
+ * shares weights between ResNetDown and ResNetUp and between RCNN and TCNN in
+ * the adjoint sense: each up map is the transpose of its down map, so
+ *   up layer i (of nu):  x <- x + s_l * (K_i^T x),  K_i^T the same-size conv
+ *                        with w_down[nu-1-i]'s channels swapped and taps flipped
+ *                        (the setup tensor applied after the conv),
+ *   TCNN = the transposed conv with w_R (exactly RCNN^T),
+ *   reChannel-out = the adjoint of reChannel-in,
+ * and B = W_in^T M_1 W_in with M_l = D_l^T (I + R^T M_{l+1} R) D_l, D_l the
+ * level's down layers: B is symmetric positive semidefinite for any weights and
+ * setup tensors (definite when the down layers are nonsingular and W_in is
+ * injective).  mgcnn_set_weights then overwrites the blob's w_up, w_P and w_out
+ * with the tied values (mgcnn_get_weights returns them); turning the option on
+ * with weights already loaded ties them at once.  Training (mgcnn_train_step,
+ * mgcnn_loss_grad) is not available in this mode (ERR_STATE).
+ *
+ * mgcnn_setup_bpx: operators as mgcnn_setup, and setup tensors that make the
+ * symmetric network the additive multilevel (BPX) preconditioner
+ *   B = sum_l 4^l R_l^T (omega D_l^{-1}) R_l  +  eps^2 sum_l R_l^T R_l,
+ * R_l = full weighting applied l times, D_l = diagonal of the level-l operator,
+ * eps = MGCNN_BPX_EPS: s_l[0] = sqrt(omega 4^l / a_C,l) / eps, other channels 0.
+ * It expects the BPX weights: w_in[0][0][1][1] = eps, w_down[0][1][0][1][1] = 1,
+ * w_R[0][0] = (1/16)[1 2 1; 2 4 2; 1 2 1], everything else 0 (the tied entries
+ * follow).  Needs the symmetric mode (ERR_STATE) and omega in (0, 2] (ERR_ARG).
+ *
+ * mgcnn_solve_pcg: preconditioned conjugate gradients, z = B r, with the
+ * residual updated recursively; stops when ||r_k||_2 / ||f||_2 <= tol or after
+ * maxit iterations (one V-cycle each).  relres (may be NULL, room for maxit+1)
+ * receives ||r_k|| / ||f|| for k = 0..*iters (k = 0: the true residual of the
+ * initial guess).
+ * mgcnn_solve_minres: preconditioned MINRES (Lanczos on B A in the B^{-1} inner
+ * product, Givens rotations on the tridiagonal least-squares problem); iterate
+ * k minimises ||f - A u||_B over the Krylov space; stops when that norm
+ * relative to its value at the initial guess is <= tol (relres receives these
+ * ratios, 1 at k = 0) or after maxit iterations.
+ * Both need the symmetric mode (ERR_STATE) and a symmetric A: pde
+ * DIV_HARMONIC with b = 0 (ERR_ARG otherwise).  f, u, *iters as in
+ * mgcnn_solve; f = 0 gives u = 0, *iters = 0.  Workspace: 4 (PCG) or 7
+ * (MINRES) vectors of n^2 doubles.  A preconditioner that is not positive
+ * definite ends MINRES with NONFINITE (the square root of a negative inner
+ * product) and may end PCG with NONFINITE.  Returns OK, NOT_CONVERGED,
+ * NONFINITE, STATE, ARG, NOMEM, CUDA. */
+#define MGCNN_BPX_EPS 0x1p-26
+int mgcnn_setup_bpx(mgcnn_ctx* ctx, const double* coeff, int n, double omega);
+int mgcnn_solve_pcg(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit, int* iters, double* relres);
+int mgcnn_solve_minres(mgcnn_ctx* ctx, const double* f, double* u, double tol, int maxit, int* iters,
+                       double* relres);
+
 /* Classical geometric multigrid (Sec. 2.3), the comparator of the learned
  * solver, on the context's operators (mgcnn_setup or mgcnn_setup_gmg must have
  * run): the stationary iteration of Eq. 1 with B one V(nu1, nu2) cycle of
@@ -313,8 +364,10 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * rows x columns); other values:
  * ERR_ARG.  Every shape gives bit-identical results: a pixel's arithmetic does
  * not depend on the tile that holds it.  Applies to mgcnn_solve and
- * mgcnn_solve_krylov; the batched solves keep their own timing. */
-enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3 };
+ * mgcnn_solve_krylov; the batched solves keep their own timing.
+ * MGCNN_OPT_SYMMETRIC (default 0): the symmetric network variant, see
+ * mgcnn_setup_bpx; 1 on, 0 off (weights stay as they are). */
+enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3, MGCNN_OPT_SYMMETRIC = 4 };
 int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).

@@ -257,7 +257,12 @@ Status vcycle_fp64(mgcnn_ctx* c, const double* r, double* e, const double* u_ski
   for (int l = c->L - 1; l >= 0; --l) {
     for (int i = 0; i < wl.nu_u; ++i) {
       ConvArgs<double> a;
-      a.x = x[l]; a.s = c->s64[l].as<double>(); a.W = W + wl.w_up + i * CC9;
+      a.x = x[l]; a.W = W + wl.w_up + i * CC9;
+      // symmetric variant: the adjoint layer x + s * (K^T x) (w_up holds K^T)
+      if (c->symmetric)
+        a.s_out = c->s64[l].as<double>();
+      else
+        a.s = c->s64[l].as<double>();
       a.skip = x[l]; a.y = t[l]; a.n = c->lv[l].n;
       MG_TRY(conv_same<double>(C, C, a, c->stream));
       std::swap(x[l], t[l]);
@@ -379,6 +384,203 @@ Status krylov_solve(mgcnn_ctx* c, const double* df, double* du, double tol, int 
     MG_TRY(launch_combine(du, Z, k, cy, 1.0, N, st));
     MG_TRY(true_residual(&beta));
     hist.push_back(beta / fn);
+  }
+  *iters = it;
+  if (!std::isfinite(hist.back())) return make_status(MGCNN_ERR_NONFINITE, "residual norm is not finite");
+  return {};
+}
+
+// ---- symmetric variant (Remark "Symmetric problem", Sec. 3.3) ---------------
+// Tied weights: w_up[i] = the adjoint kernel of w_down[nu-1-i] (channels
+// swapped, taps flipped: tap t = 3a + b -> 8 - t), w_P = w_R (the transposed
+// conv with the RCNN weights is RCNN^T), w_out = the adjoint of w_in.
+void tie_weights(const WeightLayout& wl, double* w) {
+  const int C = wl.C, nu = wl.nu_d;
+  const size_t CC9 = (size_t)C * C * 9;
+  for (int i = 0; i < nu; ++i) {
+    const double* kd = w + wl.w_down + (size_t)(nu - 1 - i) * CC9;
+    double* ku = w + wl.w_up + (size_t)i * CC9;
+    for (int co = 0; co < C; ++co)
+      for (int ci = 0; ci < C; ++ci)
+        for (int t = 0; t < 9; ++t) ku[((size_t)co * C + ci) * 9 + t] = kd[((size_t)ci * C + co) * 9 + (8 - t)];
+  }
+  std::copy(w + wl.w_R, w + wl.w_R + CC9, w + wl.w_P);
+  for (int ch = 0; ch < C; ++ch)
+    for (int t = 0; t < 9; ++t) w[wl.w_out + (size_t)ch * 9 + t] = w[wl.w_in + (size_t)ch * 9 + (8 - t)];
+}
+
+// Copy a weight blob (host or device memory) into the context, tied first in
+// the symmetric mode.
+Status load_weights(mgcnn_ctx* c, const double* w) {
+  const size_t count = c->wl.total;
+  MG_TRY(ensure(c->w64, count * sizeof(double)));
+  MG_TRY(ensure(c->w32, count * sizeof(float)));
+  std::vector<double> tied;
+  if (c->symmetric) {
+    tied.resize(count);
+    MG_CUDA(cudaMemcpy(tied.data(), w, count * sizeof(double), cudaMemcpyDefault));
+    tie_weights(c->wl, tied.data());
+    w = tied.data();
+  }
+  MG_CUDA(cudaMemcpyAsync(c->w64.p, w, count * sizeof(double), cudaMemcpyDefault, c->stream));
+  MG_TRY(convert<float>(c->w64.as<double>(), c->w32.as<float>(), count, c->stream));
+  MG_TRY(mixed_set_weights(c));
+  return sync(c);   // before `tied` goes away
+}
+
+Status require_symmetric_problem(const mgcnn_ctx* c) {
+  if (!c->symmetric) return make_status(MGCNN_ERR_STATE, "CG and MINRES need the symmetric network (MGCNN_OPT_SYMMETRIC)");
+  if (c->cfg.pde != MGCNN_PDE_DIV_HARMONIC || c->cfg.bx != 0.0 || c->cfg.by != 0.0)
+    return make_status(MGCNN_ERR_ARG, "CG and MINRES need a symmetric A: the divergence form with b = 0");
+  return {};
+}
+
+// <x, y> in FP64 with the fixed-order block reduction, read back to the host.
+Status dot_host(mgcnn_ctx* c, const double* x, const double* y, size_t N, double* out) {
+  double* d = c->kcoef.as<double>();
+  MG_TRY(launch_block_dots(x, 1, y, N, c->kpart.as<double>(), d, c->stream));
+  MG_CUDA(cudaMemcpyAsync(c->h_scalars + 7, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MG_TRY(sync(c));
+  *out = c->h_scalars[7];
+  return {};
+}
+
+// Shared start of the two drivers: ||f||, the f = 0 case, workspace of `nvec`
+// vectors, r = f - A u in vector 0.  Returns fn = 0 when the solve is done.
+Status sym_start(mgcnn_ctx* c, const double* df, double* du, int nvec, double* fn, double* rn) {
+  const size_t N = c->lv[0].N();
+  MG_TRY(sumsq(c, df, N, 1));
+  double fn2 = 0.0;
+  MG_TRY(read_scalar(c, 1, &fn2));
+  if (!std::isfinite(fn2)) return make_status(MGCNN_ERR_NONFINITE, "right-hand side is not finite");
+  *fn = std::sqrt(fn2);
+  if (fn2 == 0.0) {
+    MG_CUDA(cudaMemsetAsync(du, 0, N * sizeof(double), c->stream));
+    return {};
+  }
+  MG_TRY(ensure(c->kV, (size_t)nvec * N * sizeof(double)));
+  MG_TRY(ensure(c->kcoef, 8 * sizeof(double)));
+  MG_TRY(ensure(c->kpart, krylov_partial_count(N, 1) * sizeof(double)));
+  double* r = c->kV.as<double>();
+  MG_TRY(launch_residual(df, du, c->op[0].as<double>(), r, nullptr, c->partial.as<double>(), c->n, c->stream));
+  MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), c->scalars.as<double>() + 3, c->stream));
+  double r2 = 0.0;
+  MG_TRY(read_scalar(c, 3, &r2));
+  *rn = std::sqrt(r2);
+  return {};
+}
+
+// Preconditioned CG: z = B r, p = z + beta p, alpha = (r, z) / (p, A p),
+// beta = (r_new, z_new) / (r, z), r updated recursively.  hist[k] = ||r_k|| / ||f||.
+Status pcg_solve(mgcnn_ctx* c, const double* df, double* du, double tol, int maxit, int* iters,
+                 std::vector<double>& hist) {
+  const size_t N = c->lv[0].N();
+  cudaStream_t st = c->stream;
+  *iters = 0;
+  hist.clear();
+  double fn = 0.0, rn = 0.0;
+  MG_TRY(sym_start(c, df, du, 4, &fn, &rn));
+  if (fn == 0.0) {
+    hist.push_back(0.0);
+    return {};
+  }
+  double* r = c->kV.as<double>();
+  double* z = r + N;
+  double* p = z + N;
+  double* q = p + N;
+  hist.push_back(rn / fn);
+  double rz = 0.0;
+  int it = 0;
+  while (hist.back() > tol && it < maxit && std::isfinite(hist.back())) {
+    MG_TRY(vcycle_any(c, r, z, nullptr));
+    double rz_new = 0.0;
+    MG_TRY(dot_host(c, r, z, N, &rz_new));
+    MG_TRY(launch_axpby(p, z, 1.0, it == 0 ? 0.0 : rz_new / rz, N, st));   // p = z + beta p
+    rz = rz_new;
+    MG_TRY(launch_apply_A(c->op[0].as<double>(), p, q, c->n, st));
+    double pq = 0.0;
+    MG_TRY(dot_host(c, p, q, N, &pq));
+    const double alpha = rz / pq;
+    MG_TRY(launch_axpby(du, p, alpha, 1.0, N, st));
+    MG_TRY(launch_axpby(r, q, -alpha, 1.0, N, st));
+    ++it;
+    MG_TRY(sumsq(c, r, N, 4));
+    double r2 = 0.0;
+    MG_TRY(read_scalar(c, 4, &r2));
+    hist.push_back(std::sqrt(r2) / fn);
+  }
+  *iters = it;
+  if (!std::isfinite(hist.back())) return make_status(MGCNN_ERR_NONFINITE, "residual norm is not finite");
+  return {};
+}
+
+// Preconditioned MINRES (Lanczos on B A in the B^{-1} inner product; Givens
+// rotations on the tridiagonal least-squares problem as its columns arrive;
+// search directions w_k = (v_k - eps_k w_{k-2} - delta_k w_{k-1}) / gamma_k).
+// hist[k] = ||r_k||_B / ||r_0||_B from the recursion.
+Status minres_solve(mgcnn_ctx* c, const double* df, double* du, double tol, int maxit, int* iters,
+                    std::vector<double>& hist) {
+  const size_t N = c->lv[0].N();
+  cudaStream_t st = c->stream;
+  *iters = 0;
+  hist.clear();
+  double fn = 0.0, rn = 0.0;
+  MG_TRY(sym_start(c, df, du, 7, &fn, &rn));
+  if (fn == 0.0) {
+    hist.push_back(0.0);
+    return {};
+  }
+  double* buf = c->kV.as<double>();
+  double* r_cur = buf;            // r_k (unpreconditioned Lanczos vector, scaled by beta_k)
+  double* r_prev = buf + N;       // r_{k-1}
+  double* y = buf + 2 * N;        // B r_k
+  double* v = buf + 3 * N;
+  double* t = buf + 4 * N;
+  double* w_prev2 = buf + 5 * N;  // w_{k-2}
+  double* w_prev = buf + 6 * N;   // w_{k-1}
+  MG_CUDA(cudaMemsetAsync(w_prev2, 0, 2 * N * sizeof(double), st));
+  MG_TRY(vcycle_any(c, r_cur, y, nullptr));
+  double ry = 0.0;
+  MG_TRY(dot_host(c, r_cur, y, N, &ry));
+  if (!(ry >= 0.0)) return make_status(MGCNN_ERR_NONFINITE, "preconditioner is not positive definite");
+  const double beta1 = std::sqrt(ry);
+  hist.push_back(beta1 == 0.0 ? 0.0 : 1.0);
+  double beta_prev = 0.0, beta = beta1, cs = -1.0, sn = 0.0, dbar = 0.0, eps = 0.0, phibar = beta1;
+  int it = 0;
+  while (beta1 != 0.0 && it < maxit) {
+    MG_TRY(launch_scale(y, v, 1.0 / beta, N, st));
+    MG_TRY(launch_apply_A(c->op[0].as<double>(), v, t, c->n, st));
+    if (it > 0) MG_TRY(launch_axpby(t, r_prev, -beta / beta_prev, 1.0, N, st));
+    double alpha = 0.0;
+    MG_TRY(dot_host(c, v, t, N, &alpha));
+    MG_TRY(launch_axpby(t, r_cur, -alpha / beta, 1.0, N, st));
+    // r_{k-1} <- r_k, r_k <- t (the old r_{k-1} buffer becomes the next t)
+    double* old_prev = r_prev;
+    r_prev = r_cur;
+    r_cur = t;
+    t = old_prev;
+    MG_TRY(vcycle_any(c, r_cur, y, nullptr));
+    MG_TRY(dot_host(c, r_cur, y, N, &ry));
+    if (!(ry >= 0.0)) return make_status(MGCNN_ERR_NONFINITE, "preconditioner is not positive definite");
+    beta_prev = beta;
+    beta = std::sqrt(ry);
+    const double eps_old = eps;
+    const double delta = cs * dbar + sn * alpha;
+    const double gbar = sn * dbar - cs * alpha;
+    eps = sn * beta;
+    dbar = -cs * beta;
+    const double gamma = std::hypot(gbar, beta);
+    cs = gbar / gamma;
+    sn = beta / gamma;
+    const double phi = cs * phibar;
+    phibar = sn * phibar;
+    // w_k into the w_{k-2} buffer, then rotate the two
+    MG_TRY(launch_lincomb3(w_prev2, v, 1.0 / gamma, w_prev2, -eps_old / gamma, w_prev, -delta / gamma, N, st));
+    std::swap(w_prev2, w_prev);
+    MG_TRY(launch_axpby(du, w_prev, phi, 1.0, N, st));
+    ++it;
+    hist.push_back(std::fabs(phibar) / beta1);
+    if (hist.back() <= tol || !std::isfinite(hist.back()) || beta == 0.0) break;
   }
   *iters = it;
   if (!std::isfinite(hist.back())) return make_status(MGCNN_ERR_NONFINITE, "residual norm is not finite");
@@ -572,12 +774,7 @@ int mgcnn_set_weights(mgcnn_ctx* c, const double* w, size_t count) {
   if (count != c->wl.total)
     return finish(c, make_status(MGCNN_ERR_ARG, "weight count %zu, expected %zu", count, c->wl.total));
   Status s = [&]() -> Status {
-    MG_TRY(ensure(c->w64, count * sizeof(double)));
-    MG_TRY(ensure(c->w32, count * sizeof(float)));
-    MG_CUDA(cudaMemcpyAsync(c->w64.p, w, count * sizeof(double), cudaMemcpyDefault, c->stream));
-    MG_TRY(convert<float>(c->w64.as<double>(), c->w32.as<float>(), count, c->stream));
-    MG_TRY(mixed_set_weights(c));
-    MG_TRY(sync(c));
+    MG_TRY(load_weights(c, w));
     c->have_weights = true;
     return {};
   }();
@@ -605,6 +802,22 @@ int mgcnn_setup_gmg(mgcnn_ctx* c, const double* coeff, int n, double omega) {
       else
         MG_TRY(mixed_gmg_setup_level(c, l, omega));
     }
+    MG_TRY(sync(c));
+    c->have_setup = true;
+    return {};
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_setup_bpx(mgcnn_ctx* c, const double* coeff, int n, double omega) {
+  if (!c || !coeff) return MGCNN_ERR_ARG;
+  Status st = [&]() -> Status {
+    if (!c->symmetric) return make_status(MGCNN_ERR_STATE, "the BPX setup needs the symmetric network");
+    if (!(omega > 0.0 && omega <= 2.0)) return make_status(MGCNN_ERR_ARG, "omega must be in (0, 2]");
+    MG_TRY(setup_operators(c, coeff, n));
+    for (int l = 0; l < c->L; ++l)
+      MG_TRY(launch_bpx_setup(c->op[l].as<double>(), c->s64[l].as<double>(), c->lv[l].n, l, omega, c->cfg.channels,
+                              c->stream));
     MG_TRY(sync(c));
     c->have_setup = true;
     return {};
@@ -742,6 +955,43 @@ int mgcnn_solve_krylov(mgcnn_ctx* c, const double* f, double* u, double tol, int
   return finish(c, st);
 }
 
+// PCG (method 0) or MINRES (method 1) with the symmetric network.
+static int symmetric_entry(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int* iters,
+                           double* relres, int method) {
+  if (!c || !f || !u || !iters || maxit < 0 || !(tol >= 0.0)) return MGCNN_ERR_ARG;
+  *iters = 0;
+  Status st = [&]() -> Status {
+    MG_TRY(require_setup(c));
+    MG_TRY(require_symmetric_problem(c));
+    const size_t N = c->lv[0].N();
+    const double* df = nullptr;
+    MG_TRY(stage_in(c, f, N, c->f, &df));
+    double* du = nullptr;
+    bool host = false;
+    MG_TRY(stage_out(u, N, c->u, &du, &host));
+    if (host) MG_CUDA(cudaMemcpyAsync(du, u, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    std::vector<double> hist;
+    const Status s = method == 0 ? pcg_solve(c, df, du, tol, maxit, iters, hist)
+                                 : minres_solve(c, df, du, tol, maxit, iters, hist);
+    if (relres) std::copy(hist.begin(), hist.end(), relres);
+    MG_TRY(stage_out_finish(c, u, du, N, host));
+    MG_TRY(sync(c));
+    if (!s.ok()) return s;
+    if (hist.back() > tol)
+      return make_status(MGCNN_NOT_CONVERGED, "no convergence in %d iterations (relres %.3e)", maxit, hist.back());
+    return {};
+  }();
+  return finish(c, st);
+}
+
+int mgcnn_solve_pcg(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
+  return symmetric_entry(c, f, u, tol, maxit, iters, relres, 0);
+}
+
+int mgcnn_solve_minres(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
+  return symmetric_entry(c, f, u, tol, maxit, iters, relres, 1);
+}
+
 int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
   if (!c || !f || !u || !iters || maxit < 0 || !(tol >= 0.0)) return MGCNN_ERR_ARG;
   *iters = 0;
@@ -818,6 +1068,7 @@ static Status refresh_weights(mgcnn_ctx* c) {
 static Status loss_grad_any(mgcnn_ctx* c, int nprob, const double* const* coeff, const double* const* rhs,
                             const int* n, int K, double* loss, bool want_grad) {
   if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
+  if (c->symmetric) return make_status(MGCNN_ERR_STATE, "training is not available for the symmetric network");
   if (nprob < 1 || K < 1 || K > 64) return make_status(MGCNN_ERR_ARG, "need nprob >= 1 and 1 <= K <= 64");
   if (c->cfg.pde != MGCNN_PDE_DIV_HARMONIC) return make_status(MGCNN_ERR_ARG, "training supports the divergence form");
   for (int i = 0; i < nprob; ++i) {
@@ -980,6 +1231,26 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
     case MGCNN_OPT_DEVICE_LOOP:
       c->device_loop = value ? 1 : 0;
       return finish(c, {});
+    case MGCNN_OPT_SYMMETRIC: {
+      if (value != 0 && value != 1) return finish(c, make_status(MGCNN_ERR_ARG, "symmetric option is 0 or 1"));
+      if (value) {
+        if (c->cfg.precision != MGCNN_PREC_FP64)
+          return finish(c, make_status(MGCNN_ERR_ARG, "the symmetric network runs in FP64 precision"));
+        if (c->cfg.input_diag)
+          return finish(c, make_status(MGCNN_ERR_ARG, "the symmetric network needs input_diag = 0"));
+        if (c->wl.nu_d != c->wl.nu_u)
+          return finish(c, make_status(MGCNN_ERR_ARG, "the symmetric network needs down_layers == up_layers"));
+      }
+      const bool retie = value && !c->symmetric && c->have_weights;
+      c->symmetric = value;
+      if (!retie) return finish(c, {});
+      std::vector<double> w(c->wl.total);
+      Status st = [&]() -> Status {
+        MG_CUDA(cudaMemcpy(w.data(), c->w64.p, w.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        return load_weights(c, w.data());
+      }();
+      return finish(c, st);
+    }
     case MGCNN_OPT_TILE:
       if (value < -1 || value >= kFusedVariants)
         return finish(c, make_status(MGCNN_ERR_ARG, "tile shape %d not in -1..%d", value, kFusedVariants - 1));

@@ -115,6 +115,7 @@ struct mgcnn_ctx {
   int tile_var[2][mgcnn::kMaxLevels] = {};  // autotuned tile variants (down, up) per level
   bool tuned = false;                       // set by the first solve after a setup
   int tile_fixed = -1;                      // MGCNN_OPT_TILE: a fixed tile variant, or -1 (autotune)
+  int symmetric = 0;                        // MGCNN_OPT_SYMMETRIC: tied adjoint up sweep (FP64)
   struct TunedClass {                       // tile variants chosen for batched classes, per (n, batch)
     int n, batch;
     int var[2][mgcnn::kMaxLevels];

@@ -1,6 +1,8 @@
-// Vector kernels of the flexible GMRES driver (MGCNN as a Krylov preconditioner):
-// y = A x on the finest grid, the Gram-Schmidt dot products of one vector with
-// a block of basis vectors, and linear combinations with device coefficients.
+// Vector kernels of the Krylov drivers (MGCNN as a Krylov preconditioner:
+// flexible GMRES, and CG / MINRES for the symmetric network): y = A x on the
+// finest grid, the dot products of one vector with a block of vectors, linear
+// combinations with device coefficients, and axpby / three-term combinations
+// with host scalars.
 // FP64 throughout; every reduction sums in a fixed order (one partial per block,
 // then one block per coefficient), so results repeat bit for bit.
 #include "ops.cuh"
@@ -93,6 +95,23 @@ __global__ void __launch_bounds__(KB) scale_kernel(const double* __restrict__ x,
   if (p < N) y[p] = a * x[p];
 }
 
+// y <- a x + b y; b == 0 does not read y (it may hold anything, NaN included)
+__global__ void __launch_bounds__(KB) axpby_kernel(double* __restrict__ y, const double* __restrict__ x, double a,
+                                                   double b, size_t N) {
+  const size_t p = (size_t)blockIdx.x * KB + threadIdx.x;
+  if (p >= N) return;
+  y[p] = (b == 0.0) ? a * x[p] : fma(a, x[p], b * y[p]);
+}
+
+// out <- a x + b y + c z, the terms added in that order; out may alias y or z
+__global__ void __launch_bounds__(KB) lincomb3_kernel(double* out, const double* x, double a, const double* y,
+                                                      double b, const double* z, double c, size_t N) {
+  const size_t p = (size_t)blockIdx.x * KB + threadIdx.x;
+  if (p >= N) return;
+  const double v = a * x[p] + b * y[p];
+  out[p] = v + c * z[p];
+}
+
 int chunks(size_t N) { return (int)((N + KCHUNK - 1) / KCHUNK); }
 
 }  // namespace
@@ -125,6 +144,19 @@ Status launch_combine(double* y, const double* V, int nvec, const double* coef, 
 Status launch_scale(const double* x, double* y, double a, size_t N, cudaStream_t st) {
   scale_kernel<<<grid_for(N, KB), KB, 0, st>>>(x, y, a, N);
   MG_LAUNCH("scale_kernel");
+  return {};
+}
+
+Status launch_axpby(double* y, const double* x, double a, double b, size_t N, cudaStream_t st) {
+  axpby_kernel<<<grid_for(N, KB), KB, 0, st>>>(y, x, a, b, N);
+  MG_LAUNCH("axpby_kernel");
+  return {};
+}
+
+Status launch_lincomb3(double* out, const double* x, double a, const double* y, double b, const double* z, double c,
+                       size_t N, cudaStream_t st) {
+  lincomb3_kernel<<<grid_for(N, KB), KB, 0, st>>>(out, x, a, y, b, z, c, N);
+  MG_LAUNCH("lincomb3_kernel");
   return {};
 }
 

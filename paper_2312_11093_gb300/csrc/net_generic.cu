@@ -18,6 +18,7 @@ template <> __device__ __forceinline__ float dev_tanh<float>(float v) { return t
 
 // Same-size 3x3 convolution with the optional pieces of the network's layers:
 //   heterogeneous ResNet (Eq. heteroresnet): y = K (s * x) + x        (s, skip)
+//   its adjoint (symmetric network):          y = s * (K x) + x        (s_out, skip)
 //   NonLinearResNet (Eq. resnet_nonlinear):  y = tanh(K x + b) + x    (bias, tanh, skip)
 //   setup output scaling:                    y /= diag                (diag)
 template <typename T, int CI, int CO>
@@ -28,6 +29,7 @@ __global__ void __launch_bounds__(128) conv_same_kernel(ConvArgs<T> a) {
   const size_t bi = blockIdx.y;
   a.x += bi * a.x_bs;
   if (a.s) a.s += bi * a.s_bs;
+  if (a.s_out) a.s_out += bi * a.s_bs;   // same layout as s
   if (a.skip) a.skip += bi * a.skip_bs;
   if (a.diag) a.diag += bi * a.diag_bs;
   a.y += bi * a.y_bs;
@@ -56,6 +58,7 @@ __global__ void __launch_bounds__(128) conv_same_kernel(ConvArgs<T> a) {
   for (int co = 0; co < CO; ++co) {
     T v = acc[co];
     if (a.tanh_act) v = dev_tanh<T>(v);
+    if (a.s_out) v *= a.s_out[(size_t)p * CO + co];
     if (a.skip) v += a.skip[(size_t)p * CO + co];
     if (a.diag) v = (T)((double)v / a.diag[p]);
     if (a.out_scale != 1.0) v = (T)((double)v * a.out_scale);

@@ -45,7 +45,12 @@ Status launch_gmg_setup(const double* op, double* out, int n, double omega, cuda
 Status launch_gmg_v10_setup_bf16(const double* op, __nv_bfloat16* out, int n, double omega, cudaStream_t st,
                                  bool input_diag_level, int batch = 1);
 Status launch_axpy_to(const double* u, const double* e, double* out, size_t N, cudaStream_t st);
-// krylov.cu: vector kernels of the flexible GMRES driver (FP64, fixed-order sums)
+// Setup tensors of the BPX network (symmetric variant) on level `level`:
+// out[p][0] = sqrt(omega 4^level / a_C(p)) / eps with eps = MGCNN_BPX_EPS, the
+// other channels 0; out [N][channels] FP64.
+Status launch_bpx_setup(const double* op, double* out, int n, int level, double omega, int channels,
+                        cudaStream_t st);
+// krylov.cu: vector kernels of the Krylov drivers (FP64, fixed-order sums)
 size_t krylov_partial_count(size_t N, int nvec);   // doubles of the dots scratch
 Status launch_apply_A(const double* op, const double* x, double* y, int n, cudaStream_t st);
 // out[i] = <V_i, w>, i < nvec (V: nvec vectors of N back to back)
@@ -55,6 +60,10 @@ Status launch_block_dots(const double* V, int nvec, const double* w, size_t N, d
 Status launch_combine(double* y, const double* V, int nvec, const double* coef, double sign, size_t N,
                       cudaStream_t st);
 Status launch_scale(const double* x, double* y, double a, size_t N, cudaStream_t st);
+// y <- a x + b y (b == 0: y is not read); out <- a x + b y + c z (out may alias y or z)
+Status launch_axpby(double* y, const double* x, double a, double b, size_t N, cudaStream_t st);
+Status launch_lincomb3(double* out, const double* x, double a, const double* y, double b, const double* z, double c,
+                       size_t N, cudaStream_t st);
 
 // ---- net_generic.cu: FP64 / FP32 direct convolution kernels ----------------
 template <typename T>
@@ -63,6 +72,8 @@ struct ConvArgs {
   const T* s = nullptr;     // optional per-pixel input scale [N][CI] (Eq. heteroresnet)
   const T* W = nullptr;     // weights [CO][CI][3][3]
   const T* bias = nullptr;  // optional [CO]
+  const T* s_out = nullptr;  // optional per-pixel output scale [N][CO], applied before the skip
+                            // (the adjoint layer x + s * (K^T x) of the symmetric network)
   const T* skip = nullptr;  // optional residual input [N][CO], added after the activation
   const double* diag = nullptr;  // optional: divide the result by diag[p] (FP64 a_C)
   double out_scale = 1.0;        // multiply the result (after skip) by this constant
@@ -72,7 +83,7 @@ struct ConvArgs {
   // batch of problems of the same size: blockIdx.y selects the problem and
   // each pointer advances by its stride (elements; 0 = shared by the batch)
   int batch = 1;
-  size_t x_bs = 0, s_bs = 0, skip_bs = 0, diag_bs = 0, y_bs = 0;
+  size_t x_bs = 0, s_bs = 0, skip_bs = 0, diag_bs = 0, y_bs = 0;   // s_bs also strides s_out
 };
 
 template <typename T>

@@ -75,6 +75,9 @@ def load() -> ctypes.CDLL:
         "mgcnn_setup_batched_gmg": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double]),
         "mgcnn_check_wait_timeout": (c_int, [c_void_p]),
         "mgcnn_solve_krylov": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_void_p]),
+        "mgcnn_setup_bpx": (c_int, [c_void_p, c_void_p, c_int, c_double]),
+        "mgcnn_solve_pcg": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), c_void_p]),
+        "mgcnn_solve_minres": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), c_void_p]),
         "mgcnn_solve_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
                                         c_void_p]),
         "mgcnn_kernel_launches": (ctypes.c_longlong, []),
@@ -208,6 +211,25 @@ def gmg_v10_weights() -> np.ndarray:
     w = {"w_in": w_in, "w_down": down[None], "w_up": np.zeros((1, C, C, 3, 3)), "w_R": R, "w_P": P,
          "w_out": w_out}
     return pack_weights(w, C, 1, 1)
+
+
+BPX_EPS = 2.0 ** -26   # MGCNN_BPX_EPS of the C header
+
+
+def bpx_weights(channels: int = 4, layers: int = 1) -> np.ndarray:
+    """Weight blob of the BPX network for a symmetric context (channels >= 2,
+    down_layers = up_layers = `layers`): reChannel-in puts eps r into channel 0,
+    the first down layer copies channel 0 (scaled by the setup tensor of
+    mgcnn_setup_bpx) into channel 1, RCNN carries channel 0 by full weighting.
+    The tied up, TCNN and out entries are filled in by the library."""
+    C = channels
+    w_in = np.zeros((C, 1, 3, 3))
+    w_in[0, 0, 1, 1] = BPX_EPS
+    down = np.zeros((layers, C, C, 3, 3))
+    down[0, 1, 0, 1, 1] = 1.0
+    R = np.zeros((C, C, 3, 3))
+    R[0, 0] = np.outer([1.0, 2.0, 1.0], [1.0, 2.0, 1.0]) / 16.0
+    return pack_weights({"w_in": w_in, "w_down": down, "w_R": R}, C, layers, layers)
 
 
 class Solver:
@@ -348,6 +370,7 @@ class Solver:
     OPT_FUSED = 1
     OPT_DEVICE_LOOP = 2
     OPT_TILE = 3
+    OPT_SYMMETRIC = 4
 
     def set_option(self, option: int, value: int):
         self._check(self._L.mgcnn_set_option(self._h, int(option), int(value)), "mgcnn_set_option")
@@ -395,6 +418,29 @@ class Solver:
         e = np.empty(N) if e is None else e
         self._check(self._L.mgcnn_vcycle(self._h, _ptr(r, N), _ptr(e, N, True)), "mgcnn_vcycle")
         return e
+
+    def setup_bpx(self, coeff, n: int, omega: float = 1.0):
+        """Operators + the setup tensors that make the symmetric network BPX."""
+        self._check(self._L.mgcnn_setup_bpx(self._h, _ptr(coeff), int(n), float(omega)), "mgcnn_setup_bpx")
+        self.n = int(n)
+
+    def _solve_sym(self, fn, name, f, u, tol, maxit):
+        N = self.n * self.n
+        it = c_int(0)
+        hist = np.zeros(maxit + 1)
+        st = fn(self._h, _ptr(f, N), _ptr(u, N, True), float(tol), int(maxit), ctypes.byref(it), hist.ctypes.data)
+        self._check(st, name, ok=(OK, NOT_CONVERGED))
+        return st, it.value, hist[: it.value + 1]
+
+    def solve_pcg(self, f, u, tol: float, maxit: int):
+        """CG with the symmetric network as preconditioner, in place on u.
+        Returns (status, iters, ||r_k|| / ||f|| for k = 0..iters)."""
+        return self._solve_sym(self._L.mgcnn_solve_pcg, "mgcnn_solve_pcg", f, u, tol, maxit)
+
+    def solve_minres(self, f, u, tol: float, maxit: int):
+        """MINRES with the symmetric network as preconditioner, in place on u.
+        Returns (status, iters, ||r_k||_B / ||r_0||_B for k = 0..iters)."""
+        return self._solve_sym(self._L.mgcnn_solve_minres, "mgcnn_solve_minres", f, u, tol, maxit)
 
     def solve_krylov(self, f, u, tol: float, maxit: int, restart: int = 30):
         """Flexible GMRES with the network as preconditioner, in place on u.

@@ -60,3 +60,12 @@ def test_v10_blob_matches_oracle_construction():
     from paper_2312_11093_gb300 import mgcnn
     ref = mgcnn.pack_weights(omg.gmg_v10_weights(), omg.V10_CHANNELS, 1, 1)
     assert np.array_equal(mgcnn.gmg_v10_weights(), ref)
+
+
+def test_bpx_eps_matches_the_header():
+    """The BPX weights of the Python binding use the header's MGCNN_BPX_EPS."""
+    import re
+    from paper_2312_11093_gb300 import mgcnn
+    text = open(os.path.join(ROOT, "include", "mgcnn.h")).read()
+    m = re.search(r"#define MGCNN_BPX_EPS (\S+)", text)
+    assert m and float.fromhex(m.group(1)) == mgcnn.BPX_EPS
