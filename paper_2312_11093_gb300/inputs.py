@@ -22,6 +22,10 @@ __all__ = [
     "checkerboard_k",
     "channelised_k",
     "paper_white_noise_mu",
+    "multilevel_noise",
+    "paper_coefficient",
+    "paper_mldata_mu",
+    "paper_mldata_k",
     "normal_rhs",
     "unit_rhs",
 ]
@@ -99,6 +103,58 @@ def paper_white_noise_mu(n: int, rng: np.random.Generator, Re: float = 1000.0) -
     w = rng.uniform(0.0, 1.0, size=(n, n))
     power = w * np.log10(Re)
     return 10.0 ** (-power)
+
+
+def _resize_linear(a: np.ndarray, size: int) -> np.ndarray:
+    """Separable linear interpolation of a square array to size x size, corner
+    samples kept (sample positions spread evenly from the first to the last)."""
+    m = a.shape[0]
+    src = np.arange(m, dtype=np.float64)
+    dst = np.linspace(0.0, m - 1.0, size)
+    rows = np.stack([np.interp(dst, src, a[j]) for j in range(m)])        # m x size
+    return np.stack([np.interp(dst, src, rows[:, i]) for i in range(size)], axis=1)
+
+
+def multilevel_noise(size: int, levels: int, rng: np.random.Generator, init_size: int = 5) -> np.ndarray:
+    """The paper's multi-level data (Appendix, Algorithm "Generate Multi-Level
+    Data"): white noise on init_size^2, then `levels` times doubled in size by
+    interpolation with white noise of weight 2^-i added, finally interpolated to
+    size^2.  White noise is uniform on [0, 1) and interpolation is linear (the
+    paper names neither)."""
+    data = rng.uniform(0.0, 1.0, size=(init_size, init_size))
+    for i in range(1, levels + 1):
+        data = _resize_linear(data, 2 * data.shape[0])
+        data = data + 2.0 ** (-i) * rng.uniform(0.0, 1.0, size=data.shape)
+    return _resize_linear(data, size)
+
+
+def paper_coefficient(x: np.ndarray, Re: float = 1000.0) -> np.ndarray:
+    """The paper's map of a random tensor to a coefficient (Sec. 4.1): linearly to a
+    power in [0, log10 Re] (the tensor's minimum to 0, its maximum to log10 Re),
+    then coef = 10^(-power) in [1/Re, 1]."""
+    lo, hi = float(x.min()), float(x.max())
+    power = (x - lo) / (hi - lo) * np.log10(Re)
+    return 10.0 ** (-power)
+
+
+def _mldata_levels(size: int, init_size: int) -> int:
+    """Doublings of init_size that stay within the goal size (the paper does not say)."""
+    levels = 0
+    while init_size * 2 ** (levels + 1) <= size:
+        levels += 1
+    return levels
+
+
+def paper_mldata_mu(n: int, rng: np.random.Generator, Re: float = 1000.0, init_size: int = 5) -> np.ndarray:
+    """Non-divergence coefficient mu on the n x n interior nodes from multi-level data."""
+    return paper_coefficient(multilevel_noise(n, _mldata_levels(n, init_size), rng, init_size), Re)
+
+
+def paper_mldata_k(n: int, rng: np.random.Generator, Re: float = 1000.0, init_size: int = 5) -> np.ndarray:
+    """Divergence-form nodal k on the (n+2)^2 nodes (boundary ring included) from
+    multi-level data, mapped to [1/Re, 1] as the paper maps its coefficient."""
+    m = n + 2
+    return paper_coefficient(multilevel_noise(m, _mldata_levels(m, init_size), rng, init_size), Re)
 
 
 def normal_rhs(n: int, rng: np.random.Generator) -> np.ndarray:

@@ -42,6 +42,8 @@ def problem(n, seed, kind="grf", b=(1.0, 0.5)):
         k = inputs.random_blocks_k(n, rng)
     elif kind == "chan":
         k = inputs.channelised_k(n, rng, 0.05)
+    elif kind == "mldata":
+        k = inputs.paper_mldata_k(n, rng)
     else:
         k = inputs.checkerboard_k(n)
     f = inputs.normal_rhs(n, rng)
@@ -52,7 +54,8 @@ def to_nhwc(levels):
     return np.concatenate([s.transpose(1, 2, 0).ravel() for s in levels])
 
 
-@pytest.mark.parametrize("n,kind", [(3, "grf"), (7, "blocks"), (31, "grf"), (63, "chan"), (255, "checker")])
+@pytest.mark.parametrize("n,kind", [(3, "grf"), (7, "blocks"), (31, "grf"), (63, "chan"), (255, "checker"),
+                                    (127, "mldata")])
 def test_operator_all_levels(M, n, kind):
     k, f = problem(n, n, kind, b=(-0.4, 1.3))
     sv = M.Solver(8, 1, 1, b=(-0.4, 1.3))

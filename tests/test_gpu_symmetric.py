@@ -137,6 +137,30 @@ def test_krylov_with_bpx_iterate_for_iterate(M, method, n):
         1.0 if method == "pcg" else 10.0)
 
 
+def test_bpx_on_the_papers_multilevel_data(M):
+    """The paper's test setting (Sec. 4.1: coefficient in [1/Re, 1] with Re = 1000,
+    right-hand side 1, tol 1e-8) on its multi-level data: CG with the BPX network
+    against the oracle, as in the test above (the oracle needs 29-33 iterations
+    at 63^2-255^2)."""
+    n = 255
+    rng = np.random.default_rng(n)
+    k = inputs.paper_mldata_k(n, rng)
+    f = inputs.unit_rhs(n)
+    sts = oop.level_stencils_div(k, (0.0, 0.0), num_levels(n))
+    sv = symmetric_solver(M, 4, 1)
+    sv.set_weights(M.bpx_weights(4))
+    sv.setup_bpx(k.ravel().copy(), n, 1.0)
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve_pcg(f.ravel().copy(), u, 1e-8, 200)
+    assert st == M.OK
+    w, s = omg.bpx_weights(4), omg.bpx_setup(sts, 1.0, 4)
+    _, it_o, hist_o = ok.pcg(lambda x: oop.apply(sts[0], x), lambda r: omg.solve_phase_symmetric(w, s, r),
+                             f, None, 1e-8, 200)
+    assert abs(it - it_o) <= 2 and it <= 40
+    assert np.allclose(hist[:10], hist_o[:10], rtol=1e-9, atol=0.0)
+    assert np.linalg.norm(f - oop.apply(sts[0], u.reshape(n, n))) <= 1.05e-8 * np.linalg.norm(f)
+
+
 def test_bpx_pcg_at_1023_needs_grid_independent_iterations(M):
     """At 1023^2 CG with the BPX network still needs about as many iterations
     as at 63^2 (the oracle needs 25-31 up to 511^2 on such fields); the
