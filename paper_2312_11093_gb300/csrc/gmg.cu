@@ -80,7 +80,29 @@ __global__ void prolong_add_kernel(const double* __restrict__ ec, double* __rest
   e[p] += acc / 4.0;
 }
 
+// Setup tensors of the BPX network (symmetric variant of the learned solver,
+// the additive multilevel counterpart of the V-cycle above): the carrier
+// channel's scale that makes the smoother copy sqrt(omega 4^l / a_C) R_l r; the
+// division by eps (a power of two) is exact.
+__global__ void bpx_setup_kernel(const double* __restrict__ op, double* __restrict__ out, int n, double w4l,
+                                 int channels) {
+  const size_t N = (size_t)n * n;
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double* o = out + p * channels;
+  o[0] = sqrt(w4l / op[p]) / MGCNN_BPX_EPS;
+  for (int c = 1; c < channels; ++c) o[c] = 0.0;
+}
+
 }  // namespace
+
+Status launch_bpx_setup(const double* op, double* out, int n, int level, double omega, int channels,
+                        cudaStream_t st) {
+  bpx_setup_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, out, n, omega * std::ldexp(1.0, 2 * level),
+                                                                 channels);
+  MG_LAUNCH("bpx_setup_kernel");
+  return {};
+}
 
 // One V(nu1, nu2) cycle on level l for A_l e = r_l from e = 0; the result is in e[l].
 Status gmg_vcycle(const GmgLevels& g, int l, int nu1, int nu2, double omega, cudaStream_t st) {

@@ -466,27 +466,6 @@ Status launch_gmg_v10_setup_bf16(const double* op, __nv_bfloat16* out, int n, do
   return {};
 }
 
-// BPX network setup (symmetric variant): the carrier channel's scale that makes
-// the smoother copy sqrt(omega 4^l / a_C) R_l r; the division by eps (a power of
-// two) is exact.
-__global__ void bpx_setup_kernel(const double* __restrict__ op, double* __restrict__ out, int n, double w4l,
-                                 int channels) {
-  const size_t N = (size_t)n * n;
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
-  double* o = out + p * channels;
-  o[0] = sqrt(w4l / op[p]) / MGCNN_BPX_EPS;
-  for (int c = 1; c < channels; ++c) o[c] = 0.0;
-}
-
-Status launch_bpx_setup(const double* op, double* out, int n, int level, double omega, int channels,
-                        cudaStream_t st) {
-  bpx_setup_kernel<<<grid_for((size_t)n * n, 256), 256, 0, st>>>(op, out, n, omega * std::ldexp(1.0, 2 * level),
-                                                                 channels);
-  MG_LAUNCH("bpx_setup_kernel");
-  return {};
-}
-
 Status launch_gmg_setup(const double* op, double* out, int n, double omega, cudaStream_t st,
                         bool input_diag_level, int channels) {
   if (channels == kGmgV10Channels) {
