@@ -24,6 +24,8 @@
 // so a strip can be any 16 pixels of an odd-sized region.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <utility>
 
 #include "fpconv.cuh"
 #include "mixed.cuh"
@@ -580,17 +582,27 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
 }
 
 // Dynamic shared memory of a kernel instantiation: above 48 KB the kernel must be
-// allowed it once (cudaFuncSetAttribute); the instantiations already allowed are
-// remembered.  Returns the byte count for the launch.
+// allowed it once per device (cudaFuncSetAttribute); the (device, kernel) pairs
+// already allowed are remembered, under a lock (contexts may live in different
+// threads).  Returns the byte count for the launch; a refused attribute shows
+// up as the launch's error.
+size_t dyn_smem_allow(const void* kernel, size_t bytes) {
+  static std::mutex lock;
+  static std::vector<std::pair<int, const void*>> allowed;
+  if (bytes <= 48 * 1024) return bytes;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return bytes;
+  std::lock_guard<std::mutex> g(lock);
+  const std::pair<int, const void*> key{dev, kernel};
+  if (std::find(allowed.begin(), allowed.end(), key) == allowed.end() &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    allowed.push_back(key);
+  return bytes;
+}
+
 template <typename K>
 size_t dyn_smem(K* kernel, size_t bytes) {
-  static std::vector<const void*> allowed;
-  const void* key = reinterpret_cast<const void*>(kernel);
-  if (bytes > 48 * 1024 && std::find(allowed.begin(), allowed.end(), key) == allowed.end()) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
-      allowed.push_back(key);
-  }
-  return bytes;
+  return dyn_smem_allow(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 // Tensor map of a level tensor for a box of bw x bh pixels (copied out of the
