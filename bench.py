@@ -505,9 +505,9 @@ def main():
     if args.bpx and rank == 0:
         # the symmetric variant: CG preconditioned by the BPX network on the symmetric
         # problem of the same coefficient field (b = 0), the paper's FP64 tolerance
-        svb = mgcnn.Solver(4, 1, 1, precision="fp64", input_diag=False, b=(0.0, 0.0), stream=stream)
+        svb = mgcnn.Solver(2, 1, 1, precision="fp64", input_diag=False, b=(0.0, 0.0), stream=stream)
         svb.set_option(svb.OPT_SYMMETRIC, 1)
-        svb.set_weights(mgcnn.bpx_weights(4))
+        svb.set_weights(mgcnn.bpx_weights(2))
         ub = torch.zeros_like(u_d)
 
         def bstep():
@@ -527,7 +527,7 @@ def main():
         bms = bv0.elapsed_time(bv1) / bsteps
         result["bpx_pcg"] = {"value": 1e3 / bms, "unit": "solves/s", "ms_per_step": bms, "iters": bit,
                              "relres": float(bh[-1]), "tol": 1e-8, "converged": bool(bst == mgcnn.OK),
-                             "method": "CG, symmetric network as BPX preconditioner (C = 4, FP64), b = 0, "
+                             "method": "CG, symmetric network as BPX preconditioner (C = 2, FP64), b = 0, "
                                        "setup + solve"}
         svb.close()
     if not args.no_cpu and rank == 0 and world == 1:

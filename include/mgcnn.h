@@ -81,7 +81,8 @@ typedef struct mgcnn_ctx mgcnn_ctx;
 
 typedef struct {
   int channels;      /* C, hidden channels of both networks (Sec. 4.2: 4, 8, 12);
-                        supported: 4, 8, 12, 13, 16                              */
+                        supported: 4, 8, 12, 13, 16, and 2 in FP64 precision
+                        (the BPX form of the symmetric network)                 */
   int down_layers;   /* layers ("sweeps") in ResNetDown, >= 1 (Sec. 3.3)      */
   int up_layers;     /* layers in ResNetUp, >= 1                               */
   int precision;     /* MGCNN_PREC_*                                           */

@@ -138,7 +138,9 @@ __global__ void convert_kernel(const double* __restrict__ src, T* __restrict__ d
   if (p < count) dst[p] = (T)src[p];
 }
 
-bool channels_supported(int C) { return C == 4 || C == 8 || C == 12 || C == 13 || C == 16; }
+// 2 channels serve the BPX form of the symmetric network (FP64 only: the mixed
+// path has its own list)
+bool channels_supported(int C) { return C == 2 || C == 4 || C == 8 || C == 12 || C == 13 || C == 16; }
 
 namespace {
 
@@ -152,6 +154,7 @@ Status conv_same_launch(const ConvArgs<T>& a, cudaStream_t st) {
 // Dispatch a kernel template over the supported hidden-channel counts.
 #define MG_DISPATCH_C(C, ...)                                 \
   switch (C) {                                                \
+    case 2: { constexpr int CC = 2; __VA_ARGS__; } break;     \
     case 4: { constexpr int CC = 4; __VA_ARGS__; } break;     \
     case 8: { constexpr int CC = 8; __VA_ARGS__; } break;     \
     case 12: { constexpr int CC = 12; __VA_ARGS__; } break;   \

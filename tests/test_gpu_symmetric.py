@@ -93,19 +93,19 @@ def test_symmetric_vcycle_is_symmetric_on_the_gpu(M):
     assert x @ bx > 0.0 and y @ by > 0.0
 
 
-@pytest.mark.parametrize("n,omega", [(63, 1.0), (255, 0.7)])
-def test_bpx_setup_matches_oracle(M, n, omega):
+@pytest.mark.parametrize("n,omega,C", [(63, 1.0, 4), (255, 0.7, 2), (127, 1.0, 2)])
+def test_bpx_setup_matches_oracle(M, n, omega, C):
     rng, k, f, sts = spd_problem(n, 200 + n)
-    sv = symmetric_solver(M, 4, 1)
-    sv.set_weights(M.bpx_weights(4))
-    assert np.array_equal(sv.get_weights(), M.pack_weights(omg.bpx_weights(4), 4, 1, 1))
+    sv = symmetric_solver(M, C, 1)
+    sv.set_weights(M.bpx_weights(C))
+    assert np.array_equal(sv.get_weights(), M.pack_weights(omg.bpx_weights(C), C, 1, 1))
     sv.setup_bpx(k.ravel().copy(), n, omega)
-    s = levels_from_nhwc(sv.get_setup_tensors(), n, 4)
+    s = levels_from_nhwc(sv.get_setup_tensors(), n, C)
     # the level operators agree with the oracle's to rounding, so the tensors do too
-    for a, b in zip(s, omg.bpx_setup(sts, omega, 4)):
+    for a, b in zip(s, omg.bpx_setup(sts, omega, C)):
         assert np.all(np.abs(a - b) <= 1e-14 * np.abs(b))
     r = rng.standard_normal((n, n))
-    assert relerr(sv.vcycle(r.ravel().copy()), omg.solve_phase_symmetric(omg.bpx_weights(4), s, r)) <= 1e-13
+    assert relerr(sv.vcycle(r.ravel().copy()), omg.solve_phase_symmetric(omg.bpx_weights(C), s, r)) <= 1e-13
 
 
 @pytest.mark.parametrize("method", ["pcg", "minres"])
@@ -119,14 +119,14 @@ def test_krylov_with_bpx_iterate_for_iterate(M, method, n):
     for CG, B-norm for MINRES) must agree to 1e-9, the iteration counts to two,
     and both runs must reach the tolerance, checked with the oracle's operator."""
     rng, k, f, sts = spd_problem(n, 300 + n)
-    sv = symmetric_solver(M, 4, 1)
-    sv.set_weights(M.bpx_weights(4))
+    sv = symmetric_solver(M, 2, 1)
+    sv.set_weights(M.bpx_weights(2))
     sv.setup_bpx(k.ravel().copy(), n, 1.0)
     u = np.zeros(n * n)
     solve = sv.solve_pcg if method == "pcg" else sv.solve_minres
     st, it, hist = solve(f.ravel().copy(), u, 1e-8, 200)
     assert st == M.OK
-    w, s = omg.bpx_weights(4), omg.bpx_setup(sts, 1.0, 4)
+    w, s = omg.bpx_weights(2), omg.bpx_setup(sts, 1.0, 2)
     run = ok.pcg if method == "pcg" else ok.minres
     u_o, it_o, hist_o = run(lambda x: oop.apply(sts[0], x), lambda r: omg.solve_phase_symmetric(w, s, r),
                             f, None, 1e-8, 200)
@@ -147,13 +147,13 @@ def test_bpx_on_the_papers_multilevel_data(M):
     k = inputs.paper_mldata_k(n, rng)
     f = inputs.unit_rhs(n)
     sts = oop.level_stencils_div(k, (0.0, 0.0), num_levels(n))
-    sv = symmetric_solver(M, 4, 1)
-    sv.set_weights(M.bpx_weights(4))
+    sv = symmetric_solver(M, 2, 1)
+    sv.set_weights(M.bpx_weights(2))
     sv.setup_bpx(k.ravel().copy(), n, 1.0)
     u = np.zeros(n * n)
     st, it, hist = sv.solve_pcg(f.ravel().copy(), u, 1e-8, 200)
     assert st == M.OK
-    w, s = omg.bpx_weights(4), omg.bpx_setup(sts, 1.0, 4)
+    w, s = omg.bpx_weights(2), omg.bpx_setup(sts, 1.0, 2)
     _, it_o, hist_o = ok.pcg(lambda x: oop.apply(sts[0], x), lambda r: omg.solve_phase_symmetric(w, s, r),
                              f, None, 1e-8, 200)
     assert abs(it - it_o) <= 2 and it <= 40
@@ -167,8 +167,8 @@ def test_bpx_pcg_at_1023_needs_grid_independent_iterations(M):
     solution is checked with the oracle's operator."""
     n = 1023
     rng, k, f, sts = spd_problem(n, 9)
-    sv = symmetric_solver(M, 4, 1)
-    sv.set_weights(M.bpx_weights(4))
+    sv = symmetric_solver(M, 2, 1)
+    sv.set_weights(M.bpx_weights(2))
     sv.setup_bpx(k.ravel().copy(), n, 1.0)
     u = np.zeros(n * n)
     st, it, hist = sv.solve_pcg(f.ravel().copy(), u, 1e-8, 200)
@@ -179,6 +179,10 @@ def test_bpx_pcg_at_1023_needs_grid_independent_iterations(M):
 def test_symmetric_errors_and_special_cases(M):
     n = 31
     rng, k, f, sts = spd_problem(n, 5)
+    # two channels exist in FP64 only
+    with pytest.raises(M.MGCNNError) as ei:
+        M.Solver(2, 1, 1, precision="mixed_bf16", input_diag=False)
+    assert ei.value.status == M.ERR_SIZE
     # the mode needs FP64, input_diag 0 and equal layer counts
     for kw in ({"precision": "mixed_bf16", "input_diag": False}, {"precision": "fp64", "input_diag": True}):
         sv = M.Solver(4, 1, 1, b=(0.0, 0.0), **kw)

@@ -72,15 +72,15 @@ def fw_matrix(n):
     return R
 
 
-@pytest.mark.parametrize("omega", [1.0, 0.7])
-def test_bpx_network_is_the_textbook_bpx_operator(omega):
+@pytest.mark.parametrize("omega,C", [(1.0, 4), (0.7, 2)])
+def test_bpx_network_is_the_textbook_bpx_operator(omega, C):
     """The BPX weights and setup turn the symmetric network into
     sum_l 4^l R_l^T (omega D_l^{-1}) R_l + eps^2 sum_l R_l^T R_l, with R_l the
     l-fold full weighting and D_l the diagonal of the level-l operator."""
     n = 15
     rng, sts = spd_problem(n, 21)
-    w = omg.bpx_weights(4)
-    s = omg.bpx_setup(sts, omega, 4)
+    w = omg.bpx_weights(C)
+    s = omg.bpx_setup(sts, omega, C)
     B = dense(lambda r: omg.solve_phase_symmetric(w, s, r), n * n, n)
     ref = np.zeros((n * n, n * n))
     Rl = np.eye(n * n)
