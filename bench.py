@@ -215,7 +215,8 @@ def cpu_reference(workload: str, net: str, n_full: int = 4095, n_sample: int | N
     t_solve = scale * ((t1 - t0) + iters * (t2 - t1))
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": (f"numpy FP64 oracle: setup {t1 - t0:.2f}s + 1 cycle {t2 - t1:.2f}s at {n_sample}^2, "
+            "sample": (f"numpy FP64 oracle (elementwise work on one core, channel contractions through BLAS "
+                       f"threads): setup {t1 - t0:.2f}s + 1 cycle {t2 - t1:.2f}s at {n_sample}^2, "
                        f"x{scale:.2f} to {n_full}^2, x{iters} cycles (oracle's count at {n_iters}^2, tol {tol:g})"),
             "seconds_per_solve": t_solve}
 
