@@ -530,6 +530,18 @@ def main():
                              "relres": float(bh[-1]), "tol": 1e-8, "converged": bool(bst == mgcnn.OK),
                              "method": "CG, symmetric network as BPX preconditioner (C = 2, FP64), b = 0, "
                                        "setup + solve"}
+        # MINRES with the same preconditioner (its history is the B-norm ratio)
+        svb.setup_bpx(k_d, n, 1.0)
+        ub.zero_()
+        barrier()
+        bv0.record(stream)
+        mst, mit, mh = svb.solve_minres(f_d, ub, 1e-8, 300)
+        bv1.record(stream)
+        barrier()
+        mms = bv0.elapsed_time(bv1)
+        result["bpx_minres"] = {"value": 1e3 / mms, "unit": "solves/s", "ms_per_step": mms, "iters": mit,
+                                "relres_bnorm": float(mh[-1]), "tol": 1e-8, "converged": bool(mst == mgcnn.OK),
+                                "method": "MINRES, same preconditioner and problem, solve only"}
         svb.close()
     if not args.no_cpu and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_reference(workload, net, n, tol=tol)
