@@ -418,7 +418,8 @@ Status load_weights(mgcnn_ctx* c, const double* w) {
   std::vector<double> tied;
   if (c->symmetric) {
     tied.resize(count);
-    MG_CUDA(cudaMemcpy(tied.data(), w, count * sizeof(double), cudaMemcpyDefault));
+    MG_CUDA(cudaMemcpyAsync(tied.data(), w, count * sizeof(double), cudaMemcpyDefault, c->stream));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
     tie_weights(c->wl, tied.data());
     w = tied.data();
   }
@@ -1246,7 +1247,8 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
       if (!retie) return finish(c, {});
       std::vector<double> w(c->wl.total);
       Status st = [&]() -> Status {
-        MG_CUDA(cudaMemcpy(w.data(), c->w64.p, w.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        MG_CUDA(cudaMemcpyAsync(w.data(), c->w64.p, w.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        MG_CUDA(cudaStreamSynchronize(c->stream));
         return load_weights(c, w.data());
       }();
       return finish(c, st);
