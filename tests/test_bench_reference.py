@@ -38,3 +38,16 @@ def test_reference_line_keeps_the_contract():
 def test_reference_arm_runs_on_rank_zero_only():
     out = run_bench({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_traffic_record_matches_the_committed_profiles():
+    """The DRAM traffic that bench.py reports next to the roofline comes from the
+    committed ncu summary only while the kernel's source is the one profiled
+    (its hash is recorded beside the number); the committed summary is current."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for kernel in ("residual_kernel", "down_kernel", "up_kernel"):
+        t = bench.traffic_record(kernel, "grf_4095")
+        assert t is not None and t > 1e8, f"{kernel}: profiles/dram_traffic.txt is stale, re-profile"
+    assert bench.traffic_record("up_kernel", "channelised_4095") is None
+    assert bench.traffic_record("no_such_kernel", "grf_4095") is None
