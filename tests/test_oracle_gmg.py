@@ -74,3 +74,27 @@ def test_zero_rhs_and_maxit():
     assert it == 0 and not u.any()
     _, it, hist, _ = gmg.stationary_solve(sts, f, None, 1e-30, 3)
     assert it == 3 and len(hist) == 4
+
+
+def test_symmetric_vcycle_for_a_symmetric_operator():
+    """With b = 0 (A symmetric), Jacobi smoothing and full weighting = 1/4 x the
+    bilinear transpose, the V(nu, nu) cycle is a symmetric operator (pre- and
+    post-smoothing are adjoint, the coarsest-grid sweeps are a symmetric
+    polynomial in D^-1 A times D^-1); V(2, 1) is not."""
+    n = 15
+    rng = np.random.default_rng(8)
+    k = inputs.lognormal_k(n, 0.1, rng)
+    sts = op.level_stencils_div(k, (0.0, 0.0), num_levels(n))
+
+    def dense(nu1, nu2):
+        B = np.zeros((n * n, n * n))
+        for c in range(n * n):
+            e = np.zeros(n * n)
+            e[c] = 1.0
+            B[:, c] = gmg.vcycle(sts, e.reshape(n, n), nu1, nu2, 0.8).ravel()
+        return B
+    for nu in (1, 2):
+        B = dense(nu, nu)
+        assert np.abs(B - B.T).max() <= 1e-13 * np.abs(B).max()
+    B = dense(2, 1)
+    assert np.abs(B - B.T).max() > 1e-3 * np.abs(B).max()

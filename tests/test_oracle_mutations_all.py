@@ -1,0 +1,78 @@
+"""Mistakes planted in a temporary copy of the oracle package (CPU only, the
+repository is not touched) each make a pin fail: the pins are not vacuous.
+Each entry: oracle file, source edit, and the pin files run against the copy."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+OP = ["test_oracle_operator.py"]
+GMG = ["test_oracle_gmg.py"]
+CONV = ["test_oracle_convnet.py"]
+NET = ["test_oracle_mgcnn.py"]
+KRY = ["test_oracle_krylov.py"]
+ADJ = ["test_oracle_adjoint.py"]
+
+MUTATIONS = {
+    "face k arithmetic instead of harmonic": ("operator.py", "return 2.0 * a * b / (a + b)", "return 0.5 * (a + b)", OP),
+    "upwind on the wrong side (x)": ("operator.py", "aW = -kw * ih2 - max(bx, 0.0) / h", "aW = -kw * ih2 + min(bx, 0.0) / h", OP),
+    "convection missing from a_C": ("operator.py", "aC = (kw + ke + ks + kn) * ih2 + (abs(bx) + abs(by)) / h",
+                                    "aC = (kw + ke + ks + kn) * ih2", OP),
+    "non-div centre 3 mu": ("operator.py", "aC = 4.0 * lap +", "aC = 3.0 * lap +", OP),
+    "coarse log k unweighted": ("operator.py", "w = np.array([1.0, 2.0, 1.0])\n    num", "w = np.array([1.0, 1.0, 1.0])\n    num", OP),
+    "apply: N neighbour from the S side": ("operator.py", "+ st.aS * up[:-2, 1:-1] + st.aN * up[2:, 1:-1])",
+                                           "+ st.aS * up[2:, 1:-1] + st.aN * up[:-2, 1:-1])", OP),
+    "Jacobi without omega": ("gmg.py", "return e + omega * (r - apply(st, e)) / st.aC", "return e + (r - apply(st, e)) / st.aC", GMG),
+    "restriction weights /8": ("gmg.py", "FW = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 16.0",
+                               "FW = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 8.0", GMG),
+    "no post-smoothing": ("gmg.py", "    for _ in range(nu2):\n        e = jacobi_sweep(st, e, r, omega)\n    return e",
+                          "    return e", GMG),
+    "conv taps not centred": ("convnet.py", "y += np.tensordot(W[:, :, a, b], xp[:, a:a + n, b:b + m], axes=([1], [0]))",
+                              "y += np.tensordot(W[:, :, a, b], xp[:, b:b + n, a:a + m], axes=([1], [0]))", CONV),
+    "TCNN weight not transposed": ("convnet.py",
+                                   "y[:, a:a + 2 * nc - 1:2, b:b + 2 * nc - 1:2] += np.tensordot(W[:, :, a, b].T, x, axes=([1], [0]))",
+                                   "y[:, a:a + 2 * nc - 1:2, b:b + 2 * nc - 1:2] += np.tensordot(W[:, :, a, b], x, axes=([1], [0]))", CONV),
+    "ResNet skip dropped": ("mgcnn.py", "x[l] = x[l] + cn.conv_same(s[l] * x[l], weights[\"w_down\"][i])",
+                            "x[l] = cn.conv_same(s[l] * x[l], weights[\"w_down\"][i])", NET),
+    "setup tensor after the conv": ("mgcnn.py", "x[l] = x[l] + cn.conv_same(s[l] * x[l], weights[\"w_up\"][i])",
+                                    "x[l] = x[l] + s[l] * cn.conv_same(x[l], weights[\"w_up\"][i])", NET),
+    "U-net skip of the TCNN dropped": ("mgcnn.py",
+                                       "x[l - 1] = x[l - 1] + cn.tcnn(x[l], weights[\"w_P\"], sizes[l - 1])",
+                                       "x[l - 1] = cn.tcnn(x[l], weights[\"w_P\"], sizes[l - 1])", NET),
+    "setup tanh without skip": ("mgcnn.py", "            z = t + z\n", "            z = t\n", NET),
+    "FGMRES Givens sign": ("krylov.py", "H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]",
+                           "H[i + 1, j] = sn[i] * H[i, j] + cs[i] * H[i + 1, j]", KRY),
+    "adjoint: s gradient drops x": ("adjoint.py", "sbar_l += x_in * t", "sbar_l += t", ADJ),
+    "adjoint: skip path dropped": ("adjoint.py", "return xbar + s_l * t", "return s_l * t", ADJ),
+}
+
+
+def run_against_mutant(tmp_path, fname, old, new, files):
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle")
+    p = tmp_path / "oracle" / fname
+    src = p.read_text()
+    assert src.count(old) == 1, old
+    p.write_text(src.replace(old, new))
+    # the copy comes first on the path: the subprocess starts in it, and the
+    # repository follows for everything else
+    env = dict(os.environ, PYTHONPATH=str(tmp_path) + os.pathsep + ROOT)
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                           "--rootdir", ROOT, *[os.path.join(ROOT, "tests", f) for f in files]], cwd=str(tmp_path),
+                          env=env, capture_output=True, text=True, timeout=600)
+
+
+@pytest.mark.parametrize("name", list(MUTATIONS))
+def test_planted_mistake_fails_a_pin(tmp_path, name):
+    r = run_against_mutant(tmp_path, *MUTATIONS[name])
+    assert r.returncode == 1, r.stdout[-1500:] + r.stderr[-1500:]    # 1: tests ran and failed
+
+
+def test_the_copy_is_what_the_pins_import(tmp_path):
+    """Control: a copy whose oracle raises on import makes the pin run fail to collect."""
+    r = run_against_mutant(tmp_path, "grid.py", "from __future__ import annotations",
+                           "from __future__ import annotations\nraise ImportError('planted')", OP)
+    assert r.returncode != 0 and "planted" in (r.stdout + r.stderr)

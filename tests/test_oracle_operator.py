@@ -175,3 +175,35 @@ def test_coarse_k_restriction():
     ref = np.exp(0.3 * 2 * I - 0.2 * 2 * J + 1.0)
     np.testing.assert_allclose(kc[1:-1, 1:-1], ref[1:-1, 1:-1], rtol=1e-13)
     assert kc.shape == (9, 9)
+
+
+def test_layered_medium_flux_is_exact():
+    """Series resistances: for k that varies only in x and is constant on each
+    node's dual cell, the exact solution of -(k u_x)_x = 0 rises by
+    q (h/2)(1/k_{i-1} + 1/k_i) between neighbouring nodes (the integral of q/k).
+    A two-point flux with the harmonic-mean face reproduces that flux exactly, so
+    A u vanishes wherever the stencil sees only interior nodes."""
+    n = 15
+    h = spacing(n)
+    rng = np.random.default_rng(3)
+    kx = 10.0 ** rng.uniform(-2.0, 2.0, size=n + 2)          # one value per column, boundary ring included
+    k = np.tile(kx, (n + 2, 1))
+    u = np.zeros(n + 2)
+    for i in range(1, n + 2):
+        u[i] = u[i - 1] + 0.5 * h * (1.0 / kx[i - 1] + 1.0 / kx[i])
+    U = np.tile(u[1:-1], (n, 1))                             # interior values, u(x) only
+    Au = op.apply(op.stencil_div(k, (0.0, 0.0)), U)
+    scale = np.max(k) / h ** 2 * np.max(np.abs(U))
+    assert np.max(np.abs(Au[1:-1, 1:-1])) <= 1e-12 * scale
+
+
+def test_coarse_k_restriction_weights_on_a_quadratic():
+    """Full weighting (1, 2, 1)/4 of a quadratic adds half the squared fine
+    spacing per direction: log k = c (i^2 + j^2) restricts to
+    c ((2I)^2 + (2J)^2) + c at coarse nodes whose fine neighbourhood exists."""
+    m, c = 17, 0.01
+    j, i = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    kc = op.restrict_k(np.exp(c * (i ** 2 + j ** 2)))
+    J, I = np.meshgrid(np.arange(kc.shape[0]), np.arange(kc.shape[0]), indexing="ij")
+    ref = c * ((2 * I) ** 2 + (2 * J) ** 2) + c
+    np.testing.assert_allclose(np.log(kc)[1:-1, 1:-1], ref[1:-1, 1:-1], rtol=1e-12, atol=1e-12)
