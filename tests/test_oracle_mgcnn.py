@@ -117,6 +117,17 @@ def test_setup_features_are_scale_free():
     np.testing.assert_allclose(f2[4] - f1[4], 2.0, rtol=1e-12)
 
 
+@pytest.mark.parametrize("n", [7, 31, 127])
+def test_setup_features_do_not_depend_on_the_grid(n):
+    """For constant k the 5-point stencil is k/h^2 [-1 -1 4 -1 -1]: the ratio
+    features are -1/4 and the log feature log10(h^2 a_C) = log10(4 k) at every
+    grid size, so one set of setup weights serves every level and size."""
+    kappa = 3.7
+    f = mg.setup_features(op.stencil_div(np.full((n + 2, n + 2), kappa), (0, 0)))
+    np.testing.assert_allclose(f[:4], -0.25, rtol=1e-13)
+    np.testing.assert_allclose(f[4], np.log10(4.0 * kappa), rtol=1e-13)
+
+
 def test_gmg_equivalence_with_input_normalisation():
     """With B r = Net(D^{-1} r) the finest-level setup tensors absorb the diagonal
     (s[F_J] = omega, s[F_G] = a_C) and the network is still GMG iterate for iterate."""

@@ -46,7 +46,25 @@ MUTATIONS = {
     "setup tanh without skip": ("mgcnn.py", "            z = t + z\n", "            z = t\n", NET),
     "FGMRES Givens sign": ("krylov.py", "H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]",
                            "H[i + 1, j] = sn[i] * H[i, j] + cs[i] * H[i + 1, j]", KRY),
+    "non-div upwind on the wrong side (y)": ("operator.py", "aS = -lap - max(vy, 0.0) / h", "aS = -lap + min(vy, 0.0) / h", OP),
+    "coarse log k not renormalised at the ring": ("operator.py",
+                                                  "den += w[a] * w[b] * mask[a:a + 2 * mc - 1:2, b:b + 2 * mc - 1:2]",
+                                                  "den += w[a] * w[b]", OP),
+    "bilinear prolongation /2": ("gmg.py", "BILINEAR = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 4.0",
+                                 "BILINEAR = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 2.0", GMG),
+    "setup features not scale-free": ("mgcnn.py", "np.log10(h * h * st.aC)])", "np.log10(st.aC)])", NET),
+    "V(1,0) setup: 1 + omega": ("mgcnn.py", "s[_FG10] = (1.0 - omega) * st.aC if normalised else 1.0 - omega",
+                                "s[_FG10] = (1.0 + omega) * st.aC if normalised else 1.0 + omega", NET),
+    "input normalisation multiplies by D": ("mgcnn.py", "rin = r if d_inv is None else r * d_inv",
+                                            "rin = r if d_inv is None else r / d_inv", NET),
+    "FGMRES update with unpreconditioned directions": ("krylov.py", "u = u + y[i] * Z[i]", "u = u + y[i] * V[i]", KRY),
     "adjoint: s gradient drops x": ("adjoint.py", "sbar_l += x_in * t", "sbar_l += t", ADJ),
+    "adjoint: tanh derivative": ("adjoint.py", "dpre = zb * (1.0 - t * t)", "dpre = zb * (1.0 - t)", ADJ),
+    "adjoint: TCNN gradient from the wrong state": ("adjoint.py",
+                                                    "grads[\"w_P\"] += cn.tcnn_wgrad(keep[\"x_fin\"][l + 1], xb)",
+                                                    "grads[\"w_P\"] += cn.tcnn_wgrad(keep[\"x_down\"][l + 1], xb)", ADJ),
+    "adjoint: input normalisation not applied": ("adjoint.py", "                rbar = rbar * d_inv\n",
+                                                 "                rbar = rbar\n", ADJ),
     "adjoint: skip path dropped": ("adjoint.py", "return xbar + s_l * t", "return s_l * t", ADJ),
 }
 
