@@ -58,6 +58,16 @@ MUTATIONS = {
     "input normalisation multiplies by D": ("mgcnn.py", "rin = r if d_inv is None else r * d_inv",
                                             "rin = r if d_inv is None else r / d_inv", NET),
     "FGMRES update with unpreconditioned directions": ("krylov.py", "u = u + y[i] * Z[i]", "u = u + y[i] * V[i]", KRY),
+    "RCNN taps offset by one": ("convnet.py",
+                                "y += np.tensordot(W[:, :, a, b], x[:, a:a + 2 * nc - 1:2, b:b + 2 * nc - 1:2], axes=([1], [0]))",
+                                "y += np.tensordot(W[:, :, a, b], x[:, b:b + 2 * nc - 1:2, a:a + 2 * nc - 1:2], axes=([1], [0]))",
+                                CONV),
+    "level rule off by one": ("grid.py", "    return m - 1\n", "    return m\n", OP),
+    "GMG-equivalent Jacobi copies not divided by a_C": ("mgcnn.py",
+                                                        "s[_E[k]] = _shift_to_source(-omega * a / st.aC, dy, dx)",
+                                                        "s[_E[k]] = _shift_to_source(-omega * a, dy, dx)", NET),
+    "GMG-equivalent defect copies with the wrong sign": ("mgcnn.py", "s[_G[k]] = _shift_to_source(-a, dy, dx)",
+                                                         "s[_G[k]] = _shift_to_source(a, dy, dx)", NET),
     "adjoint: s gradient drops x": ("adjoint.py", "sbar_l += x_in * t", "sbar_l += t", ADJ),
     "adjoint: tanh derivative": ("adjoint.py", "dpre = zb * (1.0 - t * t)", "dpre = zb * (1.0 - t)", ADJ),
     "adjoint: TCNN gradient from the wrong state": ("adjoint.py",
