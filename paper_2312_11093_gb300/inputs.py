@@ -97,12 +97,15 @@ def channelised_k(n: int, rng: np.random.Generator, corr_len: float = 0.02,
 
 
 def paper_white_noise_mu(n: int, rng: np.random.Generator, Re: float = 1000.0) -> np.ndarray:
-    """The paper's coefficient generator (Sec. 4.1): white noise mapped linearly to
-    a power in [0, log10 Re], then coef = 10^(-power) in [1/Re, 1]; returned on the
-    n x n interior nodes."""
+    """The paper's white-noise coefficient (Sec. 4.1) as the diffusion mu of the
+    non-divergence operator on the n x n interior nodes.  The paper draws
+    coef = 1/Re in [1/Re, 1] (white noise mapped linearly to a power in
+    [0, log10 Re], then 10^(-power)) and its stencil is
+    (1/h){coef [0 -1 0; -1 4 -1; 0 -1 0] + v . K_upwind} (Sec. 2.5), i.e.
+    coef = mu / h: so mu = coef h, and Re is the mesh Reynolds number."""
     w = rng.uniform(0.0, 1.0, size=(n, n))
     power = w * np.log10(Re)
-    return 10.0 ** (-power)
+    return 10.0 ** (-power) / (n + 1)
 
 
 def _resize_linear(a: np.ndarray, size: int) -> np.ndarray:
@@ -146,8 +149,9 @@ def _mldata_levels(size: int, init_size: int) -> int:
 
 
 def paper_mldata_mu(n: int, rng: np.random.Generator, Re: float = 1000.0, init_size: int = 5) -> np.ndarray:
-    """Non-divergence coefficient mu on the n x n interior nodes from multi-level data."""
-    return paper_coefficient(multilevel_noise(n, _mldata_levels(n, init_size), rng, init_size), Re)
+    """Non-divergence mu on the n x n interior nodes from multi-level data: the
+    paper's coef in [1/Re, 1] times h (coef = mu / h, as for the white noise)."""
+    return paper_coefficient(multilevel_noise(n, _mldata_levels(n, init_size), rng, init_size), Re) / (n + 1)
 
 
 def paper_mldata_k(n: int, rng: np.random.Generator, Re: float = 1000.0, init_size: int = 5) -> np.ndarray:

@@ -54,7 +54,9 @@ def test_mldata_fields_are_seeded_and_shaped():
     k = inputs.paper_mldata_k(n, np.random.default_rng(4))
     assert mu.shape == (n, n) and k.shape == (n + 2, n + 2)
     assert np.array_equal(mu, inputs.paper_mldata_mu(n, np.random.default_rng(4)))
-    assert mu.min() >= 1e-3 * (1 - 1e-12) and mu.max() <= 1.0 + 1e-15
+    coef = mu * (n + 1)                                     # the paper's coef = mu / h
+    assert np.isclose(coef.min(), 1e-3, rtol=1e-12) and np.isclose(coef.max(), 1.0, rtol=1e-15)
+    assert k.min() >= 1e-3 * (1 - 1e-12) and k.max() <= 1.0 + 1e-15
     # smoother than white noise: neighbouring values are strongly correlated
     d = np.diff(np.log10(mu), axis=1)
     assert np.std(d) < 0.25 * np.std(np.log10(mu))

@@ -1,4 +1,6 @@
 """Pins for the oracle's classical GMG (Sec. 2.3) and its outer stationary loop (Eq. 1)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -98,3 +100,35 @@ def test_symmetric_vcycle_for_a_symmetric_operator():
         assert np.abs(B - B.T).max() <= 1e-13 * np.abs(B).max()
     B = dense(2, 1)
     assert np.abs(B - B.T).max() > 1e-3 * np.abs(B).max()
+
+
+def _paper_gmg_iterations():
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_gmg_iterations.txt")
+    out = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            n, v = line.split(":")
+            out[int(n)] = float(v)
+    return out
+
+
+@pytest.mark.parametrize("n", [31, 63, 127, 255])
+def test_paper_gmg_iteration_counts(n):
+    """The paper's GMG column (Table channels_double) on its own test problem: the
+    oracle's non-divergence operator (coef = mu / h, Sec. 2.5) with white-noise
+    coef in [1e-3, 1], v = (sin 0.5, cos 0.5), f = 1, and GMG with the paper's
+    settings (weight 0.67, three pre- and three post-sweeps, level = log2(n+1) - 3,
+    the coarsest grid smoothed) needs within 15% of the printed mean iteration
+    count to 1e-8 (mean over three draws here, ten there)."""
+    paper = _paper_gmg_iterations()[n]
+    v = (np.sin(0.5), np.cos(0.5))
+    its = []
+    for rep in range(3):
+        rng = np.random.default_rng(100 * n + rep)
+        mu = inputs.paper_white_noise_mu(n, rng)
+        sts = op.level_stencils_nondiv(mu, v, num_levels(n) - 2)
+        _, it, hist, _ = gmg.stationary_solve(sts, inputs.unit_rhs(n), None, 1e-8, 300, 3, 3, 0.67)
+        assert hist[-1] <= 1e-8
+        its.append(it)
+    assert abs(np.mean(its) - paper) <= 0.15 * paper, (its, paper)
