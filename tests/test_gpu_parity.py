@@ -471,3 +471,41 @@ def test_tile_option_range(M):
         with pytest.raises(M.MGCNNError) as ei:
             sv.set_option(sv.OPT_TILE, bad)
         assert ei.value.status == M.ERR_ARG
+
+
+# ---- the paper's own test problem: non-divergence form, white-noise coefficient ----
+PAPER_V = (float(np.sin(0.5)), float(np.cos(0.5)))
+
+
+@pytest.mark.parametrize("n", [31, 127])
+def test_nondiv_operator_all_levels(M, n):
+    """The non-divergence operator (Sec. 2.5; mu = coef h with the paper's
+    white-noise coef) on every level, coarse mu injected, against the oracle."""
+    mu = inputs.paper_white_noise_mu(n, np.random.default_rng(600 + n))
+    sv = M.Solver(8, 1, 1, pde="nondiv", b=PAPER_V)
+    sv.set_weights(np.zeros(sv.weight_count))
+    sv.setup(mu.ravel().copy(), n)
+    ref = oop.level_stencils_nondiv(mu, PAPER_V, num_levels(n))
+    for l, (st, nl) in enumerate(zip(ref, level_sizes(n))):
+        got = sv.get_operator(l, nl).reshape(5, nl, nl)
+        for g, r in zip(got, [st.aC, st.aW, st.aE, st.aS, st.aN]):
+            assert np.max(np.abs(g - r)) <= 1e-14 * np.max(np.abs(st.aC)), l
+
+
+def test_gpu_gmg_on_the_papers_problem(M):
+    """The GPU GMG with the paper's GMG settings (weight 0.67, three sweeps, two
+    levels fewer than MGCNN) on the paper's test problem at 255^2: the oracle's
+    cycle count (which matches the paper's printed 25.9 within 15%) and 1e-8."""
+    n = 255
+    mu = inputs.paper_white_noise_mu(n, np.random.default_rng(100 * n))
+    f = inputs.unit_rhs(n)
+    L = num_levels(n) - 2
+    sts = oop.level_stencils_nondiv(mu, PAPER_V, L)
+    _, it_o, hist_o, _ = ogmg.stationary_solve(sts, f, None, 1e-8, 300, 3, 3, 0.67)
+    sv = M.Solver(8, 1, 1, pde="nondiv", b=PAPER_V, levels=L)
+    sv.set_weights(np.zeros(sv.weight_count))
+    sv.setup(mu.ravel().copy(), n)
+    u = np.zeros(n * n)
+    st, it, hist = sv.gmg_solve(f.ravel().copy(), u, 1e-8, 300, 3, 3, 0.67)
+    assert st == M.OK and it == it_o
+    assert np.allclose(hist, hist_o, rtol=1e-9, atol=0.0)
