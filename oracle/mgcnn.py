@@ -214,8 +214,9 @@ def solve_phase_symmetric(weights: dict, s: list[np.ndarray], r: np.ndarray) -> 
 #   B = sum_l 4^l R_l^T (omega D_l^{-1}) R_l  +  eps^2 sum_l R_l^T R_l,
 # the BPX form sum_l P_l D_l^{-1} P_l^T with P_l = 4^l R_l^T (bilinear
 # prolongation) and Jacobi-scaled levels (D_l: diagonal of the rediscretised
-# level-l operator), plus a term of relative size eps^2 h^2 that eps = 2^-26
-# makes negligible.  Channels 2.. stay zero.
+# level-l operator), plus a term eps^2 a_C,l / (omega 4^l) times the level's
+# smoother term, at most 4 eps^2 k (n+1)^2 / omega: below 1e-6 with eps = 2^-26
+# up to 4095^2 for k <= 50.  Channels 2.. stay zero.
 BPX_EPS = 2.0 ** -26
 
 
