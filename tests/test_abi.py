@@ -69,3 +69,23 @@ def test_bpx_eps_matches_the_header():
     text = open(os.path.join(ROOT, "include", "mgcnn.h")).read()
     m = re.search(r"#define MGCNN_BPX_EPS (\S+)", text)
     assert m and float.fromhex(m.group(1)) == mgcnn.BPX_EPS
+
+
+def test_product_code_does_not_use_the_oracle():
+    """Only tests/, __graft_entry__.smoke() and bench.py's CPU legs may use oracle/:
+    nothing in the package imports it, and bench.py imports it only inside the
+    function that times it on the host."""
+    pkg = os.path.join(ROOT, "paper_2312_11093_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f), errors="replace").read()
+                assert not re.search(r"^\s*(import oracle|from oracle)", text, re.M), f
+    lines = open(os.path.join(ROOT, "bench.py")).read().splitlines()
+    current = None
+    for line in lines:
+        m = re.match(r"def (\w+)\(", line)
+        if m:
+            current = m.group(1)
+        if re.match(r"\s*(import oracle|from oracle)", line):
+            assert current == "cpu_reference", line
