@@ -16,6 +16,7 @@ CONV = ["test_oracle_convnet.py"]
 NET = ["test_oracle_mgcnn.py"]
 KRY = ["test_oracle_krylov.py"]
 ADJ = ["test_oracle_adjoint.py"]
+SETUP = ["test_oracle_setup.py"]
 
 MUTATIONS = {
     "face k arithmetic instead of harmonic": ("operator.py", "return 2.0 * a * b / (a + b)", "return 0.5 * (a + b)", OP),
@@ -76,15 +77,33 @@ MUTATIONS = {
     "adjoint: input normalisation not applied": ("adjoint.py", "                rbar = rbar * d_inv\n",
                                                  "                rbar = rbar\n", ADJ),
     "adjoint: skip path dropped": ("adjoint.py", "return xbar + s_l * t", "return s_l * t", ADJ),
+    "setup RCNN restricts the NonLinearResNet output": ("mgcnn.py", "c = cn.rcnn(c, weights[\"sw_R\"])",
+                                                       "c = cn.rcnn(z, weights[\"sw_R\"])", SETUP),
+    "setup RCNN restricts the scaled setup output": ("mgcnn.py", "c = cn.rcnn(c, weights[\"sw_R\"])",
+                                                    "c = cn.rcnn(outs[-1], weights[\"sw_R\"])", SETUP),
+    "level scaling in front of the NonLinearResNet": (
+        "mgcnn.py",
+        [("        z = c\n        zl, tl = [], []\n",
+          "        z = c / stencils[l].aC if int(scale_by_diag) == 1 else c\n        zl, tl = [], []\n"),
+         ("outs.append(z / stencils[l].aC)", "outs.append(z)")],
+        None, SETUP),
+    "three setup layers": ("mgcnn.py", "SETUP_LAYERS = 4", "SETUP_LAYERS = 3", SETUP),
+    "setup bias outside the tanh": ("mgcnn.py", "t = np.tanh(cn.conv_same(z, weights[\"sw\"][i], weights[\"sb\"][i]))",
+                                    "t = np.tanh(cn.conv_same(z, weights[\"sw\"][i])) + weights[\"sb\"][i][:, None, None]",
+                                    SETUP),
 }
 
 
 def run_against_mutant(tmp_path, fname, old, new, files):
+    """`old` is one source fragment replaced by `new`, or a list of (old, new)
+    pairs applied together (then `new` is None)."""
     shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle")
     p = tmp_path / "oracle" / fname
     src = p.read_text()
-    assert src.count(old) == 1, old
-    p.write_text(src.replace(old, new))
+    for o, w in (old if new is None else [(old, new)]):
+        assert src.count(o) == 1, o
+        src = src.replace(o, w)
+    p.write_text(src)
     # the copy comes first on the path: the subprocess starts in it, and the
     # repository follows for everything else
     env = dict(os.environ, PYTHONPATH=str(tmp_path) + os.pathsep + ROOT)
