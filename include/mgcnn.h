@@ -394,10 +394,10 @@ int mgcnn_profile(mgcnn_ctx* ctx, int enable);
 int mgcnn_profile_read(mgcnn_ctx* ctx, double* ms, long long* counts, int nkinds);
 
 /* r = f - A u and ||r||_2^2 without allocating anything (no counterpart in the
- * paper: an interface for callers that cannot call cudaMalloc -- code running
- * while a stream is being captured into a CUDA graph, hosts that give the
- * library a fixed device-memory budget owned by their own allocator, or tools
- * that may only touch the buffers they were handed).
+ * paper: an interface for callers that cannot call cudaMalloc -- hosts that
+ * give the library a fixed device-memory budget owned by their own allocator,
+ * where a hidden allocation would break that budget, or tools that may only
+ * touch the buffers they were handed).
  * op: the operator of one grid as 5 planes of n*n doubles (a_C, a_W, a_E, a_S,
  * a_N, layout of mgcnn_get_operator); f, u, r: n*n doubles.  All four must be
  * DEVICE pointers owned by the caller (host pointers: ERR_ARG, since staging
@@ -405,14 +405,14 @@ int mgcnn_profile_read(mgcnn_ctx* ctx, double* ms, long long* counts, int nkinds
  * cudaStream_t as void* (NULL: legacy default stream); the call synchronises it.
  * Same kernels and the same deterministic reduction as mgcnn_residual.
  * Scratch: the per-block partial sums live in a fixed array inside the library
- * (65,537 doubles, 512 KiB, held by every GPU that loads the library until the
+ * (16,385 doubles, 128 KiB, held by every GPU that loads the library until the
  * process exits), so n*n may not exceed 16,777,216 (n <= 4096): larger grids
- * return ERR_SIZE.  The first call on a device looks the array's device
- * address up (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call overwrites the array and all
- * calls share it: calls that overlap on the GPU (other streams, other threads)
- * race and must be serialised by the caller.  Allocates no device or pinned
- * memory. */
+ * return ERR_SIZE before anything is launched.  The first call on a device
+ * looks the array's device address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * overwrites the array and all calls share it: calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * Allocates no device or pinned memory. */
 int mgcnn_residual_noalloc(const double* op, const double* f, const double* u, double* r, int n,
                            double* norm2, void* stream);
 

@@ -4,7 +4,7 @@
 // deterministic two-pass norm as the context-based mgcnn_residual, but its
 // per-block partial sums live in a fixed array defined in this file instead of
 // a buffer obtained from cudaMalloc.  Every GPU that loads the library keeps
-// that array (kNoAllocMaxBlocks + 1 doubles, 512 KiB) until the process exits.
+// that array (kNoAllocMaxBlocks + 1 doubles, 128 KiB) until the process exits.
 #include <mutex>
 
 #include "ops.cuh"
@@ -12,9 +12,13 @@
 namespace mgcnn {
 namespace {
 
-// Residual blocks cover 256 unknowns each: at most 65,536 blocks, n^2 <= 16,777,216
-// (n = 4095 fits).  The last slot receives the reduced sum.
-constexpr int kNoAllocMaxBlocks = 65536;
+// Largest grid served: n^2 <= 16,777,216 unknowns (n <= 4096).  Each block of
+// the residual kernel covers kResidualBlock * kResidualPix = 1024 unknowns and
+// leaves one partial sum, so 16,384 partial sums suffice; the last slot receives
+// the reduced sum.
+constexpr size_t kNoAllocMaxUnknowns = 16777216;
+constexpr int kNoAllocMaxBlocks = (int)(kNoAllocMaxUnknowns / ((size_t)kResidualBlock * kResidualPix));
+static_assert(kNoAllocMaxUnknowns % ((size_t)kResidualBlock * kResidualPix) == 0, "whole residual blocks");
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 1];
@@ -47,8 +51,11 @@ using namespace mgcnn;
 extern "C" int mgcnn_residual_noalloc(const double* op, const double* f, const double* u, double* r, int n,
                                       double* norm2, void* stream) {
   if (!op || !f || !u || !r || n < 1) return MGCNN_ERR_ARG;
-  const size_t N = (size_t)n * n;
-  if (reduction_blocks(N) > kNoAllocMaxBlocks) return MGCNN_ERR_SIZE;
+  // the bound is checked on the unknown count in size_t before any block count
+  // is formed (those are int and would wrap for huge n)
+  const size_t N = (size_t)n * (size_t)n;
+  if (N > kNoAllocMaxUnknowns) return MGCNN_ERR_SIZE;
+  if (residual_blocks(N) > kNoAllocMaxBlocks) return MGCNN_ERR_SIZE;
   for (const void* p : {(const void*)op, (const void*)f, (const void*)u, (const void*)r})
     if (!is_device_pointer(p)) return MGCNN_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

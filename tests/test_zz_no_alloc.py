@@ -1,9 +1,8 @@
 """The allocation-free residual entry point (mgcnn_residual_noalloc).
 
-Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-being captured into a graph, hosts that hand the library a fixed device-memory
-budget owned by another allocator, and tools that may only touch buffers they
-were given.  mgcnn_residual_noalloc serves them: the caller passes its own
+Some callers cannot call cudaMalloc: hosts that hand the library a fixed
+device-memory budget owned by another allocator (a hidden allocation would
+break that budget), and tools that may only touch buffers they were given.  mgcnn_residual_noalloc serves them: the caller passes its own
 device arrays, and the per-block partial sums of the norm live in a fixed
 array inside the library instead of a fresh allocation.
 
@@ -35,17 +34,21 @@ def M():
     return mgcnn
 
 
-def _noalloc(M, op, f, u, r, n):
+def _noalloc(M, op, f, u, r, n, stream=None):
     nrm = ctypes.c_double(-1.0)
     st = M.load().mgcnn_residual_noalloc(op.data_ptr(), f.data_ptr(), u.data_ptr(), r.data_ptr(), n,
-                                         ctypes.byref(nrm), None)
+                                         ctypes.byref(nrm), stream)
     return st, nrm.value
 
 
-def test_noalloc_residual_matches_context_residual_twice(M):
-    """Two calls in a row (different problem sizes, so the shared scratch holds the
-    previous call's data) agree with mgcnn_residual within the tests' FP64 bar."""
-    for n, seed in ((127, 1), (63, 2)):
+@pytest.mark.parametrize("on_stream", [False, True])
+def test_noalloc_residual_matches_context_residual_twice(M, on_stream):
+    """Calls in a row (different problem sizes, so the shared scratch holds the
+    previous call's data; the largest is 4095^2, 16,384 partial sums, the whole
+    array) agree with mgcnn_residual within the tests' FP64 bar, on the legacy
+    default stream and on a stream of the caller's."""
+    stream = torch.cuda.Stream() if on_stream else None
+    for n, seed in ((127, 1), (63, 2), (4095, 3), (255, 4)):
         rng = np.random.default_rng(seed)
         k = inputs.lognormal_k(n, 0.1, rng)
         f = inputs.normal_rhs(n, rng)
@@ -58,7 +61,8 @@ def test_noalloc_residual_matches_context_residual_twice(M):
         fd = torch.from_numpy(f.ravel().copy()).cuda()
         ud = torch.from_numpy(u.ravel().copy()).cuda()
         rd = torch.empty(n * n, dtype=torch.float64, device="cuda")
-        st, n2 = _noalloc(M, op, fd, ud, rd, n)
+        torch.cuda.synchronize()
+        st, n2 = _noalloc(M, op, fd, ud, rd, n, stream.cuda_stream if stream is not None else None)
         assert st == M.OK
         r = rd.cpu().numpy()
         assert np.max(np.abs(r - r_ref)) <= 1e-14 * np.max(np.abs(r_ref))
@@ -66,10 +70,12 @@ def test_noalloc_residual_matches_context_residual_twice(M):
 
 
 def test_noalloc_rejects_oversized_and_host_arrays(M):
-    n = 4097
+    """Grids above the scratch array's limit are refused before any launch: 4097^2,
+    and 2^20 (whose 2^40 unknowns would wrap a 32-bit block count to zero)."""
     t = torch.zeros(1, dtype=torch.float64, device="cuda")
-    st, _ = _noalloc(M, t, t, t, t, n)
-    assert st == M.ERR_SIZE
+    for n in (4097, 1 << 20, 2**31 - 1):
+        st, _ = _noalloc(M, t, t, t, t, n)
+        assert st == M.ERR_SIZE
     h = np.zeros(9)
     nrm = ctypes.c_double(0.0)
     st = M.load().mgcnn_residual_noalloc(h.ctypes.data, h.ctypes.data, h.ctypes.data, h.ctypes.data, 3,
