@@ -26,8 +26,13 @@ def test_reference_line_keeps_the_contract():
     for key in ("metric", "value", "n_gpus", "steps", "ms_per_step", "scaling", "vs_baseline", "dtype", "data",
                 "config", "cpu_baseline", "e2e"):
         assert key in line, key
+    # at a grid no larger than the sample size nothing is extrapolated: the steps
+    # are complete solves and the rate is steps / wall
     assert line["value"] > 0 and abs(line["ms_per_step"] - 1e3 / line["value"]) <= 1e-9 * line["ms_per_step"]
+    # the claimed timed work fits inside the run
+    assert line["steps"] * line["ms_per_step"] <= 1e3 * line["wall_s"]
     cb = line["cpu_baseline"]
+    assert cb["measured"]["solves"] == line["steps"] and cb["measured"]["n"] == 63
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
