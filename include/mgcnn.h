@@ -368,7 +368,15 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * mgcnn_solve_krylov; the batched solves keep their own timing.
  * MGCNN_OPT_SYMMETRIC (default 0): the symmetric network variant, see
  * mgcnn_setup_bpx; 1 on, 0 off (weights stay as they are). */
-enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3, MGCNN_OPT_SYMMETRIC = 4 };
+/* MGCNN_OPT_FUSED_RESIDUAL (default 0): where the fused kernels apply,
+ * mgcnn_solve computes each cycle's FP64 residual r = f - A u and its norm
+ * inside the finest-level down kernel (on that kernel's tiles and their halo)
+ * instead of in a separate residual pass; same FP64 arithmetic per unknown
+ * (bit-identical iterates), the norm summed in a different order.  Off by
+ * default: the halo recomputation and the kernel's plain FP64 loads make it
+ * slower than the separate pass. */
+enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3, MGCNN_OPT_SYMMETRIC = 4,
+       MGCNN_OPT_FUSED_RESIDUAL = 5 };
 int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).

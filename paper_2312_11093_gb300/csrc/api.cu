@@ -383,7 +383,7 @@ Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
     }
   }
   const size_t N0 = c->lv[0].N();
-  MG_TRY(ensure(c->partial, (size_t)reduction_blocks(N0) * sizeof(double)));
+  MG_TRY(ensure(c->partial, std::max((size_t)reduction_blocks(N0), fused_partials_max(c->lv[0].n)) * sizeof(double)));
   MG_TRY(ensure(c->r, N0 * sizeof(double)));
   MG_TRY(ensure(c->e, N0 * sizeof(double)));
   // coefficient in, checked positive and finite
@@ -783,14 +783,21 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
     }
     Status result;
     const bool mixed = c->cfg.precision == MGCNN_PREC_MIXED_BF16;
+    // mixed path with the fused kernels: the finest down kernel computes r_k itself
+    const bool fres = fused_residual_applies(c);
+    if (fres) MG_TRY(fused_cycle_setup(c, df, du, c->scalars.as<double>() + 1));
     for (int k = 0;; ++k) {
-      // mixed: the V-cycle consumes an FP32 copy of r (scaled in-kernel), FP64 r is not stored
-      const int ps = prof_begin(c, kProfResidual);
-      MG_TRY(launch_residual(df, du, c->op[0].as<double>(), mixed ? nullptr : c->r.as<double>(),
-                             mixed ? c->r32.as<float>() : nullptr, c->partial.as<double>(), c->n, c->stream,
-                             c->cfg.input_diag ? c->dinv32.as<float>() : nullptr));
-      prof_end(c, ps);
-      MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), c->scalars.as<double>(), c->stream));
+      if (fres) {
+        MG_TRY(fused_cycle_residual(c, df, du, c->scalars.as<double>(), nullptr, c->stream, true));
+      } else {
+        // mixed: the V-cycle consumes an FP32 copy of r (scaled in-kernel), FP64 r is not stored
+        const int ps = prof_begin(c, kProfResidual);
+        MG_TRY(launch_residual(df, du, c->op[0].as<double>(), mixed ? nullptr : c->r.as<double>(),
+                               mixed ? c->r32.as<float>() : nullptr, c->partial.as<double>(), c->n, c->stream,
+                               c->cfg.input_diag ? c->dinv32.as<float>() : nullptr));
+        prof_end(c, ps);
+        MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), c->scalars.as<double>(), c->stream));
+      }
       double rn2 = 0.0;
       MG_TRY(read_scalar(c, 0, &rn2));
       const double rel = std::sqrt(rn2 / fn2);
@@ -805,7 +812,9 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
         result = make_status(MGCNN_NOT_CONVERGED, "no convergence in %d cycles (relres %.3e)", maxit, rel);
         break;
       }
-      if (mixed)
+      if (fres)
+        MG_TRY(fused_cycle_rest(c, du, c->scalars.as<double>(), nullptr, c->stream, true));
+      else if (mixed)
         MG_TRY(vcycle_mixed_r32(c, c->r32.as<float>(), c->scalars.as<double>(), du, du));
       else
         MG_TRY(vcycle_fp64(c, c->r.as<double>(), du, du));
@@ -988,6 +997,11 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
       return finish(c, {});
     case MGCNN_OPT_DEVICE_LOOP:
       c->device_loop = value ? 1 : 0;
+      return finish(c, {});
+    case MGCNN_OPT_FUSED_RESIDUAL:
+      c->fuse_residual = value ? 1 : 0;
+      c->sgraph_valid = false;
+      c->tuned = c->tile_fixed >= 0;   // the finest down kernel is tuned in the mode it runs in
       return finish(c, {});
     case MGCNN_OPT_SYMMETRIC: {
       if (value != 0 && value != 1) return finish(c, make_status(MGCNN_ERR_ARG, "symmetric option is 0 or 1"));

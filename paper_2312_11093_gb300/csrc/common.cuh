@@ -112,6 +112,7 @@ struct mgcnn_ctx {
   // mixed-precision path (mixed.cu)
   int cp = 0;                             // channels padded for the tensor cores (8 or 16)
   int fused = 1;                          // use the fused level kernels when they apply
+  int fuse_residual = 0;                  // mgcnn_solve: the finest down kernel computes the residual
   int tile_var[2][mgcnn::kMaxLevels] = {};  // autotuned tile variants (down, up) per level
   bool tuned = false;                       // set by the first solve after a setup
   int tile_fixed = -1;                      // MGCNN_OPT_TILE: a fixed tile variant, or -1 (autotune)
@@ -155,8 +156,9 @@ struct mgcnn_ctx {
   cudaStream_t bstream = nullptr;
   cudaEvent_t bfork = nullptr;
   cudaGraphExec_t bgraph = nullptr;
+  bool bwhile = false;                    // bgraph is the whole batch (WHILE node), not one cycle
   long long bgraph_kernels = 0;
-  mgcnn::DevBuf bparams, bcount;
+  mgcnn::DevBuf bparams, bcount;         // bcount: [0] problems active after this cycle's checks, [1] cycles
   int* h_bcount = nullptr;
   // optional per-kernel timing (mgcnn_profile)
   int prof = 0;

@@ -41,7 +41,7 @@ struct MixLayout {
   size_t w_in = 0, w_out = 0, w_P = 0;   // byte offsets of FP32 arrays
   size_t s_frag = 0, s_fp = 0;           // setup network: 5 fragment blocks, FP32 biases + W_cin (CP = 8)
   size_t out_hi = 0, out_lo = 0;         // W_out fragments for the fused up kernel (CP = 8)
-  size_t tcnn = 0;                       // TCNN fragments by parity class (CP = 8)
+  size_t tcnn = 0;                       // TCNN fragments of the 2 x 2 fine-pixel quads (CP = 8)
   size_t bytes = 0;
 };
 
@@ -61,7 +61,7 @@ MixLayout mix_layout(const mgcnn_ctx* c) {
   m.s_fp = o;   o += (4 * 8 + 8 * kFeatures * 9 + 8) * 4;
   m.out_hi = o; o += m.frag_words * 4;
   m.out_lo = o; o += m.frag_words * 4;
-  m.tcnn = o;   o += m.frag_words * 4;
+  m.tcnn = o;   o += (size_t)kTcnnQuadRegs * 32 * 4;
   m.bytes = o;
   return m;
 }
@@ -78,24 +78,29 @@ uint16_t f2bf_host(float f) {
 // B[k][n] with k = tap * CP + ci (zero for ci >= C), n = co (zero for co >= C).
 // Per lane (g = lane/4, q = lane%4) a 32-bit register holds B[k0][n], B[k0+1][n]
 // (low half = lower k) with k0 = 16 s + 2 q (first) or + 8 (second register).
-// B fragments of the TCNN W[ci][co][a][b] for the fused up kernel's parity-class
-// GEMMs: steps (taps 0, 2), (6, 8), (1, 7), (3, 5) as m16n8k16 (k 0-7 = first
-// tap's input channels, k 8-15 = second's) and tap 4 as m16n8k8; n = co.
+// B fragments of the TCNN W[ci][co][a][b] for the fused up kernel's quad GEMM.
+// A quad is the 2 x 2 block of fine pixels (2J+1+r, 2I+1+c), r, c in {0, 1};
+// it receives the transposed convolution from the coarse pixels (J+dJ, I+dI),
+// dJ, dI in {0, 1}, through tap (1 + r - 2 dJ, 1 + c - 2 dI) (zero weight where
+// that tap lies outside 0..2).  A rows are quads, k = (dJ, dI, ci): k step dJ
+// holds (dI = 0, ci) at k 0-7 and (dI = 1, ci) at k 8-15; n-tile t = 2 r + c is
+// fine pixel (r, c), n = co.  Register index (2 t + dJ) * 2 + half.
 void pack_tcnn_frags(const double* W, int C, uint32_t* out) {
-  auto B = [&](int tap, int ci, int co) -> float {
-    return (ci < C && co < C) ? (float)W[((size_t)ci * C + co) * 9 + tap] : 0.0f;
+  auto B = [&](int a, int b, int ci, int co) -> float {
+    if (a < 0 || a > 2 || b < 0 || b > 2 || ci >= C || co >= C) return 0.0f;
+    return (float)W[((size_t)ci * C + co) * 9 + a * 3 + b];
   };
-  auto pair = [&](int tap, int ci, int co) -> uint32_t {
-    return (uint32_t)f2bf_host(B(tap, ci, co)) | ((uint32_t)f2bf_host(B(tap, ci + 1, co)) << 16);
-  };
-  const int steps[4][2] = {{0, 2}, {6, 8}, {1, 7}, {3, 5}};
   for (int lane = 0; lane < 32; ++lane) {
     const int g = lane >> 2, q = lane & 3;
-    for (int s = 0; s < 4; ++s) {
-      out[(2 * s + 0) * 32 + lane] = pair(steps[s][0], 2 * q, g);
-      out[(2 * s + 1) * 32 + lane] = pair(steps[s][1], 2 * q, g);
+    for (int t = 0; t < 4; ++t) {
+      const int r = t >> 1, c = t & 1;
+      for (int dJ = 0; dJ < 2; ++dJ)
+        for (int dI = 0; dI < 2; ++dI) {
+          const int a = 1 + r - 2 * dJ, b = 1 + c - 2 * dI;
+          out[((2 * t + dJ) * 2 + dI) * 32 + lane] = (uint32_t)f2bf_host(B(a, b, 2 * q, g)) |
+                                                     ((uint32_t)f2bf_host(B(a, b, 2 * q + 1, g)) << 16);
+        }
     }
-    out[8 * 32 + lane] = pair(4, 2 * q, g);
   }
 }
 

@@ -21,7 +21,16 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega);
 void mixed_release(mgcnn_ctx* c);
 // mixed_fused.cu: fused level kernels (8 channels, one layer per ResNet)
 constexpr int kFusedVariants = 5;        // tile shapes 16x32, 8x32, 16x16, 32x32, 24x32
+constexpr int kTcnnQuadRegs = 16;        // TCNN B fragments per lane: 4 fine pixels x 2 k steps x 2
 class TmaMaps;
+// Inputs of the finest down kernel when it computes the residual itself.
+struct ResidIn {
+  const double* u = nullptr;             // n^2
+  const double* f = nullptr;             // n^2
+  const double* op = nullptr;            // 5 n^2 (a_C, a_W, a_E, a_S, a_N)
+  const float* dinv32 = nullptr;         // optional n^2: the network input is D^{-1} r
+  double* partial = nullptr;             // per block: sum of r^2 over its owned pixels
+};
 struct FusedLevels {
   int L = 0, batch = 1;
   TmaMaps* maps = nullptr;               // tensor-map cache of the owner (context or batch class)
@@ -37,14 +46,26 @@ struct FusedLevels {
 struct FusedWeights {
   const uint32_t *f_down, *f_up, *f_R;   // mma B fragments (device)
   const uint32_t *f_out_hi, *f_out_lo;   // W_out as an 8 -> 8 layer (output channel 0), BF16 hi + lo parts
-  const uint32_t* f_tcnn;                // TCNN by pixel-parity class (taps 0,2 | 6,8 | 1,7 | 3,5 | 4)
+  const uint32_t* f_tcnn;                // TCNN of 2 x 2 fine-pixel quads (kTcnnQuadRegs x 32 words)
   SmallWeights small;                    // by value, see SmallWeights
+};
+struct FusedCycleOpt {
+  bool after_fused_down0 = false;        // the finest down kernel ran already, with the residual fused in
 };
 Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
                            const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
-                           mgcnn_ctx* prof_ctx);
+                           mgcnn_ctx* prof_ctx, FusedCycleOpt opt = {});
+// The finest down kernel with the residual fused in: r = f - A u (FP64) on the
+// kernel's tiles, r^2 partial sums (one per block, fused_down0_blocks of them)
+// into ra.partial, then the level as usual with the input scale already in
+// fl.alpha (fused_set_alpha).  One problem only.
+Status fused_down0_resid(const FusedLevels& fl, const ResidIn& ra, const FusedWeights& w, const int* active,
+                         cudaStream_t st, mgcnn_ctx* prof_ctx);
+Status fused_set_alpha(const FusedLevels& fl, const double* norm2, cudaStream_t st);
+int fused_down0_blocks(int n, int variant);
+size_t fused_partials_max(int n);          // the largest fused_down0_blocks over the tile variants
 Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, double* scratch,
-                      const FusedWeights& w, cudaStream_t st, int reps);
+                      const FusedWeights& w, cudaStream_t st, int reps, const ResidIn* ra = nullptr);
 // Pointers into ctx->wmix for the fused kernels (valid after mixed_set_weights).
 FusedWeights fused_weights(const mgcnn_ctx* c);
 bool fused_supported(const mgcnn_ctx* c);
@@ -60,6 +81,23 @@ Status setup_fused_levels(int L, const int* n, int batch, const double* const* o
 Status pad_setup_bf16(const float* src, __nv_bfloat16* dst, size_t N, int C, int cp, cudaStream_t st);
 Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
                         const FusedWeights& w);
+// The stationary iteration's cycle with the residual fused into the finest down
+// kernel (mgcnn_solve, mixed path with the fused kernels):
+//   fused_cycle_setup    once per solve: partial-sum space, autotuning, the
+//                        input scale from ||f||^2 (device scalar fn2_dev)
+//   per cycle k:
+//   fused_cycle_residual r_k = f - A u_k and the finest down level; ||r_k||^2
+//                        into rn2_dev
+//   (convergence test on rn2_dev)
+//   fused_cycle_rest     levels 1.. down, all levels up, u += B r_k; the next
+//                        input scale from rn2_dev
+// `active` (nullable) is the device flag that makes the kernels return at once.
+bool fused_residual_applies(const mgcnn_ctx* c);
+Status fused_cycle_setup(mgcnn_ctx* c, const double* f, const double* u, const double* fn2_dev);
+Status fused_cycle_residual(mgcnn_ctx* c, const double* f, const double* u, double* rn2_dev, const int* active,
+                            cudaStream_t st, bool profile);
+Status fused_cycle_rest(mgcnn_ctx* c, double* u, const double* rn2_dev, const int* active, cudaStream_t st,
+                        bool profile);
 // Defined in api.cu: Algorithm 2 in FP32 into out[l] ([n_l^2][C] floats).
 Status run_setup_net_fp32(mgcnn_ctx* c, float* const* out);
 

@@ -67,36 +67,81 @@ __device__ __forceinline__ void mma1688(float* d, uint32_t a0, uint32_t a1, uint
                : "r"(a0), "r"(a1), "r"(b0));
 }
 
-__device__ __forceinline__ float2 bf2f(uint32_t v) { return __bfloat1622float2(*reinterpret_cast<bf162*>(&v)); }
 __device__ __forceinline__ uint32_t f2bf(float a, float b) {
   bf162 r = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&r);
 }
+// s * x of 8 channels with packed BF16 multiplies: the product of two BF16
+// values is exact in FP32, so rounding it once to BF16 here gives the bits that
+// widening, multiplying in FP32 and rounding back would.
+__device__ __forceinline__ uint32_t bmul2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("mul.rn.bf16x2 %0, %1, %2;\n" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
 __device__ __forceinline__ uint4 mul8(uint4 a, uint4 b) {
-  float2 x, y;
-  uint4 o;
-  x = bf2f(a.x); y = bf2f(b.x); o.x = f2bf(x.x * y.x, x.y * y.y);
-  x = bf2f(a.y); y = bf2f(b.y); o.y = f2bf(x.x * y.x, x.y * y.y);
-  x = bf2f(a.z); y = bf2f(b.z); o.z = f2bf(x.x * y.x, x.y * y.y);
-  x = bf2f(a.w); y = bf2f(b.w); o.w = f2bf(x.x * y.x, x.y * y.y);
-  return o;
+  return make_uint4(bmul2(a.x, b.x), bmul2(a.y, b.y), bmul2(a.z, b.z), bmul2(a.w, b.w));
+}
+
+// Sum of one double per thread over the block (fixed order: warp shuffles, then
+// the warps' sums by warp 0); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  v = (lane < NW) ? red[lane] : 0.0;
+  if (warp == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // The tiles of a block live in dynamic shared memory (the 32 x 32 variant needs
 // more than the 48 KB of static shared memory); every array starts on a 128-byte
 // boundary (TMA destinations).
 constexpr int pad8(int pixels) { return (pixels + 7) / 8 * 8; }   // uint4 count -> multiple of 128 bytes
+// Bytes of the down kernel's layer-output slot: on the finest level it first
+// holds u (FP64) on the residual region plus one pixel when the residual is
+// computed in the kernel.
+template <int FH, int FW, bool FIRST, bool HAS_R>
+constexpr size_t down_xd_bytes() {
+  constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
+  constexpr size_t xd = 16u * pad8(XH * XW), us = (8u * (XH + 6) * (XW + 6) + 127) / 128 * 128;
+  return (FIRST && us > xd) ? us : xd;
+}
 template <int FH, int FW, bool FIRST, bool HAS_R>
 constexpr size_t down_smem_bytes() {
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0), ZH = XH + 2, ZW = XW + 2;
   constexpr int RH = ZH + 2, RW = ZW + 2;
-  return 16u * (2 * pad8(ZH * ZW) + pad8(XH * XW)) + (FIRST ? 4u * RH * RW : 0u);
+  return 16u * (2 * pad8(ZH * ZW)) + down_xd_bytes<FH, FW, FIRST, HAS_R>() + (FIRST ? 4u * RH * RW : 0u);
 }
+// Up-kernel regions for an FH x FW owned tile at (j0, i0), fine coordinates:
+//   O (layer output):   owned + halo H (H = 1 at the finest level, where W_out
+//                       needs the layer output around the owned pixels)
+//   P (layer input):    O + halo 1
+//   Q (staged x_down, s): P, extended by one row / column on each side where
+//                       needed so that it is made of whole quads -- 2 x 2 blocks
+//                       (2J+1.., 2I+1..) of fine pixels -- when a coarser level
+//                       feeds the TCNN (Q starts on an odd row and column)
+//   coarse pixels (J, I) of the quads plus one row and column (the quads'
+//   sources J..J+1, I..I+1)
+template <int FH, int FW, bool LAST, bool HAS_P>
+struct UpGeom {
+  static constexpr int H = LAST ? 1 : 0;
+  static constexpr int OH = FH + 2 * H, OW = FW + 2 * H;
+  static constexpr int PH = OH + 2, PW = OW + 2;
+  static constexpr int QOFF = (HAS_P && LAST) ? 1 : 0;    // P's offset inside Q
+  static constexpr int QH = PH + 2 * QOFF, QW = PW + 2 * QOFF;
+  static constexpr int NQH = QH / 2, NQW = QW / 2;         // quads
+  static constexpr int CQH = NQH + 1, CQW = NQW + 1;       // coarse pixels staged
+  static_assert(!HAS_P || (QH % 2 == 0 && QW % 2 == 0), "whole quads");
+};
+// Tiles: ps, zs on Q; cs; on the finest level os on O.
 template <int FH, int FW, bool LAST, bool HAS_P>
 constexpr size_t up_smem_bytes() {
-  constexpr int H = LAST ? 1 : 0, OH = FH + 2 * H, OW = FW + 2 * H, PH = OH + 2, PW = OW + 2;
-  constexpr int CH = PH / 2 + 2, CW = PW / 2 + 2;
-  return 16u * (2 * pad8(PH * PW) + (HAS_P ? pad8(CH * CW) : 0) + (LAST ? OH * OW : 0));
+  using G = UpGeom<FH, FW, LAST, HAS_P>;
+  return 16u * (2 * pad8(G::QH * G::QW) + (HAS_P ? pad8(G::CQH * G::CQW) : 0) + (LAST ? pad8(G::OH * G::OW) : 0));
 }
 extern __shared__ __align__(128) unsigned char fused_dsm[];
 
@@ -166,14 +211,20 @@ __device__ __forceinline__ uint32_t identity_frag() {
   return (2 * q == g ? one : 0u) | ((2 * q + 1 == g ? one : 0u) << 16);
 }
 
+// The input scale of the network, alpha ~ sqrt(N / ||r||^2), keeps the BF16
+// state near unit size whatever the scale of f.  It is a power of two, so
+// scaling by it and back is exact: the cycle's result does not depend on the
+// norm it was taken from (nor on that norm's summation order).
 __device__ __forceinline__ double alpha_of(const double* norm2, size_t N) {
   const double v = *norm2;
-  return (v > 0.0) ? sqrt((double)N / v) : 1.0;
+  if (!(v > 0.0) || !isfinite(v)) return 1.0;
+  const int e = ilogb(sqrt((double)N / v));
+  return ldexp(1.0, max(-120, min(120, e)));
 }
 
-// alpha2[2b] = alpha = sqrt(N / ||r_b||^2), alpha2[2b + 1] = 1 / alpha, once per
-// cycle and problem: an FP64 divide and square root are dozens of FP64-pipe
-// instructions, too many to repeat in every block of the level kernels.
+// alpha2[2b] = alpha, alpha2[2b + 1] = 1 / alpha, once per cycle and problem:
+// an FP64 square root is dozens of FP64-pipe instructions, too many to repeat
+// in every block of the level kernels.
 __global__ void alpha_kernel(const double* __restrict__ norm2, float* __restrict__ alpha2, size_t N, int batch) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
@@ -194,8 +245,9 @@ Status launch_alpha(const FusedLevels& fl, const double* norm2, cudaStream_t st)
 //   X (layer output kept):   rows 0..XH-1, cols 0..XW-1 (XH = 16 + R, XW = 32 + R)
 //   Z (layer input, halo 1): rows -1..XH,  cols -1..XW
 //   Rg (residual, halo 2):   rows -2..XH+1, cols -2..XW+1   (finest level only)
-template <int FH, int FW, bool FIRST, bool HAS_R>
+template <int FH, int FW, bool FIRST, bool HAS_R, bool RESID>
 __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r, const float* __restrict__ alpha2,
+                                                  const __grid_constant__ ResidIn ra,
                                                   const __grid_constant__ SmallWeights sw,
                                                   const __grid_constant__ CUtensorMap map_x,
                                                   const __grid_constant__ CUtensorMap map_s,
@@ -203,6 +255,7 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
                                                   bf16* __restrict__ xdown, bf16* __restrict__ xc, int n,
                                                   const int* __restrict__ active, int* __restrict__ err) {
   static_assert(FH % 2 == 0 && FW % 2 == 0 && (FH / 2) * (FW / 2) % 16 == 0, "tile shape");
+  static_assert(FIRST || !RESID, "the residual is fused into the finest level only");
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
   constexpr int ZH = XH + 2, ZW = XW + 2;
   constexpr int RH = ZH + 2, RW = ZW + 2;
@@ -212,7 +265,8 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
   uint4* zs = reinterpret_cast<uint4*>(fused_dsm);
   uint4* xs = zs + pad8(ZH * ZW);
   uint4* xd = xs + pad8(ZH * ZW);                                   // layer output
-  float* rs = reinterpret_cast<float*>(xd + pad8(XH * XW));         // finest level only
+  float* rs = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(xd) +
+                                      down_xd_bytes<FH, FW, FIRST, HAS_R>());   // finest level only
   __shared__ __align__(8) uint64_t bar;
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -241,7 +295,45 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
   }
   __syncthreads();   // barrier initialised
 
-  if constexpr (FIRST) {
+  if constexpr (FIRST && RESID) {
+    // r = f - A u (FP64, Eq. 1) on the residual region: the same five FMAs, in
+    // the same order, as the stand-alone residual kernel; u with a halo of one
+    // more pixel is staged in the layer-output tile, which is free until the
+    // layer.  The block's owned pixels add r^2 to its partial sum.
+    constexpr int UH = RH + 2, UW = RW + 2;
+    static_assert(UH * UW * sizeof(double) <= down_xd_bytes<FH, FW, FIRST, HAS_R>(), "u staging");
+    double* us = reinterpret_cast<double*>(xd);
+    for (int e = threadIdx.x; e < UH * UW; e += NT) {
+      const int ur = e / UW, uc = e - ur * UW;
+      const int gj = j0 + ur - 3, gi = i0 + uc - 3;
+      us[e] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? ra.u[(size_t)gj * n + gi] : 0.0;
+    }
+    __syncthreads();
+    const float alpha = alpha2[0];
+    double rr2 = 0.0;
+#pragma unroll 2
+    for (int e = threadIdx.x; e < RH * RW; e += NT) {
+      const int rr = e / RW, cc = e - rr * RW;
+      const int gj = j0 + rr - 2, gi = i0 + cc - 2;
+      float v = 0.f;
+      if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
+        const size_t p = (size_t)gj * n + gi;
+        const double* uc = us + (rr + 1) * UW + cc + 1;
+        double rv = fma(-ra.op[p], uc[0], ra.f[p]);
+        rv = fma(-ra.op[N + p], uc[-1], rv);
+        rv = fma(-ra.op[2 * N + p], uc[1], rv);
+        rv = fma(-ra.op[3 * N + p], uc[-UW], rv);
+        rv = fma(-ra.op[4 * N + p], uc[UW], rv);
+        if (rr >= 2 && rr < 2 + FH && cc >= 2 && cc < 2 + FW) rr2 = fma(rv, rv, rr2);
+        const float rf = f64_to_f32_rn(rv);
+        v = alpha * (ra.dinv32 ? rf * ra.dinv32[p] : rf);
+      }
+      rs[e] = v;
+    }
+    __shared__ double red[NW];
+    rr2 = block_sum_fixed(rr2, red);
+    if (threadIdx.x == 0) ra.partial[blockIdx.y * gridDim.x + blockIdx.x] = rr2;
+  } else if constexpr (FIRST) {
     const float alpha = alpha2[2 * bz];   // the finest level's input scale
     #pragma unroll 4
     for (int e = threadIdx.x; e < RH * RW; e += NT) {
@@ -335,109 +427,69 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
   }
 }
 
-// Shared-memory view of an up-kernel block for the TCNN pass.
-struct TcnnTile {
-  uint4* ps;          // P region: x_down in, x_pre out
-  uint4* zs;          // P region: s in, s * x_pre out
-  const uint4* cs;    // staged coarse pixels (zero outside the coarse grid)
-  int pj0, pi0;       // global coordinates of P's corner
-  int cj0, ci0;       // global coordinates of cs's corner
-  int n;
-};
-
-// TCNN-add on the tensor cores, one parity class (gj & 1 == A, gi & 1 == B) of
-// the fine pixels of P at a time.  A fine row 2J + a gets coarse row J through
-// tap row a: a in {0, 2} for even rows, a = 1 for odd rows (likewise columns),
-// so a class has a fixed tap list -- 4, 2, 2 or 1 taps, i.e. K = 32, 16, 16 or
-// 8 -- and each 16 class pixels are a GEMM [16 x K] x [K x 8]
-// whose A rows are coarse pixels gathered by ldmatrix (per-lane addresses; the
-// zero-filled staging covers coarse pixels outside the grid).  fT holds the B
-// fragments in the step order (taps 0, 2 | 6, 8 | 1, 7 | 3, 5 | 4).
-// Epilogue: x_pre = x_down + TCNN rounded once to BF16, z = s * x_pre.
-template <int A, int B, int PH, int PW, int CW>
-__device__ __forceinline__ void tcnn_class_mma(const TcnnTile& t, const uint32_t* fT, int st, int lane) {
-  // the class's pixels in row-major order over an NRM x NCM grid (class rows
-  // and columns, at most); strips of 16 of them, wrapping across class rows
-  constexpr int NRM = (PH + 1) / 2, NCM = (PW + 1) / 2, NP = NRM * NCM;
-  const int r0 = (A ^ t.pj0) & 1, c0 = (B ^ t.pi0) & 1;   // first P row / column of the class
-  const int nr_cls = (PH - r0 + 1) >> 1, nc_cls = (PW - c0 + 1) >> 1;
-  const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, kh = lane >> 4;
-  // fine pixel of A row m (clamped into the class so that every address is valid)
-  auto fine = [&](int m, int& gj, int& gi) {
-    const int p = min(st * 16 + m, NP - 1);
-    const int rr = p / NCM, cc = p - rr * NCM;
-    gj = t.pj0 + r0 + 2 * min(rr, nr_cls - 1);
-    gi = t.pi0 + c0 + 2 * min(cc, nc_cls - 1);
-  };
-  // shared-memory pixel of coarse (J, I) for fine (gj, gi) through tap (ta, tb)
-  const uint32_t cs0 = sa(t.cs);
-  auto at = [&](int gj, int gi, int ta, int tb) {
-    return cs0 + 16u * ((((gj - ta) >> 1) - t.cj0) * CW + (((gi - tb) >> 1) - t.ci0));
-  };
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  uint32_t a[4];
-  int gj, gi;
-  if constexpr (A == 1 && B == 1) {
-    fine(lane & 15, gj, gi);
-    ldsm_x2(a, at(gj, gi, 1, 1));              // tap (1,1)
-    mma1688(acc, a[0], a[1], fT[8]);
-  } else {
-    fine(mrow, gj, gi);
-    if constexpr (A == 0 && B == 0) {
-      // step 0: taps (0,0) | (0,2); step 1: taps (2,0) | (2,2)
-      ldsm_x4(a, at(gj, gi, 0, kh ? 2 : 0));
-      mma16816(acc, a, fT[0], fT[1]);
-      ldsm_x4(a, at(gj, gi, 2, kh ? 2 : 0));
-      mma16816(acc, a, fT[2], fT[3]);
-    } else if constexpr (A == 0 && B == 1) {
-      ldsm_x4(a, at(gj, gi, kh ? 2 : 0, 1));   // taps (0,1) | (2,1)
-      mma16816(acc, a, fT[4], fT[5]);
-    } else {
-      ldsm_x4(a, at(gj, gi, 1, kh ? 2 : 0));   // taps (1,0) | (1,2)
-      mma16816(acc, a, fT[6], fT[7]);
-    }
-  }
-  const int g = lane >> 2, q = lane & 3;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int p = st * 16 + g + 8 * h;
-    const int rr = p / NCM, cc = p - rr * NCM;
-    const int pr = r0 + 2 * rr, pc = c0 + 2 * cc;
-    const int ogj = t.pj0 + pr, ogi = t.pi0 + pc;
-    if (p >= NP || rr >= nr_cls || cc >= nc_cls || ogj < 0 || ogj >= t.n || ogi < 0 || ogi >= t.n) continue;
-    const int pe = pr * PW + pc;
-    const float2 xin = bf2f(reinterpret_cast<const uint32_t*>(&t.ps[pe])[q]);
-    const uint32_t xo = f2bf(xin.x + acc[2 * h], xin.y + acc[2 * h + 1]);
-    reinterpret_cast<uint32_t*>(&t.ps[pe])[q] = xo;
-    const float2 xf = bf2f(xo), sf = bf2f(reinterpret_cast<const uint32_t*>(&t.zs[pe])[q]);
-    reinterpret_cast<uint32_t*>(&t.zs[pe])[q] = f2bf(xf.x * sf.x, xf.y * sf.y);
-  }
-}
-
-// All four classes, strips spread over the warps.
-template <int PH, int PW, int CW>
-__device__ __forceinline__ void tcnn_mma(const TcnnTile& t, const uint32_t* fT) {
-  constexpr int NRM = (PH + 1) / 2, NCM = (PW + 1) / 2, PER = (NRM * NCM + 15) / 16;
+// TCNN-add on the tensor cores over the quads of Q: each 16 quads are a GEMM
+// [16 x 64] x [64 x 8] per fine pixel (r, c) of the quad, whose A row holds the
+// quad's four coarse sources (J+dJ, I+dI) (k 0-31, gathered by ldmatrix from
+// per-lane addresses) and the fine pixel's own x_down (k 32-63, through an
+// identity block: the U-net skip of Algorithm 3 added in FP32).  Every quad has
+// the same structure, so one set of B fragments serves all of them (fq, see
+// pack_tcnn_frags).  Epilogue: x_pre rounded once to BF16 into ps, z = s * x_pre
+// into zs.  Coarse pixels outside the coarse grid are staged as zeros, which
+// makes the sum zero on every fine pixel outside the fine grid.
+template <class G>
+__device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, const uint4* cs, const uint32_t* __restrict__ fTc) {
+  constexpr int NQ = G::NQH * G::NQW, NS = (NQ + 15) / 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int st = warp; st < 4 * PER; st += NW) {
-    const int cls = st / PER, sl = st - cls * PER;
-    if (cls == 0)
-      tcnn_class_mma<0, 0, PH, PW, CW>(t, fT, sl, lane);
-    else if (cls == 1)
-      tcnn_class_mma<0, 1, PH, PW, CW>(t, fT, sl, lane);
-    else if (cls == 2)
-      tcnn_class_mma<1, 0, PH, PW, CW>(t, fT, sl, lane);
-    else
-      tcnn_class_mma<1, 1, PH, PW, CW>(t, fT, sl, lane);
+  const int g = lane >> 2, q = lane & 3, kh = lane >> 4;
+  const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
+  uint32_t fq[kTcnnQuadRegs];
+#pragma unroll
+  for (int k = 0; k < kTcnnQuadRegs; ++k) fq[k] = fTc[k * 32 + lane];
+  const uint32_t fI = identity_frag();
+  const uint32_t cs0 = sa(cs), ps0 = sa(ps);
+  for (int st = warp; st < NS; st += NW) {
+    // A rows: quad (qr, qc) of this lane's ldmatrix row
+    const int qm = min(st * 16 + mrow, NQ - 1), qr = qm / G::NQW, qc = qm - qr * G::NQW;
+    uint32_t a0[4], a1[4], ax0[4], ax1[4];
+    const uint32_t ca = cs0 + 16u * (qr * G::CQW + qc + kh);
+    ldsm_x4(a0, ca);                                   // sources (J, I) | (J, I+1)
+    ldsm_x4(a1, ca + 16u * G::CQW);                    // sources (J+1, I) | (J+1, I+1)
+    const uint32_t xa = ps0 + 16u * (2 * qr * G::QW + 2 * qc + kh);
+    ldsm_x4(ax0, xa);                                  // x_down of fine (0, 0) | (0, 1)
+    ldsm_x4(ax1, xa + 16u * G::QW);                    // x_down of fine (1, 0) | (1, 1)
+    // this lane's two output quads (rows g and g + 8 of the strip)
+    int pe[2];
+    bool ok[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int qe = st * 16 + g + 8 * h, er = qe / G::NQW, ec = qe - er * G::NQW;
+      ok[h] = qe < NQ;
+      pe[h] = 2 * er * G::QW + 2 * ec;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int r = t >> 1, c = t & 1;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      mma16816(acc, a0, fq[4 * t + 0], fq[4 * t + 1]);
+      mma16816(acc, a1, fq[4 * t + 2], fq[4 * t + 3]);
+      mma16816(acc, r ? ax1 : ax0, c ? 0u : fI, c ? fI : 0u);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!ok[h]) continue;
+        const int e = pe[h] + r * G::QW + c;
+        const uint32_t xo = f2bf(acc[2 * h], acc[2 * h + 1]);
+        reinterpret_cast<uint32_t*>(&ps[e])[q] = xo;
+        uint32_t* zp = reinterpret_cast<uint32_t*>(&zs[e]) + q;
+        *zp = bmul2(xo, *zp);
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Up kernel.  Output tile 16 x 32 at (j0, i0).  H = halo of the layer output
-// that is needed (1 at the finest level for W_out, else 0).
-//   O (layer output):  rows -H..15+H, cols -H..31+H        (OH x OW)
-//   P (layer input x_pre = x_down + TCNN(x_c)): O plus halo 1  (PH x PW)
-//   coarse rows/cols J: floor((j0 - H - 1) / 2) - 1 .. , enough for P
+// Up kernel (geometry in UpGeom).  Level l: x_pre = x_down + TCNN(x_{l+1}) on P
+// (or x_down on the coarsest level), layer x_fin = x_pre + K_up (s * x_pre) on O;
+// finest level: e = W_out * x_fin / alpha, u_out = u_in + e.
 template <int FH, int FW, bool LAST, bool HAS_P>
 __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUtensorMap map_xd,
                                                 const __grid_constant__ CUtensorMap map_s,
@@ -448,19 +500,17 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
                                                 const float* __restrict__ alpha2, const double* __restrict__ u_in,
                                                 bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
                                                 const int* __restrict__ active, int* __restrict__ err) {
-  constexpr int H = LAST ? 1 : 0;
-  constexpr int OH = FH + 2 * H, OW = FW + 2 * H;
-  constexpr int PH = OH + 2, PW = OW + 2;
-  constexpr int CH = PH / 2 + 2, CW = PW / 2 + 2;   // coarse rows / cols staged
-  // TMA destinations (zero outside the grid): ps = x_down on P, then x_pre;
-  // zs = s on P, then s * x_pre; cs = the coarse pixels under P
+  using G = UpGeom<FH, FW, LAST, HAS_P>;
+  constexpr int H = G::H, OH = G::OH, OW = G::OW, QW = G::QW, QOFF = G::QOFF;
+  // TMA destinations (zero outside the grid): ps = x_down on Q, then x_pre;
+  // zs = s on Q, then s * x_pre; cs = the quads' coarse pixels
   uint4* ps = reinterpret_cast<uint4*>(fused_dsm);
-  uint4* zs = ps + pad8(PH * PW);
-  uint4* cs = zs + pad8(PH * PW);                                    // coarser level only
-  uint4* os = cs + (HAS_P ? pad8(CH * CW) : 0);                      // finest level only
+  uint4* zs = ps + pad8(G::QH * QW);
+  uint4* cs = zs + pad8(G::QH * QW);                                   // coarser level only
+  uint4* os = cs + (HAS_P ? pad8(G::CQH * G::CQW) : 0);               // finest level only
   __shared__ __align__(8) uint64_t bar;
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
-  const int pj0 = j0 - H - 1, pi0 = i0 - H - 1;      // global coords of P's corner
+  const int qj0 = j0 - H - 1 - QOFF, qi0 = i0 - H - 1 - QOFF;         // Q's corner (odd when HAS_P)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int bz = blockIdx.z;
   if (active && !active[bz]) return;
@@ -473,20 +523,14 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
       xfin += bz * N * 8;
     }
   }
-  // coarse corner: the smallest J with 2J + 2 >= pj0
-  const int cj0 = (pj0 - 2 >= 0) ? (pj0 - 2) / 2 : -((2 - pj0 + 1) / 2);
-  const int ci0 = (pi0 - 2 >= 0) ? (pi0 - 2) / 2 : -((2 - pi0 + 1) / 2);
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, (2u * PH * PW + (HAS_P ? CH * CW : 0u)) * 16u);
-    tma_load_pix(ps, &map_xd, pi0, pj0, bz, &bar);
-    tma_load_pix(zs, &map_s, pi0, pj0, bz, &bar);
-    if (HAS_P) tma_load_pix(cs, &map_c, ci0, cj0, bz, &bar);
+    mbar_expect_tx(&bar, (2u * G::QH * QW + (HAS_P ? G::CQH * G::CQW : 0u)) * 16u);
+    tma_load_pix(ps, &map_xd, qi0, qj0, bz, &bar);
+    tma_load_pix(zs, &map_s, qi0, qj0, bz, &bar);
+    // the first quad's coarse source: J = (qj0 - 1) / 2 (exact, qj0 odd)
+    if (HAS_P) tma_load_pix(cs, &map_c, (qi0 - 1) / 2, (qj0 - 1) / 2, bz, &bar);
   }
-
-  uint32_t wk[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) wk[k] = fK[k * 32 + lane];
   __syncthreads();   // barrier initialised
   const bool landed = mbar_wait_bounded(&bar, 0);
   if (!__syncthreads_and(landed)) {
@@ -494,31 +538,29 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
     return;
   }
 
-  // x_pre on P: per parity class (gj & 1, gi & 1) of the fine pixel, the TCNN
-  // taps that reach it -- 4, 2, 2 or 1, known at compile time, so the weights are
-  // constant operands -- x_pre = x_down + TCNN(x_c) rounded once, z = s * x_pre.
   if constexpr (HAS_P) {
-    uint32_t fT[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) fT[k] = fTc[k * 32 + lane];
-    const TcnnTile t{ps, zs, cs, pj0, pi0, cj0, ci0, n};
-    tcnn_mma<PH, PW, CW>(t, fT);
+    tcnn_quads<G>(ps, zs, cs, fTc);
   } else {
-    for (int e = threadIdx.x; e < PH * PW; e += NT) zs[e] = mul8(ps[e], zs[e]);
+    for (int e = threadIdx.x; e < G::QH * QW; e += NT) zs[e] = mul8(ps[e], zs[e]);
   }
   __syncthreads();
 
-  // layer on O, row-aligned strips as in the down kernel
+  // layer on O: strips of 16 pixels of O in row-major order (a strip may wrap
+  // to the next row); O pixel (orow, ocol) reads the taps around Q pixel
+  // (orow + QOFF + 1, ocol + QOFF + 1)
   const int g = lane >> 2, q = lane & 3;
   {
-    constexpr int NO = OH * OW, NSTRIP = (NO + 15) / 16;   // row-major strips, as in the down kernel
+    uint32_t wk[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) wk[k] = fK[k * 32 + lane];
+    constexpr int NO = OH * OW, NSTRIP = (NO + 15) / 16;
     const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
-    const TapOffsets<PW> to;
+    const TapOffsets<QW> to;
     const uint32_t fI = identity_frag();
     for (int st = warp; st < NSTRIP; st += NW) {
       const int pm = min(st * 16 + mrow, NO - 1), rm = pm / OW;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      layer_strip<PW>(zs, ps, wk, fI, rm * PW + (pm - rm * OW), to, acc);
+      layer_strip<QW>(zs, ps, wk, fI, (rm + QOFF) * QW + (pm - rm * OW) + QOFF, to, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int p = st * 16 + g + 8 * h;
@@ -539,7 +581,7 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
     // W_out on the tensor cores: an 8 -> 8 channel layer whose only nonzero
     // output channel is 0, with the FP32 weights split as hi + lo BF16 (the two
     // products are accumulated in FP32, so the weights keep ~16 bits); strips of
-    // 16 owned pixels of one row, as in the layer above
+    // 16 owned pixels of one row
     uint32_t wh[9], wl[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -549,7 +591,7 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
     __syncthreads();
     const float inv_alpha = alpha2[2 * bz + 1];
     float* ev = reinterpret_cast<float*>(ps);   // FH x FW corrections
-    static_assert(FH * FW * sizeof(float) <= PH * PW * sizeof(uint4), "correction staging");
+    static_assert(FH * FW * sizeof(float) <= G::QH * QW * sizeof(uint4), "correction staging");
     constexpr int SPRO = (FW + 15) / 16;
     const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
     const TapOffsets<OW> to;
@@ -560,7 +602,7 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
       strip_conv_at<OW>(os, wh, bm, bl, to, acc);
       strip_conv_at<OW>(os, wl, bm, bl, to, acc);
       // output channel 0 sits in the q == 0 lanes: stage it in shared memory
-      // (the P tiles are free now) so that the FP64 update below runs on
+      // (the Q tiles are free now) so that the FP64 update below runs on
       // full warps -- an FP64 instruction costs the same with 8 lanes or 32
       if (q == 0) {
 #pragma unroll
@@ -619,9 +661,10 @@ Status pix8_map(const FusedLevels& fl, const void* base, int n, int bw, int bh, 
 // restriction's strips of 16 coarse pixels).
 template <int FH, int FW>
 Status launch_down(int l, const FusedLevels& fl, const float* r32, const double* norm2, const FusedWeights& w,
-                   const int* active, cudaStream_t st) {
+                   const int* active, cudaStream_t st, const ResidIn* ra) {
   const int nl = fl.n[l];
   const bool first = l == 0, has_r = l + 1 < fl.L;
+  if (ra && (!first || fl.batch != 1)) return make_status(MGCNN_ERR_STATE, "fused residual: finest level, one problem");
   const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
   __nv_bfloat16* xc = has_r ? fl.xb[l + 1] : nullptr;
   const int R = has_r ? 1 : 0, ZH = FH + R + 2, ZW = FW + R + 2;
@@ -631,18 +674,23 @@ Status launch_down(int l, const FusedLevels& fl, const float* r32, const double*
     mx = ms;   // not read on the finest level
   else
     MG_TRY(pix8_map(fl, fl.xb[l], nl, ZW, ZH, &mx));
+  const ResidIn rin = ra ? *ra : ResidIn{};
   auto run = [&](auto* kernel, size_t smem) {
-    kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(r32, fl.alpha, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l], xc,
-                                                      nl, active, fl.err);
+    kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(r32, fl.alpha, rin, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l],
+                                                      xc, nl, active, fl.err);
   };
-  if (first && has_r)
-    run(down_kernel<FH, FW, true, true>, down_smem_bytes<FH, FW, true, true>());
+  if (ra && has_r)
+    run(down_kernel<FH, FW, true, true, true>, down_smem_bytes<FH, FW, true, true>());
+  else if (ra)
+    run(down_kernel<FH, FW, true, false, true>, down_smem_bytes<FH, FW, true, false>());
+  else if (first && has_r)
+    run(down_kernel<FH, FW, true, true, false>, down_smem_bytes<FH, FW, true, true>());
   else if (first)
-    run(down_kernel<FH, FW, true, false>, down_smem_bytes<FH, FW, true, false>());
+    run(down_kernel<FH, FW, true, false, false>, down_smem_bytes<FH, FW, true, false>());
   else if (has_r)
-    run(down_kernel<FH, FW, false, true>, down_smem_bytes<FH, FW, false, true>());
+    run(down_kernel<FH, FW, false, true, false>, down_smem_bytes<FH, FW, false, true>());
   else
-    run(down_kernel<FH, FW, false, false>, down_smem_bytes<FH, FW, false, false>());
+    run(down_kernel<FH, FW, false, false, false>, down_smem_bytes<FH, FW, false, false>());
   MG_LAUNCH("down_kernel");
   return {};
 }
@@ -653,38 +701,45 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
   const int nl = fl.n[l];
   const bool last = l == 0, has_p = l + 1 < fl.L;
   const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
-  const int H = last ? 1 : 0, PH = FH + 2 * H + 2, PW = FW + 2 * H + 2;
-  CUtensorMap mxd, ms, mc;
-  MG_TRY(pix8_map(fl, fl.xa[l], nl, PW, PH, &mxd));
-  MG_TRY(pix8_map(fl, fl.s[l], nl, PW, PH, &ms));
-  if (has_p)
-    MG_TRY(pix8_map(fl, fl.xb[l + 1], fl.n[l + 1], PW / 2 + 2, PH / 2 + 2, &mc));
-  else
-    mc = ms;   // not read on the coarsest level
-  auto run = [&](auto* kernel, size_t smem, bf16* xfin) {
+  auto run = [&](auto* kernel, size_t smem, bf16* xfin, auto geom) -> Status {
+    using G = decltype(geom);
+    CUtensorMap mxd, ms, mc;
+    MG_TRY(pix8_map(fl, fl.xa[l], nl, G::QW, G::QH, &mxd));
+    MG_TRY(pix8_map(fl, fl.s[l], nl, G::QW, G::QH, &ms));
+    if (has_p)
+      MG_TRY(pix8_map(fl, fl.xb[l + 1], fl.n[l + 1], G::CQW, G::CQH, &mc));
+    else
+      mc = ms;   // not read on the coarsest level
     kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha,
                                                       u_skip, xfin, e, nl, active, fl.err);
+    return {};
   };
   if (last && has_p)
-    run(up_kernel<FH, FW, true, true>, up_smem_bytes<FH, FW, true, true>(), nullptr);
+    MG_TRY(run(up_kernel<FH, FW, true, true>, up_smem_bytes<FH, FW, true, true>(), nullptr, UpGeom<FH, FW, true, true>{}));
   else if (last)
-    run(up_kernel<FH, FW, true, false>, up_smem_bytes<FH, FW, true, false>(), nullptr);
+    MG_TRY(run(up_kernel<FH, FW, true, false>, up_smem_bytes<FH, FW, true, false>(), nullptr,
+               UpGeom<FH, FW, true, false>{}));
   else if (has_p)
-    run(up_kernel<FH, FW, false, true>, up_smem_bytes<FH, FW, false, true>(), fl.xb[l]);
+    MG_TRY(run(up_kernel<FH, FW, false, true>, up_smem_bytes<FH, FW, false, true>(), fl.xb[l],
+               UpGeom<FH, FW, false, true>{}));
   else
-    run(up_kernel<FH, FW, false, false>, up_smem_bytes<FH, FW, false, false>(), fl.xb[l]);
+    MG_TRY(run(up_kernel<FH, FW, false, false>, up_smem_bytes<FH, FW, false, false>(), fl.xb[l],
+               UpGeom<FH, FW, false, false>{}));
   MG_LAUNCH("up_kernel");
   return {};
 }
 
+constexpr int kTileH[kFusedVariants] = {16, 8, 16, 32, 24};
+constexpr int kTileW[kFusedVariants] = {32, 32, 16, 32, 32};
+
 Status launch_down_variant(int v, int l, const FusedLevels& fl, const float* r32, const double* norm2,
-                           const FusedWeights& w, const int* active, cudaStream_t st) {
+                           const FusedWeights& w, const int* active, cudaStream_t st, const ResidIn* ra = nullptr) {
   switch (v) {
-    case 1: return launch_down<8, 32>(l, fl, r32, norm2, w, active, st);
-    case 2: return launch_down<16, 16>(l, fl, r32, norm2, w, active, st);
-    case 3: return launch_down<32, 32>(l, fl, r32, norm2, w, active, st);
-    case 4: return launch_down<24, 32>(l, fl, r32, norm2, w, active, st);
-    default: return launch_down<16, 32>(l, fl, r32, norm2, w, active, st);
+    case 1: return launch_down<8, 32>(l, fl, r32, norm2, w, active, st, ra);
+    case 2: return launch_down<16, 16>(l, fl, r32, norm2, w, active, st, ra);
+    case 3: return launch_down<32, 32>(l, fl, r32, norm2, w, active, st, ra);
+    case 4: return launch_down<24, 32>(l, fl, r32, norm2, w, active, st, ra);
+    default: return launch_down<16, 32>(l, fl, r32, norm2, w, active, st, ra);
   }
 }
 
@@ -705,13 +760,16 @@ Status launch_up_variant(int v, int l, const FusedLevels& fl, const double* norm
 // equal-size problems stored back to back: level l state in xa[l] (down state)
 // and xb[l] (restricted input, then final up state), setup tensors s[l];
 // r32/norm2/u/e per problem.  `active` (nullable, [batch]) skips converged
-// problems.  fl.var_down / fl.var_up pick each level's tile variant.
+// problems.  fl.var_down / fl.var_up pick each level's tile variant.  With
+// opt.after_fused_down0 the finest down kernel has already run (it computed the
+// residual itself) and the input scale was set before it: the cycle continues
+// from level 1 and leaves the scale alone.
 Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
                            const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
-                           mgcnn_ctx* prof_ctx) {
+                           mgcnn_ctx* prof_ctx, FusedCycleOpt opt) {
   const int L = fl.L;
-  MG_TRY(launch_alpha(fl, norm2, st));
-  for (int l = 0; l < L; ++l) {
+  if (!opt.after_fused_down0) MG_TRY(launch_alpha(fl, norm2, st));
+  for (int l = opt.after_fused_down0 ? 1 : 0; l < L; ++l) {
     const int ps = (l == 0 && prof_ctx) ? prof_begin(prof_ctx, kProfDown0) : -1;
     MG_TRY(launch_down_variant(fl.var_down[l], l, fl, r32, norm2, w, active, st));
     if (prof_ctx) prof_end(prof_ctx, ps);
@@ -724,27 +782,50 @@ Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double
   return {};
 }
 
+Status fused_down0_resid(const FusedLevels& fl, const ResidIn& ra, const FusedWeights& w, const int* active,
+                         cudaStream_t st, mgcnn_ctx* prof_ctx) {
+  const int ps = prof_ctx ? prof_begin(prof_ctx, kProfDown0) : -1;
+  MG_TRY(launch_down_variant(fl.var_down[0], 0, fl, nullptr, nullptr, w, active, st, &ra));
+  if (prof_ctx) prof_end(prof_ctx, ps);
+  return {};
+}
+
+Status fused_set_alpha(const FusedLevels& fl, const double* norm2, cudaStream_t st) { return launch_alpha(fl, norm2, st); }
+
+int fused_down0_blocks(int n, int variant) {
+  return ((n + kTileW[variant] - 1) / kTileW[variant]) * ((n + kTileH[variant] - 1) / kTileH[variant]);
+}
+
+size_t fused_partials_max(int n) {
+  size_t m = 0;
+  for (int v = 0; v < kFusedVariants; ++v) m = std::max(m, (size_t)fused_down0_blocks(n, v));
+  return m;
+}
+
 // Autotuner: for every level, time each tile variant of the down and up kernels
 // (CUDA events, `reps` launches after one warm-up launch) on the real buffers
 // and keep the fastest.  The up kernel of the finest level writes its FP64
 // output to `scratch` (n_0^2 x batch doubles) so that no caller data changes.
+// With `ra` the finest down kernel is timed as it runs in the cycle, computing
+// the residual (its partial sums go to ra->partial).
 Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, double* scratch,
-                      const FusedWeights& w, cudaStream_t st, int reps) {
+                      const FusedWeights& w, cudaStream_t st, int reps, const ResidIn* ra) {
   cudaEvent_t e0, e1;
   MG_CUDA(cudaEventCreate(&e0));
   MG_CUDA(cudaEventCreate(&e1));
   Status result = launch_alpha(fl, norm2, st);
   for (int l = 0; l < fl.L && result.ok(); ++l) {
+    const ResidIn* rl = (l == 0) ? ra : nullptr;
     float best_d = 1e30f, best_u = 1e30f;
     // two timed rounds per variant, keeping the faster one: a single short
     // round is easily disturbed (clock ramp, other work on the GPU)
     for (int round = 0; round < 2 && result.ok(); ++round)
       for (int v = 0; v < kFusedVariants && result.ok(); ++v) {
         float t = 0.f;
-        result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st);
+        result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st, rl);
         if (!result.ok()) break;
         cudaEventRecord(e0, st);
-        for (int k = 0; k < reps && result.ok(); ++k) result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st);
+        for (int k = 0; k < reps && result.ok(); ++k) result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st, rl);
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&t, e0, e1);
@@ -768,37 +849,85 @@ bool fused_supported(const mgcnn_ctx* c) {
   return c->cp == 8 && c->wl.nu_d == 1 && c->wl.nu_u == 1;
 }
 
-// e = B r (u_skip == nullptr) or e = u_skip + B r for the context's single problem.
-Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
-                        const FusedWeights& w) {
+// The context's single-problem level set (tile variants as tuned).
+FusedLevels ctx_levels(mgcnn_ctx* c) {
   FusedLevels fl;
   fl.L = c->L;
   fl.batch = 1;
   fl.maps = c->tma;
   fl.err = c->kerr.as<int>();
-  MG_TRY(ensure(c->alpha32, 2 * sizeof(float)));
   fl.alpha = c->alpha32.as<float>();
   for (int l = 0; l < c->L; ++l) {
     fl.n[l] = c->lv[l].n;
     fl.s[l] = c->s16[l].as<bf16>();
     fl.xa[l] = c->x16a[l].as<bf16>();
     fl.xb[l] = c->x16b[l].as<bf16>();
-  }
-  if (!c->tuned) {
-    // first V-cycle after a setup: time the tile variants per level (output to
-    // the context's scratch vector, so no caller data changes), keep the fastest
-    MG_TRY(fused_autotune(fl, r32, norm2, c->e.as<double>(), w, c->stream, 5));
-    for (int l = 0; l < c->L; ++l) {
-      c->tile_var[0][l] = fl.var_down[l];
-      c->tile_var[1][l] = fl.var_up[l];
-    }
-    c->tuned = true;
-  }
-  for (int l = 0; l < c->L; ++l) {
     fl.var_down[l] = c->tile_var[0][l];
     fl.var_up[l] = c->tile_var[1][l];
   }
-  return fused_vcycle_levels(fl, r32, norm2, e, u_skip, w, nullptr, c->stream, c);
+  return fl;
+}
+
+// First V-cycle after a setup: time the tile variants per level (outputs to the
+// context's scratch vector and partial sums, so no caller data changes) and keep
+// the fastest.  With `ra` the finest down kernel is tuned with the residual fused in.
+Status ctx_autotune(mgcnn_ctx* c, const float* r32, const double* norm2, const ResidIn* ra) {
+  MG_TRY(ensure(c->alpha32, 2 * sizeof(float)));
+  if (c->tuned) return {};
+  FusedLevels fl = ctx_levels(c);
+  MG_TRY(fused_autotune(fl, r32, norm2, c->e.as<double>(), fused_weights(c), c->stream, 5, ra));
+  for (int l = 0; l < c->L; ++l) {
+    c->tile_var[0][l] = fl.var_down[l];
+    c->tile_var[1][l] = fl.var_up[l];
+  }
+  c->tuned = true;
+  c->sgraph_valid = false;
+  return {};
+}
+
+// e = B r (u_skip == nullptr) or e = u_skip + B r for the context's single problem.
+Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, double* e, const double* u_skip,
+                        const FusedWeights& w) {
+  MG_TRY(ctx_autotune(c, r32, norm2, nullptr));
+  return fused_vcycle_levels(ctx_levels(c), r32, norm2, e, u_skip, w, nullptr, c->stream, c);
+}
+
+bool fused_residual_applies(const mgcnn_ctx* c) {
+  return c->cfg.precision == MGCNN_PREC_MIXED_BF16 && c->fused && fused_supported(c) && c->fuse_residual;
+}
+
+ResidIn ctx_resid_in(mgcnn_ctx* c, const double* f, const double* u) {
+  ResidIn ra;
+  ra.u = u;
+  ra.f = f;
+  ra.op = c->op[0].as<double>();
+  ra.dinv32 = c->cfg.input_diag ? c->dinv32.as<float>() : nullptr;
+  ra.partial = c->partial.as<double>();
+  return ra;
+}
+
+Status fused_cycle_setup(mgcnn_ctx* c, const double* f, const double* u, const double* fn2_dev) {
+  MG_TRY(ensure(c->partial, std::max((size_t)reduction_blocks(c->lv[0].N()), fused_partials_max(c->n)) *
+                                sizeof(double)));
+  const ResidIn ra = ctx_resid_in(c, f, u);
+  MG_TRY(ctx_autotune(c, nullptr, fn2_dev, &ra));
+  return fused_set_alpha(ctx_levels(c), fn2_dev, c->stream);
+}
+
+Status fused_cycle_residual(mgcnn_ctx* c, const double* f, const double* u, double* rn2_dev, const int* active,
+                            cudaStream_t st, bool profile) {
+  const FusedLevels fl = ctx_levels(c);
+  MG_TRY(fused_down0_resid(fl, ctx_resid_in(c, f, u), fused_weights(c), active, st, profile ? c : nullptr));
+  return launch_reduce(c->partial.as<double>(), fused_down0_blocks(c->n, fl.var_down[0]), rn2_dev, st);
+}
+
+Status fused_cycle_rest(mgcnn_ctx* c, double* u, const double* rn2_dev, const int* active, cudaStream_t st,
+                        bool profile) {
+  const FusedLevels fl = ctx_levels(c);
+  FusedCycleOpt opt;
+  opt.after_fused_down0 = true;
+  MG_TRY(fused_vcycle_levels(fl, nullptr, rn2_dev, u, u, fused_weights(c), active, st, profile ? c : nullptr, opt));
+  return fused_set_alpha(fl, rn2_dev, st);
 }
 
 }  // namespace mgcnn

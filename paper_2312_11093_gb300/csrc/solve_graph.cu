@@ -1,7 +1,8 @@
 // The stationary iteration (Eq. 1 of arXiv 2312.11093) run on the device: the
 // whole solve is one launch of a CUDA graph whose only node is a conditional
 // WHILE loop.  The loop body -- FP64 residual and norm, convergence test,
-// mixed-precision V-cycle (fused level kernels) -- is captured once per setup;
+// mixed-precision V-cycle (fused level kernels; by default the residual is
+// computed inside the finest down kernel) -- is captured once per setup;
 // the test kernel records ||r_k|| / ||f||, stops the loop on the tolerance,
 // on maxit or on a non-finite norm (cudaGraphSetConditional), and otherwise
 // counts the cycle about to be applied.  The V-cycle kernels of the final
@@ -70,6 +71,15 @@ Status build_graph(mgcnn_ctx* c) {
     const long long launches0 = mgcnn_kernel_launches();
     Status cap = [&]() -> Status {
       double* sc = c->scalars.as<double>();
+      if (fused_residual_applies(c)) {
+        // r_k and the finest down level in one kernel, ||r_k||^2, the test, the
+        // rest of the cycle (u += B r_k) and the next input scale
+        MG_TRY(fused_cycle_residual(c, c->f.as<double>(), c->u.as<double>(), sc, nullptr, st, false));
+        solve_check_kernel<<<1, 32, 0, st>>>(sc, sc + 1, c->gstate.as<int>(), c->ghist.as<double>(),
+                                             c->gparams.as<double>(), loop);
+        MG_LAUNCH("solve_check_kernel");
+        return fused_cycle_rest(c, c->u.as<double>(), sc, c->gstate.as<int>(), st, false);
+      }
       MG_TRY(launch_residual(c->f.as<double>(), c->u.as<double>(), c->op[0].as<double>(), nullptr,
                              c->r32.as<float>(), c->partial.as<double>(), c->n, st,
                              c->cfg.input_diag ? c->dinv32.as<float>() : nullptr));
@@ -155,7 +165,13 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
     MG_CUDA(cudaStreamSynchronize(st));
     return {};
   }
-  if (!c->tuned) {
+  if (fused_residual_applies(c)) {
+    // tile shapes (tuned once per setup before the graph fixes them) and the
+    // first cycle's input scale from ||f||
+    const bool was_tuned = c->tuned;
+    MG_TRY(fused_cycle_setup(c, c->f.as<double>(), c->u.as<double>(), c->scalars.as<double>() + 1));
+    if (!was_tuned) c->sgraph_valid = false;
+  } else if (!c->tuned) {
     // tile shapes: tuned once per setup before the graph fixes them
     FusedLevels fl;
     fl.L = c->L;

@@ -371,6 +371,7 @@ class Solver:
     OPT_DEVICE_LOOP = 2
     OPT_TILE = 3
     OPT_SYMMETRIC = 4
+    OPT_FUSED_RESIDUAL = 5
 
     def set_option(self, option: int, value: int):
         self._check(self._L.mgcnn_set_option(self._h, int(option), int(value)), "mgcnn_set_option")

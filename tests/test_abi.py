@@ -74,7 +74,8 @@ def test_bpx_eps_matches_the_header():
 def test_product_code_does_not_use_the_oracle():
     """Only tests/, __graft_entry__.smoke() and bench.py's CPU legs may use oracle/:
     nothing in the package imports it, and bench.py imports it only inside the
-    function that times it on the host."""
+    functions that time it on the host (the worker that runs one oracle solve
+    and its network helper)."""
     pkg = os.path.join(ROOT, "paper_2312_11093_gb300")
     for dirpath, _, files in os.walk(pkg):
         for f in files:
@@ -88,4 +89,4 @@ def test_product_code_does_not_use_the_oracle():
         if m:
             current = m.group(1)
         if re.match(r"\s*(import oracle|from oracle)", line):
-            assert current == "cpu_reference", line
+            assert current in ("cpu_reference", "_oracle_solve", "_oracle_net"), line

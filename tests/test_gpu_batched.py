@@ -46,7 +46,9 @@ def _fields(sizes, seed):
 
 def test_batched_equals_single_problem_solves(M):
     """Same kernels, same arithmetic per pixel (the tile shape does not change the
-    summation order) and the same norm reduction: bit-identical iterates."""
+    summation order): bit-identical iterates.  The single solve sums its norms in
+    the fused finest down kernel's order, the batch in the residual kernel's: the
+    final relative residuals agree to rounding."""
     sizes = [63, 15, 127, 63, 7, 31, 127, 3, 63]
     ks, fs = _fields(sizes, 1)
     w = _weights(M)
@@ -63,7 +65,7 @@ def test_batched_equals_single_problem_solves(M):
         st1, it1, h1 = one.solve(fs[i].copy(), u, 1e-6, 40)
         assert it1 == iters[i], (i, n, it1, iters[i])
         assert np.array_equal(u, us[i]), (i, n)
-        assert relres[i] == h1[-1]
+        assert abs(relres[i] - h1[-1]) <= 1e-13 * h1[-1]
         assert stat[i] == st1
 
 
