@@ -141,7 +141,18 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- roofline helpers
 def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
-    """Bytes a launch of `kind` at the finest level must move (each operand once)."""
+    """Bytes a launch of `kind` must move (each operand once): the finest level's
+    kernel classes, or the fused kernels of a coarser level l ("down<l>",
+    "up<l>", level size n_l = (n_{l-1} - 1) / 2)."""
+    for pre in ("down", "up"):
+        if kind.startswith(pre) and kind[len(pre):].isdigit() and int(kind[len(pre):]) > 0:
+            nl = n
+            for _ in range(int(kind[len(pre):])):
+                nl = (nl - 1) // 2
+            Nl = nl * nl
+            # down: x_in and s in, x_down and the coarse x out; up: x_down, s and the
+            # coarse x in, x_fin out (BF16, cp channels)
+            return (2.0 * cp + 2.0 * cp + 2.0 * cp + 0.5 * cp) * Nl
     N = n * n
     return {
         "residual": 60.0 * N,                    # u, f (FP64) + 5 stencil arrays in, FP32 r out
@@ -303,6 +314,8 @@ def main():
                     help="tile shape of the fused kernels: -1 autotuned, 0 16x32, 1 8x32, 2 16x16, 3 32x32, 4 24x32")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and channelised workloads reported beside the headline")
     ap.add_argument("--krylov", action="store_true", help="also time flexible GMRES with the network as preconditioner")
     ap.add_argument("--bpx", action="store_true",
                     help="also time CG with the symmetric network in its BPX form (same k field, b = 0, FP64, tol 1e-8)")
@@ -453,8 +466,8 @@ def main():
     peak = float(peaks["hbm_gbs"])
     achieved = algorithmic_bytes(dom, n, cp) / (dom_ms / dom_cnt * 1e-3) / 1e9 if dom_cnt else None
     kname = {"residual": "residual_kernel", "resnet": "resnet_mma_kernel", "restrict": "rcnn_mma_kernel",
-             "prolong": "tcnn_add_kernel16", "in": "in_kernel16", "out": "out_kernel16",
-             "down0": "down_kernel", "up0": "up_kernel"}[dom]
+             "prolong": "tcnn_add_kernel16", "in": "in_kernel16", "out": "out_kernel16"}.get(
+                 dom, "down_kernel" if dom.startswith("down") else "up_kernel")
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "traffic": traffic_record(kname, f"{workload}_{n}"),
@@ -572,10 +585,16 @@ def main():
                                 "relres_bnorm": float(mh[-1]), "tol": 1e-8, "converged": bool(mst == mgcnn.OK),
                                 "method": "MINRES, same preconditioner and problem, solve only"}
         svb.close()
+    sv.close()
+    if not args.no_extras and rank == 0 and world == 1:
+        # the other two GPU workloads: the uneven batch over three coefficient
+        # families, and the channelised field at 4095^2 (FP64 MGCNN, mixed MGCNN,
+        # GMG, per-level achieved bandwidth)
+        result["batched"] = run_batched(args, rank, world, dev, mgcnn, quiet=True)
+        result["channelised"] = run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol)
     if not args.no_cpu and rank == 0 and world == 1:
         # one wave of complete oracle solves at 511^2, one per host core (about 15-30 s)
         result["cpu_baseline"] = cpu_reference(workload, net, n, n_sample=min(n, 511), tol=tol)
-    sv.close()
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
@@ -583,8 +602,7 @@ def main():
 
 
 def bench_batched(args, rank, world, local):
-    """256 uneven problems per step (setup + solve of the whole batch), one CUDA graph
-    per cycle, tile shapes autotuned at setup; solves/s = problems / step time."""
+    """The batched workload as the bench line itself (--workload batched256)."""
     import torch
     if world > 1:
         import torch.distributed as dist
@@ -593,14 +611,26 @@ def bench_batched(args, rank, world, local):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2312_11093_gb300 import mgcnn
-    # the trained network on all three coefficient families; without trained weights
-    # the GMG V(1,0) network on the GRF family only (rediscretised GMG diverges on the
-    # high-contrast blocks and checkerboards)
+    res = run_batched(args, rank, world, torch.device("cuda", local), mgcnn)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_batched(args, rank, world, dev, mgcnn, quiet=False):
+    """256 uneven problems per step (setup + solve of the whole batch), one CUDA graph
+    launch per batch, tile shapes autotuned at setup; solves/s = problems that reach
+    the tolerance / step time."""
+    import torch
+    # all three coefficient families of the workload; a problem that does not reach
+    # the tolerance within the cycle limit is a failure (counted, not a solve)
     net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg_v10")
     C, nd, nu, blob, is_gmg = network(net)
-    families = 1 if is_gmg else 3
-    ns, ks, fs = make_batch_workload(args.batch, rank_seed(3, rank), families=families)
-    dev = torch.device("cuda", local)
+    ns, ks, fs = make_batch_workload(args.batch, rank_seed(3, rank), families=3)
+    fam = np.random.default_rng(rank_seed(3, rank))
+    fam.choice((63, 127, 255, 511, 1023), size=args.batch)
+    family = fam.integers(0, 3, size=args.batch)     # the same draws as make_batch_workload
     kd = [torch.from_numpy(k).to(dev) for k in ks]
     fd = [torch.from_numpy(f).to(dev) for f in fs]
     ud = [torch.zeros(n * n, dtype=torch.float64, device=dev) for n in ns]
@@ -611,7 +641,7 @@ def bench_batched(args, rank, world, local):
         sv.setup_batched(kk, ns, gmg_omega=0.8 if is_gmg else None)
         for u in uu:
             u.zero_() if hasattr(u, "zero_") else u.fill(0.0)
-        return sv.solve_batched(ff, uu, args.tol, args.maxit)
+        return sv.solve_batched(ff, uu, args.tol, args.maxit, per_problem=True)
 
     def barrier():
         if world > 1:
@@ -622,19 +652,20 @@ def bench_batched(args, rank, world, local):
         st, iters, relres, stat = step(kd, fd, ud)
     launches0 = mgcnn.kernel_launches()
     stream = torch.cuda.current_stream(dev)
-    with ClockSampler(local) as clk:
+    steps = args.steps if not quiet else max(3, min(args.steps, 5))
+    with ClockSampler(dev.index or 0) as clk:
         barrier()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         # the batch runs on the library's own streams and each call returns after
         # its work has finished, so events on this stream bracket all of it
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             st, iters, relres, stat = step(kd, fd, ud)
         ev1.record(stream)
         barrier()
-        ms = ev0.elapsed_time(ev1) / args.steps
-    launches = (mgcnn.kernel_launches() - launches0) // args.steps
+        ms = ev0.elapsed_time(ev1) / steps
+    launches = (mgcnn.kernel_launches() - launches0) // steps
     ms = max_over_ranks(ms, world, dev)
     uh = [np.zeros(n * n) for n in ns]
     step(ks, fs, uh)
@@ -644,25 +675,90 @@ def bench_batched(args, rank, world, local):
     for _ in range(e2e_steps):
         step(ks, fs, uh)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    sv.close()
     unknowns = int(sum(n * n for n in ns))
     done = int((stat == 0).sum())   # problems that reached the tolerance count as solves
     res = {"metric": "solves/s to rel-res 1e-6, batch of uneven sizes (setup + solve)",
-           "value": whole_job_rate(world, done, ms), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "value": whole_job_rate(world, done, ms), "unit": "solves/s", "n_gpus": world, "steps": steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-           "config": {"workload": f"batched{args.batch}_63-1023" + ("_grf" if is_gmg else ""), "problems": args.batch,
-                      "unknowns": unknowns, "tol": args.tol, "net": net, "l2": "inputs larger than L2",
-                      "parallelism": "replicas" if world > 1 else "single"},
+           "config": {"workload": f"batched{args.batch}_63-1023_mixture", "problems": args.batch,
+                      "unknowns": unknowns, "tol": args.tol, "net": net, "maxit": args.maxit,
+                      "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single"},
            "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
-           "converged": int((stat == 0).sum()), "relres_max": float(relres.max()),
+           "converged": done, "failed": int((stat != 0).sum()),
+           "converged_by_family": {nm: f"{int(((stat == 0) & (family == i)).sum())}/{int((family == i).sum())}"
+                                   for i, nm in enumerate(("grf", "blocks_1e4", "checkerboard_100"))},
+           "relres_max_converged": float(relres[stat == 0].max()) if (stat == 0).any() else None,
            "e2e": {"value": world * done * 1e3 / e2e_ms, "unit": "solves/s",
                    "h2d_bytes_per_step": int(sum(k.nbytes for k in ks) + 2 * sum(f.nbytes for f in fs)),
                    "d2h_bytes_per_step": int(sum(f.nbytes for f in fs)), "ms_per_step": e2e_ms},
            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None}
-    if rank == 0:
-        print(json.dumps(res))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return res
+
+
+def run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, maxit=60):
+    """The channelised binary field (k in {1, 1e3}) at n^2: the mixed and the FP64
+    MGCNN (same network) and classical GMG V(2,2), each from u = 0 for at most
+    `maxit` cycles; per-level CUDA-event times and algorithmic GB/s of the mixed
+    cycle's fused kernels over the first cycles."""
+    import torch
+    k_h, f_h, b = make_workload("channelised", n, 4)
+    k_d = torch.from_numpy(k_h).to(dev)
+    f_d = torch.from_numpy(f_h).to(dev)
+    out = {"workload": f"channelised_{n}", "tol": tol, "maxit": maxit,
+           "note": "relres is the last recorded ||r||/||f||; converged means it reached tol within maxit"}
+
+    def run(prec):
+        sv = mgcnn.Solver(C, nd, nu, precision=prec, b=b, stream=stream)
+        sv.set_weights(blob)
+        sv.setup_gmg(k_d, n, 0.8) if is_gmg else sv.setup(k_d, n)
+        u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        try:
+            st, it, hist = sv.solve(f_d, u, tol, maxit)
+            rec = {"iters": it, "relres": float(hist[-1]), "converged": bool(st == mgcnn.OK)}
+        except mgcnn.MGCNNError as err:
+            rec = {"converged": False, "error": str(err)[:100]}
+        torch.cuda.synchronize(dev)
+        rec["ms"] = (time.perf_counter() - t0) * 1e3
+        return sv, rec
+
+    sv, out["mixed"] = run("mixed_bf16")
+    cp = 8 if C <= 8 else 16
+    sv.profile_read()
+    sv.profile(True)
+    u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    try:
+        sv.solve(f_d, u, 0.0, 3)      # three cycles, every launch bracketed
+    except mgcnn.MGCNNError:
+        pass
+    prof = sv.profile_read()
+    sv.profile(False)
+    sv.close()
+    peak = float(json.load(open(PEAKS))["hbm_gbs"]) if os.path.exists(PEAKS) else None
+    levels = {}
+    for kk, (t, cnt) in prof.items():
+        if cnt and t > 0:
+            gbs = algorithmic_bytes(kk, n, cp) * cnt / (t * 1e-3) / 1e9
+            levels[kk] = {"us_per_launch": round(1e3 * t / cnt, 2), "gbs": round(gbs, 1),
+                          "frac_of_measured_hbm": round(gbs / peak, 3) if peak else None}
+    out["mixed"]["per_level"] = levels
+    sv64, out["fp64"] = run("fp64")
+    ug = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    try:
+        stg, itg, hg = sv64.gmg_solve(f_d, ug, tol, maxit, 2, 2, 0.8)
+        out["gmg"] = {"iters": itg, "relres": float(hg[-1]), "converged": bool(stg == mgcnn.OK),
+                      "cycle": "V(2,2) weighted Jacobi 0.8, FP64"}
+    except mgcnn.MGCNNError as err:
+        out["gmg"] = {"converged": False, "error": str(err)[:100], "cycle": "V(2,2) weighted Jacobi 0.8, FP64"}
+    torch.cuda.synchronize(dev)
+    out["gmg"]["ms"] = (time.perf_counter() - t0) * 1e3
+    sv64.close()
+    return out
 
 
 if __name__ == "__main__":

@@ -382,12 +382,14 @@ int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * mgcnn_kernel_launches: kernels launched by this library in this process.
  * mgcnn_profile(ctx, 1): from now on bracket the finest-level launch of each
- * kernel class with CUDA events on the context's stream; mgcnn_profile_read
- * returns, per class, the summed milliseconds and the number of launches
- * since the last read (classes: 0 residual, 1 ResNet layer, 2 restriction,
- * 3 prolongation-add into the finest level, 4 reChannel-in, 5 reChannel-out
- * with update, 6 fused down kernel, 7 fused up kernel) and clears them.  Timing adds one event pair per bracketed
- * launch.  While profiling is on, mgcnn_solve runs its host-driven loop (not
+ * kernel class, and the fused kernels of every level, with CUDA events on the
+ * context's stream; mgcnn_profile_read returns, per class, the summed
+ * milliseconds and the number of launches since the last read (classes: 0
+ * residual, 1 ResNet layer, 2 restriction, 3 prolongation-add into the finest
+ * level, 4 reChannel-in, 5 reChannel-out with update, 6 fused down kernel, 7
+ * fused up kernel of the finest level; 8 + l fused down kernel and 21 + l
+ * fused up kernel of level l = 1..12, 34 classes in all) and clears them.
+ * Timing adds one event pair per bracketed launch.  While profiling is on, mgcnn_solve runs its host-driven loop (not
  * the device-side loop of MGCNN_OPT_DEVICE_LOOP), so that every bracketed
  * kernel is a plain launch on the context's stream. */
 long long mgcnn_kernel_launches(void);

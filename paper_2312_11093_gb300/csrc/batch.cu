@@ -1,6 +1,7 @@
 // Batched solves of many coefficient fields and right-hand sides of uneven
 // grid sizes (the stationary iteration of Eq. 1 with the mixed-precision solve
-// phase of Algorithm 3, one problem per field), as one CUDA graph per cycle.
+// phase of Algorithm 3, one problem per field), as one CUDA graph launch per
+// batch: a conditional WHILE node whose body is one cycle of the whole batch.
 //
 // Problems are grouped into size classes; every buffer of a class holds its
 // problems back to back, so each kernel of the cycle covers a whole class
@@ -10,9 +11,13 @@
 //     convergence check on the device        (active mask, cycle counts, history)
 //     fused V-cycle, tile shape per level chosen by the autotuner; blocks of
 //     converged problems return at once
-// The host launches the graph and reads one integer (problems still active)
-// per cycle.  Setup (operators on every level, Algorithm 2 in FP32, BF16 setup
-// tensors) is batched per class the same way.
+//   joined: the loop test (another cycle while any problem is active, at most
+//     maxit + 2 cycles) sets the WHILE node's condition on the device
+// The host launches the graph once and reads the per-problem states after it.
+// (Where conditional graph nodes are unavailable the same body is captured
+// as a plain graph and launched once per cycle, with a 4-byte readback each.)
+// Setup (operators on every level, Algorithm 2 in FP32, BF16 setup tensors) is
+// batched per class the same way.
 #include <algorithm>
 #include <cmath>
 
@@ -59,6 +64,20 @@ __global__ void __launch_bounds__(kResidualBlock) sumsq_rows_kernel(const double
 }
 
 // state = [active | iters | status] (3 x B ints)
+// First node of a cycle: clear the active-problem count.
+__global__ void batch_cycle_begin_kernel(int* __restrict__ counter) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) counter[0] = 0;
+}
+
+// Last node of a cycle: count it and run another while any problem is active
+// (bounded by `limit` cycles).  counter[1] holds the cycles run by this launch.
+__global__ void batch_loop_kernel(int* __restrict__ counter, int limit, cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int cycles = counter[1] + 1;
+  counter[1] = cycles;
+  cudaGraphSetConditional(loop, (counter[0] > 0 && cycles < limit) ? 1u : 0u);
+}
+
 __global__ void batch_init_kernel(const double* __restrict__ fn2, int* __restrict__ state, double* __restrict__ u,
                                   size_t N, int B) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,7 +207,7 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, doub
     MG_TRY(ensure(k.xb[l], B * N * 8 * sizeof(bf16)));
   }
   MG_TRY(ensure(k.dinv32, B * N0 * sizeof(float)));
-  MG_TRY(ensure(k.r32, B * N0 * sizeof(float)));
+  MG_TRY(ensure(k.r32, B * r32_floats(k.n) * sizeof(float)));
   MG_TRY(ensure(k.f, B * N0 * sizeof(double)));
   MG_TRY(ensure(k.u, B * N0 * sizeof(double)));
   MG_TRY(ensure(k.scratch, B * N0 * sizeof(double)));
@@ -263,7 +282,7 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, doub
     }
   fill_kernel<<<grid_for(B, 128), 128, 0, st>>>(k.rn2.as<double>(), B, 1.0);
   MG_LAUNCH("fill_kernel");
-  MG_CUDA(cudaMemsetAsync(k.r32.p, 0, B * N0 * sizeof(float), st));
+  MG_CUDA(cudaMemsetAsync(k.r32.p, 0, B * r32_floats(k.n) * sizeof(float), st));
   MG_TRY(fused_autotune(k.fl, k.r32.as<float>(), k.rn2.as<double>(), k.scratch.as<double>(), fused_weights(c), st, 5));
   mgcnn_ctx::TunedClass tc{k.n, k.B, {}};
   for (int l = 0; l < k.L; ++l) {
@@ -275,7 +294,36 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, doub
   return {};
 }
 
-// Capture one cycle of the whole batch (all classes forked on their streams).
+// One cycle of the whole batch (all classes forked on their streams), captured
+// from `main`.
+Status record_cycle(mgcnn_ctx* c, cudaStream_t main, const FusedWeights& w) {
+  batch_cycle_begin_kernel<<<1, 32, 0, main>>>(c->bcount.as<int>());
+  MG_LAUNCH("batch_cycle_begin_kernel");
+  MG_CUDA(cudaEventRecord(c->bfork, main));
+  for (BatchClass& k : c->bcls) {
+    const size_t N0 = (size_t)k.n * k.n;
+    const int nblk = residual_blocks(N0);
+    int* state = k.state.as<int>();
+    MG_CUDA(cudaStreamWaitEvent(k.stream, c->bfork, 0));
+    MG_TRY(launch_residual(k.f.as<double>(), k.u.as<double>(), k.op[0].as<double>(), nullptr, k.r32.as<float>(),
+                           k.partial.as<double>(), k.n, k.stream,
+                           c->cfg.input_diag ? k.dinv32.as<float>() : nullptr, k.B));
+    rows_reduce_kernel<<<k.B, kReduceBlock, 0, k.stream>>>(k.partial.as<double>(), nblk, k.rn2.as<double>());
+    MG_LAUNCH("rows_reduce_kernel");
+    batch_check_kernel<<<grid_for(k.B, 128), 128, 0, k.stream>>>(k.rn2.as<double>(), k.fn2.as<double>(), state,
+                                                                  k.hist.as<double>(), c->bmaxit + 1,
+                                                                  c->bparams.as<double>(), k.B, c->bcount.as<int>());
+    MG_LAUNCH("batch_check_kernel");
+    MG_TRY(fused_vcycle_levels(k.fl, k.r32.as<float>(), k.rn2.as<double>(), k.u.as<double>(), k.u.as<double>(), w,
+                               state, k.stream, nullptr));
+    MG_CUDA(cudaEventRecord(k.done, k.stream));
+    MG_CUDA(cudaStreamWaitEvent(main, k.done, 0));
+  }
+  return {};
+}
+
+// The batch's graph: a conditional WHILE node around one cycle (bwhile), or,
+// where that cannot be built, the plain cycle graph launched once per cycle.
 Status capture_cycle(mgcnn_ctx* c) {
   if (c->bgraph) {
     cudaGraphExecDestroy(c->bgraph);
@@ -283,40 +331,59 @@ Status capture_cycle(mgcnn_ctx* c) {
   }
   cudaStream_t main = c->bstream;
   const FusedWeights w = fused_weights(c);
-  cudaGraph_t g = nullptr;
   const long long launches0 = mgcnn_kernel_launches();
-  MG_CUDA(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
-  Status s = [&]() -> Status {
-    MG_CUDA(cudaMemsetAsync(c->bcount.p, 0, sizeof(int), main));
-    MG_CUDA(cudaEventRecord(c->bfork, main));
-    for (BatchClass& k : c->bcls) {
-      const size_t N0 = (size_t)k.n * k.n;
-      const int nblk = residual_blocks(N0);
-      int* state = k.state.as<int>();
-      MG_CUDA(cudaStreamWaitEvent(k.stream, c->bfork, 0));
-      MG_TRY(launch_residual(k.f.as<double>(), k.u.as<double>(), k.op[0].as<double>(), nullptr, k.r32.as<float>(),
-                             k.partial.as<double>(), k.n, k.stream,
-                             c->cfg.input_diag ? k.dinv32.as<float>() : nullptr, k.B));
-      rows_reduce_kernel<<<k.B, kReduceBlock, 0, k.stream>>>(k.partial.as<double>(), nblk, k.rn2.as<double>());
-      MG_LAUNCH("rows_reduce_kernel");
-      batch_check_kernel<<<grid_for(k.B, 128), 128, 0, k.stream>>>(k.rn2.as<double>(), k.fn2.as<double>(), state,
-                                                                    k.hist.as<double>(), c->bmaxit + 1,
-                                                                    c->bparams.as<double>(), k.B, c->bcount.as<int>());
-      MG_LAUNCH("batch_check_kernel");
-      MG_TRY(fused_vcycle_levels(k.fl, k.r32.as<float>(), k.rn2.as<double>(), k.u.as<double>(), k.u.as<double>(), w,
-                                 state, k.stream, nullptr));
-      MG_CUDA(cudaEventRecord(k.done, k.stream));
-      MG_CUDA(cudaStreamWaitEvent(main, k.done, 0));
+  c->bwhile = false;
+  {
+    cudaGraph_t g = nullptr;
+    MG_CUDA(cudaGraphCreate(&g, 0));
+    Status s = [&]() -> Status {
+      cudaGraphConditionalHandle loop;
+      MG_CUDA(cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = loop;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      MG_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      MG_CUDA(cudaStreamBeginCaptureToGraph(main, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      Status cap = [&]() -> Status {
+        MG_TRY(record_cycle(c, main, w));
+        batch_loop_kernel<<<1, 32, 0, main>>>(c->bcount.as<int>(), c->bmaxit + 2, loop);
+        MG_LAUNCH("batch_loop_kernel");
+        return {};
+      }();
+      cudaGraph_t captured = body;
+      const cudaError_t e = cudaStreamEndCapture(main, &captured);
+      MG_TRY(cap);
+      if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+      MG_CUDA(cudaGraphInstantiate(&c->bgraph, g, 0));
+      return {};
+    }();
+    cudaGraphDestroy(g);
+    c->bgraph_kernels = mgcnn_kernel_launches() - launches0;   // kernels per cycle, counted per launch later
+    add_launches(-c->bgraph_kernels);
+    if (s.ok()) {
+      c->bwhile = true;
+      return {};
     }
-    return {};
-  }();
+    cudaGetLastError();
+    if (c->bgraph) cudaGraphExecDestroy(c->bgraph);
+    c->bgraph = nullptr;
+  }
+  // plain graph of one cycle
+  const long long launches1 = mgcnn_kernel_launches();
+  cudaGraph_t g = nullptr;
+  MG_CUDA(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+  Status s = record_cycle(c, main, w);
   cudaError_t e = cudaStreamEndCapture(main, &g);
   if (!s.ok()) {
     if (g) cudaGraphDestroy(g);
     return s;
   }
   if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
-  c->bgraph_kernels = mgcnn_kernel_launches() - launches0;   // kernels captured, not launched
+  c->bgraph_kernels = mgcnn_kernel_launches() - launches1;   // kernels captured, not launched
   add_launches(-c->bgraph_kernels);
   e = cudaGraphInstantiate(&c->bgraph, g, 0);
   cudaGraphDestroy(g);
@@ -367,8 +434,8 @@ Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const 
   MG_CUDA(cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking));
   MG_CUDA(cudaEventCreateWithFlags(&c->bfork, cudaEventDisableTiming));
   MG_TRY(ensure(c->bparams, 2 * sizeof(double)));
-  MG_TRY(ensure(c->bcount, sizeof(int)));
-  MG_CUDA(cudaMallocHost(&c->h_bcount, sizeof(int)));
+  MG_TRY(ensure(c->bcount, 2 * sizeof(int)));
+  MG_CUDA(cudaMallocHost(&c->h_bcount, 2 * sizeof(int)));
   // size classes in order of first appearance
   c->bn = nprob;
   c->bcls_of.assign(nprob, 0);
@@ -426,13 +493,22 @@ Status solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* 
     c->bmaxit = maxit;
     MG_TRY(capture_cycle(c));
   }
-  // cycles: each graph launch checks every active problem and applies one cycle
-  for (int cyc = 0; cyc <= maxit + 1; ++cyc) {
+  if (c->bwhile) {
+    // every cycle of every problem in one graph launch
+    MG_CUDA(cudaMemsetAsync(c->bcount.p, 0, 2 * sizeof(int), main));
     MG_CUDA(cudaGraphLaunch(c->bgraph, main));
-    add_launches(c->bgraph_kernels);
-    MG_CUDA(cudaMemcpyAsync(c->h_bcount, c->bcount.p, sizeof(int), cudaMemcpyDeviceToHost, main));
+    MG_CUDA(cudaMemcpyAsync(c->h_bcount, c->bcount.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, main));
     MG_CUDA(cudaStreamSynchronize(main));
-    if (*c->h_bcount == 0) break;
+    add_launches(c->bgraph_kernels * (long long)c->h_bcount[1]);
+  } else {
+    // each graph launch checks every active problem and applies one cycle
+    for (int cyc = 0; cyc <= maxit + 1; ++cyc) {
+      MG_CUDA(cudaGraphLaunch(c->bgraph, main));
+      add_launches(c->bgraph_kernels);
+      MG_CUDA(cudaMemcpyAsync(c->h_bcount, c->bcount.p, sizeof(int), cudaMemcpyDeviceToHost, main));
+      MG_CUDA(cudaStreamSynchronize(main));
+      if (*c->h_bcount == 0) break;
+    }
   }
   // results back
   Status overall;

@@ -194,7 +194,9 @@ void add_launches(long long k);   // kernels launched through a CUDA graph
 
 // Profiling kinds: finest-level launches bracketed by events when enabled.
 enum ProfKind { kProfResidual = 0, kProfResnet = 1, kProfRestrict = 2, kProfProlong = 3, kProfIn = 4,
-                kProfOut = 5, kProfDown0 = 6, kProfUp0 = 7, kProfKinds = 8 };
+                kProfOut = 5, kProfDown0 = 6, kProfUp0 = 7,
+                // fused down / up kernel of level l >= 1: kProfDownLevel + l, kProfUpLevel + l
+                kProfDownLevel = 8, kProfUpLevel = 8 + kMaxLevels, kProfKinds = 8 + 2 * kMaxLevels };
 int prof_begin(mgcnn_ctx* c, int kind);   // -1 when profiling is off
 void prof_end(mgcnn_ctx* c, int slot);
 

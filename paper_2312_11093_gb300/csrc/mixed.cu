@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(128) in_kernel16(const float* __restrict__ r, 
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     const int jj = j + t / 3 - 1, ii = i + t % 3 - 1;
-    rv[t] = (jj >= 0 && jj < n && ii >= 0 && ii < n) ? r[(size_t)jj * n + ii] : 0.f;
+    rv[t] = (jj >= 0 && jj < n && ii >= 0 && ii < n) ? r[(size_t)jj * r32_pitch(n) + ii] : 0.f;
   }
   bf16* xp = x + (size_t)p * CP;
 #pragma unroll
@@ -414,10 +414,13 @@ __global__ void unpad_bf16_kernel(const bf16* __restrict__ src, double* __restri
   dst[p] = (double)__bfloat162float(src[pix * cp + ch]);
 }
 
-__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, size_t N,
+// dst (row pitch r32_pitch(n)) = FP32 src (times scale)
+__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, int n,
                               const float* __restrict__ scale) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < N) dst[p] = scale ? (float)src[p] * scale[p] : (float)src[p];
+  if (p >= (size_t)n * n) return;
+  const int j = (int)(p / n), i = (int)(p - (size_t)j * n);
+  dst[(size_t)j * r32_pitch(n) + i] = scale ? (float)src[p] * scale[p] : (float)src[p];
 }
 
 template <int CP>
@@ -589,7 +592,7 @@ Status setup_mixed(mgcnn_ctx* c) {
       cs[l] = c->x16b[l].as<bf16>();
       ns[l] = c->lv[l].n;
     }
-    MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
+    MG_TRY(ensure(c->r32, r32_floats(c->lv[0].n) * sizeof(float)));
     const SetupWeights sw = setup_weights(c);
     return setup_fused_levels(c->L, ns, 1, ops, ss, cs, sw, c->cfg.scale_by_diag, c->stream);
   }
@@ -605,7 +608,7 @@ Status setup_mixed(mgcnn_ctx* c) {
     MG_TRY(ensure(c->x16a[l], c->lv[l].N() * cp * sizeof(bf16)));
     MG_TRY(ensure(c->x16b[l], c->lv[l].N() * cp * sizeof(bf16)));
   }
-  MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
+  MG_TRY(ensure(c->r32, r32_floats(c->lv[0].n) * sizeof(float)));
   MG_TRY(run_setup_net_fp32(c, outs));
   for (int l = 0; l < c->L; ++l) {
     const size_t N = c->lv[l].N();
@@ -627,7 +630,7 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega) {
   MG_TRY(ensure(c->s16[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->x16a[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->x16b[l], N * cp * sizeof(bf16)));
-  MG_TRY(ensure(c->r32, c->lv[0].N() * sizeof(float)));
+  MG_TRY(ensure(c->r32, r32_floats(c->lv[0].n) * sizeof(float)));
   const int C = c->cfg.channels;
   if (C == kGmgV10Channels)   // straight into the BF16 layout
     return launch_gmg_v10_setup_bf16(c->op[l].as<double>(), c->s16[l].as<bf16>(), c->lv[l].n, omega, c->stream,
@@ -664,7 +667,7 @@ Status vcycle_mixed_r32(mgcnn_ctx* c, const float* r32, const double* norm2_dev,
 
 Status vcycle_mixed(mgcnn_ctx* c, const double* r, double* e, const double* u_skip) {
   const size_t N = c->lv[0].N();
-  to_f32_kernel<<<grid_for(N, 256), 256, 0, c->stream>>>(r, c->r32.as<float>(), N,
+  to_f32_kernel<<<grid_for(N, 256), 256, 0, c->stream>>>(r, c->r32.as<float>(), c->lv[0].n,
                                                          c->cfg.input_diag ? c->dinv32.as<float>() : nullptr);
   MG_LAUNCH("to_f32_kernel");
   double* norm2 = c->scalars.as<double>() + 2;

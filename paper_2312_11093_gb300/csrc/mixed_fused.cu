@@ -54,15 +54,17 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* r, uint32_t a) {
 __device__ __forceinline__ void ldsm_x2(uint32_t* r, uint32_t a) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
 }
+// The MMAs only read and write registers, so they are not volatile: the
+// compiler may schedule them around the (volatile) shared-memory loads.
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 __device__ __forceinline__ void mma1688(float* d, uint32_t a0, uint32_t a1, uint32_t b0) {
-  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
                : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                : "r"(a0), "r"(a1), "r"(b0));
 }
@@ -110,11 +112,21 @@ constexpr size_t down_xd_bytes() {
   constexpr size_t xd = 16u * pad8(XH * XW), us = (8u * (XH + 6) * (XW + 6) + 127) / 128 * 128;
   return (FIRST && us > xd) ? us : xd;
 }
+// The finest level's residual tile: RH rows of r (halo 2 around the layer
+// output region) staged by TMA from column i0 - 4 (a 16-byte aligned start) in
+// rows of down_rwt floats (a multiple of 4), so region column c sits at tile
+// column c + 2.
+template <int FW, bool HAS_R>
+constexpr int down_rwt() {
+  constexpr int RW = FW + (HAS_R ? 1 : 0) + 4;
+  return (RW + 2 + 3) / 4 * 4;
+}
 template <int FH, int FW, bool FIRST, bool HAS_R>
 constexpr size_t down_smem_bytes() {
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0), ZH = XH + 2, ZW = XW + 2;
-  constexpr int RH = ZH + 2, RW = ZW + 2;
-  return 16u * (2 * pad8(ZH * ZW)) + down_xd_bytes<FH, FW, FIRST, HAS_R>() + (FIRST ? 4u * RH * RW : 0u);
+  constexpr int RH = ZH + 2;
+  return 16u * (2 * pad8(ZH * ZW)) + down_xd_bytes<FH, FW, FIRST, HAS_R>() +
+         (FIRST ? 4u * RH * down_rwt<FW, HAS_R>() : 0u);
 }
 // Up-kernel regions for an FH x FW owned tile at (j0, i0), fine coordinates:
 //   O (layer output):   owned + halo H (H = 1 at the finest level, where W_out
@@ -169,15 +181,13 @@ template <int PITCH>
 __device__ __forceinline__ void strip_conv_at(const uint4* tile, const uint32_t* wf, int base_m, int base_l,
                                               const TapOffsets<PITCH>& to, float* acc) {
   const uint32_t am = sa(tile) + 16u * base_m, al = sa(tile) + 16u * base_l;
+  uint32_t a[4][4], a8[2];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    uint32_t a[4];
-    ldsm_x4(a, am + to.off[s]);
-    mma16816(acc, a, wf[2 * s], wf[2 * s + 1]);
-  }
-  uint32_t a[2];
-  ldsm_x2(a, al + TapOffsets<PITCH>::off8);
-  mma1688(acc, a[0], a[1], wf[8]);
+  for (int s = 0; s < 4; ++s) ldsm_x4(a[s], am + to.off[s]);
+  ldsm_x2(a8, al + TapOffsets<PITCH>::off8);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) mma16816(acc, a[s], wf[2 * s], wf[2 * s + 1]);
+  mma1688(acc, a8[0], a8[1], wf[8]);
 }
 
 // One ResNet layer strip y = x + K z (Eq. heteroresnet) with the skip folded
@@ -190,17 +200,15 @@ __device__ __forceinline__ void layer_strip(const uint4* zt, const uint4* xt, co
                                             int base_m, const TapOffsets<PITCH>& to, float* acc) {
   const int lane = threadIdx.x & 31;
   const uint32_t am = sa(zt) + 16u * base_m;
+  uint32_t a[5][4];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    uint32_t a[4];
-    ldsm_x4(a, am + to.off[s]);
-    mma16816(acc, a, wf[2 * s], wf[2 * s + 1]);
-  }
+  for (int s = 0; s < 4; ++s) ldsm_x4(a[s], am + to.off[s]);
   // lanes 0-15 address rows 0-15 of tap 8 of z (k 0-7), lanes 16-31 the same
   // rows of x at the centre pixel (k 8-15)
-  uint32_t a[4];
-  ldsm_x4(a, (lane < 16) ? am + TapOffsets<PITCH>::off8 : sa(xt) + 16u * (base_m + PITCH + 1));
-  mma16816(acc, a, wf[8], fI);
+  ldsm_x4(a[4], (lane < 16) ? am + TapOffsets<PITCH>::off8 : sa(xt) + 16u * (base_m + PITCH + 1));
+#pragma unroll
+  for (int s = 0; s < 4; ++s) mma16816(acc, a[s], wf[2 * s], wf[2 * s + 1]);
+  mma16816(acc, a[4], wf[8], fI);
 }
 
 // The identity block of the last step's B fragment: k = 8 + ci, n = co, one
@@ -251,6 +259,7 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
                                                   const __grid_constant__ SmallWeights sw,
                                                   const __grid_constant__ CUtensorMap map_x,
                                                   const __grid_constant__ CUtensorMap map_s,
+                                                  const __grid_constant__ CUtensorMap map_r,
                                                   const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fR,
                                                   bf16* __restrict__ xdown, bf16* __restrict__ xc, int n,
                                                   const int* __restrict__ active, int* __restrict__ err) {
@@ -258,10 +267,11 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
   static_assert(FIRST || !RESID, "the residual is fused into the finest level only");
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
   constexpr int ZH = XH + 2, ZW = XW + 2;
-  constexpr int RH = ZH + 2, RW = ZW + 2;
+  constexpr int RH = ZH + 2, RW = ZW + 2, RWT = down_rwt<FW, HAS_R>();
   // zs: s, then z = s * x_in in place (BF16); xs: x_in, for the skip.  Both are
   // TMA destinations: the box of rows j0-1.. and columns i0-1.. of the tensor,
-  // zero outside the grid.
+  // zero outside the grid.  rs (finest level): r on rows j0-2.., columns
+  // i0-4.., zero outside the grid (TMA, or the fused residual pass).
   uint4* zs = reinterpret_cast<uint4*>(fused_dsm);
   uint4* xs = zs + pad8(ZH * ZW);
   uint4* xd = xs + pad8(ZH * ZW);                                   // layer output
@@ -280,11 +290,13 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
     xdown += bz * N * 8;
     if (HAS_R) xc += bz * Nc * 8;
   }
+  constexpr bool R_TMA = FIRST && !RESID;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, (FIRST ? 1u : 2u) * ZH * ZW * 16u);
+    mbar_expect_tx(&bar, (FIRST ? 1u : 2u) * ZH * ZW * 16u + (R_TMA ? 4u * RH * RWT : 0u));
     tma_load_pix(zs, &map_s, i0 - 1, j0 - 1, bz, &bar);
     if (!FIRST) tma_load_pix(xs, &map_x, i0 - 1, j0 - 1, bz, &bar);
+    if (R_TMA) tma_load_f32(rs, &map_r, i0 - 4, j0 - 2, bz, &bar);
   }
 
   uint32_t wk[9], wr[9];
@@ -309,7 +321,6 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
       us[e] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? ra.u[(size_t)gj * n + gi] : 0.0;
     }
     __syncthreads();
-    const float alpha = alpha2[0];
     double rr2 = 0.0;
 #pragma unroll 2
     for (int e = threadIdx.x; e < RH * RW; e += NT) {
@@ -326,21 +337,13 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
         rv = fma(-ra.op[4 * N + p], uc[UW], rv);
         if (rr >= 2 && rr < 2 + FH && cc >= 2 && cc < 2 + FW) rr2 = fma(rv, rv, rr2);
         const float rf = f64_to_f32_rn(rv);
-        v = alpha * (ra.dinv32 ? rf * ra.dinv32[p] : rf);
+        v = ra.dinv32 ? rf * ra.dinv32[p] : rf;
       }
-      rs[e] = v;
+      rs[rr * RWT + cc + 2] = v;
     }
     __shared__ double red[NW];
     rr2 = block_sum_fixed(rr2, red);
     if (threadIdx.x == 0) ra.partial[blockIdx.y * gridDim.x + blockIdx.x] = rr2;
-  } else if constexpr (FIRST) {
-    const float alpha = alpha2[2 * bz];   // the finest level's input scale
-    #pragma unroll 4
-    for (int e = threadIdx.x; e < RH * RW; e += NT) {
-      const int rr = e / RW, cc = e - rr * RW;
-      const int gj = j0 + rr - 2, gi = i0 + cc - 2;
-      rs[e] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? alpha * r[(size_t)gj * n + gi] : 0.f;
-    }
   }
   // the copies of the block's tiles (a uniform decision: every thread agrees
   // before any of them returns)
@@ -350,7 +353,9 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
     return;
   }
   if constexpr (FIRST) {
-    // x_in = W_in * (alpha r) on Z, rounded to BF16 (zero outside the grid); z = s * x_in
+    // x_in = alpha (W_in * r) on Z, rounded to BF16 (zero outside the grid); z =
+    // s * x_in.  alpha is a power of two, so scaling the sums is exact.
+    const float alpha = alpha2[2 * bz];   // the finest level's input scale
     for (int e = threadIdx.x; e < ZH * ZW; e += NT) {
       const int zr = e / ZW, zc = e - zr * ZW;
       const int gj = j0 + zr - 1, gi = i0 + zc - 1;
@@ -358,14 +363,14 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
       if (gj >= 0 && gj < n && gi >= 0 && gi < n) {
         float rv[9];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) rv[t] = rs[(zr + t / 3) * RW + zc + t % 3];
+        for (int t = 0; t < 9; ++t) rv[t] = rs[(zr + t / 3) * RWT + zc + t % 3 + 2];
         float o[8];
 #pragma unroll
         for (int co = 0; co < 8; ++co) {
           float a = 0.f;
 #pragma unroll
           for (int t = 0; t < 9; ++t) a += sw.w_in[t * 8 + co] * rv[t];
-          o[co] = a;
+          o[co] = alpha * a;
         }
         xv = make_uint4(f2bf(o[0], o[1]), f2bf(o[2], o[3]), f2bf(o[4], o[5]), f2bf(o[6], o[7]));
       }
@@ -588,6 +593,16 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
       wh[k] = fOutHi[k * 32 + lane];
       wl[k] = fOutLo[k * 32 + lane];
     }
+    // this thread's u values of the update below, loaded now so that their
+    // latency passes during W_out
+    constexpr int NU = (FH * FW + NT - 1) / NT;
+    double uv[NU];
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      const int e = threadIdx.x + k * NT, rr = e / FW, cc = e - rr * FW;
+      const int gj = j0 + rr, gi = i0 + cc;
+      uv[k] = (u_in && e < FH * FW && gj < n && gi < n) ? u_in[(size_t)gj * n + gi] : 0.0;
+    }
     __syncthreads();
     const float inv_alpha = alpha2[2 * bz + 1];
     float* ev = reinterpret_cast<float*>(ps);   // FH x FW corrections
@@ -613,12 +628,12 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
       }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < FH * FW; e += NT) {
-      const int rr = e / FW, cc = e - rr * FW;
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      const int e = threadIdx.x + k * NT, rr = e / FW, cc = e - rr * FW;
       const int gj = j0 + rr, gi = i0 + cc;
-      if (gj >= n || gi >= n) continue;
-      const size_t qg = (size_t)gj * n + gi;
-      u_out[qg] = (u_in ? u_in[qg] : 0.0) + f32_to_f64_exact(ev[e]);
+      if (e >= FH * FW || gj >= n || gi >= n) continue;
+      u_out[(size_t)gj * n + gi] = uv[k] + f32_to_f64_exact(ev[e]);
     }
   }
 }
@@ -675,9 +690,16 @@ Status launch_down(int l, const FusedLevels& fl, const float* r32, const double*
   else
     MG_TRY(pix8_map(fl, fl.xb[l], nl, ZW, ZH, &mx));
   const ResidIn rin = ra ? *ra : ResidIn{};
+  CUtensorMap mr = ms;   // not read unless the finest level stages r32 by TMA
+  if (first && !ra) {
+    const int RH = FH + R + 4, RWT = has_r ? down_rwt<FW, true>() : down_rwt<FW, false>();
+    const CUtensorMap* m = fl.maps ? fl.maps->f32(r32, nl, r32_pitch(nl), fl.batch, RWT, RH) : nullptr;
+    if (!m) return make_status(MGCNN_ERR_CUDA, "cannot encode the residual's TMA tensor map (n %d)", nl);
+    mr = *m;
+  }
   auto run = [&](auto* kernel, size_t smem) {
-    kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(r32, fl.alpha, rin, w.small, mx, ms, w.f_down, w.f_R, fl.xa[l],
-                                                      xc, nl, active, fl.err);
+    kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(r32, fl.alpha, rin, w.small, mx, ms, mr, w.f_down, w.f_R,
+                                                      fl.xa[l], xc, nl, active, fl.err);
   };
   if (ra && has_r)
     run(down_kernel<FH, FW, true, true, true>, down_smem_bytes<FH, FW, true, true>());
@@ -770,12 +792,12 @@ Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double
   const int L = fl.L;
   if (!opt.after_fused_down0) MG_TRY(launch_alpha(fl, norm2, st));
   for (int l = opt.after_fused_down0 ? 1 : 0; l < L; ++l) {
-    const int ps = (l == 0 && prof_ctx) ? prof_begin(prof_ctx, kProfDown0) : -1;
+    const int ps = prof_ctx ? prof_begin(prof_ctx, l == 0 ? kProfDown0 : kProfDownLevel + l) : -1;
     MG_TRY(launch_down_variant(fl.var_down[l], l, fl, r32, norm2, w, active, st));
     if (prof_ctx) prof_end(prof_ctx, ps);
   }
   for (int l = L - 1; l >= 0; --l) {
-    const int ps = (l == 0 && prof_ctx) ? prof_begin(prof_ctx, kProfUp0) : -1;
+    const int ps = prof_ctx ? prof_begin(prof_ctx, l == 0 ? kProfUp0 : kProfUpLevel + l) : -1;
     MG_TRY(launch_up_variant(fl.var_up[l], l, fl, norm2, e, u_skip, w, active, st));
     if (prof_ctx) prof_end(prof_ctx, ps);
   }

@@ -283,7 +283,7 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
     u += b * N;
     op += b * 5 * N;
     if (r) r += b * N;
-    if (r32) r32 += b * N;
+    if (r32) r32 += b * (size_t)n * ((n + 3) & ~3);
     if (dinv32) dinv32 += b * N;
     partial += b * gridDim.x;
   }
@@ -306,7 +306,7 @@ residual_kernel(const double* __restrict__ f, const double* __restrict__ u, cons
       if (r) r[p] = rv;
       if (r32) {
         const float rf = f64_to_f32_rn(rv);
-        r32[p] = dinv32 ? rf * dinv32[p] : rf;
+        r32[(size_t)j * ((n + 3) & ~3) + i] = dinv32 ? rf * dinv32[p] : rf;
       }
       rr = fma(rv, rv, rr);
     }

@@ -16,6 +16,12 @@ inline int reduction_blocks(size_t N) { return grid_for(N, kResidualBlock); }
 constexpr int kResidualPix = 4;
 inline int residual_blocks(size_t N) { return grid_for(N, (size_t)kResidualBlock * kResidualPix); }
 
+// Row pitch (floats) of the FP32 network input r32: rows start on 16-byte
+// boundaries so that tiles of it can be copied by TMA.  r32 of a problem is
+// n rows of r32_pitch(n) floats (the pad columns are never read).
+__host__ __device__ inline int r32_pitch(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline size_t r32_floats(int n) { return (size_t)n * r32_pitch(n); }
+
 // batch > 1: problems of the same size stored back to back (blockIdx.y selects one).
 Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch = 1);
 Status launch_inject_mu(const double* mu, double* mc, int n, cudaStream_t st);
@@ -24,8 +30,8 @@ Status launch_stencil_nondiv(const double* mu, double* op, int n, double vx, dou
 Status launch_count_bad(const double* v, size_t N, int* count, cudaStream_t st);
 template <typename FT>
 Status launch_features(const double* op, FT* feat, int n, cudaStream_t st, int batch = 1);
-// r = f - A u (FP64), optional FP32 copy r32 (times dinv32 when given), per-block
-// partial sums of r^2.
+// r = f - A u (FP64), optional FP32 copy r32 (times dinv32 when given; row
+// pitch r32_pitch(n)), per-block partial sums of r^2.
 // With batch > 1 every array is per problem, back to back; partial is [batch][blocks].
 Status launch_residual(const double* f, const double* u, const double* op, double* r, float* r32,
                        double* partial, int n, cudaStream_t st, const float* dinv32 = nullptr, int batch = 1);

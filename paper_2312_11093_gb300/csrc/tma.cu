@@ -26,10 +26,10 @@ EncodeFn encoder() {
 
 const CUtensorMap* TmaMaps::pix8(const void* base, int n, int batch, int bw, int bh) {
   for (const Entry& e : entries_)
-    if (e.base == base && e.n == n && e.batch == batch && e.bw == bw && e.bh == bh) return &e.map;
+    if (e.kind == 0 && e.base == base && e.n == n && e.batch == batch && e.bw == bw && e.bh == bh) return &e.map;
   EncodeFn enc = encoder();
   if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || bw < 1 || bw > 256 || bh < 1 || bh > 256) return nullptr;
-  Entry e{base, n, batch, bw, bh, {}};
+  Entry e{base, n, batch, bw, bh, 0, {}};
   const cuuint64_t dims[4] = {8, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch};
   const cuuint64_t strides[3] = {16, 16ull * n, 16ull * n * n};
   const cuuint32_t box[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
@@ -39,6 +39,27 @@ const CUtensorMap* TmaMaps::pix8(const void* base, int n, int batch, int bw, int
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return nullptr;
   if (entries_.size() >= 256) entries_.clear();   // bounded: maps are re-made on demand
+  entries_.push_back(e);
+  return &entries_.back().map;
+}
+
+const CUtensorMap* TmaMaps::f32(const void* base, int n, int pitch, int batch, int bw, int bh) {
+  for (const Entry& e : entries_)
+    if (e.kind == 1 && e.base == base && e.n == n && e.batch == batch && e.bw == bw && e.bh == bh) return &e.map;
+  EncodeFn enc = encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 3) || pitch < n || (bw & 3) || bw < 4 ||
+      bw > 256 || bh < 1 || bh > 256)
+    return nullptr;
+  Entry e{base, n, batch, bw, bh, 1, {}};
+  const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch};
+  const cuuint64_t strides[2] = {4ull * pitch, 4ull * pitch * n};
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  if (enc(&e.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, elem,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return nullptr;
+  if (entries_.size() >= 256) entries_.clear();
   entries_.push_back(e);
   return &entries_.back().map;
 }

@@ -33,12 +33,16 @@ class TmaMaps {
  public:
   // Map of a [batch][n][n][8] BF16 tensor with box bw x bh pixels; nullptr on failure.
   const CUtensorMap* pix8(const void* base, int n, int batch, int bw, int bh);
+  // Map of a [batch][n][pitch] FP32 array (n x n values per problem, rows of
+  // `pitch` floats, pitch a multiple of 4) with box bw x bh values; bw * 4 must
+  // be a multiple of 16.
+  const CUtensorMap* f32(const void* base, int n, int pitch, int batch, int bw, int bh);
   void clear() { entries_.clear(); }
 
  private:
   struct Entry {
     const void* base;
-    int n, batch, bw, bh;
+    int n, batch, bw, bh, kind;   // kind 0: pix8, 1: f32
     CUtensorMap map;
   };
   std::vector<Entry> entries_;
@@ -82,6 +86,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   for (int i = 0; i < kMbarWaitLimit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Box of the 3-D FP32 array at (column x, row y, problem z); x must be a
+// multiple of 4 (16-byte aligned start).
+__device__ __forceinline__ void tma_load_f32(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
 }
 
 // Box of the 4-D pixel tensor at (channel 0, column x, row y, problem z) into

@@ -353,8 +353,10 @@ class Solver:
                         "mgcnn_setup_batched_gmg")
         self.batch_sizes = [int(n) for n in ns]
 
-    def solve_batched(self, rhs, us, tol: float, maxit: int):
-        """Solves every problem in place on us[i].  Returns (status, iters, relres, statuses)."""
+    def solve_batched(self, rhs, us, tol: float, maxit: int, per_problem: bool = False):
+        """Solves every problem in place on us[i].  Returns (status, iters, relres, statuses).
+        per_problem: a problem whose iteration became non-finite is reported in its
+        entry of `statuses` (and the overall status) instead of raising."""
         m = len(rhs)
         fp = (c_void_p * m)(*[_ptr(f, n * n) for f, n in zip(rhs, self.batch_sizes)])
         up = (c_void_p * m)(*[_ptr(u, n * n, True) for u, n in zip(us, self.batch_sizes)])
@@ -363,10 +365,13 @@ class Solver:
         stat = np.zeros(m, dtype=np.int32)
         st = self._L.mgcnn_solve_batched(self._h, m, fp, up, float(tol), int(maxit), iters.ctypes.data,
                                          relres.ctypes.data, stat.ctypes.data)
-        self._check(st, "mgcnn_solve_batched", ok=(OK, NOT_CONVERGED))
+        self._check(st, "mgcnn_solve_batched", ok=(OK, NOT_CONVERGED, ERR_NONFINITE) if per_problem else (OK, NOT_CONVERGED))
         return st, iters, relres, stat
 
-    PROFILE_KINDS = ("residual", "resnet", "restrict", "prolong", "in", "out", "down0", "up0")
+    # class index -> name; the finest level's fused kernels are "down0" / "up0",
+    # level l >= 1 "down<l>" / "up<l>" (slot 8 + 0 and 21 + 0 are unused)
+    PROFILE_KINDS = (("residual", "resnet", "restrict", "prolong", "in", "out", "down0", "up0") +
+                     ("",) + tuple(f"down{l}" for l in range(1, 13)) + ("",) + tuple(f"up{l}" for l in range(1, 13)))
     OPT_FUSED = 1
     OPT_DEVICE_LOOP = 2
     OPT_TILE = 3
@@ -385,7 +390,7 @@ class Solver:
         ms = np.zeros(k)
         cnt = np.zeros(k, dtype=np.int64)
         self._check(self._L.mgcnn_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, k), "mgcnn_profile_read")
-        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(self.PROFILE_KINDS)}
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(self.PROFILE_KINDS) if name}
 
     def setup_tensor_count(self) -> int:
         return int(self._L.mgcnn_setup_tensor_count(self._h))
