@@ -368,13 +368,17 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * mgcnn_solve_krylov; the batched solves keep their own timing.
  * MGCNN_OPT_SYMMETRIC (default 0): the symmetric network variant, see
  * mgcnn_setup_bpx; 1 on, 0 off (weights stay as they are). */
-/* MGCNN_OPT_FUSED_RESIDUAL (default 0): where the fused kernels apply,
- * mgcnn_solve computes each cycle's FP64 residual r = f - A u and its norm
- * inside the finest-level down kernel (on that kernel's tiles and their halo)
- * instead of in a separate residual pass; same FP64 arithmetic per unknown
- * (bit-identical iterates), the norm summed in a different order.  Off by
- * default: the halo recomputation and the kernel's plain FP64 loads make it
- * slower than the separate pass. */
+/* MGCNN_OPT_FUSED_RESIDUAL (default 0): where mgcnn_solve forms each cycle's FP64
+ * residual r = f - A u and its norm when the fused kernels apply.  0: a separate
+ * residual pass before each cycle.  1: inside the finest-level down kernel, on
+ * that kernel's tiles and their halo.  2: inside the finest-level up kernel, from
+ * the u + e it has just formed (its tiles carry a halo of one more pixel), for
+ * the next cycle; the first residual comes from the separate pass.  The same
+ * FP64 arithmetic per unknown in all three (bit-identical iterates); the norm is
+ * summed in a different order.  Modes 1 and 2 run slower than the separate pass
+ * on this GPU (the fused kernels add latency-bound FP64 loads to a kernel that
+ * is latency-bound already, mode 1 also FP64 work on the halo), so 0 is the
+ * default. */
 enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3, MGCNN_OPT_SYMMETRIC = 4,
        MGCNN_OPT_FUSED_RESIDUAL = 5 };
 int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);

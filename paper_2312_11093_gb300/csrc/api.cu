@@ -498,7 +498,7 @@ void mgcnn_destroy(mgcnn_ctx* c) {
     release(c->xa[l]); release(c->xb[l]);
   }
   release(c->setup_a); release(c->setup_b); release(c->setup_c); release(c->setup_d);
-  release(c->feat); release(c->f); release(c->u); release(c->r); release(c->e);
+  release(c->feat); release(c->f); release(c->u); release(c->u2); release(c->r); release(c->e);
   release(c->r32); release(c->partial); release(c->scalars);
   mixed_release(c);
   train_release(c);
@@ -785,10 +785,18 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
     const bool mixed = c->cfg.precision == MGCNN_PREC_MIXED_BF16;
     // mixed path with the fused kernels: the finest down kernel computes r_k itself
     const bool fres = fused_residual_applies(c);
+    const bool upres = fused_residual_mode(c) == 2;   // the finest up kernel forms the next residual
     if (fres) MG_TRY(fused_cycle_setup(c, df, du, c->scalars.as<double>() + 1));
+    if (upres) {
+      MG_TRY(ensure(c->u2, N * sizeof(double)));
+      MG_TRY(upres_cycle_setup(c, df, du, c->scalars.as<double>(), c->stream));
+    }
+    double* ucur = du;   // upres: the iterate alternates between du and c->u2
     for (int k = 0;; ++k) {
       if (fres) {
         MG_TRY(fused_cycle_residual(c, df, du, c->scalars.as<double>(), nullptr, c->stream, true));
+      } else if (upres) {
+        // ||r_k||^2 is in scalars[0] already
       } else {
         // mixed: the V-cycle consumes an FP32 copy of r (scaled in-kernel), FP64 r is not stored
         const int ps = prof_begin(c, kProfResidual);
@@ -814,11 +822,17 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
       }
       if (fres)
         MG_TRY(fused_cycle_rest(c, du, c->scalars.as<double>(), nullptr, c->stream, true));
+      else if (upres) {
+        double* unext = (ucur == du) ? c->u2.as<double>() : du;
+        MG_TRY(upres_cycle(c, df, ucur, unext, c->scalars.as<double>(), nullptr, c->stream, true));
+        ucur = unext;
+      }
       else if (mixed)
         MG_TRY(vcycle_mixed_r32(c, c->r32.as<float>(), c->scalars.as<double>(), du, du));
       else
         MG_TRY(vcycle_fp64(c, c->r.as<double>(), du, du));
     }
+    if (ucur != du) MG_CUDA(cudaMemcpyAsync(du, ucur, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     MG_TRY(stage_out_finish(c, u, du, N, host));
     MG_TRY(sync(c));
     return result;
@@ -999,7 +1013,8 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
       c->device_loop = value ? 1 : 0;
       return finish(c, {});
     case MGCNN_OPT_FUSED_RESIDUAL:
-      c->fuse_residual = value ? 1 : 0;
+      if (value < 0 || value > 2) return finish(c, make_status(MGCNN_ERR_ARG, "fused residual mode is 0, 1 or 2"));
+      c->fuse_residual = value;
       c->sgraph_valid = false;
       c->tuned = c->tile_fixed >= 0;   // the finest down kernel is tuned in the mode it runs in
       return finish(c, {});

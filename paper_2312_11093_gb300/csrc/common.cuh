@@ -106,13 +106,18 @@ struct mgcnn_ctx {
   mgcnn::DevBuf setup_a, setup_b, setup_c, setup_d;  // setup-phase scratch
   mgcnn::DevBuf feat;                     // setup features [n^2][5]
   mgcnn::DevBuf f, u, r, e;               // finest-grid FP64 vectors (staging / work)
+  mgcnn::DevBuf u2;                       // second iterate buffer: with the residual formed in the up
+                                          // kernel, cycles alternate u -> u2 -> u (halo reads of u_k
+                                          // must not see a neighbour's u_{k+1})
   mgcnn::DevBuf r32;                      // FP32 network input (r or D^{-1} r) for the mixed path
   mgcnn::DevBuf dinv, dinv32;             // 1/a_C of the finest level, FP64 and FP32
   mgcnn::DevBuf partial;                  // per-block partial sums of reductions
   // mixed-precision path (mixed.cu)
   int cp = 0;                             // channels padded for the tensor cores (8 or 16)
   int fused = 1;                          // use the fused level kernels when they apply
-  int fuse_residual = 0;                  // mgcnn_solve: the finest down kernel computes the residual
+  int fuse_residual = 0;                  // mgcnn_solve: where the residual is formed (MGCNN_OPT_FUSED_RESIDUAL)
+  bool pdl = true;                        // level kernels with programmatic dependent launch (off if a graph
+                                          // with programmatic edges cannot be built)
   int tile_var[2][mgcnn::kMaxLevels] = {};  // autotuned tile variants (down, up) per level
   bool tuned = false;                       // set by the first solve after a setup
   int tile_fixed = -1;                      // MGCNN_OPT_TILE: a fixed tile variant, or -1 (autotune)

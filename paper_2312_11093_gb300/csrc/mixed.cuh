@@ -31,11 +31,21 @@ struct ResidIn {
   const float* dinv32 = nullptr;         // optional n^2: the network input is D^{-1} r
   double* partial = nullptr;             // per block: sum of r^2 over its owned pixels
 };
+// Outputs of the finest up kernel when it also forms the next cycle's residual
+// from u + e (inputs f, op, dinv32 as in ResidIn).
+struct ResidOut {
+  const double* f = nullptr;             // n^2
+  const double* op = nullptr;            // 5 n^2
+  const float* dinv32 = nullptr;         // optional n^2
+  float* r32 = nullptr;                  // FP32 D^{-1} r, rows of r32_pitch(n)
+  double* partial = nullptr;             // per block: sum of r^2 over its owned pixels
+};
 struct FusedLevels {
   int L = 0, batch = 1;
   TmaMaps* maps = nullptr;               // tensor-map cache of the owner (context or batch class)
   int* err = nullptr;                    // device flag: a block's tile copies timed out
   float* alpha = nullptr;                // device [batch][2]: input scale alpha and 1 / alpha per problem
+  bool pdl = false;                      // launch the level kernels with programmatic dependent launch
   int n[kMaxLevels] = {};
   int var_down[kMaxLevels] = {};         // tile variant per level (autotuned)
   int var_up[kMaxLevels] = {};
@@ -51,6 +61,7 @@ struct FusedWeights {
 };
 struct FusedCycleOpt {
   bool after_fused_down0 = false;        // the finest down kernel ran already, with the residual fused in
+  const ResidOut* resid_out = nullptr;   // the finest up kernel forms the next residual
 };
 Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
                            const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
@@ -65,7 +76,8 @@ Status fused_set_alpha(const FusedLevels& fl, const double* norm2, cudaStream_t 
 int fused_down0_blocks(int n, int variant);
 size_t fused_partials_max(int n);          // the largest fused_down0_blocks over the tile variants
 Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, double* scratch,
-                      const FusedWeights& w, cudaStream_t st, int reps, const ResidIn* ra = nullptr);
+                      const FusedWeights& w, cudaStream_t st, int reps, const ResidIn* ra = nullptr,
+                      const ResidOut* ro = nullptr);
 // Pointers into ctx->wmix for the fused kernels (valid after mixed_set_weights).
 FusedWeights fused_weights(const mgcnn_ctx* c);
 bool fused_supported(const mgcnn_ctx* c);
@@ -93,6 +105,20 @@ Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, dou
 //                        input scale from rn2_dev
 // `active` (nullable) is the device flag that makes the kernels return at once.
 bool fused_residual_applies(const mgcnn_ctx* c);
+// MGCNN_OPT_FUSED_RESIDUAL as it applies to this context: 0 separate residual
+// pass, 1 residual in the finest down kernel (the functions above), 2 residual in
+// the finest up kernel:
+//   upres_cycle_setup  once per solve: autotuning, r_0 (stand-alone kernel) and
+//                      ||r_0||^2 into rn2_dev
+//   per cycle k (after the convergence test on rn2_dev):
+//   upres_cycle        the whole V-cycle, u_out = u_in + B r_k, and r_{k+1}
+//                      (FP32 copy and ||r_{k+1}||^2 into rn2_dev) formed by the
+//                      finest up kernel; u_in and u_out must differ (a tile reads
+//                      u_in around its pixels while the neighbours write u_out)
+int fused_residual_mode(const mgcnn_ctx* c);
+Status upres_cycle_setup(mgcnn_ctx* c, const double* f, const double* u, double* rn2_dev, cudaStream_t st);
+Status upres_cycle(mgcnn_ctx* c, const double* f, const double* u_in, double* u_out, double* rn2_dev,
+                   const int* active, cudaStream_t st, bool profile);
 Status fused_cycle_setup(mgcnn_ctx* c, const double* f, const double* u, const double* fn2_dev);
 Status fused_cycle_residual(mgcnn_ctx* c, const double* f, const double* u, double* rn2_dev, const int* active,
                             cudaStream_t st, bool profile);

@@ -138,21 +138,30 @@ constexpr size_t down_smem_bytes() {
 //                       feeds the TCNN (Q starts on an odd row and column)
 //   coarse pixels (J, I) of the quads plus one row and column (the quads'
 //   sources J..J+1, I..I+1)
-template <int FH, int FW, bool LAST, bool HAS_P>
+//   E (finest level):   where e = W_out * x_fin and u + e are formed: the owned
+//                       pixels, plus a halo of one when the kernel also forms
+//                       the next residual (RES), which needs u + e around
+//                       every owned pixel; O = E + halo 1
+template <int FH, int FW, bool LAST, bool HAS_P, bool RES = false>
 struct UpGeom {
-  static constexpr int H = LAST ? 1 : 0;
+  static_assert(LAST || !RES, "the residual is formed on the finest level only");
+  static constexpr int HE = RES ? 1 : 0;
+  static constexpr int EH = FH + 2 * HE, EW = FW + 2 * HE;
+  static constexpr int H = LAST ? HE + 1 : 0;
   static constexpr int OH = FH + 2 * H, OW = FW + 2 * H;
   static constexpr int PH = OH + 2, PW = OW + 2;
-  static constexpr int QOFF = (HAS_P && LAST) ? 1 : 0;    // P's offset inside Q
+  static constexpr int QOFF = (HAS_P && (H & 1)) ? 1 : 0;  // P's offset inside Q (Q starts on an odd row)
   static constexpr int QH = PH + 2 * QOFF, QW = PW + 2 * QOFF;
   static constexpr int NQH = QH / 2, NQW = QW / 2;         // quads
   static constexpr int CQH = NQH + 1, CQW = NQW + 1;       // coarse pixels staged
   static_assert(!HAS_P || (QH % 2 == 0 && QW % 2 == 0), "whole quads");
+  // finest level, after the layer: e (FP32) on E, then u + e (FP64) on E, in the Q tiles
+  static_assert(!LAST || EH * EW * (4 + 8) + 8 <= 16 * QH * QW, "E staging in the ps tile");
 };
 // Tiles: ps, zs on Q; cs; on the finest level os on O.
-template <int FH, int FW, bool LAST, bool HAS_P>
+template <int FH, int FW, bool LAST, bool HAS_P, bool RES = false>
 constexpr size_t up_smem_bytes() {
-  using G = UpGeom<FH, FW, LAST, HAS_P>;
+  using G = UpGeom<FH, FW, LAST, HAS_P, RES>;
   return 16u * (2 * pad8(G::QH * G::QW) + (HAS_P ? pad8(G::CQH * G::CQW) : 0) + (LAST ? pad8(G::OH * G::OW) : 0));
 }
 extern __shared__ __align__(128) unsigned char fused_dsm[];
@@ -213,6 +222,14 @@ __device__ __forceinline__ void layer_strip(const uint4* zt, const uint4* xt, co
 
 // The identity block of the last step's B fragment: k = 8 + ci, n = co, one
 // where ci == co (this lane holds ci = 2q, 2q + 1 for co = g).
+// Programmatic dependent launch: a level kernel launched with the programmatic
+// stream-serialisation attribute may start while its predecessor finishes; it
+// runs its prologue (barrier set-up, weight fragments), then waits here until
+// the predecessor grid has completed and its memory is visible.  Without the
+// attribute both instructions have no effect.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t identity_frag() {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const uint32_t one = 0x3F80u;   // BF16 1.0
@@ -283,27 +300,28 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
   const size_t N = (size_t)n * n;
   // problem blockIdx.z of a batch of equal-size problems stored back to back
   const int bz = blockIdx.z;
-  if (active && !active[bz]) return;
   {
     const size_t Nc = (size_t)((n - 1) / 2) * ((n - 1) / 2);
     if (FIRST) r += bz * N;
     xdown += bz * N * 8;
     if (HAS_R) xc += bz * Nc * 8;
   }
-  constexpr bool R_TMA = FIRST && !RESID;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, (FIRST ? 1u : 2u) * ZH * ZW * 16u + (R_TMA ? 4u * RH * RWT : 0u));
-    tma_load_pix(zs, &map_s, i0 - 1, j0 - 1, bz, &bar);
-    if (!FIRST) tma_load_pix(xs, &map_x, i0 - 1, j0 - 1, bz, &bar);
-    if (R_TMA) tma_load_f32(rs, &map_r, i0 - 4, j0 - 2, bz, &bar);
-  }
-
+  // prologue (may overlap the previous kernel's end): weight fragments, barrier
   uint32_t wk[9], wr[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     wk[k] = fK[k * 32 + lane];
     if (HAS_R) wr[k] = fR[k * 32 + lane];
+  }
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  pdl_wait();
+  if (active && !active[bz]) return;
+  constexpr bool R_TMA = FIRST && !RESID;
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, (FIRST ? 1u : 2u) * ZH * ZW * 16u + (R_TMA ? 4u * RH * RWT : 0u));
+    tma_load_pix(zs, &map_s, i0 - 1, j0 - 1, bz, &bar);
+    if (!FIRST) tma_load_pix(xs, &map_x, i0 - 1, j0 - 1, bz, &bar);
+    if (R_TMA) tma_load_f32(rs, &map_r, i0 - 4, j0 - 2, bz, &bar);
   }
   __syncthreads();   // barrier initialised
 
@@ -364,15 +382,18 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
         float rv[9];
 #pragma unroll
         for (int t = 0; t < 9; ++t) rv[t] = rs[(zr + t / 3) * RWT + zc + t % 3 + 2];
-        float o[8];
+        // channel pairs on packed FP32 FMAs: per lane the same fused multiply-adds in
+        // the same tap order as one channel at a time
+        float2 o[4];
 #pragma unroll
-        for (int co = 0; co < 8; ++co) {
-          float a = 0.f;
+        for (int k = 0; k < 4; ++k) {
+          float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int t = 0; t < 9; ++t) a += sw.w_in[t * 8 + co] * rv[t];
-          o[co] = alpha * a;
+          for (int t = 0; t < 9; ++t)
+            a = __ffma2_rn(make_float2(sw.w_in[t * 8 + 2 * k], sw.w_in[t * 8 + 2 * k + 1]), make_float2(rv[t], rv[t]), a);
+          o[k] = make_float2(alpha * a.x, alpha * a.y);
         }
-        xv = make_uint4(f2bf(o[0], o[1]), f2bf(o[2], o[3]), f2bf(o[4], o[5]), f2bf(o[6], o[7]));
+        xv = make_uint4(f2bf(o[0].x, o[0].y), f2bf(o[1].x, o[1].y), f2bf(o[2].x, o[2].y), f2bf(o[3].x, o[3].y));
       }
       xs[e] = xv;
       zs[e] = mul8(xv, zs[e]);
@@ -430,6 +451,7 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
       }
     }
   }
+  pdl_trigger();   // the next kernel may start its prologue
 }
 
 // TCNN-add on the tensor cores over the quads of Q: each 16 quads are a GEMM
@@ -442,14 +464,11 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
 // into zs.  Coarse pixels outside the coarse grid are staged as zeros, which
 // makes the sum zero on every fine pixel outside the fine grid.
 template <class G>
-__device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, const uint4* cs, const uint32_t* __restrict__ fTc) {
+__device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, const uint4* cs, const uint32_t* fq) {
   constexpr int NQ = G::NQH * G::NQW, NS = (NQ + 15) / 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, q = lane & 3, kh = lane >> 4;
   const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
-  uint32_t fq[kTcnnQuadRegs];
-#pragma unroll
-  for (int k = 0; k < kTcnnQuadRegs; ++k) fq[k] = fTc[k * 32 + lane];
   const uint32_t fI = identity_frag();
   const uint32_t cs0 = sa(cs), ps0 = sa(ps);
   for (int st = warp; st < NS; st += NW) {
@@ -495,7 +514,7 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, const uint4* cs
 // Up kernel (geometry in UpGeom).  Level l: x_pre = x_down + TCNN(x_{l+1}) on P
 // (or x_down on the coarsest level), layer x_fin = x_pre + K_up (s * x_pre) on O;
 // finest level: e = W_out * x_fin / alpha, u_out = u_in + e.
-template <int FH, int FW, bool LAST, bool HAS_P>
+template <int FH, int FW, bool LAST, bool HAS_P, bool RES>
 __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUtensorMap map_xd,
                                                 const __grid_constant__ CUtensorMap map_s,
                                                 const __grid_constant__ CUtensorMap map_c,
@@ -504,9 +523,11 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
                                                 const uint32_t* __restrict__ fOutLo,
                                                 const float* __restrict__ alpha2, const double* __restrict__ u_in,
                                                 bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
-                                                const int* __restrict__ active, int* __restrict__ err) {
-  using G = UpGeom<FH, FW, LAST, HAS_P>;
+                                                const int* __restrict__ active, int* __restrict__ err,
+                                                const __grid_constant__ ResidOut ro) {
+  using G = UpGeom<FH, FW, LAST, HAS_P, RES>;
   constexpr int H = G::H, OH = G::OH, OW = G::OW, QW = G::QW, QOFF = G::QOFF;
+  constexpr int HE = G::HE, EH = G::EH, EW = G::EW;
   // TMA destinations (zero outside the grid): ps = x_down on Q, then x_pre;
   // zs = s on Q, then s * x_pre; cs = the quads' coarse pixels
   uint4* ps = reinterpret_cast<uint4*>(fused_dsm);
@@ -518,7 +539,6 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   const int qj0 = j0 - H - 1 - QOFF, qi0 = i0 - H - 1 - QOFF;         // Q's corner (odd when HAS_P)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int bz = blockIdx.z;
-  if (active && !active[bz]) return;
   {
     const size_t N = (size_t)n * n;
     if (LAST) {
@@ -528,8 +548,16 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
       xfin += bz * N * 8;
     }
   }
+  // weight fragments of the TCNN and of the layer, loaded before the tiles land
+  uint32_t fq[kTcnnQuadRegs], wk[9];
+#pragma unroll
+  for (int k = 0; k < kTcnnQuadRegs; ++k) fq[k] = HAS_P ? fTc[k * 32 + lane] : 0u;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) wk[k] = fK[k * 32 + lane];
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  pdl_wait();
+  if (active && !active[bz]) return;
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
     mbar_expect_tx(&bar, (2u * G::QH * QW + (HAS_P ? G::CQH * G::CQW : 0u)) * 16u);
     tma_load_pix(ps, &map_xd, qi0, qj0, bz, &bar);
     tma_load_pix(zs, &map_s, qi0, qj0, bz, &bar);
@@ -544,7 +572,7 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   }
 
   if constexpr (HAS_P) {
-    tcnn_quads<G>(ps, zs, cs, fTc);
+    tcnn_quads<G>(ps, zs, cs, fq);
   } else {
     for (int e = threadIdx.x; e < G::QH * QW; e += NT) zs[e] = mul8(ps[e], zs[e]);
   }
@@ -555,9 +583,6 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   // (orow + QOFF + 1, ocol + QOFF + 1)
   const int g = lane >> 2, q = lane & 3;
   {
-    uint32_t wk[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) wk[k] = fK[k * 32 + lane];
     constexpr int NO = OH * OW, NSTRIP = (NO + 15) / 16;
     const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
     const TapOffsets<QW> to;
@@ -586,7 +611,8 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
     // W_out on the tensor cores: an 8 -> 8 channel layer whose only nonzero
     // output channel is 0, with the FP32 weights split as hi + lo BF16 (the two
     // products are accumulated in FP32, so the weights keep ~16 bits); strips of
-    // 16 owned pixels of one row
+    // 16 pixels of E in row-major order.  E pixel (er, ec) reads the taps around
+    // O pixel (er + 1, ec + 1).
     uint32_t wh[9], wl[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -594,26 +620,26 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
       wl[k] = fOutLo[k * 32 + lane];
     }
     // this thread's u values of the update below, loaded now so that their
-    // latency passes during W_out
-    constexpr int NU = (FH * FW + NT - 1) / NT;
+    // latency passes during W_out (zero outside the grid)
+    constexpr int NE = EH * EW, NU = (NE + NT - 1) / NT;
     double uv[NU];
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
-      const int e = threadIdx.x + k * NT, rr = e / FW, cc = e - rr * FW;
-      const int gj = j0 + rr, gi = i0 + cc;
-      uv[k] = (u_in && e < FH * FW && gj < n && gi < n) ? u_in[(size_t)gj * n + gi] : 0.0;
+      const int e = threadIdx.x + k * NT, er = e / EW, ec = e - er * EW;
+      const int gj = j0 - HE + er, gi = i0 - HE + ec;
+      uv[k] = (u_in && e < NE && gj >= 0 && gj < n && gi >= 0 && gi < n) ? u_in[(size_t)gj * n + gi] : 0.0;
     }
     __syncthreads();
     const float inv_alpha = alpha2[2 * bz + 1];
-    float* ev = reinterpret_cast<float*>(ps);   // FH x FW corrections
-    static_assert(FH * FW * sizeof(float) <= G::QH * QW * sizeof(uint4), "correction staging");
-    constexpr int SPRO = (FW + 15) / 16;
+    float* ev = reinterpret_cast<float*>(ps);                                  // e on E
+    double* un = reinterpret_cast<double*>(ps) + (NE + 1) / 2;                  // u + e on E
     const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
     const TapOffsets<OW> to;
-    for (int st = warp; st < FH * SPRO; st += NW) {
-      const int rr = st / SPRO, c0 = (st - rr * SPRO) * 16;
+    for (int st = warp; st < (NE + 15) / 16; st += NW) {
+      const int pm = min(st * 16 + mrow, NE - 1), pl = min(st * 16 + lrow, NE - 1);
+      const int rm = pm / EW, rl = pl / EW;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      const int bm = rr * OW + min(c0 + mrow, FW - 1), bl = rr * OW + min(c0 + lrow, FW - 1);
+      const int bm = rm * OW + (pm - rm * EW), bl = rl * OW + (pl - rl * EW);
       strip_conv_at<OW>(os, wh, bm, bl, to, acc);
       strip_conv_at<OW>(os, wl, bm, bl, to, acc);
       // output channel 0 sits in the q == 0 lanes: stage it in shared memory
@@ -622,20 +648,54 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
       if (q == 0) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int cc = c0 + g + 8 * h;
-          if (cc < FW) ev[rr * FW + cc] = acc[2 * h] * inv_alpha;
+          const int p = st * 16 + g + 8 * h;
+          if (p < NE) ev[p] = acc[2 * h] * inv_alpha;
         }
       }
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
-      const int e = threadIdx.x + k * NT, rr = e / FW, cc = e - rr * FW;
-      const int gj = j0 + rr, gi = i0 + cc;
-      if (e >= FH * FW || gj >= n || gi >= n) continue;
-      u_out[(size_t)gj * n + gi] = uv[k] + f32_to_f64_exact(ev[e]);
+      const int e = threadIdx.x + k * NT, er = e / EW, ec = e - er * EW;
+      const int gj = j0 - HE + er, gi = i0 - HE + ec;
+      if (e >= NE) continue;
+      const bool in = gj >= 0 && gj < n && gi >= 0 && gi < n;
+      const double un_e = in ? uv[k] + f32_to_f64_exact(ev[e]) : 0.0;
+      if (RES) un[e] = un_e;
+      if (in && er >= HE && er < HE + FH && ec >= HE && ec < HE + FW) u_out[(size_t)gj * n + gi] = un_e;
+    }
+    if constexpr (RES) {
+      // the next cycle's residual on the owned pixels: r = f - A u (FP64, Eq. 1)
+      // with the same five FMAs, in the same order, as the stand-alone residual
+      // kernel, from u + e of this block (its halo pixels hold the same bits as
+      // the neighbouring blocks' owned pixels: every pixel's e is the same
+      // instruction sequence on the same data); the FP32 copy of D^{-1} r for
+      // the next cycle and the block's partial sum of r^2
+      __syncthreads();
+      const size_t N = (size_t)n * n;
+      double rr2 = 0.0;
+      const int pitch = r32_pitch(n);
+      for (int e = threadIdx.x; e < FH * FW; e += NT) {
+        const int rr = e / FW, cc = e - rr * FW;
+        const int gj = j0 + rr, gi = i0 + cc;
+        if (gj >= n || gi >= n) continue;
+        const size_t p = (size_t)gj * n + gi;
+        const double* uc = un + (rr + 1) * EW + cc + 1;
+        double rv = fma(-ro.op[p], uc[0], ro.f[p]);
+        rv = fma(-ro.op[N + p], uc[-1], rv);
+        rv = fma(-ro.op[2 * N + p], uc[1], rv);
+        rv = fma(-ro.op[3 * N + p], uc[-EW], rv);
+        rv = fma(-ro.op[4 * N + p], uc[EW], rv);
+        rr2 = fma(rv, rv, rr2);
+        const float rf = f64_to_f32_rn(rv);
+        ro.r32[(size_t)gj * pitch + gi] = ro.dinv32 ? rf * ro.dinv32[p] : rf;
+      }
+      __shared__ double red[NW];
+      rr2 = block_sum_fixed(rr2, red);
+      if (threadIdx.x == 0) ro.partial[blockIdx.y * gridDim.x + blockIdx.x] = rr2;
     }
   }
+  pdl_trigger();
 }
 
 // Dynamic shared memory of a kernel instantiation: above 48 KB the kernel must be
@@ -660,6 +720,25 @@ size_t dyn_smem_allow(const void* kernel, size_t bytes) {
 template <typename K>
 size_t dyn_smem(K* kernel, size_t bytes) {
   return dyn_smem_allow(reinterpret_cast<const void*>(kernel), bytes);
+}
+
+// Launch of a level kernel; with `pdl` the launch may begin while the previous
+// kernel in the stream finishes (programmatic stream serialisation: the kernel
+// waits for it in pdl_wait before touching its output).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_level(void (*kernel)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, bool pdl,
+                         Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Tensor map of a level tensor for a box of bw x bh pixels (copied out of the
@@ -697,9 +776,10 @@ Status launch_down(int l, const FusedLevels& fl, const float* r32, const double*
     if (!m) return make_status(MGCNN_ERR_CUDA, "cannot encode the residual's TMA tensor map (n %d)", nl);
     mr = *m;
   }
+  cudaError_t le = cudaSuccess;
   auto run = [&](auto* kernel, size_t smem) {
-    kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(r32, fl.alpha, rin, w.small, mx, ms, mr, w.f_down, w.f_R,
-                                                      fl.xa[l], xc, nl, active, fl.err);
+    le = launch_level(kernel, grid, dyn_smem(kernel, smem), st, fl.pdl, r32, (const float*)fl.alpha, rin, w.small, mx,
+                      ms, mr, w.f_down, w.f_R, fl.xa[l], xc, nl, active, fl.err);
   };
   if (ra && has_r)
     run(down_kernel<FH, FW, true, true, true>, down_smem_bytes<FH, FW, true, true>());
@@ -713,16 +793,19 @@ Status launch_down(int l, const FusedLevels& fl, const float* r32, const double*
     run(down_kernel<FH, FW, false, true, false>, down_smem_bytes<FH, FW, false, true>());
   else
     run(down_kernel<FH, FW, false, false, false>, down_smem_bytes<FH, FW, false, false>());
+  if (le != cudaSuccess) return cuda_status(le, "down_kernel launch");
   MG_LAUNCH("down_kernel");
   return {};
 }
 
 template <int FH, int FW>
 Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, const double* u_skip,
-                 const FusedWeights& w, const int* active, cudaStream_t st) {
+                 const FusedWeights& w, const int* active, cudaStream_t st, const ResidOut* ro) {
   const int nl = fl.n[l];
   const bool last = l == 0, has_p = l + 1 < fl.L;
+  if (ro && (!last || fl.batch != 1)) return make_status(MGCNN_ERR_STATE, "fused residual: finest level, one problem");
   const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
+  const ResidOut rout = ro ? *ro : ResidOut{};
   auto run = [&](auto* kernel, size_t smem, bf16* xfin, auto geom) -> Status {
     using G = decltype(geom);
     CUtensorMap mxd, ms, mc;
@@ -732,20 +815,29 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
       MG_TRY(pix8_map(fl, fl.xb[l + 1], fl.n[l + 1], G::CQW, G::CQH, &mc));
     else
       mc = ms;   // not read on the coarsest level
-    kernel<<<grid, NT, dyn_smem(kernel, smem), st>>>(mxd, ms, mc, w.f_up, w.f_tcnn, w.f_out_hi, w.f_out_lo, fl.alpha,
-                                                      u_skip, xfin, e, nl, active, fl.err);
+    const cudaError_t le = launch_level(kernel, grid, dyn_smem(kernel, smem), st, fl.pdl, mxd, ms, mc, w.f_up,
+                                        w.f_tcnn, w.f_out_hi, w.f_out_lo, (const float*)fl.alpha, u_skip, xfin, e, nl,
+                                        active, fl.err, rout);
+    if (le != cudaSuccess) return cuda_status(le, "up_kernel launch");
     return {};
   };
-  if (last && has_p)
-    MG_TRY(run(up_kernel<FH, FW, true, true>, up_smem_bytes<FH, FW, true, true>(), nullptr, UpGeom<FH, FW, true, true>{}));
+  if (ro && has_p)
+    MG_TRY(run(up_kernel<FH, FW, true, true, true>, up_smem_bytes<FH, FW, true, true, true>(), nullptr,
+               UpGeom<FH, FW, true, true, true>{}));
+  else if (ro)
+    MG_TRY(run(up_kernel<FH, FW, true, false, true>, up_smem_bytes<FH, FW, true, false, true>(), nullptr,
+               UpGeom<FH, FW, true, false, true>{}));
+  else if (last && has_p)
+    MG_TRY(run(up_kernel<FH, FW, true, true, false>, up_smem_bytes<FH, FW, true, true>(), nullptr,
+               UpGeom<FH, FW, true, true>{}));
   else if (last)
-    MG_TRY(run(up_kernel<FH, FW, true, false>, up_smem_bytes<FH, FW, true, false>(), nullptr,
+    MG_TRY(run(up_kernel<FH, FW, true, false, false>, up_smem_bytes<FH, FW, true, false>(), nullptr,
                UpGeom<FH, FW, true, false>{}));
   else if (has_p)
-    MG_TRY(run(up_kernel<FH, FW, false, true>, up_smem_bytes<FH, FW, false, true>(), fl.xb[l],
+    MG_TRY(run(up_kernel<FH, FW, false, true, false>, up_smem_bytes<FH, FW, false, true>(), fl.xb[l],
                UpGeom<FH, FW, false, true>{}));
   else
-    MG_TRY(run(up_kernel<FH, FW, false, false>, up_smem_bytes<FH, FW, false, false>(), fl.xb[l],
+    MG_TRY(run(up_kernel<FH, FW, false, false, false>, up_smem_bytes<FH, FW, false, false>(), fl.xb[l],
                UpGeom<FH, FW, false, false>{}));
   MG_LAUNCH("up_kernel");
   return {};
@@ -766,13 +858,13 @@ Status launch_down_variant(int v, int l, const FusedLevels& fl, const float* r32
 }
 
 Status launch_up_variant(int v, int l, const FusedLevels& fl, const double* norm2, double* e, const double* u_skip,
-                         const FusedWeights& w, const int* active, cudaStream_t st) {
+                         const FusedWeights& w, const int* active, cudaStream_t st, const ResidOut* ro = nullptr) {
   switch (v) {
-    case 1: return launch_up<8, 32>(l, fl, norm2, e, u_skip, w, active, st);
-    case 2: return launch_up<16, 16>(l, fl, norm2, e, u_skip, w, active, st);
-    case 3: return launch_up<32, 32>(l, fl, norm2, e, u_skip, w, active, st);
-    case 4: return launch_up<24, 32>(l, fl, norm2, e, u_skip, w, active, st);
-    default: return launch_up<16, 32>(l, fl, norm2, e, u_skip, w, active, st);
+    case 1: return launch_up<8, 32>(l, fl, norm2, e, u_skip, w, active, st, ro);
+    case 2: return launch_up<16, 16>(l, fl, norm2, e, u_skip, w, active, st, ro);
+    case 3: return launch_up<32, 32>(l, fl, norm2, e, u_skip, w, active, st, ro);
+    case 4: return launch_up<24, 32>(l, fl, norm2, e, u_skip, w, active, st, ro);
+    default: return launch_up<16, 32>(l, fl, norm2, e, u_skip, w, active, st, ro);
   }
 }
 
@@ -798,7 +890,7 @@ Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double
   }
   for (int l = L - 1; l >= 0; --l) {
     const int ps = prof_ctx ? prof_begin(prof_ctx, l == 0 ? kProfUp0 : kProfUpLevel + l) : -1;
-    MG_TRY(launch_up_variant(fl.var_up[l], l, fl, norm2, e, u_skip, w, active, st));
+    MG_TRY(launch_up_variant(fl.var_up[l], l, fl, norm2, e, u_skip, w, active, st, l == 0 ? opt.resid_out : nullptr));
     if (prof_ctx) prof_end(prof_ctx, ps);
   }
   return {};
@@ -831,13 +923,14 @@ size_t fused_partials_max(int n) {
 // With `ra` the finest down kernel is timed as it runs in the cycle, computing
 // the residual (its partial sums go to ra->partial).
 Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, double* scratch,
-                      const FusedWeights& w, cudaStream_t st, int reps, const ResidIn* ra) {
+                      const FusedWeights& w, cudaStream_t st, int reps, const ResidIn* ra, const ResidOut* ro) {
   cudaEvent_t e0, e1;
   MG_CUDA(cudaEventCreate(&e0));
   MG_CUDA(cudaEventCreate(&e1));
   Status result = launch_alpha(fl, norm2, st);
   for (int l = 0; l < fl.L && result.ok(); ++l) {
     const ResidIn* rl = (l == 0) ? ra : nullptr;
+    const ResidOut* rol = (l == 0) ? ro : nullptr;
     float best_d = 1e30f, best_u = 1e30f;
     // two timed rounds per variant, keeping the faster one: a single short
     // round is easily disturbed (clock ramp, other work on the GPU)
@@ -852,10 +945,11 @@ Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, do
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&t, e0, e1);
         if (t < best_d) { best_d = t; fl.var_down[l] = v; }
-        result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st);
+        result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st, rol);
         if (!result.ok()) break;
         cudaEventRecord(e0, st);
-        for (int k = 0; k < reps && result.ok(); ++k) result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st);
+        for (int k = 0; k < reps && result.ok(); ++k)
+          result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st, rol);
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&t, e0, e1);
@@ -879,6 +973,7 @@ FusedLevels ctx_levels(mgcnn_ctx* c) {
   fl.maps = c->tma;
   fl.err = c->kerr.as<int>();
   fl.alpha = c->alpha32.as<float>();
+  fl.pdl = c->pdl;
   for (int l = 0; l < c->L; ++l) {
     fl.n[l] = c->lv[l].n;
     fl.s[l] = c->s16[l].as<bf16>();
@@ -893,11 +988,12 @@ FusedLevels ctx_levels(mgcnn_ctx* c) {
 // First V-cycle after a setup: time the tile variants per level (outputs to the
 // context's scratch vector and partial sums, so no caller data changes) and keep
 // the fastest.  With `ra` the finest down kernel is tuned with the residual fused in.
-Status ctx_autotune(mgcnn_ctx* c, const float* r32, const double* norm2, const ResidIn* ra) {
+Status ctx_autotune(mgcnn_ctx* c, const float* r32, const double* norm2, const ResidIn* ra,
+                    const ResidOut* ro = nullptr) {
   MG_TRY(ensure(c->alpha32, 2 * sizeof(float)));
   if (c->tuned) return {};
   FusedLevels fl = ctx_levels(c);
-  MG_TRY(fused_autotune(fl, r32, norm2, c->e.as<double>(), fused_weights(c), c->stream, 5, ra));
+  MG_TRY(fused_autotune(fl, r32, norm2, c->e.as<double>(), fused_weights(c), c->stream, 5, ra, ro));
   for (int l = 0; l < c->L; ++l) {
     c->tile_var[0][l] = fl.var_down[l];
     c->tile_var[1][l] = fl.var_up[l];
@@ -914,8 +1010,43 @@ Status vcycle_fused_cp8(mgcnn_ctx* c, const float* r32, const double* norm2, dou
   return fused_vcycle_levels(ctx_levels(c), r32, norm2, e, u_skip, w, nullptr, c->stream, c);
 }
 
-bool fused_residual_applies(const mgcnn_ctx* c) {
-  return c->cfg.precision == MGCNN_PREC_MIXED_BF16 && c->fused && fused_supported(c) && c->fuse_residual;
+int fused_residual_mode(const mgcnn_ctx* c) {
+  return (c->cfg.precision == MGCNN_PREC_MIXED_BF16 && c->fused && fused_supported(c)) ? c->fuse_residual : 0;
+}
+
+bool fused_residual_applies(const mgcnn_ctx* c) { return fused_residual_mode(c) == 1; }
+
+ResidOut ctx_resid_out(mgcnn_ctx* c, const double* f) {
+  ResidOut ro;
+  ro.f = f;
+  ro.op = c->op[0].as<double>();
+  ro.dinv32 = c->cfg.input_diag ? c->dinv32.as<float>() : nullptr;
+  ro.r32 = c->r32.as<float>();
+  ro.partial = c->partial.as<double>();
+  return ro;
+}
+
+Status upres_cycle_setup(mgcnn_ctx* c, const double* f, const double* u, double* rn2_dev, cudaStream_t st) {
+  MG_TRY(ensure(c->partial, std::max((size_t)reduction_blocks(c->lv[0].N()), fused_partials_max(c->n)) *
+                                sizeof(double)));
+  const ResidOut ro = ctx_resid_out(c, f);
+  MG_TRY(ctx_autotune(c, c->r32.as<float>(), rn2_dev, nullptr, &ro));
+  // r_0 and ||r_0||^2 by the stand-alone kernel; later residuals come from the up kernel
+  MG_TRY(launch_residual(f, u, c->op[0].as<double>(), nullptr, c->r32.as<float>(), c->partial.as<double>(), c->n, st,
+                         c->cfg.input_diag ? c->dinv32.as<float>() : nullptr));
+  return launch_reduce(c->partial.as<double>(), residual_blocks(c->lv[0].N()), rn2_dev, st);
+}
+
+Status upres_cycle(mgcnn_ctx* c, const double* f, const double* u_in, double* u_out, double* rn2_dev,
+                   const int* active, cudaStream_t st, bool profile) {
+  if (u_in == u_out) return make_status(MGCNN_ERR_STATE, "the residual-forming cycle needs two iterate buffers");
+  const FusedLevels fl = ctx_levels(c);
+  const ResidOut ro = ctx_resid_out(c, f);
+  FusedCycleOpt opt;
+  opt.resid_out = &ro;
+  MG_TRY(fused_vcycle_levels(fl, c->r32.as<float>(), rn2_dev, u_out, u_in, fused_weights(c), active, st,
+                             profile ? c : nullptr, opt));
+  return launch_reduce(c->partial.as<double>(), fused_down0_blocks(c->n, fl.var_up[0]), rn2_dev, st);
 }
 
 ResidIn ctx_resid_in(mgcnn_ctx* c, const double* f, const double* u) {

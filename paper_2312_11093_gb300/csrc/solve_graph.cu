@@ -71,6 +71,22 @@ Status build_graph(mgcnn_ctx* c) {
     const long long launches0 = mgcnn_kernel_launches();
     Status cap = [&]() -> Status {
       double* sc = c->scalars.as<double>();
+      if (fused_residual_mode(c) == 2) {
+        // two cycles per pass, u -> u2 -> u: the test on ||r_k||, then the whole
+        // cycle, whose finest up kernel forms r_{k+1} and its norm for the next
+        // test (r_0 comes before the loop); a stop after the first half leaves
+        // the iterate in u2 (odd cycle count)
+        double* ua = c->u.as<double>();
+        double* ub = c->u2.as<double>();
+        for (int half = 0; half < 2; ++half) {
+          solve_check_kernel<<<1, 32, 0, st>>>(sc, sc + 1, c->gstate.as<int>(), c->ghist.as<double>(),
+                                               c->gparams.as<double>(), loop);
+          MG_LAUNCH("solve_check_kernel");
+          MG_TRY(upres_cycle(c, c->f.as<double>(), half ? ub : ua, half ? ua : ub, sc, c->gstate.as<int>(), st,
+                             false));
+        }
+        return {};
+      }
       if (fused_residual_applies(c)) {
         // r_k and the finest down level in one kernel, ||r_k||^2, the test, the
         // rest of the cycle (u += B r_k) and the next input scale
@@ -93,6 +109,7 @@ Status build_graph(mgcnn_ctx* c) {
       fl.maps = c->tma;
       fl.err = c->kerr.as<int>();
       fl.alpha = c->alpha32.as<float>();
+      fl.pdl = c->pdl;
       for (int l = 0; l < c->L; ++l) {
         fl.n[l] = c->lv[l].n;
         fl.s[l] = c->s16[l].as<__nv_bfloat16>();
@@ -165,7 +182,17 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
     MG_CUDA(cudaStreamSynchronize(st));
     return {};
   }
-  if (fused_residual_applies(c)) {
+  if (fused_residual_mode(c) == 2) {
+    // tile shapes (tuned once per setup before the graph fixes them), then r_0
+    // and ||r_0||^2 before the loop
+    if (c->u2.bytes < N0 * sizeof(double)) {
+      MG_TRY(ensure(c->u2, N0 * sizeof(double)));
+      c->sgraph_valid = false;
+    }
+    const bool was_tuned = c->tuned;
+    MG_TRY(upres_cycle_setup(c, c->f.as<double>(), c->u.as<double>(), c->scalars.as<double>(), st));
+    if (!was_tuned) c->sgraph_valid = false;
+  } else if (fused_residual_applies(c)) {
     // tile shapes (tuned once per setup before the graph fixes them) and the
     // first cycle's input scale from ||f||
     const bool was_tuned = c->tuned;
@@ -197,6 +224,12 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
   if (!c->gstream) MG_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
   if (!c->sgraph_valid) {
     Status b = build_graph(c);
+    if (!b.ok() && c->pdl) {
+      // programmatic edges not available in this graph: plain launches
+      cudaGetLastError();
+      c->pdl = false;
+      b = build_graph(c);
+    }
     if (!b.ok()) {
       cudaGetLastError();
       c->graph_failed = true;   // conditional graphs unavailable: host loop from now on
@@ -212,10 +245,17 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
   MG_CUDA(cudaGraphLaunch(c->sgraph, st));
   int state[4];
   MG_CUDA(cudaMemcpyAsync(state, c->gstate.p, sizeof(state), cudaMemcpyDeviceToHost, st));
-  if (u != c->u.as<double>()) MG_CUDA(cudaMemcpyAsync(u, c->u.p, N0 * sizeof(double), cudaMemcpyDefault, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  // with the residual formed in the up kernel an odd number of cycles leaves the
+  // iterate in u2
+  const double* ures = (fused_residual_mode(c) == 2 && (state[1] & 1)) ? c->u2.as<double>() : c->u.as<double>();
+  if (u != ures) MG_CUDA(cudaMemcpyAsync(u, ures, N0 * sizeof(double), cudaMemcpyDefault, st));
   MG_CUDA(cudaStreamSynchronize(st));
   *iters = state[1];
-  add_launches(c->sgraph_kernels * (long long)(state[1] + 1));
+  // graph passes run: one per cycle plus the final test (two cycles per pass with
+  // the residual formed in the up kernel)
+  const long long passes = (fused_residual_mode(c) == 2) ? state[1] / 2 + 1 : state[1] + 1;
+  add_launches(c->sgraph_kernels * passes);
   if (relres) {
     const int nh = state[2] == MGCNN_ERR_NONFINITE ? state[1] : state[1] + 1;
     if (nh > 0) MG_CUDA(cudaMemcpy(relres, c->ghist.p, nh * sizeof(double), cudaMemcpyDeviceToHost));

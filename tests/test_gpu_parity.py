@@ -466,18 +466,20 @@ def test_every_tile_shape_gives_identical_iterates(M, n, net):
         assert np.array_equal(out[tile][1], out[-1][1]), tile
 
 
-@pytest.mark.parametrize("n,loop", [(63, 1), (255, 0), (1023, 1)])
+@pytest.mark.parametrize("n,loop", [(63, 1), (255, 0), (1023, 1), (4095, 1)])
 def test_fused_residual_equals_separate_residual(M, n, loop):
-    """mgcnn_solve with the residual computed inside the finest down kernel (the
-    same FP64 FMAs, in the same order, as the stand-alone residual kernel) and with
-    the separate residual pass: bit-identical iterates and cycle counts (the input
-    scale is a power of two, so the norm it comes from does not change a bit), norms
-    equal to rounding (summed in another order)."""
+    """mgcnn_solve with the residual formed by the separate residual pass (mode 0),
+    inside the finest down kernel (mode 1) and inside the finest up kernel from its
+    own u + e (mode 2; the halo pixels' u + e must be the bits the neighbouring
+    tiles own) -- each with the same FP64 FMAs, in the same order, as the stand-alone
+    residual kernel: bit-identical iterates and cycle counts (the input scale is a
+    power of two, so the norm it comes from does not change a bit), norms equal to
+    rounding (summed in other orders)."""
     from paper_2312_11093_gb300.train import init_weights
     k, f = problem(n, 90 + n)
     w = init_weights(8, 1, 1, np.random.default_rng(11), out_scale=0.05)
     out = {}
-    for fres in (1, 0):
+    for fres in (2, 1, 0):
         sv = M.Solver(8, 1, 1, precision="mixed_bf16")
         sv.set_option(sv.OPT_DEVICE_LOOP, loop)
         sv.set_option(sv.OPT_FUSED_RESIDUAL, fres)
@@ -486,9 +488,10 @@ def test_fused_residual_equals_separate_residual(M, n, loop):
         u = np.zeros(n * n)
         st, it, hist = sv.solve(f.ravel().copy(), u, 1e-30, 6)
         out[fres] = (it, hist.copy(), u)
-    assert out[1][0] == out[0][0] == 6
-    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-13, atol=0)
-    assert np.array_equal(out[1][2], out[0][2])
+    for fres in (1, 2):
+        assert out[fres][0] == out[0][0] == 6
+        np.testing.assert_allclose(out[fres][1], out[0][1], rtol=1e-13, atol=0)
+        assert np.array_equal(out[fres][2], out[0][2]), fres
 
 
 def test_tile_option_range(M):
