@@ -1,5 +1,6 @@
-"""Batched solves of uneven sizes (one CUDA graph per cycle) against independent
-single-problem solves of the same fields with the same network."""
+"""Batched solves of uneven sizes (one CUDA graph launch per batch) against
+independent single-problem solves of the same fields with the same network,
+and against the oracle."""
 import numpy as np
 import pytest
 import torch
@@ -121,3 +122,29 @@ def test_batched_gmg_v10_equals_single_solves_and_converges(M):
         st_ = oop.stencil_div(ks[i].reshape(n + 2, n + 2), (1.0, 0.5))
         r = fs[i].reshape(n, n) - oop.apply(st_, us[i].reshape(n, n))
         assert np.linalg.norm(r) / np.linalg.norm(fs[i]) <= 1.01e-6
+
+
+@pytest.mark.parametrize("cfg", [(0, True), (1, False)])
+def test_batched_first_cycle_against_the_oracle(M, cfg):
+    """Every problem of an uneven batch over the three coefficient families, one
+    cycle from u = 0 (u_1 = B f with the batch's BF16 network and setup network),
+    against the oracle's FP64 B f with the same weights: the bar of the
+    single-problem mixed test, 5e-2 (BF16 rounding along one cycle)."""
+    from oracle import operator as oop
+    from oracle.grid import num_levels
+    sbd, idiag = cfg
+    sizes = [31, 63, 15, 127, 63, 7]
+    ks, fs = _fields(sizes, 21)
+    w = omg.random_weights(8, 1, 1, np.random.default_rng(22))
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16", scale_by_diag=sbd, input_diag=idiag)
+    sv.set_weights(M.pack_weights(w, 8, 1, 1))
+    sv.setup_batched(ks, sizes)
+    us = [np.zeros(n * n) for n in sizes]
+    st, iters, relres, stat = sv.solve_batched(fs, us, 0.0, 1, per_problem=True)
+    for i, n in enumerate(sizes):
+        assert iters[i] == 1 and stat[i] == M.NOT_CONVERGED, i
+        sts = oop.level_stencils_div(ks[i].reshape(n + 2, n + 2), (1.0, 0.5), num_levels(n))
+        s = omg.setup(w, sts, scale_by_diag=sbd)
+        e_ref = omg.solve_phase(w, s, fs[i].reshape(n, n), d_inv=(1.0 / sts[0].aC) if idiag else None)
+        err = np.linalg.norm(us[i] - e_ref.ravel()) / np.linalg.norm(e_ref)
+        assert err <= 5e-2, (i, n, err)
