@@ -134,6 +134,7 @@ struct mgcnn_ctx {
   mgcnn::DevBuf kerr;                     // device flag: a kernel gave up waiting for its tile copies
   mgcnn::DevBuf alpha32;                  // input scale of the fused V-cycle (alpha, 1 / alpha)
   mgcnn::SmallWeights small_w{};          // host copy of the fused down kernel's W_in
+  int out_lo = 1;                         // W_out has a nonzero BF16 lo part (the fused up kernel's second pass)
   mgcnn::SetupSmallWeights setup_small_w{};  // host copy of the fused setup kernel's small layers
   mgcnn::DevBuf s32tmp;                   // FP32 setup output before the BF16 cast
   mgcnn::DevBuf scalars;                  // device scalars (norms)

@@ -499,7 +499,7 @@ FusedWeights fused_weights(const mgcnn_ctx* c) {
   return FusedWeights{reinterpret_cast<const uint32_t*>(wb + ml.down), reinterpret_cast<const uint32_t*>(wb + ml.up),
                       reinterpret_cast<const uint32_t*>(wb + ml.R), reinterpret_cast<const uint32_t*>(wb + ml.out_hi),
                       reinterpret_cast<const uint32_t*>(wb + ml.out_lo), reinterpret_cast<const uint32_t*>(wb + ml.tcnn),
-                      c->small_w};
+                      c->small_w, c->out_lo};
 }
 
 Status mixed_set_weights(mgcnn_ctx* c) {
@@ -540,6 +540,8 @@ Status mixed_set_weights(mgcnn_ctx* c) {
         whi[ci * 9 + t] = hi;
         wlo[ci * 9 + t] = (double)(v - hi);
       }
+    c->out_lo = 0;
+    for (double v : wlo) c->out_lo |= (v != 0.0);
     pack_frags(whi.data(), 8, 8, reinterpret_cast<uint32_t*>(blob.data() + ml.out_hi));
     pack_frags(wlo.data(), 8, 8, reinterpret_cast<uint32_t*>(blob.data() + ml.out_lo));
     pack_tcnn_frags(w.data() + c->wl.w_P, C, reinterpret_cast<uint32_t*>(blob.data() + ml.tcnn));

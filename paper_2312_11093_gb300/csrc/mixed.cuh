@@ -58,6 +58,7 @@ struct FusedWeights {
   const uint32_t *f_out_hi, *f_out_lo;   // W_out as an 8 -> 8 layer (output channel 0), BF16 hi + lo parts
   const uint32_t* f_tcnn;                // TCNN of 2 x 2 fine-pixel quads (kTcnnQuadRegs x 32 words)
   SmallWeights small;                    // by value, see SmallWeights
+  int out_lo = 1;                        // 0: W_out is exact in BF16 (its lo part is zero), one pass suffices
 };
 struct FusedCycleOpt {
   bool after_fused_down0 = false;        // the finest down kernel ran already, with the residual fused in

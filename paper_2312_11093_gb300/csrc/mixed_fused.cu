@@ -81,6 +81,9 @@ __device__ __forceinline__ uint32_t bmul2(uint32_t a, uint32_t b) {
   asm("mul.rn.bf16x2 %0, %1, %2;\n" : "=r"(d) : "r"(a), "r"(b));
   return d;
 }
+__device__ __forceinline__ float2 bf2_to_f2(uint32_t v) {
+  return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+}
 __device__ __forceinline__ uint4 mul8(uint4 a, uint4 b) {
   return make_uint4(bmul2(a.x, b.x), bmul2(a.y, b.y), bmul2(a.z, b.z), bmul2(a.w, b.w));
 }
@@ -155,14 +158,14 @@ struct UpGeom {
   static constexpr int NQH = QH / 2, NQW = QW / 2;         // quads
   static constexpr int CQH = NQH + 1, CQW = NQW + 1;       // coarse pixels staged
   static_assert(!HAS_P || (QH % 2 == 0 && QW % 2 == 0), "whole quads");
-  // finest level, after the layer: e (FP32) on E, then u + e (FP64) on E, in the Q tiles
-  static_assert(!LAST || EH * EW * (4 + 8) + 8 <= 16 * QH * QW, "E staging in the ps tile");
+  // finest level, after the layer: e (FP32) on E, then u + e (FP64) on E, in the z tile
+  static_assert(!LAST || EH * EW * (4 + 8) + 8 <= 16 * QH * QW, "E staging in the z tile");
 };
-// Tiles: ps, zs on Q; cs; on the finest level os on O.
+// Tiles: ps, zs on Q; on the finest level pl on O; cs.
 template <int FH, int FW, bool LAST, bool HAS_P, bool RES = false>
 constexpr size_t up_smem_bytes() {
   using G = UpGeom<FH, FW, LAST, HAS_P, RES>;
-  return 16u * (2 * pad8(G::QH * G::QW) + (HAS_P ? pad8(G::CQH * G::CQW) : 0) + (LAST ? pad8(G::OH * G::OW) : 0));
+  return 16u * (2 * pad8(G::QH * G::QW) + (LAST ? pad8(G::OH * G::OW) : 0) + (HAS_P ? pad8(G::CQH * G::CQW) : 0));
 }
 extern __shared__ __align__(128) unsigned char fused_dsm[];
 
@@ -463,8 +466,8 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
 // pack_tcnn_frags).  Epilogue: x_pre rounded once to BF16 into ps, z = s * x_pre
 // into zs.  Coarse pixels outside the coarse grid are staged as zeros, which
 // makes the sum zero on every fine pixel outside the fine grid.
-template <class G>
-__device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, const uint4* cs, const uint32_t* fq) {
+template <class G, bool WIDE>
+__device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, const uint4* cs, const uint32_t* fq) {
   constexpr int NQ = G::NQH * G::NQW, NS = (NQ + 15) / 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, q = lane & 3, kh = lane >> 4;
@@ -482,13 +485,16 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, const uint4* cs
     ldsm_x4(ax0, xa);                                  // x_down of fine (0, 0) | (0, 1)
     ldsm_x4(ax1, xa + 16u * G::QW);                    // x_down of fine (1, 0) | (1, 1)
     // this lane's two output quads (rows g and g + 8 of the strip)
-    int pe[2];
+    int pe[2], po[2];
     bool ok[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int qe = st * 16 + g + 8 * h, er = qe / G::NQW, ec = qe - er * G::NQW;
       ok[h] = qe < NQ;
       pe[h] = 2 * er * G::QW + 2 * ec;
+      // the quad's first fine pixel in O coordinates (Q pixel (qr, qc) is O pixel
+      // (qr - QOFF - 1, qc - QOFF - 1)), packed as row * 65536 + column + offset
+      po[h] = (2 * er - G::QOFF - 1 + 2) * 65536 + (2 * ec - G::QOFF - 1 + 2);
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -504,7 +510,17 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, const uint4* cs
         const uint32_t xo = f2bf(acc[2 * h], acc[2 * h + 1]);
         reinterpret_cast<uint32_t*>(&ps[e])[q] = xo;
         uint32_t* zp = reinterpret_cast<uint32_t*>(&zs[e]) + q;
-        *zp = bmul2(xo, *zp);
+        if constexpr (WIDE) {
+          // finest level: z from the FP32 sum, and the sum's low BF16 part kept on
+          // the layer-output region O (the layer adds it to its skip)
+          const float2 hi = bf2_to_f2(xo), sv = bf2_to_f2(*zp);
+          *zp = f2bf(sv.x * acc[2 * h], sv.y * acc[2 * h + 1]);
+          const int orow = (po[h] >> 16) - 2 + r, ocol = (po[h] & 0xffff) - 2 + c;
+          if (orow >= 0 && orow < G::OH && ocol >= 0 && ocol < G::OW)
+            reinterpret_cast<uint32_t*>(&pl[orow * G::OW + ocol])[q] = f2bf(acc[2 * h] - hi.x, acc[2 * h + 1] - hi.y);
+        } else {
+          *zp = bmul2(xo, *zp);
+        }
       }
     }
   }
@@ -524,16 +540,18 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
                                                 const float* __restrict__ alpha2, const double* __restrict__ u_in,
                                                 bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
                                                 const int* __restrict__ active, int* __restrict__ err,
-                                                const __grid_constant__ ResidOut ro) {
+                                                const __grid_constant__ ResidOut ro, int out_lo) {
   using G = UpGeom<FH, FW, LAST, HAS_P, RES>;
   constexpr int H = G::H, OH = G::OH, OW = G::OW, QW = G::QW, QOFF = G::QOFF;
   constexpr int HE = G::HE, EH = G::EH, EW = G::EW;
   // TMA destinations (zero outside the grid): ps = x_down on Q, then x_pre;
   // zs = s on Q, then s * x_pre; cs = the quads' coarse pixels
+  // finest level: pl = the low BF16 part of x_pre on O, then (in place) that of
+  // the layer output; the layer output's high part replaces x_pre's in ps
   uint4* ps = reinterpret_cast<uint4*>(fused_dsm);
   uint4* zs = ps + pad8(G::QH * QW);
-  uint4* cs = zs + pad8(G::QH * QW);                                   // coarser level only
-  uint4* os = cs + (HAS_P ? pad8(G::CQH * G::CQW) : 0);               // finest level only
+  uint4* pl = zs + pad8(G::QH * QW);                                   // finest level only
+  uint4* cs = pl + (LAST ? pad8(OH * OW) : 0);                         // coarser level only
   __shared__ __align__(8) uint64_t bar;
   const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
   const int qj0 = j0 - H - 1 - QOFF, qi0 = i0 - H - 1 - QOFF;         // Q's corner (odd when HAS_P)
@@ -572,9 +590,11 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   }
 
   if constexpr (HAS_P) {
-    tcnn_quads<G>(ps, zs, cs, fq);
+    tcnn_quads<G, LAST>(ps, zs, pl, cs, fq);
   } else {
     for (int e = threadIdx.x; e < G::QH * QW; e += NT) zs[e] = mul8(ps[e], zs[e]);
+    if (LAST)
+      for (int e = threadIdx.x; e < OH * OW; e += NT) pl[e] = make_uint4(0u, 0u, 0u, 0u);   // x_pre = x_down
   }
   __syncthreads();
 
@@ -591,6 +611,12 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
       const int pm = min(st * 16 + mrow, NO - 1), rm = pm / OW;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
       layer_strip<QW>(zs, ps, wk, fI, (rm + QOFF) * QW + (pm - rm * OW) + QOFF, to, acc);
+      if constexpr (LAST) {
+        // the skip's low part: x_lo at the pixel itself through an identity block
+        uint32_t a[2];
+        ldsm_x2(a, sa(pl) + 16u * min(st * 16 + (lane & 15), NO - 1));
+        mma1688(acc, a[0], a[1], fI);
+      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int p = st * 16 + g + 8 * h;
@@ -599,8 +625,12 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
         const uint32_t o = f2bf(acc[2 * h], acc[2 * h + 1]);
         const int gj = j0 - H + orow, gi = i0 - H + ocol;
         if constexpr (LAST) {
-          // zero outside the grid: W_out's zero padding
-          reinterpret_cast<uint32_t*>(&os[orow * OW + ocol])[q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? o : 0u;
+          // the output as hi + lo BF16, zero outside the grid (W_out's zero
+          // padding), in place: only this strip reads these pixels of ps and pl
+          const bool in = gj >= 0 && gj < n && gi >= 0 && gi < n;
+          const float2 hi = bf2_to_f2(o);
+          reinterpret_cast<uint32_t*>(&ps[(orow + QOFF + 1) * QW + ocol + QOFF + 1])[q] = in ? o : 0u;
+          reinterpret_cast<uint32_t*>(&pl[p])[q] = in ? f2bf(acc[2 * h] - hi.x, acc[2 * h + 1] - hi.y) : 0u;
         } else {
           if (gj < n && gi < n) reinterpret_cast<uint32_t*>(xfin + ((size_t)gj * n + gi) * 8)[q] = o;
         }
@@ -609,15 +639,16 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   }
   if constexpr (LAST) {
     // W_out on the tensor cores: an 8 -> 8 channel layer whose only nonzero
-    // output channel is 0, with the FP32 weights split as hi + lo BF16 (the two
-    // products are accumulated in FP32, so the weights keep ~16 bits); strips of
-    // 16 pixels of E in row-major order.  E pixel (er, ec) reads the taps around
-    // O pixel (er + 1, ec + 1).
+    // output channel is 0, with the FP32 weights and the layer output each split
+    // as hi + lo BF16 -- hi(w) hi(y) + lo(w) hi(y) + hi(w) lo(y), accumulated in
+    // FP32 (about 16 bits on each side); strips of 16 pixels of E in row-major
+    // order.  E pixel (er, ec) reads the taps around O pixel (er + 1, ec + 1),
+    // i.e. Q pixel (er + QOFF + 2, ec + QOFF + 2) of ps.
     uint32_t wh[9], wl[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       wh[k] = fOutHi[k * 32 + lane];
-      wl[k] = fOutLo[k * 32 + lane];
+      wl[k] = out_lo ? fOutLo[k * 32 + lane] : 0u;
     }
     // this thread's u values of the update below, loaded now so that their
     // latency passes during W_out (zero outside the grid)
@@ -631,17 +662,19 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
     }
     __syncthreads();
     const float inv_alpha = alpha2[2 * bz + 1];
-    float* ev = reinterpret_cast<float*>(ps);                                  // e on E
-    double* un = reinterpret_cast<double*>(ps) + (NE + 1) / 2;                  // u + e on E
+    float* ev = reinterpret_cast<float*>(zs);                                  // e on E
+    double* un = reinterpret_cast<double*>(zs) + (NE + 1) / 2;                  // u + e on E
     const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
     const TapOffsets<OW> to;
+    const TapOffsets<QW> tq;
     for (int st = warp; st < (NE + 15) / 16; st += NW) {
-      const int pm = min(st * 16 + mrow, NE - 1), pl = min(st * 16 + lrow, NE - 1);
-      const int rm = pm / EW, rl = pl / EW;
+      const int pm = min(st * 16 + mrow, NE - 1), pn = min(st * 16 + lrow, NE - 1);
+      const int rm = pm / EW, rl = pn / EW, cm = pm - rm * EW, cl = pn - rl * EW;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      const int bm = rm * OW + (pm - rm * EW), bl = rl * OW + (pl - rl * EW);
-      strip_conv_at<OW>(os, wh, bm, bl, to, acc);
-      strip_conv_at<OW>(os, wl, bm, bl, to, acc);
+      const int bm = (rm + QOFF + 1) * QW + cm + QOFF + 1, bl = (rl + QOFF + 1) * QW + cl + QOFF + 1;
+      strip_conv_at<QW>(ps, wh, bm, bl, tq, acc);
+      if (out_lo) strip_conv_at<QW>(ps, wl, bm, bl, tq, acc);   // a zero lo part adds exactly nothing
+      strip_conv_at<OW>(pl, wh, rm * OW + cm, rl * OW + cl, to, acc);
       // output channel 0 sits in the q == 0 lanes: stage it in shared memory
       // (the Q tiles are free now) so that the FP64 update below runs on
       // full warps -- an FP64 instruction costs the same with 8 lanes or 32
@@ -817,7 +850,7 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
       mc = ms;   // not read on the coarsest level
     const cudaError_t le = launch_level(kernel, grid, dyn_smem(kernel, smem), st, fl.pdl, mxd, ms, mc, w.f_up,
                                         w.f_tcnn, w.f_out_hi, w.f_out_lo, (const float*)fl.alpha, u_skip, xfin, e, nl,
-                                        active, fl.err, rout);
+                                        active, fl.err, rout, w.out_lo);
     if (le != cudaSuccess) return cuda_status(le, "up_kernel launch");
     return {};
   };
