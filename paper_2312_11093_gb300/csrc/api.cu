@@ -166,7 +166,7 @@ Status sync(mgcnn_ctx* c) {
 // ||v||_2^2 of N doubles into scalars[slot] on the device.
 Status sumsq(mgcnn_ctx* c, const double* v, size_t N, int slot) {
   MG_TRY(launch_sumsq(v, N, c->partial.as<double>(), c->stream));
-  MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), c->scalars.as<double>() + slot, c->stream));
+  MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), c->scalars.as<double>() + slot, c->stream));
   return {};
 }
 

@@ -674,7 +674,7 @@ Status vcycle_mixed(mgcnn_ctx* c, const double* r, double* e, const double* u_sk
   MG_LAUNCH("to_f32_kernel");
   double* norm2 = c->scalars.as<double>() + 2;
   MG_TRY(launch_sumsq(r, N, c->partial.as<double>(), c->stream));
-  MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N), norm2, c->stream));
+  MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N), norm2, c->stream));
   return vcycle_mixed_r32(c, c->r32.as<float>(), norm2, e, u_skip);
 }
 

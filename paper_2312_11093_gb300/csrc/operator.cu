@@ -323,16 +323,17 @@ Status launch_residual(const double* f, const double* u, const double* op, doubl
   return {};
 }
 
+// 1/a_C: the FP32 copy (the mixed path's network input scale) in FP32 from the
+// integer-converted diagonal, the same value whether or not the FP64 copy
+// (FP64 division) is wanted too.
 __global__ void diag_inverse_kernel(const double* __restrict__ op, double* __restrict__ dinv,
                                     float* __restrict__ dinv32, size_t N) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   op += (size_t)blockIdx.y * 5 * N;
-  if (dinv) dinv += (size_t)blockIdx.y * N;
   dinv32 += (size_t)blockIdx.y * N;
-  const double d = 1.0 / op[p];
-  if (dinv) dinv[p] = d;
-  dinv32[p] = (float)d;
+  dinv32[p] = 1.0f / f64_to_f32_rn(op[p]);
+  if (dinv) dinv[(size_t)blockIdx.y * N + p] = 1.0 / op[p];
 }
 
 Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t N, cudaStream_t st, int batch) {
@@ -341,17 +342,24 @@ Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t
   return {};
 }
 
+// per-block partial sums of v^2, kResidualPix values per thread (the residual
+// kernel's blocks: residual_blocks(N) partial sums)
 __global__ void __launch_bounds__(kResidualBlock)
 sumsq_kernel(const double* __restrict__ v, size_t N, double* __restrict__ partial) {
   __shared__ double smem[32];
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double x = (p < N) ? v[p] : 0.0;
-  x = block_sum(x * x, smem);
+  const size_t base = (size_t)blockIdx.x * (kResidualPix * kResidualBlock) + threadIdx.x;
+  double x = 0.0;
+#pragma unroll
+  for (int k = 0; k < kResidualPix; ++k) {
+    const size_t p = base + (size_t)k * kResidualBlock;
+    if (p < N) x = fma(v[p], v[p], x);
+  }
+  x = block_sum(x, smem);
   if (threadIdx.x == 0) partial[blockIdx.x] = x;
 }
 
 Status launch_sumsq(const double* v, size_t N, double* partial, cudaStream_t st) {
-  sumsq_kernel<<<reduction_blocks(N), kResidualBlock, 0, st>>>(v, N, partial);
+  sumsq_kernel<<<residual_blocks(N), kResidualBlock, 0, st>>>(v, N, partial);
   MG_LAUNCH("sumsq_kernel");
   return {};
 }
@@ -441,26 +449,42 @@ __global__ void gmg_v10_setup_kernel(const double* __restrict__ op, double* __re
   gmg_v10_values(op, n, omega, input_diag_level, p, out + (size_t)p * kGmgV10Channels);
 }
 
-// BF16 variant for the mixed-precision path: one 16-byte pixel per node, the
-// values rounded as FP64 -> FP32 -> BF16 (the rounding of the FP64 -> BF16
-// padding copy), for a batch of problems stored back to back.
+// BF16 variant for the mixed-precision path: one 16-byte pixel per node, for a
+// batch of problems stored back to back.  BF16 keeps 8 bits, so the values are
+// formed in FP32 (24 bits) from the FP64 stencil converted with integer
+// operations (fpconv.cuh) -- the FP64 pipe, about 1/58 of the FP32 rate here,
+// stays idle -- and rounded once to BF16 (within 2^-9 of the FP64 values, plus
+// FP32 rounding far below that).
 __global__ void gmg_v10_setup_bf16_kernel(const double* __restrict__ op, __nv_bfloat16* __restrict__ out, int n,
-                                          double omega, int input_diag_level) {
+                                          float omega, int input_diag_level) {
   const size_t N = (size_t)n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (int)N) return;
   op += (size_t)blockIdx.y * 5 * N;
   out += (size_t)blockIdx.y * N * kGmgV10Channels;
-  double o[8];
-  gmg_v10_values(op, n, omega, input_diag_level, p, o);
+  const int j = p / n, i = p - j * n;
+  const int dy[4] = {0, 0, -1, 1}, dx[4] = {-1, 1, 0, 0};  // W, E, S, N
+  const float aCq = f64_to_f32_rn(op[p]);
+  const float inv = input_diag_level ? 1.0f : 1.0f / aCq;
+  float o[8];
+  for (int k = 0; k < 4; ++k) {
+    const int pj = j - dy[k], pi = i - dx[k];
+    o[k] = (pj >= 0 && pj < n && pi >= 0 && pi < n)
+               ? -omega * f64_to_f32_rn(op[(k + 1) * N + (size_t)pj * n + pi]) * inv
+               : 0.0f;
+  }
+  o[4] = input_diag_level ? (1.0f - omega) * aCq : 1.0f - omega;
+  o[5] = omega * inv;
+  o[6] = 0.0f;
+  o[7] = 0.0f;
   __nv_bfloat162 h[4];
-  for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn((float)o[2 * k], (float)o[2 * k + 1]);
+  for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(o[2 * k], o[2 * k + 1]);
   reinterpret_cast<uint4*>(out)[p] = *reinterpret_cast<const uint4*>(h);
 }
 
 Status launch_gmg_v10_setup_bf16(const double* op, __nv_bfloat16* out, int n, double omega, cudaStream_t st,
                                  bool input_diag_level, int batch) {
-  gmg_v10_setup_bf16_kernel<<<dim3(grid_for((size_t)n * n, 256), batch), 256, 0, st>>>(op, out, n, omega,
+  gmg_v10_setup_bf16_kernel<<<dim3(grid_for((size_t)n * n, 256), batch), 256, 0, st>>>(op, out, n, (float)omega,
                                                                                         input_diag_level ? 1 : 0);
   MG_LAUNCH("gmg_v10_setup_bf16_kernel");
   return {};

@@ -37,6 +37,7 @@ Status launch_residual(const double* f, const double* u, const double* op, doubl
                        double* partial, int n, cudaStream_t st, const float* dinv32 = nullptr, int batch = 1);
 // dinv = 1/a_C (FP64, may be null, and FP32) from the first plane of op.
 Status launch_diag_inverse(const double* op, double* dinv, float* dinv32, size_t N, cudaStream_t st, int batch = 1);
+// per-block partial sums of v^2: residual_blocks(N) of them
 Status launch_sumsq(const double* v, size_t N, double* partial, cudaStream_t st);
 // out[0] = sum of partial[0..count) in a fixed order (deterministic).
 Status launch_reduce(const double* partial, int count, double* out, cudaStream_t st);

@@ -169,7 +169,7 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
   if (u != c->u.as<double>()) MG_CUDA(cudaMemcpyAsync(c->u.p, u, N0 * sizeof(double), cudaMemcpyDefault, st));
   // ||f||^2 into scalars[1]
   MG_TRY(launch_sumsq(c->f.as<double>(), N0, c->partial.as<double>(), st));
-  MG_TRY(launch_reduce(c->partial.as<double>(), reduction_blocks(N0), c->scalars.as<double>() + 1, st));
+  MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N0), c->scalars.as<double>() + 1, st));
   MG_CUDA(cudaMemcpyAsync(c->h_scalars + 1, c->scalars.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
   MG_CUDA(cudaStreamSynchronize(st));
   const double fn2 = c->h_scalars[1];
