@@ -144,6 +144,14 @@ def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
     """Bytes a launch of `kind` must move (each operand once): the finest level's
     kernel classes, or the fused kernels of a coarser level l ("down<l>",
     "up<l>", level size n_l = (n_{l-1} - 1) / 2)."""
+    if kind == "tail":
+        # the coarse tail kernel: down and up of every level from the first with
+        # n_l <= 255 (level 1 at the earliest, at most 8 levels) to the coarsest
+        sizes = [n]
+        while sizes[-1] > 3:
+            sizes.append((sizes[-1] - 1) // 2)
+        tail = [nl for lvl, nl in enumerate(sizes) if lvl >= 1 and nl <= 255][-8:]
+        return sum(2 * (2.0 * cp + 2.0 * cp + 2.0 * cp + 0.5 * cp) * nl * nl for nl in tail)
     for pre in ("down", "up"):
         if kind.startswith(pre) and kind[len(pre):].isdigit() and int(kind[len(pre):]) > 0:
             nl = n
@@ -325,6 +333,9 @@ def main():
     ap.add_argument("--maxit", type=int, default=100, help="cycle limit of the batched solves")
     ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="tile shape of the fused kernels: -1 autotuned, 0 16x32, 1 8x32, 2 16x16, 3 32x32, 4 24x32")
+    ap.add_argument("--coarse-tail", type=int, default=-1,
+                    help="largest grid side of the coarse levels run as one cooperative kernel "
+                         "(0: a launch per level; -1: the library default)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -387,6 +398,8 @@ def main():
         sv.set_weights(blob)
         if args.tile >= 0:
             sv.set_option(sv.OPT_TILE, args.tile)
+        if args.coarse_tail >= 0:
+            sv.set_option(sv.OPT_COARSE_TAIL, args.coarse_tail)
         return sv
 
     def step(sv, k, f, u):

@@ -379,8 +379,22 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * on this GPU (the fused kernels add latency-bound FP64 loads to a kernel that
  * is latency-bound already, mode 1 also FP64 work on the halo), so 0 is the
  * default. */
+/* MGCNN_OPT_COARSE_TAIL (default 0): where the fused kernels apply, the levels
+ * below the finest whose grid side is at most this value (and at most 255),
+ * when there are at least two of them, run down and back up in one cooperative
+ * kernel with grid-wide barriers between the levels (16 x 32 tiles) instead of
+ * two launches per level: the same arithmetic per pixel, results bit-identical.
+ * Slower than a launch per level on a GB300 (each level step inside one kernel,
+ * tile copies and the barrier included, takes longer than a level kernel
+ * launched programmatically after the previous one), so off by default.
+ * 0: one launch per level, as also where the device offers no cooperative launch
+ * or a CUDA graph of the solve cannot hold one (the context then keeps 0).
+ * The classes of a batch share the device's resident blocks between their tail
+ * kernels; contexts whose solves overlap on one device do not, and should set 0
+ * (the barrier waits are bounded: past about a second the call fails
+ * with MGCNN_ERR_TIMEOUT instead of hanging). */
 enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3, MGCNN_OPT_SYMMETRIC = 4,
-       MGCNN_OPT_FUSED_RESIDUAL = 5 };
+       MGCNN_OPT_FUSED_RESIDUAL = 5, MGCNN_OPT_COARSE_TAIL = 6 };
 int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).

@@ -155,9 +155,11 @@ Status sync(mgcnn_ctx* c) {
     MG_CUDA(cudaMemcpyAsync(&flag, c->kerr.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     MG_CUDA(cudaStreamSynchronize(c->stream));
     if (flag) {
-      MG_CUDA(cudaMemsetAsync(c->kerr.p, 0, sizeof(int), c->stream));
+      // the flag and the grid barriers a kernel may have left mid-way
+      MG_CUDA(cudaMemsetAsync(c->kerr.p, 0, kErrWords * sizeof(int), c->stream));
       MG_CUDA(cudaStreamSynchronize(c->stream));
-      return make_status(MGCNN_ERR_TIMEOUT, "a fused kernel gave up waiting for its tile copies (TMA)");
+      return make_status(MGCNN_ERR_TIMEOUT,
+                         "a fused kernel gave up waiting for its tile copies (TMA) or for a grid barrier");
     }
   }
   return {};
@@ -471,8 +473,9 @@ int mgcnn_create(const mgcnn_config* cfg, mgcnn_ctx** out) {
     return MGCNN_ERR_CUDA;
   }
   Status s = ensure(c->scalars, 8 * sizeof(double));
-  if (s.ok()) s = ensure(c->kerr, sizeof(int));
-  if (s.ok() && cudaMemset(c->kerr.p, 0, sizeof(int)) != cudaSuccess) s = make_status(MGCNN_ERR_CUDA, "cudaMemset");
+  if (s.ok()) s = ensure(c->kerr, kErrWords * sizeof(int));
+  if (s.ok() && cudaMemset(c->kerr.p, 0, kErrWords * sizeof(int)) != cudaSuccess)
+    s = make_status(MGCNN_ERR_CUDA, "cudaMemset");
   if (s.ok()) {
     c->tma = new (std::nothrow) TmaMaps();
     if (!c->tma) s = make_status(MGCNN_ERR_NOMEM, "tensor map cache");
@@ -1011,6 +1014,12 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
       return finish(c, {});
     case MGCNN_OPT_DEVICE_LOOP:
       c->device_loop = value ? 1 : 0;
+      return finish(c, {});
+    case MGCNN_OPT_COARSE_TAIL:
+      if (value < 0) return finish(c, make_status(MGCNN_ERR_ARG, "coarse tail grid side must be >= 0"));
+      c->tail_n = value;
+      c->sgraph_valid = false;
+      c->bmaxit = -1;   // batch graphs are captured again
       return finish(c, {});
     case MGCNN_OPT_FUSED_RESIDUAL:
       if (value < 0 || value > 2) return finish(c, make_status(MGCNN_ERR_ARG, "fused residual mode is 0, 1 or 2"));

@@ -300,10 +300,19 @@ Status record_cycle(mgcnn_ctx* c, cudaStream_t main, const FusedWeights& w) {
   batch_cycle_begin_kernel<<<1, 32, 0, main>>>(c->bcount.as<int>());
   MG_LAUNCH("batch_cycle_begin_kernel");
   MG_CUDA(cudaEventRecord(c->bfork, main));
+  // coarse tail: one grid-barrier word pair per class; the classes run
+  // concurrently, so their tail kernels split the resident blocks
+  int pair = 1;
+  const int share = std::min((int)c->bcls.size(), kTailBarriers - 1);
   for (BatchClass& k : c->bcls) {
     const size_t N0 = (size_t)k.n * k.n;
     const int nblk = residual_blocks(N0);
     int* state = k.state.as<int>();
+    FusedLevels fl = k.fl;
+    fl.tail_n = pair < kTailBarriers ? c->tail_n : 0;
+    fl.tail_bar = c->kerr.as<unsigned>() + kTailBarrierWord + 2 * pair;
+    fl.tail_share = share;
+    ++pair;
     MG_CUDA(cudaStreamWaitEvent(k.stream, c->bfork, 0));
     MG_TRY(launch_residual(k.f.as<double>(), k.u.as<double>(), k.op[0].as<double>(), nullptr, k.r32.as<float>(),
                            k.partial.as<double>(), k.n, k.stream,
@@ -314,7 +323,7 @@ Status record_cycle(mgcnn_ctx* c, cudaStream_t main, const FusedWeights& w) {
                                                                   k.hist.as<double>(), c->bmaxit + 1,
                                                                   c->bparams.as<double>(), k.B, c->bcount.as<int>());
     MG_LAUNCH("batch_check_kernel");
-    MG_TRY(fused_vcycle_levels(k.fl, k.r32.as<float>(), k.rn2.as<double>(), k.u.as<double>(), k.u.as<double>(), w,
+    MG_TRY(fused_vcycle_levels(fl, k.r32.as<float>(), k.rn2.as<double>(), k.u.as<double>(), k.u.as<double>(), w,
                                state, k.stream, nullptr));
     MG_CUDA(cudaEventRecord(k.done, k.stream));
     MG_CUDA(cudaStreamWaitEvent(main, k.done, 0));
@@ -322,9 +331,22 @@ Status record_cycle(mgcnn_ctx* c, cudaStream_t main, const FusedWeights& w) {
   return {};
 }
 
+Status capture_cycle_once(mgcnn_ctx* c);
+
 // The batch's graph: a conditional WHILE node around one cycle (bwhile), or,
-// where that cannot be built, the plain cycle graph launched once per cycle.
+// where that cannot be built, the plain cycle graph launched once per cycle;
+// without the coarse tail kernel where neither holds it.
 Status capture_cycle(mgcnn_ctx* c) {
+  Status s = capture_cycle_once(c);
+  if (!s.ok() && c->tail_n > 0) {
+    cudaGetLastError();
+    c->tail_n = 0;
+    s = capture_cycle_once(c);
+  }
+  return s;
+}
+
+Status capture_cycle_once(mgcnn_ctx* c) {
   if (c->bgraph) {
     cudaGraphExecDestroy(c->bgraph);
     c->bgraph = nullptr;

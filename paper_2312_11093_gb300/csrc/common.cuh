@@ -116,6 +116,8 @@ struct mgcnn_ctx {
   int cp = 0;                             // channels padded for the tensor cores (8 or 16)
   int fused = 1;                          // use the fused level kernels when they apply
   int fuse_residual = 0;                  // mgcnn_solve: where the residual is formed (MGCNN_OPT_FUSED_RESIDUAL)
+  int tail_n = 0;                         // MGCNN_OPT_COARSE_TAIL: the levels of at most this grid side in one
+                                          // cooperative kernel (0: a launch per level; reset to 0 if refused)
   bool pdl = true;                        // level kernels with programmatic dependent launch (off if a graph
                                           // with programmatic edges cannot be built)
   int tile_var[2][mgcnn::kMaxLevels] = {};  // autotuned tile variants (down, up) per level
@@ -201,8 +203,15 @@ void add_launches(long long k);   // kernels launched through a CUDA graph
 // Profiling kinds: finest-level launches bracketed by events when enabled.
 enum ProfKind { kProfResidual = 0, kProfResnet = 1, kProfRestrict = 2, kProfProlong = 3, kProfIn = 4,
                 kProfOut = 5, kProfDown0 = 6, kProfUp0 = 7,
-                // fused down / up kernel of level l >= 1: kProfDownLevel + l, kProfUpLevel + l
-                kProfDownLevel = 8, kProfUpLevel = 8 + kMaxLevels, kProfKinds = 8 + 2 * kMaxLevels };
+                // fused down / up kernel of level l >= 1: kProfDownLevel + l, kProfUpLevel + l;
+                // the coarse tail kernel takes the unused slot of level 0
+                kProfDownLevel = 8, kProfTail = kProfDownLevel, kProfUpLevel = 8 + kMaxLevels,
+                kProfKinds = 8 + 2 * kMaxLevels };
+// The context's device error flag (kerr) is the first of kErrWords words; from
+// word kTailBarrierWord on, pairs of words hold the coarse tail kernels' grid
+// barriers (arrival count, generation; zero when no kernel is inside one): pair
+// 0 for the context's single problem, pair 1 + i for class i of a batch.
+constexpr int kErrWords = 64, kTailBarrierWord = 2, kTailBarriers = (kErrWords - kTailBarrierWord) / 2;
 int prof_begin(mgcnn_ctx* c, int kind);   // -1 when profiling is off
 void prof_end(mgcnn_ctx* c, int slot);
 

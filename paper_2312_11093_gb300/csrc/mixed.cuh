@@ -46,6 +46,10 @@ struct FusedLevels {
   int* err = nullptr;                    // device flag: a block's tile copies timed out
   float* alpha = nullptr;                // device [batch][2]: input scale alpha and 1 / alpha per problem
   bool pdl = false;                      // launch the level kernels with programmatic dependent launch
+  int tail_n = 0;                        // levels of at most this grid side run as one cooperative kernel (0: off)
+  unsigned* tail_bar = nullptr;          // that kernel's grid barrier: two zeroed words of the owner's
+  int tail_share = 1;                    // tail kernels that may run at once (batch classes): each takes at
+                                         // most 1 / tail_share of the resident blocks, so all fit together
   int n[kMaxLevels] = {};
   int var_down[kMaxLevels] = {};         // tile variant per level (autotuned)
   int var_up[kMaxLevels] = {};

@@ -273,16 +273,15 @@ Status launch_alpha(const FusedLevels& fl, const double* norm2, cudaStream_t st)
 //   X (layer output kept):   rows 0..XH-1, cols 0..XW-1 (XH = 16 + R, XW = 32 + R)
 //   Z (layer input, halo 1): rows -1..XH,  cols -1..XW
 //   Rg (residual, halo 2):   rows -2..XH+1, cols -2..XW+1   (finest level only)
+// The down kernel's work on the tile (tbx, tby) of problem tbz (one block).
 template <int FH, int FW, bool FIRST, bool HAS_R, bool RESID>
-__global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r, const float* __restrict__ alpha2,
-                                                  const __grid_constant__ ResidIn ra,
-                                                  const __grid_constant__ SmallWeights sw,
-                                                  const __grid_constant__ CUtensorMap map_x,
-                                                  const __grid_constant__ CUtensorMap map_s,
-                                                  const __grid_constant__ CUtensorMap map_r,
-                                                  const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fR,
-                                                  bf16* __restrict__ xdown, bf16* __restrict__ xc, int n,
-                                                  const int* __restrict__ active, int* __restrict__ err) {
+__device__ __forceinline__ void down_body(const float* __restrict__ r, const float* __restrict__ alpha2,
+                                          const ResidIn& ra, const SmallWeights& sw, const CUtensorMap& map_x,
+                                          const CUtensorMap& map_s, const CUtensorMap& map_r,
+                                          const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fR,
+                                          bf16* __restrict__ xdown, bf16* __restrict__ xc, int n,
+                                          const int* __restrict__ active, int* __restrict__ err, int tbx, int tby,
+                                          int tbz) {
   static_assert(FH % 2 == 0 && FW % 2 == 0 && (FH / 2) * (FW / 2) % 16 == 0, "tile shape");
   static_assert(FIRST || !RESID, "the residual is fused into the finest level only");
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
@@ -298,11 +297,11 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
   float* rs = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(xd) +
                                       down_xd_bytes<FH, FW, FIRST, HAS_R>());   // finest level only
   __shared__ __align__(8) uint64_t bar;
-  const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
+  const int j0 = tby * FH, i0 = tbx * FW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t N = (size_t)n * n;
-  // problem blockIdx.z of a batch of equal-size problems stored back to back
-  const int bz = blockIdx.z;
+  // problem tbz of a batch of equal-size problems stored back to back
+  const int bz = tbz;
   {
     const size_t Nc = (size_t)((n - 1) / 2) * ((n - 1) / 2);
     if (FIRST) r += bz * N;
@@ -439,7 +438,7 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
     // (2 cr + a, 2 cc + b) of X; strips of 16 coarse pixels in row-major order
     constexpr int CH = FH / 2, CW = FW / 2;
     const int nc = (n - 1) / 2;
-    const int J0 = blockIdx.y * CH, I0 = blockIdx.x * CW;
+    const int J0 = tby * CH, I0 = tbx * CW;
     const TapOffsets<XW> tr;
     for (int st = warp; st < CH * CW / 16; st += NW) {
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -455,6 +454,20 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
     }
   }
   pdl_trigger();   // the next kernel may start its prologue
+}
+
+template <int FH, int FW, bool FIRST, bool HAS_R, bool RESID>
+__global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r, const float* __restrict__ alpha2,
+                                                  const __grid_constant__ ResidIn ra,
+                                                  const __grid_constant__ SmallWeights sw,
+                                                  const __grid_constant__ CUtensorMap map_x,
+                                                  const __grid_constant__ CUtensorMap map_s,
+                                                  const __grid_constant__ CUtensorMap map_r,
+                                                  const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fR,
+                                                  bf16* __restrict__ xdown, bf16* __restrict__ xc, int n,
+                                                  const int* __restrict__ active, int* __restrict__ err) {
+  down_body<FH, FW, FIRST, HAS_R, RESID>(r, alpha2, ra, sw, map_x, map_s, map_r, fK, fR, xdown, xc, n, active, err,
+                                         blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // TCNN-add on the tensor cores over the quads of Q: each 16 quads are a GEMM
@@ -530,17 +543,15 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, cons
 // Up kernel (geometry in UpGeom).  Level l: x_pre = x_down + TCNN(x_{l+1}) on P
 // (or x_down on the coarsest level), layer x_fin = x_pre + K_up (s * x_pre) on O;
 // finest level: e = W_out * x_fin / alpha, u_out = u_in + e.
+// The up kernel's work on the tile (tbx, tby) of problem tbz (one block).
 template <int FH, int FW, bool LAST, bool HAS_P, bool RES>
-__global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUtensorMap map_xd,
-                                                const __grid_constant__ CUtensorMap map_s,
-                                                const __grid_constant__ CUtensorMap map_c,
-                                                const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
-                                                const uint32_t* __restrict__ fOutHi,
-                                                const uint32_t* __restrict__ fOutLo,
-                                                const float* __restrict__ alpha2, const double* __restrict__ u_in,
-                                                bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
-                                                const int* __restrict__ active, int* __restrict__ err,
-                                                const __grid_constant__ ResidOut ro, int out_lo) {
+__device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtensorMap& map_s, const CUtensorMap& map_c,
+                                        const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
+                                        const uint32_t* __restrict__ fOutHi, const uint32_t* __restrict__ fOutLo,
+                                        const float* __restrict__ alpha2, const double* __restrict__ u_in,
+                                        bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
+                                        const int* __restrict__ active, int* __restrict__ err, const ResidOut& ro,
+                                        int out_lo, int tbx, int tby, int tbz) {
   using G = UpGeom<FH, FW, LAST, HAS_P, RES>;
   constexpr int H = G::H, OH = G::OH, OW = G::OW, QW = G::QW, QOFF = G::QOFF;
   constexpr int HE = G::HE, EH = G::EH, EW = G::EW;
@@ -553,10 +564,10 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   uint4* pl = zs + pad8(G::QH * QW);                                   // finest level only
   uint4* cs = pl + (LAST ? pad8(OH * OW) : 0);                         // coarser level only
   __shared__ __align__(8) uint64_t bar;
-  const int j0 = blockIdx.y * FH, i0 = blockIdx.x * FW;
+  const int j0 = tby * FH, i0 = tbx * FW;
   const int qj0 = j0 - H - 1 - QOFF, qi0 = i0 - H - 1 - QOFF;         // Q's corner (odd when HAS_P)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int bz = blockIdx.z;
+  const int bz = tbz;
   {
     const size_t N = (size_t)n * n;
     if (LAST) {
@@ -731,6 +742,121 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
   pdl_trigger();
 }
 
+template <int FH, int FW, bool LAST, bool HAS_P, bool RES>
+__global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUtensorMap map_xd,
+                                                const __grid_constant__ CUtensorMap map_s,
+                                                const __grid_constant__ CUtensorMap map_c,
+                                                const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
+                                                const uint32_t* __restrict__ fOutHi,
+                                                const uint32_t* __restrict__ fOutLo,
+                                                const float* __restrict__ alpha2, const double* __restrict__ u_in,
+                                                bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
+                                                const int* __restrict__ active, int* __restrict__ err,
+                                                const __grid_constant__ ResidOut ro, int out_lo) {
+  up_body<FH, FW, LAST, HAS_P, RES>(map_xd, map_s, map_c, fK, fTc, fOutHi, fOutLo, alpha2, u_in, xfin, u_out, n,
+                                    active, err, ro, out_lo, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// The coarse tail of the cycle in one launch.  From level `lt` down (grids of
+// at most kTailMaxN points per side) every level's kernel is a few blocks whose
+// cost is launch and ramp time, so one cooperative kernel runs them all: the
+// blocks take the tiles of level lt's down step, then of level lt+1, ... the
+// coarsest, then the up steps back to lt, a grid-wide barrier between the
+// levels.  Same tile bodies (16 x 32 tiles), same arithmetic per pixel.
+constexpr int kTailFH = 16, kTailFW = 32, kTailMaxN = 255, kTailMaxLevels = 8;
+struct TailLevel {
+  CUtensorMap dx, ds;              // down: the level's input x (box of Z), s (box of Z)
+  CUtensorMap ux, us, uc;          // up: x_down, s (boxes of Q), the coarser level's x (coarse box)
+  bf16 *xa, *xb, *xc;              // x_down, x (input, then output of the up step), coarser level's x
+  int n, tx, ty;                   // grid side, tiles per row / column
+};
+struct TailArgs {
+  TailLevel lv[kTailMaxLevels];
+  int nl, batch;
+  const uint32_t *f_down, *f_R, *f_up, *f_tcnn;
+  const int* active;
+  int* err;
+  unsigned* bar;                   // [0] arrivals, [1] generation (zero when idle)
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of the tail (all blocks resident: cooperative launch).  The
+// block's global writes are made visible to the other blocks, TMA loads
+// included; the wait is bounded (false and the error flag past the limit).
+__device__ __forceinline__ bool tail_sync(unsigned* bar, int* err) {
+  // the block's writes are ordered before thread 0's release by the CTA barrier
+  // and the cumulative fence that follows it
+  __syncthreads();
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned gen = ld_acquire(bar + 1);
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);   // the last arrival resets the count, then opens the next generation
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      ok = 0;
+      for (int i = 0; i < (1 << 21) && !ok; ++i)   // about a second of L2 round trips
+        if (ld_acquire(bar + 1) != gen) ok = 1;
+      if (!ok) atomicExch(err, 1);
+    }
+    __threadfence();
+    asm volatile("fence.proxy.async.global;" ::: "memory");   // the TMA loads this thread issues next
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(NT, 4) tail_kernel(const __grid_constant__ TailArgs ta) {
+  const ResidIn no_ra{};
+  const ResidOut no_ro{};
+  const SmallWeights no_sw{};
+  for (int k = 0; k < ta.nl; ++k) {
+    const TailLevel& L = ta.lv[k];
+    const int per = L.tx * L.ty, tiles = per * ta.batch;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const int bz = t / per, tl = t - bz * per, ty = tl / L.tx, tx = tl - ty * L.tx;
+      if (k + 1 < ta.nl)
+        down_body<kTailFH, kTailFW, false, true, false>(nullptr, nullptr, no_ra, no_sw, L.dx, L.ds, L.ds, ta.f_down,
+                                                        ta.f_R, L.xa, L.xc, L.n, ta.active, ta.err, tx, ty, bz);
+      else
+        down_body<kTailFH, kTailFW, false, false, false>(nullptr, nullptr, no_ra, no_sw, L.dx, L.ds, L.ds, ta.f_down,
+                                                         ta.f_R, L.xa, nullptr, L.n, ta.active, ta.err, tx, ty, bz);
+      // the next tile's copies overwrite the shared tiles this one read and wrote
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+    }
+    if (!tail_sync(ta.bar, ta.err)) return;
+  }
+  for (int k = ta.nl - 1; k >= 0; --k) {
+    const TailLevel& L = ta.lv[k];
+    const int per = L.tx * L.ty, tiles = per * ta.batch;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const int bz = t / per, tl = t - bz * per, ty = tl / L.tx, tx = tl - ty * L.tx;
+      if (k + 1 < ta.nl)
+        up_body<kTailFH, kTailFW, false, true, false>(L.ux, L.us, L.uc, ta.f_up, ta.f_tcnn, nullptr, nullptr, nullptr,
+                                                      nullptr, L.xb, nullptr, L.n, ta.active, ta.err, no_ro, 0, tx, ty,
+                                                      bz);
+      else
+        up_body<kTailFH, kTailFW, false, false, false>(L.ux, L.us, L.us, ta.f_up, ta.f_tcnn, nullptr, nullptr,
+                                                       nullptr, nullptr, L.xb, nullptr, L.n, ta.active, ta.err, no_ro,
+                                                       0, tx, ty, bz);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+    }
+    if (k > 0 && !tail_sync(ta.bar, ta.err)) return;
+  }
+}
+
 // Dynamic shared memory of a kernel instantiation: above 48 KB the kernel must be
 // allowed it once per device (cudaFuncSetAttribute); the (device, kernel) pairs
 // already allowed are remembered, under a lock (contexts may live in different
@@ -876,6 +1002,113 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
   return {};
 }
 
+int tail_capacity();
+
+// The coarse tail (tail_kernel): the levels from `lt` to the coarsest in one
+// cooperative launch, when at least two levels qualify (grid side at most
+// fl.tail_n and kTailMaxN, level 1 or coarser, at most kTailMaxLevels levels).
+int tail_start(const FusedLevels& fl) {
+  if (fl.tail_n <= 0 || !fl.tail_bar || tail_capacity() <= 0) return fl.L;
+  int lt = fl.L;
+  for (int l = fl.L - 1; l >= 1 && fl.n[l] <= std::min(fl.tail_n, kTailMaxN) && fl.L - l <= kTailMaxLevels; --l)
+    lt = l;
+  return fl.L - lt >= 2 ? lt : fl.L;
+}
+
+constexpr size_t tail_smem_bytes() {
+  return std::max(std::max(down_smem_bytes<kTailFH, kTailFW, false, true>(),
+                           down_smem_bytes<kTailFH, kTailFW, false, false>()),
+                  std::max(up_smem_bytes<kTailFH, kTailFW, false, true>(),
+                           up_smem_bytes<kTailFH, kTailFW, false, false>()));
+}
+
+// Blocks of the tail kernel that fit on the device at once (0: no cooperative
+// launch), once per device.
+int tail_capacity() {
+  static std::mutex lock;
+  static std::vector<std::pair<int, int>> known;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> g(lock);
+  for (const auto& k : known)
+    if (k.first == dev) return k.second;
+  int coop = 0, sms = 0, per_sm = 0;
+  const size_t smem = dyn_smem(tail_kernel, tail_smem_bytes());
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tail_kernel, NT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    coop = 0;
+  }
+  const int cap = coop ? per_sm * sms : 0;
+  known.emplace_back(dev, cap);
+  return cap;
+}
+
+template <bool HAS_R, bool HAS_P>
+Status tail_level_maps(const FusedLevels& fl, int l, TailLevel* t) {
+  using G = UpGeom<kTailFH, kTailFW, false, HAS_P>;
+  const int n = fl.n[l], R = HAS_R ? 1 : 0, ZH = kTailFH + R + 2, ZW = kTailFW + R + 2;
+  MG_TRY(pix8_map(fl, fl.xb[l], n, ZW, ZH, &t->dx));
+  MG_TRY(pix8_map(fl, fl.s[l], n, ZW, ZH, &t->ds));
+  MG_TRY(pix8_map(fl, fl.xa[l], n, G::QW, G::QH, &t->ux));
+  MG_TRY(pix8_map(fl, fl.s[l], n, G::QW, G::QH, &t->us));
+  if (HAS_P)
+    MG_TRY(pix8_map(fl, fl.xb[l + 1], fl.n[l + 1], G::CQW, G::CQH, &t->uc));
+  else
+    t->uc = t->us;   // not read on the coarsest level
+  return {};
+}
+
+// Levels lt .. L-1 down and back up in one cooperative launch.  Returns
+// MGCNN_ERR_CUDA (launch refused) without side effects on the level state.
+Status launch_tail(const FusedLevels& fl, int lt, const FusedWeights& w, const int* active, cudaStream_t st) {
+  const int cap = tail_capacity();
+  if (cap <= 0) return make_status(MGCNN_ERR_CUDA, "no cooperative launch on this device");
+  TailArgs ta{};
+  ta.nl = fl.L - lt;
+  ta.batch = fl.batch;
+  ta.f_down = w.f_down;
+  ta.f_R = w.f_R;
+  ta.f_up = w.f_up;
+  ta.f_tcnn = w.f_tcnn;
+  ta.active = active;
+  ta.err = fl.err;
+  ta.bar = fl.tail_bar;
+  int tiles = 0;
+  for (int k = 0; k < ta.nl; ++k) {
+    const int l = lt + k;
+    TailLevel& t = ta.lv[k];
+    if (l + 1 < fl.L)
+      MG_TRY((tail_level_maps<true, true>(fl, l, &t)));
+    else
+      MG_TRY((tail_level_maps<false, false>(fl, l, &t)));
+    t.xa = fl.xa[l];
+    t.xb = fl.xb[l];
+    t.xc = l + 1 < fl.L ? fl.xb[l + 1] : nullptr;
+    t.n = fl.n[l];
+    t.tx = (t.n + kTailFW - 1) / kTailFW;
+    t.ty = (t.n + kTailFH - 1) / kTailFH;
+    tiles = std::max(tiles, t.tx * t.ty * fl.batch);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(std::max(1, std::min(tiles, cap / std::max(1, fl.tail_share))));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = dyn_smem(tail_kernel, tail_smem_bytes());
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, tail_kernel, ta);
+  if (le != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(le, "tail_kernel launch");
+  }
+  return {};
+}
+
 constexpr int kTileH[kFusedVariants] = {16, 8, 16, 32, 24};
 constexpr int kTileW[kFusedVariants] = {32, 32, 16, 32, 32};
 
@@ -914,14 +1147,20 @@ Status launch_up_variant(int v, int l, const FusedLevels& fl, const double* norm
 Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double* norm2, double* e,
                            const double* u_skip, const FusedWeights& w, const int* active, cudaStream_t st,
                            mgcnn_ctx* prof_ctx, FusedCycleOpt opt) {
-  const int L = fl.L;
+  const int L = fl.L, lt = tail_start(fl);
   if (!opt.after_fused_down0) MG_TRY(launch_alpha(fl, norm2, st));
-  for (int l = opt.after_fused_down0 ? 1 : 0; l < L; ++l) {
+  for (int l = opt.after_fused_down0 ? 1 : 0; l < lt; ++l) {
     const int ps = prof_ctx ? prof_begin(prof_ctx, l == 0 ? kProfDown0 : kProfDownLevel + l) : -1;
     MG_TRY(launch_down_variant(fl.var_down[l], l, fl, r32, norm2, w, active, st));
     if (prof_ctx) prof_end(prof_ctx, ps);
   }
-  for (int l = L - 1; l >= 0; --l) {
+  if (lt < L) {
+    const int ps = prof_ctx ? prof_begin(prof_ctx, kProfTail) : -1;
+    MG_TRY(launch_tail(fl, lt, w, active, st));
+    MG_LAUNCH("tail_kernel");
+    if (prof_ctx) prof_end(prof_ctx, ps);
+  }
+  for (int l = lt - 1; l >= 0; --l) {
     const int ps = prof_ctx ? prof_begin(prof_ctx, l == 0 ? kProfUp0 : kProfUpLevel + l) : -1;
     MG_TRY(launch_up_variant(fl.var_up[l], l, fl, norm2, e, u_skip, w, active, st, l == 0 ? opt.resid_out : nullptr));
     if (prof_ctx) prof_end(prof_ctx, ps);
@@ -1007,6 +1246,8 @@ FusedLevels ctx_levels(mgcnn_ctx* c) {
   fl.err = c->kerr.as<int>();
   fl.alpha = c->alpha32.as<float>();
   fl.pdl = c->pdl;
+  fl.tail_n = c->tail_n;
+  fl.tail_bar = c->kerr.as<unsigned>() + kTailBarrierWord;
   for (int l = 0; l < c->L; ++l) {
     fl.n[l] = c->lv[l].n;
     fl.s[l] = c->s16[l].as<bf16>();

@@ -110,6 +110,8 @@ Status build_graph(mgcnn_ctx* c) {
       fl.err = c->kerr.as<int>();
       fl.alpha = c->alpha32.as<float>();
       fl.pdl = c->pdl;
+      fl.tail_n = c->tail_n;
+      fl.tail_bar = c->kerr.as<unsigned>() + kTailBarrierWord;
       for (int l = 0; l < c->L; ++l) {
         fl.n[l] = c->lv[l].n;
         fl.s[l] = c->s16[l].as<__nv_bfloat16>();
@@ -224,6 +226,12 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
   if (!c->gstream) MG_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
   if (!c->sgraph_valid) {
     Status b = build_graph(c);
+    if (!b.ok() && c->tail_n > 0) {
+      // no cooperative kernel in this graph: a launch per coarse level
+      cudaGetLastError();
+      c->tail_n = 0;
+      b = build_graph(c);
+    }
     if (!b.ok() && c->pdl) {
       // programmatic edges not available in this graph: plain launches
       cudaGetLastError();

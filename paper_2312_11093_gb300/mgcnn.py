@@ -369,14 +369,15 @@ class Solver:
         return st, iters, relres, stat
 
     # class index -> name; the finest level's fused kernels are "down0" / "up0",
-    # level l >= 1 "down<l>" / "up<l>" (slot 8 + 0 and 21 + 0 are unused)
+    # level l >= 1 "down<l>" / "up<l>", the coarse tail kernel "tail" (slot 21 is unused)
     PROFILE_KINDS = (("residual", "resnet", "restrict", "prolong", "in", "out", "down0", "up0") +
-                     ("",) + tuple(f"down{l}" for l in range(1, 13)) + ("",) + tuple(f"up{l}" for l in range(1, 13)))
+                     ("tail",) + tuple(f"down{l}" for l in range(1, 13)) + ("",) + tuple(f"up{l}" for l in range(1, 13)))
     OPT_FUSED = 1
     OPT_DEVICE_LOOP = 2
     OPT_TILE = 3
     OPT_SYMMETRIC = 4
     OPT_FUSED_RESIDUAL = 5
+    OPT_COARSE_TAIL = 6
 
     def set_option(self, option: int, value: int):
         self._check(self._L.mgcnn_set_option(self._h, int(option), int(value)), "mgcnn_set_option")

@@ -70,6 +70,29 @@ def test_batched_equals_single_problem_solves(M):
         assert stat[i] == st1
 
 
+def test_batched_coarse_tail_equals_a_launch_per_level(M):
+    """Classes run concurrently, each with its own coarse tail kernel and grid
+    barrier; a class with more tiles than the cooperative grid has blocks (24
+    problems of 255^2: 768 tiles on level 1) strides them.  Against a launch per
+    level: bit-identical iterates."""
+    sizes = [255] * 24 + [63] * 30 + [1023] * 2 + [15] * 3
+    ks, fs = _fields(sizes, 5)
+    w = _weights(M)
+    res = {}
+    for t in (255, 0):
+        sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+        sv.set_option(sv.OPT_COARSE_TAIL, t)
+        sv.set_weights(w)
+        sv.setup_batched(ks, sizes)
+        us = [np.zeros(n * n) for n in sizes]
+        st, iters, relres, stat = sv.solve_batched(fs, us, 1e-30, 4, per_problem=True)
+        res[t] = (list(iters), us, list(stat))
+    assert res[255][0] == res[0][0]
+    assert res[255][2] == res[0][2]
+    for a, b in zip(res[255][1], res[0][1]):
+        assert np.array_equal(a, b)
+
+
 def test_batched_statuses_and_special_cases(M):
     sizes = [31, 31, 15]
     ks, fs = _fields(sizes, 2)

@@ -494,6 +494,47 @@ def test_fused_residual_equals_separate_residual(M, n, loop):
         assert np.array_equal(out[fres][2], out[0][2]), fres
 
 
+@pytest.mark.parametrize("n,loop,tail", [(63, 1, 255), (255, 0, 255), (1023, 1, 255), (1023, 0, 15),
+                                         (4095, 1, 255), (4095, 0, 63)])
+def test_coarse_tail_equals_a_launch_per_level(M, n, loop, tail):
+    """The coarse levels in one cooperative kernel (16 x 32 tiles, grid-wide
+    barriers between the levels) against a launch per level: the same arithmetic
+    per pixel, so bit-identical iterates and cycle counts, in the device loop's
+    graph and in the host loop; the profiled pass records the tail kernel."""
+    from paper_2312_11093_gb300.train import init_weights
+    k, f = problem(n, 70 + n)
+    w = init_weights(8, 1, 1, np.random.default_rng(12), out_scale=0.05)
+    out = {}
+    for t in (tail, 0):
+        sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+        sv.set_option(sv.OPT_DEVICE_LOOP, loop)
+        sv.set_option(sv.OPT_COARSE_TAIL, t)
+        sv.set_weights(w)
+        sv.setup(k.ravel().copy(), n)
+        u = np.zeros(n * n)
+        st, it, hist = sv.solve(f.ravel().copy(), u, 1e-30, 5)
+        out[t] = (it, hist.copy(), u)
+        sv.profile(True)
+        sv.solve(f.ravel().copy(), np.zeros(n * n), 1e-30, 2)
+        prof = sv.profile_read()
+        sv.profile(False)
+        if t:
+            assert prof["tail"][1] >= 2, prof["tail"]
+            assert prof["up1"][1] == (0 if n <= 2 * min(t, 255) + 1 else prof["up0"][1]), prof
+        else:
+            assert prof["tail"][1] == 0
+    assert out[tail][0] == out[0][0] == 5
+    np.testing.assert_allclose(out[tail][1], out[0][1], rtol=1e-13, atol=0)
+    assert np.array_equal(out[tail][2], out[0][2])
+
+
+def test_coarse_tail_option_range(M):
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.set_option(sv.OPT_COARSE_TAIL, -1)
+    assert ei.value.status == M.ERR_ARG
+
+
 def test_tile_option_range(M):
     sv = M.Solver(8, 1, 1, precision="mixed_bf16")
     for bad in (-2, 5):
