@@ -1049,12 +1049,16 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
       return finish(c, st);
     }
     case MGCNN_OPT_TILE:
-      if (value < -1 || value >= kFusedVariants)
-        return finish(c, make_status(MGCNN_ERR_ARG, "tile shape %d not in -1..%d", value, kFusedVariants - 1));
+      if (value < -1 || value >= kUpVariants)
+        return finish(c, make_status(MGCNN_ERR_ARG, "tile shape %d not in -1..%d", value, kUpVariants - 1));
       c->tile_fixed = value;
       c->sgraph_valid = false;   // the captured loop holds the old shapes
       if (value >= 0) {
-        for (int l = 0; l < kMaxLevels; ++l) c->tile_var[0][l] = c->tile_var[1][l] = value;
+        // the up-kernel-only shapes pair with the down kernel's 24 x 32
+        for (int l = 0; l < kMaxLevels; ++l) {
+          c->tile_var[0][l] = value < kFusedVariants ? value : 4;
+          c->tile_var[1][l] = value;
+        }
         c->tuned = true;
       } else {
         c->tuned = false;

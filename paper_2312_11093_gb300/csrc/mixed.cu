@@ -40,7 +40,7 @@ struct MixLayout {
   size_t down = 0, up = 0, R = 0;        // byte offsets of the fragment blocks
   size_t w_in = 0, w_out = 0, w_P = 0;   // byte offsets of FP32 arrays
   size_t s_frag = 0, s_fp = 0;           // setup network: 5 fragment blocks, FP32 biases + W_cin (CP = 8)
-  size_t out_hi = 0, out_lo = 0;         // W_out fragments for the fused up kernel (CP = 8)
+  size_t out_taps = 0;                   // W_out fragments by tap for the fused up kernel (CP = 8)
   size_t tcnn = 0;                       // TCNN fragments of the 2 x 2 fine-pixel quads (CP = 8)
   size_t bytes = 0;
 };
@@ -59,8 +59,7 @@ MixLayout mix_layout(const mgcnn_ctx* c) {
   m.w_P = o;   o += (size_t)m.cp * m.cp * 9 * 4;
   m.s_frag = o; o += 5 * m.frag_words * 4;
   m.s_fp = o;   o += (4 * 8 + 8 * kFeatures * 9 + 8) * 4;
-  m.out_hi = o; o += m.frag_words * 4;
-  m.out_lo = o; o += m.frag_words * 4;
+  m.out_taps = o; o += (size_t)kOutTapRegs * 32 * 4;
   m.tcnn = o;   o += (size_t)kTcnnQuadRegs * 32 * 4;
   m.bytes = o;
   return m;
@@ -102,6 +101,27 @@ void pack_tcnn_frags(const double* W, int C, uint32_t* out) {
         }
     }
   }
+}
+
+// W_out (one output channel) by tap, for the fused up kernel's product
+// D[pixel][tap] = sum_ch (hi(y) + lo(y))[ch] w_tap[ch] as one K = 16 MMA over
+// A = [hi(y) | lo(y)]: B tile b holds taps 6 b .. (n = tap - 6 b; n past tap 8
+// zero), as [w_hi ; w_hi] (hl = 0) and [w_lo ; 0] (hl = 1, the weights' low
+// parts times hi(y)).  Word ((b * 2 + hl) * 2 + reg) * 32 + lane; reg 0 holds k
+// = 2q, 2q + 1 (channels of hi(y)), reg 1 k = 8 + 2q, 9 + 2q (those of lo(y)).
+// whi[ch * 9 + tap] and wlo[ch * 9 + tap] are the BF16-exact hi and lo parts of w_out.
+void pack_out_taps(const std::vector<double>& whi, const std::vector<double>& wlo, uint32_t* out) {
+  for (int b = 0; b < 2; ++b)
+    for (int hl = 0; hl < 2; ++hl)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, q = lane & 3, tap = 6 * b + g;
+        const bool valid = b == 0 ? g < 6 : g < 3;
+        const std::vector<double>& w = hl ? wlo : whi;
+        auto wv = [&](int ch) -> uint32_t { return valid ? f2bf_host((float)w[ch * 9 + tap]) : 0u; };
+        const uint32_t pr = wv(2 * q) | (wv(2 * q + 1) << 16);
+        out[((b * 2 + hl) * 2 + 0) * 32 + lane] = pr;
+        out[((b * 2 + hl) * 2 + 1) * 32 + lane] = hl ? 0u : pr;
+      }
 }
 
 void pack_frags(const double* W, int C, int cp, uint32_t* out) {
@@ -497,8 +517,8 @@ FusedWeights fused_weights(const mgcnn_ctx* c) {
   const MixLayout ml = mix_layout(c);
   const char* wb = c->wmix.as<char>();
   return FusedWeights{reinterpret_cast<const uint32_t*>(wb + ml.down), reinterpret_cast<const uint32_t*>(wb + ml.up),
-                      reinterpret_cast<const uint32_t*>(wb + ml.R), reinterpret_cast<const uint32_t*>(wb + ml.out_hi),
-                      reinterpret_cast<const uint32_t*>(wb + ml.out_lo), reinterpret_cast<const uint32_t*>(wb + ml.tcnn),
+                      reinterpret_cast<const uint32_t*>(wb + ml.R), reinterpret_cast<const uint32_t*>(wb + ml.out_taps),
+                      reinterpret_cast<const uint32_t*>(wb + ml.tcnn),
                       c->small_w, c->out_lo};
 }
 
@@ -542,8 +562,7 @@ Status mixed_set_weights(mgcnn_ctx* c) {
       }
     c->out_lo = 0;
     for (double v : wlo) c->out_lo |= (v != 0.0);
-    pack_frags(whi.data(), 8, 8, reinterpret_cast<uint32_t*>(blob.data() + ml.out_hi));
-    pack_frags(wlo.data(), 8, 8, reinterpret_cast<uint32_t*>(blob.data() + ml.out_lo));
+    pack_out_taps(whi, wlo, reinterpret_cast<uint32_t*>(blob.data() + ml.out_taps));
     pack_tcnn_frags(w.data() + c->wl.w_P, C, reinterpret_cast<uint32_t*>(blob.data() + ml.tcnn));
     // W_in of the fused down kernel, zero beyond C channels
     SmallWeights& sw = c->small_w;

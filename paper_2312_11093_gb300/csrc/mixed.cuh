@@ -21,7 +21,9 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega);
 void mixed_release(mgcnn_ctx* c);
 // mixed_fused.cu: fused level kernels (8 channels, one layer per ResNet)
 constexpr int kFusedVariants = 5;        // tile shapes 16x32, 8x32, 16x16, 32x32, 24x32
+constexpr int kUpVariants = 7;           // the up kernel also: 24x30, 32x30 (finest level: rows of 32 layer outputs)
 constexpr int kTcnnQuadRegs = 16;        // TCNN B fragments per lane: 4 fine pixels x 2 k steps x 2
+constexpr int kOutTapRegs = 8;           // W_out B fragments per lane: 2 tap tiles x (hi, lo) x 2 k halves
 class TmaMaps;
 // Inputs of the finest down kernel when it computes the residual itself.
 struct ResidIn {
@@ -59,7 +61,7 @@ struct FusedLevels {
 };
 struct FusedWeights {
   const uint32_t *f_down, *f_up, *f_R;   // mma B fragments (device)
-  const uint32_t *f_out_hi, *f_out_lo;   // W_out as an 8 -> 8 layer (output channel 0), BF16 hi + lo parts
+  const uint32_t* f_out_taps;            // W_out by tap (kOutTapWords, see pack_out_taps), BF16 hi + lo parts
   const uint32_t* f_tcnn;                // TCNN of 2 x 2 fine-pixel quads (kTcnnQuadRegs x 32 words)
   SmallWeights small;                    // by value, see SmallWeights
   int out_lo = 1;                        // 0: W_out is exact in BF16 (its lo part is zero), one pass suffices
@@ -78,7 +80,7 @@ Status fused_vcycle_levels(const FusedLevels& fl, const float* r32, const double
 Status fused_down0_resid(const FusedLevels& fl, const ResidIn& ra, const FusedWeights& w, const int* active,
                          cudaStream_t st, mgcnn_ctx* prof_ctx);
 Status fused_set_alpha(const FusedLevels& fl, const double* norm2, cudaStream_t st);
-int fused_down0_blocks(int n, int variant);
+int fused_down0_blocks(int n, int variant);  // blocks of a finest-level launch of tile variant `variant`
 size_t fused_partials_max(int n);          // the largest fused_down0_blocks over the tile variants
 Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, double* scratch,
                       const FusedWeights& w, cudaStream_t st, int reps, const ResidIn* ra = nullptr,

@@ -106,13 +106,40 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
 // more than the 48 KB of static shared memory); every array starts on a 128-byte
 // boundary (TMA destinations).
 constexpr int pad8(int pixels) { return (pixels + 7) / 8 * 8; }   // uint4 count -> multiple of 128 bytes
-// Bytes of the down kernel's layer-output slot: on the finest level it first
+// The down kernel's layer output tile split by column parity: row pitch XP
+// pixels, column c at c / 2 (even c) or XE + c / 2 (odd c).  The restriction's
+// A rows (16 coarse pixels of a row, stride two in fine columns) then sit on
+// consecutive pixels, free of shared-memory bank conflicts; XE = 4 (mod 8)
+// keeps the layer's stores of eight consecutive columns conflict-free too.
+constexpr int split_xe(int xw) { return ((xw + 1) / 2 + 3) / 8 * 8 + 4; }
+constexpr int split_xp(int xw) { return split_xe(xw) + xw / 2; }
+template <int XW>
+struct SplitCols {
+  static constexpr int XE = split_xe(XW);
+  static constexpr int XP = split_xp(XW);
+  static __device__ __forceinline__ int col(int c) { return (c & 1) ? XE + (c >> 1) : (c >> 1); }
+  // the restriction's taps (a, b): row a, column b of the coarse pixel's 3 x 3 window
+  uint32_t off[4];
+  __device__ __forceinline__ SplitCols() {
+    const int kh = (threadIdx.x & 31) >> 4;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int t = 2 * s + kh, b = t % 3;
+      off[s] = 16u * ((t / 3) * XP + (b == 1 ? XE : b / 2));
+    }
+  }
+  static constexpr uint32_t off8 = 16u * (2 * XP + 1);
+};
+
+// Bytes of the down kernel's layer-output slot (the split-column tile where a
+// restriction follows): on the finest level it first
 // holds u (FP64) on the residual region plus one pixel when the residual is
 // computed in the kernel.
 template <int FH, int FW, bool FIRST, bool HAS_R>
 constexpr size_t down_xd_bytes() {
   constexpr int XH = FH + (HAS_R ? 1 : 0), XW = FW + (HAS_R ? 1 : 0);
-  constexpr size_t xd = 16u * pad8(XH * XW), us = (8u * (XH + 6) * (XW + 6) + 127) / 128 * 128;
+  constexpr size_t xd = HAS_R ? 16u * pad8(XH * split_xp(XW)) : 0u;
+  constexpr size_t us = FIRST ? (8u * (XH + 6) * (XW + 6) + 127) / 128 * 128 : 0u;
   return (FIRST && us > xd) ? us : xd;
 }
 // The finest level's residual tile: RH rows of r (halo 2 around the layer
@@ -189,17 +216,23 @@ struct TapOffsets {
 // strip_conv with precomputed addressing: base_m is the tap-(0,0) pixel of
 // A row m = (lane & 7) + 8 ((lane >> 3) & 1) (the x4 loads), base_l the one of
 // row lane & 15 (the ninth tap's x2 load).
-template <int PITCH>
-__device__ __forceinline__ void strip_conv_at(const uint4* tile, const uint32_t* wf, int base_m, int base_l,
-                                              const TapOffsets<PITCH>& to, float* acc) {
+template <class Taps>
+__device__ __forceinline__ void strip_conv_taps(const uint4* tile, const uint32_t* wf, int base_m, int base_l,
+                                                const Taps& to, float* acc) {
   const uint32_t am = sa(tile) + 16u * base_m, al = sa(tile) + 16u * base_l;
   uint32_t a[4][4], a8[2];
 #pragma unroll
   for (int s = 0; s < 4; ++s) ldsm_x4(a[s], am + to.off[s]);
-  ldsm_x2(a8, al + TapOffsets<PITCH>::off8);
+  ldsm_x2(a8, al + Taps::off8);
 #pragma unroll
   for (int s = 0; s < 4; ++s) mma16816(acc, a[s], wf[2 * s], wf[2 * s + 1]);
   mma1688(acc, a8[0], a8[1], wf[8]);
+}
+
+template <int PITCH>
+__device__ __forceinline__ void strip_conv_at(const uint4* tile, const uint32_t* wf, int base_m, int base_l,
+                                              const TapOffsets<PITCH>& to, float* acc) {
+  strip_conv_taps(tile, wf, base_m, base_l, to, acc);
 }
 
 // One ResNet layer strip y = x + K z (Eq. heteroresnet) with the skip folded
@@ -410,22 +443,26 @@ __device__ __forceinline__ void down_body(const float* __restrict__ r, const flo
   const int g = lane >> 2, q = lane & 3;
   const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
   {
-    // strips of 16 consecutive pixels of X in row-major order (a strip may wrap
-    // to the next row); the division by the compile-time width is a multiply
-    constexpr int NX = XH * XW, NSTRIP = (NX + 15) / 16;
+    // strips of 16 consecutive pixels of the Z tile's rows 0..XH-1 (pitch ZW,
+    // so a strip's A rows are consecutive tile pixels even where it wraps to
+    // the next row: no shared-memory bank conflicts); pixel p of a row is the
+    // tap-(0,0) pixel of X pixel p, the last ZW - XW of each row are dropped.
+    // The division by the compile-time pitch is a multiply.
+    constexpr int NX = XH * ZW, NSTRIP = (NX + 15) / 16;
+    static_assert(pad8(ZH * ZW) >= ZH * ZW + ZW - XW, "the dropped pixels' taps stay inside the z tile");
     const TapOffsets<ZW> to;
     const uint32_t fI = identity_frag();
     for (int st = warp; st < NSTRIP; st += NW) {
-      const int pm = min(st * 16 + mrow, NX - 1), rm = pm / XW;
+      const int pm = min(st * 16 + mrow, NX - 1);
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      layer_strip<ZW>(zs, xs, wk, fI, rm * ZW + (pm - rm * XW), to, acc);
+      layer_strip<ZW>(zs, xs, wk, fI, pm, to, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int p = st * 16 + g + 8 * h;
-        if (p >= NX) continue;
-        const int xr = p / XW, xcol = p - xr * XW;
+        const int xr = p / ZW, xcol = p - xr * ZW;
+        if (p >= NX || xcol >= XW) continue;
         const uint32_t o = f2bf(acc[2 * h], acc[2 * h + 1]);
-        reinterpret_cast<uint32_t*>(&xd[xr * XW + xcol])[q] = o;
+        if (HAS_R) reinterpret_cast<uint32_t*>(&xd[xr * SplitCols<XW>::XP + SplitCols<XW>::col(xcol)])[q] = o;
         const int gj = j0 + xr, gi = i0 + xcol;
         if (xr < FH && xcol < FW && gj < n && gi < n)
           reinterpret_cast<uint32_t*>(xdown + ((size_t)gj * n + gi) * 8)[q] = o;
@@ -439,11 +476,13 @@ __device__ __forceinline__ void down_body(const float* __restrict__ r, const flo
     constexpr int CH = FH / 2, CW = FW / 2;
     const int nc = (n - 1) / 2;
     const int J0 = tby * CH, I0 = tbx * CW;
-    const TapOffsets<XW> tr;
+    using SC = SplitCols<XW>;
+    const SC tr;
     for (int st = warp; st < CH * CW / 16; st += NW) {
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
       const int pm = st * 16 + mrow, pl = st * 16 + lrow;
-      strip_conv_at<XW>(xd, wr, 2 * (pm / CW) * XW + 2 * (pm % CW), 2 * (pl / CW) * XW + 2 * (pl % CW), tr, acc);
+      // tap (0, 0) of coarse (cr, cc) is X pixel (2 cr, 2 cc): split column cc
+      strip_conv_taps(xd, wr, 2 * (pm / CW) * SC::XP + pm % CW, 2 * (pl / CW) * SC::XP + pl % CW, tr, acc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int p = st * 16 + g + 8 * h, cr = p / CW, cc = p - cr * CW;
@@ -487,16 +526,17 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, cons
   const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
   const uint32_t fI = identity_frag();
   const uint32_t cs0 = sa(cs), ps0 = sa(ps);
-  for (int st = warp; st < NS; st += NW) {
+  // work items: (strip of 16 quads, quad row r) -- twice as many as strips, so
+  // that the warps' shares differ by at most half a strip
+  for (int it = warp; it < 2 * NS; it += NW) {
+    const int st = it >> 1, r = it & 1;
     // A rows: quad (qr, qc) of this lane's ldmatrix row
     const int qm = min(st * 16 + mrow, NQ - 1), qr = qm / G::NQW, qc = qm - qr * G::NQW;
-    uint32_t a0[4], a1[4], ax0[4], ax1[4];
+    uint32_t a0[4], a1[4], ax[4];
     const uint32_t ca = cs0 + 16u * (qr * G::CQW + qc + kh);
     ldsm_x4(a0, ca);                                   // sources (J, I) | (J, I+1)
     ldsm_x4(a1, ca + 16u * G::CQW);                    // sources (J+1, I) | (J+1, I+1)
-    const uint32_t xa = ps0 + 16u * (2 * qr * G::QW + 2 * qc + kh);
-    ldsm_x4(ax0, xa);                                  // x_down of fine (0, 0) | (0, 1)
-    ldsm_x4(ax1, xa + 16u * G::QW);                    // x_down of fine (1, 0) | (1, 1)
+    ldsm_x4(ax, ps0 + 16u * ((2 * qr + r) * G::QW + 2 * qc + kh));   // x_down of fine (r, 0) | (r, 1)
     // this lane's two output quads (rows g and g + 8 of the strip)
     int pe[2], po[2];
     bool ok[2];
@@ -510,12 +550,15 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, cons
       po[h] = (2 * er - G::QOFF - 1 + 2) * 65536 + (2 * ec - G::QOFF - 1 + 2);
     }
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int r = t >> 1, c = t & 1;
+    for (int c = 0; c < 2; ++c) {
+      // B fragments of fine pixel t = 2 r + c (selected, so that fq stays in registers)
+      uint32_t b[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) b[k] = r ? fq[8 + 4 * c + k] : fq[4 * c + k];
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      mma16816(acc, a0, fq[4 * t + 0], fq[4 * t + 1]);
-      mma16816(acc, a1, fq[4 * t + 2], fq[4 * t + 3]);
-      mma16816(acc, r ? ax1 : ax0, c ? 0u : fI, c ? fI : 0u);
+      mma16816(acc, a0, b[0], b[1]);
+      mma16816(acc, a1, b[2], b[3]);
+      mma16816(acc, ax, c ? 0u : fI, c ? fI : 0u);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (!ok[h]) continue;
@@ -547,8 +590,8 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, cons
 template <int FH, int FW, bool LAST, bool HAS_P, bool RES>
 __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtensorMap& map_s, const CUtensorMap& map_c,
                                         const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
-                                        const uint32_t* __restrict__ fOutHi, const uint32_t* __restrict__ fOutLo,
-                                        const float* __restrict__ alpha2, const double* __restrict__ u_in,
+                                        const uint32_t* __restrict__ fOutTaps, const float* __restrict__ alpha2,
+                                        const double* __restrict__ u_in,
                                         bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
                                         const int* __restrict__ active, int* __restrict__ err, const ResidOut& ro,
                                         int out_lo, int tbx, int tby, int tbz) {
@@ -558,11 +601,12 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
   // TMA destinations (zero outside the grid): ps = x_down on Q, then x_pre;
   // zs = s on Q, then s * x_pre; cs = the quads' coarse pixels
   // finest level: pl = the low BF16 part of x_pre on O, then (in place) that of
-  // the layer output; the layer output's high part replaces x_pre's in ps
+  // the layer output; the layer output's high part replaces x_pre's in ps;
+  // then W_out's per-tap planes in zs and cs (contiguous)
   uint4* ps = reinterpret_cast<uint4*>(fused_dsm);
-  uint4* zs = ps + pad8(G::QH * QW);
-  uint4* pl = zs + pad8(G::QH * QW);                                   // finest level only
-  uint4* cs = pl + (LAST ? pad8(OH * OW) : 0);                         // coarser level only
+  uint4* pl = ps + pad8(G::QH * QW);                                   // finest level only
+  uint4* zs = pl + (LAST ? pad8(OH * OW) : 0);
+  uint4* cs = zs + pad8(G::QH * QW);                                   // coarser level only
   __shared__ __align__(8) uint64_t bar;
   const int j0 = tby * FH, i0 = tbx * FW;
   const int qj0 = j0 - H - 1 - QOFF, qi0 = i0 - H - 1 - QOFF;         // Q's corner (odd when HAS_P)
@@ -611,7 +655,8 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
 
   // layer on O: strips of 16 pixels of O in row-major order (a strip may wrap
   // to the next row); O pixel (orow, ocol) reads the taps around Q pixel
-  // (orow + QOFF + 1, ocol + QOFF + 1)
+  // (orow + QOFF + 1, ocol + QOFF + 1).  (Strips at the Q tile's pitch, free of
+  // the wrap's bank conflicts, cost more in the extra pixels than they save.)
   const int g = lane >> 2, q = lane & 3;
   {
     constexpr int NO = OH * OW, NSTRIP = (NO + 15) / 16;
@@ -649,18 +694,19 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
     }
   }
   if constexpr (LAST) {
-    // W_out on the tensor cores: an 8 -> 8 channel layer whose only nonzero
-    // output channel is 0, with the FP32 weights and the layer output each split
-    // as hi + lo BF16 -- hi(w) hi(y) + lo(w) hi(y) + hi(w) lo(y), accumulated in
-    // FP32 (about 16 bits on each side); strips of 16 pixels of E in row-major
-    // order.  E pixel (er, ec) reads the taps around O pixel (er + 1, ec + 1),
-    // i.e. Q pixel (er + QOFF + 2, ec + QOFF + 2) of ps.
-    uint32_t wh[9], wl[9];
+    // W_out (Eq. reCh-out: 8 channels -> 1) tap by tap.  Every O pixel's layer
+    // output y (hi + lo BF16 in ps and pl) meets the tap weights once, in one
+    // K = 16 MMA per 16 pixels: D_t(o) = sum_ch (hi + lo)(y(o))[ch] w_t[ch]
+    // (w split as hi + lo BF16 too: the products hi(w) hi(y) + hi(w) lo(y) +
+    // lo(w) hi(y), about 16 bits on each side, summed in FP32), written to
+    // per-tap planes in shared memory; then e(E pixel) = sum over taps t = 0..8
+    // of D_t at the pixel's tap t, in that order, in FP32.  E pixel (er, ec)
+    // is O pixel (er + 1, ec + 1); tap (a, b) reads O pixel (er + a, ec + b).
+    // The planes take PASS taps at a time (PASS = 6 where zs and cs hold six
+    // planes, else 3), in consecutive passes.
+    uint32_t bt[kOutTapRegs];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      wh[k] = fOutHi[k * 32 + lane];
-      wl[k] = out_lo ? fOutLo[k * 32 + lane] : 0u;
-    }
+    for (int k = 0; k < kOutTapRegs; ++k) bt[k] = fOutTaps[k * 32 + lane];
     // this thread's u values of the update below, loaded now so that their
     // latency passes during W_out (zero outside the grid)
     constexpr int NE = EH * EW, NU = (NE + NT - 1) / NT;
@@ -671,40 +717,62 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
       const int gj = j0 - HE + er, gi = i0 - HE + ec;
       uv[k] = (u_in && e < NE && gj >= 0 && gj < n && gi >= 0 && gi < n) ? u_in[(size_t)gj * n + gi] : 0.0;
     }
-    __syncthreads();
-    const float inv_alpha = alpha2[2 * bz + 1];
-    float* ev = reinterpret_cast<float*>(zs);                                  // e on E
-    double* un = reinterpret_cast<double*>(zs) + (NE + 1) / 2;                  // u + e on E
-    const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8, lrow = lane & 15;
-    const TapOffsets<OW> to;
-    const TapOffsets<QW> tq;
-    for (int st = warp; st < (NE + 15) / 16; st += NW) {
-      const int pm = min(st * 16 + mrow, NE - 1), pn = min(st * 16 + lrow, NE - 1);
-      const int rm = pm / EW, rl = pn / EW, cm = pm - rm * EW, cl = pn - rl * EW;
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      const int bm = (rm + QOFF + 1) * QW + cm + QOFF + 1, bl = (rl + QOFF + 1) * QW + cl + QOFF + 1;
-      strip_conv_at<QW>(ps, wh, bm, bl, tq, acc);
-      if (out_lo) strip_conv_at<QW>(ps, wl, bm, bl, tq, acc);   // a zero lo part adds exactly nothing
-      strip_conv_at<OW>(pl, wh, rm * OW + cm, rl * OW + cl, to, acc);
-      // output channel 0 sits in the q == 0 lanes: stage it in shared memory
-      // (the Q tiles are free now) so that the FP64 update below runs on
-      // full warps -- an FP64 instruction costs the same with 8 lanes or 32
-      if (q == 0) {
+    constexpr int NO = OH * OW, NSO = (NO + 15) / 16;
+    constexpr int PL = (NO + 27) / 32 * 32 + 4;    // plane pitch (floats), 4 (mod 32): conflict-free stores
+    constexpr int FREE = 16 * (pad8(G::QH * QW) + (HAS_P ? pad8(G::CQH * G::CQW) : 0));
+    constexpr int PASS = 6 * PL * 4 <= FREE ? 6 : 3;
+    static_assert(PASS * PL * 4 <= FREE, "W_out planes in the z and coarse tiles");
+    float* dpl = reinterpret_cast<float*>(zs);
+    float esum[NU];
+#pragma unroll
+    for (int k = 0; k < NU; ++k) esum[k] = 0.f;
+    __syncthreads();   // the layer's y is complete; z and the coarse tile are free
+#pragma unroll
+    for (int t0 = 0; t0 < 9; t0 += PASS) {
+      // B tile of this pass: taps 6 b .. 6 b + 5 in columns n = tap - 6 b
+      const int b = t0 / 6, base = 6 * b;
+      for (int st = warp; st < NSO; st += NW) {
+        // A rows: 16 O pixels; lanes 0-15 address hi(y) in ps, 16-31 lo(y) in pl
+        const int pr = min(st * 16 + (lane & 15), NO - 1), orr = pr / OW, oc = pr - orr * OW;
+        uint32_t a[4];
+        ldsm_x4(a, lane < 16 ? sa(ps) + 16u * ((orr + QOFF + 1) * QW + oc + QOFF + 1) : sa(pl) + 16u * pr);
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma16816(d, a, bt[4 * b + 0], bt[4 * b + 1]);
+        if (out_lo) mma16816(d, a, bt[4 * b + 2], bt[4 * b + 3]);   // a zero lo part adds exactly nothing
+        // lane (g, q): taps base + 2q, base + 2q + 1 of pixels g and g + 8 of the strip
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int p = st * 16 + g + 8 * h;
-          if (p < NE) ev[p] = acc[2 * h] * inv_alpha;
+          if (p >= NO) continue;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const int tp = base + 2 * q + j - t0;   // plane of this tap in the pass
+            if (tp >= 0 && tp < PASS && t0 + tp < 9) dpl[tp * PL + p] = d[2 * h + j];
+          }
         }
       }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < NU; ++k) {
+        const int e = threadIdx.x + k * NT, er = e / EW, ec = e - er * EW;
+        if (e >= NE) continue;
+#pragma unroll
+        for (int tp = 0; tp < PASS && t0 + tp < 9; ++tp) {
+          const int t = t0 + tp;
+          esum[k] += dpl[tp * PL + (er + t / 3) * OW + ec + t % 3];
+        }
+      }
+      __syncthreads();   // the next pass (or the u + e staging) overwrites the planes
     }
-    __syncthreads();
+    const float inv_alpha = alpha2[2 * bz + 1];
+    double* un = reinterpret_cast<double*>(zs);    // u + e on E (residual in this kernel)
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
       const int e = threadIdx.x + k * NT, er = e / EW, ec = e - er * EW;
       const int gj = j0 - HE + er, gi = i0 - HE + ec;
       if (e >= NE) continue;
       const bool in = gj >= 0 && gj < n && gi >= 0 && gi < n;
-      const double un_e = in ? uv[k] + f32_to_f64_exact(ev[e]) : 0.0;
+      const double un_e = in ? uv[k] + f32_to_f64_exact(esum[k] * inv_alpha) : 0.0;
       if (RES) un[e] = un_e;
       if (in && er >= HE && er < HE + FH && ec >= HE && ec < HE + FW) u_out[(size_t)gj * n + gi] = un_e;
     }
@@ -747,13 +815,12 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
                                                 const __grid_constant__ CUtensorMap map_s,
                                                 const __grid_constant__ CUtensorMap map_c,
                                                 const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
-                                                const uint32_t* __restrict__ fOutHi,
-                                                const uint32_t* __restrict__ fOutLo,
+                                                const uint32_t* __restrict__ fOutTaps,
                                                 const float* __restrict__ alpha2, const double* __restrict__ u_in,
                                                 bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
                                                 const int* __restrict__ active, int* __restrict__ err,
                                                 const __grid_constant__ ResidOut ro, int out_lo) {
-  up_body<FH, FW, LAST, HAS_P, RES>(map_xd, map_s, map_c, fK, fTc, fOutHi, fOutLo, alpha2, u_in, xfin, u_out, n,
+  up_body<FH, FW, LAST, HAS_P, RES>(map_xd, map_s, map_c, fK, fTc, fOutTaps, alpha2, u_in, xfin, u_out, n,
                                     active, err, ro, out_lo, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -844,12 +911,11 @@ __global__ void __launch_bounds__(NT, 4) tail_kernel(const __grid_constant__ Tai
       const int bz = t / per, tl = t - bz * per, ty = tl / L.tx, tx = tl - ty * L.tx;
       if (k + 1 < ta.nl)
         up_body<kTailFH, kTailFW, false, true, false>(L.ux, L.us, L.uc, ta.f_up, ta.f_tcnn, nullptr, nullptr, nullptr,
-                                                      nullptr, L.xb, nullptr, L.n, ta.active, ta.err, no_ro, 0, tx, ty,
-                                                      bz);
+                                                      L.xb, nullptr, L.n, ta.active, ta.err, no_ro, 0, tx, ty, bz);
       else
         up_body<kTailFH, kTailFW, false, false, false>(L.ux, L.us, L.us, ta.f_up, ta.f_tcnn, nullptr, nullptr,
-                                                       nullptr, nullptr, L.xb, nullptr, L.n, ta.active, ta.err, no_ro,
-                                                       0, tx, ty, bz);
+                                                       nullptr, L.xb, nullptr, L.n, ta.active, ta.err, no_ro, 0, tx,
+                                                       ty, bz);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
     }
@@ -975,7 +1041,7 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
     else
       mc = ms;   // not read on the coarsest level
     const cudaError_t le = launch_level(kernel, grid, dyn_smem(kernel, smem), st, fl.pdl, mxd, ms, mc, w.f_up,
-                                        w.f_tcnn, w.f_out_hi, w.f_out_lo, (const float*)fl.alpha, u_skip, xfin, e, nl,
+                                        w.f_tcnn, w.f_out_taps, (const float*)fl.alpha, u_skip, xfin, e, nl,
                                         active, fl.err, rout, w.out_lo);
     if (le != cudaSuccess) return cuda_status(le, "up_kernel launch");
     return {};
@@ -1109,8 +1175,8 @@ Status launch_tail(const FusedLevels& fl, int lt, const FusedWeights& w, const i
   return {};
 }
 
-constexpr int kTileH[kFusedVariants] = {16, 8, 16, 32, 24};
-constexpr int kTileW[kFusedVariants] = {32, 32, 16, 32, 32};
+constexpr int kTileH[kUpVariants] = {16, 8, 16, 32, 24, 24, 32};
+constexpr int kTileW[kUpVariants] = {32, 32, 16, 32, 32, 30, 30};
 
 Status launch_down_variant(int v, int l, const FusedLevels& fl, const float* r32, const double* norm2,
                            const FusedWeights& w, const int* active, cudaStream_t st, const ResidIn* ra = nullptr) {
@@ -1130,6 +1196,10 @@ Status launch_up_variant(int v, int l, const FusedLevels& fl, const double* norm
     case 2: return launch_up<16, 16>(l, fl, norm2, e, u_skip, w, active, st, ro);
     case 3: return launch_up<32, 32>(l, fl, norm2, e, u_skip, w, active, st, ro);
     case 4: return launch_up<24, 32>(l, fl, norm2, e, u_skip, w, active, st, ro);
+    // up kernel only (the restriction needs (FH / 2) (FW / 2) a multiple of 16):
+    // on the finest level the layer output is 32 pixels wide, whole strips of 16
+    case 5: return launch_up<24, 30>(l, fl, norm2, e, u_skip, w, active, st, ro);
+    case 6: return launch_up<32, 30>(l, fl, norm2, e, u_skip, w, active, st, ro);
     default: return launch_up<16, 32>(l, fl, norm2, e, u_skip, w, active, st, ro);
   }
 }
@@ -1184,7 +1254,7 @@ int fused_down0_blocks(int n, int variant) {
 
 size_t fused_partials_max(int n) {
   size_t m = 0;
-  for (int v = 0; v < kFusedVariants; ++v) m = std::max(m, (size_t)fused_down0_blocks(n, v));
+  for (int v = 0; v < kUpVariants; ++v) m = std::max(m, (size_t)fused_down0_blocks(n, v));
   return m;
 }
 
@@ -1207,16 +1277,19 @@ Status fused_autotune(FusedLevels& fl, const float* r32, const double* norm2, do
     // two timed rounds per variant, keeping the faster one: a single short
     // round is easily disturbed (clock ramp, other work on the GPU)
     for (int round = 0; round < 2 && result.ok(); ++round)
-      for (int v = 0; v < kFusedVariants && result.ok(); ++v) {
+      for (int v = 0; v < kUpVariants && result.ok(); ++v) {
         float t = 0.f;
-        result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st, rl);
-        if (!result.ok()) break;
-        cudaEventRecord(e0, st);
-        for (int k = 0; k < reps && result.ok(); ++k) result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st, rl);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        cudaEventElapsedTime(&t, e0, e1);
-        if (t < best_d) { best_d = t; fl.var_down[l] = v; }
+        if (v < kFusedVariants) {
+          result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st, rl);
+          if (!result.ok()) break;
+          cudaEventRecord(e0, st);
+          for (int k = 0; k < reps && result.ok(); ++k)
+            result = launch_down_variant(v, l, fl, r32, norm2, w, nullptr, st, rl);
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&t, e0, e1);
+          if (t < best_d) { best_d = t; fl.var_down[l] = v; }
+        }
         result = launch_up_variant(v, l, fl, norm2, scratch, nullptr, w, nullptr, st, rol);
         if (!result.ok()) break;
         cudaEventRecord(e0, st);
