@@ -462,7 +462,7 @@ __device__ __forceinline__ void down_body(const float* __restrict__ r, const flo
         const int xr = p / ZW, xcol = p - xr * ZW;
         if (p >= NX || xcol >= XW) continue;
         const uint32_t o = f2bf(acc[2 * h], acc[2 * h + 1]);
-        if (HAS_R) reinterpret_cast<uint32_t*>(&xd[xr * SplitCols<XW>::XP + SplitCols<XW>::col(xcol)])[q] = o;
+        if constexpr (HAS_R) reinterpret_cast<uint32_t*>(&xd[xr * SplitCols<XW>::XP + SplitCols<XW>::col(xcol)])[q] = o;
         const int gj = j0 + xr, gi = i0 + xcol;
         if (xr < FH && xcol < FW && gj < n && gi < n)
           reinterpret_cast<uint32_t*>(xdown + ((size_t)gj * n + gi) * 8)[q] = o;
