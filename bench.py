@@ -178,9 +178,10 @@ def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
 KERNEL_SOURCE = {"residual_kernel": "operator.cu", "down_kernel": "mixed_fused.cu", "up_kernel": "mixed_fused.cu"}
 
 
-def traffic_record(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current source of that kernel (source hash recorded beside the number)."""
+def _profile_fields(kernel: str, workload: str):
+    """The fields recorded for (kernel, workload) in the committed ncu summary, if
+    it was taken on the current source of that kernel (source hash recorded beside
+    the numbers)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path) or kernel not in KERNEL_SOURCE:
         return None
@@ -189,8 +190,24 @@ def traffic_record(kernel: str, workload: str):
     for ln in open(path):
         parts = ln.split()
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[2] == h:
-            return float(parts[3])
+            return parts[3:]
     return None
+
+
+def traffic_record(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary (current source only)."""
+    f = _profile_fields(kernel, workload)
+    return float(f[0]) if f else None
+
+
+def sm_pipes_record(kernel: str, workload: str):
+    """The SM-side limits of the same capture: busy fraction of the shared-memory
+    data pipe and the fraction of cycles with an instruction issued."""
+    f = _profile_fields(kernel, workload)
+    if not f or len(f) < 3:
+        return None
+    return {"shared_memory_data_pipe_busy": float(f[1]), "issue_active": float(f[2]),
+            "source": f"ncu --set full capture, profiles/{kernel}_{workload}.md"}
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -510,6 +527,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "traffic": traffic_record(kname, f"{workload}_{n}"),
+                "sm_pipes": sm_pipes_record(kname, f"{workload}_{n}"),
                 "algorithmic_bytes_per_launch": algorithmic_bytes(dom, n, cp),
                 "avg_launch_ms": dom_ms / dom_cnt if dom_cnt else None,
                 "timing": "CUDA events around each finest-level launch, second timed pass of the same steps "
