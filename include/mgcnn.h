@@ -125,7 +125,8 @@ int mgcnn_create(const mgcnn_config* cfg, mgcnn_ctx** out);
 void mgcnn_destroy(mgcnn_ctx* ctx);
 
 /* Bind the context to a CUDA stream (cudaStream_t passed as void*; NULL is
- * the legacy default stream).  All later work is issued on it. */
+ * the legacy default stream).  All later work is issued on it; work still
+ * running on the previous stream (a setup's kernels) is waited for first. */
 int mgcnn_set_stream(mgcnn_ctx* ctx, void* stream);
 
 /* Load the weight blob (layout of mgcnn_weight_count; count must equal it).
@@ -138,7 +139,12 @@ int mgcnn_set_weights(mgcnn_ctx* ctx, const double* w, size_t count);
  * level (Sec. 2.3: rediscretised coarse operators), runs the setup network
  * on all levels and keeps the setup tensors on the device.
  * Errors: ARG, SIZE, STATE (weights not set), NOMEM, NONFINITE (k <= 0 or
- * non-finite), CUDA. */
+ * non-finite), CUDA.
+ * Synchronisation: the call returns once coeff has been copied and checked; the
+ * setup kernels run on the context's stream after it returns (every later call
+ * on the context is ordered after them, and mgcnn_solve's copies of host inputs
+ * overlap them); an error they meet is reported by the next call that
+ * synchronises. */
 int mgcnn_setup(mgcnn_ctx* ctx, const double* coeff, int n);
 
 /* Setup for the 13-channel network whose solve phase is exactly classical
@@ -165,7 +171,7 @@ int mgcnn_setup(mgcnn_ctx* ctx, const double* coeff, int n);
  *   s[T_o](q) = -omega a_o(q-o), s[F_G] = (1 - omega) a_C, s[F_J] = omega.
  * Its weights come from the binding's gmg_v10_weights().
  * Errors: SIZE (any other channels / layer counts), ARG (omega not in (0,2)),
- * as mgcnn_setup. */
+ * as mgcnn_setup.  Synchronisation as mgcnn_setup. */
 int mgcnn_setup_gmg(mgcnn_ctx* ctx, const double* coeff, int n, double omega);
 
 /* Number of doubles of all setup tensors of the current setup:

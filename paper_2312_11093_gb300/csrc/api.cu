@@ -139,6 +139,38 @@ Status stage_out(const double* dst, size_t count, DevBuf& stage, double** out, b
   return {};
 }
 
+// mgcnn_solve's inputs from host memory go on the context's copy stream, so
+// that they can overlap the setup kernels that mgcnn_setup / mgcnn_setup_gmg
+// leave running on the context's stream (those touch neither c->f nor c->u,
+// and every other call synchronises before it returns); join_copies orders the
+// stream after them.
+Status copy_stream(mgcnn_ctx* c) {
+  if (!c->cstream) MG_CUDA(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+  if (!c->cevent) MG_CUDA(cudaEventCreateWithFlags(&c->cevent, cudaEventDisableTiming));
+  return {};
+}
+
+Status stage_in_overlapped(mgcnn_ctx* c, const double* src, size_t count, DevBuf& stage, const double** out,
+                           bool* copied) {
+  if (is_device_pointer(src)) {
+    *out = src;
+    return {};
+  }
+  MG_TRY(ensure(stage, count * sizeof(double)));
+  MG_TRY(copy_stream(c));
+  MG_CUDA(cudaMemcpyAsync(stage.p, src, count * sizeof(double), cudaMemcpyHostToDevice, c->cstream));
+  *out = stage.as<double>();
+  *copied = true;
+  return {};
+}
+
+Status join_copies(mgcnn_ctx* c, bool copied) {
+  if (!copied) return {};
+  MG_CUDA(cudaEventRecord(c->cevent, c->cstream));
+  MG_CUDA(cudaStreamWaitEvent(c->stream, c->cevent, 0));
+  return {};
+}
+
 Status stage_out_finish(mgcnn_ctx* c, double* dst, const double* dev, size_t count, bool host) {
   if (host) MG_CUDA(cudaMemcpyAsync(dst, dev, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return {};
@@ -426,7 +458,10 @@ Status do_setup(mgcnn_ctx* c, const double* coeff, int n) {
   } else {
     MG_TRY(setup_mixed(c));
   }
-  MG_TRY(sync(c));
+  // no synchronisation: the setup kernels run on after the call returns (the
+  // solve's input copies overlap them); a kernel error surfaces at the next
+  // synchronising call
+  MG_CUDA(cudaGetLastError());
   c->have_setup = true;
   return {};
 }
@@ -494,7 +529,8 @@ int mgcnn_create(const mgcnn_config* cfg, mgcnn_ctx** out) {
 
 void mgcnn_destroy(mgcnn_ctx* c) {
   if (!c) return;
-  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream);
+  if (c->cstream) cudaStreamSynchronize(c->cstream);
   release(c->w64); release(c->w32);
   for (int l = 0; l < kMaxLevels; ++l) {
     release(c->coef[l]); release(c->op[l]); release(c->s64[l]); release(c->s16[l]);
@@ -516,6 +552,8 @@ void mgcnn_destroy(mgcnn_ctx* c) {
     cudaEventDestroy(c->ev_start[i]);
     cudaEventDestroy(c->ev_stop[i]);
   }
+  if (c->cevent) cudaEventDestroy(c->cevent);
+  if (c->cstream) cudaStreamDestroy(c->cstream);
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   release(c->kerr);
   for (DevBuf* b : {&c->kV, &c->kZ, &c->kw, &c->kr, &c->kcoef, &c->kpart}) release(*b);
@@ -526,8 +564,9 @@ void mgcnn_destroy(mgcnn_ctx* c) {
 
 int mgcnn_set_stream(mgcnn_ctx* c, void* stream) {
   if (!c) return MGCNN_ERR_ARG;
+  Status st = sync(c);   // work a setup left on the old stream
   c->stream = static_cast<cudaStream_t>(stream);
-  return finish(c, {});
+  return finish(c, st);
 }
 
 int mgcnn_set_weights(mgcnn_ctx* c, const double* w, size_t count) {
@@ -563,7 +602,8 @@ int mgcnn_setup_gmg(mgcnn_ctx* c, const double* coeff, int n, double omega) {
       else
         MG_TRY(mixed_gmg_setup_level(c, l, omega));
     }
-    MG_TRY(sync(c));
+    // no synchronisation, as in do_setup
+    MG_CUDA(cudaGetLastError());
     c->have_setup = true;
     return {};
   }();
@@ -760,11 +800,17 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
     MG_TRY(require_setup(c));
     const size_t N = c->lv[0].N();
     const double* df = nullptr;
-    MG_TRY(stage_in(c, f, N, c->f, &df));
+    bool copied = false;
+    MG_TRY(stage_in_overlapped(c, f, N, c->f, &df, &copied));
     double* du = nullptr;
     bool host = false;
     MG_TRY(stage_out(u, N, c->u, &du, &host));
-    if (host) MG_CUDA(cudaMemcpyAsync(du, u, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (host) {
+      MG_TRY(copy_stream(c));
+      MG_CUDA(cudaMemcpyAsync(du, u, N * sizeof(double), cudaMemcpyHostToDevice, c->cstream));
+      copied = true;
+    }
+    MG_TRY(join_copies(c, copied));
     MG_TRY(sumsq(c, df, N, 1));
     double fn2 = 0.0;
     MG_TRY(read_scalar(c, 1, &fn2));

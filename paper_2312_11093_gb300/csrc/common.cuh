@@ -150,6 +150,8 @@ struct mgcnn_ctx {
   cudaGraphExec_t sgraph = nullptr;
   long long sgraph_kernels = 0;
   cudaStream_t gstream = nullptr;
+  cudaStream_t cstream = nullptr;         // host-to-device copies of mgcnn_solve's inputs, overlapping the
+  cudaEvent_t cevent = nullptr;           // setup kernels still running on `stream`; joined by this event
   mgcnn::DevBuf gstate, ghist, gparams;
   // classical GMG comparator (gmg.cu): per-level rhs, correction, ping-pong
   mgcnn::DevBuf gmg_r[mgcnn::kMaxLevels], gmg_e[mgcnn::kMaxLevels], gmg_t[mgcnn::kMaxLevels];
