@@ -348,9 +348,9 @@ def main():
     ap.add_argument("--workload", default=None, choices=["channelised", "grf", "batched256"])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--maxit", type=int, default=100, help="cycle limit of the batched solves")
-    ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
+    ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6, 7],
                     help="tile shape of the fused kernels: -1 autotuned, 0 16x32, 1 8x32, 2 16x16, 3 32x32, 4 24x32, "
-                         "5 24x30 (up) + 24x32 (down), 6 32x30 (up) + 24x32 (down)")
+                         "5 24x30 (up) + 24x32 (down), 6 32x30 (up) + 24x32 (down), 7 22x30 (up) + 24x32 (down)")
     ap.add_argument("--coarse-tail", type=int, default=-1,
                     help="largest grid side of the coarse levels run as one cooperative kernel "
                          "(0: a launch per level; -1: the library default)")
@@ -544,7 +544,7 @@ def main():
               "config": {"workload": f"{workload}_{n}", "n": n, "tol": tol, "net": net, "channels": C,
                          "down_layers": nd, "up_layers": nu, "b": list(b), "l2": "inputs larger than L2",
                          "tile": "autotuned" if args.tile < 0 else ["16x32", "8x32", "16x16", "32x32", "24x32", "24x30 up, 24x32 down",
-                                                      "32x30 up, 24x32 down"][args.tile],
+                                                      "32x30 up, 24x32 down", "22x30 up, 24x32 down"][args.tile],
                          "parallelism": "replicas" if world > 1 else "single"},
               "iters": iters, "relres": relres_mixed, "solve_only_ms": solve_only_ms,
               "e2e": {"value": world * 1e3 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": h2d,

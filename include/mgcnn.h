@@ -366,10 +366,11 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * (one 8-byte readback per cycle).  Both give identical iterates.
  * MGCNN_OPT_TILE (default -1): tile shape of the fused kernels.  -1: the first
  * solve after a setup on a new grid size times every shape on every level and
- * keeps the fastest; 0..6: that shape on every level, no timing (0 = 16 x 32,
+ * keeps the fastest; 0..7: that shape on every level, no timing (0 = 16 x 32,
  * 1 = 8 x 32, 2 = 16 x 16, 3 = 32 x 32, 4 = 24 x 32 fine pixels per block,
- * rows x columns; 5 = 24 x 30 and 6 = 32 x 30 for the up kernels with 24 x 32
- * for the down kernels, whose restriction needs other widths); other values:
+ * rows x columns; 5 = 24 x 30, 6 = 32 x 30 and 7 = 22 x 30 for the up kernels
+ * with 24 x 32 for the down kernels, whose restriction needs other widths);
+ * other values:
  * ERR_ARG.  Every shape gives bit-identical results: a pixel's arithmetic does
  * not depend on the tile that holds it.  Applies to mgcnn_solve and
  * mgcnn_solve_krylov; the batched solves keep their own timing.

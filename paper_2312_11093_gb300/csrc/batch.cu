@@ -205,6 +205,7 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, doub
     MG_TRY(ensure(k.s16[l], B * N * 8 * sizeof(bf16)));
     MG_TRY(ensure(k.xa[l], B * N * 8 * sizeof(bf16)));
     MG_TRY(ensure(k.xb[l], B * N * 8 * sizeof(bf16)));
+    if (l > 0) MG_TRY(ensure(k.xl[l], B * N * 8 * sizeof(bf16)));
   }
   MG_TRY(ensure(k.dinv32, B * N0 * sizeof(float)));
   MG_TRY(ensure(k.r32, B * r32_floats(k.n) * sizeof(float)));
@@ -268,6 +269,7 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, doub
     k.fl.s[l] = k.s16[l].as<bf16>();
     k.fl.xa[l] = k.xa[l].as<bf16>();
     k.fl.xb[l] = k.xb[l].as<bf16>();
+    k.fl.xbl[l] = k.xl[l].as<bf16>();
   }
   // tile shapes: reuse the choice made for an earlier class of the same size and
   // batch (the timing depends only on the shapes), else time the variants
@@ -421,7 +423,7 @@ void batch_release(mgcnn_ctx* c) {
   for (BatchClass& k : c->bcls) {
     release(k.coef);
     for (int l = 0; l < kMaxLevels; ++l) {
-      release(k.op[l]); release(k.s16[l]); release(k.xa[l]); release(k.xb[l]);
+      release(k.op[l]); release(k.s16[l]); release(k.xa[l]); release(k.xb[l]); release(k.xl[l]);
     }
     for (DevBuf* b : {&k.dinv32, &k.r32, &k.f, &k.u, &k.partial, &k.rn2, &k.alpha, &k.fn2, &k.state, &k.hist, &k.feat,
                       &k.ca, &k.cb, &k.za, &k.zb, &k.s32, &k.scratch})

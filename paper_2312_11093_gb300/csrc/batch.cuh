@@ -14,6 +14,7 @@ struct BatchClass {
   DevBuf coef;                                 // [2][B][(n+2)^2] nodal k, level ping-pong
   DevBuf op[kMaxLevels];                       // [B][5][N_l] FP64 operators
   DevBuf s16[kMaxLevels], xa[kMaxLevels], xb[kMaxLevels];  // [B][N_l][8] BF16
+  DevBuf xl[kMaxLevels];                                     // low part of the up sweep's output (l >= 1)
   DevBuf dinv32, r32;                          // [B][N] FP32
   DevBuf f, u;                                 // [B][N] FP64
   DevBuf partial;                              // [B][blocks]

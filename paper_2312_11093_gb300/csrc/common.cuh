@@ -131,6 +131,7 @@ struct mgcnn_ctx {
   std::vector<TunedClass> tuned_classes;
   mgcnn::DevBuf x16a[mgcnn::kMaxLevels];  // BF16 state ping-pong, [n_l^2][cp]
   mgcnn::DevBuf x16b[mgcnn::kMaxLevels];
+  mgcnn::DevBuf x16l[mgcnn::kMaxLevels];  // low BF16 part of the up sweep's output, levels >= 1
   mgcnn::DevBuf wmix;                     // packed weights: mma fragments + FP32 small layers
   mgcnn::TmaMaps* tma = nullptr;          // tensor maps of the fused kernels' TMA tile loads
   mgcnn::DevBuf kerr;                     // device flag: a kernel gave up waiting for its tile copies

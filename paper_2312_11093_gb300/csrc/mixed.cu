@@ -608,6 +608,7 @@ Status setup_mixed(mgcnn_ctx* c) {
       MG_TRY(ensure(c->s16[l], N * cp * sizeof(bf16)));
       MG_TRY(ensure(c->x16a[l], N * cp * sizeof(bf16)));
       MG_TRY(ensure(c->x16b[l], N * cp * sizeof(bf16)));
+      if (l > 0) MG_TRY(ensure(c->x16l[l], N * cp * sizeof(bf16)));
       ops[l] = c->op[l].as<double>();
       ss[l] = c->s16[l].as<bf16>();
       cs[l] = c->x16b[l].as<bf16>();
@@ -628,6 +629,7 @@ Status setup_mixed(mgcnn_ctx* c) {
     MG_TRY(ensure(c->s16[l], c->lv[l].N() * cp * sizeof(bf16)));
     MG_TRY(ensure(c->x16a[l], c->lv[l].N() * cp * sizeof(bf16)));
     MG_TRY(ensure(c->x16b[l], c->lv[l].N() * cp * sizeof(bf16)));
+    if (l > 0) MG_TRY(ensure(c->x16l[l], c->lv[l].N() * cp * sizeof(bf16)));
   }
   MG_TRY(ensure(c->r32, r32_floats(c->lv[0].n) * sizeof(float)));
   MG_TRY(run_setup_net_fp32(c, outs));
@@ -651,6 +653,7 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega) {
   MG_TRY(ensure(c->s16[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->x16a[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->x16b[l], N * cp * sizeof(bf16)));
+  if (l > 0) MG_TRY(ensure(c->x16l[l], N * cp * sizeof(bf16)));
   MG_TRY(ensure(c->r32, r32_floats(c->lv[0].n) * sizeof(float)));
   const int C = c->cfg.channels;
   if (C == kGmgV10Channels)   // straight into the BF16 layout
@@ -701,6 +704,7 @@ void mixed_release(mgcnn_ctx* c) {
   for (int l = 0; l < kMaxLevels; ++l) {
     release(c->x16a[l]);
     release(c->x16b[l]);
+    release(c->x16l[l]);
   }
   release(c->wmix);
   release(c->s32tmp);

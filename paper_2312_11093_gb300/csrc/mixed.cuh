@@ -21,7 +21,8 @@ Status mixed_gmg_setup_level(mgcnn_ctx* c, int l, double omega);
 void mixed_release(mgcnn_ctx* c);
 // mixed_fused.cu: fused level kernels (8 channels, one layer per ResNet)
 constexpr int kFusedVariants = 5;        // tile shapes 16x32, 8x32, 16x16, 32x32, 24x32
-constexpr int kUpVariants = 7;           // the up kernel also: 24x30, 32x30 (finest level: rows of 32 layer outputs)
+constexpr int kUpVariants = 8;           // the up kernel also: 24x30, 32x30, 22x30 (finest level: rows of 32 layer
+                                         // outputs; 22x30 keeps four blocks per SM with both coarse tiles)
 constexpr int kTcnnQuadRegs = 16;        // TCNN B fragments per lane: 4 fine pixels x 2 k steps x 2
 constexpr int kOutTapRegs = 8;           // W_out B fragments per lane: 2 tap tiles x (hi, lo) x 2 k halves
 class TmaMaps;
@@ -58,6 +59,7 @@ struct FusedLevels {
   const __nv_bfloat16* s[kMaxLevels] = {};
   __nv_bfloat16* xa[kMaxLevels] = {};
   __nv_bfloat16* xb[kMaxLevels] = {};
+  __nv_bfloat16* xbl[kMaxLevels] = {};   // low BF16 part of the up sweep's x_fin (levels >= 1)
 };
 struct FusedWeights {
   const uint32_t *f_down, *f_up, *f_R;   // mma B fragments (device)

@@ -188,11 +188,11 @@ struct UpGeom {
   // finest level, after the layer: e (FP32) on E, then u + e (FP64) on E, in the z tile
   static_assert(!LAST || EH * EW * (4 + 8) + 8 <= 16 * QH * QW, "E staging in the z tile");
 };
-// Tiles: ps, zs on Q; on the finest level pl on O; cs.
+// Tiles: ps, zs on Q; pl on O; the coarse tiles cs (hi) and cl (lo).
 template <int FH, int FW, bool LAST, bool HAS_P, bool RES = false>
 constexpr size_t up_smem_bytes() {
   using G = UpGeom<FH, FW, LAST, HAS_P, RES>;
-  return 16u * (2 * pad8(G::QH * G::QW) + (LAST ? pad8(G::OH * G::OW) : 0) + (HAS_P ? pad8(G::CQH * G::CQW) : 0));
+  return 16u * (2 * pad8(G::QH * G::QW) + pad8(G::OH * G::OW) + (HAS_P ? 2 * pad8(G::CQH * G::CQW) : 0));
 }
 extern __shared__ __align__(128) unsigned char fused_dsm[];
 
@@ -510,32 +510,37 @@ __global__ void __launch_bounds__(NT, 4) down_kernel(const float* __restrict__ r
 }
 
 // TCNN-add on the tensor cores over the quads of Q: each 16 quads are a GEMM
-// [16 x 64] x [64 x 8] per fine pixel (r, c) of the quad, whose A row holds the
-// quad's four coarse sources (J+dJ, I+dI) (k 0-31, gathered by ldmatrix from
-// per-lane addresses) and the fine pixel's own x_down (k 32-63, through an
-// identity block: the U-net skip of Algorithm 3 added in FP32).  Every quad has
-// the same structure, so one set of B fragments serves all of them (fq, see
-// pack_tcnn_frags).  Epilogue: x_pre rounded once to BF16 into ps, z = s * x_pre
-// into zs.  Coarse pixels outside the coarse grid are staged as zeros, which
-// makes the sum zero on every fine pixel outside the fine grid.
-template <class G, bool WIDE>
-__device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, const uint4* cs, const uint32_t* fq) {
+// [16 x 96] x [96 x 8] per fine pixel (r, c) of the quad, whose A row holds the
+// quad's four coarse sources (J+dJ, I+dI) as their high BF16 parts (k 0-31) and
+// low BF16 parts (k 32-63), gathered by ldmatrix from per-lane addresses, and
+// the fine pixel's own x_down (k 64-95, through an identity block: the U-net
+// skip of Algorithm 3 added in FP32).  Every quad has the same structure, so
+// one set of B fragments serves all of them and both parts (fq, see
+// pack_tcnn_frags).  Epilogue: x_pre = hi + lo BF16 (hi into ps, lo into pl on
+// the layer-output region O, the layer adds it to its skip) and z = s * x_pre
+// from the FP32 sum into zs.  Coarse pixels outside the coarse grid are staged
+// as zeros, which makes the sum zero on every fine pixel outside the fine grid.
+// Work items: (strip of 16 quads, quad row r), so that the warps' shares differ
+// by at most half a strip.
+template <class G>
+__device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, const uint4* cs, const uint4* cl,
+                                           const uint32_t* fq) {
   constexpr int NQ = G::NQH * G::NQW, NS = (NQ + 15) / 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, q = lane & 3, kh = lane >> 4;
   const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
   const uint32_t fI = identity_frag();
-  const uint32_t cs0 = sa(cs), ps0 = sa(ps);
-  // work items: (strip of 16 quads, quad row r) -- twice as many as strips, so
-  // that the warps' shares differ by at most half a strip
+  const uint32_t cs0 = sa(cs), cl0 = sa(cl), ps0 = sa(ps);
   for (int it = warp; it < 2 * NS; it += NW) {
     const int st = it >> 1, r = it & 1;
     // A rows: quad (qr, qc) of this lane's ldmatrix row
     const int qm = min(st * 16 + mrow, NQ - 1), qr = qm / G::NQW, qc = qm - qr * G::NQW;
-    uint32_t a0[4], a1[4], ax[4];
-    const uint32_t ca = cs0 + 16u * (qr * G::CQW + qc + kh);
-    ldsm_x4(a0, ca);                                   // sources (J, I) | (J, I+1)
-    ldsm_x4(a1, ca + 16u * G::CQW);                    // sources (J+1, I) | (J+1, I+1)
+    uint32_t a0[4], a1[4], b0[4], b1[4], ax[4];
+    const uint32_t co = 16u * (qr * G::CQW + qc + kh);
+    ldsm_x4(a0, cs0 + co);                             // sources (J, I) | (J, I+1), high parts
+    ldsm_x4(a1, cs0 + co + 16u * G::CQW);              // sources (J+1, I) | (J+1, I+1)
+    ldsm_x4(b0, cl0 + co);                             // the same, low parts
+    ldsm_x4(b1, cl0 + co + 16u * G::CQW);
     ldsm_x4(ax, ps0 + 16u * ((2 * qr + r) * G::QW + 2 * qc + kh));   // x_down of fine (r, 0) | (r, 1)
     // this lane's two output quads (rows g and g + 8 of the strip)
     int pe[2], po[2];
@@ -552,12 +557,14 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, cons
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       // B fragments of fine pixel t = 2 r + c (selected, so that fq stays in registers)
-      uint32_t b[4];
+      uint32_t bw[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) b[k] = r ? fq[8 + 4 * c + k] : fq[4 * c + k];
+      for (int k = 0; k < 4; ++k) bw[k] = r ? fq[8 + 4 * c + k] : fq[4 * c + k];
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      mma16816(acc, a0, b[0], b[1]);
-      mma16816(acc, a1, b[2], b[3]);
+      mma16816(acc, a0, bw[0], bw[1]);
+      mma16816(acc, a1, bw[2], bw[3]);
+      mma16816(acc, b0, bw[0], bw[1]);
+      mma16816(acc, b1, bw[2], bw[3]);
       mma16816(acc, ax, c ? 0u : fI, c ? fI : 0u);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -566,17 +573,11 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, cons
         const uint32_t xo = f2bf(acc[2 * h], acc[2 * h + 1]);
         reinterpret_cast<uint32_t*>(&ps[e])[q] = xo;
         uint32_t* zp = reinterpret_cast<uint32_t*>(&zs[e]) + q;
-        if constexpr (WIDE) {
-          // finest level: z from the FP32 sum, and the sum's low BF16 part kept on
-          // the layer-output region O (the layer adds it to its skip)
-          const float2 hi = bf2_to_f2(xo), sv = bf2_to_f2(*zp);
-          *zp = f2bf(sv.x * acc[2 * h], sv.y * acc[2 * h + 1]);
-          const int orow = (po[h] >> 16) - 2 + r, ocol = (po[h] & 0xffff) - 2 + c;
-          if (orow >= 0 && orow < G::OH && ocol >= 0 && ocol < G::OW)
-            reinterpret_cast<uint32_t*>(&pl[orow * G::OW + ocol])[q] = f2bf(acc[2 * h] - hi.x, acc[2 * h + 1] - hi.y);
-        } else {
-          *zp = bmul2(xo, *zp);
-        }
+        const float2 hi = bf2_to_f2(xo), sv = bf2_to_f2(*zp);
+        *zp = f2bf(sv.x * acc[2 * h], sv.y * acc[2 * h + 1]);
+        const int orow = (po[h] >> 16) - 2 + r, ocol = (po[h] & 0xffff) - 2 + c;
+        if (orow >= 0 && orow < G::OH && ocol >= 0 && ocol < G::OW)
+          reinterpret_cast<uint32_t*>(&pl[orow * G::OW + ocol])[q] = f2bf(acc[2 * h] - hi.x, acc[2 * h + 1] - hi.y);
       }
     }
   }
@@ -585,28 +586,35 @@ __device__ __forceinline__ void tcnn_quads(uint4* ps, uint4* zs, uint4* pl, cons
 // ---------------------------------------------------------------------------
 // Up kernel (geometry in UpGeom).  Level l: x_pre = x_down + TCNN(x_{l+1}) on P
 // (or x_down on the coarsest level), layer x_fin = x_pre + K_up (s * x_pre) on O;
-// finest level: e = W_out * x_fin / alpha, u_out = u_in + e.
+// finest level: e = W_out * x_fin / alpha, u_out = u_in + e.  The up path
+// carries x_pre and x_fin as BF16 hi + lo pairs (about 16 significant bits):
+// rounding the coarse-grid correction to BF16 on its way up costs cycles of
+// the stationary iteration (37 instead of 30 at 4095^2, measured by emulating
+// the roundings); a level's x_fin goes to the next finer level as xfin (hi)
+// and xfin_lo (lo), which that level's TCNN reads through map_c and map_cl.
 // The up kernel's work on the tile (tbx, tby) of problem tbz (one block).
 template <int FH, int FW, bool LAST, bool HAS_P, bool RES>
 __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtensorMap& map_s, const CUtensorMap& map_c,
-                                        const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
-                                        const uint32_t* __restrict__ fOutTaps, const float* __restrict__ alpha2,
-                                        const double* __restrict__ u_in,
-                                        bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
-                                        const int* __restrict__ active, int* __restrict__ err, const ResidOut& ro,
-                                        int out_lo, int tbx, int tby, int tbz) {
+                                        const CUtensorMap& map_cl, const uint32_t* __restrict__ fK,
+                                        const uint32_t* __restrict__ fTc, const uint32_t* __restrict__ fOutTaps,
+                                        const float* __restrict__ alpha2, const double* __restrict__ u_in,
+                                        bf16* __restrict__ xfin, bf16* __restrict__ xfin_lo,
+                                        double* __restrict__ u_out, int n, const int* __restrict__ active,
+                                        int* __restrict__ err, const ResidOut& ro, int out_lo, int tbx, int tby,
+                                        int tbz) {
   using G = UpGeom<FH, FW, LAST, HAS_P, RES>;
   constexpr int H = G::H, OH = G::OH, OW = G::OW, QW = G::QW, QOFF = G::QOFF;
   constexpr int HE = G::HE, EH = G::EH, EW = G::EW;
-  // TMA destinations (zero outside the grid): ps = x_down on Q, then x_pre;
-  // zs = s on Q, then s * x_pre; cs = the quads' coarse pixels
-  // finest level: pl = the low BF16 part of x_pre on O, then (in place) that of
-  // the layer output; the layer output's high part replaces x_pre's in ps;
-  // then W_out's per-tap planes in zs and cs (contiguous)
+  // TMA destinations (zero outside the grid): ps = x_down on Q, then x_pre's
+  // high BF16 part; zs = s on Q, then s * x_pre; cs, cl = the quads' coarse
+  // pixels (high, low parts).  pl = the low part of x_pre on O; on the finest
+  // level the layer output's parts then replace x_pre's in ps and pl, and W_out's
+  // per-tap planes use zs, cs and cl (contiguous)
   uint4* ps = reinterpret_cast<uint4*>(fused_dsm);
-  uint4* pl = ps + pad8(G::QH * QW);                                   // finest level only
-  uint4* zs = pl + (LAST ? pad8(OH * OW) : 0);
+  uint4* pl = ps + pad8(G::QH * QW);
+  uint4* zs = pl + pad8(OH * OW);
   uint4* cs = zs + pad8(G::QH * QW);                                   // coarser level only
+  uint4* cl = cs + pad8(G::CQH * G::CQW);
   __shared__ __align__(8) uint64_t bar;
   const int j0 = tby * FH, i0 = tbx * FW;
   const int qj0 = j0 - H - 1 - QOFF, qi0 = i0 - H - 1 - QOFF;         // Q's corner (odd when HAS_P)
@@ -619,6 +627,7 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
       u_out += bz * N;
     } else {
       xfin += bz * N * 8;
+      xfin_lo += bz * N * 8;
     }
   }
   // weight fragments of the TCNN and of the layer, loaded before the tiles land
@@ -631,11 +640,14 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
   pdl_wait();
   if (active && !active[bz]) return;
   if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar, (2u * G::QH * QW + (HAS_P ? G::CQH * G::CQW : 0u)) * 16u);
+    mbar_expect_tx(&bar, (2u * G::QH * QW + (HAS_P ? 2u * G::CQH * G::CQW : 0u)) * 16u);
     tma_load_pix(ps, &map_xd, qi0, qj0, bz, &bar);
     tma_load_pix(zs, &map_s, qi0, qj0, bz, &bar);
     // the first quad's coarse source: J = (qj0 - 1) / 2 (exact, qj0 odd)
-    if (HAS_P) tma_load_pix(cs, &map_c, (qi0 - 1) / 2, (qj0 - 1) / 2, bz, &bar);
+    if (HAS_P) {
+      tma_load_pix(cs, &map_c, (qi0 - 1) / 2, (qj0 - 1) / 2, bz, &bar);
+      tma_load_pix(cl, &map_cl, (qi0 - 1) / 2, (qj0 - 1) / 2, bz, &bar);
+    }
   }
   __syncthreads();   // barrier initialised
   const bool landed = mbar_wait_bounded(&bar, 0);
@@ -645,11 +657,10 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
   }
 
   if constexpr (HAS_P) {
-    tcnn_quads<G, LAST>(ps, zs, pl, cs, fq);
+    tcnn_quads<G>(ps, zs, pl, cs, cl, fq);
   } else {
     for (int e = threadIdx.x; e < G::QH * QW; e += NT) zs[e] = mul8(ps[e], zs[e]);
-    if (LAST)
-      for (int e = threadIdx.x; e < OH * OW; e += NT) pl[e] = make_uint4(0u, 0u, 0u, 0u);   // x_pre = x_down
+    for (int e = threadIdx.x; e < OH * OW; e += NT) pl[e] = make_uint4(0u, 0u, 0u, 0u);   // x_pre = x_down
   }
   __syncthreads();
 
@@ -667,7 +678,7 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
       const int pm = min(st * 16 + mrow, NO - 1), rm = pm / OW;
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
       layer_strip<QW>(zs, ps, wk, fI, (rm + QOFF) * QW + (pm - rm * OW) + QOFF, to, acc);
-      if constexpr (LAST) {
+      {
         // the skip's low part: x_lo at the pixel itself through an identity block
         uint32_t a[2];
         ldsm_x2(a, sa(pl) + 16u * min(st * 16 + (lane & 15), NO - 1));
@@ -687,8 +698,12 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
           const float2 hi = bf2_to_f2(o);
           reinterpret_cast<uint32_t*>(&ps[(orow + QOFF + 1) * QW + ocol + QOFF + 1])[q] = in ? o : 0u;
           reinterpret_cast<uint32_t*>(&pl[p])[q] = in ? f2bf(acc[2 * h] - hi.x, acc[2 * h + 1] - hi.y) : 0u;
-        } else {
-          if (gj < n && gi < n) reinterpret_cast<uint32_t*>(xfin + ((size_t)gj * n + gi) * 8)[q] = o;
+        } else if (gj < n && gi < n) {
+          // x_fin to the next finer level as hi + lo BF16
+          const float2 hi = bf2_to_f2(o);
+          const size_t gp = ((size_t)gj * n + gi) * 8;
+          reinterpret_cast<uint32_t*>(xfin + gp)[q] = o;
+          reinterpret_cast<uint32_t*>(xfin_lo + gp)[q] = f2bf(acc[2 * h] - hi.x, acc[2 * h + 1] - hi.y);
         }
       }
     }
@@ -719,7 +734,7 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
     }
     constexpr int NO = OH * OW, NSO = (NO + 15) / 16;
     constexpr int PL = (NO + 27) / 32 * 32 + 4;    // plane pitch (floats), 4 (mod 32): conflict-free stores
-    constexpr int FREE = 16 * (pad8(G::QH * QW) + (HAS_P ? pad8(G::CQH * G::CQW) : 0));
+    constexpr int FREE = 16 * (pad8(G::QH * QW) + (HAS_P ? 2 * pad8(G::CQH * G::CQW) : 0));
     constexpr int PASS = 6 * PL * 4 <= FREE ? 6 : 3;
     static_assert(PASS * PL * 4 <= FREE, "W_out planes in the z and coarse tiles");
     float* dpl = reinterpret_cast<float*>(zs);
@@ -814,14 +829,16 @@ template <int FH, int FW, bool LAST, bool HAS_P, bool RES>
 __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUtensorMap map_xd,
                                                 const __grid_constant__ CUtensorMap map_s,
                                                 const __grid_constant__ CUtensorMap map_c,
+                                                const __grid_constant__ CUtensorMap map_cl,
                                                 const uint32_t* __restrict__ fK, const uint32_t* __restrict__ fTc,
                                                 const uint32_t* __restrict__ fOutTaps,
                                                 const float* __restrict__ alpha2, const double* __restrict__ u_in,
-                                                bf16* __restrict__ xfin, double* __restrict__ u_out, int n,
-                                                const int* __restrict__ active, int* __restrict__ err,
-                                                const __grid_constant__ ResidOut ro, int out_lo) {
-  up_body<FH, FW, LAST, HAS_P, RES>(map_xd, map_s, map_c, fK, fTc, fOutTaps, alpha2, u_in, xfin, u_out, n,
-                                    active, err, ro, out_lo, blockIdx.x, blockIdx.y, blockIdx.z);
+                                                bf16* __restrict__ xfin, bf16* __restrict__ xfin_lo,
+                                                double* __restrict__ u_out, int n, const int* __restrict__ active,
+                                                int* __restrict__ err, const __grid_constant__ ResidOut ro,
+                                                int out_lo) {
+  up_body<FH, FW, LAST, HAS_P, RES>(map_xd, map_s, map_c, map_cl, fK, fTc, fOutTaps, alpha2, u_in, xfin, xfin_lo,
+                                    u_out, n, active, err, ro, out_lo, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -834,8 +851,8 @@ __global__ void __launch_bounds__(NT, 4) up_kernel(const __grid_constant__ CUten
 constexpr int kTailFH = 16, kTailFW = 32, kTailMaxN = 255, kTailMaxLevels = 8;
 struct TailLevel {
   CUtensorMap dx, ds;              // down: the level's input x (box of Z), s (box of Z)
-  CUtensorMap ux, us, uc;          // up: x_down, s (boxes of Q), the coarser level's x (coarse box)
-  bf16 *xa, *xb, *xc;              // x_down, x (input, then output of the up step), coarser level's x
+  CUtensorMap ux, us, uc, ucl;     // up: x_down, s (boxes of Q), the coarser level's x hi, lo (coarse box)
+  bf16 *xa, *xb, *xbl, *xc;        // x_down, x (input, then output of the up step: hi), its lo, coarser level's x
   int n, tx, ty;                   // grid side, tiles per row / column
 };
 struct TailArgs {
@@ -910,12 +927,13 @@ __global__ void __launch_bounds__(NT, 4) tail_kernel(const __grid_constant__ Tai
     for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
       const int bz = t / per, tl = t - bz * per, ty = tl / L.tx, tx = tl - ty * L.tx;
       if (k + 1 < ta.nl)
-        up_body<kTailFH, kTailFW, false, true, false>(L.ux, L.us, L.uc, ta.f_up, ta.f_tcnn, nullptr, nullptr, nullptr,
-                                                      L.xb, nullptr, L.n, ta.active, ta.err, no_ro, 0, tx, ty, bz);
+        up_body<kTailFH, kTailFW, false, true, false>(L.ux, L.us, L.uc, L.ucl, ta.f_up, ta.f_tcnn, nullptr, nullptr,
+                                                      nullptr, L.xb, L.xbl, nullptr, L.n, ta.active, ta.err, no_ro, 0,
+                                                      tx, ty, bz);
       else
-        up_body<kTailFH, kTailFW, false, false, false>(L.ux, L.us, L.us, ta.f_up, ta.f_tcnn, nullptr, nullptr,
-                                                       nullptr, L.xb, nullptr, L.n, ta.active, ta.err, no_ro, 0, tx,
-                                                       ty, bz);
+        up_body<kTailFH, kTailFW, false, false, false>(L.ux, L.us, L.us, L.us, ta.f_up, ta.f_tcnn, nullptr,
+                                                       nullptr, nullptr, L.xb, L.xbl, nullptr, L.n, ta.active, ta.err,
+                                                       no_ro, 0, tx, ty, bz);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
     }
@@ -1031,18 +1049,23 @@ Status launch_up(int l, const FusedLevels& fl, const double* norm2, double* e, c
   if (ro && (!last || fl.batch != 1)) return make_status(MGCNN_ERR_STATE, "fused residual: finest level, one problem");
   const dim3 grid((nl + FW - 1) / FW, (nl + FH - 1) / FH, fl.batch);
   const ResidOut rout = ro ? *ro : ResidOut{};
+  if (!last && !fl.xbl[l]) return make_status(MGCNN_ERR_STATE, "level %d: no buffer for the low part of x_fin", l);
+  if (has_p && !fl.xbl[l + 1]) return make_status(MGCNN_ERR_STATE, "level %d: no low part of x_fin", l + 1);
   auto run = [&](auto* kernel, size_t smem, bf16* xfin, auto geom) -> Status {
     using G = decltype(geom);
-    CUtensorMap mxd, ms, mc;
+    CUtensorMap mxd, ms, mc, mcl;
     MG_TRY(pix8_map(fl, fl.xa[l], nl, G::QW, G::QH, &mxd));
     MG_TRY(pix8_map(fl, fl.s[l], nl, G::QW, G::QH, &ms));
-    if (has_p)
+    if (has_p) {
       MG_TRY(pix8_map(fl, fl.xb[l + 1], fl.n[l + 1], G::CQW, G::CQH, &mc));
-    else
-      mc = ms;   // not read on the coarsest level
-    const cudaError_t le = launch_level(kernel, grid, dyn_smem(kernel, smem), st, fl.pdl, mxd, ms, mc, w.f_up,
-                                        w.f_tcnn, w.f_out_taps, (const float*)fl.alpha, u_skip, xfin, e, nl,
-                                        active, fl.err, rout, w.out_lo);
+      MG_TRY(pix8_map(fl, fl.xbl[l + 1], fl.n[l + 1], G::CQW, G::CQH, &mcl));
+    } else {
+      mc = mcl = ms;   // not read on the coarsest level
+    }
+    bf16* xfin_lo = last ? nullptr : fl.xbl[l];
+    const cudaError_t le = launch_level(kernel, grid, dyn_smem(kernel, smem), st, fl.pdl, mxd, ms, mc, mcl, w.f_up,
+                                        w.f_tcnn, w.f_out_taps, (const float*)fl.alpha, u_skip, xfin, xfin_lo, e,
+                                        nl, active, fl.err, rout, w.out_lo);
     if (le != cudaSuccess) return cuda_status(le, "up_kernel launch");
     return {};
   };
@@ -1119,10 +1142,12 @@ Status tail_level_maps(const FusedLevels& fl, int l, TailLevel* t) {
   MG_TRY(pix8_map(fl, fl.s[l], n, ZW, ZH, &t->ds));
   MG_TRY(pix8_map(fl, fl.xa[l], n, G::QW, G::QH, &t->ux));
   MG_TRY(pix8_map(fl, fl.s[l], n, G::QW, G::QH, &t->us));
-  if (HAS_P)
+  if (HAS_P) {
     MG_TRY(pix8_map(fl, fl.xb[l + 1], fl.n[l + 1], G::CQW, G::CQH, &t->uc));
-  else
-    t->uc = t->us;   // not read on the coarsest level
+    MG_TRY(pix8_map(fl, fl.xbl[l + 1], fl.n[l + 1], G::CQW, G::CQH, &t->ucl));
+  } else {
+    t->uc = t->ucl = t->us;   // not read on the coarsest level
+  }
   return {};
 }
 
@@ -1151,6 +1176,7 @@ Status launch_tail(const FusedLevels& fl, int lt, const FusedWeights& w, const i
       MG_TRY((tail_level_maps<false, false>(fl, l, &t)));
     t.xa = fl.xa[l];
     t.xb = fl.xb[l];
+    t.xbl = fl.xbl[l];
     t.xc = l + 1 < fl.L ? fl.xb[l + 1] : nullptr;
     t.n = fl.n[l];
     t.tx = (t.n + kTailFW - 1) / kTailFW;
@@ -1175,8 +1201,8 @@ Status launch_tail(const FusedLevels& fl, int lt, const FusedWeights& w, const i
   return {};
 }
 
-constexpr int kTileH[kUpVariants] = {16, 8, 16, 32, 24, 24, 32};
-constexpr int kTileW[kUpVariants] = {32, 32, 16, 32, 32, 30, 30};
+constexpr int kTileH[kUpVariants] = {16, 8, 16, 32, 24, 24, 32, 22};
+constexpr int kTileW[kUpVariants] = {32, 32, 16, 32, 32, 30, 30, 30};
 
 Status launch_down_variant(int v, int l, const FusedLevels& fl, const float* r32, const double* norm2,
                            const FusedWeights& w, const int* active, cudaStream_t st, const ResidIn* ra = nullptr) {
@@ -1200,6 +1226,7 @@ Status launch_up_variant(int v, int l, const FusedLevels& fl, const double* norm
     // on the finest level the layer output is 32 pixels wide, whole strips of 16
     case 5: return launch_up<24, 30>(l, fl, norm2, e, u_skip, w, active, st, ro);
     case 6: return launch_up<32, 30>(l, fl, norm2, e, u_skip, w, active, st, ro);
+    case 7: return launch_up<22, 30>(l, fl, norm2, e, u_skip, w, active, st, ro);
     default: return launch_up<16, 32>(l, fl, norm2, e, u_skip, w, active, st, ro);
   }
 }
@@ -1326,6 +1353,7 @@ FusedLevels ctx_levels(mgcnn_ctx* c) {
     fl.s[l] = c->s16[l].as<bf16>();
     fl.xa[l] = c->x16a[l].as<bf16>();
     fl.xb[l] = c->x16b[l].as<bf16>();
+    fl.xbl[l] = c->x16l[l].as<bf16>();
     fl.var_down[l] = c->tile_var[0][l];
     fl.var_up[l] = c->tile_var[1][l];
   }

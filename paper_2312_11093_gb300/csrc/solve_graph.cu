@@ -117,6 +117,7 @@ Status build_graph(mgcnn_ctx* c) {
         fl.s[l] = c->s16[l].as<__nv_bfloat16>();
         fl.xa[l] = c->x16a[l].as<__nv_bfloat16>();
         fl.xb[l] = c->x16b[l].as<__nv_bfloat16>();
+        fl.xbl[l] = c->x16l[l].as<__nv_bfloat16>();
         fl.var_down[l] = c->tile_var[0][l];
         fl.var_up[l] = c->tile_var[1][l];
       }
@@ -213,6 +214,7 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
       fl.s[l] = c->s16[l].as<__nv_bfloat16>();
       fl.xa[l] = c->x16a[l].as<__nv_bfloat16>();
       fl.xb[l] = c->x16b[l].as<__nv_bfloat16>();
+      fl.xbl[l] = c->x16l[l].as<__nv_bfloat16>();
     }
     MG_TRY(fused_autotune(fl, c->r32.as<float>(), c->scalars.as<double>() + 1, c->e.as<double>(), fused_weights(c),
                           st, 5));

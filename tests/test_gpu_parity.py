@@ -441,7 +441,7 @@ def test_tile_wait_timeout_is_reported_and_context_survives(M):
 @pytest.mark.parametrize("net", ["gmg_v10", "random"])
 def test_every_tile_shape_gives_identical_iterates(M, n, net):
     """Each tile shape of the fused kernels (16 x 32, 8 x 32, 16 x 16, 32 x 32,
-    24 x 32, and the up kernels' 24 x 30 and 32 x 30, forced by MGCNN_OPT_TILE)
+    24 x 32, and the up kernels' 24 x 30, 32 x 30 and 22 x 30, forced by MGCNN_OPT_TILE)
     and the autotuned choice give bit-identical
     iterates: a pixel's arithmetic does not depend on the tile that holds it.  The
     residual norms, summed per tile by the finest down kernel, agree to rounding.
@@ -450,7 +450,7 @@ def test_every_tile_shape_gives_identical_iterates(M, n, net):
     k, f = problem(n, 80 + n, "blocks")
     w = M.gmg_v10_weights() if net == "gmg_v10" else init_weights(8, 1, 1, np.random.default_rng(9), out_scale=0.05)
     out = {}
-    for tile in (-1, 0, 1, 2, 3, 4, 5, 6):
+    for tile in (-1, 0, 1, 2, 3, 4, 5, 6, 7):
         sv = M.Solver(8, 1, 1, precision="mixed_bf16")
         sv.set_option(sv.OPT_TILE, tile)
         sv.set_weights(w)
@@ -462,7 +462,7 @@ def test_every_tile_shape_gives_identical_iterates(M, n, net):
         st, it, hist = sv.solve(f.ravel().copy(), u, 1e-30, 4)
         assert it == 4
         out[tile] = (hist.copy(), u)
-    for tile in (0, 1, 2, 3, 4, 5, 6):
+    for tile in (0, 1, 2, 3, 4, 5, 6, 7):
         np.testing.assert_allclose(out[tile][0], out[-1][0], rtol=1e-13, atol=0)
         assert np.array_equal(out[tile][1], out[-1][1]), tile
 
@@ -538,7 +538,7 @@ def test_coarse_tail_option_range(M):
 
 def test_tile_option_range(M):
     sv = M.Solver(8, 1, 1, precision="mixed_bf16")
-    for bad in (-2, 7):
+    for bad in (-2, 8):
         with pytest.raises(M.MGCNNError) as ei:
             sv.set_option(sv.OPT_TILE, bad)
         assert ei.value.status == M.ERR_ARG
