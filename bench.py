@@ -144,6 +144,10 @@ def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
     """Bytes a launch of `kind` must move (each operand once): the finest level's
     kernel classes, or the fused kernels of a coarser level l ("down<l>",
     "up<l>", level size n_l = (n_{l-1} - 1) / 2)."""
+    # per level unknown, BF16 with cp channels: down = x_in, s in; x_down and the
+    # coarse x out (6.5 cp bytes); up = x_down, s and the coarse x_fin (hi + lo
+    # parts) in; x_fin (hi + lo) out (9 cp bytes)
+    down_l, up_l = 6.5 * cp, 9.0 * cp
     if kind == "tail":
         # the coarse tail kernel: down and up of every level from the first with
         # n_l <= 255 (level 1 at the earliest, at most 8 levels) to the coarsest
@@ -151,16 +155,13 @@ def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
         while sizes[-1] > 3:
             sizes.append((sizes[-1] - 1) // 2)
         tail = [nl for lvl, nl in enumerate(sizes) if lvl >= 1 and nl <= 255][-8:]
-        return sum(2 * (2.0 * cp + 2.0 * cp + 2.0 * cp + 0.5 * cp) * nl * nl for nl in tail)
+        return sum((down_l + up_l) * nl * nl for nl in tail)
     for pre in ("down", "up"):
         if kind.startswith(pre) and kind[len(pre):].isdigit() and int(kind[len(pre):]) > 0:
             nl = n
             for _ in range(int(kind[len(pre):])):
                 nl = (nl - 1) // 2
-            Nl = nl * nl
-            # down: x_in and s in, x_down and the coarse x out; up: x_down, s and the
-            # coarse x in, x_fin out (BF16, cp channels)
-            return (2.0 * cp + 2.0 * cp + 2.0 * cp + 0.5 * cp) * Nl
+            return (down_l if pre == "down" else up_l) * nl * nl
     N = n * n
     return {
         "residual": 60.0 * N,                    # u, f (FP64) + 5 stencil arrays in, FP32 r out
@@ -171,7 +172,7 @@ def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
         "out": (2.0 * cp + 16.0) * N,            # BF16 x in, FP64 u in/out
         # fused level kernels at the finest level (8 channels):
         "down0": (4.0 + 2.0 * cp + 2.0 * cp + 0.5 * cp) * N,  # r (FP32), s in; x_down, coarse x out
-        "up0": (2.0 * cp + 2.0 * cp + 0.5 * cp + 16.0) * N,   # x_down, s, coarse x, u in; u out
+        "up0": (2.0 * cp + 2.0 * cp + 1.0 * cp + 16.0) * N,   # x_down, s, coarse x (hi + lo), u in; u out
     }[kind]
 
 
