@@ -722,15 +722,33 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
     uint32_t bt[kOutTapRegs];
 #pragma unroll
     for (int k = 0; k < kOutTapRegs; ++k) bt[k] = fOutTaps[k * 32 + lane];
+    // E pixels of this thread: with rows of 17..32 pixels, E row er = warp + NW k
+    // to one warp (lane = column), so that a warp's reads of a tap plane are one
+    // row, consecutive words, free of bank conflicts; else consecutive pixels
+    constexpr int NE = EH * EW;
+    constexpr bool ROWS = EW > 16 && EW <= 32;
+    constexpr int NU = ROWS ? (EH + NW - 1) / NW : (NE + NT - 1) / NT;
+    auto epix = [&](int k, int& er, int& ec) -> bool {
+      if constexpr (ROWS) {
+        er = warp + NW * k;
+        ec = lane;
+        return er < EH && ec < EW;
+      } else {
+        const int e = threadIdx.x + k * NT;
+        er = e / EW;
+        ec = e - er * EW;
+        return e < NE;
+      }
+    };
     // this thread's u values of the update below, loaded now so that their
     // latency passes during W_out (zero outside the grid)
-    constexpr int NE = EH * EW, NU = (NE + NT - 1) / NT;
     double uv[NU];
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
-      const int e = threadIdx.x + k * NT, er = e / EW, ec = e - er * EW;
+      int er, ec;
+      const bool valid = epix(k, er, ec);
       const int gj = j0 - HE + er, gi = i0 - HE + ec;
-      uv[k] = (u_in && e < NE && gj >= 0 && gj < n && gi >= 0 && gi < n) ? u_in[(size_t)gj * n + gi] : 0.0;
+      uv[k] = (u_in && valid && gj >= 0 && gj < n && gi >= 0 && gi < n) ? u_in[(size_t)gj * n + gi] : 0.0;
     }
     constexpr int NO = OH * OW, NSO = (NO + 15) / 16;
     constexpr int PL = (NO + 27) / 32 * 32 + 4;    // plane pitch (floats), 4 (mod 32): conflict-free stores
@@ -769,8 +787,8 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < NU; ++k) {
-        const int e = threadIdx.x + k * NT, er = e / EW, ec = e - er * EW;
-        if (e >= NE) continue;
+        int er, ec;
+        if (!epix(k, er, ec)) continue;
 #pragma unroll
         for (int tp = 0; tp < PASS && t0 + tp < 9; ++tp) {
           const int t = t0 + tp;
@@ -783,12 +801,12 @@ __device__ __forceinline__ void up_body(const CUtensorMap& map_xd, const CUtenso
     double* un = reinterpret_cast<double*>(zs);    // u + e on E (residual in this kernel)
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
-      const int e = threadIdx.x + k * NT, er = e / EW, ec = e - er * EW;
+      int er, ec;
+      if (!epix(k, er, ec)) continue;
       const int gj = j0 - HE + er, gi = i0 - HE + ec;
-      if (e >= NE) continue;
       const bool in = gj >= 0 && gj < n && gi >= 0 && gi < n;
       const double un_e = in ? uv[k] + f32_to_f64_exact(esum[k] * inv_alpha) : 0.0;
-      if (RES) un[e] = un_e;
+      if (RES) un[er * EW + ec] = un_e;
       if (in && er >= HE && er < HE + FH && ec >= HE && ec < HE + FW) u_out[(size_t)gj * n + gi] = un_e;
     }
     if constexpr (RES) {
