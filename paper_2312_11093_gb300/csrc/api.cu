@@ -442,7 +442,10 @@ Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
       if (l < L - 1) MG_TRY(launch_inject_mu(c->coef[l].as<double>(), c->coef[l + 1].as<double>(), nlv, c->stream));
     }
   }
-  MG_TRY(launch_diag_inverse(c->op[0].as<double>(), c->dinv.as<double>(), c->dinv32.as<float>(), N0, c->stream));
+  // the FP64 copy of 1/a_C feeds the FP64 network only (an FP64 division per unknown)
+  MG_TRY(launch_diag_inverse(c->op[0].as<double>(),
+                             c->cfg.precision == MGCNN_PREC_FP64 ? c->dinv.as<double>() : nullptr,
+                             c->dinv32.as<float>(), N0, c->stream));
   return {};
 }
 

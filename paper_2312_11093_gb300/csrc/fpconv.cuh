@@ -46,4 +46,41 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
   return __uint_as_float(sign | r);
 }
 
+// FP64 reciprocal and 16th root with few FP64 instructions, for the setup
+// kernels (every FP64 instruction per grid node there costs ~30 us at 4095^2).
+// Both start from an FP32 value and refine it by Newton-Raphson iteration in
+// FP64 fused multiply-adds (quadratic convergence: an FP32 start, relative error
+// ~1e-7, is below FP64 rounding after two steps); results within a few units
+// in the last place of the correctly rounded value.
+
+// 1 / d for d > 0 with binary exponent in [-1000, 1000] (callers check): d =
+// m 2^e with m in [1, 2); start from the FP32 reciprocal of m truncated to
+// FP32 (from the bit pattern, no FP64 conversion), iterate r <- r + r (1 - m r)
+// twice, scale by 2^-e (exact).
+__device__ __forceinline__ double recip_newton(double d) {
+  const long long b = __double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  const float mf = __uint_as_float(0x3f800000u | (uint32_t)((b >> 29) & 0x7fffffu));
+  double r = f32_to_f64_exact(__frcp_rn(mf));
+  r = fma(r, fma(-m, r, 1.0), r);
+  r = fma(r, fma(-m, r, 1.0), r);
+  return r * __longlong_as_double((long long)(1023 - e) << 52);
+}
+
+// x^(1/16) for x in [1, 2^16): z = x^(-1/16) starts in FP32 (exp2f of -log2f(x)
+// / 16) and takes two Newton-Raphson steps for z^-16 = x, z <- z + z (1 - x z^16)
+// / 16 (no division); then x^(1/16) = 1 / z.
+__device__ __forceinline__ double root16_newton(double x) {
+  const long long b = __double_as_longlong(x);
+  const float xf = __uint_as_float((uint32_t)(((b >> 52) & 0x7ff) - 896) << 23 | (uint32_t)((b >> 29) & 0x7fffffu));
+  double z = f32_to_f64_exact(exp2f(-0.0625f * log2f(xf)));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double z2 = z * z, z4 = z2 * z2, z8 = z4 * z4, z16 = z8 * z8;
+    z = fma(z, 0.0625 * fma(-x, z16, 1.0), z);
+  }
+  return recip_newton(z);
+}
+
 }  // namespace mgcnn

@@ -24,7 +24,8 @@ namespace mgcnn {
 // formed from the binary mantissas m in [1, 2) and exponents e of the nine k
 // (k = m 2^e): P = prod m^w lies in [1, 2^16), E = sum w e, and
 //   k_c = P^(1/16) * 2^(r/16) * 2^q  with E = 16 q + r, 0 <= r < 16,
-// P^(1/16) by four square roots, 2^(r/16) from a table made on the host.
+// P^(1/16) by Newton-Raphson from an FP32 start (root16_newton), 2^(r/16) from
+// a table made on the host.
 // Ring nodes (renormalised weights) and subnormal k take the log / exp form.
 struct Pow2Sixteenths {
   double t[16];   // t[r] = 2^(r/16)
@@ -60,7 +61,7 @@ __global__ void restrict_k_kernel(const double* __restrict__ k, double* __restri
       const double c2 = v[4] * v[4];
       const double P = corners * (edges * edges) * (c2 * c2);
       const int E = (e[0] + e[2] + e[6] + e[8]) + 2 * (e[1] + e[3] + e[5] + e[7]) + 4 * e[4];
-      const double root = sqrt(sqrt(sqrt(sqrt(P))));
+      const double root = root16_newton(P);
       const int q = E >> 4, r = E & 15;
       kc[p] = (root * p2.t[r]) * __longlong_as_double((long long)(q + 1023) << 52);
       return;
@@ -114,9 +115,10 @@ Status launch_inject_mu(const double* mu, double* mc, int n, cudaStream_t st) {
 //   a_C = (k_w + k_e + k_s + k_n)/h^2 + (|bx| + |by|)/h
 // Output layout: op[0..N) = a_C, then a_W, a_E, a_S, a_N.
 // The constant terms come from the host (StencilConsts); the four harmonic
-// means 2 k_c k_o / (k_c + k_o) share one FP64 reciprocal of the product of
-// the four sums (an FP64 divide is a long FP64-pipe sequence), with the plain
-// divisions as the fallback when that product leaves the normal range.
+// means 2 k_c k_o / (k_c + k_o) share one reciprocal of the product of the
+// four sums, by Newton-Raphson from an FP32 start (recip_newton: an FP64
+// divide is a long FP64-pipe sequence), with the plain divisions as the
+// fallback when that product's exponent leaves [-1000, 1000].
 struct StencilConsts {
   double ih2;          // 1 / h^2
   double cW, cE, cS, cN, cC;   // max(bx,0)/h, min(bx,0)/h, max(by,0)/h, min(by,0)/h, (|bx|+|by|)/h
@@ -139,26 +141,29 @@ __global__ void stencil_div_kernel(const double* __restrict__ k, double* __restr
   const double sW = kc + kwn, sE = kc + ken, sS = kc + ksn, sN = kc + knn;
   const double pWE = sW * sE, pSN = sS * sN;
   const double D = pWE * pSN;
-  const double t2 = 2.0 * kc;
-  double kw, ke, ks, kn;
-  if (D >= 1e-300 && D <= 1e300) {
-    const double R = 1.0 / D;
+  const double T = kc * (2.0 * sc.ih2);   // 2 k_c / h^2
+  double iW, iE, iS, iN;                  // 1 / s_o
+  const int ed = (int)((__double_as_longlong(D) >> 52) & 0x7ff) - 1023;
+  if (ed >= -1000 && ed <= 1000) {
+    const double R = recip_newton(D);
     const double rWE = R * pSN, rSN = R * pWE;   // 1 / (sW sE), 1 / (sS sN)
-    kw = t2 * kwn * (sE * rWE);
-    ke = t2 * ken * (sW * rWE);
-    ks = t2 * ksn * (sN * rSN);
-    kn = t2 * knn * (sS * rSN);
+    iW = sE * rWE;
+    iE = sW * rWE;
+    iS = sN * rSN;
+    iN = sS * rSN;
   } else {
-    kw = t2 * kwn / sW;
-    ke = t2 * ken / sE;
-    ks = t2 * ksn / sS;
-    kn = t2 * knn / sN;
+    iW = 1.0 / sW;
+    iE = 1.0 / sE;
+    iS = 1.0 / sS;
+    iN = 1.0 / sN;
   }
-  op[1 * N + p] = -kw * sc.ih2 - sc.cW;
-  op[2 * N + p] = -ke * sc.ih2 + sc.cE;
-  op[3 * N + p] = -ks * sc.ih2 - sc.cS;
-  op[4 * N + p] = -kn * sc.ih2 + sc.cN;
-  op[p] = (kw + ke + ks + kn) * sc.ih2 + sc.cC;
+  // k_o / h^2 = (2 k_c / h^2) k_o / s_o
+  const double kw = T * kwn * iW, ke = T * ken * iE, ks = T * ksn * iS, kn = T * knn * iN;
+  op[1 * N + p] = -kw - sc.cW;
+  op[2 * N + p] = -ke + sc.cE;
+  op[3 * N + p] = -ks - sc.cS;
+  op[4 * N + p] = -kn + sc.cN;
+  op[p] = (kw + ke) + (ks + kn) + sc.cC;
 }
 
 Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st, int batch) {
