@@ -313,6 +313,17 @@ def pinned_copy(a: np.ndarray) -> np.ndarray:
 pinned_copy.keep = []
 
 
+def pinned_zeros(count: int, dev) -> np.ndarray:
+    """A zeroed page-locked host array, written by a copy from the device so that
+    the device has reached its pages once (a host buffer's first transfers here
+    run several times slower than later ones), like a buffer the caller reuses."""
+    import torch
+    t = torch.empty(count, dtype=torch.float64, pin_memory=True)
+    t.copy_(torch.zeros(count, dtype=torch.float64, device=dev))
+    pinned_copy.keep.append(t)
+    return t.numpy()
+
+
 # --------------------------------------------------------------------------- ranks
 def max_over_ranks(ms: float, world: int, device) -> float:
     """The slowest rank's time: each rank (one GPU) runs its own replica of the
@@ -497,7 +508,7 @@ def main():
     # make the mean depend on whether one of them lands in the region)
     e2e_steps = max(3, args.steps)
     k_p, f_p = pinned_copy(k_h), pinned_copy(f_h)
-    u_p = [pinned_copy(np.zeros(n * n)) for _ in range(e2e_steps + 1)]
+    u_p = [pinned_zeros(n * n, dev) for _ in range(e2e_steps + 1)]
 
     def e2e_step(u):
         if is_gmg:
@@ -733,7 +744,7 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
     e2e_steps = 2
     kp = [pinned_copy(k) for k in ks]
     fp = [pinned_copy(f) for f in fs]
-    ups = [[pinned_copy(np.zeros(n * n)) for n in ns] for _ in range(e2e_steps + 1)]
+    ups = [[pinned_zeros(n * n, dev) for n in ns] for _ in range(e2e_steps + 1)]
 
     def e2e_step(uu):
         sv.setup_batched(kp, ns, gmg_omega=0.8 if is_gmg else None)
