@@ -13,7 +13,7 @@ constexpr int kReduceBlock = 1024;
 // sizes the partial-sum buffer with it.
 inline int reduction_blocks(size_t N) { return grid_for(N, kResidualBlock); }
 // The residual kernel's blocks (and partial sums): kResidualPix pixels per thread.
-constexpr int kResidualPix = 4;
+constexpr int kResidualPix = 8;
 inline int residual_blocks(size_t N) { return grid_for(N, (size_t)kResidualBlock * kResidualPix); }
 
 // Row pitch (floats) of the FP32 network input r32: rows start on 16-byte
