@@ -441,7 +441,7 @@ int mgcnn_profile_read(mgcnn_ctx* ctx, double* ms, long long* counts, int nkinds
  * cudaStream_t as void* (NULL: legacy default stream); the call synchronises it.
  * Same kernels and the same deterministic reduction as mgcnn_residual.
  * Scratch: the per-block partial sums live in a fixed array inside the library
- * (16,385 doubles, 128 KiB, held by every GPU that loads the library until the
+ * (8,193 doubles, 64 KiB, held by every GPU that loads the library until the
  * process exits), so n*n may not exceed 16,777,216 (n <= 4096): larger grids
  * return ERR_SIZE before anything is launched.  The first call on a device
  * looks the array's device address up (cudaGetSymbolAddress) with that device

@@ -4,7 +4,7 @@
 // deterministic two-pass norm as the context-based mgcnn_residual, but its
 // per-block partial sums live in a fixed array defined in this file instead of
 // a buffer obtained from cudaMalloc.  Every GPU that loads the library keeps
-// that array (kNoAllocMaxBlocks + 1 doubles, 128 KiB) until the process exits.
+// that array (kNoAllocMaxBlocks + 1 doubles, 64 KiB) until the process exits.
 #include <mutex>
 
 #include "ops.cuh"
@@ -13,8 +13,8 @@ namespace mgcnn {
 namespace {
 
 // Largest grid served: n^2 <= 16,777,216 unknowns (n <= 4096).  Each block of
-// the residual kernel covers kResidualBlock * kResidualPix = 1024 unknowns and
-// leaves one partial sum, so 16,384 partial sums suffice; the last slot receives
+// the residual kernel covers kResidualBlock * kResidualPix = 2048 unknowns and
+// leaves one partial sum, so 8,192 partial sums suffice; the last slot receives
 // the reduced sum.
 constexpr size_t kNoAllocMaxUnknowns = 16777216;
 constexpr int kNoAllocMaxBlocks = (int)(kNoAllocMaxUnknowns / ((size_t)kResidualBlock * kResidualPix));
