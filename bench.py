@@ -665,6 +665,7 @@ def main():
         # GMG, per-level achieved bandwidth)
         result["batched"] = run_batched(args, rank, world, dev, mgcnn, quiet=True)
         result["channelised"] = run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol)
+        result["setup_network"] = time_setup_network(n, dev, stream, mgcnn, k_d, b)
     if not args.no_cpu and rank == 0 and world == 1:
         # one wave of complete oracle solves at 511^2, one per host core (about 15-30 s)
         result["cpu_baseline"] = cpu_reference(workload, net, n, n_sample=min(n, 511), tol=tol)
@@ -778,6 +779,30 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
                    "d2h_bytes_per_step": int(sum(f.nbytes for f in fs)), "ms_per_step": e2e_ms},
            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None}
     return res
+
+
+def time_setup_network(n, dev, stream, mgcnn, k_d, b, reps=5):
+    """The learned network's setup phase (Algorithm 2: features, reChannel, four
+    tanh ResNet layers and the setup RCNN per level, fused BF16 kernels) on the
+    bench's coefficient field, with randomly initialised weights (no trained
+    weights here): the cost the analytic GMG setup of the headline replaces."""
+    import torch
+    from paper_2312_11093_gb300.train import init_weights
+    sv = mgcnn.Solver(8, 1, 1, precision="mixed_bf16", b=b, stream=stream)
+    sv.set_weights(init_weights(8, 1, 1, np.random.default_rng(1)))
+    sv.setup(k_d, n)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        sv.setup(k_d, n)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    sv.close()
+    return {"ms_per_setup": ms, "reps": reps,
+            "what": "mgcnn_setup at %d^2: operators on every level plus the setup network, random weights" % n}
 
 
 def run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, maxit=60):
