@@ -176,7 +176,18 @@ def algorithmic_bytes(kind: str, n: int, cp: int) -> float:
     }[kind]
 
 
-KERNEL_SOURCE = {"residual_kernel": "operator.cu", "down_kernel": "mixed_fused.cu", "up_kernel": "mixed_fused.cu"}
+# the sources whose hash identifies a kernel's build (its file and the headers that
+# shape it)
+KERNEL_SOURCE = {"residual_kernel": ("operator.cu", "ops.cuh", "fpconv.cuh"),
+                 "down_kernel": ("mixed_fused.cu", "mixed.cuh", "tma.cuh", "ops.cuh"),
+                 "up_kernel": ("mixed_fused.cu", "mixed.cuh", "tma.cuh", "ops.cuh")}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCE[kernel]:
+        h.update(open(os.path.join(ROOT, "paper_2312_11093_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
 
 
 def _profile_fields(kernel: str, workload: str):
@@ -186,8 +197,7 @@ def _profile_fields(kernel: str, workload: str):
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path) or kernel not in KERNEL_SOURCE:
         return None
-    src = open(os.path.join(ROOT, "paper_2312_11093_gb300", "csrc", KERNEL_SOURCE[kernel]), "rb").read()
-    h = hashlib.sha1(src).hexdigest()[:12]
+    h = kernel_source_hash(kernel)
     for ln in open(path):
         parts = ln.split()
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[2] == h:
