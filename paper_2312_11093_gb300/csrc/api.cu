@@ -826,7 +826,7 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
     }
     if (c->device_loop && !c->prof) {   // profiling brackets need plain stream launches
       bool used = false;
-      Status d = solve_on_device(c, df, du, tol, maxit, iters, relres, &used);
+      Status d = solve_on_device(c, df, du, tol, maxit, iters, relres, &used, fn2);
       if (used || !d.ok()) {
         MG_TRY(stage_out_finish(c, u, du, N, host));
         MG_TRY(sync(c));

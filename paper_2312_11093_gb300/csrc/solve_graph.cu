@@ -154,7 +154,7 @@ void graph_release(mgcnn_ctx* c) {
 // arrays of n^2 doubles (u in place).  *used = false when the graph could not be
 // built (the caller then runs the host loop); the context remembers that.
 Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int* iters,
-                       double* relres, bool* used) {
+                       double* relres, bool* used, double fn2_known) {
   *used = false;
   if (c->graph_failed || !(c->cfg.precision == MGCNN_PREC_MIXED_BF16 && c->fused && fused_supported(c))) return {};
   const size_t N0 = c->lv[0].N();
@@ -170,12 +170,15 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
   MG_TRY(ensure(c->u, N0 * sizeof(double)));
   if (f != c->f.as<double>()) MG_CUDA(cudaMemcpyAsync(c->f.p, f, N0 * sizeof(double), cudaMemcpyDefault, st));
   if (u != c->u.as<double>()) MG_CUDA(cudaMemcpyAsync(c->u.p, u, N0 * sizeof(double), cudaMemcpyDefault, st));
-  // ||f||^2 into scalars[1]
-  MG_TRY(launch_sumsq(c->f.as<double>(), N0, c->partial.as<double>(), st));
-  MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N0), c->scalars.as<double>() + 1, st));
-  MG_CUDA(cudaMemcpyAsync(c->h_scalars + 1, c->scalars.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
-  MG_CUDA(cudaStreamSynchronize(st));
-  const double fn2 = c->h_scalars[1];
+  // ||f||^2 into scalars[1] (unless the caller has it there already)
+  double fn2 = fn2_known;
+  if (!(fn2_known > 0.0)) {
+    MG_TRY(launch_sumsq(c->f.as<double>(), N0, c->partial.as<double>(), st));
+    MG_TRY(launch_reduce(c->partial.as<double>(), residual_blocks(N0), c->scalars.as<double>() + 1, st));
+    MG_CUDA(cudaMemcpyAsync(c->h_scalars + 1, c->scalars.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+    fn2 = c->h_scalars[1];
+  }
   if (!std::isfinite(fn2)) return make_status(MGCNN_ERR_NONFINITE, "right-hand side is not finite");
   *used = true;
   *iters = 0;
