@@ -56,3 +56,23 @@ def test_traffic_record_matches_the_committed_profiles():
         assert t is not None and t > 1e8, f"{kernel}: profiles/dram_traffic.txt is stale, re-profile"
     assert bench.traffic_record("up_kernel", "channelised_4095") is None
     assert bench.traffic_record("no_such_kernel", "grf_4095") is None
+
+
+def test_algorithmic_bytes_per_unknown():
+    """The per-unknown byte counts behind the roofline (8 channels, BF16 state,
+    FP64 u, f and stencil): residual 60 (u, f, five stencil planes in; FP32 r
+    out), finest down 40 (FP32 r, s in; x_down, coarse x out), finest up 56
+    (x_down, s, the coarse x_fin's high and low parts, u in; u out), coarser
+    down 52 and up 72 per level unknown (the up sweep's x_fin in and out as high
+    and low parts); the coarse tail sums its levels."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n = 4095
+    N = n * n
+    assert bench.algorithmic_bytes("residual", n, 8) == 60 * N
+    assert bench.algorithmic_bytes("down0", n, 8) == 40 * N
+    assert bench.algorithmic_bytes("up0", n, 8) == 56 * N
+    assert bench.algorithmic_bytes("down1", n, 8) == 52 * 2047 * 2047
+    assert bench.algorithmic_bytes("up2", n, 8) == 72 * 1023 * 1023
+    levels = [255, 127, 63, 31, 15, 7, 3]
+    assert bench.algorithmic_bytes("tail", n, 8) == sum((52 + 72) * m * m for m in levels)
