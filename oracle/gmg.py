@@ -48,28 +48,55 @@ def prolong_bilinear(ec: np.ndarray, n_fine: int) -> np.ndarray:
     return e
 
 
-def vcycle(stencils: list[Stencil], r: np.ndarray, nu1: int, nu2: int, omega: float,
+def level_omegas(levels: int, omega) -> list[float]:
+    """Jacobi weight of every level, finest first.
+
+    `omega` is one weight for every level, or three weights (w_fine, w_mid,
+    w_coarsest): w_fine on the finest level, w_coarsest on the coarsest, w_mid
+    on every level in between; a one-level hierarchy takes w_fine.  Reading:
+    Sec. 2.3 smooths with weighted Jacobi and fixes no weight, so the weight
+    may be chosen per level like any other smoother parameter.
+    """
+    if np.ndim(omega) == 0:
+        return [float(omega)] * levels
+    w_fine, w_mid, w_coarsest = (float(x) for x in omega)
+    if levels == 1:
+        return [w_fine]
+    return [w_fine] + [w_mid] * (levels - 2) + [w_coarsest]
+
+
+def _omega_at(omega, level: int) -> float:
+    """omega: one weight, or a list with one weight per level."""
+    return float(omega) if np.ndim(omega) == 0 else float(omega[level])
+
+
+def vcycle(stencils: list[Stencil], r: np.ndarray, nu1: int, nu2: int, omega,
            level: int = 0) -> np.ndarray:
-    """One V(nu1, nu2) cycle for A_level e = r from e = 0; returns e."""
+    """One V(nu1, nu2) cycle for A_level e = r from e = 0; returns e.
+
+    omega: one Jacobi weight, or a list with one weight per level (finest first)."""
     st = stencils[level]
+    om = _omega_at(omega, level)
     e = np.zeros_like(r)
     if level == len(stencils) - 1:
         for _ in range(nu1 + nu2):
-            e = jacobi_sweep(st, e, r, omega)
+            e = jacobi_sweep(st, e, r, om)
         return e
     for _ in range(nu1):
-        e = jacobi_sweep(st, e, r, omega)
+        e = jacobi_sweep(st, e, r, om)
     d = r - apply(st, e)
     ec = vcycle(stencils, restrict_fw(d), nu1, nu2, omega, level + 1)
     e = e + prolong_bilinear(ec, r.shape[0])
     for _ in range(nu2):
-        e = jacobi_sweep(st, e, r, omega)
+        e = jacobi_sweep(st, e, r, om)
     return e
 
 
 def stationary_solve(stencils: list[Stencil], f: np.ndarray, u0: np.ndarray | None, tol: float,
-                     maxit: int, nu1: int = 2, nu2: int = 2, omega: float = 0.8):
+                     maxit: int, nu1: int = 2, nu2: int = 2, omega=0.8):
     """u^{k+1} = u^k + V(f - A u^k) until ||r||_2/||f||_2 <= tol (checked before each cycle).
+
+    omega: one Jacobi weight, or a list with one weight per level (`level_omegas`).
 
     Returns (u, iters, relres_history, iterates) with iterates[k] = u^k.
     """

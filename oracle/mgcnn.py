@@ -333,25 +333,32 @@ def _shift_to_source(a: np.ndarray, dy: int, dx: int) -> np.ndarray:
     return out
 
 
-def gmg_equivalent_setup(stencils: list[Stencil], omega: float = 0.8, input_diag: bool = False) -> list[np.ndarray]:
+def _level_weight(omega, lev: int) -> float:
+    """omega: one Jacobi weight, or a list with one weight per level (finest first)."""
+    return float(omega) if np.ndim(omega) == 0 else float(omega[lev])
+
+
+def gmg_equivalent_setup(stencils: list[Stencil], omega=0.8, input_diag: bool = False) -> list[np.ndarray]:
     """Setup tensors for `gmg_equivalent_weights` on every level:
     s[E_o](q) = -omega a_o(q-o)/a_C(q-o),  s[F_J] = omega/a_C,
     s[G_o](q) = -a_o(q-o),                 s[F_G] = 1,  s[D] = 0.
     With input_diag the finest level's rhs copies hold D^{-1} r, so there
-    s[F_J] = omega and s[F_G] = a_C (the same Jacobi update and defect)."""
+    s[F_J] = omega and s[F_G] = a_C (the same Jacobi update and defect).
+    omega: one weight, or one per level (level l's tensors use omega[l])."""
     outs = []
     for lev, st in enumerate(stencils):
+        omega_l = _level_weight(omega, lev)
         n = st.n
         s = np.zeros((GMG_CHANNELS, n, n))
         coeffs = [st.aC, st.aW, st.aE, st.aS, st.aN]
         for k, ((dy, dx), a) in enumerate(zip(_OFFS, coeffs)):
-            s[_E[k]] = _shift_to_source(-omega * a / st.aC, dy, dx)
+            s[_E[k]] = _shift_to_source(-omega_l * a / st.aC, dy, dx)
             s[_G[k]] = _shift_to_source(-a, dy, dx)
         if input_diag and lev == 0:
-            s[_FJ] = omega
+            s[_FJ] = omega_l
             s[_FG] = st.aC
         else:
-            s[_FJ] = omega / st.aC
+            s[_FJ] = omega_l / st.aC
             s[_FG] = 1.0
         outs.append(s)
     return outs
@@ -401,20 +408,22 @@ def gmg_v10_weights() -> dict:
             "w_R": R, "w_P": P, "w_out": w_out}
 
 
-def gmg_v10_setup(stencils: list[Stencil], omega: float = 0.8, input_diag: bool = False) -> list[np.ndarray]:
+def gmg_v10_setup(stencils: list[Stencil], omega=0.8, input_diag: bool = False) -> list[np.ndarray]:
     """Setup tensors for `gmg_v10_weights` on every level:
     s[T_o](q) = -omega a_o(q-o)/a_C(q),  s[F_G] = 1 - omega,  s[F_J] = omega/a_C,  s[D] = s[E] = 0.
     With input_diag the finest level's rhs copies hold D^{-1} r, so there
-    s[T_o](q) = -omega a_o(q-o), s[F_G] = (1 - omega) a_C, s[F_J] = omega."""
+    s[T_o](q) = -omega a_o(q-o), s[F_G] = (1 - omega) a_C, s[F_J] = omega.
+    omega: one weight, or one per level (level l's tensors use omega[l])."""
     outs = []
     for lev, st in enumerate(stencils):
+        omega_l = _level_weight(omega, lev)
         n = st.n
         s = np.zeros((V10_CHANNELS, n, n))
         normalised = input_diag and lev == 0
         for ch, (dy, dx), a in zip(_T10, _OFFS[1:], [st.aW, st.aE, st.aS, st.aN]):
-            shifted = _shift_to_source(-omega * a, dy, dx)
+            shifted = _shift_to_source(-omega_l * a, dy, dx)
             s[ch] = shifted if normalised else shifted / st.aC
-        s[_FG10] = (1.0 - omega) * st.aC if normalised else 1.0 - omega
-        s[_FJ10] = omega if normalised else omega / st.aC
+        s[_FG10] = (1.0 - omega_l) * st.aC if normalised else 1.0 - omega_l
+        s[_FJ10] = omega_l if normalised else omega_l / st.aC
         outs.append(s)
     return outs

@@ -133,3 +133,52 @@ def test_paper_gmg_iteration_counts(n):
         assert hist[-1] <= 1e-8
         its.append(it)
     assert abs(np.mean(its) - paper) <= 0.15 * paper, (its, paper)
+
+
+def test_level_omegas_rule():
+    """One weight for every level, or (finest, in between, coarsest)."""
+    assert gmg.level_omegas(3, 0.8) == [0.8, 0.8, 0.8]
+    assert gmg.level_omegas(1, (0.7, 1.3, 1.1)) == [0.7]
+    assert gmg.level_omegas(2, (0.7, 1.3, 1.1)) == [0.7, 1.1]
+    assert gmg.level_omegas(5, (0.7, 1.3, 1.1)) == [0.7, 1.3, 1.3, 1.3, 1.1]
+
+
+def _dense_fw(n: int) -> np.ndarray:
+    """Full weighting as a dense (nc^2 x n^2) matrix: coarse node (J, I) takes
+    fine nodes (2J + a, 2I + b), a, b in {0, 1, 2}, with weights (1 2 1)(1 2 1)^T / 16."""
+    nc = (n - 1) // 2
+    w = np.array([1.0, 2.0, 1.0])
+    R = np.zeros((nc * nc, n * n))
+    for J in range(nc):
+        for I in range(nc):
+            for a in range(3):
+                for b in range(3):
+                    R[J * nc + I, (2 * J + a) * n + 2 * I + b] = w[a] * w[b] / 16.0
+    return R
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 0), (2, 1)])
+def test_vcycle_with_level_weights_equals_the_error_propagation_matrix(nu1, nu2):
+    """With a different Jacobi weight on every level, one V(nu1, nu2) cycle from
+    e = 0 equals (I - E_0) A_0^{-1} r, E the textbook two-grid recursion built
+    from dense matrices: S_l = I - omega_l D_l^{-1} A_l, E_L = S_L^(nu1+nu2) on the
+    coarsest grid, E_l = S_l^nu2 (I - P (I - E_{l+1}) A_{l+1}^{-1} R A_l) S_l^nu1,
+    R full weighting and P = 4 R^T (bilinear interpolation)."""
+    n = 15
+    rng = np.random.default_rng(8)
+    k = np.exp(rng.standard_normal((n + 2, n + 2)))
+    sts = op.level_stencils_div(k, (1.0, -0.5), num_levels(n))
+    oms = [0.7, 1.3, 1.1]
+    assert len(sts) == 3
+    A = [op.dense_matrix(st) for st in sts]
+    S = [np.eye(a.shape[0]) - om * np.diag(1.0 / np.diag(a)) @ a for a, om in zip(A, oms)]
+    E = np.linalg.matrix_power(S[2], nu1 + nu2)
+    for lev in (1, 0):
+        R = _dense_fw(sts[lev].n)
+        P = 4.0 * R.T
+        cgc = np.eye(A[lev].shape[0]) - P @ (np.eye(E.shape[0]) - E) @ np.linalg.solve(A[lev + 1], R @ A[lev])
+        E = np.linalg.matrix_power(S[lev], nu2) @ cgc @ np.linalg.matrix_power(S[lev], nu1)
+    r = rng.standard_normal(n * n)
+    expect = (np.eye(n * n) - E) @ np.linalg.solve(A[0], r)
+    got = gmg.vcycle(sts, r.reshape(n, n), nu1, nu2, oms).ravel()
+    assert np.linalg.norm(got - expect) <= 1e-11 * np.linalg.norm(expect)

@@ -64,6 +64,24 @@ def test_gmg_equivalence_other_sizes_and_sweeps():
         assert np.linalg.norm(e_m - e_g) <= 1e-13 * np.linalg.norm(e_g)
 
 
+
+@pytest.mark.parametrize("input_diag", [False, True])
+def test_networks_with_level_weights_are_gmg_with_level_weights(input_diag):
+    """A Jacobi weight per level (finest 0.8, in between 1.3, coarsest 1.0) in the
+    setup tensors of the 13-channel V(2,1) network and of the 8-channel V(1,0)
+    network gives GMG with the same weight on each level, iterate for iterate."""
+    n = 63
+    sts, f = _problem(n, 71, b=(2.0, -1.0))
+    oms = gmg.level_omegas(len(sts), (0.8, 1.3, 1.0))
+    assert oms[0] == 0.8 and oms[-1] == 1.0 and oms[1] == 1.3
+    for w, s, nu in ((mg.gmg_equivalent_weights(2, 1), mg.gmg_equivalent_setup(sts, oms, input_diag), (2, 1)),
+                     (mg.gmg_v10_weights(), mg.gmg_v10_setup(sts, oms, input_diag), (1, 0))):
+        u_m, it_m, _, its_m = mg.stationary_solve(w, s, sts[0], f, None, 1e-9, 200, input_diag=input_diag)
+        u_g, it_g, _, its_g = gmg.stationary_solve(sts, f, None, 1e-9, 200, *nu, oms)
+        assert it_m == it_g < 200
+        for a, c in zip(its_m[1:], its_g[1:]):
+            assert np.linalg.norm(a - c) <= 1e-12 * np.linalg.norm(c)
+
 def _torch_setup(w, sts, feat):
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a))
     c = F.conv2d(T(feat)[None], T(w["sw_in"]), T(w["sb_in"]), padding=1)

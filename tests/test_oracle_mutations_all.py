@@ -30,7 +30,7 @@ MUTATIONS = {
     "Jacobi without omega": ("gmg.py", "return e + omega * (r - apply(st, e)) / st.aC", "return e + (r - apply(st, e)) / st.aC", GMG),
     "restriction weights /8": ("gmg.py", "FW = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 16.0",
                                "FW = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 8.0", GMG),
-    "no post-smoothing": ("gmg.py", "    for _ in range(nu2):\n        e = jacobi_sweep(st, e, r, omega)\n    return e",
+    "no post-smoothing": ("gmg.py", "    for _ in range(nu2):\n        e = jacobi_sweep(st, e, r, om)\n    return e",
                           "    return e", GMG),
     "conv taps not centred": ("convnet.py", "y += np.tensordot(W[:, :, a, b], xp[:, a:a + n, b:b + m], axes=([1], [0]))",
                               "y += np.tensordot(W[:, :, a, b], xp[:, b:b + n, a:a + m], axes=([1], [0]))", CONV),
@@ -54,8 +54,8 @@ MUTATIONS = {
     "bilinear prolongation /2": ("gmg.py", "BILINEAR = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 4.0",
                                  "BILINEAR = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 2.0], [1.0, 2.0, 1.0]]) / 2.0", GMG),
     "setup features not scale-free": ("mgcnn.py", "np.log10(h * h * st.aC)])", "np.log10(st.aC)])", NET),
-    "V(1,0) setup: 1 + omega": ("mgcnn.py", "s[_FG10] = (1.0 - omega) * st.aC if normalised else 1.0 - omega",
-                                "s[_FG10] = (1.0 + omega) * st.aC if normalised else 1.0 + omega", NET),
+    "V(1,0) setup: 1 + omega": ("mgcnn.py", "s[_FG10] = (1.0 - omega_l) * st.aC if normalised else 1.0 - omega_l",
+                                "s[_FG10] = (1.0 + omega_l) * st.aC if normalised else 1.0 + omega_l", NET),
     "input normalisation multiplies by D": ("mgcnn.py", "rin = r if d_inv is None else r * d_inv",
                                             "rin = r if d_inv is None else r / d_inv", NET),
     "FGMRES update with unpreconditioned directions": ("krylov.py", "u = u + y[i] * Z[i]", "u = u + y[i] * V[i]", KRY),
@@ -65,8 +65,8 @@ MUTATIONS = {
                                 CONV),
     "level rule off by one": ("grid.py", "    return m - 1\n", "    return m\n", OP),
     "GMG-equivalent Jacobi copies not divided by a_C": ("mgcnn.py",
-                                                        "s[_E[k]] = _shift_to_source(-omega * a / st.aC, dy, dx)",
-                                                        "s[_E[k]] = _shift_to_source(-omega * a, dy, dx)", NET),
+                                                        "s[_E[k]] = _shift_to_source(-omega_l * a / st.aC, dy, dx)",
+                                                        "s[_E[k]] = _shift_to_source(-omega_l * a, dy, dx)", NET),
     "GMG-equivalent defect copies with the wrong sign": ("mgcnn.py", "s[_G[k]] = _shift_to_source(-a, dy, dx)",
                                                          "s[_G[k]] = _shift_to_source(a, dy, dx)", NET),
     "adjoint: s gradient drops x": ("adjoint.py", "sbar_l += x_in * t", "sbar_l += t", ADJ),
@@ -91,6 +91,16 @@ MUTATIONS = {
     "setup bias outside the tanh": ("mgcnn.py", "t = np.tanh(cn.conv_same(z, weights[\"sw\"][i], weights[\"sb\"][i]))",
                                     "t = np.tanh(cn.conv_same(z, weights[\"sw\"][i])) + weights[\"sb\"][i][:, None, None]",
                                     SETUP),
+    "coarsest level takes the in-between weight": ("gmg.py", "return [w_fine] + [w_mid] * (levels - 2) + [w_coarsest]",
+                                                   "return [w_fine] + [w_mid] * (levels - 1)", GMG),
+    "V-cycle smooths every level with the finest weight": ("gmg.py", "om = _omega_at(omega, level)",
+                                                           "om = _omega_at(omega, 0)", GMG),
+    "V(1,0) setup uses the finest weight on every level": (
+        "mgcnn.py", "omega_l = _level_weight(omega, lev)\n        n = st.n\n        s = np.zeros((V10_CHANNELS",
+        "omega_l = _level_weight(omega, 0)\n        n = st.n\n        s = np.zeros((V10_CHANNELS", NET),
+    "GMG-equivalent setup uses the finest weight on every level": (
+        "mgcnn.py", "omega_l = _level_weight(omega, lev)\n        n = st.n\n        s = np.zeros((GMG_CHANNELS",
+        "omega_l = _level_weight(omega, 0)\n        n = st.n\n        s = np.zeros((GMG_CHANNELS", NET),
 }
 
 
