@@ -90,6 +90,25 @@ def network(kind: str):
     return 8, 1, 1, np.ascontiguousarray(blob, dtype=np.float64), False
 
 
+def parse_omega(text: str):
+    """'0.8' -> 0.8 (every level); '0.8,1.5,1.0' -> (finest, in between, coarsest)."""
+    parts = [float(x) for x in str(text).split(",")]
+    if len(parts) == 1:
+        return parts[0]
+    if len(parts) != 3:
+        raise SystemExit("--omega takes one weight or three (finest,in-between,coarsest)")
+    return tuple(parts)
+
+
+def omega_record(omega, net: str):
+    """The Jacobi weights of the analytic network, as the bench line records them."""
+    if net not in ("gmg", "gmg_v10"):
+        return None
+    if isinstance(omega, tuple):
+        return {"finest": omega[0], "in_between": omega[1], "coarsest": omega[2]}
+    return omega
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
@@ -222,12 +241,14 @@ def sm_pipes_record(kernel: str, workload: str):
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def _oracle_net(net, sts):
+def _oracle_net(net, sts, omega=0.8):
+    import oracle.gmg as ogmg
     import oracle.mgcnn as omg
+    oms = ogmg.level_omegas(len(sts), omega)
     if net == "gmg":
-        return omg.gmg_equivalent_weights(2, 2), omg.gmg_equivalent_setup(sts, 0.8), False
+        return omg.gmg_equivalent_weights(2, 2), omg.gmg_equivalent_setup(sts, oms), False
     if net == "gmg_v10":
-        return omg.gmg_v10_weights(), omg.gmg_v10_setup(sts, 0.8), False
+        return omg.gmg_v10_weights(), omg.gmg_v10_setup(sts, oms), False
     w = unpack_blob(np.load(TRAINED), 8, 1, 1)
     return w, omg.setup(w, sts, scale_by_diag=False), True
 
@@ -237,7 +258,7 @@ def _oracle_solve(job):
     (timed) the operators on every level, the network's setup and the stationary
     iteration from u = 0 to ||f - A u|| / ||f|| <= tol.  Returns (seconds, cycles,
     final relative residual)."""
-    workload, net, n, seed, tol = job
+    workload, net, n, seed, tol, omega = job
     import oracle.mgcnn as omg
     import oracle.operator as oop
     from oracle.grid import num_levels
@@ -245,7 +266,7 @@ def _oracle_solve(job):
     m = n + 2
     t0 = time.perf_counter()
     sts = oop.level_stencils_div(k.reshape(m, m), b, num_levels(n))
-    w, s, diag = _oracle_net(net, sts)
+    w, s, diag = _oracle_net(net, sts, omega)
     _, iters, hist, _ = omg.stationary_solve(w, s, sts[0], f.reshape(n, n), None, tol, 300, input_diag=diag)
     return time.perf_counter() - t0, int(iters), float(hist[-1])
 
@@ -255,7 +276,7 @@ def host_cores() -> int:
 
 
 def cpu_reference(workload: str, net: str, n_full: int = 4095, n_sample: int = 1023, count: int | None = None,
-                  tol: float = 1e-6, seed0: int = 500):
+                  tol: float = 1e-6, seed0: int = 500, omega=0.8):
     """The FP64 oracle timed on this host's cores: `count` complete solves of the same
     workload family at n_sample^2 (each its own seeded problem), run one per core in
     spawned worker processes (one BLAS thread each), wall clock around all of them.
@@ -266,12 +287,12 @@ def cpu_reference(workload: str, net: str, n_full: int = 4095, n_sample: int = 1
     cores = host_cores()
     count = count or cores
     workers = max(1, min(count, cores))
-    jobs = [(workload, net, n_sample, seed0 + i, tol) for i in range(count)]
+    jobs = [(workload, net, n_sample, seed0 + i, tol, omega) for i in range(count)]
     saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     os.environ.update({v: "1" for v in saved})      # inherited by the workers only
     try:
         with mp.get_context("spawn").Pool(workers) as pool:
-            pool.map(_oracle_solve, [(workload, net, 31, 1, tol)] * workers)   # start-up, untimed
+            pool.map(_oracle_solve, [(workload, net, 31, 1, tol, omega)] * workers)   # start-up, untimed
             t0 = time.perf_counter()
             res = pool.map(_oracle_solve, jobs, chunksize=1)
             wall = time.perf_counter() - t0
@@ -376,6 +397,8 @@ def main():
     ap.add_argument("--coarse-tail", type=int, default=-1,
                     help="largest grid side of the coarse levels run as one cooperative kernel "
                          "(0: a launch per level; -1: the library default)")
+    ap.add_argument("--omega", default="0.8,1.5,1.0",
+                    help="Jacobi weight(s) of the analytic networks: one for every level, or finest,in-between,coarsest")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -385,6 +408,7 @@ def main():
                     help="also time CG with the symmetric network in its BPX form (same k field, b = 0, FP64, tol 1e-8)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.omega = parse_omega(args.omega)
     net = args.net or ("trained" if os.path.exists(TRAINED) else "gmg_v10")
     workload = args.workload or "grf"
     args.net_resolved = net
@@ -399,14 +423,15 @@ def main():
         t0 = time.perf_counter()
         # each step is one complete oracle solve at 1023^2, run one per host core
         ns = min(args.n, 1023)
-        base = cpu_reference(workload, net, args.n, n_sample=ns, count=args.steps, tol=args.tol)
+        base = cpu_reference(workload, net, args.n, n_sample=ns, count=args.steps, tol=args.tol, omega=args.omega)
         wall = base["measured"]["wall_s"]
         v = base["value"]
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
                           "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * wall / args.steps,
                           "step": f"one complete FP64 oracle solve at {ns}^2 (steps run concurrently, one per core)",
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": f"{workload}_{args.n}", "net": net, "tol": args.tol},
+                          "data": "synthetic", "config": {"workload": f"{workload}_{args.n}", "net": net, "tol": args.tol,
+                                     "omega": omega_record(args.omega, net)},
                           "cpu_baseline": base,
                           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                           "wall_s": time.perf_counter() - t0}))
@@ -444,7 +469,7 @@ def main():
 
     def step(sv, k, f, u):
         if is_gmg:
-            sv.setup_gmg(k, n, 0.8)
+            sv.setup_gmg(k, n, args.omega)
         else:
             sv.setup(k, n)
         if isinstance(u, np.ndarray):
@@ -500,7 +525,7 @@ def main():
 
     # solve-only time (setup excluded), as the paper splits them
     if is_gmg:
-        sv.setup_gmg(k_d, n, 0.8)
+        sv.setup_gmg(k_d, n, args.omega)
     else:
         sv.setup(k_d, n)
     torch.cuda.synchronize(dev)
@@ -522,7 +547,7 @@ def main():
 
     def e2e_step(u):
         if is_gmg:
-            sv.setup_gmg(k_p, n, 0.8)
+            sv.setup_gmg(k_p, n, args.omega)
         else:
             sv.setup(k_p, n)
         return sv.solve(f_p, u, tol, 300)
@@ -566,7 +591,8 @@ def main():
     result = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-              "config": {"workload": f"{workload}_{n}", "n": n, "tol": tol, "net": net, "channels": C,
+              "config": {"workload": f"{workload}_{n}", "n": n, "tol": tol, "net": net, "omega": omega_record(args.omega, net),
+                         "channels": C,
                          "down_layers": nd, "up_layers": nu, "b": list(b), "l2": "inputs larger than L2",
                          "tile": "autotuned" if args.tile < 0 else ["16x32", "8x32", "16x16", "32x32", "24x32", "24x30 up, 24x32 down",
                                                       "32x30 up, 24x32 down", "22x30 up, 24x32 down"][args.tile],
@@ -589,19 +615,30 @@ def main():
                           "mixed_vs_fp64_rel_err": err, "mixed_speedup": value / world * t64}
         sv64.close()
     if not args.no_fp64 and rank == 0:
-        # classical GMG comparator (Sec. 2.3): FP64 V(2,2), omega 0.8, same operators and tolerance
+        # classical GMG comparator (Sec. 2.3): FP64 V(2,2), omega 0.8, same operators and tolerance;
+        # beside it the same cycle with the per-level weights of the analytic network
         svg = make_solver("fp64")
         svg.setup_gmg(k_d, n, 0.8) if is_gmg else svg.setup(k_d, n)
         ug = torch.zeros_like(u_d)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        try:
-            stg, itg, hg = svg.gmg_solve(f_d, ug, tol, 300, 2, 2, 0.8)
-            tg = time.perf_counter() - t0
-            result["gmg"] = {"value": 1.0 / tg, "unit": "solves/s", "iters": itg, "relres": float(hg[-1]),
-                             "converged": bool(stg == mgcnn.OK), "cycle": "V(2,2) weighted Jacobi 0.8, FP64"}
-        except mgcnn.MGCNNError as err:
-            result["gmg"] = {"converged": False, "error": str(err)[:120], "cycle": "V(2,2) weighted Jacobi 0.8, FP64"}
+        gmg_runs = [("gmg", 0.8, "V(2,2) weighted Jacobi 0.8, FP64")]
+        if isinstance(args.omega, tuple):
+            gmg_runs.append(("gmg_levels", args.omega, "V(2,2) weighted Jacobi %g finest, %g in between, %g coarsest, "
+                                                       "FP64" % args.omega))
+        for key, om, cycle in gmg_runs:
+            try:                       # untimed first call: allocates the comparator's level buffers
+                svg.gmg_solve(f_d, ug, tol, 2, 2, 2, om)
+            except mgcnn.MGCNNError:
+                pass
+            ug.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            try:
+                stg, itg, hg = svg.gmg_solve(f_d, ug, tol, 300, 2, 2, om)
+                tg = time.perf_counter() - t0
+                result[key] = {"value": 1.0 / tg, "unit": "solves/s", "iters": itg, "relres": float(hg[-1]),
+                               "converged": bool(stg == mgcnn.OK), "cycle": cycle}
+            except mgcnn.MGCNNError as err:
+                result[key] = {"converged": False, "error": str(err)[:120], "cycle": cycle}
         svg.close()
     if args.krylov and rank == 0:
         # the same network as the preconditioner of flexible GMRES(30), same tolerance
@@ -609,7 +646,7 @@ def main():
 
         def kstep():
             if is_gmg:
-                sv.setup_gmg(k_d, n, 0.8)
+                sv.setup_gmg(k_d, n, args.omega)
             else:
                 sv.setup(k_d, n)
             uk.zero_()
@@ -674,11 +711,11 @@ def main():
         # families, and the channelised field at 4095^2 (FP64 MGCNN, mixed MGCNN,
         # GMG, per-level achieved bandwidth)
         result["batched"] = run_batched(args, rank, world, dev, mgcnn, quiet=True)
-        result["channelised"] = run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol)
+        result["channelised"] = run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, args.omega)
         result["setup_network"] = time_setup_network(n, dev, stream, mgcnn, k_d, b)
     if not args.no_cpu and rank == 0 and world == 1:
         # one wave of complete oracle solves at 511^2, one per host core (about 15-30 s)
-        result["cpu_baseline"] = cpu_reference(workload, net, n, n_sample=min(n, 511), tol=tol)
+        result["cpu_baseline"] = cpu_reference(workload, net, n, n_sample=min(n, 511), tol=tol, omega=args.omega)
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
@@ -722,7 +759,7 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
     sv.set_weights(blob)
 
     def step(kk, ff, uu):
-        sv.setup_batched(kk, ns, gmg_omega=0.8 if is_gmg else None)
+        sv.setup_batched(kk, ns, gmg_omega=args.omega if is_gmg else None)
         for u in uu:
             u.zero_() if hasattr(u, "zero_") else u.fill(0.0)
         return sv.solve_batched(ff, uu, args.tol, args.maxit, per_problem=True)
@@ -758,7 +795,7 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
     ups = [[pinned_zeros(n * n, dev) for n in ns] for _ in range(e2e_steps + 1)]
 
     def e2e_step(uu):
-        sv.setup_batched(kp, ns, gmg_omega=0.8 if is_gmg else None)
+        sv.setup_batched(kp, ns, gmg_omega=args.omega if is_gmg else None)
         return sv.solve_batched(fp, uu, args.tol, args.maxit, per_problem=True)
     e2e_step(ups[-1])
     barrier()
@@ -777,7 +814,8 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
            "config": {"workload": f"batched{args.batch}_63-1023_mixture", "problems": args.batch,
-                      "unknowns": unknowns, "tol": args.tol, "net": net, "maxit": args.maxit,
+                      "unknowns": unknowns, "tol": args.tol, "net": net, "omega": omega_record(args.omega, net),
+                      "maxit": args.maxit,
                       "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single"},
            "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
            "converged": done, "failed": int((stat != 0).sum()),
@@ -815,7 +853,7 @@ def time_setup_network(n, dev, stream, mgcnn, k_d, b, reps=5):
             "what": "mgcnn_setup at %d^2: operators on every level plus the setup network, random weights" % n}
 
 
-def run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, maxit=60):
+def run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, omega, maxit=60):
     """The channelised binary field (k in {1, 1e3}) at n^2: the mixed and the FP64
     MGCNN (same network) and classical GMG V(2,2), each from u = 0 for at most
     `maxit` cycles; per-level CUDA-event times and algorithmic GB/s of the mixed
@@ -830,7 +868,7 @@ def run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, maxit=6
     def run(prec):
         sv = mgcnn.Solver(C, nd, nu, precision=prec, b=b, stream=stream)
         sv.set_weights(blob)
-        sv.setup_gmg(k_d, n, 0.8) if is_gmg else sv.setup(k_d, n)
+        sv.setup_gmg(k_d, n, omega) if is_gmg else sv.setup(k_d, n)
         u = torch.zeros(n * n, dtype=torch.float64, device=dev)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()

@@ -589,28 +589,39 @@ int mgcnn_setup(mgcnn_ctx* c, const double* coeff, int n) {
   return finish(c, do_setup(c, coeff, n));
 }
 
+namespace {
+
+Status setup_gmg_levels(mgcnn_ctx* c, const double* coeff, int n, const LevelWeights& omega) {
+  const bool v10 = c->cfg.channels == kGmgV10Channels && c->cfg.down_layers == 1 && c->cfg.up_layers == 1;
+  if (c->cfg.channels != kGmgChannels && !v10)
+    return make_status(MGCNN_ERR_SIZE, "GMG-equivalent setup needs %d channels, or %d channels with one down "
+                       "and one up layer", kGmgChannels, kGmgV10Channels);
+  if (!omega.valid()) return make_status(MGCNN_ERR_ARG, "every Jacobi weight must be in (0, 2)");
+  MG_TRY(setup_operators(c, coeff, n));
+  for (int l = 0; l < c->L; ++l) {
+    const double w = omega.at(l, c->L);
+    if (c->cfg.precision == MGCNN_PREC_FP64)
+      MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->s64[l].as<double>(), c->lv[l].n, w, c->stream,
+                              l == 0 && c->cfg.input_diag, c->cfg.channels));
+    else
+      MG_TRY(mixed_gmg_setup_level(c, l, w));
+  }
+  // no synchronisation, as in do_setup
+  MG_CUDA(cudaGetLastError());
+  c->have_setup = true;
+  return {};
+}
+
+}  // namespace
+
 int mgcnn_setup_gmg(mgcnn_ctx* c, const double* coeff, int n, double omega) {
   if (!c || !coeff) return MGCNN_ERR_ARG;
-  Status st = [&]() -> Status {
-    const bool v10 = c->cfg.channels == kGmgV10Channels && c->cfg.down_layers == 1 && c->cfg.up_layers == 1;
-    if (c->cfg.channels != kGmgChannels && !v10)
-      return make_status(MGCNN_ERR_SIZE, "GMG-equivalent setup needs %d channels, or %d channels with one down "
-                         "and one up layer", kGmgChannels, kGmgV10Channels);
-    if (!(omega > 0.0 && omega < 2.0)) return make_status(MGCNN_ERR_ARG, "omega must be in (0, 2)");
-    MG_TRY(setup_operators(c, coeff, n));
-    for (int l = 0; l < c->L; ++l) {
-      if (c->cfg.precision == MGCNN_PREC_FP64)
-        MG_TRY(launch_gmg_setup(c->op[l].as<double>(), c->s64[l].as<double>(), c->lv[l].n, omega, c->stream,
-                                l == 0 && c->cfg.input_diag, c->cfg.channels));
-      else
-        MG_TRY(mixed_gmg_setup_level(c, l, omega));
-    }
-    // no synchronisation, as in do_setup
-    MG_CUDA(cudaGetLastError());
-    c->have_setup = true;
-    return {};
-  }();
-  return finish(c, st);
+  return finish(c, setup_gmg_levels(c, coeff, n, LevelWeights::uniform(omega)));
+}
+
+int mgcnn_setup_gmg_levels(mgcnn_ctx* c, const double* coeff, int n, const double* omega) {
+  if (!c || !coeff || !omega) return MGCNN_ERR_ARG;
+  return finish(c, setup_gmg_levels(c, coeff, n, LevelWeights{omega[0], omega[1], omega[2]}));
 }
 
 int mgcnn_setup_bpx(mgcnn_ctx* c, const double* coeff, int n, double omega) {
@@ -978,8 +989,17 @@ int mgcnn_check_wait_timeout(mgcnn_ctx* c) {
 
 int mgcnn_setup_batched_gmg(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* n, double omega) {
   if (!c || !coeff || !n) return MGCNN_ERR_ARG;
-  if (!(omega > 0.0 && omega < 2.0)) return finish(c, make_status(MGCNN_ERR_ARG, "omega must be in (0, 2)"));
-  return finish(c, setup_batched(c, nprob, coeff, n, omega));
+  const LevelWeights w = LevelWeights::uniform(omega);
+  if (!w.valid()) return finish(c, make_status(MGCNN_ERR_ARG, "omega must be in (0, 2)"));
+  return finish(c, setup_batched(c, nprob, coeff, n, &w));
+}
+
+int mgcnn_setup_batched_gmg_levels(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* n,
+                                   const double* omega) {
+  if (!c || !coeff || !n || !omega) return MGCNN_ERR_ARG;
+  const LevelWeights w{omega[0], omega[1], omega[2]};
+  if (!w.valid()) return finish(c, make_status(MGCNN_ERR_ARG, "every Jacobi weight must be in (0, 2)"));
+  return finish(c, setup_batched(c, nprob, coeff, n, &w));
 }
 
 int mgcnn_solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol, int maxit,
@@ -988,10 +1008,12 @@ int mgcnn_solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, doubl
   return finish(c, solve_batched(c, nprob, rhs, u, tol, maxit, iters, relres, status));
 }
 
-int mgcnn_gmg_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int nu1, int nu2, double omega,
-                    int* iters, double* relres) {
+namespace {
+
+int gmg_solve_levels(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int nu1, int nu2,
+                     const LevelWeights& omega, int* iters, double* relres) {
   if (!c || !f || !u || !iters || maxit < 0 || !(tol >= 0.0) || nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 ||
-      !(omega > 0.0 && omega < 2.0))
+      !omega.valid())
     return MGCNN_ERR_ARG;
   *iters = 0;
   Status st = [&]() -> Status {
@@ -1052,6 +1074,19 @@ int mgcnn_gmg_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int ma
     return result;
   }();
   return finish(c, st);
+}
+
+}  // namespace
+
+int mgcnn_gmg_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int nu1, int nu2, double omega,
+                    int* iters, double* relres) {
+  return gmg_solve_levels(c, f, u, tol, maxit, nu1, nu2, LevelWeights::uniform(omega), iters, relres);
+}
+
+int mgcnn_gmg_solve_levels(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int nu1, int nu2,
+                           const double* omega, int* iters, double* relres) {
+  if (!omega) return MGCNN_ERR_ARG;
+  return gmg_solve_levels(c, f, u, tol, maxit, nu1, nu2, LevelWeights{omega[0], omega[1], omega[2]}, iters, relres);
 }
 
 int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {

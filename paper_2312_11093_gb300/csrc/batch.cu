@@ -182,9 +182,9 @@ Status batched_setup_net(mgcnn_ctx* c, BatchClass& k) {
   return {};
 }
 
-// omega > 0: the analytic setup tensors of the 8-channel GMG V(1, 0) network
-// instead of the setup network.
-Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, double omega) {
+// omega non-null: the analytic setup tensors of the 8-channel GMG V(1, 0)
+// network (level l's Jacobi weight omega->at(l, L)) instead of the setup network.
+Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, const LevelWeights* omega) {
   const int C = c->cfg.channels;
   const int m0 = k.n + 2;
   const size_t N0 = (size_t)k.n * k.n;
@@ -239,9 +239,9 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, doub
     if (l + 1 < k.L) MG_TRY(launch_restrict_k(kh[l & 1], kh[(l + 1) & 1], k.nl[l] + 2, st, k.B));
   }
   MG_TRY(launch_diag_inverse(k.op[0].as<double>(), nullptr, k.dinv32.as<float>(), N0, st, k.B));
-  if (omega > 0.0) {
+  if (omega) {
     for (int l = 0; l < k.L; ++l)
-      MG_TRY(launch_gmg_v10_setup_bf16(k.op[l].as<double>(), k.s16[l].as<bf16>(), k.nl[l], omega, st,
+      MG_TRY(launch_gmg_v10_setup_bf16(k.op[l].as<double>(), k.s16[l].as<bf16>(), k.nl[l], omega->at(l, k.L), st,
                                        l == 0 && c->cfg.input_diag, k.B));
   } else if (c->fused) {
     const double* ops[kMaxLevels];
@@ -443,7 +443,7 @@ void batch_release(mgcnn_ctx* c) {
   c->bready = false;
 }
 
-Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* ns, double omega) {
+Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* ns, const LevelWeights* omega) {
   if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
   if (c->cfg.precision != MGCNN_PREC_MIXED_BF16 || !fused_supported(c) || c->cfg.pde != MGCNN_PDE_DIV_HARMONIC)
     return make_status(MGCNN_ERR_SIZE, "batched solves need MIXED_BF16, 8 channels, one layer per ResNet, "

@@ -30,8 +30,10 @@ struct BatchClass {
 };
 
 void batch_release(mgcnn_ctx* c);
-// omega > 0: analytic setup tensors of the 8-channel GMG V(1, 0) network (Jacobi weight omega)
-Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* ns, double omega = 0.0);
+// omega non-null: analytic setup tensors of the 8-channel GMG V(1, 0) network
+// (Jacobi weights per level) instead of the setup network
+Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const int* ns,
+                     const LevelWeights* omega = nullptr);
 Status solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol, int maxit,
                      int* iters, double* relres, int* status);
 

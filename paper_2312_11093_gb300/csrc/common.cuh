@@ -64,6 +64,21 @@ struct Level {
   size_t N() const { return (size_t)n * n; }
 };
 
+// Jacobi weights of the analytic (GMG-equivalent) setup tensors: `fine` on the
+// finest level, `coarsest` on the coarsest, `mid` on every level in between; a
+// one-level hierarchy takes `fine` (weighted Jacobi of Sec. 2.3 with the weight
+// chosen per level).
+struct LevelWeights {
+  double fine = 0.0, mid = 0.0, coarsest = 0.0;
+  static LevelWeights uniform(double w) { return {w, w, w}; }
+  bool valid() const {
+    for (double w : {fine, mid, coarsest})
+      if (!(w > 0.0 && w < 2.0)) return false;
+    return true;
+  }
+  double at(int l, int L) const { return l == 0 ? fine : (l == L - 1 ? coarsest : mid); }
+};
+
 class TmaMaps;   // tma.cuh
 
 // FP32 weights of the fused down kernel's input layer W_in (8 channels), passed

@@ -105,7 +105,9 @@ Status launch_bpx_setup(const double* op, double* out, int n, int level, double 
 }
 
 // One V(nu1, nu2) cycle on level l for A_l e = r_l from e = 0; the result is in e[l].
-Status gmg_vcycle(const GmgLevels& g, int l, int nu1, int nu2, double omega, cudaStream_t st) {
+// Level l smooths with the weight omega.at(l, g.L).
+Status gmg_vcycle(const GmgLevels& g, int l, int nu1, int nu2, const LevelWeights& omegas, cudaStream_t st) {
+  const double omega = omegas.at(l, g.L);
   const int n = g.n[l];
   const size_t N = (size_t)n * n;
   const int grid = grid_for(N, 256);
@@ -124,7 +126,7 @@ Status gmg_vcycle(const GmgLevels& g, int l, int nu1, int nu2, double omega, cud
     const int nc = g.n[l + 1];
     defect_restrict_kernel<<<grid_for((size_t)nc * nc, 256), 256, 0, st>>>(g.op[l], g.r[l], e, g.r[l + 1], n);
     MG_LAUNCH("defect_restrict_kernel");
-    MG_TRY(gmg_vcycle(g, l + 1, nu1, nu2, omega, st));
+    MG_TRY(gmg_vcycle(g, l + 1, nu1, nu2, omegas, st));
     prolong_add_kernel<<<grid, 256, 0, st>>>(g.e[l + 1], e, n);
     MG_LAUNCH("prolong_add_kernel");
     for (int s = 0; s < nu2; ++s) {

@@ -14,6 +14,7 @@ struct GmgLevels {
   double* t[kMaxLevels] = {};          // Jacobi ping-pong
 };
 
-Status gmg_vcycle(const GmgLevels& g, int l, int nu1, int nu2, double omega, cudaStream_t st);
+// level l smooths with weight omega.at(l, g.L)
+Status gmg_vcycle(const GmgLevels& g, int l, int nu1, int nu2, const LevelWeights& omega, cudaStream_t st);
 
 }  // namespace mgcnn

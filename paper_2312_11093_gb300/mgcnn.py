@@ -57,6 +57,7 @@ def load() -> ctypes.CDLL:
         "mgcnn_set_weights": (c_int, [c_void_p, c_void_p, c_size_t]),
         "mgcnn_setup": (c_int, [c_void_p, c_void_p, c_int]),
         "mgcnn_setup_gmg": (c_int, [c_void_p, c_void_p, c_int, c_double]),
+        "mgcnn_setup_gmg_levels": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
         "mgcnn_setup_tensor_count": (c_size_t, [c_void_p]),
         "mgcnn_set_setup_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
         "mgcnn_get_setup_tensors": (c_int, [c_void_p, c_void_p, c_size_t]),
@@ -71,8 +72,11 @@ def load() -> ctypes.CDLL:
         "mgcnn_set_option": (c_int, [c_void_p, c_int, c_int]),
         "mgcnn_gmg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_int, c_double,
                                     POINTER(c_int), c_void_p]),
+        "mgcnn_gmg_solve_levels": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_int, c_void_p,
+                                    POINTER(c_int), c_void_p]),
         "mgcnn_setup_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
         "mgcnn_setup_batched_gmg": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double]),
+        "mgcnn_setup_batched_gmg_levels": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
         "mgcnn_check_wait_timeout": (c_int, [c_void_p]),
         "mgcnn_solve_krylov": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_void_p]),
         "mgcnn_setup_bpx": (c_int, [c_void_p, c_void_p, c_int, c_double]),
@@ -92,6 +96,14 @@ def load() -> ctypes.CDLL:
         fn.argtypes = args
     _lib = L
     return L
+
+
+def _level_weights(omega) -> np.ndarray:
+    """(finest, in between, coarsest) Jacobi weights as 3 contiguous doubles."""
+    w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).ravel())
+    if w.size != 3:
+        raise ValueError("per-level Jacobi weights are (finest, in between, coarsest)")
+    return w
 
 
 def _ptr(a, n: int | None = None, writable: bool = False) -> int:
@@ -288,9 +300,17 @@ class Solver:
         self._check(self._L.mgcnn_setup(self._h, _ptr(coeff), int(n)), "mgcnn_setup")
         self.n = int(n)
 
-    def setup_gmg(self, coeff, n: int, omega: float = 0.8):
-        """Operators + analytic GMG-equivalent setup tensors (needs channels == 13)."""
-        self._check(self._L.mgcnn_setup_gmg(self._h, _ptr(coeff), int(n), float(omega)), "mgcnn_setup_gmg")
+    def setup_gmg(self, coeff, n: int, omega=0.8):
+        """Operators + analytic GMG-equivalent setup tensors (13 channels, or the
+        8-channel V(1,0) network).  omega: one Jacobi weight, or three (finest
+        level, levels in between, coarsest level)."""
+        if np.ndim(omega) == 0:
+            st = self._L.mgcnn_setup_gmg(self._h, _ptr(coeff), int(n), float(omega))
+            self._check(st, "mgcnn_setup_gmg")
+        else:
+            w = _level_weights(omega)
+            self._check(self._L.mgcnn_setup_gmg_levels(self._h, _ptr(coeff), int(n), w.ctypes.data),
+                        "mgcnn_setup_gmg_levels")
         self.n = int(n)
 
     # -- training (Sec. 3.4) ---------------------------------------------------
@@ -328,29 +348,42 @@ class Solver:
         self._check(self._L.mgcnn_get_weights(self._h, w.ctypes.data, w.size), "mgcnn_get_weights")
         return w
 
-    def gmg_solve(self, f, u, tol: float, maxit: int, nu1: int = 2, nu2: int = 2, omega: float = 0.8):
+    def gmg_solve(self, f, u, tol: float, maxit: int, nu1: int = 2, nu2: int = 2, omega=0.8):
         """Classical GMG V(nu1, nu2) on this context's operators, in place on u.
+        omega: one Jacobi weight, or three (finest, in between, coarsest).
         Returns (status, iters, relres[0..iters])."""
         N = self.n * self.n
         it = c_int(0)
         hist = np.zeros(maxit + 1)
-        st = self._L.mgcnn_gmg_solve(self._h, _ptr(f, N), _ptr(u, N, True), float(tol), int(maxit), int(nu1),
-                                     int(nu2), float(omega), ctypes.byref(it), hist.ctypes.data)
-        self._check(st, "mgcnn_gmg_solve", ok=(OK, NOT_CONVERGED))
+        if np.ndim(omega) == 0:
+            name = "mgcnn_gmg_solve"
+            st = self._L.mgcnn_gmg_solve(self._h, _ptr(f, N), _ptr(u, N, True), float(tol), int(maxit), int(nu1),
+                                         int(nu2), float(omega), ctypes.byref(it), hist.ctypes.data)
+        else:
+            name = "mgcnn_gmg_solve_levels"
+            w = _level_weights(omega)
+            st = self._L.mgcnn_gmg_solve_levels(self._h, _ptr(f, N), _ptr(u, N, True), float(tol), int(maxit),
+                                                int(nu1), int(nu2), w.ctypes.data, ctypes.byref(it), hist.ctypes.data)
+        self._check(st, name, ok=(OK, NOT_CONVERGED))
         return st, it.value, hist[: it.value + 1]
 
     # -- batched solves -----------------------------------------------------------
-    def setup_batched(self, coeffs, ns, gmg_omega: float | None = None):
+    def setup_batched(self, coeffs, ns, gmg_omega=None):
         """coeffs[i]: nodal k of problem i ((n_i+2)^2 doubles), ns[i] = n_i.  With
-        gmg_omega, the analytic setup of the 8-channel GMG V(1,0) network."""
+        gmg_omega (one Jacobi weight, or finest / in between / coarsest), the
+        analytic setup of the 8-channel GMG V(1,0) network."""
         m = len(coeffs)
         kp = (c_void_p * m)(*[_ptr(k, (n + 2) * (n + 2)) for k, n in zip(coeffs, ns)])
         nn = (c_int * m)(*[int(n) for n in ns])
         if gmg_omega is None:
             self._check(self._L.mgcnn_setup_batched(self._h, m, kp, nn), "mgcnn_setup_batched")
-        else:
+        elif np.ndim(gmg_omega) == 0:
             self._check(self._L.mgcnn_setup_batched_gmg(self._h, m, kp, nn, float(gmg_omega)),
                         "mgcnn_setup_batched_gmg")
+        else:
+            w = _level_weights(gmg_omega)
+            self._check(self._L.mgcnn_setup_batched_gmg_levels(self._h, m, kp, nn, w.ctypes.data),
+                        "mgcnn_setup_batched_gmg_levels")
         self.batch_sizes = [int(n) for n in ns]
 
     def solve_batched(self, rhs, us, tol: float, maxit: int, per_problem: bool = False):

@@ -147,6 +147,31 @@ def test_batched_gmg_v10_equals_single_solves_and_converges(M):
         assert np.linalg.norm(r) / np.linalg.norm(fs[i]) <= 1.01e-6
 
 
+
+def test_batched_level_weights_equal_single_solves(M):
+    """Batched setup with per-level Jacobi weights (finest, in between, coarsest):
+    each problem gets the weights on its own hierarchy, so every iterate equals the
+    single-problem solve with mgcnn_setup_gmg_levels bit for bit."""
+    sizes = [63, 255, 31, 127, 63]
+    rng = np.random.default_rng(19)
+    ks = [np.ascontiguousarray(inputs.lognormal_k(n, 0.1, rng).ravel()) for n in sizes]
+    fs = [np.ascontiguousarray(inputs.normal_rhs(n, rng).ravel()) for n in sizes]
+    om = (0.8, 1.5, 1.0)
+    w = M.gmg_v10_weights()
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(w)
+    sv.setup_batched(ks, sizes, gmg_omega=om)
+    us = [np.zeros(n * n) for n in sizes]
+    st, iters, relres, stat = sv.solve_batched(fs, us, 1e-6, 200)
+    assert st == M.OK and (stat == M.OK).all()
+    for i, n in enumerate(sizes):
+        one = M.Solver(8, 1, 1, precision="mixed_bf16")
+        one.set_weights(w)
+        one.setup_gmg(ks[i], n, om)
+        u1 = np.zeros(n * n)
+        st1, it1, h1 = one.solve(fs[i].copy(), u1, 1e-6, 200)
+        assert it1 == iters[i] and np.array_equal(u1, us[i]), i
+
 @pytest.mark.parametrize("cfg", [(0, True), (1, False)])
 def test_batched_first_cycle_against_the_oracle(M, cfg):
     """Every problem of an uneven batch over the three coefficient families, one

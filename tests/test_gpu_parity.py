@@ -422,6 +422,98 @@ def test_v10_fused_mixed_reaches_1e8_in_fp64(M, n):
     assert its["mixed_bf16"] <= its["fp64"] + 3
 
 
+
+# ---- a Jacobi weight per level (finest, in between, coarsest) -----------------
+LEVEL_OMEGA = (0.8, 1.5, 1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
+def test_level_weights_setup_matches_oracle(M, precision):
+    """mgcnn_setup_gmg_levels builds each level's V(1,0) tensors with that level's
+    weight: the oracle's tensors for the per-level list (BF16: one rounding)."""
+    n = 63
+    k, f = problem(n, 44)
+    b = (0.7, -1.2)
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    s_ref = to_nhwc(omg.gmg_v10_setup(sts, ogmg.level_omegas(len(sts), LEVEL_OMEGA), input_diag=True))
+    sv = M.Solver(8, 1, 1, precision=precision, b=b)
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_gmg(k.ravel().copy(), n, LEVEL_OMEGA)
+    got = sv.get_setup_tensors()
+    if precision == "fp64":
+        assert relerr(got, s_ref) <= 1e-15
+    else:
+        assert np.all(np.abs(got - s_ref) <= 2.0 ** -8 * np.abs(s_ref))
+
+
+@pytest.mark.parametrize("channels,nu", [(8, (1, 0)), (13, (2, 2))])
+def test_level_weights_fp64_iterate_for_iterate(M, channels, nu):
+    """FP64 path with per-level weights (V(1,0) 8-channel and V(2,2) 13-channel
+    networks): the oracle GMG's iteration count with the same weights, every
+    cycle within 1e-12 of the oracle's on the oracle's own iterate."""
+    n = 127
+    k, f = problem(n, 45)
+    b = (1.0, 0.5)
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    oms = ogmg.level_omegas(len(sts), LEVEL_OMEGA)
+    u_o, it_o, hist_o, its_o = ogmg.stationary_solve(sts, f, None, 1e-8, 200, *nu, oms)
+    if channels == 8:
+        sv = M.Solver(8, 1, 1, precision="fp64", b=b)
+        sv.set_weights(M.gmg_v10_weights())
+    else:
+        sv = M.Solver(13, nu[0] + 1, nu[1], precision="fp64", b=b)
+        sv.set_weights(M.gmg_weights(*nu))
+    sv.setup_gmg(k.ravel().copy(), n, LEVEL_OMEGA)
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(f.ravel().copy(), u, 1e-8, 200)
+    assert st == M.OK and it == it_o
+    assert relerr(u, u_o) <= 1e-12
+    for k_ in range(0, it_o, 4):
+        r = f - oop.apply(sts[0], its_o[k_])
+        e = sv.vcycle(r.ravel().copy())
+        assert relerr(its_o[k_].ravel() + e, its_o[k_ + 1]) <= 1e-12, k_
+
+
+@pytest.mark.parametrize("n", [255, 1023])
+def test_level_weights_mixed_reaches_1e8_in_fewer_cycles(M, n):
+    """On the lognormal workload with b = 10 (cos t, sin t) the per-level weights
+    take the mixed V(1,0) solve to relres 1e-8 (the oracle's residual) in fewer
+    cycles than a uniform 0.8, within a few cycles of the FP64 path."""
+    rng = np.random.default_rng(46 + n)
+    t = rng.uniform(0.0, 2.0 * np.pi)
+    k = inputs.lognormal_k(n, 0.05, rng)
+    f = inputs.normal_rhs(n, rng)
+    b = (10.0 * np.cos(t), 10.0 * np.sin(t))
+    sts = oop.level_stencils_div(k, b, num_levels(n))
+    its = {}
+    for prec, om in (("fp64", LEVEL_OMEGA), ("mixed_bf16", LEVEL_OMEGA), ("mixed_bf16", 0.8)):
+        sv = M.Solver(8, 1, 1, precision=prec, b=b)
+        sv.set_weights(M.gmg_v10_weights())
+        sv.setup_gmg(k.ravel().copy(), n, om)
+        u = np.zeros(n * n)
+        st, its[(prec, om)], hist = sv.solve(f.ravel().copy(), u, 1e-8, 200)
+        assert st == M.OK
+        rtrue = f - oop.apply(sts[0], u.reshape(n, n))
+        assert np.linalg.norm(rtrue) / np.linalg.norm(f) <= 1.05e-8
+    assert its[("mixed_bf16", LEVEL_OMEGA)] <= its[("fp64", LEVEL_OMEGA)] + 3
+    assert its[("mixed_bf16", LEVEL_OMEGA)] < its[("mixed_bf16", 0.8)]
+
+
+@pytest.mark.parametrize("bad", [(0.8, 2.0, 1.0), (0.0, 1.3, 1.0), (0.8, 1.3, float("nan")), (0.8, 1.3)])
+def test_level_weights_rejected(M, bad):
+    """Weights outside (0, 2), non-finite weights and a wrong count are errors."""
+    n = 15
+    k, f = problem(n, 47)
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(M.gmg_v10_weights())
+    if len(bad) != 3:
+        with pytest.raises(ValueError):
+            sv.setup_gmg(k.ravel().copy(), n, bad)
+        return
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.setup_gmg(k.ravel().copy(), n, bad)
+    assert ei.value.status == M.ERR_ARG
+
 def test_tile_wait_timeout_is_reported_and_context_survives(M):
     """The fused kernels wait for their TMA tiles with a bounded wait.  A block
     waiting on a copy that is never issued gives up, flags the error, and the call
