@@ -391,6 +391,8 @@ def main():
     ap.add_argument("--workload", default=None, choices=["channelised", "grf", "batched256"])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--maxit", type=int, default=100, help="cycle limit of the batched solves")
+    ap.add_argument("--divtol", type=int, default=6,
+                    help="batched solves stop a problem as diverged once ||r||/||f|| > 10^divtol (0: never)")
     ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6, 7],
                     help="tile shape of the fused kernels: -1 autotuned, 0 16x32, 1 8x32, 2 16x16, 3 32x32, 4 24x32, "
                          "5 24x30 (up) + 24x32 (down), 6 32x30 (up) + 24x32 (down), 7 22x30 (up) + 24x32 (down)")
@@ -757,6 +759,9 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
     ud = [torch.zeros(n * n, dtype=torch.float64, device=dev) for n in ns]
     sv = mgcnn.Solver(C, nd, nu, precision="mixed_bf16")
     sv.set_weights(blob)
+    if args.divtol > 0:
+        # a problem whose ||r||/||f|| exceeds 10^divtol is stopped as diverged (a failure)
+        sv.set_option(sv.OPT_DIVTOL, args.divtol)
 
     def step(kk, ff, uu):
         sv.setup_batched(kk, ns, gmg_omega=args.omega if is_gmg else None)
@@ -815,10 +820,13 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
            "config": {"workload": f"batched{args.batch}_63-1023_mixture", "problems": args.batch,
                       "unknowns": unknowns, "tol": args.tol, "net": net, "omega": omega_record(args.omega, net),
-                      "maxit": args.maxit,
+                      "maxit": args.maxit, "divtol": 10.0 ** args.divtol if args.divtol > 0 else None,
                       "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single"},
            "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
            "converged": done, "failed": int((stat != 0).sum()),
+           "failed_by_status": {nm: int((stat == code).sum()) for nm, code in
+                                (("not_converged", mgcnn.NOT_CONVERGED), ("nonfinite", mgcnn.ERR_NONFINITE),
+                                 ("diverged", mgcnn.ERR_DIVERGED))},
            "converged_by_family": {nm: f"{int(((stat == 0) & (family == i)).sum())}/{int((family == i).sum())}"
                                    for i, nm in enumerate(("grf", "blocks_1e4", "checkerboard_100"))},
            "relres_max_converged": float(relres[stat == 0].max()) if (stat == 0).any() else None,

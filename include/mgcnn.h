@@ -53,7 +53,8 @@ enum {
   MGCNN_ERR_NOMEM = -4,      /* device allocation failed                         */
   MGCNN_ERR_CUDA = -5,       /* a CUDA runtime call or kernel launch failed      */
   MGCNN_ERR_NONFINITE = -6,  /* NaN/Inf in an input or in the iterate's residual */
-  MGCNN_ERR_TIMEOUT = -7     /* a bounded device-side wait gave up               */
+  MGCNN_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up               */
+  MGCNN_ERR_DIVERGED = -8    /* ||r||/||f|| rose above the limit MGCNN_OPT_DIVTOL */
 };
 
 /* Arithmetic of the solve phase.  The residual, the update and the
@@ -427,8 +428,13 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * kernels; contexts whose solves overlap on one device do not, and should set 0
  * (the barrier waits are bounded: past about a second the call fails
  * with MGCNN_ERR_TIMEOUT instead of hanging). */
+/* MGCNN_OPT_DIVTOL (default 0, off): a value d in 1..300 stops mgcnn_solve and
+ * each problem of mgcnn_solve_batched once ||r_k||/||f|| > 10^d, before cycle k,
+ * with status MGCNN_ERR_DIVERGED (iters = k, relres[k] recorded, u the iterate
+ * u_k); the usual divergence test of iterative solvers, which ends a failing
+ * problem long before maxit.  Errors: ARG for a value outside 0..300. */
 enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3, MGCNN_OPT_SYMMETRIC = 4,
-       MGCNN_OPT_FUSED_RESIDUAL = 5, MGCNN_OPT_COARSE_TAIL = 6 };
+       MGCNN_OPT_FUSED_RESIDUAL = 5, MGCNN_OPT_COARSE_TAIL = 6, MGCNN_OPT_DIVTOL = 7 };
 int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).

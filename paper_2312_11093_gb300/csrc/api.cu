@@ -878,6 +878,10 @@ int mgcnn_solve(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit,
         break;
       }
       if (relres) relres[k] = rel;
+      if (c->divtol > 0.0 && rel > c->divtol) {
+        result = make_status(MGCNN_ERR_DIVERGED, "relres %.3e above the divergence limit at cycle %d", rel, k);
+        break;
+      }
       if (rel <= tol) break;
       if (k == maxit) {
         result = make_status(MGCNN_NOT_CONVERGED, "no convergence in %d cycles (relres %.3e)", maxit, rel);
@@ -1099,6 +1103,10 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
     case MGCNN_OPT_DEVICE_LOOP:
       c->device_loop = value ? 1 : 0;
       return finish(c, {});
+    case MGCNN_OPT_DIVTOL:
+      if (value < 0 || value > 300) return finish(c, make_status(MGCNN_ERR_ARG, "divergence exponent is 0..300"));
+      c->divtol = value == 0 ? 0.0 : std::pow(10.0, value);
+      return finish(c, {});
     case MGCNN_OPT_COARSE_TAIL:
       if (value < 0) return finish(c, make_status(MGCNN_ERR_ARG, "coarse tail grid side must be >= 0"));
       c->tail_n = value;
@@ -1195,6 +1203,7 @@ const char* mgcnn_status_string(int s) {
     case MGCNN_ERR_CUDA: return "MGCNN_ERR_CUDA";
     case MGCNN_ERR_NONFINITE: return "MGCNN_ERR_NONFINITE";
     case MGCNN_ERR_TIMEOUT: return "MGCNN_ERR_TIMEOUT";
+    case MGCNN_ERR_DIVERGED: return "MGCNN_ERR_DIVERGED";
     default: return "MGCNN_UNKNOWN_STATUS";
   }
 }

@@ -105,6 +105,7 @@ __global__ void batch_check_kernel(const double* __restrict__ rn2, const double*
   if (b >= B || !state[b]) return;
   const double tol = params[0];
   const int maxit = (int)params[1];
+  const double divtol = params[2];
   const int it = state[B + b];
   const double rel = sqrt(rn2[b] / fn2[b]);
   if (!isfinite(rel)) {
@@ -113,6 +114,11 @@ __global__ void batch_check_kernel(const double* __restrict__ rn2, const double*
     return;
   }
   hist[(size_t)b * hist_stride + it] = rel;
+  if (divtol > 0.0 && rel > divtol) {
+    state[b] = 0;
+    state[2 * B + b] = MGCNN_ERR_DIVERGED;
+    return;
+  }
   if (rel <= tol) {
     state[b] = 0;
     return;
@@ -457,7 +463,7 @@ Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const 
   batch_release(c);
   MG_CUDA(cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking));
   MG_CUDA(cudaEventCreateWithFlags(&c->bfork, cudaEventDisableTiming));
-  MG_TRY(ensure(c->bparams, 2 * sizeof(double)));
+  MG_TRY(ensure(c->bparams, 3 * sizeof(double)));
   MG_TRY(ensure(c->bcount, 2 * sizeof(int)));
   MG_CUDA(cudaMallocHost(&c->h_bcount, 2 * sizeof(int)));
   // size classes in order of first appearance
@@ -510,7 +516,7 @@ Status solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* 
                                                             N0, k.B);
     MG_LAUNCH("batch_init_kernel");
   }
-  const double params[2] = {tol, (double)maxit};
+  const double params[3] = {tol, (double)maxit, c->divtol};
   MG_CUDA(cudaMemcpyAsync(c->bparams.p, params, sizeof(params), cudaMemcpyHostToDevice, main));
   if (maxit != c->bmaxit) {
     for (BatchClass& k : c->bcls) MG_TRY(ensure(k.hist, (size_t)k.B * (maxit + 1) * sizeof(double)));

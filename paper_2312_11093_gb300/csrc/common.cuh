@@ -162,6 +162,7 @@ struct mgcnn_ctx {
   long long adam_t = 0;
   // device-side solve loop (solve_graph.cu)
   int device_loop = 1;                    // option: run mgcnn_solve as one conditional CUDA graph
+  double divtol = 0.0;                    // MGCNN_OPT_DIVTOL: stop when ||r||/||f|| > divtol (0: never)
   bool graph_failed = false, sgraph_valid = false;
   cudaGraphExec_t sgraph = nullptr;
   long long sgraph_kernels = 0;

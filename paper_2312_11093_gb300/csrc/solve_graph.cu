@@ -29,6 +29,7 @@ __global__ void solve_check_kernel(const double* __restrict__ rn2, const double*
   }
   const double tol = params[0];
   const int maxit = (int)params[1];
+  const double divtol = params[2];
   const int it = state[1];
   const double rel = sqrt(rn2[0] / fn2[0]);
   if (!isfinite(rel)) {
@@ -38,6 +39,12 @@ __global__ void solve_check_kernel(const double* __restrict__ rn2, const double*
     return;
   }
   hist[it] = rel;
+  if (divtol > 0.0 && rel > divtol) {
+    state[0] = 0;
+    state[2] = MGCNN_ERR_DIVERGED;
+    cudaGraphSetConditional(loop, 0);
+    return;
+  }
   if (rel <= tol || it >= maxit) {
     state[0] = 0;
     state[2] = (rel <= tol) ? MGCNN_OK : MGCNN_NOT_CONVERGED;
@@ -161,7 +168,7 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
   cudaStream_t st = c->stream;
   MG_TRY(ensure(c->gstate, 4 * sizeof(int)));
   MG_TRY(ensure(c->alpha32, 2 * sizeof(float)));
-  MG_TRY(ensure(c->gparams, 2 * sizeof(double)));
+  MG_TRY(ensure(c->gparams, 3 * sizeof(double)));
   if (c->ghist.bytes < (size_t)(maxit + 1) * sizeof(double)) {
     MG_TRY(ensure(c->ghist, (size_t)(maxit + 1) * sizeof(double)));
     c->sgraph_valid = false;
@@ -251,7 +258,7 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
     }
     c->sgraph_valid = true;
   }
-  const double params[2] = {tol, (double)maxit};
+  const double params[3] = {tol, (double)maxit, c->divtol};
   const int state0[4] = {1, 0, MGCNN_OK, 0};
   MG_CUDA(cudaMemcpyAsync(c->gparams.p, params, sizeof(params), cudaMemcpyHostToDevice, st));
   MG_CUDA(cudaMemcpyAsync(c->gstate.p, state0, sizeof(state0), cudaMemcpyHostToDevice, st));
@@ -277,6 +284,9 @@ Status solve_on_device(mgcnn_ctx* c, const double* f, double* u, double tol, int
     return make_status(MGCNN_ERR_NONFINITE, "residual norm is not finite at cycle %d", state[1]);
   if (state[2] == MGCNN_NOT_CONVERGED)
     return make_status(MGCNN_NOT_CONVERGED, "no convergence in %d cycles", maxit);
+  if (state[2] == MGCNN_ERR_DIVERGED)
+    return make_status(MGCNN_ERR_DIVERGED, "relres %.3e above the divergence limit at cycle %d",
+                       relres ? relres[state[1]] : 0.0, state[1]);
   return {};
 }
 

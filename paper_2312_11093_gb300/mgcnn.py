@@ -17,7 +17,7 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmgcnn.so")
 
 OK, NOT_CONVERGED = 0, 1
-ERR_ARG, ERR_SIZE, ERR_STATE, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
+ERR_ARG, ERR_SIZE, ERR_STATE, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_DIVERGED = -1, -2, -3, -4, -5, -6, -7, -8
 PREC = {"fp64": 0, "mixed_bf16": 1}
 PDE = {"div": 0, "nondiv": 1}
 SETUP_LAYERS = 4
@@ -388,8 +388,9 @@ class Solver:
 
     def solve_batched(self, rhs, us, tol: float, maxit: int, per_problem: bool = False):
         """Solves every problem in place on us[i].  Returns (status, iters, relres, statuses).
-        per_problem: a problem whose iteration became non-finite is reported in its
-        entry of `statuses` (and the overall status) instead of raising."""
+        per_problem: a problem whose iteration became non-finite, or rose above the
+        divergence limit (OPT_DIVTOL), is reported in its entry of `statuses` (and the
+        overall status) instead of raising."""
         m = len(rhs)
         fp = (c_void_p * m)(*[_ptr(f, n * n) for f, n in zip(rhs, self.batch_sizes)])
         up = (c_void_p * m)(*[_ptr(u, n * n, True) for u, n in zip(us, self.batch_sizes)])
@@ -398,7 +399,8 @@ class Solver:
         stat = np.zeros(m, dtype=np.int32)
         st = self._L.mgcnn_solve_batched(self._h, m, fp, up, float(tol), int(maxit), iters.ctypes.data,
                                          relres.ctypes.data, stat.ctypes.data)
-        self._check(st, "mgcnn_solve_batched", ok=(OK, NOT_CONVERGED, ERR_NONFINITE) if per_problem else (OK, NOT_CONVERGED))
+        self._check(st, "mgcnn_solve_batched",
+                    ok=(OK, NOT_CONVERGED, ERR_NONFINITE, ERR_DIVERGED) if per_problem else (OK, NOT_CONVERGED))
         return st, iters, relres, stat
 
     # class index -> name; the finest level's fused kernels are "down0" / "up0",
@@ -411,6 +413,7 @@ class Solver:
     OPT_SYMMETRIC = 4
     OPT_FUSED_RESIDUAL = 5
     OPT_COARSE_TAIL = 6
+    OPT_DIVTOL = 7
 
     def set_option(self, option: int, value: int):
         self._check(self._L.mgcnn_set_option(self._h, int(option), int(value)), "mgcnn_set_option")

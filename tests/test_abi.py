@@ -49,6 +49,8 @@ def test_weight_count_matches_layout(lib):
 def test_status_strings(lib):
     assert lib.mgcnn_status_string(0) == b"MGCNN_OK"
     assert lib.mgcnn_status_string(-6) == b"MGCNN_ERR_NONFINITE"
+    assert lib.mgcnn_status_string(-8) == b"MGCNN_ERR_DIVERGED"
+    assert lib.mgcnn_status_string(-9) == b"MGCNN_UNKNOWN_STATUS"
 
 
 def test_v10_blob_matches_oracle_construction():

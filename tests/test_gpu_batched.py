@@ -172,6 +172,36 @@ def test_batched_level_weights_equal_single_solves(M):
         st1, it1, h1 = one.solve(fs[i].copy(), u1, 1e-6, 200)
         assert it1 == iters[i] and np.array_equal(u1, us[i]), i
 
+
+def test_batched_divergence_limit(M):
+    """A batch mixing GRF problems (which converge) with random-block problems
+    (which diverge): with OPT_DIVTOL = 6 every block problem ends with ERR_DIVERGED
+    at its first cycle above 1e6, and every GRF problem's iterate is bit for bit the
+    one without the limit."""
+    sizes = [63, 127, 63, 255, 127, 31]
+    rng = np.random.default_rng(23)
+    ks, fs = [], []
+    for i, n in enumerate(sizes):
+        k = inputs.lognormal_k(n, 0.1, rng) if i % 2 == 0 else inputs.random_blocks_k(n, rng)
+        ks.append(np.ascontiguousarray(k.ravel()))
+        fs.append(np.ascontiguousarray(inputs.normal_rhs(n, rng).ravel()))
+    out = {}
+    for divtol in (0, 6):
+        sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+        sv.set_weights(M.gmg_v10_weights())
+        sv.set_option(sv.OPT_DIVTOL, divtol)
+        sv.setup_batched(ks, sizes, gmg_omega=0.8)
+        us = [np.zeros(n * n) for n in sizes]
+        st, iters, relres, stat = sv.solve_batched(fs, us, 1e-6, 60, per_problem=True)
+        out[divtol] = (iters.copy(), relres.copy(), stat.copy(), us)
+    it0, rr0, st0, u0 = out[0]
+    it6, rr6, st6, u6 = out[6]
+    for i in range(len(sizes)):
+        if i % 2 == 0:
+            assert st0[i] == st6[i] == M.OK and it0[i] == it6[i] and np.array_equal(u0[i], u6[i]), i
+        else:
+            assert st6[i] == M.ERR_DIVERGED and rr6[i] > 1e6 and it6[i] < it0[i], i
+
 @pytest.mark.parametrize("cfg", [(0, True), (1, False)])
 def test_batched_first_cycle_against_the_oracle(M, cfg):
     """Every problem of an uneven batch over the three coefficient families, one

@@ -514,6 +514,50 @@ def test_level_weights_rejected(M, bad):
         sv.setup_gmg(k.ravel().copy(), n, bad)
     assert ei.value.status == M.ERR_ARG
 
+
+@pytest.mark.parametrize("device_loop", [1, 0])
+def test_divergence_limit_stops_a_diverging_solve(M, device_loop):
+    """On random blocks of contrast 1e4 the V(1,0) network diverges (the residual
+    grows many times per cycle).  With OPT_DIVTOL = 6 the solve stops before the
+    first cycle whose ||r_k||/||f|| exceeds 1e6, with ERR_DIVERGED; the cycles
+    before it are the same as without the limit, device loop and host loop alike."""
+    n = 127
+    k, f = problem(n, 48, "blocks")
+    hists = {}
+    for divtol in (0, 6):
+        sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+        sv.set_weights(M.gmg_v10_weights())
+        sv.set_option(sv.OPT_DEVICE_LOOP, device_loop)
+        sv.set_option(sv.OPT_DIVTOL, divtol)
+        sv.setup_gmg(k.ravel().copy(), n, 0.8)
+        u = np.zeros(n * n)
+        if divtol == 0:
+            st, it, hists[0] = sv.solve(f.ravel().copy(), u, 1e-6, 12)
+            assert st == M.NOT_CONVERGED
+        else:
+            with pytest.raises(M.MGCNNError) as ei:
+                sv.solve(f.ravel().copy(), u, 1e-6, 200)
+            assert ei.value.status == M.ERR_DIVERGED
+    h0 = hists[0]
+    first = int(np.argmax(h0 > 1e6))
+    assert h0[first] > 1e6 and np.all(h0[:first] <= 1e6) and 0 < first < 12
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(M.gmg_v10_weights())
+    sv.set_option(sv.OPT_DEVICE_LOOP, device_loop)
+    sv.set_option(sv.OPT_DIVTOL, 6)
+    sv.setup_gmg(k.ravel().copy(), n, 0.8)
+    u = np.zeros(n * n)
+    fr = f.ravel().copy()      # kept alive across the call
+    it = M.c_int(0)
+    hist = np.zeros(201)
+    st = sv._L.mgcnn_solve(sv._h, M._ptr(fr, n * n), M._ptr(u, n * n, True), 1e-6, 200,
+                           M.ctypes.byref(it), hist.ctypes.data)
+    assert st == M.ERR_DIVERGED and it.value == first
+    assert np.array_equal(hist[: first + 1], h0[: first + 1])
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.set_option(sv.OPT_DIVTOL, 301)
+    assert ei.value.status == M.ERR_ARG
+
 def test_tile_wait_timeout_is_reported_and_context_survives(M):
     """The fused kernels wait for their TMA tiles with a bounded wait.  A block
     waiting on a copy that is never issued gives up, flags the error, and the call
