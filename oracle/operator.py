@@ -90,28 +90,35 @@ def inject_k(k: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(k[::2, ::2])
 
 
-def restrict_k(k: np.ndarray) -> np.ndarray:
-    """Coarse nodal k for the divergence form: full weighting of log k around fine node 2I.
+def restrict_k(k: np.ndarray, mean: str = "log") -> np.ndarray:
+    """Coarse nodal k for the divergence form: full weighting around fine node 2I.
 
-    log k_c(I, J) = sum_ab w_a w_b log k(2J + a - 1, 2I + b - 1) / sum of the weights used,
-    w = (1, 2, 1), over the fine nodes that exist (the boundary ring renormalises).
+    mean="log" (default): log k_c(I, J) = sum_ab w_a w_b log k(2J + a - 1, 2I + b - 1)
+    / sum of the weights used; mean="arith": k_c = sum_ab w_a w_b k(...) / sum of
+    the weights used; w = (1, 2, 1), over the fine nodes that exist (the boundary
+    ring renormalises).
     Reading: Sec. 2.3 rediscretises the PDE on the coarse grid without saying how a
     heterogeneous k gets there, and the setup phase restricts coefficients with a
-    strided 3x3 convolution (Eq. setup1); a geometric full-weighting average keeps
-    rediscretised GMG convergent on blocky high-contrast k where injection diverges.
+    strided 3x3 convolution (Eq. setup1).  The geometric average keeps
+    rediscretised GMG convergent on smooth lognormal k; the arithmetic average
+    (never below the geometric one) gives stiffer coarse operators, which keep the
+    coarse-grid correction from over-correcting on piecewise-constant
+    high-contrast k, where the geometric one makes GMG diverge.
     """
+    if mean not in ("log", "arith"):
+        raise ValueError(mean)
     m = k.shape[0]
     mc = (m + 1) // 2
-    lk = np.pad(np.log(k), 1)
+    g = np.pad(np.log(k) if mean == "log" else k, 1)
     mask = np.pad(np.ones_like(k), 1)
     w = np.array([1.0, 2.0, 1.0])
     num = np.zeros((mc, mc))
     den = np.zeros((mc, mc))
     for a in range(3):
         for b in range(3):
-            num += w[a] * w[b] * lk[a:a + 2 * mc - 1:2, b:b + 2 * mc - 1:2]
+            num += w[a] * w[b] * g[a:a + 2 * mc - 1:2, b:b + 2 * mc - 1:2]
             den += w[a] * w[b] * mask[a:a + 2 * mc - 1:2, b:b + 2 * mc - 1:2]
-    return np.exp(num / den)
+    return np.exp(num / den) if mean == "log" else num / den
 
 
 def inject_mu(mu: np.ndarray) -> np.ndarray:
@@ -119,14 +126,15 @@ def inject_mu(mu: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(mu[1::2, 1::2])
 
 
-def level_stencils_div(k: np.ndarray, b, levels: int) -> list[Stencil]:
+def level_stencils_div(k: np.ndarray, b, levels: int, mean: str = "log") -> list[Stencil]:
     """Rediscretised operators on every level (Sec. 2.3: coarse operators by discretising
-    the PDE on the coarse grid), with k carried to the coarse grid by `restrict_k`."""
+    the PDE on the coarse grid), with k carried to the coarse grid by `restrict_k`
+    (`mean`: its averaging, geometric or arithmetic)."""
     out = []
     kl = k
     for _ in range(levels):
         out.append(stencil_div(kl, b))
-        kl = restrict_k(kl)
+        kl = restrict_k(kl, mean)
     return out
 
 

@@ -101,6 +101,10 @@ MUTATIONS = {
     "GMG-equivalent setup uses the finest weight on every level": (
         "mgcnn.py", "omega_l = _level_weight(omega, lev)\n        n = st.n\n        s = np.zeros((GMG_CHANNELS",
         "omega_l = _level_weight(omega, 0)\n        n = st.n\n        s = np.zeros((GMG_CHANNELS", NET),
+    "arithmetic coarse k averages log k": ("operator.py", "g = np.pad(np.log(k) if mean == \"log\" else k, 1)",
+                                           "g = np.pad(np.log(k), 1)", OP),
+    "arithmetic coarse k returned as a geometric mean": (
+        "operator.py", "return np.exp(num / den) if mean == \"log\" else num / den", "return np.exp(num / den)", OP),
 }
 
 

@@ -207,3 +207,34 @@ def test_coarse_k_restriction_weights_on_a_quadratic():
     J, I = np.meshgrid(np.arange(kc.shape[0]), np.arange(kc.shape[0]), indexing="ij")
     ref = c * ((2 * I) ** 2 + (2 * J) ** 2) + c
     np.testing.assert_allclose(np.log(kc)[1:-1, 1:-1], ref[1:-1, 1:-1], rtol=1e-12, atol=1e-12)
+
+
+def test_arithmetic_coarse_k_restriction():
+    """The arithmetic full weighting keeps a constant k, reproduces a linear k
+    exactly and a quadratic k = 1 + c (i^2 + j^2) as 1 + c ((2I)^2 + (2J)^2) + c
+    (the (1, 2, 1)/4 average of x^2 is x^2 + 1/2 per direction) at coarse nodes
+    whose fine neighbourhood exists; at a ring node it averages the fine nodes that
+    exist with their weights renormalised, and it is never below the geometric
+    average (AM-GM)."""
+    m = 17
+    np.testing.assert_allclose(op.restrict_k(np.full((m, m), 4.2), "arith"), 4.2, rtol=1e-14)
+    j, i = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    J, I = np.meshgrid(np.arange(9), np.arange(9), indexing="ij")
+    kc = op.restrict_k(2.0 + 0.3 * i + 0.2 * j, "arith")
+    np.testing.assert_allclose(kc[1:-1, 1:-1], (2.0 + 0.6 * I + 0.4 * J)[1:-1, 1:-1], rtol=1e-13)
+    c = 0.01
+    kc = op.restrict_k(1.0 + c * (i ** 2 + j ** 2), "arith")
+    ref = 1.0 + c * ((2 * I) ** 2 + (2 * J) ** 2) + c
+    np.testing.assert_allclose(kc[1:-1, 1:-1], ref[1:-1, 1:-1], rtol=1e-13)
+    k = 10.0 ** np.random.default_rng(4).uniform(-2, 2, size=(m, m))
+    kc = op.restrict_k(k, "arith")
+    # corner coarse node (0, 0): fine nodes (0..1, 0..1) with weights 4, 2, 2, 1
+    expect = (4 * k[0, 0] + 2 * k[0, 1] + 2 * k[1, 0] + k[1, 1]) / 9.0
+    assert abs(kc[0, 0] - expect) <= 1e-14 * expect
+    # edge coarse node (0, 3): fine rows 0..1, columns 5..7
+    wv = np.array([[2.0, 4.0, 2.0], [1.0, 2.0, 1.0]])
+    expect = np.sum(wv * k[0:2, 5:8]) / np.sum(wv)
+    assert abs(kc[0, 3] - expect) <= 1e-14 * expect
+    assert np.all(kc >= op.restrict_k(k) * (1 - 1e-14))
+    with pytest.raises(ValueError):
+        op.restrict_k(k, "harmonic")
