@@ -433,8 +433,18 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * with status MGCNN_ERR_DIVERGED (iters = k, relres[k] recorded, u the iterate
  * u_k); the usual divergence test of iterative solvers, which ends a failing
  * problem long before maxit.  Errors: ARG for a value outside 0..300. */
+/* MGCNN_OPT_COARSE_K (default 0): how the divergence form's k reaches the
+ * coarse grids before rediscretisation (Sec. 2.3 leaves it open).  0: full
+ * weighting of log k (a geometric mean), 1: full weighting of k itself (an
+ * arithmetic mean, never below the geometric one, so stiffer coarse
+ * operators).  On smooth lognormal k the geometric mean converges in fewer
+ * cycles.  On piecewise-constant high-contrast k the geometric mean makes the
+ * coarse-grid correction over-correct and the V-cycle diverge.  The arithmetic
+ * mean keeps the V-cycle stable there, a preconditioner that flexible GMRES
+ * (mgcnn_solve_krylov) turns into a solver.  Takes effect at the next setup;
+ * the non-divergence form injects mu either way.  Errors: ARG for other values. */
 enum { MGCNN_OPT_FUSED = 1, MGCNN_OPT_DEVICE_LOOP = 2, MGCNN_OPT_TILE = 3, MGCNN_OPT_SYMMETRIC = 4,
-       MGCNN_OPT_FUSED_RESIDUAL = 5, MGCNN_OPT_COARSE_TAIL = 6, MGCNN_OPT_DIVTOL = 7 };
+       MGCNN_OPT_FUSED_RESIDUAL = 5, MGCNN_OPT_COARSE_TAIL = 6, MGCNN_OPT_DIVTOL = 7, MGCNN_OPT_COARSE_K = 8 };
 int mgcnn_set_option(mgcnn_ctx* ctx, int option, int value);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).

@@ -436,7 +436,9 @@ Status setup_operators(mgcnn_ctx* c, const double* coeff, int n) {
     const int nlv = c->lv[l].n;
     if (div) {
       MG_TRY(launch_stencil_div(c->coef[l].as<double>(), c->op[l].as<double>(), nlv, c->cfg.bx, c->cfg.by, c->stream));
-      if (l < L - 1) MG_TRY(launch_restrict_k(c->coef[l].as<double>(), c->coef[l + 1].as<double>(), nlv + 2, c->stream));
+      if (l < L - 1)
+        MG_TRY(launch_restrict_k(c->coef[l].as<double>(), c->coef[l + 1].as<double>(), nlv + 2, c->stream, 1,
+                                 c->coarse_k_arith != 0));
     } else {
       MG_TRY(launch_stencil_nondiv(c->coef[l].as<double>(), c->op[l].as<double>(), nlv, c->cfg.bx, c->cfg.by, c->stream));
       if (l < L - 1) MG_TRY(launch_inject_mu(c->coef[l].as<double>(), c->coef[l + 1].as<double>(), nlv, c->stream));
@@ -1102,6 +1104,10 @@ int mgcnn_set_option(mgcnn_ctx* c, int option, int value) {
       return finish(c, {});
     case MGCNN_OPT_DEVICE_LOOP:
       c->device_loop = value ? 1 : 0;
+      return finish(c, {});
+    case MGCNN_OPT_COARSE_K:
+      if (value < 0 || value > 1) return finish(c, make_status(MGCNN_ERR_ARG, "coarse k rule is 0 or 1"));
+      c->coarse_k_arith = value;
       return finish(c, {});
     case MGCNN_OPT_DIVTOL:
       if (value < 0 || value > 300) return finish(c, make_status(MGCNN_ERR_ARG, "divergence exponent is 0..300"));

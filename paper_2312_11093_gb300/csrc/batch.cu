@@ -242,7 +242,8 @@ Status setup_class(mgcnn_ctx* c, BatchClass& k, const double* const* coeff, cons
   double* kh[2] = {k0, k0 + B * m0 * m0};
   for (int l = 0; l < k.L; ++l) {
     MG_TRY(launch_stencil_div(kh[l & 1], k.op[l].as<double>(), k.nl[l], c->cfg.bx, c->cfg.by, st, k.B));
-    if (l + 1 < k.L) MG_TRY(launch_restrict_k(kh[l & 1], kh[(l + 1) & 1], k.nl[l] + 2, st, k.B));
+    if (l + 1 < k.L)
+      MG_TRY(launch_restrict_k(kh[l & 1], kh[(l + 1) & 1], k.nl[l] + 2, st, k.B, c->coarse_k_arith != 0));
   }
   MG_TRY(launch_diag_inverse(k.op[0].as<double>(), nullptr, k.dinv32.as<float>(), N0, st, k.B));
   if (omega) {

@@ -163,6 +163,7 @@ struct mgcnn_ctx {
   // device-side solve loop (solve_graph.cu)
   int device_loop = 1;                    // option: run mgcnn_solve as one conditional CUDA graph
   double divtol = 0.0;                    // MGCNN_OPT_DIVTOL: stop when ||r||/||f|| > divtol (0: never)
+  int coarse_k_arith = 0;                 // MGCNN_OPT_COARSE_K: arithmetic full weighting of k
   bool graph_failed = false, sgraph_valid = false;
   cudaGraphExec_t sgraph = nullptr;
   long long sgraph_kernels = 0;

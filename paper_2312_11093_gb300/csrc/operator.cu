@@ -15,7 +15,8 @@ namespace mgcnn {
 // ---------------------------------------------------------------------------
 // Coarse coefficient: log k_c(J, I) = weighted mean of log k over the fine
 // nodes (2J + a - 1, 2I + b - 1), weights (1,2,1)x(1,2,1), renormalised over
-// the nodes that exist.  m = fine nodes per side incl. the ring.
+// the nodes that exist (or, with `arith`, the weighted mean of k itself).
+// m = fine nodes per side incl. the ring.
 //
 // FP64 log and exp cost dozens of FP64-pipe instructions each, and FP64 runs
 // at 1/58 of the FP32 rate here, so interior coarse nodes (all nine fine nodes
@@ -38,13 +39,29 @@ __device__ __forceinline__ double split_pow2(double x, int& e) {
 }
 
 __global__ void restrict_k_kernel(const double* __restrict__ k, double* __restrict__ kc, int m,
-                                  const Pow2Sixteenths p2) {
+                                  const Pow2Sixteenths p2, int arith) {
   const int mc = (m + 1) / 2;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= mc * mc) return;
   k += (size_t)blockIdx.y * m * m;      // problem blockIdx.y of a batch stored back to back
   kc += (size_t)blockIdx.y * mc * mc;
   const int J = p / mc, I = p - J * mc;
+  if (arith) {
+    // arithmetic full weighting: sum w k / sum w over the fine nodes that exist
+    const double w[3] = {1.0, 2.0, 1.0};
+    double num = 0.0, den = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const int jj = 2 * J + a - 1;
+      for (int b = 0; b < 3; ++b) {
+        const int ii = 2 * I + b - 1;
+        if (jj < 0 || jj >= m || ii < 0 || ii >= m) continue;
+        num += w[a] * w[b] * k[(size_t)jj * m + ii];
+        den += w[a] * w[b];
+      }
+    }
+    kc[p] = num / den;
+    return;
+  }
   if (J >= 1 && I >= 1 && 2 * J + 1 < m && 2 * I + 1 < m) {
     const double* k0 = k + (size_t)(2 * J - 1) * m + (2 * I - 1);
     int e[9];
@@ -81,14 +98,14 @@ __global__ void restrict_k_kernel(const double* __restrict__ k, double* __restri
   kc[p] = exp(num / den);
 }
 
-Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch) {
+Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch, bool arith) {
   static const Pow2Sixteenths p2 = [] {
     Pow2Sixteenths t{};
     for (int r = 0; r < 16; ++r) t.t[r] = std::exp2(r / 16.0);
     return t;
   }();
   const int mc = (m + 1) / 2;
-  restrict_k_kernel<<<dim3(grid_for((size_t)mc * mc, 256), batch), 256, 0, st>>>(k, kc, m, p2);
+  restrict_k_kernel<<<dim3(grid_for((size_t)mc * mc, 256), batch), 256, 0, st>>>(k, kc, m, p2, arith ? 1 : 0);
   MG_LAUNCH("restrict_k_kernel");
   return {};
 }

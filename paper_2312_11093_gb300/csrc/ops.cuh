@@ -23,7 +23,8 @@ __host__ __device__ inline int r32_pitch(int n) { return (n + 3) & ~3; }
 __host__ __device__ inline size_t r32_floats(int n) { return (size_t)n * r32_pitch(n); }
 
 // batch > 1: problems of the same size stored back to back (blockIdx.y selects one).
-Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch = 1);
+// arith: arithmetic instead of geometric full weighting of k (MGCNN_OPT_COARSE_K)
+Status launch_restrict_k(const double* k, double* kc, int m, cudaStream_t st, int batch = 1, bool arith = false);
 Status launch_inject_mu(const double* mu, double* mc, int n, cudaStream_t st);
 Status launch_stencil_div(const double* k, double* op, int n, double bx, double by, cudaStream_t st, int batch = 1);
 Status launch_stencil_nondiv(const double* mu, double* op, int n, double vx, double vy, cudaStream_t st);

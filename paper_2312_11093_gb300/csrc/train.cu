@@ -667,7 +667,7 @@ Status loss_grad_impl(mgcnn_ctx* c, int nprob, const double* const* coeff, const
         double* kin = (l % 2 == 0) ? k0 : k1;
         double* kout = (l % 2 == 0) ? k1 : k0;
         MG_TRY(launch_stencil_div(kin, opl, nlv, c->cfg.bx, c->cfg.by, st));
-        if (l + 1 < g.L) MG_TRY(launch_restrict_k(kin, kout, nlv + 2, st));
+        if (l + 1 < g.L) MG_TRY(launch_restrict_k(kin, kout, nlv + 2, st, 1, c->coarse_k_arith != 0));
       }
       MG_TRY(launch_features<T>(g.op[0].as<double>() + (size_t)b * 5 * N0, g.feat.as<T>() + (size_t)b * N0 * kFeatures,
                                 n, st));

@@ -414,6 +414,7 @@ class Solver:
     OPT_FUSED_RESIDUAL = 5
     OPT_COARSE_TAIL = 6
     OPT_DIVTOL = 7
+    OPT_COARSE_K = 8
 
     def set_option(self, option: int, value: int):
         self._check(self._L.mgcnn_set_option(self._h, int(option), int(value)), "mgcnn_set_option")

@@ -148,10 +148,12 @@ def test_batched_gmg_v10_equals_single_solves_and_converges(M):
 
 
 
-def test_batched_level_weights_equal_single_solves(M):
-    """Batched setup with per-level Jacobi weights (finest, in between, coarsest):
-    each problem gets the weights on its own hierarchy, so every iterate equals the
-    single-problem solve with mgcnn_setup_gmg_levels bit for bit."""
+@pytest.mark.parametrize("coarse_k", [0, 1])
+def test_batched_level_weights_equal_single_solves(M, coarse_k):
+    """Batched setup with per-level Jacobi weights (finest, in between, coarsest),
+    and either coarse-coefficient rule: each problem gets the weights on its own
+    hierarchy, so every iterate equals the single-problem solve with
+    mgcnn_setup_gmg_levels bit for bit."""
     sizes = [63, 255, 31, 127, 63]
     rng = np.random.default_rng(19)
     ks = [np.ascontiguousarray(inputs.lognormal_k(n, 0.1, rng).ravel()) for n in sizes]
@@ -160,6 +162,7 @@ def test_batched_level_weights_equal_single_solves(M):
     w = M.gmg_v10_weights()
     sv = M.Solver(8, 1, 1, precision="mixed_bf16")
     sv.set_weights(w)
+    sv.set_option(sv.OPT_COARSE_K, coarse_k)
     sv.setup_batched(ks, sizes, gmg_omega=om)
     us = [np.zeros(n * n) for n in sizes]
     st, iters, relres, stat = sv.solve_batched(fs, us, 1e-6, 200)
@@ -167,6 +170,7 @@ def test_batched_level_weights_equal_single_solves(M):
     for i, n in enumerate(sizes):
         one = M.Solver(8, 1, 1, precision="mixed_bf16")
         one.set_weights(w)
+        one.set_option(one.OPT_COARSE_K, coarse_k)
         one.setup_gmg(ks[i], n, om)
         u1 = np.zeros(n * n)
         st1, it1, h1 = one.solve(fs[i].copy(), u1, 1e-6, 200)

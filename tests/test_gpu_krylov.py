@@ -52,6 +52,60 @@ def test_fp64_fgmres_matches_oracle(M):
     assert np.linalg.norm(u - u_o.ravel()) / np.linalg.norm(u_o) <= 1e-9
 
 
+LEVEL_OMEGA = (0.8, 1.5, 1.0)
+
+
+def test_fp64_fgmres_high_contrast_matches_oracle(M):
+    """Random blocks of contrast 1e4 with the arithmetic coarse coefficient and
+    per-level weights, FP64 network, FGMRES(30): the oracle's iteration count and
+    history."""
+    from oracle import gmg as ogmg
+    n, b = 63, (1.0, 0.5)
+    rng = np.random.default_rng(52)
+    k = inputs.random_blocks_k(n, rng)
+    f = inputs.normal_rhs(n, rng)
+    sts = oop.level_stencils_div(k, b, num_levels(n), "arith")
+    oms = ogmg.level_omegas(len(sts), LEVEL_OMEGA)
+    w = omg.gmg_v10_weights()
+    s = omg.gmg_v10_setup(sts, oms, input_diag=True)
+    dinv = 1.0 / sts[0].aC
+    u_o, it_o, h_o = okr.fgmres(lambda x: oop.apply(sts[0], x), lambda v: omg.solve_phase(w, s, v, d_inv=dinv),
+                                f, None, 1e-8, 300, 30)
+    assert h_o[-1] <= 1e-8
+    sv = M.Solver(8, 1, 1, precision="fp64", b=b)
+    sv.set_weights(M.gmg_v10_weights())
+    sv.set_option(sv.OPT_COARSE_K, 1)
+    sv.setup_gmg(k.ravel().copy(), n, LEVEL_OMEGA)
+    u = np.zeros(n * n)
+    st, it, h = sv.solve_krylov(f.ravel().copy(), u, 1e-8, 300, restart=30)
+    assert st == M.OK and it == it_o
+    h_o = np.array(h_o)
+    early = h_o > 1e-6
+    np.testing.assert_allclose(h[early], h_o[early], rtol=1e-6)
+    assert np.linalg.norm(u - u_o.ravel()) / np.linalg.norm(u_o) <= 1e-7
+
+
+@pytest.mark.parametrize("n,kind", [(255, "blocks"), (1023, "blocks"), (511, "checker")])
+def test_mixed_fgmres_solves_high_contrast_families(M, n, kind):
+    """The families on which every stationary network here diverges: with the
+    arithmetic coarse coefficient, per-level weights and the mixed network as
+    FGMRES(30) preconditioner the solve reaches 1e-6, checked by the oracle's own
+    residual in FP64."""
+    b = (1.0, 0.5)
+    rng = np.random.default_rng(53 + n)
+    k = inputs.random_blocks_k(n, rng) if kind == "blocks" else inputs.checkerboard_k(n)
+    f = inputs.normal_rhs(n, rng)
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16", b=b)
+    sv.set_weights(M.gmg_v10_weights())
+    sv.set_option(sv.OPT_COARSE_K, 1)
+    sv.setup_gmg(k.ravel().copy(), n, LEVEL_OMEGA)
+    u = np.zeros(n * n)
+    st, it, h = sv.solve_krylov(f.ravel().copy(), u, 1e-6, 300, restart=30)
+    assert st == M.OK and it < 150
+    rtrue = f - oop.apply(oop.stencil_div(k, b), u.reshape(n, n))
+    assert np.linalg.norm(rtrue) / np.linalg.norm(f) <= 1.05e-6
+
+
 @pytest.mark.parametrize("n", [255, 1023])
 def test_mixed_fgmres_reaches_1e8_and_beats_stationary(M, n):
     rng = np.random.default_rng(60 + n)

@@ -68,6 +68,29 @@ def test_operator_all_levels(M, n, kind):
             assert np.max(np.abs(g - r)) <= 1e-14 * np.max(np.abs(st.aC)), l
 
 
+@pytest.mark.parametrize("n,kind", [(7, "blocks"), (63, "blocks"), (255, "checker"), (127, "grf")])
+def test_operator_all_levels_arithmetic_coarse_k(M, n, kind):
+    """MGCNN_OPT_COARSE_K = 1: every level's operator is the oracle's with k carried
+    down by arithmetic full weighting."""
+    b = (0.7, -1.1)
+    k, f = problem(n, n + 3, kind, b=b)
+    ref = oop.level_stencils_div(k, b, num_levels(n), "arith")
+    sv = M.Solver(8, 1, 1, b=b)
+    sv.set_weights(np.zeros(sv.weight_count))
+    sv.set_option(sv.OPT_COARSE_K, 1)
+    sv.setup(k.ravel().copy(), n)
+    for l, (st, nl) in enumerate(zip(ref, level_sizes(n))):
+        got = sv.get_operator(l, nl).reshape(5, nl, nl)
+        for g, r in zip(got, [st.aC, st.aW, st.aE, st.aS, st.aN]):
+            assert np.max(np.abs(g - r)) <= 1e-14 * np.max(np.abs(st.aC)), l
+    log = oop.level_stencils_div(k, b, num_levels(n))
+    if num_levels(n) > 1:
+        assert np.max(np.abs(log[1].aC - ref[1].aC)) > 1e-6 * np.max(ref[1].aC)   # the rule matters here
+    with pytest.raises(M.MGCNNError) as ei:
+        sv.set_option(sv.OPT_COARSE_K, 2)
+    assert ei.value.status == M.ERR_ARG
+
+
 def test_residual_and_norm(M):
     n = 127
     k, f = problem(n, 1)
