@@ -714,6 +714,8 @@ def main():
         # GMG, per-level achieved bandwidth)
         result["batched"] = run_batched(args, rank, world, dev, mgcnn, quiet=True)
         result["channelised"] = run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, args.omega)
+        if is_gmg:
+            result["high_contrast_krylov"] = run_high_contrast(n, dev, stream, mgcnn, C, nd, nu, blob, args.omega, tol)
         result["setup_network"] = time_setup_network(n, dev, stream, mgcnn, k_d, b)
     if not args.no_cpu and rank == 0 and world == 1:
         # one wave of complete oracle solves at 511^2, one per host core (about 15-30 s)
@@ -922,6 +924,57 @@ def run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, omega, 
     torch.cuda.synchronize(dev)
     out["gmg"]["ms"] = (time.perf_counter() - t0) * 1e3
     sv64.close()
+    if is_gmg:
+        # the mixed network with the arithmetic coarse coefficient as the
+        # preconditioner of flexible GMRES(30), where every stationary solve diverges
+        out["mixed_krylov"] = krylov_solve_record(mgcnn, n, k_d, f_d, b, dev, stream, C, nd, nu, blob, omega, tol)
+    return out
+
+
+def krylov_solve_record(mgcnn, n, k_d, f_d, b, dev, stream, C, nd, nu, blob, omega, tol, maxit=300, restart=30):
+    """One setup + FGMRES(restart) solve with the mixed analytic network on the
+    arithmetic coarse coefficient (MGCNN_OPT_COARSE_K = 1), timed with CUDA events
+    after one untimed run; the final relative residual recomputed in FP64."""
+    import torch
+    sv = mgcnn.Solver(C, nd, nu, precision="mixed_bf16", b=b, stream=stream)
+    sv.set_weights(blob)
+    sv.set_option(sv.OPT_COARSE_K, 1)
+    u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+
+    def once():
+        sv.setup_gmg(k_d, n, omega)
+        u.zero_()
+        return sv.solve_krylov(f_d, u, tol, maxit, restart)
+    once()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    st, it, hist = once()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    r = torch.empty_like(u)
+    _, rn2 = sv.residual(f_d, u, r)
+    fn = float(torch.linalg.norm(f_d))
+    sv.close()
+    return {"iters": it, "converged": bool(st == mgcnn.OK), "ms": e0.elapsed_time(e1),
+            "relres_fp64": float(np.sqrt(rn2)) / fn,
+            "method": f"flexible GMRES({restart}), mixed V(1,0) network as right preconditioner, arithmetic coarse k, "
+                      "setup + solve"}
+
+
+def run_high_contrast(n, dev, stream, mgcnn, C, nd, nu, blob, omega, tol):
+    """Single solves at n^2 of the batched workload's two high-contrast families
+    (random blocks with contrast 1e4, 16 x 16 checkerboard {1, 100}; b = (1, 0.5)),
+    on which the stationary iteration diverges, by FGMRES(30) with the mixed network."""
+    import torch
+    rng = np.random.default_rng(5)
+    fields = {"blocks_1e4": inputs.random_blocks_k(n, rng), "checkerboard_100": inputs.checkerboard_k(n)}
+    f_d = torch.from_numpy(np.ascontiguousarray(inputs.normal_rhs(n, rng).ravel())).to(dev)
+    out = {"n": n, "tol": tol, "b": [1.0, 0.5]}
+    for name, k in fields.items():
+        k_d = torch.from_numpy(np.ascontiguousarray(k.ravel())).to(dev)
+        out[name] = krylov_solve_record(mgcnn, n, k_d, f_d, (1.0, 0.5), dev, stream, C, nd, nu, blob, omega, tol)
     return out
 
 
