@@ -348,6 +348,23 @@ int mgcnn_setup_batched_gmg_levels(mgcnn_ctx* ctx, int nprob, const double* cons
 int mgcnn_solve_batched(mgcnn_ctx* ctx, int nprob, const double* const* rhs, double* const* u, double tol,
                         int maxit, int* iters, double* relres, int* status);
 
+/* Flexible GMRES(restart) for every problem of the batch (after
+ * mgcnn_setup_batched or mgcnn_setup_batched_gmg(_levels)), the batch's mixed
+ * network as right preconditioner, as mgcnn_solve_krylov does for one problem:
+ * z_j = B v_j, Arnoldi by classical Gram-Schmidt applied twice, Givens
+ * rotations, u += Z y at the end of a cycle and a restart from the true FP64
+ * residual.  The problems of a size class advance in lockstep, one inner
+ * iteration of each problem still in its cycle per pass; the Hessenberg
+ * matrices, rotations and estimates stay on the device.  iters[i]: inner
+ * iterations of problem i; relres[i]: the last ||r||/||f|| (the true residual
+ * at the end of its last cycle); status[i]: OK, NOT_CONVERGED (maxit inner
+ * iterations), ERR_NONFINITE, or ERR_DIVERGED (MGCNN_OPT_DIVTOL, tested before
+ * each cycle).  restart: 1..MGCNN_KRYLOV_MAX_RESTART.  Workspace per problem:
+ * 2 restart + 1 vectors of n_i^2 doubles.  Returns as mgcnn_solve_batched;
+ * ARG for a restart outside its range. */
+int mgcnn_solve_batched_krylov(mgcnn_ctx* ctx, int nprob, const double* const* rhs, double* const* u, double tol,
+                               int maxit, int restart, int* iters, double* relres, int* status);
+
 /* ---- Training (Sec. 3.4, Eq. loss) ------------------------------------------
  * Loss of a batch of problems after K stationary cycles from u = 0,
  *     r_0 = f,  r_{k+1} = r_k - A B(r_k),   L = (1/N) sum_i ||r_K,i||^2 / ||f_i||^2

@@ -1014,6 +1014,12 @@ int mgcnn_solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, doubl
   return finish(c, solve_batched(c, nprob, rhs, u, tol, maxit, iters, relres, status));
 }
 
+int mgcnn_solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol,
+                               int maxit, int restart, int* iters, double* relres, int* status) {
+  if (!c || !rhs || !u || maxit < 0 || !(tol >= 0.0)) return MGCNN_ERR_ARG;
+  return finish(c, solve_batched_krylov(c, nprob, rhs, u, tol, maxit, restart, iters, relres, status));
+}
+
 namespace {
 
 int gmg_solve_levels(mgcnn_ctx* c, const double* f, double* u, double tol, int maxit, int nu1, int nu2,

@@ -433,7 +433,7 @@ void batch_release(mgcnn_ctx* c) {
       release(k.op[l]); release(k.s16[l]); release(k.xa[l]); release(k.xb[l]); release(k.xl[l]);
     }
     for (DevBuf* b : {&k.dinv32, &k.r32, &k.f, &k.u, &k.partial, &k.rn2, &k.alpha, &k.fn2, &k.state, &k.hist, &k.feat,
-                      &k.ca, &k.cb, &k.za, &k.zb, &k.s32, &k.scratch})
+                      &k.ca, &k.cb, &k.za, &k.zb, &k.s32, &k.scratch, &k.kV, &k.kZ, &k.kpart, &k.kdbl, &k.kint})
       release(*b);
     if (k.stream) cudaStreamDestroy(k.stream);
     if (k.done) cudaEventDestroy(k.done);

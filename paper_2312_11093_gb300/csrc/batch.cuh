@@ -24,6 +24,8 @@ struct BatchClass {
   DevBuf hist;                                 // [B][maxit + 1]
   DevBuf feat, ca, cb, za, zb, s32;            // FP32 setup scratch
   DevBuf scratch;                              // [B][N] FP64 (autotuning output)
+  DevBuf kV, kZ;                               // FGMRES: [restart + 1][B][N] and [restart][B][N] FP64
+  DevBuf kpart, kdbl, kint;                    // FGMRES: dot partials, per-problem scalars and matrices, flags
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   FusedLevels fl;
@@ -36,5 +38,8 @@ Status setup_batched(mgcnn_ctx* c, int nprob, const double* const* coeff, const 
                      const LevelWeights* omega = nullptr);
 Status solve_batched(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol, int maxit,
                      int* iters, double* relres, int* status);
+// batch_krylov.cu: flexible GMRES(restart) of every problem, the batch's network as preconditioner
+Status solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, double* const* u, double tol,
+                            int maxit, int restart, int* iters, double* relres, int* status);
 
 }  // namespace mgcnn

@@ -77,6 +77,8 @@ def load() -> ctypes.CDLL:
         "mgcnn_setup_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
         "mgcnn_setup_batched_gmg": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double]),
         "mgcnn_setup_batched_gmg_levels": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+        "mgcnn_solve_batched_krylov": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p,
+                                               c_void_p, c_void_p]),
         "mgcnn_check_wait_timeout": (c_int, [c_void_p]),
         "mgcnn_solve_krylov": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_void_p]),
         "mgcnn_setup_bpx": (c_int, [c_void_p, c_void_p, c_int, c_double]),
@@ -400,6 +402,22 @@ class Solver:
         st = self._L.mgcnn_solve_batched(self._h, m, fp, up, float(tol), int(maxit), iters.ctypes.data,
                                          relres.ctypes.data, stat.ctypes.data)
         self._check(st, "mgcnn_solve_batched",
+                    ok=(OK, NOT_CONVERGED, ERR_NONFINITE, ERR_DIVERGED) if per_problem else (OK, NOT_CONVERGED))
+        return st, iters, relres, stat
+
+    def solve_batched_krylov(self, rhs, us, tol: float, maxit: int, restart: int = 30, per_problem: bool = False):
+        """Flexible GMRES(restart) of every problem in place on us[i], the batch's
+        network as preconditioner.  Returns (status, iters, relres, statuses);
+        per_problem as in solve_batched."""
+        m = len(rhs)
+        fp = (c_void_p * m)(*[_ptr(f, n * n) for f, n in zip(rhs, self.batch_sizes)])
+        up = (c_void_p * m)(*[_ptr(u, n * n, True) for u, n in zip(us, self.batch_sizes)])
+        iters = np.zeros(m, dtype=np.int32)
+        relres = np.zeros(m)
+        stat = np.zeros(m, dtype=np.int32)
+        st = self._L.mgcnn_solve_batched_krylov(self._h, m, fp, up, float(tol), int(maxit), int(restart),
+                                                iters.ctypes.data, relres.ctypes.data, stat.ctypes.data)
+        self._check(st, "mgcnn_solve_batched_krylov",
                     ok=(OK, NOT_CONVERGED, ERR_NONFINITE, ERR_DIVERGED) if per_problem else (OK, NOT_CONVERGED))
         return st, iters, relres, stat
 

@@ -206,6 +206,75 @@ def test_batched_divergence_limit(M):
         else:
             assert st6[i] == M.ERR_DIVERGED and rr6[i] > 1e6 and it6[i] < it0[i], i
 
+
+def _mixture(sizes, seed):
+    """Problems over the three coefficient families in turn (GRF, random blocks of
+    contrast 1e4, 16 x 16 checkerboard {1, 100})."""
+    rng = np.random.default_rng(seed)
+    ks, fs = [], []
+    for i, n in enumerate(sizes):
+        fam = i % 3
+        k = (inputs.lognormal_k(n, 0.1, rng) if fam == 0 else
+             inputs.random_blocks_k(n, rng) if fam == 1 else inputs.checkerboard_k(n))
+        ks.append(np.ascontiguousarray(k.ravel()))
+        fs.append(np.ascontiguousarray(inputs.normal_rhs(n, rng).ravel()))
+    return ks, fs
+
+
+def test_batched_krylov_solves_the_three_families(M):
+    """Batched FGMRES(30) with the V(1,0) network on the arithmetic coarse
+    coefficient: every problem of an uneven three-family batch reaches 1e-6
+    (checked by the oracle's FP64 residual), in the iteration count of the
+    single-problem FGMRES within two (the dot products sum in another order)."""
+    from oracle import operator as oop
+    sizes = [63, 127, 31, 255, 63, 127, 31, 63, 255]
+    ks, fs = _mixture(sizes, 31)
+    om = (0.8, 1.5, 1.0)
+    w = M.gmg_v10_weights()
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(w)
+    sv.set_option(sv.OPT_COARSE_K, 1)
+    sv.setup_batched(ks, sizes, gmg_omega=om)
+    us = [np.zeros(n * n) for n in sizes]
+    st, iters, relres, stat = sv.solve_batched_krylov(fs, us, 1e-6, 300, 30)
+    assert st == M.OK and (stat == M.OK).all(), stat
+    for i, n in enumerate(sizes):
+        r = fs[i].reshape(n, n) - oop.apply(oop.stencil_div(ks[i].reshape(n + 2, n + 2), (1.0, 0.5)),
+                                            us[i].reshape(n, n))
+        true = np.linalg.norm(r) / np.linalg.norm(fs[i])
+        assert true <= 1.05e-6 and abs(true - relres[i]) <= 1e-3 * true, (i, true, relres[i])
+        one = M.Solver(8, 1, 1, precision="mixed_bf16")
+        one.set_weights(w)
+        one.set_option(one.OPT_COARSE_K, 1)
+        one.setup_gmg(ks[i], n, om)
+        u1 = np.zeros(n * n)
+        st1, it1, h1 = one.solve_krylov(fs[i].copy(), u1, 1e-6, 300, 30)
+        assert st1 == M.OK and abs(it1 - iters[i]) <= 2, (i, it1, iters[i])
+
+
+def test_batched_krylov_edge_cases(M):
+    """A zero right-hand side gives u = 0 in no iterations; maxit = 0 reports
+    NOT_CONVERGED with the initial residual; a restart outside 1..64 is an error;
+    the stationary batched solve still works on the same setup afterwards."""
+    sizes = [31, 63, 31]
+    ks, fs = _mixture(sizes, 32)
+    fs[2] = np.zeros(31 * 31)
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16")
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_batched(ks, sizes, gmg_omega=0.8)
+    us = [np.full(n * n, 0.5) for n in sizes]
+    st, iters, relres, stat = sv.solve_batched_krylov(fs, us, 1e-6, 0, 30)
+    assert st == M.NOT_CONVERGED
+    assert stat[2] == M.OK and iters[2] == 0 and not us[2].any()
+    assert stat[0] == M.NOT_CONVERGED and iters[0] == 0 and relres[0] > 1e-6
+    for bad in (0, 65):
+        with pytest.raises(M.MGCNNError) as ei:
+            sv.solve_batched_krylov(fs, us, 1e-6, 10, bad)
+        assert ei.value.status == M.ERR_ARG
+    us = [np.zeros(n * n) for n in sizes]
+    st, iters, relres, stat = sv.solve_batched(fs[:1] + fs[1:], us, 1e-6, 200, per_problem=True)
+    assert stat[0] == M.OK and stat[2] == M.OK
+
 @pytest.mark.parametrize("cfg", [(0, True), (1, False)])
 def test_batched_first_cycle_against_the_oracle(M, cfg):
     """Every problem of an uneven batch over the three coefficient families, one
