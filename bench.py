@@ -391,6 +391,8 @@ def main():
     ap.add_argument("--workload", default=None, choices=["channelised", "grf", "batched256"])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--maxit", type=int, default=100, help="cycle limit of the batched solves")
+    ap.add_argument("--batch-solver", default="stationary", choices=["stationary", "krylov"],
+                    help="solver of the batched workload line (the default line reports both)")
     ap.add_argument("--divtol", type=int, default=6,
                     help="batched solves stop a problem as diverged once ||r||/||f|| > 10^divtol (0: never)")
     ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6, 7],
@@ -713,6 +715,8 @@ def main():
         # families, and the channelised field at 4095^2 (FP64 MGCNN, mixed MGCNN,
         # GMG, per-level achieved bandwidth)
         result["batched"] = run_batched(args, rank, world, dev, mgcnn, quiet=True)
+        if args.batch_solver == "stationary":
+            result["batched_krylov"] = run_batched(args, rank, world, dev, mgcnn, quiet=True, solver="krylov")
         result["channelised"] = run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, args.omega)
         if is_gmg:
             result["high_contrast_krylov"] = run_high_contrast(n, dev, stream, mgcnn, C, nd, nu, blob, args.omega, tol)
@@ -736,17 +740,20 @@ def bench_batched(args, rank, world, local):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2312_11093_gb300 import mgcnn
-    res = run_batched(args, rank, world, torch.device("cuda", local), mgcnn)
+    res = run_batched(args, rank, world, torch.device("cuda", local), mgcnn, solver=args.batch_solver)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_batched(args, rank, world, dev, mgcnn, quiet=False):
-    """256 uneven problems per step (setup + solve of the whole batch), one CUDA graph
-    launch per batch, tile shapes autotuned at setup; solves/s = problems that reach
-    the tolerance / step time."""
+def run_batched(args, rank, world, dev, mgcnn, quiet=False, solver="stationary"):
+    """256 uneven problems per step (setup + solve of the whole batch), tile shapes
+    autotuned at setup; solves/s = problems that reach the tolerance / step time.
+    solver "stationary": the stationary iteration, one CUDA graph launch per batch;
+    "krylov": batched FGMRES(30) with the network on the arithmetic coarse
+    coefficient as preconditioner, at most 300 inner iterations."""
+    krylov = solver == "krylov"
     import torch
     # all three coefficient families of the workload; a problem that does not reach
     # the tolerance within the cycle limit is a failure (counted, not a solve)
@@ -764,12 +771,20 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
     if args.divtol > 0:
         # a problem whose ||r||/||f|| exceeds 10^divtol is stopped as diverged (a failure)
         sv.set_option(sv.OPT_DIVTOL, args.divtol)
+    if krylov:
+        sv.set_option(sv.OPT_COARSE_K, 1)
+    maxit = 300 if krylov else args.maxit
+
+    def solve(ff, uu):
+        if krylov:
+            return sv.solve_batched_krylov(ff, uu, args.tol, maxit, 30, per_problem=True)
+        return sv.solve_batched(ff, uu, args.tol, maxit, per_problem=True)
 
     def step(kk, ff, uu):
         sv.setup_batched(kk, ns, gmg_omega=args.omega if is_gmg else None)
         for u in uu:
             u.zero_() if hasattr(u, "zero_") else u.fill(0.0)
-        return sv.solve_batched(ff, uu, args.tol, args.maxit, per_problem=True)
+        return solve(ff, uu)
 
     def barrier():
         if world > 1:
@@ -803,7 +818,7 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
 
     def e2e_step(uu):
         sv.setup_batched(kp, ns, gmg_omega=args.omega if is_gmg else None)
-        return sv.solve_batched(fp, uu, args.tol, args.maxit, per_problem=True)
+        return solve(fp, uu)
     e2e_step(ups[-1])
     barrier()
     t0 = time.perf_counter()
@@ -822,7 +837,9 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False):
            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
            "config": {"workload": f"batched{args.batch}_63-1023_mixture", "problems": args.batch,
                       "unknowns": unknowns, "tol": args.tol, "net": net, "omega": omega_record(args.omega, net),
-                      "maxit": args.maxit, "divtol": 10.0 ** args.divtol if args.divtol > 0 else None,
+                      "maxit": maxit, "divtol": 10.0 ** args.divtol if args.divtol > 0 else None,
+                      "solver": ("flexible GMRES(30), the network on the arithmetic coarse coefficient as "
+                                 "preconditioner" if krylov else "stationary iteration"),
                       "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single"},
            "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
            "converged": done, "failed": int((stat != 0).sum()),
