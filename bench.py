@@ -393,6 +393,7 @@ def main():
     ap.add_argument("--maxit", type=int, default=100, help="cycle limit of the batched solves")
     ap.add_argument("--batch-solver", default="stationary", choices=["stationary", "krylov"],
                     help="solver of the batched workload line (the default line reports both)")
+    ap.add_argument("--batch-restart", type=int, default=12, help="restart length of the batched FGMRES")
     ap.add_argument("--divtol", type=int, default=6,
                     help="batched solves stop a problem as diverged once ||r||/||f|| > 10^divtol (0: never)")
     ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6, 7],
@@ -751,8 +752,8 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False, solver="stationary")
     """256 uneven problems per step (setup + solve of the whole batch), tile shapes
     autotuned at setup; solves/s = problems that reach the tolerance / step time.
     solver "stationary": the stationary iteration, one CUDA graph launch per batch;
-    "krylov": batched FGMRES(30) with the network on the arithmetic coarse
-    coefficient as preconditioner, at most 300 inner iterations."""
+    "krylov": batched FGMRES(--batch-restart) with the network on the arithmetic
+    coarse coefficient as preconditioner, at most 300 inner iterations."""
     krylov = solver == "krylov"
     import torch
     # all three coefficient families of the workload; a problem that does not reach
@@ -777,7 +778,7 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False, solver="stationary")
 
     def solve(ff, uu):
         if krylov:
-            return sv.solve_batched_krylov(ff, uu, args.tol, maxit, 30, per_problem=True)
+            return sv.solve_batched_krylov(ff, uu, args.tol, maxit, args.batch_restart, per_problem=True)
         return sv.solve_batched(ff, uu, args.tol, maxit, per_problem=True)
 
     def step(kk, ff, uu):
@@ -838,8 +839,8 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False, solver="stationary")
            "config": {"workload": f"batched{args.batch}_63-1023_mixture", "problems": args.batch,
                       "unknowns": unknowns, "tol": args.tol, "net": net, "omega": omega_record(args.omega, net),
                       "maxit": maxit, "divtol": 10.0 ** args.divtol if args.divtol > 0 else None,
-                      "solver": ("flexible GMRES(30), the network on the arithmetic coarse coefficient as "
-                                 "preconditioner" if krylov else "stationary iteration"),
+                      "solver": (f"flexible GMRES({args.batch_restart}), the network on the arithmetic coarse "
+                                 "coefficient as preconditioner" if krylov else "stationary iteration"),
                       "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single"},
            "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
            "converged": done, "failed": int((stat != 0).sum()),

@@ -10,8 +10,9 @@
 // with the Hessenberg matrix, its Givens rotations and the residual estimate
 // per problem on the device (one thread per problem).  At the end of a cycle
 // (restart iterations, or the estimate below tol, or maxit) u += Z y and the
-// next cycle starts from the true FP64 residual.  The host reads one counter
-// per inner pass to stop early once no problem is left in its cycle.
+// next cycle starts from the true FP64 residual.  The classes run concurrently
+// on their own streams; the host reads one counter per inner pass to stop
+// early once no problem is left in its cycle.
 #include <algorithm>
 #include <cmath>
 
@@ -339,6 +340,19 @@ Status solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, d
                                                        P, Ly.fn, Ly.one);
     MG_LAUNCH("bk_init_kernel");
   }
+  // the classes run concurrently on their own streams between a fork and a join on `st`
+  auto fork = [&]() -> Status {
+    MG_CUDA(cudaEventRecord(c->bfork, st));
+    for (BatchClass& k : c->bcls) MG_CUDA(cudaStreamWaitEvent(k.stream, c->bfork, 0));
+    return {};
+  };
+  auto join = [&]() -> Status {
+    for (BatchClass& k : c->bcls) {
+      MG_CUDA(cudaEventRecord(k.done, k.stream));
+      MG_CUDA(cudaStreamWaitEvent(st, k.done, 0));
+    }
+    return {};
+  };
   int h_count = 0;
   auto read_counter = [&]() -> Status {
     MG_CUDA(cudaMemcpyAsync(&h_count, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -348,11 +362,13 @@ Status solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, d
   for (;;) {
     // true residual into v_0, ||r||^2, stopping tests, cycle start
     MG_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    MG_TRY(fork());
     for (BatchClass& k : c->bcls) {
       const size_t N = (size_t)k.n * k.n;
       const BkLayout Ly(k.B, m);
       double* D = k.kdbl.as<double>();
       const BkParams P{tol, c->divtol, maxit, m, k.B};
+      cudaStream_t st = k.stream;
       MG_TRY(launch_residual(k.f.as<double>(), k.u.as<double>(), k.op[0].as<double>(), k.kV.as<double>(), nullptr,
                              k.kpart.as<double>(), k.n, st, nullptr, k.B));
       const int nr = residual_blocks(N);
@@ -365,16 +381,19 @@ Status solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, d
                                                                    k.kint.as<int>() + kInner * k.B);
       MG_LAUNCH("bk_scale_kernel");
     }
+    MG_TRY(join());
     MG_TRY(read_counter());
     if (h_count == 0) break;
     for (int j = 0; j < m; ++j) {
       MG_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+      MG_TRY(fork());
       for (BatchClass& k : c->bcls) {
         const size_t N = (size_t)k.n * k.n;
         const BkLayout Ly(k.B, m);
         double* D = k.kdbl.as<double>();
         int* inner = k.kint.as<int>() + kInner * k.B;
         const BkParams P{tol, c->divtol, maxit, m, k.B};
+        cudaStream_t st = k.stream;
         double* V = k.kV.as<double>();
         double* Vj = V + (size_t)j * k.B * N;
         double* Wv = V + (size_t)(j + 1) * k.B * N;      // w is formed in the slot of v_{j+1}
@@ -407,15 +426,18 @@ Status solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, d
         bk_scale_kernel<<<pg, 256, 0, st>>>(Wv, D + Ly.inv, N, inner);
         MG_LAUNCH("bk_scale_kernel");
       }
+      MG_TRY(join());
       MG_TRY(read_counter());
       if (h_count == 0) break;
     }
     // u += Z y for every problem that ran a cycle
+    MG_TRY(fork());
     for (BatchClass& k : c->bcls) {
       const size_t N = (size_t)k.n * k.n;
       const BkLayout Ly(k.B, m);
       double* D = k.kdbl.as<double>();
       const BkParams P{tol, c->divtol, maxit, m, k.B};
+      cudaStream_t st = k.stream;
       bk_solve_y_kernel<<<grid_for(k.B, 128), 128, 0, st>>>(D, k.kint.as<int>(), P, Ly);
       MG_LAUNCH("bk_solve_y_kernel");
       bk_combine_kernel<<<dim3(grid_for(N, 256), k.B), 256, 0, st>>>(k.u.as<double>(), k.kZ.as<double>(), m,
@@ -425,6 +447,7 @@ Status solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, d
       bk_end_cycle_kernel<<<grid_for(k.B, 128), 128, 0, st>>>(k.kint.as<int>(), k.B);
       MG_LAUNCH("bk_end_cycle_kernel");
     }
+    MG_TRY(join());
   }
   // results back
   Status overall;
