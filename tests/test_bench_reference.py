@@ -6,6 +6,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -76,3 +78,17 @@ def test_algorithmic_bytes_per_unknown():
     assert bench.algorithmic_bytes("up2", n, 8) == 72 * 1023 * 1023
     levels = [255, 127, 63, 31, 15, 7, 3]
     assert bench.algorithmic_bytes("tail", n, 8) == sum((52 + 72) * m * m for m in levels)
+
+
+def test_omega_argument_and_record():
+    """--omega takes one Jacobi weight or three (finest, in between, coarsest); the
+    bench line records them for the analytic networks only."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.parse_omega("0.8") == 0.8
+    assert bench.parse_omega("0.8,1.5,1.0") == (0.8, 1.5, 1.0)
+    with pytest.raises(SystemExit):
+        bench.parse_omega("0.8,1.5")
+    assert bench.omega_record((0.8, 1.5, 1.0), "gmg_v10") == {"finest": 0.8, "in_between": 1.5, "coarsest": 1.0}
+    assert bench.omega_record(0.8, "gmg") == 0.8
+    assert bench.omega_record((0.8, 1.5, 1.0), "trained") is None
