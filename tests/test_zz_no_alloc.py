@@ -44,8 +44,8 @@ def _noalloc(M, op, f, u, r, n, stream=None):
 @pytest.mark.parametrize("on_stream", [False, True])
 def test_noalloc_residual_matches_context_residual_twice(M, on_stream):
     """Calls in a row (different problem sizes, so the shared scratch holds the
-    previous call's data; the largest is 4095^2, 16,384 partial sums, the whole
-    array) agree with mgcnn_residual within the tests' FP64 bar, on the legacy
+    previous call's data; the largest is 4095^2, 8,188 of the array's 8,192
+    partial sums) agree with mgcnn_residual within the tests' FP64 bar, on the legacy
     default stream and on a stream of the caller's."""
     stream = torch.cuda.Stream() if on_stream else None
     for n, seed in ((127, 1), (63, 2), (4095, 3), (255, 4)):
