@@ -943,18 +943,22 @@ def run_channelised(n, dev, stream, mgcnn, C, nd, nu, blob, is_gmg, tol, omega, 
     out["gmg"]["ms"] = (time.perf_counter() - t0) * 1e3
     sv64.close()
     if is_gmg:
-        # the mixed network with the arithmetic coarse coefficient as the
+        # the mixed and the FP64 network with the arithmetic coarse coefficient as the
         # preconditioner of flexible GMRES(30), where every stationary solve diverges
         out["mixed_krylov"] = krylov_solve_record(mgcnn, n, k_d, f_d, b, dev, stream, C, nd, nu, blob, omega, tol)
+        out["fp64_krylov"] = krylov_solve_record(mgcnn, n, k_d, f_d, b, dev, stream, C, nd, nu, blob, omega, tol,
+                                                 precision="fp64", warm=False)
     return out
 
 
-def krylov_solve_record(mgcnn, n, k_d, f_d, b, dev, stream, C, nd, nu, blob, omega, tol, maxit=300, restart=30):
-    """One setup + FGMRES(restart) solve with the mixed analytic network on the
-    arithmetic coarse coefficient (MGCNN_OPT_COARSE_K = 1), timed with CUDA events
-    after one untimed run; the final relative residual recomputed in FP64."""
+def krylov_solve_record(mgcnn, n, k_d, f_d, b, dev, stream, C, nd, nu, blob, omega, tol, maxit=300, restart=30,
+                        precision="mixed_bf16", warm=True):
+    """One setup + FGMRES(restart) solve with the analytic network (mixed or FP64)
+    on the arithmetic coarse coefficient (MGCNN_OPT_COARSE_K = 1), timed with CUDA
+    events (after one untimed run when `warm`); the final relative residual
+    recomputed in FP64."""
     import torch
-    sv = mgcnn.Solver(C, nd, nu, precision="mixed_bf16", b=b, stream=stream)
+    sv = mgcnn.Solver(C, nd, nu, precision=precision, b=b, stream=stream)
     sv.set_weights(blob)
     sv.set_option(sv.OPT_COARSE_K, 1)
     u = torch.zeros(n * n, dtype=torch.float64, device=dev)
@@ -963,7 +967,8 @@ def krylov_solve_record(mgcnn, n, k_d, f_d, b, dev, stream, C, nd, nu, blob, ome
         sv.setup_gmg(k_d, n, omega)
         u.zero_()
         return sv.solve_krylov(f_d, u, tol, maxit, restart)
-    once()
+    if warm:
+        once()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
@@ -977,8 +982,8 @@ def krylov_solve_record(mgcnn, n, k_d, f_d, b, dev, stream, C, nd, nu, blob, ome
     sv.close()
     return {"iters": it, "converged": bool(st == mgcnn.OK), "ms": e0.elapsed_time(e1),
             "relres_fp64": float(np.sqrt(rn2)) / fn,
-            "method": f"flexible GMRES({restart}), mixed V(1,0) network as right preconditioner, arithmetic coarse k, "
-                      "setup + solve"}
+            "method": f"flexible GMRES({restart}), {'mixed' if precision == 'mixed_bf16' else 'FP64'} V(1,0) network "
+                      "as right preconditioner, arithmetic coarse k, setup + solve"}
 
 
 def run_high_contrast(n, dev, stream, mgcnn, C, nd, nu, blob, omega, tol):
