@@ -69,16 +69,21 @@ __device__ __forceinline__ double bk_block_sum(double v, double* smem) {
 }
 
 // partial[(b * pstride + i) * nblk + blk] = sum over the block's pixels of
-// V_i[b] * w[b], i < nvec; V_i[b] = V + (i * B + b) * N, w[b] = w + b * wstride.
-// Problems with flag[b] == 0 are skipped (flag may be null).
+// V_i[b] * w[b], i < nvec <= kBkMaxVec; V_i[b] = V + (i * B + b) * N, w[b] = w +
+// b * wstride.  Problems with flag[b] == 0 are skipped (flag may be null).  A
+// vector's sum is reduced within each warp by shuffles, with no block-wide
+// barrier per vector (the next vectors' loads stay in flight); the warp sums are
+// added in warp order at the end.
+constexpr int kBkMaxVec = MGCNN_KRYLOV_MAX_RESTART + 1;
 __global__ void __launch_bounds__(kBkThreads) bk_dots_kernel(const double* __restrict__ V, int nvec,
                                                              const double* __restrict__ w, size_t wstride, size_t N,
                                                              int B, const int* __restrict__ flag,
                                                              double* __restrict__ partial, int pstride) {
-  __shared__ double smem[32];
+  __shared__ double wsum[kBkMaxVec][kBkThreads / 32];
   const int b = blockIdx.y;
   if (flag && !flag[b]) return;
   const int nblk = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t base = (size_t)blockIdx.x * kBkSpan + threadIdx.x;
   double wv[kBkPix];
 #pragma unroll
@@ -86,6 +91,7 @@ __global__ void __launch_bounds__(kBkThreads) bk_dots_kernel(const double* __res
     const size_t p = base + (size_t)t * kBkThreads;
     wv[t] = p < N ? w[(size_t)b * wstride + p] : 0.0;
   }
+#pragma unroll 2
   for (int i = 0; i < nvec; ++i) {
     const double* v = V + ((size_t)i * B + b) * N;
     double s = 0.0;
@@ -94,8 +100,15 @@ __global__ void __launch_bounds__(kBkThreads) bk_dots_kernel(const double* __res
       const size_t p = base + (size_t)t * kBkThreads;
       if (p < N) s += v[p] * wv[t];
     }
-    s = bk_block_sum(s, smem);
-    if (threadIdx.x == 0) partial[((size_t)b * pstride + i) * nblk + blockIdx.x] = s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) wsum[i][warp] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvec; i += kBkThreads) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kBkThreads / 32; ++q) t += wsum[i][q];
+    partial[((size_t)b * pstride + i) * nblk + blockIdx.x] = t;
   }
 }
 
@@ -115,18 +128,35 @@ __global__ void __launch_bounds__(1024) bk_reduce_kernel(const double* __restric
 }
 
 // y[b] += sign * sum_{i < cnt} coef[b * cstride + i] * V_i[b], cnt = nvec, or
-// count[b] when count is given; problems with flag[b] == 0 are skipped.
+// count[b] when count is given; problems with flag[b] == 0 are skipped.  A
+// thread's kCombPix pixels advance together through the vectors, so every step
+// issues kCombPix independent loads.
+constexpr int kCombPix = 4;
 __global__ void bk_combine_kernel(double* __restrict__ y, const double* __restrict__ V, int nvec,
                                   const int* __restrict__ count, const double* __restrict__ coef, int cstride,
                                   double sign, size_t N, int B, const int* __restrict__ flag) {
   const int b = blockIdx.y;
   if (flag && !flag[b]) return;
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
+  const size_t base = (size_t)blockIdx.x * blockDim.x * kCombPix + threadIdx.x;
   const int cnt = count ? count[b] : nvec;
-  double s = 0.0;
-  for (int i = 0; i < cnt; ++i) s += coef[(size_t)b * cstride + i] * V[((size_t)i * B + b) * N + p];
-  y[(size_t)b * N + p] += sign * s;
+  double s[kCombPix];
+#pragma unroll
+  for (int t = 0; t < kCombPix; ++t) s[t] = 0.0;
+#pragma unroll 2
+  for (int i = 0; i < cnt; ++i) {
+    const double c = coef[(size_t)b * cstride + i];
+    const double* v = V + ((size_t)i * B + b) * N;
+#pragma unroll
+    for (int t = 0; t < kCombPix; ++t) {
+      const size_t p = base + (size_t)t * blockDim.x;
+      if (p < N) s[t] += c * v[p];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kCombPix; ++t) {
+    const size_t p = base + (size_t)t * blockDim.x;
+    if (p < N) y[(size_t)b * N + p] += sign * s[t];
+  }
 }
 
 // x[b] *= s[b] for problems with flag[b]
@@ -413,7 +443,8 @@ Status solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, d
           MG_LAUNCH("bk_dots_kernel");
           bk_reduce_kernel<<<dim3(j + 1, k.B), 1024, 0, st>>>(k.kpart.as<double>(), nb, m + 1, inner, hc, m + 1);
           MG_LAUNCH("bk_reduce_kernel");
-          bk_combine_kernel<<<pg, 256, 0, st>>>(Wv, V, j + 1, nullptr, hc, m + 1, -1.0, N, k.B, inner);
+          bk_combine_kernel<<<dim3(grid_for(N, 256 * kCombPix), k.B), 256, 0, st>>>(Wv, V, j + 1, nullptr, hc, m + 1,
+                                                                                    -1.0, N, k.B, inner);
           MG_LAUNCH("bk_combine_kernel");
         }
         bk_dots_kernel<<<dim3(nb, k.B), kBkThreads, 0, st>>>(Wv, 1, Wv, N, N, k.B, inner, k.kpart.as<double>(), 1);
@@ -440,7 +471,7 @@ Status solve_batched_krylov(mgcnn_ctx* c, int nprob, const double* const* rhs, d
       cudaStream_t st = k.stream;
       bk_solve_y_kernel<<<grid_for(k.B, 128), 128, 0, st>>>(D, k.kint.as<int>(), P, Ly);
       MG_LAUNCH("bk_solve_y_kernel");
-      bk_combine_kernel<<<dim3(grid_for(N, 256), k.B), 256, 0, st>>>(k.u.as<double>(), k.kZ.as<double>(), m,
+      bk_combine_kernel<<<dim3(grid_for(N, 256 * kCombPix), k.B), 256, 0, st>>>(k.u.as<double>(), k.kZ.as<double>(), m,
                                                                      k.kint.as<int>() + kCyc * k.B, D + Ly.y, m, 1.0,
                                                                      N, k.B, nullptr);
       MG_LAUNCH("bk_combine_kernel");

@@ -12,7 +12,7 @@ namespace mgcnn {
 namespace {
 
 constexpr int KB = 256;            // threads per block
-constexpr int KPIX = 4;            // pixels per thread
+constexpr int KPIX = 8;            // pixels per thread
 constexpr int KCHUNK = KB * KPIX;  // pixels per block
 
 __device__ __forceinline__ double block_sum_d(double v, double* smem) {
@@ -46,22 +46,43 @@ __global__ void __launch_bounds__(KB) apply_kernel(const double* __restrict__ op
   }
 }
 
-// partial[i * gridDim.x + b] = sum over block b's pixels of V_i[p] w[p], i < nvec.
+// partial[i * gridDim.x + b] = sum over block b's pixels of V_i[p] w[p], i < nvec
+// (nvec <= kMaxDots).  Each thread keeps its KPIX values of w in registers and
+// streams the basis vectors past them; a vector's sum is reduced within each
+// warp by shuffles (no block-wide barrier per vector, so the loads of the next
+// vectors stay in flight), the eight warp sums meet in shared memory once at the
+// end and are added in warp order.
+constexpr int kMaxDots = 72;
 __global__ void __launch_bounds__(KB) dots_partial_kernel(const double* __restrict__ V, int nvec,
                                                           const double* __restrict__ w, size_t N,
                                                           double* __restrict__ partial) {
-  __shared__ double smem[32];
+  __shared__ double wsum[kMaxDots][KB / 32];
   const size_t base = (size_t)blockIdx.x * KCHUNK + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double wv[KPIX];
+#pragma unroll
+  for (int k = 0; k < KPIX; ++k) {
+    const size_t p = base + (size_t)k * KB;
+    wv[k] = p < N ? w[p] : 0.0;
+  }
+#pragma unroll 2
   for (int i = 0; i < nvec; ++i) {
     const double* v = V + (size_t)i * N;
     double acc = 0.0;
 #pragma unroll
     for (int k = 0; k < KPIX; ++k) {
       const size_t p = base + (size_t)k * KB;
-      if (p < N) acc = fma(v[p], w[p], acc);
+      if (p < N) acc = fma(v[p], wv[k], acc);
     }
-    acc = block_sum_d(acc, smem);
-    if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) wsum[i][warp] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvec; i += KB) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < KB / 32; ++q) t += wsum[i][q];
+    partial[(size_t)i * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -76,16 +97,31 @@ __global__ void __launch_bounds__(KB) dots_final_kernel(const double* __restrict
 }
 
 // y[p] <- y[p] + sign * sum_i coef[i] V_i[p], the terms added in the order i = 0, 1, ...
+// The KPIX pixels of a thread advance together through the vectors, so every
+// step of the loop issues KPIX independent loads.
 __global__ void __launch_bounds__(KB) combine_kernel(double* __restrict__ y, const double* __restrict__ V, int nvec,
                                                      const double* __restrict__ coef, double sign, size_t N) {
   const size_t base = (size_t)blockIdx.x * KCHUNK + threadIdx.x;
+  double acc[KPIX];
 #pragma unroll
   for (int k = 0; k < KPIX; ++k) {
     const size_t p = base + (size_t)k * KB;
-    if (p >= N) continue;
-    double acc = y[p];
-    for (int i = 0; i < nvec; ++i) acc = fma(sign * coef[i], V[(size_t)i * N + p], acc);
-    y[p] = acc;
+    acc[k] = p < N ? y[p] : 0.0;
+  }
+#pragma unroll 2
+  for (int i = 0; i < nvec; ++i) {
+    const double c = sign * coef[i];
+    const double* v = V + (size_t)i * N;
+#pragma unroll
+    for (int k = 0; k < KPIX; ++k) {
+      const size_t p = base + (size_t)k * KB;
+      if (p < N) acc[k] = fma(c, v[p], acc[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KPIX; ++k) {
+    const size_t p = base + (size_t)k * KB;
+    if (p < N) y[p] = acc[k];
   }
 }
 
@@ -126,6 +162,7 @@ Status launch_apply_A(const double* op, const double* x, double* y, int n, cudaS
 
 Status launch_block_dots(const double* V, int nvec, const double* w, size_t N, double* partial, double* out,
                          cudaStream_t st) {
+  if (nvec < 1 || nvec > kMaxDots) return make_status(MGCNN_ERR_ARG, "%d dot products, at most %d", nvec, kMaxDots);
   const int nb = chunks(N);
   dots_partial_kernel<<<nb, KB, 0, st>>>(V, nvec, w, N, partial);
   MG_LAUNCH("dots_partial_kernel");
