@@ -449,7 +449,9 @@ int mgcnn_get_weights(mgcnn_ctx* ctx, double* w, size_t count);
  * each problem of mgcnn_solve_batched once ||r_k||/||f|| > 10^d, before cycle k,
  * with status MGCNN_ERR_DIVERGED (iters = k, relres[k] recorded, u the iterate
  * u_k); the usual divergence test of iterative solvers, which ends a failing
- * problem long before maxit.  Errors: ARG for a value outside 0..300. */
+ * problem long before maxit.  mgcnn_solve_batched_krylov applies it to the true
+ * residual before each restart cycle; mgcnn_solve_krylov does not use it.
+ * Errors: ARG for a value outside 0..300. */
 /* MGCNN_OPT_COARSE_K (default 0): how the divergence form's k reaches the
  * coarse grids before rediscretisation (Sec. 2.3 leaves it open).  0: full
  * weighting of log k (a geometric mean), 1: full weighting of k itself (an
