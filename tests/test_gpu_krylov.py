@@ -142,3 +142,30 @@ def test_krylov_arguments_and_limits(M):
     assert st == M.NOT_CONVERGED and it == 3 and len(h) == 4
     st, it, h = sv.solve_krylov(np.zeros(n * n), u, 1e-8, 10)
     assert st == M.OK and it == 0 and not u.any()
+
+
+def test_mixed_fgmres_on_the_papers_problem(M):
+    """The paper's own test problem at 255^2 (non-divergence form, white-noise
+    coefficient with mesh Reynolds numbers up to 1000, v = (sin 0.5, cos 0.5),
+    f = 1), on which the stationary V(1,0) network diverges: as the FGMRES(30)
+    preconditioner, with per-level weights, the mixed network reaches 1e-8 in the
+    oracle's iteration count within a few (oracle: 63), checked by the oracle's
+    own residual."""
+    from oracle import gmg as ogmg
+    n = 255
+    v = (float(np.sin(0.5)), float(np.cos(0.5)))
+    mu = inputs.paper_white_noise_mu(n, np.random.default_rng(n))
+    f = inputs.unit_rhs(n)
+    sts = oop.level_stencils_nondiv(mu, v, num_levels(n))
+    oms = ogmg.level_omegas(len(sts), LEVEL_OMEGA)
+    _, it_o, h_o = okr.fgmres(lambda x: oop.apply(sts[0], x), lambda r: ogmg.vcycle(sts, r, 1, 0, oms), f, None,
+                              1e-8, 300, 30)
+    assert h_o[-1] <= 1e-8
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16", pde="nondiv", b=v)
+    sv.set_weights(M.gmg_v10_weights())
+    sv.setup_gmg(mu.ravel().copy(), n, LEVEL_OMEGA)
+    u = np.zeros(n * n)
+    st, it, h = sv.solve_krylov(f.ravel().copy(), u, 1e-8, 300, restart=30)
+    assert st == M.OK and abs(it - it_o) <= 5, (it, it_o)
+    r = f - oop.apply(sts[0], u.reshape(n, n))
+    assert np.linalg.norm(r) / np.linalg.norm(f) <= 1.05e-8
