@@ -409,6 +409,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and channelised workloads reported beside the headline")
     ap.add_argument("--krylov", action="store_true", help="also time flexible GMRES with the network as preconditioner")
+    ap.add_argument("--paper-table", action="store_true",
+                    help="also record iterations against n (31..4095) on the paper's own test problem")
     ap.add_argument("--bpx", action="store_true",
                     help="also time CG with the symmetric network in its BPX form (same k field, b = 0, FP64, tol 1e-8)")
     args = ap.parse_args()
@@ -710,6 +712,8 @@ def main():
                                 "relres_bnorm": float(mh[-1]), "tol": 1e-8, "converged": bool(mst == mgcnn.OK),
                                 "method": "MINRES, same preconditioner and problem, solve only"}
         svb.close()
+    if args.paper_table and rank == 0:
+        result["paper_problem"] = run_paper_table(dev, stream, mgcnn, args.omega)
     sv.close()
     if not args.no_extras and rank == 0 and world == 1:
         # the other two GPU workloads: the uneven batch over three coefficient
@@ -855,6 +859,54 @@ def run_batched(args, rank, world, dev, mgcnn, quiet=False, solver="stationary")
                    "d2h_bytes_per_step": int(sum(f.nbytes for f in fs)), "ms_per_step": e2e_ms},
            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None}
     return res
+
+
+def run_paper_table(dev, stream, mgcnn, omega, sizes=(31, 63, 127, 255, 511, 1023, 2047, 4095), tol=1e-8):
+    """Iterations against n on the paper's own test problem (Sec. 4.1: the
+    non-divergence operator with white-noise coef in [1e-3, 1], v = (sin 0.5,
+    cos 0.5), f = 1, tol 1e-8), the shape of its Table channels_double: classical
+    GMG with the paper's GMG settings (weight 0.67, V(3,3), two levels fewer than
+    MGCNN) and the mixed 8-channel V(1,0) network with per-level weights as the
+    FGMRES(30) preconditioner (its stationary iteration diverges on this
+    problem).  One draw per size; time from CUDA events, setup included."""
+    import torch
+    v = (math.sin(0.5), math.cos(0.5))
+    rows = []
+    for n in sizes:
+        rng = np.random.default_rng(100 * n)
+        mu = torch.from_numpy(np.ascontiguousarray(inputs.paper_white_noise_mu(n, rng).ravel())).to(dev)
+        f = torch.from_numpy(np.ascontiguousarray(inputs.unit_rhs(n).ravel())).to(dev)
+        u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+        L = int(round(math.log2(n + 1))) - 1
+        row = {"n": n}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        # classical GMG, the paper's settings
+        sg = mgcnn.Solver(8, 1, 1, pde="nondiv", b=v, levels=max(1, L - 2), stream=stream)
+        sg.set_weights(np.zeros(sg.weight_count))
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        sg.setup(mu, n)
+        st, it, h = sg.gmg_solve(f, u, tol, 400, 3, 3, 0.67)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        row["gmg_v33"] = {"iters": it, "converged": bool(st == mgcnn.OK), "ms": e0.elapsed_time(e1)}
+        sg.close()
+        # the mixed network as the FGMRES preconditioner
+        sk = mgcnn.Solver(8, 1, 1, precision="mixed_bf16", pde="nondiv", b=v, stream=stream)
+        sk.set_weights(mgcnn.gmg_v10_weights())
+        u.zero_()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        sk.setup_gmg(mu, n, omega)
+        st, it, h = sk.solve_krylov(f, u, tol, 400, 30)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        row["mgcnn_v10_fgmres"] = {"iters": it, "converged": bool(st == mgcnn.OK), "ms": e0.elapsed_time(e1)}
+        sk.close()
+        rows.append(row)
+    return {"problem": "Sec. 4.1 test problem: non-divergence form, white-noise coef in [1e-3, 1], "
+                       "v = (sin 0.5, cos 0.5), f = 1, one draw per size", "tol": tol, "rows": rows}
 
 
 def time_setup_network(n, dev, stream, mgcnn, k_d, b, reps=5):
