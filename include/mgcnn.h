@@ -372,8 +372,9 @@ int mgcnn_solve_batched_krylov(mgcnn_ctx* ctx, int nprob, const double* const* r
  * gradient with respect to every weight of the setup and solve networks,
  * from a hand-written adjoint (reverse sweep over the cycles with per-cycle
  * checkpointing: only r_k is kept, B's intermediates are recomputed).
- * coeff[i]: nodal k of problem i, (n[i]+2)^2 doubles; rhs[i]: f, n[i]^2
- * doubles; host or device.  Problems of equal n are batched together.
+ * coeff[i]: nodal k of problem i, (n[i]+2)^2 doubles (the non-divergence
+ * form: mu on the n[i]^2 interior nodes); rhs[i]: f, n[i]^2 doubles; host or
+ * device.  Problems of equal n are batched together.
  * Arithmetic: FP64 for an FP64 context, FP32 otherwise (gradients are
  * accumulated in FP64).  grad (weight_count doubles, host or device) may be
  * NULL to evaluate the loss only.  Divergence form only.

@@ -920,7 +920,6 @@ static Status loss_grad_any(mgcnn_ctx* c, int nprob, const double* const* coeff,
   if (!c->have_weights) return make_status(MGCNN_ERR_STATE, "weights not set");
   if (c->symmetric) return make_status(MGCNN_ERR_STATE, "training is not available for the symmetric network");
   if (nprob < 1 || K < 1 || K > 64) return make_status(MGCNN_ERR_ARG, "need nprob >= 1 and 1 <= K <= 64");
-  if (c->cfg.pde != MGCNN_PDE_DIV_HARMONIC) return make_status(MGCNN_ERR_ARG, "training supports the divergence form");
   for (int i = 0; i < nprob; ++i) {
     if (!coeff[i] || !rhs[i]) return make_status(MGCNN_ERR_ARG, "null problem array %d", i);
     if (levels_of(n[i]) < 1 || levels_of(n[i]) > kMaxLevels) return make_status(MGCNN_ERR_SIZE, "bad n=%d", n[i]);

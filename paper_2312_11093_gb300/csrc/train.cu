@@ -615,7 +615,8 @@ void train_release(mgcnn_ctx* c) {
 }
 
 // Loss (and gradient) over problems grouped by size.  Arrays: coeff[i] nodal k
-// ((n_i+2)^2) and rhs[i] (n_i^2), device or host.
+// ((n_i+2)^2; the non-divergence form: mu on the n_i^2 interior nodes) and
+// rhs[i] (n_i^2), device or host.
 template <typename T>
 Status loss_grad_impl(mgcnn_ctx* c, int nprob, const double* const* coeff, const double* const* rhs, const int* ns,
                       int K, double* loss, bool want_grad) {
@@ -655,19 +656,26 @@ Status loss_grad_impl(mgcnn_ctx* c, int nprob, const double* const* coeff, const
     MG_TRY(alloc_group(c, g, n, B, K, sizeof(T)));
     const size_t N0 = g.lv[0].N();
     // operators and features per problem; f into r_0
+    const bool div = c->cfg.pde == MGCNN_PDE_DIV_HARMONIC;
     for (int b = 0; b < B; ++b) {
       const int i = members[b];
       const int m = n + 2;
       double* k0 = g.coef.as<double>();
       double* k1 = k0 + (size_t)m * m;
-      MG_CUDA(cudaMemcpyAsync(k0, coeff[i], (size_t)m * m * sizeof(double), cudaMemcpyDefault, st));
+      const size_t cn = div ? (size_t)m * m : N0;
+      MG_CUDA(cudaMemcpyAsync(k0, coeff[i], cn * sizeof(double), cudaMemcpyDefault, st));
       for (int l = 0; l < g.L; ++l) {
         const int nlv = g.lv[l].n;
         double* opl = g.op[l].as<double>() + (size_t)b * 5 * g.lv[l].N();
         double* kin = (l % 2 == 0) ? k0 : k1;
         double* kout = (l % 2 == 0) ? k1 : k0;
-        MG_TRY(launch_stencil_div(kin, opl, nlv, c->cfg.bx, c->cfg.by, st));
-        if (l + 1 < g.L) MG_TRY(launch_restrict_k(kin, kout, nlv + 2, st, 1, c->coarse_k_arith != 0));
+        if (div) {
+          MG_TRY(launch_stencil_div(kin, opl, nlv, c->cfg.bx, c->cfg.by, st));
+          if (l + 1 < g.L) MG_TRY(launch_restrict_k(kin, kout, nlv + 2, st, 1, c->coarse_k_arith != 0));
+        } else {
+          MG_TRY(launch_stencil_nondiv(kin, opl, nlv, c->cfg.bx, c->cfg.by, st));
+          if (l + 1 < g.L) MG_TRY(launch_inject_mu(kin, kout, nlv, st));
+        }
       }
       MG_TRY(launch_features<T>(g.op[0].as<double>() + (size_t)b * 5 * N0, g.feat.as<T>() + (size_t)b * N0 * kFeatures,
                                 n, st));

@@ -316,11 +316,12 @@ class Solver:
         self.n = int(n)
 
     # -- training (Sec. 3.4) ---------------------------------------------------
-    @staticmethod
-    def _problems(problems):
-        """[(k, f, n), ...] -> ctypes arrays of pointers and sizes (arrays are kept alive by the caller)."""
+    def _problems(self, problems):
+        """[(k, f, n), ...] -> ctypes arrays of pointers and sizes (arrays are kept alive by the caller).
+        k: nodal k on (n+2)^2 nodes, or mu on the n^2 interior nodes for the non-divergence form."""
         m = len(problems)
-        kp = (c_void_p * m)(*[_ptr(k, (n + 2) * (n + 2)) for k, f, n in problems])
+        div = self.cfg.pde == PDE["div"]
+        kp = (c_void_p * m)(*[_ptr(k, (n + 2) * (n + 2) if div else n * n) for k, f, n in problems])
         fp = (c_void_p * m)(*[_ptr(f, n * n) for k, f, n in problems])
         ns = (c_int * m)(*[int(n) for k, f, n in problems])
         return m, kp, fp, ns

@@ -26,6 +26,8 @@ if os.path.dirname(HERE) not in sys.path:
 from paper_2312_11093_gb300 import inputs, mgcnn  # noqa: E402
 
 WEIGHTS = os.path.join(HERE, "weights", "mgcnn_c8_trained.npy")
+# weights trained on the paper's own test family (PAPER_SCHEDULE, workload "paper")
+PAPER_WEIGHTS = os.path.join(HERE, "weights", "mgcnn_c8_paper_problem.npy")
 
 
 def _autograd():
@@ -100,6 +102,24 @@ def make_batch(step: int, sizes=(63, 127), per_size=32, corr_len: float = 0.1):
     return probs
 
 
+PAPER_V = (float(np.sin(0.5)), float(np.cos(0.5)))
+
+
+def make_paper_batch(step: int, sizes=(31, 63, 127, 255), per_size=(16, 8, 4, 2), corr_len: float = 0.0):
+    """Fresh problems of the paper's own test family (Sec. 4.1: the non-divergence
+    operator with white-noise coef in [1e-3, 1], mu = coef h, v = (sin 0.5, cos 0.5)),
+    white-noise right-hand sides; the coefficient array is mu on the n^2 interior nodes."""
+    rng = np.random.default_rng(2000 + step)
+    counts = per_size if isinstance(per_size, (list, tuple)) else [per_size] * len(sizes)
+    probs = []
+    for n, m in zip(sizes, counts):
+        for _ in range(m):
+            mu = inputs.paper_white_noise_mu(n, rng)
+            f = inputs.normal_rhs(n, rng)
+            probs.append((np.ascontiguousarray(mu.ravel()), np.ascontiguousarray(f.ravel()), n))
+    return probs
+
+
 # Training schedule.  The 63^2 / 127^2 recipe alone (5-6 levels) gives weights
 # that diverge on 9-11 levels, and continuing from them on larger grids starts
 # from exploding losses.  Every batch therefore mixes the sizes of the paper's
@@ -108,6 +128,9 @@ def make_batch(step: int, sizes=(63, 127), per_size=32, corr_len: float = 0.1):
 # K = 8, Adam at lr 1e-4, then 3e-5 (the paper decays its rate stepwise; at 1e-3
 # the K-cycle loss of this mix blows up within the first hundred steps).
 SCHEDULE = [((63, 127, 255, 511), (16, 8, 4, 2), 1500, 1e-4), ((63, 127, 255, 511), (16, 8, 4, 2), 500, 3e-5)]
+# The paper's own test family (make_paper_batch): the sizes of its progressive
+# schedule up to 255^2 in every batch, 1200 steps at lr 1e-4, then 300 at 3e-5.
+PAPER_SCHEDULE = [((31, 63, 127, 255), (16, 8, 4, 2), 1200, 1e-4), ((31, 63, 127, 255), (16, 8, 4, 2), 300, 3e-5)]
 # The recipe on 63^2 / 127^2 only (batch 64, 2000 steps, lr 1e-3).
 RECIPE_63_127 = [((63, 127), (32, 32), 2000, 1e-3)]
 
@@ -143,7 +166,7 @@ def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int 
           log_every: int = 50, out: str | None = WEIGHTS, precision: str = "mixed_bf16", per_size=None,
           setup_scale: int = 0, mg_transfers: bool = True, schedule=None, snapshot_every: int = 25,
           spike: float = 50.0, max_restarts: int = 8, init: np.ndarray | None = None, hard_every: int = 0,
-          hard_sizes=(63, 127, 255, 511)):
+          hard_sizes=(63, 127, 255, 511), workload: str = "grf"):
     """Run the schedule (or a single phase when steps/lr/per_size are given) and
     return (weights, loss history).
 
@@ -158,12 +181,19 @@ def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int 
     size in hard_sizes and replace its right-hand side by the slowest residual
     mode of the current network (`slow_modes`); these problems join every batch
     until the next refresh, so the loss sees the mode that limits Eq. 1.
-    init: start from these weights instead of the random initialisation."""
+    init: start from these weights instead of the random initialisation.
+    workload: "grf" (lognormal k, divergence form, b = (1, 0.5)) or "paper" (the
+    paper's non-divergence test family, make_paper_batch)."""
+    paper = workload == "paper"
+    if paper and hard_every:
+        raise ValueError("hard_every draws divergence-form problems: use it with the grf workload")
+    batch_fn = make_paper_batch if paper else make_batch
     if schedule is None:
         schedule = SCHEDULE if steps is None else [((63, 127), per_size or (32, 32), steps, lr or 1e-3)]
 
     def fresh(weights):
-        sv = mgcnn.Solver(C, 1, 1, precision=precision, b=(1.0, 0.5), scale_by_diag=setup_scale, input_diag=True)
+        sv = mgcnn.Solver(C, 1, 1, precision=precision, b=PAPER_V if paper else (1.0, 0.5),
+                          pde="nondiv" if paper else "div", scale_by_diag=setup_scale, input_diag=True)
         sv.set_weights(weights)
         return sv
 
@@ -177,11 +207,11 @@ def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int 
     for sizes, counts, nsteps, plr in schedule:
         for _ in range(nsteps):
             if hard_every and step % hard_every == 0:
-                base = make_batch(500000 + step, hard_sizes, 1)
+                base = batch_fn(500000 + step, hard_sizes, 1)
                 modes = slow_modes(sv.get_weights(), base, C=C, precision=precision, seed=step)
                 hard = [(k, v, n) for (k, _, n), v in zip(base, modes)]
             try:
-                loss = sv.train_step(make_batch(step, sizes, counts) + hard, K, plr)
+                loss = sv.train_step(batch_fn(step, sizes, counts) + hard, K, plr)
             except mgcnn.MGCNNError as err:
                 if err.status != mgcnn.ERR_NONFINITE:
                     raise
@@ -215,6 +245,12 @@ def train(steps: int | None = None, K: int = 8, lr: float | None = None, C: int 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--workload", default="grf", choices=["grf", "paper"],
+                    help="grf: the lognormal divergence-form family (SCHEDULE); paper: the paper's own "
+                         "non-divergence test family (PAPER_SCHEDULE)")
     args = ap.parse_args()
-    train(out=args.out)
+    if args.workload == "paper":
+        train(schedule=PAPER_SCHEDULE, workload="paper", out=args.out or PAPER_WEIGHTS)
+    else:
+        train(out=args.out or WEIGHTS)

@@ -128,3 +128,73 @@ def test_training_steps_reduce_loss(M):
     sv.set_weights(init_weights(8, 1, 1, np.random.default_rng(0)))
     losses = [sv.train_step(make_batch(s, sizes=(31,), per_size=(8,)), 4, 1e-3) for s in range(40)]
     assert np.mean(losses[-5:]) < 0.7 * np.mean(losses[:5])
+
+
+def test_nondiv_loss_and_gradient_match_oracle_adjoint(M):
+    """The training path on the paper's non-divergence operator (white-noise mu =
+    coef h, v = (sin 0.5, cos 0.5), coarse mu injected): loss and gradient equal
+    the oracle adjoint's on the oracle's operators."""
+    v = (float(np.sin(0.5)), float(np.cos(0.5)))
+    rng = np.random.default_rng(21)
+    gpu, ora = [], []
+    for n in (7, 15, 31, 15):
+        mu = inputs.paper_white_noise_mu(n, rng)
+        f = inputs.normal_rhs(n, rng)
+        gpu.append((np.ascontiguousarray(mu.ravel()), np.ascontiguousarray(f.ravel()), n))
+        ora.append((oop.level_stencils_nondiv(mu, v, num_levels(n)), f))
+    C, nd, nu, K = 8, 1, 1, 3
+    w = omg.random_weights(C, nd, nu, np.random.default_rng(22), scale=0.5)
+    L_ref, g_ref = oadj.loss_and_grad(w, ora, K, scale_by_diag=0, input_diag=True)
+    sv = M.Solver(C, nd, nu, precision="fp64", pde="nondiv", b=v, scale_by_diag=0, input_diag=True)
+    sv.set_weights(M.pack_weights(w, C, nd, nu))
+    L, g = sv.loss_grad(gpu, K)
+    assert abs(L - L_ref) <= 1e-12 * abs(L_ref)
+    g_ref_blob = M.pack_weights(g_ref, C, nd, nu)
+    assert np.linalg.norm(g - g_ref_blob) <= 1e-10 * np.linalg.norm(g_ref_blob)
+
+
+def test_network_trained_on_the_papers_problem(M):
+    """Weights trained on the paper's own test family (train.PAPER_SCHEDULE, sizes
+    31^2 ... 255^2): on a test draw of the paper's problem (f = 1) the learned
+    network's stationary iteration converges where the analytic V(1,0) network
+    diverges.  FP64 at 31^2: the oracle's cycle count and iterate (same weights,
+    the oracle's Algorithm 2 and 3); mixed at 127^2: 1e-8, checked by the oracle's
+    own residual."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_2312_11093_gb300.train import PAPER_V, PAPER_WEIGHTS
+    blob = np.ascontiguousarray(np.load(PAPER_WEIGHTS), dtype=np.float64)
+    w = bench.unpack_blob(blob, 8, 1, 1)
+    n = 31
+    mu = inputs.paper_white_noise_mu(n, np.random.default_rng(100 * n))
+    f = inputs.unit_rhs(n)
+    sts = oop.level_stencils_nondiv(mu, PAPER_V, num_levels(n))
+    s = omg.setup(w, sts, scale_by_diag=False)
+    u_o, it_o, hist_o, _ = omg.stationary_solve(w, s, sts[0], f, None, 1e-8, 400, input_diag=True)
+    assert hist_o[-1] <= 1e-8
+    sv = M.Solver(8, 1, 1, precision="fp64", pde="nondiv", b=PAPER_V, scale_by_diag=0, input_diag=True)
+    sv.set_weights(blob)
+    sv.setup(mu.ravel().copy(), n)
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(f.ravel().copy(), u, 1e-8, 400)
+    assert st == M.OK and it == it_o
+    assert np.linalg.norm(u - u_o.ravel()) <= 1e-10 * np.linalg.norm(u_o)
+    n = 127
+    mu = inputs.paper_white_noise_mu(n, np.random.default_rng(100 * n))
+    f = inputs.unit_rhs(n)
+    sv = M.Solver(8, 1, 1, precision="mixed_bf16", pde="nondiv", b=PAPER_V, scale_by_diag=0, input_diag=True)
+    sv.set_weights(blob)
+    sv.setup(mu.ravel().copy(), n)
+    u = np.zeros(n * n)
+    st, it, hist = sv.solve(f.ravel().copy(), u, 1e-8, 300)
+    assert st == M.OK
+    r = f - oop.apply(oop.stencil_nondiv(mu, PAPER_V), u.reshape(n, n))
+    assert np.linalg.norm(r) / np.linalg.norm(f) <= 1.05e-8
+    an = M.Solver(8, 1, 1, precision="mixed_bf16", pde="nondiv", b=PAPER_V)
+    an.set_weights(M.gmg_v10_weights())
+    an.setup_gmg(mu.ravel().copy(), n, 0.8)
+    u = np.zeros(n * n)
+    with pytest.raises(M.MGCNNError):
+        an.solve(f.ravel().copy(), u, 1e-8, 300, raise_on_limit=True)
