@@ -74,3 +74,30 @@ def test_loss_spike_counts_as_a_blow_up(scripted):
 def test_repeated_blow_ups_end_the_run(scripted):
     with pytest.raises(RuntimeError):
         run([1.0] * 6 + ["nonfinite"] * 3, 9, max_restarts=2)
+
+
+def test_paper_batch_is_the_papers_family():
+    """make_paper_batch draws the paper's white-noise coefficient as mu = coef h on
+    the interior nodes (coef in [1e-3, 1]) with white-noise right-hand sides, per
+    size and count, reproducibly per step."""
+    probs = T.make_paper_batch(3, sizes=(15, 31), per_size=(2, 1))
+    assert [n for _, _, n in probs] == [15, 15, 31]
+    for mu, f, n in probs:
+        assert mu.shape == (n * n,) and f.shape == (n * n,)
+        coef = mu * (n + 1)
+        assert coef.min() >= 1e-3 * (1 - 1e-12) and coef.max() <= 1.0
+    again = T.make_paper_batch(3, sizes=(15, 31), per_size=(2, 1))
+    assert all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(probs, again))
+    assert not np.array_equal(T.make_paper_batch(4, sizes=(15,), per_size=1)[0][0], probs[0][0])
+
+
+def test_paper_workload_rejects_divergence_form_hard_modes():
+    with pytest.raises(ValueError):
+        T.train(schedule=[((15,), (1,), 1, 1e-4)], workload="paper", hard_every=5, out=None)
+
+
+def test_shipped_paper_weights_fit_the_network():
+    """The shipped weights of the paper-family network are one finite blob of the
+    8-channel, one-down-one-up layout."""
+    w = np.load(T.PAPER_WEIGHTS)
+    assert w.dtype == np.float64 and w.shape == (mgcnn.weight_count(8, 1, 1),) and np.isfinite(w).all()
